@@ -1,0 +1,413 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Every function returns (ok, detail).  Each takes the oracle ``variant`` so the
+same pins can be run against deliberately wrong builds of the oracle
+(test_oracle_plants.py): a pin set is only trusted if a plausible mistake in
+the oracle makes at least one of them fail.
+"""
+from __future__ import annotations
+
+import math
+import os
+
+import numpy as np
+
+import oracle
+from paper_1808_00270_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def closed_form_vacf(t, K0, tau, mass=1.0):
+    """Normalised VACF of a free particle with K(t) = K0 exp(-t/tau): the
+    Laplace-domain solution of M dC/dt = -int K(t-s) C(s) ds has poles at
+    -1/(2 tau) +- i Omega, Omega^2 = K0/M - 1/(4 tau^2)."""
+    om2 = K0 / mass - 1.0 / (4.0 * tau * tau)
+    t = np.asarray(t, dtype=float)
+    if om2 > 0:
+        om = math.sqrt(om2)
+        return np.exp(-t / (2 * tau)) * (np.cos(om * t) + np.sin(om * t) / (2 * tau * om))
+    om = math.sqrt(-om2)
+    return np.exp(-t / (2 * tau)) * (np.cosh(om * t) + np.sinh(om * t) / (2 * tau * om))
+
+
+# ---------------------------------------------------------------- Philox --
+def pin_philox_kat(variant=0):
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                rows.append([int(w, 16) for w in line.split()])
+    for r in rows:
+        got = oracle.philox4x32_10(r[:4], r[4:6])
+        if list(got) != r[6:]:
+            return False, f"philox mismatch {got} vs {r[6:]}"
+    return True, f"{len(rows)} vectors"
+
+
+def pin_gauss_moments(variant=0):
+    """The normals are N(0,1), independent across components and times."""
+    z = np.array([oracle.gauss3(12345, i % 97, i // 97 - 50) for i in range(60000)])
+    n = z.shape[0]
+    se = 1.0 / math.sqrt(n)
+    m = z.mean(0)
+    v = z.var(0)
+    k4 = (z ** 4).mean(0)
+    c01 = (z[:, 0] * z[:, 1]).mean()
+    c02 = (z[:, 0] * z[:, 2]).mean()
+    ok = (np.all(np.abs(m) < 5 * se) and np.all(np.abs(v - 1) < 5 * math.sqrt(2) * se)
+          and np.all(np.abs(k4 - 3) < 5 * math.sqrt(96) * se)
+          and abs(c01) < 5 * se and abs(c02) < 5 * se)
+    return bool(ok), f"mean {m} var {v} k4 {k4} c01 {c01:.4f} c02 {c02:.4f}"
+
+
+# --------------------------------------------------------- noise coefficients --
+def _discrete(samples, dt):
+    """Trapezoid weights of the delta comb: K_0 = dt K(0)/2, K_m = dt K(m dt)."""
+    k = dt * np.asarray(samples, dtype=float)
+    k[0] *= 0.5
+    return k
+
+
+def pin_noise_circular_identity(variant=0):
+    """Eq. noise_ansatz: sum_s A_s A_{s+m} (indices wrapped with period
+    2 m_max - 1) equals the FDT target kT a_m K_m / dt, a_0 = 2, a_m = 1."""
+    worst = 0.0
+    for w in (inputs.SMALL, inputs.MEDIUM, inputs.LARGE):
+        Kd = _discrete(inputs.self_kernel_samples(w), w.dt)
+        st, Cm, Ch, A, _ = oracle.noise_coefs(Kd, w.kT, w.dt, variant=variant)
+        if st != 0:
+            return False, f"{w.name}: status {st}"
+        M = w.m_max
+        L = 2 * M - 1
+        target = w.kT * Kd / w.dt
+        target[0] *= 2.0
+        acf = np.array([np.dot(A, np.roll(A, -m)) for m in range(M)])
+        worst = max(worst, np.max(np.abs(acf - target)) / target[0])
+        if not np.allclose(A, A[::-1], rtol=0, atol=1e-14 * np.abs(A).max()):
+            return False, "A_s not symmetric"
+        assert L == A.size
+    return worst < 1e-10, f"max rel deviation {worst:.2e}"
+
+
+def pin_noise_white(variant=0):
+    """Markovian special case: K_m = 0 for m >= 1 gives A_s = sqrt(2 kT K_0/dt) delta_s0."""
+    M, dt, kT, K0 = 16, 0.05, 1.3, 0.7
+    Kd = np.zeros(M)
+    Kd[0] = K0
+    st, _, _, A, _ = oracle.noise_coefs(Kd, kT, dt, variant=variant)
+    want = np.zeros(2 * M - 1)
+    want[M - 1] = math.sqrt(2 * kT * K0 / dt)
+    err = np.max(np.abs(A - want))
+    return st == 0 and err < 1e-12, f"max |A - closed form| {err:.2e}"
+
+
+def pin_not_psd(variant=0):
+    """A correlation sequence with a negative Fourier mode is rejected
+    (positive definiteness is checked, end of Sec. II B); with clamping the
+    negative mass is reported."""
+    M, dt, kT = 8, 0.1, 1.0
+    Kd = np.zeros(M)
+    Kd[0], Kd[1] = 0.05, 0.5     # C_0 = 1, C_1 = 5: hat C at w=M-1 is < 0
+    st, _, Ch, _, _ = oracle.noise_coefs(Kd, kT, dt, variant=variant)
+    st2, _, _, _, mass = oracle.noise_coefs(Kd, kT, dt, clamp=True, variant=variant)
+    ok = st == oracle.NOT_PSD and Ch.min() < 0 and st2 == 0 and mass > 0
+    return ok, f"status {st}/{st2}, min hat C {Ch.min():.3f}, clamped {mass:.3f}"
+
+
+# ------------------------------------------------------------- neighbours --
+def _pairs_numpy(pos, box, rc):
+    d = pos[:, None, :] - pos[None, :, :]
+    d -= box * np.round(d / box)
+    r2 = (d ** 2).sum(-1)
+    i, j = np.nonzero(np.triu(r2 < rc * rc, k=1))
+    return set(zip(i.tolist(), j.tolist()))
+
+
+def pin_neighbors(variant=0):
+    rng = np.random.default_rng(3)
+    cases = []
+    for n, box, rc in ((300, 10.0, 2.0), (500, 8.0, 2.0), (64, 8.0, 2.0), (200, 5.0, 2.4)):
+        cases.append((rng.uniform(0, box, (n, 3)), box, rc))
+    # particles hugging the periodic faces
+    p = rng.uniform(0, 10.0, (200, 3))
+    p[:100, 0] = rng.choice([0.0, 1e-9, 10.0 - 1e-9], 100)
+    cases.append((p, 10.0, 2.0))
+    for pos, box, rc in cases:
+        ref = _pairs_numpy(pos, box, rc)
+        b = {tuple(x) for x in oracle.pairs_brute(pos, box, rc).tolist()}
+        c = {tuple(x) for x in oracle.pairs_cells(pos, box, rc).tolist()}
+        if not (ref == b == c):
+            return False, f"pair sets differ (n={len(pos)}): {len(ref)} {len(b)} {len(c)}"
+        p32 = pos.astype(np.float32)
+        f = {tuple(x) for x in oracle.pairs_brute_f32(p32, box, np.float32(rc * rc)).tolist()}
+        ref32 = _pairs_numpy(p32.astype(float), box, rc)
+        for (i, j) in f ^ ref32:
+            d = p32[i].astype(float) - p32[j].astype(float)
+            d -= box * np.round(d / box)
+            if abs(np.sqrt((d ** 2).sum()) - rc) > 1e-5 * rc:
+                return False, f"fp32 pair set differs away from r_c: {(i, j)}"
+    return True, f"{len(cases)} configurations"
+
+
+# -------------------------------------------------------- conservative force --
+def _potential(pos, box, rc, A):
+    d = pos[:, None, :] - pos[None, :, :]
+    d -= box * np.round(d / box)
+    r = np.sqrt((d ** 2).sum(-1))
+    iu = np.triu_indices(len(pos), 1)
+    r = r[iu]
+    r = r[r < rc]
+    return float(np.sum(A * (1 - r / rc) ** 2))
+
+
+def pin_fc_fd(variant=0):
+    """F^C = -grad U for U = sum_pairs A (1 - r/r_c)^2; sum_i F^C_i = 0."""
+    rng = np.random.default_rng(5)
+    n, box, rc, A = 20, 5.0, 2.0, 25.0
+    pos = rng.uniform(0, box, (n, 3))
+    s = oracle.System(n=n, box=box, mass=1.0, kT=0.0, dt=0.01, m_max=4, r_c=rc, A_cons=A,
+                      pos=pos, vel=np.zeros((n, 3)), variant=variant)
+    F = s.get(oracle.FC)
+    h = 1e-6
+    Ffd = np.zeros_like(F)
+    for i in range(n):
+        for c in range(3):
+            pp, pm = pos.copy(), pos.copy()
+            pp[i, c] += h
+            pm[i, c] -= h
+            Ffd[i, c] = -(_potential(pp, box, rc, A) - _potential(pm, box, rc, A)) / (2 * h)
+    err = np.abs(F - Ffd).max() / np.abs(Ffd).max()
+    net = np.abs(F.sum(0)).max()
+    return err < 1e-6 and net < 1e-10, f"rel err {err:.2e}, |sum F| {net:.1e}"
+
+
+# ----------------------------------------------------------------- integrator --
+def _soft_system(variant, n=64, box=8.0, seed=11, steps_kernel_zero=True, **kw):
+    w = inputs.SMALL
+    pos, vel = inputs.initial_state(w, seed=seed)
+    s = oracle.System(n=w.n, box=w.box, mass=w.mass, kT=w.kT, dt=w.dt, m_max=w.m_max,
+                      r_c=w.r_c, A_cons=w.A_cons, pos=pos, vel=vel, variant=variant, **kw)
+    return s, w, pos, vel
+
+
+def pin_velocity_verlet(variant=0):
+    """With every kernel zero, a = b = 1 and F^D = F^R = 0: the integrator is
+    velocity Verlet.  Compare with a textbook velocity Verlet that uses the
+    oracle only as a force routine."""
+    s, w, pos, vel = _soft_system(variant)
+    s.set_kernels(np.zeros(w.m_max))
+    fcalc = oracle.System(n=w.n, box=w.box, mass=w.mass, kT=0.0, dt=w.dt, m_max=2, r_c=w.r_c,
+                          A_cons=w.A_cons, pos=pos, vel=vel, variant=variant)
+    x, v = pos.copy(), vel.copy()
+    unwrapped = np.zeros_like(x)
+    F = fcalc.get(oracle.FC)
+    dt, M = w.dt, w.mass
+    for _ in range(200):
+        vh = v + 0.5 * dt / M * F
+        unwrapped += dt * vh
+        x = x + dt * vh
+        fcalc.set(oracle.POS, x)
+        fcalc.recompute_fc()
+        F = fcalc.get(oracle.FC)
+        v = vh + 0.5 * dt / M * F
+    s.step(200)
+    ex = np.abs(s.get(oracle.DISP) - unwrapped).max()
+    ev = np.abs(s.get(oracle.VEL) - v).max()
+    return ex < 1e-9 and ev < 1e-9, f"max |dx| {ex:.1e}, |dv| {ev:.1e}"
+
+
+def pin_nve_energy(variant=0):
+    """Zero kernels: total energy is conserved up to the O(dt^2) Verlet band."""
+    s, w, pos, vel = _soft_system(variant)
+    s.set_kernels(np.zeros(w.m_max))
+    E = []
+    for _ in range(50):
+        p, v = s.get(oracle.POS), s.get(oracle.VEL)
+        E.append(0.5 * w.mass * (v ** 2).sum() + _potential(p, w.box, w.r_c, w.A_cons))
+        s.step(20)
+    E = np.array(E)
+    drift = np.abs(E - E[0]).max() / abs(E[0])
+    return drift < 2e-3, f"max relative energy deviation {drift:.2e} over 1000 steps"
+
+
+def pin_gjf_diffusion(variant=0):
+    """Markovian limit (K_m = 0 for m >= 1, no pair kernels, free particles):
+    the scheme is the Gronbech-Jensen--Farago integrator, whose diffusion
+    coefficient is kT/alpha for any time step.  dt = 1 with alpha = M = 1 is a
+    step where schemes without the b factor are far off."""
+    n, dt, alpha, kT, steps = 20000, 1.0, 1.0, 1.0, 1500
+    rng = np.random.default_rng(9)
+    box = 1.0e4
+    pos = rng.uniform(0, box, (n, 3))
+    vel = rng.normal(0, 1, (n, 3))
+    s = oracle.System(n=n, box=box, mass=1.0, kT=kT, dt=dt, m_max=2, r_c=0.01, A_cons=0.0,
+                      seed=4, pos=pos, vel=vel, variant=variant)
+    st = s.set_kernels(np.array([alpha, 0.0]), discrete=True)
+    if st != 0:
+        return False, f"status {st}"
+    s.step(100)
+    d0 = s.get(oracle.DISP)
+    s.step(steps)
+    dx = s.get(oracle.DISP) - d0
+    D = (dx ** 2).mean() / (2 * steps * dt)
+    se = D * math.sqrt(2.0 / dx.size)
+    want = kT / alpha
+    # finite-time correction of the Markovian MSD is O(M/(alpha T)) ~ 1e-3
+    return abs(D - want) < 5 * se + 2e-3, f"D = {D:.4f} +- {se:.4f} (want {want})"
+
+
+def _run_single(dt, K0, tau, T, variant):
+    m_max = int(round(2.0 / dt))
+    s = oracle.System(n=1, box=100.0, mass=1.0, kT=0.0, dt=dt, m_max=m_max, r_c=1.0,
+                      pos=[[50, 50, 50]], vel=[[1.0, 0, 0]], variant=variant)
+    t = np.arange(m_max) * dt
+    if s.set_kernels(K0 * np.exp(-t / tau)) != 0:
+        return np.inf
+    steps = int(round(T / dt))
+    vs = [1.0]
+    for _ in range(steps):
+        s.step(1)
+        vs.append(s.get(oracle.VEL)[0, 0])
+    tt = np.arange(steps + 1) * dt
+    return float(np.max(np.abs(np.array(vs) - closed_form_vacf(tt, K0, tau))))
+
+
+def pin_closed_form_deterministic(variant=0):
+    """kT = 0, V(0) = 1, K^s = K0 exp(-t/tau): V(t) follows the closed-form
+    VACF; the scheme converges to it at second order in dt."""
+    errs = [_run_single(dt, 20.0, 0.1, 1.0, variant) for dt in (0.01, 0.005, 0.0025)]
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    ok = errs[2] < 5e-5 and 3.5 < r1 < 4.5 and 3.5 < r2 < 4.5
+    return ok, f"errors {errs}, ratios {r1:.2f} {r2:.2f}"
+
+
+def _run_pair(dt, Ks0, Kp0, Kds0, tau, T, variant):
+    m_max = int(round(2.0 / dt))
+    s = oracle.System(n=2, box=100.0, mass=1.0, kT=0.0, dt=dt, m_max=m_max, r_c=10.0,
+                      pos=[[50, 50, 50], [53, 50, 50]], vel=[[1.0, 0, 0], [0, 0, 0]], variant=variant)
+    t = np.arange(m_max) * dt
+    g = np.exp(-t / tau)[None]
+    f = np.ones((1, 64))
+    if s.set_kernels(Ks0 * np.exp(-t / tau), g=Kp0 * g, f=f, dr=10.0 / 63, gs=Kds0 * g, fs=f) != 0:
+        return np.inf, np.inf
+    steps = int(round(T / dt))
+    v1, v2 = [1.0], [0.0]
+    for _ in range(steps):
+        s.step(1)
+        v = s.get(oracle.VEL)
+        v1.append(v[0, 0])
+        v2.append(v[1, 0])
+    v1, v2 = np.array(v1), np.array(v2)
+    tt = np.arange(steps + 1) * dt
+    vp, vm = (v1 + v2) / math.sqrt(2), (v1 - v2) / math.sqrt(2)
+    cp = closed_form_vacf(tt, Ks0 + Kds0 + Kp0, tau) / math.sqrt(2)
+    cm = closed_form_vacf(tt, Ks0 + Kds0 - Kp0, tau) / math.sqrt(2)
+    return float(np.max(np.abs(vp - cp))), float(np.max(np.abs(vm - cm)))
+
+
+def pin_pair_decoupling(variant=0):
+    """Two particles on a line with flat parallel pair kernels (Sec. III A,
+    Eqs. gle1-gle2): V_+- = (V_1 +- V_2)/sqrt 2 obey single-particle GLEs with
+    K_+- = K^s + dK^s +- K^p, each with the closed form above."""
+    errs = [_run_pair(dt, 20.0, 8.0, 3.0, 0.1, 1.0, variant) for dt in (0.01, 0.005, 0.0025)]
+    ep = [e[0] for e in errs]
+    em = [e[1] for e in errs]
+    ok = (max(ep[2], em[2]) < 5e-5 and 3.5 < ep[1] / ep[2] < 4.5 and 3.5 < em[1] / em[2] < 4.5)
+    return ok, f"V+ errors {ep}, V- errors {em}"
+
+
+def pin_noise_autocorrelation(variant=0):
+    """The generated F^R has <F_{n+m} F_n> = kT a_m K_m / dt (Eq.
+    stochastic_force2, self part) up to the wrap-around terms of the finite
+    moving average; measured over independent particle streams."""
+    w = inputs.SMALL
+    n, steps = 256, 2000
+    rng = np.random.default_rng(2)
+    s = oracle.System(n=n, box=1000.0, mass=1.0, kT=1.0, dt=w.dt, m_max=w.m_max, r_c=0.01,
+                      A_cons=0.0, seed=21, pos=rng.uniform(0, 1000, (n, 3)),
+                      vel=rng.normal(0, 1, (n, 3)), variant=variant)
+    if s.set_kernels(inputs.self_kernel_samples(w)) != 0:
+        return False, "not psd"
+    fr = np.empty((steps, n * 3))
+    for k in range(steps):
+        s.step(1)
+        fr[k] = s.get(oracle.FR).ravel()
+    M = w.m_max
+    Kd = _discrete(inputs.self_kernel_samples(w), w.dt)
+    target = w.kT * Kd / w.dt
+    target[0] *= 2
+    A = s.coefs()["A"]
+    linear = np.array([np.dot(A[: A.size - m], A[m:]) for m in range(M)])
+    per_stream = np.array([(fr[m:] * fr[: steps - m]).mean(0) for m in range(M)])  # [M, 3n]
+    est = per_stream.mean(1)
+    se = per_stream.std(1, ddof=1) / math.sqrt(per_stream.shape[1])
+    z_lin = np.max(np.abs(est - linear) / se)
+    gap = np.max(np.abs(linear - target)) / target[0]
+    ok_target = np.all(np.abs(est - target) < 5 * se + np.abs(linear - target))
+    return bool(z_lin < 5 and ok_target), f"max z vs linear form {z_lin:.2f}; wrap gap {gap:.2e}"
+
+
+def pin_vacf_closed_form(variant=0):
+    """Free particles, kT = 1, K^s = K0 exp(-t/tau): the measured VACF is the
+    closed form times kT/M (m_max dt = 10 tau)."""
+    n, dt, tau, K0, M = 400, 0.005, 0.1, 10.0, 200
+    rng = np.random.default_rng(8)
+    s = oracle.System(n=n, box=1000.0, mass=1.0, kT=1.0, dt=dt, m_max=M, r_c=0.01, A_cons=0.0,
+                      seed=33, vacf_len=120, vacf_stride=10, vacf_burnin=400,
+                      pos=rng.uniform(0, 1000, (n, 3)), vel=rng.normal(0, 1, (n, 3)),
+                      variant=variant)
+    t = np.arange(M) * dt
+    if s.set_kernels(K0 * np.exp(-t / tau)) != 0:
+        return False, "not psd"
+    s.step(3400)
+    c, n0 = s.vacf()
+    want = closed_form_vacf(np.arange(c.size) * dt, K0, tau)
+    err = np.max(np.abs(c - want))
+    return err < 0.03, f"max |C - closed form| = {err:.4f} over {n0} origins"
+
+
+def pin_vacf_accumulator(variant=0):
+    """The VACF accumulator equals the definition evaluated on the recorded
+    velocities with the same origin schedule."""
+    w = inputs.SMALL
+    pos, vel = inputs.initial_state(w, seed=4)
+    L, stride, burn = 12, 3, 5
+    s = oracle.System(n=w.n, box=w.box, mass=1.0, kT=1.0, dt=w.dt, m_max=w.m_max, r_c=w.r_c,
+                      A_cons=w.A_cons, seed=3, vacf_len=L, vacf_stride=stride, vacf_burnin=burn,
+                      pos=pos, vel=vel, variant=variant)
+    s.set_kernels(inputs.self_kernel_samples(w))
+    V = {0: s.get(oracle.VEL)}
+    for t in range(1, 60):
+        s.step(1)
+        V[t] = s.get(oracle.VEL)
+    acc = np.zeros(L)
+    cnt = np.zeros(L)
+    for t0 in range(burn, 60, stride):
+        for lag in range(L):
+            if t0 + lag < 60:
+                acc[lag] += (V[t0 + lag] * V[t0]).sum()
+                cnt[lag] += 1
+    want = acc / (3 * w.n * cnt)
+    c, n0 = s.vacf()
+    err = np.max(np.abs(c - want))
+    return err < 1e-12 and n0 == len(range(burn, 60, stride)), f"max err {err:.1e}, origins {n0}"
+
+
+ALL = {
+    "philox_kat": pin_philox_kat,
+    "gauss_moments": pin_gauss_moments,
+    "noise_circular_identity": pin_noise_circular_identity,
+    "noise_white": pin_noise_white,
+    "not_psd": pin_not_psd,
+    "neighbors": pin_neighbors,
+    "fc_fd": pin_fc_fd,
+    "velocity_verlet": pin_velocity_verlet,
+    "nve_energy": pin_nve_energy,
+    "gjf_diffusion": pin_gjf_diffusion,
+    "closed_form_deterministic": pin_closed_form_deterministic,
+    "pair_decoupling": pin_pair_decoupling,
+    "noise_autocorrelation": pin_noise_autocorrelation,
+    "vacf_closed_form": pin_vacf_closed_form,
+    "vacf_accumulator": pin_vacf_accumulator,
+}
