@@ -1,0 +1,227 @@
+/*
+ * gld.h -- C ABI of the GB300 (sm_103a) integrator for discretized generalized
+ * Langevin dynamics (GLD), after Jung, Hanke & Schmid, "Generalized Langevin
+ * dynamics: Construction and numerical integration of non-Markovian
+ * particle-based models" (arXiv:1808.00270).
+ *
+ * One GLD step (Sec. II B, Eq. GLD_integrator) on N particles in a cubic
+ * periodic box:
+ *   R_{n+1} = R_n + b dt V_n + b dt^2/(2M) (F^C_n + F^D_n + F^R_n)
+ *   V_{n+1} = a V_n + dt/(2M) (a F^C_n + F^C_{n+1}) + b dt/M (F^D_n + F^R_n)
+ * with b = [1 + dt K^s_0/(2M)]^-1, a = b [1 - dt K^s_0/(2M)] (Eq. aa-bb); the
+ * conservative soft repulsion F^C over a cell list; the dissipative memory
+ * force F^D of Eq. dissipative_force2, evaluated from a device-resident ring
+ * of the last m_max-1 displacements dR_{n-m}; and the colored random force
+ * F^R_n = sum_{s=-(m_max-1)}^{m_max-1} A_s W_{n+s} of Eq. noise_production
+ * built from counter-based Philox4x32-10 Gaussians, with A_s derived from the
+ * self kernel by the Fourier route of Sec. II C.
+ *
+ * Conventions shared by every call:
+ *   - All pointers passed to gld_create / gld_set_kernels / gld_get_* /
+ *     gld_set_* / gld_vacf are HOST pointers owned by the caller; the library
+ *     copies from or into them and keeps no reference.  Arrays of particle
+ *     vectors are row-major [n][3] doubles.
+ *   - The library owns all device memory of a context.  It allocates through
+ *     gld_params.alloc / .free when given (e.g. a framework's caching
+ *     allocator), else with cudaMalloc / cudaFree.
+ *   - Work is queued on gld_params.stream (a cudaStream_t; NULL = legacy
+ *     default stream).  gld_step returns without waiting; errors raised on the
+ *     device are latched and returned by the next synchronizing call
+ *     (gld_sync, gld_vacf, gld_get_*).  gld_last_error gives a message.
+ *   - No call is thread-safe against another call on the same context.
+ *
+ * Entry points whose names end in _dev take DEVICE pointers allocated by the
+ * caller, run one kernel on the given stream and return without waiting.
+ */
+#ifndef GLD_H
+#define GLD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gld_ctx gld_ctx;
+
+typedef enum {
+    GLD_OK = 0,
+    GLD_E_INVAL = -1,     /* bad argument or parameter combination            */
+    GLD_E_NOMEM = -2,     /* device allocation failed                         */
+    GLD_E_NOT_PSD = -3,   /* noise spectrum has a negative mode (Sec. II B)   */
+    GLD_E_CUDA = -4,      /* a CUDA runtime call or launch failed             */
+    GLD_E_NONFINITE = -5, /* a non-finite displacement was produced           */
+    GLD_E_TIMEOUT = -6,   /* a bounded device wait gave up                     */
+    GLD_E_STATE = -7      /* call out of order (e.g. gld_step before kernels) */
+} gld_status;
+
+enum { GLD_HIST_F32 = 0, GLD_HIST_BF16 = 1 };
+enum { GLD_KCONT = 0, GLD_KDISCRETE = 1 };
+
+/* Optional device allocator: returns a pointer to at least `bytes` bytes of
+ * device memory usable on `stream`, or NULL. */
+typedef void* (*gld_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*gld_free_fn)(void* ptr, void* stream, void* user);
+
+typedef struct gld_params {
+    int32_t n;           /* particles, >= 1                                        */
+    double box;          /* edge L of the cubic periodic box (Sec. II A, App. B)   */
+    double mass;         /* particle mass M                                         */
+    double kT;           /* k_B T of the fluctuation-dissipation theorem, Eq. FDT   */
+    double dt;           /* time step                                               */
+    int32_t m_max;       /* memory cutoff: K_m for m < m_max (Eq. k-discrete), >= 2 */
+    double r_c;          /* spatial cutoff of F^C and pair kernels, 0 < r_c <= L/2  */
+    double r_c_min;      /* kernels evaluated at max(r, r_c_min) (Sec. III B)       */
+    double A_cons;       /* soft repulsion U(r) = A (1 - r/r_c)^2 for r < r_c        */
+    uint64_t seed;       /* Philox key of the white noise W                         */
+    int32_t hist_dtype;  /* GLD_HIST_F32 (default) or GLD_HIST_BF16 ring storage    */
+    int32_t kahan;       /* 1: compensated summation over the m_max-1 history terms */
+    int32_t vacf_len;    /* VACF lags kept (0 = no VACF)                             */
+    int32_t vacf_stride; /* steps between VACF time origins (>= 1)                   */
+    int64_t vacf_burnin; /* first origin time; < 0 selects 2 m_max                  */
+    int32_t noise_block; /* steps of F^R produced per noise launch (0 = 64)          */
+    int32_t psd_clamp;   /* 1: clamp negative noise modes to 0 instead of failing    */
+    int32_t use_graphs;  /* 1 (default): replay steps from a captured CUDA graph     */
+    void* stream;        /* cudaStream_t for all work of this context                */
+    gld_alloc_fn alloc;  /* optional device allocator (NULL: cudaMalloc)             */
+    gld_free_fn free;
+    void* alloc_user;
+} gld_params;
+
+/* Fills *p with defaults (kT = 1, mass = 1, r_c_min = 0, F32 history, no Kahan,
+ * vacf_stride = 1, vacf_burnin = -1, noise_block = 64, graphs on). */
+void gld_params_default(gld_params* p);
+
+/* Creates a context on the current CUDA device.  pos and vel are [n][3]
+ * host arrays (positions are wrapped into [0, L)).  Computes F^C_0 at R_0.
+ * The displacement history starts at zero (cold start).  Returns GLD_E_INVAL
+ * for n < 1, m_max < 2, r_c > L/2, non-positive L, M, dt, or an unknown
+ * hist_dtype; GLD_E_NOMEM if device memory runs out. */
+gld_status gld_create(const gld_params* p, const double* pos, const double* vel, gld_ctx** out);
+
+/* Sets the memory kernels (Sec. II A, Eqs. GLD_basic, GLD_basic2, parallel
+ * components only; Sec. II B, Eq. k-discrete) and derives everything the
+ * step needs, in FP64 on the device:
+ *   Ks[m_max]        self kernel K^s.  With GLD_KCONT these are continuous
+ *                    samples K^s(m dt); the discrete weights are
+ *                    K_m = dt K(m dt) for m >= 1 and K_0 = dt K(0)/2.
+ *                    With GLD_KDISCRETE they are the K_m themselves.
+ *   Q, g[Q][m_max], f[Q][nr]
+ *                    pair kernel K^p_m(r) = sum_q f_q(r) g_q[m] (parallel
+ *                    component, acting through e e^T); g converted like Ks;
+ *                    f tabulated on r = k dr, k < nr, linear interpolation,
+ *                    constant past the last entry.  Q = 0 disables it.
+ *   dKs_g[Qs][m_max], dKs_f[Qs][nr], Qs
+ *                    neighbour contribution to the self kernel dK^s_m(r), same
+ *                    representation.  Qs = 0 (pointers may be NULL) disables it.
+ * Then: noise target C_m = kT a_m K^s_m / dt (Eq. FDT_discretized, a_0 = 2),
+ * its length-(2 m_max - 1) transform (Eq. FT), A_s = inverse transform of
+ * sqrt(hat C) (Sec. II C), and a, b (Eq. aa-bb).  Returns GLD_E_NOT_PSD if a
+ * mode of hat C is negative (beyond 1e-12 of the largest) unless psd_clamp;
+ * GLD_E_INVAL for Q or Qs outside [0, 4] or nr < 2 / dr <= 0 with Q+Qs > 0.
+ * Synchronizes the stream. */
+gld_status gld_set_kernels(gld_ctx* ctx, const double* Ks, int32_t Q, const double* g,
+                           const double* f, int32_t nr, double dr, const double* dKs_g,
+                           const double* dKs_f, int32_t Qs, int32_t kernel_convention);
+
+/* Queues nsteps GLD steps (>= 0) on the context's stream; returns without
+ * waiting.  GLD_E_STATE if no kernels are set. */
+gld_status gld_step(gld_ctx* ctx, int64_t nsteps);
+
+/* Waits for the context's stream; returns the first latched error. */
+gld_status gld_sync(gld_ctx* ctx);
+
+/* Velocity autocorrelation (Sec. III A, self part of C^a), per Cartesian
+ * component: out[tau] = < V_x(t0 + tau) V_x(t0) > averaged over particles,
+ * components and time origins t0 = burnin + k vacf_stride, accumulated in
+ * FP64 on the device.  out has vacf_len entries; *n_origins (may be NULL)
+ * receives the number of origins so far.  Synchronizes. */
+gld_status gld_vacf(gld_ctx* ctx, double* out, int64_t* n_origins);
+
+/* Current wrapped positions and velocities, [n][3] each (either may be NULL).
+ * Synchronizes. */
+gld_status gld_get_state(gld_ctx* ctx, double* pos, double* vel);
+
+/* Arrays that can be read (and, where marked, written) for checks and
+ * checkpoints.  Sizes: [n][3] unless stated. */
+enum {
+    GLD_ARR_POS = 0,  /* R_n, wrapped (rw; writing rebuilds cells and F^C)        */
+    GLD_ARR_VEL = 1,  /* V_n (rw)                                                 */
+    GLD_ARR_FC = 2,   /* F^C_n (rw)                                               */
+    GLD_ARR_FD = 3,   /* F^D of the last completed step (r)                       */
+    GLD_ARR_FR = 4,   /* F^R of the last completed step (r)                       */
+    GLD_ARR_DISP = 5, /* unwrapped displacement since creation, sum of dR (rw)    */
+    GLD_ARR_HIST = 6, /* [m_max-1][n][3]: entry m-1 holds dR_{n-m} (rw)           */
+    GLD_ARR_CONV = 7  /* [1+Q+Qs][n][3]: history projections of the last step (r) */
+};
+gld_status gld_get_array(gld_ctx* ctx, int32_t which, double* out);
+gld_status gld_set_array(gld_ctx* ctx, int32_t which, const double* in);
+
+/* Step counter n (the time index of R_n) and its setter (n >= 0, else
+ * GLD_E_INVAL); setting it invalidates the noise window, which is rebuilt
+ * from the counters. */
+gld_status gld_get_step(gld_ctx* ctx, int64_t* step);
+gld_status gld_set_step(gld_ctx* ctx, int64_t step);
+
+/* FP64 results of gld_set_kernels: Kd[m_max] discrete K^s_m, A[2 m_max - 1]
+ * noise coefficients A_s at s + m_max - 1, ab[2] = {a, b}, spec[2] = {min
+ * mode of hat C, clamped negative mass}.  Any pointer may be NULL. */
+gld_status gld_get_coefs(gld_ctx* ctx, double* Kd, double* A, double* ab, double* spec);
+
+/* Pairs (i < j) with |R_i - R_j| < r_c found by the cell-list traversal that
+ * the force kernels use, at the current positions.  The distance test is
+ * single precision with this exact order: d = x_i - x_j; if d > L/2 then
+ * d -= L, else if d < -L/2 then d += L; r2 = (dx*dx + dy*dy) + dz*dz without
+ * fused multiply-add; pair if r2 < float(r_c^2).  pairs is [cap][2] int32;
+ * *count receives the total (may exceed cap).  Synchronizes. */
+gld_status gld_get_pairs(gld_ctx* ctx, int32_t* pairs, int64_t cap, int64_t* count);
+
+/* Runs nsteps steps with every kernel launched directly (no graph) and
+ * bracketed by CUDA events on the context's stream; adds each kernel
+ * family's device time in milliseconds to ms[GLD_PROF_N] and its launch count
+ * to launches[GLD_PROF_N] (either may be NULL).  Advances the simulation like
+ * gld_step.  Synchronizes. */
+enum {
+    GLD_PROF_NOISE = 0,  /* white-noise generation + moving average (per block) */
+    GLD_PROF_HIST = 1,   /* history convolution                               */
+    GLD_PROF_PAIR = 2,   /* F^D, position update, history write               */
+    GLD_PROF_CELL = 3,   /* cell list build (3 kernels)                       */
+    GLD_PROF_CFORCE = 4, /* F^C_{n+1} and velocity update                     */
+    GLD_PROF_VACF = 5,   /* velocity autocorrelation                          */
+    GLD_PROF_N = 6
+};
+gld_status gld_profile_steps(gld_ctx* ctx, int64_t nsteps, double* ms, int64_t* launches);
+
+const char* gld_last_error(const gld_ctx* ctx);
+gld_status gld_destroy(gld_ctx* ctx);
+
+/* ---- single kernels on caller-owned device memory ----------------------- */
+
+/* Philox4x32-10 (Salmon et al., SC'11) on n counters: ctr [n][4] uint32,
+ * key[2] (host), out [n][4] uint32. */
+gld_status gld_philox_dev(const uint32_t* ctr, const uint32_t key[2], uint32_t* out, int64_t n,
+                          void* stream);
+
+/* White noise W_{i,k}: for item j, particle[j] and time[j] give the counter
+ * (particle, (time + 2^62) low word, high word, stream_id); out [n][3] float.
+ * u = ((x >> 8) + 1/2) 2^-24; Box-Muller on words (0,1) gives x, y and on
+ * (2,3) gives z (Sec. II C requires uncorrelated unit Gaussians). */
+gld_status gld_gauss3_dev(uint64_t seed, const uint32_t* particle, const int64_t* time,
+                          uint32_t stream_id, float* out, int64_t n, void* stream);
+
+/* History convolution of Eq. dissipative_force2 for every particle and
+ * component (the memory-bound step):
+ *   out[a][c][i] = sum_{m=1}^{m_max-1} coef[a][m] dR_{i,c,step-m}
+ * ring: [m_max-1][3][n_pad] (float, or bf16 when bf16 != 0); dR_k is at slot
+ * k mod (m_max-1).  coef: [nacc][m_max] float; out: [nacc][3][n_pad] float.
+ * n_pad must be a multiple of 32 and the pointers 16-byte aligned; nacc in
+ * [1, 9].  kahan != 0 uses compensated sums. */
+gld_status gld_hist_conv_dev(const void* ring, int32_t bf16, int32_t n_pad, int32_t m_max,
+                             int64_t step, const float* coef, int32_t nacc, float* out,
+                             int32_t kahan, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GLD_H */

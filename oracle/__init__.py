@@ -257,3 +257,17 @@ class System:
         fd, fr = np.zeros((idx.size, 3)), np.zeros((idx.size, 3))
         self._L.or_forces_subset(self._h, _p(idx), idx.size, _p(fd), _p(fr))
         return fd, fr
+
+
+def history_projections(hist, coef) -> np.ndarray:
+    """The history sums of Eq. dissipative_force2 written out in FP64:
+    out[a, i, c] = sum_{m=1}^{m_max-1} coef[a, m] * hist[m-1, i, c],
+    where hist[m-1] holds dR_{n-m}.  Used as the reference of the
+    history-convolution kernel on identical FP32 inputs."""
+    hist = np.asarray(hist, dtype=np.float64)
+    coef = np.asarray(coef, dtype=np.float64)
+    out = np.zeros((coef.shape[0],) + hist.shape[1:])
+    for a in range(coef.shape[0]):
+        for m in range(1, coef.shape[1]):
+            out[a] += coef[a, m] * hist[m - 1]
+    return out

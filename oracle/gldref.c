@@ -429,7 +429,7 @@ int or_set_kernels(or_sys* s, const double* Ks, int Q, const double* g, const do
                    double dr, int Qs, const double* gs, const double* fs, int discrete, int clamp)
 {
     int M = s->m_max;
-    if (Q < 0 || Qs < 0 || (Q + Qs > 0 && (nr < 2 || !(dr > 0)))) return -1;
+    if (Q < 0 || Qs < 0 || Q > 8 || Qs > 8 || (Q + Qs > 0 && (nr < 2 || !(dr > 0)))) return -1;
     free(s->Kd); free(s->gd); free(s->f); free(s->gsd); free(s->fs);
     free(s->C); free(s->Chat); free(s->A);
     s->Q = Q; s->Qs = Qs; s->nr = nr; s->dr = dr; s->clamp = clamp;
@@ -516,10 +516,14 @@ static void dissipative_force_i(const or_sys* s, int i, const int32_t* nb, int64
         double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         double e[3] = { d[0] / r, d[1] / r, d[2] / r };
         double rt = r < s->rc_min ? s->rc_min : r;
+        double fq[8], fsq[8]; /* radial factors f_q(r), fs_q(r) (Q, Qs <= 8) */
+        for (int q = 0; q < Q; ++q) fq[q] = table_at(s->f + (size_t)q * s->nr, s->nr, s->dr, rt);
+        for (int q = 0; q < Qs; ++q) fsq[q] = table_at(s->fs + (size_t)q * s->nr, s->nr, s->dr, rt);
         for (int m = 0; m < M; ++m) {
+            /* K^p_m(r) = sum_q f_q(r) g_q[m],  dK^s_m(r) = sum_q fs_q(r) gs_q[m] */
             double kp = 0.0, kds = 0.0;
-            for (int q = 0; q < Q; ++q) kp += table_at(s->f + (size_t)q * s->nr, s->nr, s->dr, rt) * s->gd[(size_t)q * M + m];
-            for (int q = 0; q < Qs; ++q) kds += table_at(s->fs + (size_t)q * s->nr, s->nr, s->dr, rt) * s->gsd[(size_t)q * M + m];
+            for (int q = 0; q < Q; ++q) kp += fq[q] * s->gd[(size_t)q * M + m];
+            for (int q = 0; q < Qs; ++q) kds += fsq[q] * s->gsd[(size_t)q * M + m];
             const double *xj, *xi;
             double scale;
             if (m == 0) { xj = s->vel + 3 * (OR_PLANT == 7 ? i : j); xi = s->vel + 3 * i; scale = 1.0; }
@@ -540,13 +544,17 @@ static void dissipative_force_i(const or_sys* s, int i, const int32_t* nb, int64
 }
 
 /* F^R_i,n = sum_{s=-(m_max-1)}^{m_max-1} A_s W_{i,n+s}, Eq. noise_production
- * for the self kernel. */
-static void random_force_i(const or_sys* s, int i, double F[3])
+ * for the self kernel.  With direct != 0 the W are drawn here instead of
+ * being read from the cache of the full-system step. */
+static void random_force_i(const or_sys* s, int i, double F[3], int direct)
 {
     const int M = s->m_max;
     F[0] = F[1] = F[2] = 0.0;
     for (int sh = -(M - 1); sh <= M - 1; ++sh) {
-        const double* w = W_at(s, s->step + sh) + 3 * i;
+        double wd[3];
+        const double* w = wd;
+        if (direct) or_gauss3(s->seed, (uint32_t)i, s->step + sh, 0u, wd);
+        else w = W_at(s, s->step + sh) + 3 * i;
         double A = s->A[sh + M - 1];
         for (int c = 0; c < 3; ++c) F[c] += A * w[c];
     }
@@ -595,7 +603,7 @@ int or_step(or_sys* s, int64_t nsteps)
         for (int i = 0; i < n; ++i) {
             double FD[3], FR[3];
             dissipative_force_i(s, i, s->nl.list + s->nl.start[i], s->nl.start[i + 1] - s->nl.start[i], FD);
-            random_force_i(s, i, FR);
+            random_force_i(s, i, FR, 0);
             for (int c = 0; c < 3; ++c) {
                 double v = s->vel[3 * i + c];
                 double Ft = s->fc[3 * i + c] + FD[c] + FR[c];
@@ -624,7 +632,6 @@ int or_step(or_sys* s, int64_t nsteps)
  * brute force), without advancing the state. */
 void or_forces_subset(or_sys* s, const int32_t* idx, int count, double* fd, double* fr)
 {
-    ensure_noise(s, s->step);
 #pragma omp parallel for schedule(dynamic, 1)
     for (int k = 0; k < count; ++k) {
         int i = idx[k];
@@ -643,7 +650,7 @@ void or_forces_subset(or_sys* s, const int32_t* idx, int count, double* fd, doub
             }
         }
         dissipative_force_i(s, i, nb, nn, fd + 3 * k);
-        random_force_i(s, i, fr + 3 * k);
+        random_force_i(s, i, fr + 3 * k, 1);
         free(nb);
     }
 }

@@ -1,0 +1,299 @@
+"""ctypes binding of the GLD CUDA library (include/gld.h).
+
+Argument marshalling only: every step of the integrator runs in the CUDA
+kernels of libgld.so.  PyTorch supplies device memory (its caching allocator,
+handed to the library as an allocation callback) and streams.  If the
+library is missing the import fails; there is no CPU or other fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, E_INVAL, E_NOMEM, E_NOT_PSD, E_CUDA, E_NONFINITE, E_TIMEOUT, E_STATE = 0, -1, -2, -3, -4, -5, -6, -7
+HIST_F32, HIST_BF16 = 0, 1
+KCONT, KDISCRETE = 0, 1
+ARR_POS, ARR_VEL, ARR_FC, ARR_FD, ARR_FR, ARR_DISP, ARR_HIST, ARR_CONV = range(8)
+_NAMES = {OK: "GLD_OK", E_INVAL: "GLD_E_INVAL", E_NOMEM: "GLD_E_NOMEM", E_NOT_PSD: "GLD_E_NOT_PSD",
+          E_CUDA: "GLD_E_CUDA", E_NONFINITE: "GLD_E_NONFINITE", E_TIMEOUT: "GLD_E_TIMEOUT",
+          E_STATE: "GLD_E_STATE"}
+
+
+class GLDError(RuntimeError):
+    def __init__(self, status: int, message: str = ""):
+        self.status = status
+        super().__init__(f"{_NAMES.get(status, status)}: {message}")
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class Params(C.Structure):
+    _fields_ = [("n", C.c_int32), ("box", C.c_double), ("mass", C.c_double), ("kT", C.c_double),
+                ("dt", C.c_double), ("m_max", C.c_int32), ("r_c", C.c_double), ("r_c_min", C.c_double),
+                ("A_cons", C.c_double), ("seed", C.c_uint64), ("hist_dtype", C.c_int32),
+                ("kahan", C.c_int32), ("vacf_len", C.c_int32), ("vacf_stride", C.c_int32),
+                ("vacf_burnin", C.c_int64), ("noise_block", C.c_int32), ("psd_clamp", C.c_int32),
+                ("use_graphs", C.c_int32), ("stream", C.c_void_p), ("alloc", ALLOC_FN),
+                ("free", FREE_FN), ("alloc_user", C.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Loads libgld.so (building it with nvcc if it is absent or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not _build.up_to_date():
+            path = _build.build()
+        if not os.path.exists(path):
+            raise ImportError("libgld.so is missing and could not be built")
+        L = C.CDLL(path)
+        vp, i32, i64, d, u32, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_uint32, C.c_uint64
+        sig = {
+            "gld_params_default": (None, [C.POINTER(Params)]),
+            "gld_create": (i32, [C.POINTER(Params), vp, vp, C.POINTER(vp)]),
+            "gld_set_kernels": (i32, [vp, vp, i32, vp, vp, i32, d, vp, vp, i32, i32]),
+            "gld_step": (i32, [vp, i64]),
+            "gld_sync": (i32, [vp]),
+            "gld_vacf": (i32, [vp, vp, C.POINTER(i64)]),
+            "gld_get_state": (i32, [vp, vp, vp]),
+            "gld_get_array": (i32, [vp, i32, vp]),
+            "gld_set_array": (i32, [vp, i32, vp]),
+            "gld_get_step": (i32, [vp, C.POINTER(i64)]),
+            "gld_set_step": (i32, [vp, i64]),
+            "gld_get_coefs": (i32, [vp, vp, vp, vp, vp]),
+            "gld_get_pairs": (i32, [vp, vp, i64, C.POINTER(i64)]),
+            "gld_profile_steps": (i32, [vp, i64, vp, vp]),
+            "gld_last_error": (C.c_char_p, [vp]),
+            "gld_destroy": (i32, [vp]),
+            "gld_philox_dev": (i32, [vp, vp, vp, i64, vp]),
+            "gld_gauss3_dev": (i32, [u64, vp, vp, u32, vp, i64, vp]),
+            "gld_hist_conv_dev": (i32, [vp, i32, i32, i32, i64, vp, i32, vp, i32, vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    """Names of the C entry points the binding expects the library to export."""
+    return ["gld_params_default", "gld_create", "gld_set_kernels", "gld_step", "gld_sync", "gld_vacf",
+            "gld_get_state", "gld_get_array", "gld_set_array", "gld_get_step", "gld_set_step",
+            "gld_get_coefs", "gld_get_pairs", "gld_profile_steps", "gld_last_error", "gld_destroy", "gld_philox_dev",
+            "gld_gauss3_dev", "gld_hist_conv_dev"]
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _current_stream() -> int:
+    import torch
+    return int(torch.cuda.current_stream().cuda_stream)
+
+
+class _TorchAllocator:
+    """Device memory from PyTorch's caching allocator, passed as C callbacks."""
+
+    def __init__(self):
+        import torch
+        self._torch = torch
+        self._device = torch.cuda.current_device()
+
+        def _alloc(nbytes, stream, user):
+            try:
+                return int(self._torch.cuda.caching_allocator_alloc(int(nbytes), self._device,
+                                                                    int(stream or 0)))
+            except Exception:
+                return None
+
+        def _free(ptr, stream, user):
+            if ptr:
+                self._torch.cuda.caching_allocator_delete(int(ptr))
+
+        self.alloc = ALLOC_FN(_alloc)
+        self.free = FREE_FN(_free)
+
+
+class GLD:
+    """One GLD system on the current CUDA device (wraps a gld_ctx)."""
+
+    def __init__(self, *, n, box, dt, m_max, r_c, pos, vel, mass=1.0, kT=1.0, r_c_min=0.0,
+                 A_cons=0.0, seed=1, hist_dtype="f32", kahan=False, vacf_len=0, vacf_stride=1,
+                 vacf_burnin=-1, noise_block=64, psd_clamp=False, use_graphs=True, stream=None,
+                 torch_allocator=True):
+        L = lib()
+        p = Params()
+        L.gld_params_default(C.byref(p))
+        p.n, p.box, p.mass, p.kT, p.dt = int(n), float(box), float(mass), float(kT), float(dt)
+        p.m_max, p.r_c, p.r_c_min, p.A_cons = int(m_max), float(r_c), float(r_c_min), float(A_cons)
+        p.seed = int(seed)
+        p.hist_dtype = HIST_BF16 if hist_dtype in ("bf16", HIST_BF16) else HIST_F32
+        p.kahan = int(bool(kahan))
+        p.vacf_len, p.vacf_stride, p.vacf_burnin = int(vacf_len), int(vacf_stride), int(vacf_burnin)
+        p.noise_block, p.psd_clamp, p.use_graphs = int(noise_block), int(bool(psd_clamp)), int(bool(use_graphs))
+        self.stream = _current_stream() if stream is None else int(stream)
+        p.stream = self.stream
+        self._alloc = _TorchAllocator() if torch_allocator else None
+        if self._alloc is not None:
+            p.alloc, p.free = self._alloc.alloc, self._alloc.free
+        self._params = p
+        self.n, self.m_max, self.vacf_len = int(n), int(m_max), int(vacf_len)
+        pos, vel = _f64(pos).reshape(self.n, 3), _f64(vel).reshape(self.n, 3)
+        h = C.c_void_p()
+        st = L.gld_create(C.byref(p), _ptr(pos), _ptr(vel), C.byref(h))
+        if st != OK:
+            raise GLDError(st, "gld_create failed")
+        self._h = h
+        self.nacc = 1
+
+    # -- life cycle ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().gld_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int):
+        if st != OK:
+            raise GLDError(st, lib().gld_last_error(self._h).decode())
+
+    # -- model ----------------------------------------------------------------
+    def set_kernels(self, Ks, g=None, f=None, dr=1.0, gs=None, fs=None, discrete=False):
+        M = self.m_max
+        Ks = _f64(Ks)
+        g = None if g is None else _f64(g).reshape(-1, M)
+        gs = None if gs is None else _f64(gs).reshape(-1, M)
+        Q = 0 if g is None else g.shape[0]
+        Qs = 0 if gs is None else gs.shape[0]
+        nr = 2
+        if f is not None:
+            f = _f64(f).reshape(Q, -1)
+            nr = f.shape[1]
+        if fs is not None:
+            fs = _f64(fs).reshape(Qs, -1)
+            nr = fs.shape[1]
+        keep = (Ks, g, f, gs, fs)
+        st = lib().gld_set_kernels(self._h, _ptr(Ks), Q, None if g is None else _ptr(g),
+                                   None if f is None else _ptr(f), nr, float(dr),
+                                   None if gs is None else _ptr(gs), None if fs is None else _ptr(fs),
+                                   Qs, KDISCRETE if discrete else KCONT)
+        del keep
+        self._check(st)
+        self.nacc = 1 + Q + Qs
+
+    def step(self, nsteps: int = 1):
+        self._check(lib().gld_step(self._h, int(nsteps)))
+
+    def sync(self):
+        self._check(lib().gld_sync(self._h))
+
+    def vacf(self):
+        out = np.zeros(max(self.vacf_len, 1))
+        n0 = C.c_int64()
+        self._check(lib().gld_vacf(self._h, _ptr(out), C.byref(n0)))
+        return out[: self.vacf_len], int(n0.value)
+
+    def get_state(self):
+        pos, vel = np.zeros((self.n, 3)), np.zeros((self.n, 3))
+        self._check(lib().gld_get_state(self._h, _ptr(pos), _ptr(vel)))
+        return pos, vel
+
+    def get(self, which: int) -> np.ndarray:
+        if which == ARR_HIST:
+            shape = (self.m_max - 1, self.n, 3)
+        elif which == ARR_CONV:
+            shape = (self.nacc, self.n, 3)
+        else:
+            shape = (self.n, 3)
+        out = np.zeros(shape)
+        self._check(lib().gld_get_array(self._h, int(which), _ptr(out)))
+        return out
+
+    def set(self, which: int, values) -> None:
+        v = _f64(values)
+        self._check(lib().gld_set_array(self._h, int(which), _ptr(v)))
+
+    @property
+    def step_index(self) -> int:
+        s = C.c_int64()
+        self._check(lib().gld_get_step(self._h, C.byref(s)))
+        return int(s.value)
+
+    def set_step(self, step: int) -> None:
+        self._check(lib().gld_set_step(self._h, int(step)))
+
+    def coefs(self) -> dict:
+        M = self.m_max
+        Kd, A, ab, spec = np.zeros(M), np.zeros(2 * M - 1), np.zeros(2), np.zeros(2)
+        self._check(lib().gld_get_coefs(self._h, _ptr(Kd), _ptr(A), _ptr(ab), _ptr(spec)))
+        return dict(Kd=Kd, A=A, a=ab[0], b=ab[1], spec_min=spec[0], clamped_mass=spec[1])
+
+    PROF_NAMES = ("noise", "hist_conv", "pair_force_integrate", "cell_build", "cforce", "vacf")
+
+    def profile_steps(self, nsteps: int):
+        """Runs nsteps steps with per-kernel CUDA-event timing; returns
+        {family: (milliseconds, launches)}."""
+        ms, n = np.zeros(6), np.zeros(6, dtype=np.int64)
+        self._check(lib().gld_profile_steps(self._h, int(nsteps), _ptr(ms), _ptr(n)))
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.PROF_NAMES)}
+
+    def pairs(self) -> np.ndarray:
+        cnt = C.c_int64()
+        self._check(lib().gld_get_pairs(self._h, None, 0, C.byref(cnt)))
+        cap = int(cnt.value)
+        out = np.zeros((max(cap, 1), 2), dtype=np.int32)
+        self._check(lib().gld_get_pairs(self._h, _ptr(out), cap, C.byref(cnt)))
+        return out[: int(cnt.value)]
+
+
+# ---- single kernels on torch device tensors ------------------------------------
+def _dptr(t) -> int:
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    return int(t.data_ptr())
+
+
+def philox_dev(ctr, key, out, stream=None):
+    """ctr: uint32-valued int32/uint32 CUDA tensor [n, 4]; out: same shape."""
+    k = (C.c_uint32 * 2)(int(key[0]) & 0xffffffff, int(key[1]) & 0xffffffff)
+    st = lib().gld_philox_dev(_dptr(ctr), k, _dptr(out), int(ctr.shape[0]),
+                              _current_stream() if stream is None else stream)
+    if st != OK:
+        raise GLDError(st, "gld_philox_dev")
+
+
+def gauss3_dev(seed, particle, time, out, stream_id=0, stream=None):
+    """particle: int32 [n]; time: int64 [n]; out: float32 [n, 3] (CUDA tensors)."""
+    st = lib().gld_gauss3_dev(int(seed), _dptr(particle), _dptr(time), int(stream_id), _dptr(out),
+                              int(particle.shape[0]), _current_stream() if stream is None else stream)
+    if st != OK:
+        raise GLDError(st, "gld_gauss3_dev")
+
+
+def hist_conv_dev(ring, n_pad, m_max, step, coef, nacc, out, bf16=False, kahan=False, stream=None):
+    st = lib().gld_hist_conv_dev(_dptr(ring), int(bool(bf16)), int(n_pad), int(m_max), int(step),
+                                 _dptr(coef), int(nacc), _dptr(out), int(bool(kahan)),
+                                 _current_stream() if stream is None else stream)
+    if st != OK:
+        raise GLDError(st, "gld_hist_conv_dev")

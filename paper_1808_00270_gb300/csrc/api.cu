@@ -1,0 +1,815 @@
+// api.cu -- the C ABI of include/gld.h: context life cycle, device memory,
+// step orchestration and CUDA-graph replay.
+//
+// One step n -> n+1 is five kernels on the context's stream:
+//   hist_conv -> pair_force_integrate -> cell build (3 small kernels)
+//   -> cforce (F^C_{n+1}, V_{n+1}, n += 1) -> vacf (when enabled)
+// and every T steps one noise block (wgen + fir) produces F^R for the next T
+// steps.  The step counter lives on the device, so a graph holding one noise
+// block and T steps is captured once and replayed for as long as the kernels
+// stay the same.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "gld.h"
+#include "launch.h"
+
+using namespace gld;
+
+struct gld_ctx {
+    gld_params prm{};
+    StepParams P{};
+    int device = 0, num_sms = 0;
+    cudaStream_t st = nullptr;   // the caller's stream
+    cudaStream_t cap = nullptr;  // private stream used only to capture graphs
+    std::vector<void*> allocs;
+    ParticleBuffers B{};
+    float* W = nullptr;
+    float* Acp = nullptr;
+    int la = 0;
+    float* coef = nullptr;
+    float* g0 = nullptr;
+    float* ftab = nullptr;
+    double *d_Kd = nullptr, *d_C = nullptr, *d_Chat = nullptr, *d_A = nullptr, *d_scal = nullptr, *d_in = nullptr;
+    int* d_status = nullptr;
+    size_t ring_elem = 4;
+    long long host_step = 0, block_start = 0, noise_end = 0, last_fr_row = -1;
+    bool noise_valid = false, have_kernels = false;
+    std::vector<double> Kd, A;
+    double a = 1.0, b = 1.0, spec_min = 0.0, clamped = 0.0;
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_failed = false;
+    std::string msg;
+    gld_status latched = GLD_OK;
+};
+
+namespace {
+
+// Device-side and CUDA failures are latched (the context's device state can
+// no longer be trusted); argument and ordering errors only set the message.
+gld_status fail(gld_ctx* c, gld_status s, const std::string& m)
+{
+    if (c) {
+        c->msg = m;
+        const bool sticky = s == GLD_E_CUDA || s == GLD_E_NONFINITE || s == GLD_E_TIMEOUT;
+        if (sticky && c->latched == GLD_OK) c->latched = s;
+    }
+    return s;
+}
+
+gld_status cuda_check(gld_ctx* c, cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return GLD_OK;
+    return fail(c, GLD_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define GLD_TRY(expr)                          \
+    do {                                       \
+        gld_status s_ = (expr);                \
+        if (s_ != GLD_OK) return s_;           \
+    } while (0)
+
+#define GLD_CUDA(c, expr) GLD_TRY(cuda_check((c), (expr), #expr))
+
+void* dalloc(gld_ctx* c, size_t bytes)
+{
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (bytes == 0) bytes = 256;
+    void* p = nullptr;
+    if (c->prm.alloc) p = c->prm.alloc(bytes, c->prm.stream, c->prm.alloc_user);
+    else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+    if (p) {
+        c->allocs.push_back(p);
+        cudaMemsetAsync(p, 0, bytes, c->st);
+    }
+    return p;
+}
+
+void dfree(gld_ctx* c, void* p)
+{
+    if (!p) return;
+    for (size_t k = 0; k < c->allocs.size(); ++k)
+        if (c->allocs[k] == p) {
+            c->allocs.erase(c->allocs.begin() + (long)k);
+            break;
+        }
+    if (c->prm.free) c->prm.free(p, c->prm.stream, c->prm.alloc_user);
+    else cudaFree(p);
+}
+
+template <class Tp>
+Tp* alloc_n(gld_ctx* c, size_t count, bool& ok)
+{
+    Tp* p = (Tp*)dalloc(c, sizeof(Tp) * count);
+    if (!p) ok = false;
+    return p;
+}
+
+double wrap_host(double x, double L)
+{
+    x = std::fmod(x, L);
+    if (x < 0) x += L;
+    if (x >= L) x = 0.0;
+    return x;
+}
+
+// Host <-> device transfers of [n][3] vectors stored as float4 by id.
+gld_status upload_vec(gld_ctx* c, float4* dst, const double* src, bool wrap)
+{
+    const int n = c->P.n;
+    std::vector<float4> h((size_t)c->P.n_pad, make_float4(0.f, 0.f, 0.f, 0.f));
+    for (int i = 0; i < n; ++i) {
+        double x = src[3 * i], y = src[3 * i + 1], z = src[3 * i + 2];
+        if (wrap) {
+            x = wrap_host(x, c->prm.box);
+            y = wrap_host(y, c->prm.box);
+            z = wrap_host(z, c->prm.box);
+        }
+        float fx = (float)x, fy = (float)y, fz = (float)z;
+        if (wrap) {  // rounding to float may land on L
+            fx = fx >= c->P.box ? 0.f : fx;
+            fy = fy >= c->P.box ? 0.f : fy;
+            fz = fz >= c->P.box ? 0.f : fz;
+        }
+        h[i] = make_float4(fx, fy, fz, 0.f);
+    }
+    GLD_CUDA(c, cudaMemcpyAsync(dst, h.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, c->st));
+    GLD_CUDA(c, cudaStreamSynchronize(c->st));
+    return GLD_OK;
+}
+
+gld_status download_vec(gld_ctx* c, const float4* src, double* dst)
+{
+    const int n = c->P.n;
+    std::vector<float4> h((size_t)n);
+    GLD_CUDA(c, cudaMemcpyAsync(h.data(), src, sizeof(float4) * n, cudaMemcpyDeviceToHost, c->st));
+    GLD_CUDA(c, cudaStreamSynchronize(c->st));
+    for (int i = 0; i < n; ++i) {
+        dst[3 * i] = h[i].x;
+        dst[3 * i + 1] = h[i].y;
+        dst[3 * i + 2] = h[i].z;
+    }
+    return GLD_OK;
+}
+
+// [rows][3][n_pad] float planes <-> [rows][n][3] doubles.
+gld_status download_planes(gld_ctx* c, const float* src, int rows, double* dst)
+{
+    const int n = c->P.n;
+    const size_t np = c->P.n_pad;
+    std::vector<float> h(rows * 3 * np);
+    GLD_CUDA(c, cudaMemcpyAsync(h.data(), src, sizeof(float) * h.size(), cudaMemcpyDeviceToHost, c->st));
+    GLD_CUDA(c, cudaStreamSynchronize(c->st));
+    for (int r = 0; r < rows; ++r)
+        for (int i = 0; i < n; ++i)
+            for (int k = 0; k < 3; ++k) dst[((size_t)r * n + i) * 3 + k] = h[(r * 3 + k) * np + i];
+    return GLD_OK;
+}
+
+gld_status sync_and_check(gld_ctx* c)
+{
+    GLD_CUDA(c, cudaStreamSynchronize(c->st));
+    unsigned err = 0;
+    GLD_CUDA(c, cudaMemcpy(&err, &c->B.ctrl->err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (err & kErrNonFinite) fail(c, GLD_E_NONFINITE, "non-finite displacement produced on the device");
+    else if (err & kErrTimeout) fail(c, GLD_E_TIMEOUT, "a bounded device wait gave up");
+    else if (err & kErrNoise) fail(c, GLD_E_CUDA, "a step ran outside its noise block");
+    return c->latched;
+}
+
+void invalidate_graph(gld_ctx* c)
+{
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    c->graph_failed = false;
+}
+
+gld_status invalidate_noise(gld_ctx* c)
+{
+    c->noise_valid = false;
+    long long w[2] = {0, 1};  // {w_hi, w_lo}: w_hi < w_lo marks the W ring empty
+    GLD_CUDA(c, cudaMemcpyAsync(&c->B.ctrl->w_hi, w, sizeof(w), cudaMemcpyHostToDevice, c->st));
+    return GLD_OK;
+}
+
+gld_status rebuild_cells_and_fc(gld_ctx* c)
+{
+    GLD_CUDA(c, launch_cell_build(c->P, c->B, c->st));
+    GLD_CUDA(c, launch_cforce(c->P, c->B, 0, c->st));
+    return GLD_OK;
+}
+
+cudaError_t launch_noise(gld_ctx* c, cudaStream_t s)
+{
+    return launch_noise_block(c->P, c->B.ctrl, c->W, c->Acp, c->la, c->B.frblock, c->prm.seed, c->num_sms, s);
+}
+
+cudaError_t launch_one_step(gld_ctx* c, cudaStream_t s)
+{
+    cudaError_t e = launch_hist_conv(c->B.ring, c->P.hist_bf16, c->P.n_pad, c->P.m_max, c->B.ctrl, 0, c->coef,
+                                     c->P.nacc, c->B.conv, c->prm.kahan, s);
+    if (e != cudaSuccess) return e;
+    if ((e = launch_pair_force_integrate(c->P, c->B, s)) != cudaSuccess) return e;
+    if ((e = launch_cell_build(c->P, c->B, s)) != cudaSuccess) return e;
+    if ((e = launch_cforce(c->P, c->B, 1, s)) != cudaSuccess) return e;
+    return launch_vacf(c->P, c->B, s);
+}
+
+bool capture_graph(gld_ctx* c)
+{
+    if (c->gexec) return true;
+    if (c->graph_failed) return false;
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        cudaError_t e = launch_noise(c, c->cap);
+        for (int t = 0; t < c->P.T && e == cudaSuccess; ++t) e = launch_one_step(c, c->cap);
+        const cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
+        ok = e == cudaSuccess && e2 == cudaSuccess && g != nullptr;
+    }
+    if (ok) ok = cudaGraphInstantiate(&c->gexec, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+        c->gexec = nullptr;
+        c->graph_failed = true;
+        cudaGetLastError();
+    }
+    return ok;
+}
+
+int clamp_block(int t)
+{
+    if (t <= 16) return 16;
+    if (t <= 32) return 32;
+    return kMaxNoiseBlock;
+}
+
+}  // namespace
+
+extern "C" {
+
+void gld_params_default(gld_params* p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->mass = 1.0;
+    p->kT = 1.0;
+    p->dt = 0.005;
+    p->m_max = 2;
+    p->hist_dtype = GLD_HIST_F32;
+    p->vacf_stride = 1;
+    p->vacf_burnin = -1;
+    p->noise_block = kMaxNoiseBlock;
+    p->use_graphs = 1;
+}
+
+gld_status gld_create(const gld_params* p, const double* pos, const double* vel, gld_ctx** out)
+{
+    if (!out) return GLD_E_INVAL;
+    *out = nullptr;
+    if (!p || !pos || !vel) return GLD_E_INVAL;
+    if (p->n < 1 || p->m_max < 2 || p->m_max > 4096 || !(p->box > 0) || !(p->mass > 0) || !(p->dt > 0) ||
+        !(p->r_c > 0) || p->r_c > 0.5 * p->box || p->kT < 0 || p->r_c_min < 0 ||
+        (p->hist_dtype != GLD_HIST_F32 && p->hist_dtype != GLD_HIST_BF16) || p->vacf_len < 0 ||
+        (p->vacf_len > 0 && p->vacf_stride < 1))
+        return GLD_E_INVAL;
+    gld_ctx* c = new gld_ctx();
+    c->prm = *p;
+    c->st = (cudaStream_t)p->stream;
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        delete c;
+        return GLD_E_CUDA;
+    }
+    StepParams& P = c->P;
+    P.n = p->n;
+    P.n_pad = (p->n + 31) & ~31;
+    P.m_max = p->m_max;
+    P.H = p->m_max - 1;
+    P.Q = P.Qs = 0;
+    P.nacc = 1;
+    P.nr = 2;
+    // Cells of edge >= r_c (with a margin well above FP32 rounding of the
+    // coordinates), at most ~8 per particle; fewer than 3 per side -> 1.
+    int nc = (int)std::floor(p->box / p->r_c);
+    while (nc > 0 && p->box / nc < p->r_c * (1.0 + 1e-5)) --nc;
+    const int ncap = (int)std::floor(std::cbrt(8.0 * p->n));
+    if (nc > ncap) nc = ncap;
+    if (nc < 3) nc = 1;
+    P.nc = nc;
+    P.T = clamp_block(p->noise_block > 0 ? p->noise_block : kMaxNoiseBlock);
+    P.lw = (long long)P.T + 2LL * P.H;
+    P.box = (float)p->box;
+    P.half_box = 0.5f * P.box;
+    P.inv_cell = (float)(nc / p->box);
+    P.rc2 = (float)(p->r_c * p->r_c);
+    P.rc_min = (float)p->r_c_min;
+    P.inv_dr = 1.f;
+    P.inv_dt = (float)(1.0 / p->dt);
+    P.pos_v = (float)p->dt;
+    P.pos_f = (float)(p->dt * p->dt / (2.0 * p->mass));
+    P.vh_v = 1.f;
+    P.vh_fc = (float)(p->dt / (2.0 * p->mass));
+    P.vh_f = (float)(p->dt / p->mass);
+    P.vf_fc = (float)(p->dt / (2.0 * p->mass));
+    P.fc_mag = (float)(2.0 * p->A_cons / p->r_c);
+    P.inv_rc = (float)(1.0 / p->r_c);
+    P.hist_bf16 = p->hist_dtype == GLD_HIST_BF16;
+    P.vacf_len = p->vacf_len;
+    P.vacf_stride = p->vacf_stride > 0 ? p->vacf_stride : 1;
+    P.n_os = p->vacf_len > 0 ? (p->vacf_len + P.vacf_stride - 1) / P.vacf_stride : 0;
+    P.vacf_burnin = p->vacf_burnin < 0 ? 2LL * p->m_max : p->vacf_burnin;
+    c->ring_elem = P.hist_bf16 ? 2 : 4;
+
+    const size_t np = P.n_pad, n3 = 3 * np;
+    const int ncells = nc * nc * nc;
+    const int chunks = (ncells + 511) / 512;
+    ParticleBuffers& B = c->B;
+    bool ok = true;
+    B.ctrl = alloc_n<Ctrl>(c, 1, ok);
+    B.pos_sorted = alloc_n<float4>(c, np, ok);
+    B.pos_new = alloc_n<float4>(c, np, ok);
+    B.vel = alloc_n<float4>(c, np, ok);
+    B.vhalf = alloc_n<float4>(c, np, ok);
+    B.fc = alloc_n<float4>(c, np, ok);
+    B.fd = alloc_n<float4>(c, np, ok);
+    B.disp = alloc_n<float4>(c, np, ok);
+    B.ring = dalloc(c, c->ring_elem * n3 * P.H);
+    if (!B.ring) ok = false;
+    B.conv = alloc_n<float>(c, kMaxAcc * n3, ok);
+    B.frblock = alloc_n<float>(c, (size_t)P.T * n3, ok);
+    c->W = alloc_n<float>(c, (size_t)P.lw * n3, ok);
+    B.ncells = ncells;
+    B.cell_start = alloc_n<int>(c, ncells + 1, ok);
+    B.cell_count = alloc_n<int>(c, ncells, ok);
+    B.cell_head = alloc_n<int>(c, ncells, ok);
+    B.cell_next = alloc_n<int>(c, np, ok);
+    B.chunk_sum = alloc_n<int>(c, chunks, ok);
+    B.chunk_off = alloc_n<int>(c, chunks, ok);
+    B.vacf_gx = std::max(1, std::min((P.n + 255) / 256, 2 * c->num_sms));
+    B.vorig = alloc_n<float4>(c, (size_t)std::max(P.n_os, 1) * P.n, ok);
+    B.vpartial = alloc_n<double>(c, (size_t)std::max(P.n_os, 1) * B.vacf_gx, ok);
+    B.csum = alloc_n<double>(c, std::max(P.vacf_len, 1), ok);
+    B.ccnt = alloc_n<long long>(c, std::max(P.vacf_len, 1), ok);
+    B.norig = alloc_n<long long>(c, 1, ok);
+    B.vdone = alloc_n<unsigned>(c, 1, ok);
+    c->la = fir_copy_len(P.T, P.H);
+    c->Acp = alloc_n<float>(c, 4 * (size_t)c->la, ok);
+    c->coef = alloc_n<float>(c, (size_t)kMaxAcc * P.m_max, ok);
+    c->g0 = alloc_n<float>(c, 2 * kMaxQ, ok);
+    c->d_Kd = alloc_n<double>(c, P.m_max, ok);
+    c->d_C = alloc_n<double>(c, P.m_max, ok);
+    c->d_Chat = alloc_n<double>(c, P.m_max, ok);
+    c->d_A = alloc_n<double>(c, 2 * P.m_max, ok);
+    c->d_scal = alloc_n<double>(c, 4, ok);
+    c->d_status = alloc_n<int>(c, 1, ok);
+    c->d_in = alloc_n<double>(c, (size_t)(1 + 2 * kMaxQ) * P.m_max, ok);
+    B.g0 = c->g0;
+    if (!ok) {
+        gld_destroy(c);
+        return GLD_E_NOMEM;
+    }
+    gld_status s = GLD_OK;
+    if (cudaMemsetAsync(B.cell_head, 0xff, sizeof(int) * ncells, c->st) != cudaSuccess) s = GLD_E_CUDA;
+    Ctrl h{};
+    h.w_lo = 1;
+    h.w_hi = 0;
+    if (s == GLD_OK && cudaMemcpyAsync(B.ctrl, &h, sizeof(h), cudaMemcpyHostToDevice, c->st) != cudaSuccess) s = GLD_E_CUDA;
+    const int total = P.n;
+    if (s == GLD_OK && cudaMemcpyAsync(B.cell_start + ncells, &total, sizeof(int), cudaMemcpyHostToDevice, c->st) != cudaSuccess)
+        s = GLD_E_CUDA;
+    if (s == GLD_OK) s = upload_vec(c, B.pos_new, pos, true);
+    if (s == GLD_OK) s = upload_vec(c, B.vel, vel, false);
+    if (s == GLD_OK) s = rebuild_cells_and_fc(c);
+    if (s == GLD_OK) s = sync_and_check(c);
+    if (s != GLD_OK) {
+        gld_destroy(c);
+        return s;
+    }
+    *out = c;
+    return GLD_OK;
+}
+
+gld_status gld_set_kernels(gld_ctx* c, const double* Ks, int32_t Q, const double* g, const double* f, int32_t nr,
+                           double dr, const double* dKs_g, const double* dKs_f, int32_t Qs, int32_t conv)
+{
+    if (!c) return GLD_E_INVAL;
+    if (!Ks || Q < 0 || Q > kMaxQ || Qs < 0 || Qs > kMaxQ || (Q > 0 && (!g || !f)) || (Qs > 0 && (!dKs_g || !dKs_f)) ||
+        (Q + Qs > 0 && (nr < 2 || !(dr > 0))) || (conv != GLD_KCONT && conv != GLD_KDISCRETE))
+        return fail(c, GLD_E_INVAL, "gld_set_kernels: invalid kernel description");
+    const int M = c->P.m_max;
+    std::vector<double> in((size_t)(1 + 2 * kMaxQ) * M, 0.0);
+    std::memcpy(in.data(), Ks, sizeof(double) * M);
+    if (Q) std::memcpy(in.data() + M, g, sizeof(double) * (size_t)Q * M);
+    if (Qs) std::memcpy(in.data() + (size_t)(1 + Q) * M, dKs_g, sizeof(double) * (size_t)Qs * M);
+    GLD_CUDA(c, cudaMemcpyAsync(c->d_in, in.data(), sizeof(double) * in.size(), cudaMemcpyHostToDevice, c->st));
+    const int nt = Q + Qs;
+    const int nrr = nt > 0 ? nr : 2;
+    std::vector<float> tab((size_t)std::max(nt, 1) * nrr, 0.f);
+    for (int q = 0; q < Q; ++q)
+        for (int k = 0; k < nr; ++k) tab[(size_t)q * nr + k] = (float)f[(size_t)q * nr + k];
+    for (int q = 0; q < Qs; ++q)
+        for (int k = 0; k < nr; ++k) tab[(size_t)(Q + q) * nr + k] = (float)dKs_f[(size_t)q * nr + k];
+    if (c->ftab) dfree(c, c->ftab);
+    c->ftab = (float*)dalloc(c, sizeof(float) * tab.size());
+    if (!c->ftab) return fail(c, GLD_E_NOMEM, "gld_set_kernels: table allocation failed");
+    GLD_CUDA(c, cudaMemcpyAsync(c->ftab, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice, c->st));
+    PrepArgs a{};
+    a.m_max = M;
+    a.Q = Q;
+    a.Qs = Qs;
+    a.discrete = conv == GLD_KDISCRETE;
+    a.clamp = c->prm.psd_clamp;
+    a.T = c->P.T;
+    a.dt = c->prm.dt;
+    a.kT = c->prm.kT;
+    a.mass = c->prm.mass;
+    a.Ks = c->d_in;
+    a.g = c->d_in + M;
+    a.gs = c->d_in + (size_t)(1 + Q) * M;
+    a.Kd = c->d_Kd;
+    a.C = c->d_C;
+    a.Chat = c->d_Chat;
+    a.A = c->d_A;
+    a.scal = c->d_scal;
+    a.status = c->d_status;
+    a.coef = c->coef;
+    a.g0 = c->g0;
+    a.Acp = c->Acp;
+    a.la = c->la;
+    GLD_CUDA(c, launch_prep(a, c->st));
+    double scal[4];
+    int status = 0;
+    c->Kd.assign(M, 0.0);
+    c->A.assign(2 * M - 1, 0.0);
+    GLD_CUDA(c, cudaMemcpyAsync(scal, c->d_scal, sizeof(scal), cudaMemcpyDeviceToHost, c->st));
+    GLD_CUDA(c, cudaMemcpyAsync(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    GLD_CUDA(c, cudaMemcpyAsync(c->Kd.data(), c->d_Kd, sizeof(double) * M, cudaMemcpyDeviceToHost, c->st));
+    GLD_CUDA(c, cudaMemcpyAsync(c->A.data(), c->d_A, sizeof(double) * (2 * M - 1), cudaMemcpyDeviceToHost, c->st));
+    GLD_CUDA(c, cudaStreamSynchronize(c->st));
+    c->a = scal[0];
+    c->b = scal[1];
+    c->spec_min = scal[2];
+    c->clamped = scal[3];
+    invalidate_graph(c);
+    if (status != 0) {
+        c->have_kernels = false;
+        c->msg = "gld_set_kernels: the noise spectrum has a negative mode (not positive semi-definite)";
+        return GLD_E_NOT_PSD;
+    }
+    StepParams& P = c->P;
+    const double dt = c->prm.dt, M2 = 2.0 * c->prm.mass;
+    P.Q = Q;
+    P.Qs = Qs;
+    P.nacc = 1 + Q + Qs;
+    P.nr = nrr;
+    P.inv_dr = nt > 0 ? (float)(1.0 / dr) : 1.f;
+    P.pos_v = (float)(c->b * dt);
+    P.pos_f = (float)(c->b * dt * dt / M2);
+    P.vh_v = (float)c->a;
+    P.vh_fc = (float)(c->a * dt / M2);
+    P.vh_f = (float)(c->b * dt / c->prm.mass);
+    P.vf_fc = (float)(dt / M2);
+    c->B.ftab = c->ftab;
+    c->have_kernels = true;
+    GLD_TRY(invalidate_noise(c));
+    return sync_and_check(c);
+}
+
+gld_status gld_step(gld_ctx* c, int64_t nsteps)
+{
+    if (!c || nsteps < 0) return GLD_E_INVAL;
+    if (!c->have_kernels) return fail(c, GLD_E_STATE, "gld_step: gld_set_kernels has not succeeded");
+    if (c->latched != GLD_OK) return c->latched;
+    const int T = c->P.T;
+    while (nsteps > 0) {
+        if (!c->noise_valid || c->host_step >= c->noise_end) {
+            if (c->prm.use_graphs && nsteps >= T && capture_graph(c)) {
+                GLD_CUDA(c, cudaGraphLaunch(c->gexec, c->st));
+                c->block_start = c->host_step;
+                c->host_step += T;
+                c->noise_end = c->host_step;
+                c->noise_valid = true;
+                c->last_fr_row = T - 1;
+                nsteps -= T;
+                continue;
+            }
+            GLD_CUDA(c, launch_noise(c, c->st));
+            c->block_start = c->host_step;
+            c->noise_end = c->host_step + T;
+            c->noise_valid = true;
+        }
+        GLD_CUDA(c, launch_one_step(c, c->st));
+        c->last_fr_row = c->host_step - c->block_start;
+        ++c->host_step;
+        --nsteps;
+    }
+    return GLD_OK;
+}
+
+gld_status gld_sync(gld_ctx* c)
+{
+    if (!c) return GLD_E_INVAL;
+    return sync_and_check(c);
+}
+
+gld_status gld_vacf(gld_ctx* c, double* out, int64_t* n_origins)
+{
+    if (!c) return GLD_E_INVAL;
+    GLD_TRY(sync_and_check(c));
+    const int L = c->P.vacf_len;
+    long long no = 0;
+    if (L > 0) {
+        std::vector<double> s(L);
+        std::vector<long long> k(L);
+        GLD_CUDA(c, cudaMemcpy(s.data(), c->B.csum, sizeof(double) * L, cudaMemcpyDeviceToHost));
+        GLD_CUDA(c, cudaMemcpy(k.data(), c->B.ccnt, sizeof(long long) * L, cudaMemcpyDeviceToHost));
+        GLD_CUDA(c, cudaMemcpy(&no, c->B.norig, sizeof(long long), cudaMemcpyDeviceToHost));
+        if (out)
+            for (int l = 0; l < L; ++l) out[l] = k[l] > 0 ? s[l] / (3.0 * c->P.n * (double)k[l]) : 0.0;
+    }
+    if (n_origins) *n_origins = no;
+    return GLD_OK;
+}
+
+gld_status gld_get_state(gld_ctx* c, double* pos, double* vel)
+{
+    if (!c) return GLD_E_INVAL;
+    GLD_TRY(sync_and_check(c));
+    if (pos) GLD_TRY(download_vec(c, c->B.pos_new, pos));
+    if (vel) GLD_TRY(download_vec(c, c->B.vel, vel));
+    return GLD_OK;
+}
+
+gld_status gld_get_array(gld_ctx* c, int32_t which, double* out)
+{
+    if (!c || !out) return GLD_E_INVAL;
+    GLD_TRY(sync_and_check(c));
+    const StepParams& P = c->P;
+    const size_t np = P.n_pad;
+    switch (which) {
+    case GLD_ARR_POS: return download_vec(c, c->B.pos_new, out);
+    case GLD_ARR_VEL: return download_vec(c, c->B.vel, out);
+    case GLD_ARR_FC: return download_vec(c, c->B.fc, out);
+    case GLD_ARR_FD: return download_vec(c, c->B.fd, out);
+    case GLD_ARR_DISP: return download_vec(c, c->B.disp, out);
+    case GLD_ARR_FR:
+        if (c->last_fr_row < 0) return fail(c, GLD_E_STATE, "gld_get_array: no step has run");
+        return download_planes(c, c->B.frblock + (size_t)c->last_fr_row * 3 * np, 1, out);
+    case GLD_ARR_CONV: return download_planes(c, c->B.conv, P.nacc, out);
+    case GLD_ARR_HIST: {
+        const int H = P.H, n = P.n;
+        std::vector<unsigned char> h(c->ring_elem * 3 * np * H);
+        GLD_CUDA(c, cudaMemcpy(h.data(), c->B.ring, h.size(), cudaMemcpyDeviceToHost));
+        for (int m = 1; m <= H; ++m) {
+            long long slot = (c->host_step - m) % H;
+            if (slot < 0) slot += H;
+            for (int k = 0; k < 3; ++k)
+                for (int i = 0; i < n; ++i) {
+                    const size_t idx = ((size_t)slot * 3 + k) * np + i;
+                    float v;
+                    if (P.hist_bf16) {
+                        uint16_t b16;
+                        std::memcpy(&b16, h.data() + 2 * idx, 2);
+                        const uint32_t w = (uint32_t)b16 << 16;
+                        std::memcpy(&v, &w, 4);
+                    } else {
+                        std::memcpy(&v, h.data() + 4 * idx, 4);
+                    }
+                    out[((size_t)(m - 1) * n + i) * 3 + k] = v;
+                }
+        }
+        return GLD_OK;
+    }
+    default: return fail(c, GLD_E_INVAL, "gld_get_array: unknown array");
+    }
+}
+
+gld_status gld_set_array(gld_ctx* c, int32_t which, const double* in)
+{
+    if (!c || !in) return GLD_E_INVAL;
+    GLD_TRY(sync_and_check(c));
+    const StepParams& P = c->P;
+    switch (which) {
+    case GLD_ARR_POS:
+        GLD_TRY(upload_vec(c, c->B.pos_new, in, true));
+        GLD_TRY(rebuild_cells_and_fc(c));
+        return sync_and_check(c);
+    case GLD_ARR_VEL: return upload_vec(c, c->B.vel, in, false);
+    case GLD_ARR_FC: return upload_vec(c, c->B.fc, in, false);
+    case GLD_ARR_DISP: return upload_vec(c, c->B.disp, in, false);
+    case GLD_ARR_HIST: {
+        const int H = P.H, n = P.n;
+        const size_t np = P.n_pad;
+        std::vector<unsigned char> h(c->ring_elem * 3 * np * H, 0);
+        for (int m = 1; m <= H; ++m) {
+            long long slot = (c->host_step - m) % H;
+            if (slot < 0) slot += H;
+            for (int k = 0; k < 3; ++k)
+                for (int i = 0; i < n; ++i) {
+                    const size_t idx = ((size_t)slot * 3 + k) * np + i;
+                    const float v = (float)in[((size_t)(m - 1) * n + i) * 3 + k];
+                    if (P.hist_bf16) {
+                        const __nv_bfloat16 b = __float2bfloat16_rn(v);
+                        std::memcpy(h.data() + 2 * idx, &b, 2);
+                    } else {
+                        std::memcpy(h.data() + 4 * idx, &v, 4);
+                    }
+                }
+        }
+        GLD_CUDA(c, cudaMemcpy(c->B.ring, h.data(), h.size(), cudaMemcpyHostToDevice));
+        return GLD_OK;
+    }
+    default: return fail(c, GLD_E_INVAL, "gld_set_array: array is read-only or unknown");
+    }
+}
+
+gld_status gld_get_step(gld_ctx* c, int64_t* step)
+{
+    if (!c || !step) return GLD_E_INVAL;
+    *step = c->host_step;
+    return GLD_OK;
+}
+
+gld_status gld_set_step(gld_ctx* c, int64_t step)
+{
+    if (!c || step < 0) return GLD_E_INVAL;
+    GLD_TRY(sync_and_check(c));
+    c->host_step = step;
+    long long s = step;
+    GLD_CUDA(c, cudaMemcpyAsync(&c->B.ctrl->step, &s, sizeof(s), cudaMemcpyHostToDevice, c->st));
+    GLD_TRY(invalidate_noise(c));
+    c->last_fr_row = -1;
+    return sync_and_check(c);
+}
+
+gld_status gld_get_coefs(gld_ctx* c, double* Kd, double* A, double* ab, double* spec)
+{
+    if (!c) return GLD_E_INVAL;
+    if (c->Kd.empty()) return fail(c, GLD_E_STATE, "gld_get_coefs: no kernels set");
+    const int M = c->P.m_max;
+    if (Kd) std::memcpy(Kd, c->Kd.data(), sizeof(double) * M);
+    if (A) std::memcpy(A, c->A.data(), sizeof(double) * (2 * M - 1));
+    if (ab) {
+        ab[0] = c->a;
+        ab[1] = c->b;
+    }
+    if (spec) {
+        spec[0] = c->spec_min;
+        spec[1] = c->clamped;
+    }
+    return GLD_OK;
+}
+
+gld_status gld_get_pairs(gld_ctx* c, int32_t* pairs, int64_t cap, int64_t* count)
+{
+    if (!c || (!pairs && cap > 0) || cap < 0) return GLD_E_INVAL;
+    GLD_TRY(sync_and_check(c));
+    int* d_pairs = (int*)dalloc(c, sizeof(int) * 2 * (size_t)std::max<int64_t>(cap, 1));
+    unsigned long long* d_cnt = (unsigned long long*)dalloc(c, sizeof(unsigned long long));
+    if (!d_pairs || !d_cnt) {
+        dfree(c, d_pairs);
+        dfree(c, d_cnt);
+        return fail(c, GLD_E_NOMEM, "gld_get_pairs: allocation failed");
+    }
+    gld_status s = cuda_check(c, launch_pair_list(c->P, c->B, d_pairs, cap, d_cnt, c->st), "pair_list");
+    unsigned long long cnt = 0;
+    if (s == GLD_OK) s = cuda_check(c, cudaStreamSynchronize(c->st), "sync");
+    if (s == GLD_OK) s = cuda_check(c, cudaMemcpy(&cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost), "copy");
+    if (s == GLD_OK && cap > 0)
+        s = cuda_check(c, cudaMemcpy(pairs, d_pairs, sizeof(int) * 2 * (size_t)std::min<long long>(cap, (long long)cnt),
+                                     cudaMemcpyDeviceToHost), "copy");
+    if (count) *count = (int64_t)cnt;
+    cudaStreamSynchronize(c->st);
+    dfree(c, d_pairs);
+    dfree(c, d_cnt);
+    return s;
+}
+
+gld_status gld_profile_steps(gld_ctx* c, int64_t nsteps, double* ms, int64_t* launches)
+{
+    if (!c || nsteps < 0) return GLD_E_INVAL;
+    if (!c->have_kernels) return fail(c, GLD_E_STATE, "gld_profile_steps: gld_set_kernels has not succeeded");
+    GLD_TRY(sync_and_check(c));
+    cudaEvent_t ev[2 * GLD_PROF_N];
+    for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return fail(c, GLD_E_CUDA, "cudaEventCreate");
+    double acc[GLD_PROF_N] = {0};
+    int64_t cnt[GLD_PROF_N] = {0};
+    gld_status s = GLD_OK;
+    auto timed = [&](int fam, auto&& launch) -> gld_status {
+        if (cudaEventRecord(ev[2 * fam], c->st) != cudaSuccess) return fail(c, GLD_E_CUDA, "cudaEventRecord");
+        const cudaError_t e = launch();
+        if (e != cudaSuccess) return cuda_check(c, e, "launch");
+        if (cudaEventRecord(ev[2 * fam + 1], c->st) != cudaSuccess) return fail(c, GLD_E_CUDA, "cudaEventRecord");
+        cnt[fam] += 1;
+        return GLD_OK;
+    };
+    for (int64_t it = 0; it < nsteps && s == GLD_OK; ++it) {
+        bool used[GLD_PROF_N] = {false};
+        if (!c->noise_valid || c->host_step >= c->noise_end) {
+            s = timed(GLD_PROF_NOISE, [&] { return launch_noise(c, c->st); });
+            used[GLD_PROF_NOISE] = true;
+            c->block_start = c->host_step;
+            c->noise_end = c->host_step + c->P.T;
+            c->noise_valid = true;
+        }
+        if (s == GLD_OK) {
+            s = timed(GLD_PROF_HIST, [&] {
+                return launch_hist_conv(c->B.ring, c->P.hist_bf16, c->P.n_pad, c->P.m_max, c->B.ctrl, 0, c->coef,
+                                        c->P.nacc, c->B.conv, c->prm.kahan, c->st);
+            });
+            used[GLD_PROF_HIST] = true;
+        }
+        if (s == GLD_OK) {
+            s = timed(GLD_PROF_PAIR, [&] { return launch_pair_force_integrate(c->P, c->B, c->st); });
+            used[GLD_PROF_PAIR] = true;
+        }
+        if (s == GLD_OK) {
+            s = timed(GLD_PROF_CELL, [&] { return launch_cell_build(c->P, c->B, c->st); });
+            used[GLD_PROF_CELL] = true;
+        }
+        if (s == GLD_OK) {
+            s = timed(GLD_PROF_CFORCE, [&] { return launch_cforce(c->P, c->B, 1, c->st); });
+            used[GLD_PROF_CFORCE] = true;
+        }
+        if (s == GLD_OK && c->P.vacf_len > 0) {
+            s = timed(GLD_PROF_VACF, [&] { return launch_vacf(c->P, c->B, c->st); });
+            used[GLD_PROF_VACF] = true;
+        }
+        if (s != GLD_OK) break;
+        c->last_fr_row = c->host_step - c->block_start;
+        ++c->host_step;
+        if (cudaEventSynchronize(ev[2 * GLD_PROF_CFORCE + 1]) != cudaSuccess ||
+            (c->P.vacf_len > 0 && cudaEventSynchronize(ev[2 * GLD_PROF_VACF + 1]) != cudaSuccess)) {
+            s = fail(c, GLD_E_CUDA, "cudaEventSynchronize");
+            break;
+        }
+        for (int f = 0; f < GLD_PROF_N; ++f) {
+            if (!used[f]) continue;
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, ev[2 * f], ev[2 * f + 1]) == cudaSuccess) acc[f] += t;
+        }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (cnt[GLD_PROF_CELL]) cnt[GLD_PROF_CELL] *= 3;  // three kernels per build
+    if (cnt[GLD_PROF_NOISE]) cnt[GLD_PROF_NOISE] *= 2;  // white noise + moving average
+    for (int f = 0; f < GLD_PROF_N; ++f) {
+        if (ms) ms[f] += acc[f];
+        if (launches) launches[f] += cnt[f];
+    }
+    if (s != GLD_OK) return s;
+    return sync_and_check(c);
+}
+
+const char* gld_last_error(const gld_ctx* c) { return c ? c->msg.c_str() : "null context"; }
+
+gld_status gld_destroy(gld_ctx* c)
+{
+    if (!c) return GLD_E_INVAL;
+    if (c->st || c->cap) cudaStreamSynchronize(c->st);
+    invalidate_graph(c);
+    for (void* p : c->allocs) {
+        if (c->prm.free) c->prm.free(p, c->prm.stream, c->prm.alloc_user);
+        else cudaFree(p);
+    }
+    if (c->cap) cudaStreamDestroy(c->cap);
+    delete c;
+    return GLD_OK;
+}
+
+gld_status gld_philox_dev(const uint32_t* ctr, const uint32_t key[2], uint32_t* out, int64_t n, void* stream)
+{
+    if (!key || n < 0 || (n > 0 && (!ctr || !out))) return GLD_E_INVAL;
+    return launch_philox(ctr, key[0], key[1], out, n, (cudaStream_t)stream) == cudaSuccess ? GLD_OK : GLD_E_CUDA;
+}
+
+gld_status gld_gauss3_dev(uint64_t seed, const uint32_t* particle, const int64_t* time, uint32_t stream_id,
+                          float* out, int64_t n, void* stream)
+{
+    if (n < 0 || (n > 0 && (!particle || !time || !out))) return GLD_E_INVAL;
+    return launch_gauss3((uint32_t)seed, (uint32_t)(seed >> 32), particle, (const long long*)time, stream_id, out, n,
+                         (cudaStream_t)stream) == cudaSuccess
+               ? GLD_OK
+               : GLD_E_CUDA;
+}
+
+gld_status gld_hist_conv_dev(const void* ring, int32_t bf16, int32_t n_pad, int32_t m_max, int64_t step,
+                             const float* coef, int32_t nacc, float* out, int32_t kahan, void* stream)
+{
+    if (!ring || !coef || !out || n_pad <= 0 || n_pad % 32 || m_max < 2 || nacc < 1 || nacc > kMaxAcc ||
+        ((uintptr_t)ring & 15) || ((uintptr_t)out & 15))
+        return GLD_E_INVAL;
+    return launch_hist_conv(ring, bf16, n_pad, m_max, nullptr, step, coef, nacc, out, kahan, (cudaStream_t)stream) ==
+                   cudaSuccess
+               ? GLD_OK
+               : GLD_E_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,413 @@
+// k_particles.cu -- the per-particle kernels of one GLD step.
+//
+//   pair_force_integrate  F^D_n (Eq. dissipative_force2) from the history
+//                         projections and the neighbours at R_n, then the
+//                         position half of Eq. GLD_integrator (with b, App. A),
+//                         the new displacement into the history ring, and the
+//                         velocity terms that do not need F^C_{n+1}.
+//   cell build            cell list at R_{n+1}: per-cell linked lists, a
+//                         chunked exclusive scan, cells filled in id order.
+//   cforce                F^C_{n+1} = sum_j 2A/r_c (1 - r/r_c) e_ij and the
+//                         rest of the velocity update; advances n.
+//   vacf                  FP64 accumulation of <V(t0+tau) V(t0)> (Sec. III A).
+//
+// Particles are visited in cell order (thread k handles the k-th particle of
+// the cell-sorted list) so that a warp's neighbour cells overlap; all
+// per-particle arrays stay indexed by the particle id, which never changes,
+// so the displacement history is never permuted.
+#include <cuda_bf16.h>
+
+#include "launch.h"
+
+namespace gld {
+
+namespace {
+
+constexpr int kPairThreads = 128;
+constexpr int kCellThreads = 512;
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ float dot3(float ax, float ay, float az, float bx, float by, float bz)
+{
+    return fmaf(ax, bx, fmaf(ay, by, az * bz));
+}
+
+__global__ void __launch_bounds__(kPairThreads)
+    pair_force_integrate(const StepParams P, const Ctrl* __restrict__ ctrl, const float4* __restrict__ pos_sorted,
+                         const int* __restrict__ cell_start, const float4* __restrict__ vel,
+                         const float4* __restrict__ fc, const float* __restrict__ conv,
+                         const float* __restrict__ frblock, const float* __restrict__ ftab,
+                         const float* __restrict__ g0, void* __restrict__ ring, float4* __restrict__ pos_new,
+                         float4* __restrict__ vhalf, float4* __restrict__ fd_out, float4* __restrict__ disp,
+                         unsigned* __restrict__ err)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P.n) return;
+    const long long n = ctrl->step;
+    const long long np = P.n_pad;
+    const float4 pi = pos_sorted[k];
+    const int id = __float_as_int(pi.w);
+    const float4 vi = vel[id];
+
+    float ps[kMaxQ][3];
+#pragma unroll
+    for (int q = 0; q < kMaxQ; ++q) {
+        if (q < P.Qs) {
+            const float* p = conv + (size_t)(1 + P.Q + q) * 3 * np + id;
+            ps[q][0] = p[0];
+            ps[q][1] = p[np];
+            ps[q][2] = p[2 * np];
+        } else {
+            ps[q][0] = ps[q][1] = ps[q][2] = 0.f;
+        }
+    }
+    float f0x = 0.f, f0y = 0.f, f0z = 0.f;  // instantaneous (m = 0) pair terms
+    float fhx = 0.f, fhy = 0.f, fhz = 0.f;  // history pair terms (times -1, before 1/dt)
+    if (P.Q + P.Qs > 0) {
+        for_each_neighbor(pi, id, pos_sorted, cell_start, P, [&](int jd, float dx, float dy, float dz, float r2) {
+            const float r = sqrtf(r2);
+            const float inv_r = 1.0f / r;
+            const float ex = dx * inv_r, ey = dy * inv_r, ez = dz * inv_r;
+            const float x = fmaxf(r, P.rc_min) * P.inv_dr;
+            const float4 vj = __ldg(vel + jd);
+            const float evj = dot3(ex, ey, ez, vj.x, vj.y, vj.z);
+            const float evi = dot3(ex, ey, ez, vi.x, vi.y, vi.z);
+            float inst = 0.f, hist = 0.f;
+            for (int q = 0; q < P.Q; ++q) {
+                const float fq = table_at(ftab + q * P.nr, P.nr, x);
+                const float* pj = conv + (size_t)(1 + q) * 3 * np + jd;
+                const float epj = dot3(ex, ey, ez, __ldg(pj), __ldg(pj + np), __ldg(pj + 2 * np));
+                inst = fmaf(fq * __ldg(g0 + q), evj, inst);
+                hist = fmaf(fq, epj, hist);
+            }
+            for (int q = 0; q < P.Qs; ++q) {
+                const float fq = table_at(ftab + (P.Q + q) * P.nr, P.nr, x);
+                const float epi = dot3(ex, ey, ez, ps[q][0], ps[q][1], ps[q][2]);
+                inst = fmaf(fq * __ldg(g0 + P.Q + q), evi, inst);
+                hist = fmaf(fq, epi, hist);
+            }
+            f0x = fmaf(-inst, ex, f0x); f0y = fmaf(-inst, ey, f0y); f0z = fmaf(-inst, ez, f0z);
+            fhx = fmaf(-hist, ex, fhx); fhy = fmaf(-hist, ey, fhy); fhz = fmaf(-hist, ez, fhz);
+        });
+    }
+    // F^D = -sum_j (K^p_0 V_j + dK^s_0 V_i) - (1/dt) (S_i + sum_j ...)
+    const float sx = conv[id], sy = conv[np + id], sz = conv[2 * np + id];
+    const float fdx = fmaf(fhx - sx, P.inv_dt, f0x);
+    const float fdy = fmaf(fhy - sy, P.inv_dt, f0y);
+    const float fdz = fmaf(fhz - sz, P.inv_dt, f0z);
+    const long long row = n - ctrl->noise_n0;
+    float frx = 0.f, fry = 0.f, frz = 0.f;
+    if (row >= 0 && row < P.T) {
+        const float* fr = frblock + (size_t)row * 3 * np + id;
+        frx = fr[0];
+        fry = fr[np];
+        frz = fr[2 * np];
+    } else if (k == 0) {
+        atomicOr(err, kErrNoise);  // the host scheduled a step outside the noise block
+    }
+    const float4 fci = fc[id];
+    // Eq. GLD_integrator, position: dR = b dt V + b dt^2/(2M) (F^C + F^D + F^R)
+    const float dRx = fmaf(P.pos_f, fci.x + fdx + frx, P.pos_v * vi.x);
+    const float dRy = fmaf(P.pos_f, fci.y + fdy + fry, P.pos_v * vi.y);
+    const float dRz = fmaf(P.pos_f, fci.z + fdz + frz, P.pos_v * vi.z);
+    const long long slot = n % P.H;
+    if (P.hist_bf16) {
+        __nv_bfloat16* h = (__nv_bfloat16*)ring + (size_t)slot * 3 * np + id;
+        h[0] = __float2bfloat16_rn(dRx);
+        h[np] = __float2bfloat16_rn(dRy);
+        h[2 * np] = __float2bfloat16_rn(dRz);
+    } else {
+        float* h = (float*)ring + (size_t)slot * 3 * np + id;
+        h[0] = dRx;
+        h[np] = dRy;
+        h[2 * np] = dRz;
+    }
+    pos_new[id] = make_float4(wrap_box(__fadd_rn(pi.x, dRx), P.box), wrap_box(__fadd_rn(pi.y, dRy), P.box),
+                              wrap_box(__fadd_rn(pi.z, dRz), P.box), 0.f);
+    // velocity part known now: a V + a dt/(2M) F^C_n + b dt/M (F^D + F^R)
+    vhalf[id] = make_float4(fmaf(P.vh_f, fdx + frx, fmaf(P.vh_fc, fci.x, P.vh_v * vi.x)),
+                            fmaf(P.vh_f, fdy + fry, fmaf(P.vh_fc, fci.y, P.vh_v * vi.y)),
+                            fmaf(P.vh_f, fdz + frz, fmaf(P.vh_fc, fci.z, P.vh_v * vi.z)), 0.f);
+    fd_out[id] = make_float4(fdx, fdy, fdz, 0.f);
+    const float4 d = disp[id];
+    disp[id] = make_float4(d.x + dRx, d.y + dRy, d.z + dRz, 0.f);
+    if (!(isfinite(dRx) && isfinite(dRy) && isfinite(dRz))) atomicOr(err, kErrNonFinite);
+}
+
+// ---- cell list --------------------------------------------------------------
+__global__ void cell_assign(const StepParams P, const float4* __restrict__ pos, int* __restrict__ head,
+                            int* __restrict__ next, int* __restrict__ count)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    const int c = cell_of(pos[i], P);
+    atomicAdd(count + c, 1);
+    next[i] = atomicExch(head + c, i);
+}
+
+// Exclusive block scan of one int per thread; returns the block total.
+__device__ int block_exclusive_scan(int v, int* out_excl)
+{
+    __shared__ int warp_tot[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        int t = lane < nw ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) warp_tot[lane] = t;
+    }
+    __syncthreads();
+    const int base = w > 0 ? warp_tot[w - 1] : 0;
+    *out_excl = base + x - v;
+    const int total = warp_tot[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return total;
+}
+
+// Chunk sums of the cell counts; the last block to finish scans them.
+__global__ void __launch_bounds__(kCellThreads)
+    cell_scan(const int* __restrict__ count, int ncells, int* __restrict__ chunk_sum, int* __restrict__ chunk_off,
+              unsigned* __restrict__ done)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    int excl;
+    const int tot = block_exclusive_scan(c < ncells ? count[c] : 0, &excl);
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        chunk_sum[blockIdx.x] = tot;
+        __threadfence();
+        last = atomicAdd(done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    int carry = 0;
+    for (int base = 0; base < (int)gridDim.x; base += blockDim.x) {
+        const int b = base + threadIdx.x;
+        const int v = b < (int)gridDim.x ? ((volatile int*)chunk_sum)[b] : 0;
+        int e;
+        const int t = block_exclusive_scan(v, &e);
+        if (b < (int)gridDim.x) chunk_off[b] = carry + e;
+        carry += t;
+    }
+    if (threadIdx.x == 0) *done = 0u;
+}
+
+// Cell starts, and each cell's particles in increasing id order.
+__global__ void __launch_bounds__(kCellThreads)
+    cell_fill(const StepParams P, int ncells, const float4* __restrict__ pos, int* __restrict__ count,
+              int* __restrict__ head, const int* __restrict__ next, const int* __restrict__ chunk_off,
+              int* __restrict__ cell_start, float4* __restrict__ pos_sorted)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int cnt = c < ncells ? count[c] : 0;
+    int excl;
+    block_exclusive_scan(cnt, &excl);
+    if (c >= ncells) return;
+    const int start = chunk_off[blockIdx.x] + excl;
+    cell_start[c] = start;
+    int j = head[c];
+    for (int r = 0; r < cnt && j >= 0; ++r) {
+        // insertion by id into [start, start + r)
+        int p = start + r;
+        while (p > start && __float_as_int(pos_sorted[p - 1].w) > j) {
+            pos_sorted[p] = pos_sorted[p - 1];
+            --p;
+        }
+        const float4 x = pos[j];
+        pos_sorted[p] = make_float4(x.x, x.y, x.z, __int_as_float(j));
+        j = next[j];
+    }
+    head[c] = -1;
+    count[c] = 0;
+}
+
+// ---- conservative force and velocity finish --------------------------------
+template <bool STEP>
+__global__ void __launch_bounds__(kThreads)
+    cforce(const StepParams P, Ctrl* __restrict__ ctrl, const float4* __restrict__ pos_sorted,
+           const int* __restrict__ cell_start, const float4* __restrict__ vhalf, float4* __restrict__ vel,
+           float4* __restrict__ fc)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < P.n) {
+        const float4 pi = pos_sorted[k];
+        const int id = __float_as_int(pi.w);
+        float fx = 0.f, fy = 0.f, fz = 0.f;
+        for_each_neighbor(pi, id, pos_sorted, cell_start, P, [&](int, float dx, float dy, float dz, float r2) {
+            const float r = sqrtf(r2);
+            // -dU/dr e_ij with U = A (1 - r/r_c)^2, e_ij = (R_i - R_j)/r
+            const float s = P.fc_mag * (1.0f - r * P.inv_rc) / r;
+            fx = fmaf(s, dx, fx);
+            fy = fmaf(s, dy, fy);
+            fz = fmaf(s, dz, fz);
+        });
+        fc[id] = make_float4(fx, fy, fz, 0.f);
+        if (STEP) {
+            const float4 vh = vhalf[id];
+            vel[id] = make_float4(fmaf(P.vf_fc, fx, vh.x), fmaf(P.vf_fc, fy, vh.y), fmaf(P.vf_fc, fz, vh.z), 0.f);
+        }
+    }
+    if (STEP) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(&ctrl->done_cforce, 1u) == gridDim.x - 1) {
+                ctrl->step += 1;
+                ctrl->done_cforce = 0u;
+                __threadfence();
+            }
+        }
+    }
+}
+
+// ---- velocity autocorrelation ------------------------------------------------
+// grid (gx, n_os): blockIdx.y = age j of the origin (0 = newest).
+__global__ void __launch_bounds__(kThreads)
+    vacf(const StepParams P, const Ctrl* __restrict__ ctrl, const float4* __restrict__ vel,
+         float4* __restrict__ vorig, double* __restrict__ partial, double* __restrict__ csum,
+         long long* __restrict__ ccnt, long long* __restrict__ norig, unsigned* __restrict__ done)
+{
+    const long long t = ctrl->step;  // V_t was completed by the previous kernel
+    if (t < P.vacf_burnin) return;  // uniform over the grid
+    const long long rel = t - P.vacf_burnin;
+    const long long o_now = rel / P.vacf_stride;
+    const bool is_origin = (rel % P.vacf_stride) == 0;
+    const int j = blockIdx.y;
+    const long long o = o_now - j;
+    const long long lag = rel - o * (long long)P.vacf_stride;
+    const bool active = o >= 0 && lag < P.vacf_len;
+    const bool fresh = j == 0 && is_origin;
+    double s = 0.0;
+    if (active) {
+        float acc = 0.f;
+        const float4* v0 = vorig + (size_t)(o % P.n_os) * P.n;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+            const float4 v = vel[i];
+            const float4 w = fresh ? v : v0[i];
+            acc += dot3(v.x, v.y, v.z, w.x, w.y, w.z);
+            if (fresh) vorig[(size_t)(o % P.n_os) * P.n + i] = v;
+        }
+        s = (double)acc;
+    }
+    // deterministic block reduction in FP64
+    __shared__ double red[kThreads];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        partial[(size_t)j * gridDim.x + blockIdx.x] = red[0];
+        __threadfence();
+        last = atomicAdd(done, 1u) == gridDim.x * gridDim.y - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int jj = 0; jj < (int)gridDim.y; ++jj) {
+        const long long oo = o_now - jj;
+        const long long lg = rel - oo * (long long)P.vacf_stride;
+        if (!(oo >= 0 && lg < P.vacf_len)) continue;  // uniform in the block
+        double v = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+            v += ((volatile double*)partial)[(size_t)jj * gridDim.x + b];
+        red[threadIdx.x] = v;
+        __syncthreads();
+        for (int w = kThreads / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            csum[lg] += red[0];
+            ccnt[lg] += 1;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (is_origin) *norig += 1;
+        *done = 0u;
+    }
+}
+
+// ---- explicit pair list (checks of the traversal) ---------------------------
+__global__ void pair_list(const StepParams P, const float4* __restrict__ pos_sorted, const int* __restrict__ cell_start,
+                          int* __restrict__ pairs, long long cap, unsigned long long* __restrict__ count)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P.n) return;
+    const float4 pi = pos_sorted[k];
+    const int id = __float_as_int(pi.w);
+    for_each_neighbor(pi, id, pos_sorted, cell_start, P, [&](int jd, float, float, float, float) {
+        if (jd > id) {
+            const unsigned long long slot = atomicAdd(count, 1ull);
+            if ((long long)slot < cap) {
+                pairs[2 * slot] = id;
+                pairs[2 * slot + 1] = jd;
+            }
+        }
+    });
+}
+
+}  // namespace
+
+cudaError_t launch_pair_force_integrate(const StepParams& P, const ParticleBuffers& B, cudaStream_t st)
+{
+    const unsigned grid = (unsigned)((P.n + kPairThreads - 1) / kPairThreads);
+    pair_force_integrate<<<grid, kPairThreads, 0, st>>>(P, B.ctrl, B.pos_sorted, B.cell_start, B.vel, B.fc, B.conv,
+                                                        B.frblock, B.ftab, B.g0, B.ring, B.pos_new, B.vhalf, B.fd,
+                                                        B.disp, &B.ctrl->err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cell_build(const StepParams& P, const ParticleBuffers& B, cudaStream_t st)
+{
+    cell_assign<<<(P.n + kThreads - 1) / kThreads, kThreads, 0, st>>>(P, B.pos_new, B.cell_head, B.cell_next,
+                                                                       B.cell_count);
+    const unsigned chunks = (unsigned)((B.ncells + kCellThreads - 1) / kCellThreads);
+    cell_scan<<<chunks, kCellThreads, 0, st>>>(B.cell_count, B.ncells, B.chunk_sum, B.chunk_off, &B.ctrl->done_scan);
+    cell_fill<<<chunks, kCellThreads, 0, st>>>(P, B.ncells, B.pos_new, B.cell_count, B.cell_head, B.cell_next,
+                                               B.chunk_off, B.cell_start, B.pos_sorted);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cforce(const StepParams& P, const ParticleBuffers& B, int mode, cudaStream_t st)
+{
+    const unsigned grid = (unsigned)((P.n + kThreads - 1) / kThreads);
+    if (mode) cforce<true><<<grid, kThreads, 0, st>>>(P, B.ctrl, B.pos_sorted, B.cell_start, B.vhalf, B.vel, B.fc);
+    else cforce<false><<<grid, kThreads, 0, st>>>(P, B.ctrl, B.pos_sorted, B.cell_start, B.vhalf, B.vel, B.fc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vacf(const StepParams& P, const ParticleBuffers& B, cudaStream_t st)
+{
+    if (P.vacf_len <= 0) return cudaSuccess;
+    dim3 grid(B.vacf_gx, P.n_os);
+    vacf<<<grid, kThreads, 0, st>>>(P, B.ctrl, B.vel, B.vorig, B.vpartial, B.csum, B.ccnt, B.norig, B.vdone);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_list(const StepParams& P, const ParticleBuffers& B, int* pairs, long long cap,
+                             unsigned long long* count, cudaStream_t st)
+{
+    pair_list<<<(P.n + kThreads - 1) / kThreads, kThreads, 0, st>>>(P, B.pos_sorted, B.cell_start, pairs, cap, count);
+    return cudaGetLastError();
+}
+
+int cell_chunk_threads() { return kCellThreads; }
+
+}  // namespace gld

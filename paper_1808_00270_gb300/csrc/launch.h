@@ -1,0 +1,75 @@
+// launch.h -- host-side launchers of the GLD kernels (one per kernel family),
+// shared by the translation units of the library.  All return the CUDA error
+// of the launch.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "gld_internal.cuh"
+
+namespace gld {
+
+// History convolution (k_history.cu).  ctrl != nullptr: the step is read on
+// the device; otherwise `step` is used.
+cudaError_t launch_hist_conv(const void* ring, int bf16, int n_pad, int m_max, const Ctrl* ctrl,
+                             long long step, const float* coef, int nacc, float* out, int kahan,
+                             cudaStream_t st);
+
+// Particle kernels (k_particles.cu).
+struct ParticleBuffers {
+    Ctrl* ctrl;
+    float4 *pos_sorted, *pos_new, *vel, *vhalf, *fc, *fd, *disp;
+    void* ring;
+    float* conv;
+    float* frblock;
+    const float* ftab;
+    const float* g0;
+    int *cell_start, *cell_count, *cell_head, *cell_next, *chunk_sum, *chunk_off;
+    int ncells;
+    // VACF
+    float4* vorig;
+    double* vpartial;
+    double* csum;
+    long long* ccnt;
+    long long* norig;
+    unsigned* vdone;
+    int vacf_gx;
+};
+
+cudaError_t launch_pair_force_integrate(const StepParams& P, const ParticleBuffers& B, cudaStream_t st);
+cudaError_t launch_cell_build(const StepParams& P, const ParticleBuffers& B, cudaStream_t st);
+// mode 0: F^C only (initialisation); mode 1: F^C_{n+1}, V_{n+1}, step += 1.
+cudaError_t launch_cforce(const StepParams& P, const ParticleBuffers& B, int mode, cudaStream_t st);
+cudaError_t launch_vacf(const StepParams& P, const ParticleBuffers& B, cudaStream_t st);
+cudaError_t launch_pair_list(const StepParams& P, const ParticleBuffers& B, int* pairs,
+                             long long cap, unsigned long long* count, cudaStream_t st);
+
+// Noise and kernel preparation (k_noise.cu).
+struct PrepArgs {
+    int m_max, Q, Qs, discrete, clamp, T;
+    double dt, kT, mass;
+    const double* Ks;   // [m_max]
+    const double* g;    // [Q][m_max]
+    const double* gs;   // [Qs][m_max]
+    double* Kd;         // [m_max] discrete K^s
+    double* C;          // [m_max]
+    double* Chat;       // [m_max]
+    double* A;          // [2 m_max - 1]
+    double* scal;       // [4]: a, b, min mode, clamped mass
+    int* status;        // 0 or -3
+    float* coef;        // [1+Q+Qs][m_max] discrete weights for the convolution
+    float* g0;          // [Q+Qs] discrete m = 0 weights
+    float* Acp;         // [4][la] shifted zero-padded copies of A for the FIR
+    int la;
+};
+cudaError_t launch_prep(const PrepArgs& a, cudaStream_t st);
+int fir_copy_len(int T, int H);
+
+cudaError_t launch_noise_block(const StepParams& P, Ctrl* ctrl, float* W, const float* Acp, int la,
+                               float* frblock, unsigned long long seed, int num_sms, cudaStream_t st);
+cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out, long long n,
+                          cudaStream_t st);
+cudaError_t launch_gauss3(uint32_t k0, uint32_t k1, const uint32_t* particle, const long long* time,
+                          uint32_t stream_id, float* out, long long n, cudaStream_t st);
+
+}  // namespace gld

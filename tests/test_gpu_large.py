@@ -1,0 +1,74 @@
+"""Parity at the full sizes (needs a GPU): the 262144-particle, m_max = 400
+suspension on sampled particles in the launch configuration bench.py times
+(graphs, 64-step noise blocks), and the VACF of the 4096-particle system over
+10^4 steps against an independent oracle run."""
+import numpy as np
+import pytest
+
+import oracle
+from gld_cases import make_gpu, make_oracle, oracle_from_gpu, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def test_large_suspension_sampled_forces():
+    from paper_1808_00270_gb300 import ARR_FD, ARR_FR, inputs
+    w = inputs.LARGE
+    gpu = make_gpu(w)
+    gpu.step(448)  # past m_max - 1: every ring slot holds a real displacement
+    ref = oracle_from_gpu(w, gpu)
+    rng = np.random.default_rng(11)
+    idx = np.sort(rng.choice(w.n, size=1500, replace=False)).astype(np.int32)
+    fd_ref, fr_ref = ref.forces_subset(idx)
+    gpu.step(1)
+    fd, fr = gpu.get(ARR_FD)[idx], gpu.get(ARR_FR)[idx]
+    assert rel_l2(fd, fd_ref) < 1e-5
+    assert rel_l2(fr, fr_ref) < 1e-5
+
+
+def test_vacf_accumulator_definition():
+    """The FP64 VACF accumulator equals the definition evaluated on the
+    recorded velocities with the same origin schedule."""
+    from paper_1808_00270_gb300 import inputs
+    w = inputs.SMALL
+    L, stride, burn = 12, 3, 5
+    gpu = make_gpu(w, vacf_len=L, vacf_stride=stride, vacf_burnin=burn)
+    V = {0: gpu.get_state()[1]}
+    for t in range(1, 60):
+        gpu.step(1)
+        V[t] = gpu.get_state()[1]
+    acc, cnt = np.zeros(L), np.zeros(L)
+    for t0 in range(burn, 60, stride):
+        for lag in range(L):
+            if t0 + lag < 60:
+                acc[lag] += (V[t0 + lag] * V[t0]).sum()
+                cnt[lag] += 1
+    want = acc / (3 * w.n * cnt)
+    c, n0 = gpu.vacf()
+    assert n0 == len(range(burn, 60, stride))
+    assert np.max(np.abs(c - want)) < 1e-6 * np.abs(want).max()
+
+
+def test_vacf_medium_matches_oracle():
+    from paper_1808_00270_gb300 import inputs
+    w = inputs.MEDIUM
+    kw = dict(vacf_len=200, vacf_stride=10, vacf_burnin=400)
+    gpu = make_gpu(w, **kw)
+    gpu.step(w.steps)
+    c_gpu, n_gpu = gpu.vacf()
+    ref = make_oracle(w, **kw)
+    ref.step(w.steps)
+    c_ref, n_ref = ref.vacf()
+    assert n_gpu == n_ref
+    dev = np.max(np.abs(c_gpu - c_ref)) / c_ref[0]
+    print(f"VACF max deviation / C(0) = {dev:.4f}")
+    assert dev <= 0.02
