@@ -205,7 +205,7 @@ gld_status gld_philox_dev(const uint32_t* ctr, const uint32_t key[2], uint32_t* 
 
 /* White noise W_{i,k}: for item j, particle[j] and time[j] give the counter
  * (particle, (time + 2^62) low word, high word, stream_id); out [n][3] float.
- * u = ((x >> 8) + 1/2) 2^-24; Box-Muller on words (0,1) gives x, y and on
+ * u = ((x >> 9) + 1/2) 2^-23 (exact in FP32); Box-Muller on words (0,1) gives x, y and on
  * (2,3) gives z (Sec. II C requires uncorrelated unit Gaussians). */
 gld_status gld_gauss3_dev(uint64_t seed, const uint32_t* particle, const int64_t* time,
                           uint32_t stream_id, float* out, int64_t n, void* stream);

@@ -89,10 +89,11 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
 }
 
 /* Counter of the white noise W_{i,k}: (particle, time+2^62 low, high, stream).
- * Key: the 64-bit seed split into two words.  Uniform u = ((x>>8)+1/2) 2^-24
- * lies strictly inside (0,1).  Box-Muller on (x0,x1) gives the x and y
- * components, on (x2,x3) the z component. */
-static double u01(uint32_t x) { return ((double)(x >> 8) + 0.5) * (1.0 / 16777216.0); }
+ * Key: the 64-bit seed split into two words.  Uniform u = ((x>>9)+1/2) 2^-23
+ * lies strictly inside (0,1) and is exact in single precision as well, so
+ * every implementation sees the same u.  Box-Muller on (x0,x1) gives the x
+ * and y components, on (x2,x3) the z component. */
+static double u01(uint32_t x) { return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0); }
 
 void or_gauss3(uint64_t seed, uint32_t particle, int64_t time, uint32_t stream, double z[3])
 {

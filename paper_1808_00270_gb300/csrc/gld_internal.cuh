@@ -77,8 +77,9 @@ __host__ __device__ inline void philox4x32_10(uint32_t c[4], uint32_t k0, uint32
     }
 }
 
-// u in (0, 1) from the top 24 bits; exact in FP32.
-__device__ inline float u01(uint32_t x) { return ((float)(x >> 8) + 0.5f) * (1.0f / 16777216.0f); }
+// u in (0, 1) from the top 23 bits: (x >> 9) + 1/2 needs 24 significant
+// bits, so u is exact in FP32.
+__device__ inline float u01(uint32_t x) { return ((float)(x >> 9) + 0.5f) * (1.0f / 8388608.0f); }
 
 // W_{i,k} for particle i at time k: counter (i, (k + 2^62) lo, hi, stream).
 __device__ inline float3 gauss3(uint32_t k0, uint32_t k1, uint32_t particle, long long time,

@@ -136,8 +136,7 @@ def test_edge_cases():
         kw = dict(n=4, box=10.0, dt=0.01, m_max=4, r_c=2.0, pos=rng.uniform(0, 10, (4, 3)),
                   vel=np.zeros((4, 3)))
         kw.update(bad)
-        if kw["n"] != 4:
-            kw["pos"], kw["vel"] = np.zeros((max(kw["n"], 1), 3)), np.zeros((max(kw["n"], 1), 3))
+        kw["pos"], kw["vel"] = kw["pos"][: kw["n"]], kw["vel"][: kw["n"]]
         with pytest.raises(GLDError) as e:
             GLD(**kw)
         assert e.value.status == E_INVAL
