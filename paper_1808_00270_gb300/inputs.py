@@ -67,7 +67,12 @@ MEDIUM = Workload("gld_n4096_m200", n=4096, box=box_for_density(4096, 0.1), m_ma
 LARGE = Workload("gld_n262144_m400", n=262144, box=box_for_density(262144, 0.1), m_max=400,
                  dt=0.005, r_c=2.5, tau_s=0.5, tau_p=0.3, steps=1000, tail=True)
 
-WORKLOADS = {w.name: w for w in (SMALL, MEDIUM, LARGE)}
+# A quarter-size copy of the suspension for profiler captures (its 0.31 GB
+# history ring is still larger than L2).
+LARGE_QUARTER = Workload("gld_n65536_m400", n=65536, box=box_for_density(65536, 0.1), m_max=400,
+                         dt=0.005, r_c=2.5, tau_s=0.5, tau_p=0.3, steps=1000, tail=True)
+
+WORKLOADS = {w.name: w for w in (SMALL, MEDIUM, LARGE, LARGE_QUARTER)}
 
 
 def initial_state(w: Workload, seed: int | None = None):
