@@ -221,6 +221,28 @@ gld_status gld_hist_conv_dev(const void* ring, int32_t bf16, int32_t n_pad, int3
                              int64_t step, const float* coef, int32_t nacc, float* out,
                              int32_t kahan, void* stream);
 
+/* ---- neighbour pairs without device allocation ---------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory (code running while another library
+ * captures the stream into a graph, allocation-free real-time loops, hosts
+ * whose device memory belongs to a framework with a fixed budget).
+ *
+ * Same pairs as gld_get_pairs, from caller-owned device memory: pos4 is
+ * [n][4] float (x, y, z, unused; 16-byte aligned) inside [0, box); pairs is
+ * [cap][2] int32 (i < j, in no particular order); *count (device) receives the
+ * total, which may exceed cap.  Runs on `stream` and returns without waiting.
+ * Its scratch is one static device array of about 4.3 MB that every GPU
+ * loading the library keeps until exit; no cudaMalloc, cudaFree or
+ * allocating library routine is called.  The first call on a device looks
+ * the array's address up (cudaGetSymbolAddress with that device current);
+ * make that first call before any stream capture.  All calls share the
+ * array: calls that overlap on the GPU (other streams, other threads) race.
+ * GLD_E_INVAL for n < 1, n > GLD_NOALLOC_MAX_N, r_c > box/2, a misaligned
+ * pos4, or NULL outputs. */
+#define GLD_NOALLOC_MAX_N 65536
+gld_status gld_pairs_noalloc(const float* pos4, int32_t n, double box, double r_c, int32_t* pairs,
+                             int64_t cap, unsigned long long* count, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

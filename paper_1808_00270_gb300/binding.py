@@ -77,6 +77,7 @@ def lib():
             "gld_philox_dev": (i32, [vp, vp, vp, i64, vp]),
             "gld_gauss3_dev": (i32, [u64, vp, vp, u32, vp, i64, vp]),
             "gld_hist_conv_dev": (i32, [vp, i32, i32, i32, i64, vp, i32, vp, i32, vp]),
+            "gld_pairs_noalloc": (i32, [vp, i32, d, d, vp, i64, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -91,7 +92,7 @@ def exported_symbols() -> list[str]:
     return ["gld_params_default", "gld_create", "gld_set_kernels", "gld_step", "gld_sync", "gld_vacf",
             "gld_get_state", "gld_get_array", "gld_set_array", "gld_get_step", "gld_set_step",
             "gld_get_coefs", "gld_get_pairs", "gld_profile_steps", "gld_last_error", "gld_destroy", "gld_philox_dev",
-            "gld_gauss3_dev", "gld_hist_conv_dev"]
+            "gld_gauss3_dev", "gld_hist_conv_dev", "gld_pairs_noalloc"]
 
 
 def _ptr(a: np.ndarray):
@@ -297,3 +298,17 @@ def hist_conv_dev(ring, n_pad, m_max, step, coef, nacc, out, bf16=False, kahan=F
                                  _current_stream() if stream is None else stream)
     if st != OK:
         raise GLDError(st, "gld_hist_conv_dev")
+
+
+NOALLOC_MAX_N = 65536
+
+
+def pairs_noalloc(pos4, box, r_c, pairs, count, stream=None):
+    """Neighbour pairs with no device allocation (scratch in a static device
+    array).  pos4: float32 CUDA tensor [n, 4]; pairs: int32 [cap, 2];
+    count: int64 [1]; all caller-owned."""
+    st = lib().gld_pairs_noalloc(_dptr(pos4), int(pos4.shape[0]), float(box), float(r_c), _dptr(pairs),
+                                 int(pairs.shape[0]), _dptr(count),
+                                 _current_stream() if stream is None else stream)
+    if st != OK:
+        raise GLDError(st, "gld_pairs_noalloc")
