@@ -74,6 +74,7 @@ typedef struct gld_params {
     double r_c;          /* spatial cutoff of F^C and pair kernels, 0 < r_c <= L/2  */
     double r_c_min;      /* kernels evaluated at max(r, r_c_min) (Sec. III B)       */
     double A_cons;       /* soft repulsion U(r) = A (1 - r/r_c)^2 for r < r_c        */
+    double skin;         /* Verlet-list skin (0: 0.2 r_c); lists hold r < r_c + skin */
     uint64_t seed;       /* Philox key of the white noise W                         */
     int32_t hist_dtype;  /* GLD_HIST_F32 (default) or GLD_HIST_BF16 ring storage    */
     int32_t kahan;       /* 1: compensated summation over the m_max-1 history terms */
@@ -89,8 +90,13 @@ typedef struct gld_params {
     void* alloc_user;
 } gld_params;
 
-/* Fills *p with defaults (kT = 1, mass = 1, r_c_min = 0, F32 history, no Kahan,
- * vacf_stride = 1, vacf_burnin = -1, noise_block = 64, graphs on). */
+/* Fills *p with defaults (kT = 1, mass = 1, r_c_min = 0, skin = 0 (auto), F32
+ * history, no Kahan, vacf_stride = 1, vacf_burnin = -1, noise_block = 64,
+ * graphs on).  Neighbour sums use Verlet lists of radius r_c + skin, rebuilt on
+ * the device whenever a particle has moved more than 0.45 skin since the last
+ * build; the r < r_c test is applied exactly at every use, so results do not
+ * depend on the skin.  A list longer than its capacity (set from the density
+ * at creation) latches GLD_E_STATE. */
 void gld_params_default(gld_params* p);
 
 /* Creates a context on the current CUDA device.  pos and vel are [n][3]
@@ -186,7 +192,7 @@ enum {
     GLD_PROF_NOISE = 0,  /* white-noise generation + moving average (per block) */
     GLD_PROF_HIST = 1,   /* history convolution                               */
     GLD_PROF_PAIR = 2,   /* F^D, position update, history write               */
-    GLD_PROF_CELL = 3,   /* cell list build (3 kernels)                       */
+    GLD_PROF_CELL = 3,   /* cell + neighbour-list rebuild (4 kernels, gated)  */
     GLD_PROF_CFORCE = 4, /* F^C_{n+1} and velocity update                     */
     GLD_PROF_VACF = 5,   /* velocity autocorrelation                          */
     GLD_PROF_N = 6

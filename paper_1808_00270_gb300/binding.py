@@ -36,7 +36,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 class Params(C.Structure):
     _fields_ = [("n", C.c_int32), ("box", C.c_double), ("mass", C.c_double), ("kT", C.c_double),
                 ("dt", C.c_double), ("m_max", C.c_int32), ("r_c", C.c_double), ("r_c_min", C.c_double),
-                ("A_cons", C.c_double), ("seed", C.c_uint64), ("hist_dtype", C.c_int32),
+                ("A_cons", C.c_double), ("skin", C.c_double), ("seed", C.c_uint64), ("hist_dtype", C.c_int32),
                 ("kahan", C.c_int32), ("vacf_len", C.c_int32), ("vacf_stride", C.c_int32),
                 ("vacf_burnin", C.c_int64), ("noise_block", C.c_int32), ("psd_clamp", C.c_int32),
                 ("use_graphs", C.c_int32), ("stream", C.c_void_p), ("alloc", ALLOC_FN),
@@ -135,7 +135,7 @@ class GLD:
     """One GLD system on the current CUDA device (wraps a gld_ctx)."""
 
     def __init__(self, *, n, box, dt, m_max, r_c, pos, vel, mass=1.0, kT=1.0, r_c_min=0.0,
-                 A_cons=0.0, seed=1, hist_dtype="f32", kahan=False, vacf_len=0, vacf_stride=1,
+                 A_cons=0.0, skin=0.0, seed=1, hist_dtype="f32", kahan=False, vacf_len=0, vacf_stride=1,
                  vacf_burnin=-1, noise_block=64, psd_clamp=False, use_graphs=True, stream=None,
                  torch_allocator=True):
         L = lib()
@@ -143,6 +143,7 @@ class GLD:
         L.gld_params_default(C.byref(p))
         p.n, p.box, p.mass, p.kT, p.dt = int(n), float(box), float(mass), float(kT), float(dt)
         p.m_max, p.r_c, p.r_c_min, p.A_cons = int(m_max), float(r_c), float(r_c_min), float(A_cons)
+        p.skin = float(skin)
         p.seed = int(seed)
         p.hist_dtype = HIST_BF16 if hist_dtype in ("bf16", HIST_BF16) else HIST_F32
         p.kahan = int(bool(kahan))

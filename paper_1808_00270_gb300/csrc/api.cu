@@ -177,6 +177,10 @@ gld_status sync_and_check(gld_ctx* c)
     unsigned err = 0;
     GLD_CUDA(c, cudaMemcpy(&err, &c->B.ctrl->err, sizeof(unsigned), cudaMemcpyDeviceToHost));
     if (err & kErrNonFinite) fail(c, GLD_E_NONFINITE, "non-finite displacement produced on the device");
+    else if (err & kErrNbrOverflow) {
+        c->msg = "a neighbour list exceeded its capacity (density far above the one at creation)";
+        if (c->latched == GLD_OK) c->latched = GLD_E_STATE;
+    }
     else if (err & kErrTimeout) fail(c, GLD_E_TIMEOUT, "a bounded device wait gave up");
     else if (err & kErrNoise) fail(c, GLD_E_CUDA, "a step ran outside its noise block");
     return c->latched;
@@ -197,9 +201,12 @@ gld_status invalidate_noise(gld_ctx* c)
     return GLD_OK;
 }
 
+// Positions were replaced (pos and pos_next hold them): new lists and F^C.
 gld_status rebuild_cells_and_fc(gld_ctx* c)
 {
-    GLD_CUDA(c, launch_cell_build(c->P, c->B, c->st));
+    const int one = 1;
+    GLD_CUDA(c, cudaMemcpyAsync(&c->B.ctrl->rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, c->st));
+    GLD_CUDA(c, launch_rebuild(c->P, c->B, c->st));
     GLD_CUDA(c, launch_cforce(c->P, c->B, 0, c->st));
     return GLD_OK;
 }
@@ -215,7 +222,7 @@ cudaError_t launch_one_step(gld_ctx* c, cudaStream_t s)
                                      c->P.nacc, c->B.conv, c->prm.kahan, s);
     if (e != cudaSuccess) return e;
     if ((e = launch_pair_force_integrate(c->P, c->B, s)) != cudaSuccess) return e;
-    if ((e = launch_cell_build(c->P, c->B, s)) != cudaSuccess) return e;
+    if ((e = launch_rebuild(c->P, c->B, s)) != cudaSuccess) return e;
     if ((e = launch_cforce(c->P, c->B, 1, s)) != cudaSuccess) return e;
     return launch_vacf(c->P, c->B, s);
 }
@@ -274,7 +281,7 @@ gld_status gld_create(const gld_params* p, const double* pos, const double* vel,
     *out = nullptr;
     if (!p || !pos || !vel) return GLD_E_INVAL;
     if (p->n < 1 || p->m_max < 2 || p->m_max > 4096 || !(p->box > 0) || !(p->mass > 0) || !(p->dt > 0) ||
-        !(p->r_c > 0) || p->r_c > 0.5 * p->box || p->kT < 0 || p->r_c_min < 0 ||
+        !(p->r_c > 0) || p->r_c > 0.5 * p->box || p->kT < 0 || p->r_c_min < 0 || p->skin < 0 ||
         (p->hist_dtype != GLD_HIST_F32 && p->hist_dtype != GLD_HIST_BF16) || p->vacf_len < 0 ||
         (p->vacf_len > 0 && p->vacf_stride < 1))
         return GLD_E_INVAL;
@@ -295,10 +302,14 @@ gld_status gld_create(const gld_params* p, const double* pos, const double* vel,
     P.Q = P.Qs = 0;
     P.nacc = 1;
     P.nr = 2;
-    // Cells of edge >= r_c (with a margin well above FP32 rounding of the
-    // coordinates), at most ~8 per particle; fewer than 3 per side -> 1.
-    int nc = (int)std::floor(p->box / p->r_c);
-    while (nc > 0 && p->box / nc < p->r_c * (1.0 + 1e-5)) --nc;
+    // Verlet lists of radius r_l = r_c + skin (r_l <= L/2), built from cells of
+    // edge >= r_l (with a margin well above FP32 rounding of the coordinates),
+    // at most ~8 cells per particle; fewer than 3 per side -> one cell.
+    double skin = p->skin > 0 ? p->skin : 0.2 * p->r_c;
+    if (p->r_c + skin > 0.5 * p->box) skin = 0.5 * p->box - p->r_c;
+    const double rl = p->r_c + skin;
+    int nc = (int)std::floor(p->box / rl);
+    while (nc > 0 && p->box / nc < rl * (1.0 + 1e-5)) --nc;
     const int ncap = (int)std::floor(std::cbrt(8.0 * p->n));
     if (nc > ncap) nc = ncap;
     if (nc < 3) nc = 1;
@@ -320,6 +331,13 @@ gld_status gld_create(const gld_params* p, const double* pos, const double* vel,
     P.vf_fc = (float)(p->dt / (2.0 * p->mass));
     P.fc_mag = (float)(2.0 * p->A_cons / p->r_c);
     P.inv_rc = (float)(1.0 / p->r_c);
+    P.rl2 = (float)(rl * rl);
+    P.trig2 = (float)(0.45 * skin * 0.45 * skin);
+    {
+        const double expect = p->n / (p->box * p->box * p->box) * 4.18879020478639 * rl * rl * rl;
+        P.maxnb = std::min(p->n, ((int)std::ceil(2.0 * expect + 32.0) + 7) & ~7);
+        if (P.maxnb < 1) P.maxnb = 1;
+    }
     P.hist_bf16 = p->hist_dtype == GLD_HIST_BF16;
     P.vacf_len = p->vacf_len;
     P.vacf_stride = p->vacf_stride > 0 ? p->vacf_stride : 1;
@@ -334,7 +352,12 @@ gld_status gld_create(const gld_params* p, const double* pos, const double* vel,
     bool ok = true;
     B.ctrl = alloc_n<Ctrl>(c, 1, ok);
     B.pos_sorted = alloc_n<float4>(c, np, ok);
-    B.pos_new = alloc_n<float4>(c, np, ok);
+    B.pos = alloc_n<float4>(c, np, ok);
+    B.pos_next = alloc_n<float4>(c, np, ok);
+    B.disp_build = alloc_n<float4>(c, np, ok);
+    B.nbr = alloc_n<int>(c, (size_t)P.maxnb * np, ok);
+    B.nbr_cnt = alloc_n<int>(c, np, ok);
+    B.perm = alloc_n<int>(c, np, ok);
     B.vel = alloc_n<float4>(c, np, ok);
     B.vhalf = alloc_n<float4>(c, np, ok);
     B.fc = alloc_n<float4>(c, np, ok);
@@ -384,7 +407,8 @@ gld_status gld_create(const gld_params* p, const double* pos, const double* vel,
     const int total = P.n;
     if (s == GLD_OK && cudaMemcpyAsync(B.cell_start + ncells, &total, sizeof(int), cudaMemcpyHostToDevice, c->st) != cudaSuccess)
         s = GLD_E_CUDA;
-    if (s == GLD_OK) s = upload_vec(c, B.pos_new, pos, true);
+    if (s == GLD_OK) s = upload_vec(c, B.pos, pos, true);
+    if (s == GLD_OK) s = upload_vec(c, B.pos_next, pos, true);
     if (s == GLD_OK) s = upload_vec(c, B.vel, vel, false);
     if (s == GLD_OK) s = rebuild_cells_and_fc(c);
     if (s == GLD_OK) s = sync_and_check(c);
@@ -542,7 +566,7 @@ gld_status gld_get_state(gld_ctx* c, double* pos, double* vel)
 {
     if (!c) return GLD_E_INVAL;
     GLD_TRY(sync_and_check(c));
-    if (pos) GLD_TRY(download_vec(c, c->B.pos_new, pos));
+    if (pos) GLD_TRY(download_vec(c, c->B.pos, pos));
     if (vel) GLD_TRY(download_vec(c, c->B.vel, vel));
     return GLD_OK;
 }
@@ -554,7 +578,7 @@ gld_status gld_get_array(gld_ctx* c, int32_t which, double* out)
     const StepParams& P = c->P;
     const size_t np = P.n_pad;
     switch (which) {
-    case GLD_ARR_POS: return download_vec(c, c->B.pos_new, out);
+    case GLD_ARR_POS: return download_vec(c, c->B.pos, out);
     case GLD_ARR_VEL: return download_vec(c, c->B.vel, out);
     case GLD_ARR_FC: return download_vec(c, c->B.fc, out);
     case GLD_ARR_FD: return download_vec(c, c->B.fd, out);
@@ -598,12 +622,22 @@ gld_status gld_set_array(gld_ctx* c, int32_t which, const double* in)
     const StepParams& P = c->P;
     switch (which) {
     case GLD_ARR_POS:
-        GLD_TRY(upload_vec(c, c->B.pos_new, in, true));
+        GLD_TRY(upload_vec(c, c->B.pos, in, true));
+        GLD_TRY(upload_vec(c, c->B.pos_next, in, true));
         GLD_TRY(rebuild_cells_and_fc(c));
         return sync_and_check(c);
     case GLD_ARR_VEL: return upload_vec(c, c->B.vel, in, false);
     case GLD_ARR_FC: return upload_vec(c, c->B.fc, in, false);
-    case GLD_ARR_DISP: return upload_vec(c, c->B.disp, in, false);
+    case GLD_ARR_DISP: {
+        // The list-rebuild criterion measures motion as disp - disp_build, so a
+        // replaced displacement gets fresh lists (positions are unchanged).
+        GLD_TRY(upload_vec(c, c->B.disp, in, false));
+        const int one = 1, zero = 0;
+        GLD_CUDA(c, cudaMemcpyAsync(&c->B.ctrl->rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, c->st));
+        GLD_CUDA(c, launch_rebuild(c->P, c->B, c->st));
+        GLD_CUDA(c, cudaMemcpyAsync(&c->B.ctrl->rebuild, &zero, sizeof(int), cudaMemcpyHostToDevice, c->st));
+        return sync_and_check(c);
+    }
     case GLD_ARR_HIST: {
         const int H = P.H, n = P.n;
         const size_t np = P.n_pad;
@@ -678,7 +712,7 @@ gld_status gld_get_pairs(gld_ctx* c, int32_t* pairs, int64_t cap, int64_t* count
         dfree(c, d_cnt);
         return fail(c, GLD_E_NOMEM, "gld_get_pairs: allocation failed");
     }
-    gld_status s = cuda_check(c, launch_pair_list(c->P, c->B, d_pairs, cap, d_cnt, c->st), "pair_list");
+    gld_status s = cuda_check(c, launch_list_pair_list(c->P, c->B, d_pairs, cap, d_cnt, c->st), "pair_list");
     unsigned long long cnt = 0;
     if (s == GLD_OK) s = cuda_check(c, cudaStreamSynchronize(c->st), "sync");
     if (s == GLD_OK) s = cuda_check(c, cudaMemcpy(&cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost), "copy");
@@ -732,7 +766,7 @@ gld_status gld_profile_steps(gld_ctx* c, int64_t nsteps, double* ms, int64_t* la
             used[GLD_PROF_PAIR] = true;
         }
         if (s == GLD_OK) {
-            s = timed(GLD_PROF_CELL, [&] { return launch_cell_build(c->P, c->B, c->st); });
+            s = timed(GLD_PROF_CELL, [&] { return launch_rebuild(c->P, c->B, c->st); });
             used[GLD_PROF_CELL] = true;
         }
         if (s == GLD_OK) {
@@ -758,7 +792,7 @@ gld_status gld_profile_steps(gld_ctx* c, int64_t nsteps, double* ms, int64_t* la
         }
     }
     for (auto& e : ev) cudaEventDestroy(e);
-    if (cnt[GLD_PROF_CELL]) cnt[GLD_PROF_CELL] *= 3;  // three kernels per build
+    if (cnt[GLD_PROF_CELL]) cnt[GLD_PROF_CELL] *= 4;  // three cell kernels + list build
     if (cnt[GLD_PROF_NOISE]) cnt[GLD_PROF_NOISE] *= 2;  // white noise + moving average
     for (int f = 0; f < GLD_PROF_N; ++f) {
         if (ms) ms[f] += acc[f];

@@ -18,7 +18,7 @@ constexpr int kMaxAcc = 1 + 2 * kMaxQ;
 constexpr int kMaxNoiseBlock = 64;  // register-resident outputs per FIR thread
 
 // Latched device error bits.
-enum : unsigned { kErrNonFinite = 1u, kErrTimeout = 2u, kErrNoise = 4u };
+enum : unsigned { kErrNonFinite = 1u, kErrTimeout = 2u, kErrNoise = 4u, kErrNbrOverflow = 8u };
 
 // Device control block: the step counter lives on the device so that a
 // captured graph of several steps can be replayed without new arguments.
@@ -31,6 +31,8 @@ struct Ctrl {
     unsigned done_cforce;  // last-block counters (reset by the last block)
     unsigned done_scan;
     unsigned done_fir;
+    int rebuild;           // != 0: rebuild cells and neighbour lists after this step's move
+    int pad_;
 };
 
 // Everything a step kernel needs, passed by value.
@@ -45,6 +47,9 @@ struct StepParams {
     float vh_v, vh_fc, vh_f;  // a, a dt/(2M), b dt/M
     float vf_fc;              // dt/(2M)
     float fc_mag, inv_rc;     // 2A/r_c, 1/r_c
+    float rl2;                // (r_c + skin)^2: neighbour-list radius
+    float trig2;              // rebuild when a particle moved more than sqrt(trig2)
+    int maxnb;                // neighbour-list capacity per particle
     int hist_bf16;
     // VACF
     int vacf_len, vacf_stride, n_os;
@@ -132,11 +137,13 @@ __device__ inline float wrap_box(float x, float L)
     return x;
 }
 
-// Visits every particle j != i with r_ij < r_c, cells in a fixed order and
-// particles of a cell by increasing id: f(j, dx, dy, dz, r2) with d = R_i - R_j.
+// Visits every particle j != i with r_ij^2 < r2max over the 27-cell stencil,
+// cells in a fixed order and particles of a cell by increasing id:
+// f(j, dx, dy, dz, r2) with d = R_i - R_j.
 template <class F>
-__device__ inline void for_each_neighbor(const float4 pi, const int id, const float4* __restrict__ pos_sorted,
-                                         const int* __restrict__ cell_start, const StepParams& P, F&& f)
+__device__ inline void for_each_in_stencil(const float4 pi, const int id, const float4* __restrict__ pos_sorted,
+                                           const int* __restrict__ cell_start, const StepParams& P, float r2max,
+                                           F&& f)
 {
     const int nc = P.nc;
     const int span = nc == 1 ? 0 : 1;
@@ -161,10 +168,46 @@ __device__ inline void for_each_neighbor(const float4 pi, const int id, const fl
                     const float dy = min_image(pi.y, pj.y, P.box, P.half_box);
                     const float dz = min_image(pi.z, pj.z, P.box, P.half_box);
                     const float r2 = dist2(dx, dy, dz);
-                    if (r2 < P.rc2) f(jd, dx, dy, dz, r2);
+                    if (r2 < r2max) f(jd, dx, dy, dz, r2);
                 }
             }
         }
+    }
+}
+
+// Visits every j != i with r_ij < r_c from i's neighbour list (a superset built
+// with r_c + skin, sorted by id): f(j, dx, dy, dz, r2) with d = R_i - R_j.
+// The distance test is the same as the stencil's, so the pairs are the same.
+template <class F>
+__device__ inline void for_each_listed(const float4 pi, const int k, const int* __restrict__ nbr,
+                                       const int cnt, const int stride, const float4* __restrict__ pos,
+                                       const StepParams& P, F&& f)
+{
+    int s = 0;
+    for (; s + 4 <= cnt; s += 4) {
+        int j[4];
+        float4 pj[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) j[u] = __ldg(nbr + (size_t)(s + u) * stride + k);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) pj[u] = __ldg(pos + j[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float dx = min_image(pi.x, pj[u].x, P.box, P.half_box);
+            const float dy = min_image(pi.y, pj[u].y, P.box, P.half_box);
+            const float dz = min_image(pi.z, pj[u].z, P.box, P.half_box);
+            const float r2 = dist2(dx, dy, dz);
+            if (r2 < P.rc2) f(j[u], dx, dy, dz, r2);
+        }
+    }
+    for (; s < cnt; ++s) {
+        const int j = __ldg(nbr + (size_t)s * stride + k);
+        const float4 pj = __ldg(pos + j);
+        const float dx = min_image(pi.x, pj.x, P.box, P.half_box);
+        const float dy = min_image(pi.y, pj.y, P.box, P.half_box);
+        const float dz = min_image(pi.z, pj.z, P.box, P.half_box);
+        const float r2 = dist2(dx, dy, dz);
+        if (r2 < P.rc2) f(j, dx, dy, dz, r2);
     }
 }
 

@@ -4,17 +4,23 @@
 //                         projections and the neighbours at R_n, then the
 //                         position half of Eq. GLD_integrator (with b, App. A),
 //                         the new displacement into the history ring, and the
-//                         velocity terms that do not need F^C_{n+1}.
-//   cell build            cell list at R_{n+1}: per-cell linked lists, a
-//                         chunked exclusive scan, cells filled in id order.
+//                         velocity terms that do not need F^C_{n+1}.  Requests
+//                         a neighbour-list rebuild when a particle has moved
+//                         more than half the skin since the last build.
+//   cell build + nbr_build (only when a rebuild was requested): cell list at
+//                         R_{n+1} (per-cell linked lists, chunked scan, cells
+//                         filled in id order), then per particle the ids within
+//                         r_c + skin, sorted by id.
 //   cforce                F^C_{n+1} = sum_j 2A/r_c (1 - r/r_c) e_ij and the
 //                         rest of the velocity update; advances n.
 //   vacf                  FP64 accumulation of <V(t0+tau) V(t0)> (Sec. III A).
 //
-// Particles are visited in cell order (thread k handles the k-th particle of
-// the cell-sorted list) so that a warp's neighbour cells overlap; all
-// per-particle arrays stay indexed by the particle id, which never changes,
-// so the displacement history is never permuted.
+// Every neighbour sum runs over a Verlet list with the exact FP32 r < r_c test
+// of the cell traversal, so the pair set is the same; lists are sorted by
+// neighbour id, so the order of every sum does not depend on when the list was
+// built.  Particles are visited in the cell order of the last build; all
+// per-particle arrays stay indexed by the particle id, which never changes, so
+// the displacement history is never permuted.
 #include <cuda_bf16.h>
 
 #include "launch.h"
@@ -33,20 +39,21 @@ __device__ __forceinline__ float dot3(float ax, float ay, float az, float bx, fl
 }
 
 __global__ void __launch_bounds__(kPairThreads)
-    pair_force_integrate(const StepParams P, const Ctrl* __restrict__ ctrl, const float4* __restrict__ pos_sorted,
-                         const int* __restrict__ cell_start, const float4* __restrict__ vel,
-                         const float4* __restrict__ fc, const float* __restrict__ conv,
+    pair_force_integrate(const StepParams P, Ctrl* __restrict__ ctrl, const float4* __restrict__ pos,
+                         const int* __restrict__ perm, const int* __restrict__ nbr, const int* __restrict__ nbr_cnt,
+                         const float4* __restrict__ vel, const float4* __restrict__ fc, const float* __restrict__ conv,
                          const float* __restrict__ frblock, const float* __restrict__ ftab,
-                         const float* __restrict__ g0, void* __restrict__ ring, float4* __restrict__ pos_new,
+                         const float* __restrict__ g0, void* __restrict__ ring, float4* __restrict__ pos_next,
                          float4* __restrict__ vhalf, float4* __restrict__ fd_out, float4* __restrict__ disp,
-                         unsigned* __restrict__ err)
+                         const float4* __restrict__ disp_build)
 {
+    unsigned* err = &ctrl->err;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= P.n) return;
     const long long n = ctrl->step;
     const long long np = P.n_pad;
-    const float4 pi = pos_sorted[k];
-    const int id = __float_as_int(pi.w);
+    const int id = perm[k];
+    const float4 pi = pos[id];
     const float4 vi = vel[id];
 
     float ps[kMaxQ][3];
@@ -64,7 +71,7 @@ __global__ void __launch_bounds__(kPairThreads)
     float f0x = 0.f, f0y = 0.f, f0z = 0.f;  // instantaneous (m = 0) pair terms
     float fhx = 0.f, fhy = 0.f, fhz = 0.f;  // history pair terms (times -1, before 1/dt)
     if (P.Q + P.Qs > 0) {
-        for_each_neighbor(pi, id, pos_sorted, cell_start, P, [&](int jd, float dx, float dy, float dz, float r2) {
+        for_each_listed(pi, k, nbr, nbr_cnt[k], P.n_pad, pos, P, [&](int jd, float dx, float dy, float dz, float r2) {
             const float r = sqrtf(r2);
             const float inv_r = 1.0f / r;
             const float ex = dx * inv_r, ey = dy * inv_r, ez = dz * inv_r;
@@ -122,22 +129,31 @@ __global__ void __launch_bounds__(kPairThreads)
         h[np] = dRy;
         h[2 * np] = dRz;
     }
-    pos_new[id] = make_float4(wrap_box(__fadd_rn(pi.x, dRx), P.box), wrap_box(__fadd_rn(pi.y, dRy), P.box),
-                              wrap_box(__fadd_rn(pi.z, dRz), P.box), 0.f);
+    pos_next[id] = make_float4(wrap_box(__fadd_rn(pi.x, dRx), P.box), wrap_box(__fadd_rn(pi.y, dRy), P.box),
+                               wrap_box(__fadd_rn(pi.z, dRz), P.box), 0.f);
     // velocity part known now: a V + a dt/(2M) F^C_n + b dt/M (F^D + F^R)
     vhalf[id] = make_float4(fmaf(P.vh_f, fdx + frx, fmaf(P.vh_fc, fci.x, P.vh_v * vi.x)),
                             fmaf(P.vh_f, fdy + fry, fmaf(P.vh_fc, fci.y, P.vh_v * vi.y)),
                             fmaf(P.vh_f, fdz + frz, fmaf(P.vh_fc, fci.z, P.vh_v * vi.z)), 0.f);
     fd_out[id] = make_float4(fdx, fdy, fdz, 0.f);
     const float4 d = disp[id];
-    disp[id] = make_float4(d.x + dRx, d.y + dRy, d.z + dRz, 0.f);
-    if (!(isfinite(dRx) && isfinite(dRy) && isfinite(dRz))) atomicOr(err, kErrNonFinite);
+    const float4 dn = make_float4(d.x + dRx, d.y + dRy, d.z + dRz, 0.f);
+    disp[id] = dn;
+    // Verlet criterion: a particle moved more than half the skin since the build.
+    const float4 db = disp_build[id];
+    const float mx = dn.x - db.x, my = dn.y - db.y, mz = dn.z - db.z;
+    if (mx * mx + my * my + mz * mz > P.trig2) atomicOr(&ctrl->rebuild, 1);
+    if (!(isfinite(dRx) && isfinite(dRy) && isfinite(dRz))) {
+        atomicOr(err, kErrNonFinite);
+        atomicOr(&ctrl->rebuild, 1);
+    }
 }
 
 // ---- cell list --------------------------------------------------------------
-__global__ void cell_assign(const StepParams P, const float4* __restrict__ pos, int* __restrict__ head,
-                            int* __restrict__ next, int* __restrict__ count)
+__global__ void cell_assign(const StepParams P, const int* __restrict__ gate, const float4* __restrict__ pos,
+                            int* __restrict__ head, int* __restrict__ next, int* __restrict__ count)
 {
+    if (gate && *gate == 0) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.n) return;
     const int c = cell_of(pos[i], P);
@@ -178,9 +194,10 @@ __device__ int block_exclusive_scan(int v, int* out_excl)
 
 // Chunk sums of the cell counts; the last block to finish scans them.
 __global__ void __launch_bounds__(kCellThreads)
-    cell_scan(const int* __restrict__ count, int ncells, int* __restrict__ chunk_sum, int* __restrict__ chunk_off,
-              unsigned* __restrict__ done)
+    cell_scan(const int* __restrict__ gate, const int* __restrict__ count, int ncells, int* __restrict__ chunk_sum,
+              int* __restrict__ chunk_off, unsigned* __restrict__ done)
 {
+    if (gate && *gate == 0) return;  // uniform over the grid
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     int excl;
     const int tot = block_exclusive_scan(c < ncells ? count[c] : 0, &excl);
@@ -207,10 +224,11 @@ __global__ void __launch_bounds__(kCellThreads)
 
 // Cell starts, and each cell's particles in increasing id order.
 __global__ void __launch_bounds__(kCellThreads)
-    cell_fill(const StepParams P, int ncells, const float4* __restrict__ pos, int* __restrict__ count,
-              int* __restrict__ head, const int* __restrict__ next, const int* __restrict__ chunk_off,
-              int* __restrict__ cell_start, float4* __restrict__ pos_sorted)
+    cell_fill(const StepParams P, const int* __restrict__ gate, int ncells, const float4* __restrict__ pos,
+              int* __restrict__ count, int* __restrict__ head, const int* __restrict__ next,
+              const int* __restrict__ chunk_off, int* __restrict__ cell_start, float4* __restrict__ pos_sorted)
 {
+    if (gate && *gate == 0) return;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int cnt = c < ncells ? count[c] : 0;
     int excl;
@@ -234,19 +252,60 @@ __global__ void __launch_bounds__(kCellThreads)
     count[c] = 0;
 }
 
+// Per particle, in cell order: the ids within r_c + skin, sorted by id.
+__global__ void __launch_bounds__(kThreads)
+    nbr_build(const StepParams P, Ctrl* __restrict__ ctrl, const float4* __restrict__ pos_sorted,
+              const int* __restrict__ cell_start, int* __restrict__ nbr, int* __restrict__ nbr_cnt,
+              int* __restrict__ perm, const float4* __restrict__ disp, float4* __restrict__ disp_build)
+{
+    if (ctrl->rebuild == 0) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P.n) return;
+    const float4 pi = pos_sorted[k];
+    const int id = __float_as_int(pi.w);
+    const int stride = P.n_pad, cap = P.maxnb;
+    int c = 0;
+    for_each_in_stencil(pi, id, pos_sorted, cell_start, P, P.rl2, [&](int jd, float, float, float, float) {
+        if (c < cap) {
+            // insertion by id
+            int p = c;
+            while (p > 0) {
+                const int q = nbr[(size_t)(p - 1) * stride + k];
+                if (q < jd) break;
+                nbr[(size_t)p * stride + k] = q;
+                --p;
+            }
+            nbr[(size_t)p * stride + k] = jd;
+        }
+        ++c;
+    });
+    if (c > cap) {
+        atomicOr(&ctrl->err, kErrNbrOverflow);
+        c = cap;
+    }
+    nbr_cnt[k] = c;
+    perm[k] = id;
+    disp_build[id] = disp[id];
+}
+
 // ---- conservative force and velocity finish --------------------------------
+// R_{n+1} is read from pos_next (every thread reads neighbours there) and
+// copied into pos for the next step.
 template <bool STEP>
 __global__ void __launch_bounds__(kThreads)
-    cforce(const StepParams P, Ctrl* __restrict__ ctrl, const float4* __restrict__ pos_sorted,
-           const int* __restrict__ cell_start, const float4* __restrict__ vhalf, float4* __restrict__ vel,
+    cforce(const StepParams P, Ctrl* __restrict__ ctrl, const float4* __restrict__ pos_next,
+           float4* __restrict__ pos, const int* __restrict__ perm, const int* __restrict__ nbr,
+           const int* __restrict__ nbr_cnt, const float4* __restrict__ vhalf, float4* __restrict__ vel,
            float4* __restrict__ fc)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0) ctrl->rebuild = 0;  // the lists are current for R_{n+1}
     if (k < P.n) {
-        const float4 pi = pos_sorted[k];
-        const int id = __float_as_int(pi.w);
+        const int id = perm[k];
+        const float4 pi = pos_next[id];
+        pos[id] = pi;
         float fx = 0.f, fy = 0.f, fz = 0.f;
-        for_each_neighbor(pi, id, pos_sorted, cell_start, P, [&](int, float dx, float dy, float dz, float r2) {
+        for_each_listed(pi, k, nbr, nbr_cnt[k], P.n_pad, pos_next, P, [&](int, float dx, float dy, float dz, float r2) {
             const float r = sqrtf(r2);
             // -dU/dr e_ij with U = A (1 - r/r_c)^2, e_ij = (R_i - R_j)/r
             const float s = P.fc_mag * (1.0f - r * P.inv_rc) / r;
@@ -274,7 +333,18 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // ---- velocity autocorrelation ------------------------------------------------
-// grid (gx, n_os): blockIdx.y = age j of the origin (0 = newest).
+constexpr int kVacfGroup = 8;  // origins accumulated per pass over V
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block b reads each velocity once and dots it with every active origin's
+// stored velocity (origin j = age 0 is the newest); per-block FP64 partials,
+// reduced in a fixed order by the last block to finish.
 __global__ void __launch_bounds__(kThreads)
     vacf(const StepParams P, const Ctrl* __restrict__ ctrl, const float4* __restrict__ vel,
          float4* __restrict__ vorig, double* __restrict__ partial, double* __restrict__ csum,
@@ -285,58 +355,63 @@ __global__ void __launch_bounds__(kThreads)
     const long long rel = t - P.vacf_burnin;
     const long long o_now = rel / P.vacf_stride;
     const bool is_origin = (rel % P.vacf_stride) == 0;
-    const int j = blockIdx.y;
-    const long long o = o_now - j;
-    const long long lag = rel - o * (long long)P.vacf_stride;
-    const bool active = o >= 0 && lag < P.vacf_len;
-    const bool fresh = j == 0 && is_origin;
-    double s = 0.0;
-    if (active) {
-        float acc = 0.f;
-        const float4* v0 = vorig + (size_t)(o % P.n_os) * P.n;
+    // active ages j: o = o_now - j >= 0 and lag = rel - o stride < vacf_len
+    int n_act = 0;
+    for (int jj = 0; jj < P.n_os; ++jj) {
+        const long long o = o_now - jj;
+        if (o >= 0 && rel - o * (long long)P.vacf_stride < P.vacf_len) n_act = jj + 1;
+    }
+    __shared__ double wsum[kThreads / 32][kVacfGroup];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int g0 = 0; g0 < n_act; g0 += kVacfGroup) {
+        float acc[kVacfGroup];
+#pragma unroll
+        for (int q = 0; q < kVacfGroup; ++q) acc[q] = 0.f;
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
             const float4 v = vel[i];
-            const float4 w = fresh ? v : v0[i];
-            acc += dot3(v.x, v.y, v.z, w.x, w.y, w.z);
-            if (fresh) vorig[(size_t)(o % P.n_os) * P.n + i] = v;
+#pragma unroll
+            for (int q = 0; q < kVacfGroup; ++q) {
+                const int jj = g0 + q;
+                if (jj >= n_act) break;
+                const long long o = o_now - jj;
+                const float4* v0 = vorig + (size_t)(o % P.n_os) * P.n;
+                const float4 w = (jj == 0 && is_origin) ? v : v0[i];
+                acc[q] += dot3(v.x, v.y, v.z, w.x, w.y, w.z);
+            }
+            if (g0 == 0 && is_origin) vorig[(size_t)(o_now % P.n_os) * P.n + i] = v;
         }
-        s = (double)acc;
-    }
-    // deterministic block reduction in FP64
-    __shared__ double red[kThreads];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = kThreads / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+#pragma unroll
+        for (int q = 0; q < kVacfGroup; ++q) {
+            const double s = warp_sum((double)acc[q]);
+            if (lane == 0) wsum[warp][q] = s;
+        }
+        __syncthreads();
+        if (threadIdx.x < kVacfGroup && g0 + (int)threadIdx.x < n_act) {
+            double s = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) s += wsum[w][threadIdx.x];
+            partial[(size_t)(g0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+        }
         __syncthreads();
     }
     __shared__ bool last;
     if (threadIdx.x == 0) {
-        partial[(size_t)j * gridDim.x + blockIdx.x] = red[0];
         __threadfence();
-        last = atomicAdd(done, 1u) == gridDim.x * gridDim.y - 1;
+        last = atomicAdd(done, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int jj = 0; jj < (int)gridDim.y; ++jj) {
-        const long long oo = o_now - jj;
-        const long long lg = rel - oo * (long long)P.vacf_stride;
-        if (!(oo >= 0 && lg < P.vacf_len)) continue;  // uniform in the block
+    for (int jj = warp; jj < n_act; jj += kThreads / 32) {
+        const long long o = o_now - jj;
+        const long long lg = rel - o * (long long)P.vacf_stride;
+        if (o < 0 || lg >= P.vacf_len) continue;
         double v = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-            v += ((volatile double*)partial)[(size_t)jj * gridDim.x + b];
-        red[threadIdx.x] = v;
-        __syncthreads();
-        for (int w = kThreads / 2; w > 0; w >>= 1) {
-            if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            csum[lg] += red[0];
+        for (int b = lane; b < (int)gridDim.x; b += 32) v += ((volatile double*)partial)[(size_t)jj * gridDim.x + b];
+        v = warp_sum(v);
+        if (lane == 0) {
+            csum[lg] += v;
             ccnt[lg] += 1;
         }
-        __syncthreads();
     }
     if (threadIdx.x == 0) {
         if (is_origin) *norig += 1;
@@ -344,7 +419,32 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-// ---- explicit pair list (checks of the traversal) ---------------------------
+// ---- explicit pair lists (checks of the traversals) -------------------------
+__device__ __forceinline__ void emit_pair(int id, int jd, int* __restrict__ pairs, long long cap,
+                                          unsigned long long* __restrict__ count)
+{
+    if (jd > id) {
+        const unsigned long long slot = atomicAdd(count, 1ull);
+        if ((long long)slot < cap) {
+            pairs[2 * slot] = id;
+            pairs[2 * slot + 1] = jd;
+        }
+    }
+}
+
+// The pairs the force kernels use: from the neighbour lists at R_n.
+__global__ void list_pair_list(const StepParams P, const float4* __restrict__ pos, const int* __restrict__ perm,
+                               const int* __restrict__ nbr, const int* __restrict__ nbr_cnt, int* __restrict__ pairs,
+                               long long cap, unsigned long long* __restrict__ count)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P.n) return;
+    const int id = perm[k];
+    for_each_listed(pos[id], k, nbr, nbr_cnt[k], P.n_pad, pos, P,
+                    [&](int jd, float, float, float, float) { emit_pair(id, jd, pairs, cap, count); });
+}
+
+// The pairs of a fresh cell traversal (no lists).
 __global__ void pair_list(const StepParams P, const float4* __restrict__ pos_sorted, const int* __restrict__ cell_start,
                           int* __restrict__ pairs, long long cap, unsigned long long* __restrict__ count)
 {
@@ -352,7 +452,7 @@ __global__ void pair_list(const StepParams P, const float4* __restrict__ pos_sor
     if (k >= P.n) return;
     const float4 pi = pos_sorted[k];
     const int id = __float_as_int(pi.w);
-    for_each_neighbor(pi, id, pos_sorted, cell_start, P, [&](int jd, float, float, float, float) {
+    for_each_in_stencil(pi, id, pos_sorted, cell_start, P, P.rc2, [&](int jd, float, float, float, float) {
         if (jd > id) {
             const unsigned long long slot = atomicAdd(count, 1ull);
             if ((long long)slot < cap) {
@@ -368,36 +468,50 @@ __global__ void pair_list(const StepParams P, const float4* __restrict__ pos_sor
 cudaError_t launch_pair_force_integrate(const StepParams& P, const ParticleBuffers& B, cudaStream_t st)
 {
     const unsigned grid = (unsigned)((P.n + kPairThreads - 1) / kPairThreads);
-    pair_force_integrate<<<grid, kPairThreads, 0, st>>>(P, B.ctrl, B.pos_sorted, B.cell_start, B.vel, B.fc, B.conv,
-                                                        B.frblock, B.ftab, B.g0, B.ring, B.pos_new, B.vhalf, B.fd,
-                                                        B.disp, &B.ctrl->err);
+    pair_force_integrate<<<grid, kPairThreads, 0, st>>>(P, B.ctrl, B.pos, B.perm, B.nbr, B.nbr_cnt, B.vel, B.fc,
+                                                        B.conv, B.frblock, B.ftab, B.g0, B.ring, B.pos_next,
+                                                        B.vhalf, B.fd, B.disp, B.disp_build);
     return cudaGetLastError();
 }
 
-cudaError_t launch_cell_build(const StepParams& P, const ParticleBuffers& B, cudaStream_t st)
+cudaError_t launch_cell_build(const StepParams& P, const ParticleBuffers& B, const float4* src, const int* gate,
+                              cudaStream_t st)
 {
-    cell_assign<<<(P.n + kThreads - 1) / kThreads, kThreads, 0, st>>>(P, B.pos_new, B.cell_head, B.cell_next,
+    cell_assign<<<(P.n + kThreads - 1) / kThreads, kThreads, 0, st>>>(P, gate, src, B.cell_head, B.cell_next,
                                                                        B.cell_count);
     const unsigned chunks = (unsigned)((B.ncells + kCellThreads - 1) / kCellThreads);
-    cell_scan<<<chunks, kCellThreads, 0, st>>>(B.cell_count, B.ncells, B.chunk_sum, B.chunk_off, &B.ctrl->done_scan);
-    cell_fill<<<chunks, kCellThreads, 0, st>>>(P, B.ncells, B.pos_new, B.cell_count, B.cell_head, B.cell_next,
+    cell_scan<<<chunks, kCellThreads, 0, st>>>(gate, B.cell_count, B.ncells, B.chunk_sum, B.chunk_off,
+                                               &B.ctrl->done_scan);
+    cell_fill<<<chunks, kCellThreads, 0, st>>>(P, gate, B.ncells, src, B.cell_count, B.cell_head, B.cell_next,
                                                B.chunk_off, B.cell_start, B.pos_sorted);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rebuild(const StepParams& P, const ParticleBuffers& B, cudaStream_t st)
+{
+    cudaError_t e = launch_cell_build(P, B, B.pos_next, &B.ctrl->rebuild, st);
+    if (e != cudaSuccess) return e;
+    nbr_build<<<(P.n + kThreads - 1) / kThreads, kThreads, 0, st>>>(P, B.ctrl, B.pos_sorted, B.cell_start, B.nbr,
+                                                                     B.nbr_cnt, B.perm, B.disp, B.disp_build);
     return cudaGetLastError();
 }
 
 cudaError_t launch_cforce(const StepParams& P, const ParticleBuffers& B, int mode, cudaStream_t st)
 {
     const unsigned grid = (unsigned)((P.n + kThreads - 1) / kThreads);
-    if (mode) cforce<true><<<grid, kThreads, 0, st>>>(P, B.ctrl, B.pos_sorted, B.cell_start, B.vhalf, B.vel, B.fc);
-    else cforce<false><<<grid, kThreads, 0, st>>>(P, B.ctrl, B.pos_sorted, B.cell_start, B.vhalf, B.vel, B.fc);
+    if (mode)
+        cforce<true><<<grid, kThreads, 0, st>>>(P, B.ctrl, B.pos_next, B.pos, B.perm, B.nbr, B.nbr_cnt, B.vhalf,
+                                                B.vel, B.fc);
+    else
+        cforce<false><<<grid, kThreads, 0, st>>>(P, B.ctrl, B.pos_next, B.pos, B.perm, B.nbr, B.nbr_cnt, B.vhalf,
+                                                 B.vel, B.fc);
     return cudaGetLastError();
 }
 
 cudaError_t launch_vacf(const StepParams& P, const ParticleBuffers& B, cudaStream_t st)
 {
     if (P.vacf_len <= 0) return cudaSuccess;
-    dim3 grid(B.vacf_gx, P.n_os);
-    vacf<<<grid, kThreads, 0, st>>>(P, B.ctrl, B.vel, B.vorig, B.vpartial, B.csum, B.ccnt, B.norig, B.vdone);
+    vacf<<<B.vacf_gx, kThreads, 0, st>>>(P, B.ctrl, B.vel, B.vorig, B.vpartial, B.csum, B.ccnt, B.norig, B.vdone);
     return cudaGetLastError();
 }
 
@@ -408,6 +522,12 @@ cudaError_t launch_pair_list(const StepParams& P, const ParticleBuffers& B, int*
     return cudaGetLastError();
 }
 
-int cell_chunk_threads() { return kCellThreads; }
+cudaError_t launch_list_pair_list(const StepParams& P, const ParticleBuffers& B, int* pairs, long long cap,
+                                  unsigned long long* count, cudaStream_t st)
+{
+    list_pair_list<<<(P.n + kThreads - 1) / kThreads, kThreads, 0, st>>>(P, B.pos, B.perm, B.nbr, B.nbr_cnt, pairs,
+                                                                         cap, count);
+    return cudaGetLastError();
+}
 
 }  // namespace gld

@@ -18,7 +18,10 @@ cudaError_t launch_hist_conv(const void* ring, int bf16, int n_pad, int m_max, c
 // Particle kernels (k_particles.cu).
 struct ParticleBuffers {
     Ctrl* ctrl;
-    float4 *pos_sorted, *pos_new, *vel, *vhalf, *fc, *fd, *disp;
+    float4 *pos, *pos_next;      // R_n and R_{n+1} by particle id
+    float4 *pos_sorted;          // cell-ordered copy with the id in w (last build)
+    float4 *vel, *vhalf, *fc, *fd, *disp, *disp_build;
+    int *nbr, *nbr_cnt, *perm;   // neighbour lists [maxnb][n_pad] in build order
     void* ring;
     float* conv;
     float* frblock;
@@ -37,12 +40,22 @@ struct ParticleBuffers {
 };
 
 cudaError_t launch_pair_force_integrate(const StepParams& P, const ParticleBuffers& B, cudaStream_t st);
-cudaError_t launch_cell_build(const StepParams& P, const ParticleBuffers& B, cudaStream_t st);
+// Cell list of the positions `src`; skipped on the device when gate != nullptr
+// and *gate == 0.
+cudaError_t launch_cell_build(const StepParams& P, const ParticleBuffers& B, const float4* src, const int* gate,
+                              cudaStream_t st);
+// Cell list and neighbour lists at R_{n+1} (pos_next), when ctrl->rebuild != 0.
+cudaError_t launch_rebuild(const StepParams& P, const ParticleBuffers& B, cudaStream_t st);
 // mode 0: F^C only (initialisation); mode 1: F^C_{n+1}, V_{n+1}, step += 1.
+// Both copy pos_next into pos and clear ctrl->rebuild.
 cudaError_t launch_cforce(const StepParams& P, const ParticleBuffers& B, int mode, cudaStream_t st);
 cudaError_t launch_vacf(const StepParams& P, const ParticleBuffers& B, cudaStream_t st);
+// Pairs from a fresh cell traversal of pos_sorted / cell_start.
 cudaError_t launch_pair_list(const StepParams& P, const ParticleBuffers& B, int* pairs,
                              long long cap, unsigned long long* count, cudaStream_t st);
+// Pairs the force kernels use (neighbour lists at R_n).
+cudaError_t launch_list_pair_list(const StepParams& P, const ParticleBuffers& B, int* pairs,
+                                  long long cap, unsigned long long* count, cudaStream_t st);
 
 // Noise and kernel preparation (k_noise.cu).
 struct PrepArgs {

@@ -90,7 +90,7 @@ extern "C" gld_status gld_pairs_noalloc(const float* pos4, int32_t n, double box
     ParticleBuffers B{};
     B.ctrl = (Ctrl*)(s + kOffCtrl);
     B.pos_sorted = (float4*)(s + kOffSorted);
-    B.pos_new = (float4*)pos4;  // read only by the cell build
+    const float4* src = (const float4*)pos4;  // read only by the cell build
     B.cell_next = (int*)(s + kOffNext);
     B.cell_start = (int*)(s + kOffStart);
     B.cell_count = (int*)(s + kOffCount);
@@ -107,7 +107,7 @@ extern "C" gld_status gld_pairs_noalloc(const float* pos4, int32_t n, double box
         return GLD_E_CUDA;
     set_int<<<1, 1, 0, st>>>(B.cell_start + ncells, n);
     if (cudaGetLastError() != cudaSuccess) return GLD_E_CUDA;
-    if (launch_cell_build(P, B, st) != cudaSuccess) return GLD_E_CUDA;
+    if (launch_cell_build(P, B, src, nullptr, st) != cudaSuccess) return GLD_E_CUDA;
     if (launch_pair_list(P, B, pairs, cap, count, st) != cudaSuccess) return GLD_E_CUDA;
     return GLD_OK;
 }
