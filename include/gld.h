@@ -183,11 +183,14 @@ gld_status gld_get_coefs(gld_ctx* ctx, double* Kd, double* A, double* ab, double
  * *count receives the total (may exceed cap).  Synchronizes. */
 gld_status gld_get_pairs(gld_ctx* ctx, int32_t* pairs, int64_t cap, int64_t* count);
 
-/* Runs nsteps steps with every kernel launched directly (no graph) and
- * bracketed by CUDA events on the context's stream; adds each kernel
- * family's device time in milliseconds to ms[GLD_PROF_N] and its launch count
- * to launches[GLD_PROF_N] (either may be NULL).  Advances the simulation like
- * gld_step.  Synchronizes. */
+/* Runs at least nsteps steps (rounded up to whole noise blocks, after untimed
+ * steps up to the next block boundary) with every kernel family bracketed by
+ * CUDA events on the context's stream; each block starts with a 0.2 ms idle
+ * kernel so that the host enqueues the block ahead of the device and the
+ * event pairs time device work only.  Adds each family's device time in
+ * milliseconds to ms[GLD_PROF_N] and its launch count to launches[GLD_PROF_N]
+ * (either may be NULL).  Advances the simulation like gld_step.
+ * Synchronizes. */
 enum {
     GLD_PROF_NOISE = 0,  /* white-noise generation + moving average (per block) */
     GLD_PROF_HIST = 1,   /* history convolution                               */

@@ -730,70 +730,67 @@ gld_status gld_profile_steps(gld_ctx* c, int64_t nsteps, double* ms, int64_t* la
 {
     if (!c || nsteps < 0) return GLD_E_INVAL;
     if (!c->have_kernels) return fail(c, GLD_E_STATE, "gld_profile_steps: gld_set_kernels has not succeeded");
+    if (c->latched != GLD_OK) return c->latched;
+    // untimed steps up to the next noise-block boundary
+    if (c->noise_valid && c->host_step < c->noise_end) GLD_TRY(gld_step(c, c->noise_end - c->host_step));
     GLD_TRY(sync_and_check(c));
-    cudaEvent_t ev[2 * GLD_PROF_N];
+    const int T = c->P.T;
+    const int64_t blocks = (nsteps + T - 1) / T;
+    // Per noise block: a short delay kernel lets the host enqueue the whole
+    // block ahead of the device, then every kernel family is bracketed by an
+    // event pair, so the device times contain no host launch gaps.
+    const bool vac = c->P.vacf_len > 0;
+    const size_t nk = 1 + (size_t)T * (vac ? 5 : 4);
+    std::vector<cudaEvent_t> ev(2 * nk, nullptr);
+    std::vector<int> fam(nk);
+    gld_status s = GLD_OK;
     for (auto& e : ev)
-        if (cudaEventCreate(&e) != cudaSuccess) return fail(c, GLD_E_CUDA, "cudaEventCreate");
+        if (cudaEventCreate(&e) != cudaSuccess) s = fail(c, GLD_E_CUDA, "cudaEventCreate");
     double acc[GLD_PROF_N] = {0};
     int64_t cnt[GLD_PROF_N] = {0};
-    gld_status s = GLD_OK;
-    auto timed = [&](int fam, auto&& launch) -> gld_status {
-        if (cudaEventRecord(ev[2 * fam], c->st) != cudaSuccess) return fail(c, GLD_E_CUDA, "cudaEventRecord");
-        const cudaError_t e = launch();
-        if (e != cudaSuccess) return cuda_check(c, e, "launch");
-        if (cudaEventRecord(ev[2 * fam + 1], c->st) != cudaSuccess) return fail(c, GLD_E_CUDA, "cudaEventRecord");
-        cnt[fam] += 1;
-        return GLD_OK;
-    };
-    for (int64_t it = 0; it < nsteps && s == GLD_OK; ++it) {
-        bool used[GLD_PROF_N] = {false};
-        if (!c->noise_valid || c->host_step >= c->noise_end) {
-            s = timed(GLD_PROF_NOISE, [&] { return launch_noise(c, c->st); });
-            used[GLD_PROF_NOISE] = true;
-            c->block_start = c->host_step;
-            c->noise_end = c->host_step + c->P.T;
-            c->noise_valid = true;
+    for (int64_t b = 0; b < blocks && s == GLD_OK; ++b) {
+        if (launch_delay(200000, c->st) != cudaSuccess) {
+            s = fail(c, GLD_E_CUDA, "delay kernel");
+            break;
         }
-        if (s == GLD_OK) {
-            s = timed(GLD_PROF_HIST, [&] {
+        size_t k = 0;
+        auto timed = [&](int f, auto&& launch) {
+            if (s != GLD_OK) return;
+            fam[k] = f;
+            if (cudaEventRecord(ev[2 * k], c->st) != cudaSuccess || launch() != cudaSuccess ||
+                cudaEventRecord(ev[2 * k + 1], c->st) != cudaSuccess)
+                s = fail(c, GLD_E_CUDA, "gld_profile_steps: launch failed");
+            ++k;
+        };
+        timed(GLD_PROF_NOISE, [&] { return launch_noise(c, c->st); });
+        c->block_start = c->host_step;
+        c->noise_end = c->host_step + T;
+        c->noise_valid = true;
+        for (int t = 0; t < T; ++t) {
+            timed(GLD_PROF_HIST, [&] {
                 return launch_hist_conv(c->B.ring, c->P.hist_bf16, c->P.n_pad, c->P.m_max, c->B.ctrl, 0, c->coef,
                                         c->P.nacc, c->B.conv, c->prm.kahan, c->st);
             });
-            used[GLD_PROF_HIST] = true;
+            timed(GLD_PROF_PAIR, [&] { return launch_pair_force_integrate(c->P, c->B, c->st); });
+            timed(GLD_PROF_CELL, [&] { return launch_rebuild(c->P, c->B, c->st); });
+            timed(GLD_PROF_CFORCE, [&] { return launch_cforce(c->P, c->B, 1, c->st); });
+            if (vac) timed(GLD_PROF_VACF, [&] { return launch_vacf(c->P, c->B, c->st); });
+            c->last_fr_row = t;
+            ++c->host_step;
         }
-        if (s == GLD_OK) {
-            s = timed(GLD_PROF_PAIR, [&] { return launch_pair_force_integrate(c->P, c->B, c->st); });
-            used[GLD_PROF_PAIR] = true;
-        }
-        if (s == GLD_OK) {
-            s = timed(GLD_PROF_CELL, [&] { return launch_rebuild(c->P, c->B, c->st); });
-            used[GLD_PROF_CELL] = true;
-        }
-        if (s == GLD_OK) {
-            s = timed(GLD_PROF_CFORCE, [&] { return launch_cforce(c->P, c->B, 1, c->st); });
-            used[GLD_PROF_CFORCE] = true;
-        }
-        if (s == GLD_OK && c->P.vacf_len > 0) {
-            s = timed(GLD_PROF_VACF, [&] { return launch_vacf(c->P, c->B, c->st); });
-            used[GLD_PROF_VACF] = true;
-        }
-        if (s != GLD_OK) break;
-        c->last_fr_row = c->host_step - c->block_start;
-        ++c->host_step;
-        if (cudaEventSynchronize(ev[2 * GLD_PROF_CFORCE + 1]) != cudaSuccess ||
-            (c->P.vacf_len > 0 && cudaEventSynchronize(ev[2 * GLD_PROF_VACF + 1]) != cudaSuccess)) {
-            s = fail(c, GLD_E_CUDA, "cudaEventSynchronize");
-            break;
-        }
-        for (int f = 0; f < GLD_PROF_N; ++f) {
-            if (!used[f]) continue;
+        if (s == GLD_OK && cudaStreamSynchronize(c->st) != cudaSuccess) s = fail(c, GLD_E_CUDA, "sync");
+        for (size_t q = 0; q < k && s == GLD_OK; ++q) {
             float t = 0.f;
-            if (cudaEventElapsedTime(&t, ev[2 * f], ev[2 * f + 1]) == cudaSuccess) acc[f] += t;
+            if (cudaEventElapsedTime(&t, ev[2 * q], ev[2 * q + 1]) != cudaSuccess) {
+                s = fail(c, GLD_E_CUDA, "cudaEventElapsedTime");
+                break;
+            }
+            acc[fam[q]] += t;
+            cnt[fam[q]] += fam[q] == GLD_PROF_CELL ? 4 : (fam[q] == GLD_PROF_NOISE ? 2 : 1);
         }
     }
-    for (auto& e : ev) cudaEventDestroy(e);
-    if (cnt[GLD_PROF_CELL]) cnt[GLD_PROF_CELL] *= 4;  // three cell kernels + list build
-    if (cnt[GLD_PROF_NOISE]) cnt[GLD_PROF_NOISE] *= 2;  // white noise + moving average
+    for (auto& e : ev)
+        if (e) cudaEventDestroy(e);
     for (int f = 0; f < GLD_PROF_N; ++f) {
         if (ms) ms[f] += acc[f];
         if (launches) launches[f] += cnt[f];

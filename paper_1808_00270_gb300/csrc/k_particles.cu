@@ -463,7 +463,25 @@ __global__ void pair_list(const StepParams P, const float4* __restrict__ pos_sor
     });
 }
 
+// A bounded idle wait of one thread (lets the host run ahead of the device
+// before a timed sequence of launches).
+__global__ void delay_kernel(unsigned long long ns)
+{
+    unsigned long long t0, t1;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    do {
+        __nanosleep(1000);
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+    } while (t1 - t0 < ns);
+}
+
 }  // namespace
+
+cudaError_t launch_delay(unsigned long long ns, cudaStream_t st)
+{
+    delay_kernel<<<1, 1, 0, st>>>(ns < 10000000ull ? ns : 10000000ull);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_pair_force_integrate(const StepParams& P, const ParticleBuffers& B, cudaStream_t st)
 {

@@ -40,6 +40,8 @@ struct ParticleBuffers {
 };
 
 cudaError_t launch_pair_force_integrate(const StepParams& P, const ParticleBuffers& B, cudaStream_t st);
+// One thread idles for ns nanoseconds (at most 10 ms) on the device.
+cudaError_t launch_delay(unsigned long long ns, cudaStream_t st);
 // Cell list of the positions `src`; skipped on the device when gate != nullptr
 // and *gate == 0.
 cudaError_t launch_cell_build(const StepParams& P, const ParticleBuffers& B, const float4* src, const int* gate,

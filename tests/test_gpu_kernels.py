@@ -76,7 +76,8 @@ def _ring_case(n, m_max, nacc, step, bf16, rng):
 
 
 @pytest.mark.parametrize("n,m_max,nacc,step", [(1000, 37, 2, 0), (1000, 37, 2, 123), (1100, 64, 3, 5),
-                                               (333, 9, 9, 1000001), (4096, 200, 2, 777), (70, 2, 1, 3)])
+                                               (333, 9, 9, 1000001), (4096, 200, 2, 777), (70, 2, 1, 3),
+                                               (20000, 400, 2, 12345), (20000, 400, 1, 3), (7000, 130, 3, 64)])
 @pytest.mark.parametrize("bf16", [False, True])
 @pytest.mark.parametrize("kahan", [False, True])
 def test_hist_conv_parity(n, m_max, nacc, step, bf16, kahan):
