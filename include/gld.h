@@ -79,11 +79,13 @@ typedef struct gld_params {
     int32_t hist_dtype;  /* GLD_HIST_F32 (default) or GLD_HIST_BF16 ring storage    */
     int32_t kahan;       /* 1: compensated summation over the m_max-1 history terms */
     int32_t vacf_len;    /* VACF lags kept (0 = no VACF)                             */
-    int32_t vacf_stride; /* steps between VACF time origins (>= 1)                   */
+    int32_t vacf_stride; /* steps between VACF time origins (>= 1); at most 32      */
+                         /* origins in flight: ceil(vacf_len / vacf_stride) <= 32   */
     int64_t vacf_burnin; /* first origin time; < 0 selects 2 m_max                  */
     int32_t noise_block; /* steps of F^R produced per noise launch (0 = 64)          */
     int32_t psd_clamp;   /* 1: clamp negative noise modes to 0 instead of failing    */
     int32_t use_graphs;  /* 1 (default): replay steps from a captured CUDA graph     */
+    const int32_t* order; /* optional [n]: internal storage order (see gld_get_order) */
     void* stream;        /* cudaStream_t for all work of this context                */
     gld_alloc_fn alloc;  /* optional device allocator (NULL: cudaMalloc)             */
     gld_free_fn free;
@@ -163,6 +165,15 @@ enum {
 };
 gld_status gld_get_array(gld_ctx* ctx, int32_t which, double* out);
 gld_status gld_set_array(gld_ctx* ctx, int32_t which, const double* in);
+
+/* Internally particles are stored in the Morton order of their cells at
+ * creation, so that neighbours sit close in memory; every array of this API
+ * is in the caller's order and the noise of a particle depends only on the
+ * caller's index.  Summation orders inside the library follow the internal
+ * order, so a checkpoint resumes bit for bit when the new context is created
+ * with the same order: int2ext[k] (length n) receives the caller's index of
+ * the particle stored at position k; pass it as gld_params.order. */
+gld_status gld_get_order(gld_ctx* ctx, int32_t* int2ext);
 
 /* Step counter n (the time index of R_n) and its setter (n >= 0, else
  * GLD_E_INVAL); setting it invalidates the noise window, which is rebuilt

@@ -39,7 +39,7 @@ class Params(C.Structure):
                 ("A_cons", C.c_double), ("skin", C.c_double), ("seed", C.c_uint64), ("hist_dtype", C.c_int32),
                 ("kahan", C.c_int32), ("vacf_len", C.c_int32), ("vacf_stride", C.c_int32),
                 ("vacf_burnin", C.c_int64), ("noise_block", C.c_int32), ("psd_clamp", C.c_int32),
-                ("use_graphs", C.c_int32), ("stream", C.c_void_p), ("alloc", ALLOC_FN),
+                ("use_graphs", C.c_int32), ("order", C.c_void_p), ("stream", C.c_void_p), ("alloc", ALLOC_FN),
                 ("free", FREE_FN), ("alloc_user", C.c_void_p)]
 
 
@@ -71,6 +71,7 @@ def lib():
             "gld_set_step": (i32, [vp, i64]),
             "gld_get_coefs": (i32, [vp, vp, vp, vp, vp]),
             "gld_get_pairs": (i32, [vp, vp, i64, C.POINTER(i64)]),
+            "gld_get_order": (i32, [vp, vp]),
             "gld_profile_steps": (i32, [vp, i64, vp, vp]),
             "gld_last_error": (C.c_char_p, [vp]),
             "gld_destroy": (i32, [vp]),
@@ -91,7 +92,7 @@ def exported_symbols() -> list[str]:
     """Names of the C entry points the binding expects the library to export."""
     return ["gld_params_default", "gld_create", "gld_set_kernels", "gld_step", "gld_sync", "gld_vacf",
             "gld_get_state", "gld_get_array", "gld_set_array", "gld_get_step", "gld_set_step",
-            "gld_get_coefs", "gld_get_pairs", "gld_profile_steps", "gld_last_error", "gld_destroy", "gld_philox_dev",
+            "gld_get_coefs", "gld_get_pairs", "gld_get_order", "gld_profile_steps", "gld_last_error", "gld_destroy", "gld_philox_dev",
             "gld_gauss3_dev", "gld_hist_conv_dev", "gld_pairs_noalloc"]
 
 
@@ -137,7 +138,7 @@ class GLD:
     def __init__(self, *, n, box, dt, m_max, r_c, pos, vel, mass=1.0, kT=1.0, r_c_min=0.0,
                  A_cons=0.0, skin=0.0, seed=1, hist_dtype="f32", kahan=False, vacf_len=0, vacf_stride=1,
                  vacf_burnin=-1, noise_block=64, psd_clamp=False, use_graphs=True, stream=None,
-                 torch_allocator=True):
+                 torch_allocator=True, order=None):
         L = lib()
         p = Params()
         L.gld_params_default(C.byref(p))
@@ -154,6 +155,10 @@ class GLD:
         self._alloc = _TorchAllocator() if torch_allocator else None
         if self._alloc is not None:
             p.alloc, p.free = self._alloc.alloc, self._alloc.free
+        self._order = None
+        if order is not None:
+            self._order = np.ascontiguousarray(order, dtype=np.int32)
+            p.order = _ptr(self._order)
         self._params = p
         self.n, self.m_max, self.vacf_len = int(n), int(m_max), int(vacf_len)
         pos, vel = _f64(pos).reshape(self.n, 3), _f64(vel).reshape(self.n, 3)
@@ -244,6 +249,12 @@ class GLD:
 
     def set_step(self, step: int) -> None:
         self._check(lib().gld_set_step(self._h, int(step)))
+
+    def order(self) -> np.ndarray:
+        """Internal storage order: entry k is the caller's index stored at k."""
+        out = np.zeros(self.n, dtype=np.int32)
+        self._check(lib().gld_get_order(self._h, _ptr(out)))
+        return out
 
     def coefs(self) -> dict:
         M = self.m_max

@@ -8,6 +8,7 @@
 // steps.  The step counter lives on the device, so a graph holding one noise
 // block and T steps is captured once and replayed for as long as the kernels
 // stay the same.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -46,6 +47,8 @@ struct gld_ctx {
     bool graph_failed = false;
     std::string msg;
     gld_status latched = GLD_OK;
+    std::vector<int> int2ext;  // caller's index of the particle stored at k
+    int* d_int2ext = nullptr;
 };
 
 namespace {
@@ -118,13 +121,15 @@ double wrap_host(double x, double L)
     return x;
 }
 
-// Host <-> device transfers of [n][3] vectors stored as float4 by id.
+// Host <-> device transfers of [n][3] vectors (caller's order) stored as
+// float4 in internal order.
 gld_status upload_vec(gld_ctx* c, float4* dst, const double* src, bool wrap)
 {
     const int n = c->P.n;
     std::vector<float4> h((size_t)c->P.n_pad, make_float4(0.f, 0.f, 0.f, 0.f));
     for (int i = 0; i < n; ++i) {
-        double x = src[3 * i], y = src[3 * i + 1], z = src[3 * i + 2];
+        const size_t e = (size_t)c->int2ext[i];
+        double x = src[3 * e], y = src[3 * e + 1], z = src[3 * e + 2];
         if (wrap) {
             x = wrap_host(x, c->prm.box);
             y = wrap_host(y, c->prm.box);
@@ -150,9 +155,10 @@ gld_status download_vec(gld_ctx* c, const float4* src, double* dst)
     GLD_CUDA(c, cudaMemcpyAsync(h.data(), src, sizeof(float4) * n, cudaMemcpyDeviceToHost, c->st));
     GLD_CUDA(c, cudaStreamSynchronize(c->st));
     for (int i = 0; i < n; ++i) {
-        dst[3 * i] = h[i].x;
-        dst[3 * i + 1] = h[i].y;
-        dst[3 * i + 2] = h[i].z;
+        const size_t e = (size_t)c->int2ext[i];
+        dst[3 * e] = h[i].x;
+        dst[3 * e + 1] = h[i].y;
+        dst[3 * e + 2] = h[i].z;
     }
     return GLD_OK;
 }
@@ -167,7 +173,7 @@ gld_status download_planes(gld_ctx* c, const float* src, int rows, double* dst)
     GLD_CUDA(c, cudaStreamSynchronize(c->st));
     for (int r = 0; r < rows; ++r)
         for (int i = 0; i < n; ++i)
-            for (int k = 0; k < 3; ++k) dst[((size_t)r * n + i) * 3 + k] = h[(r * 3 + k) * np + i];
+            for (int k = 0; k < 3; ++k) dst[((size_t)r * n + c->int2ext[i]) * 3 + k] = h[(r * 3 + k) * np + i];
     return GLD_OK;
 }
 
@@ -213,7 +219,7 @@ gld_status rebuild_cells_and_fc(gld_ctx* c)
 
 cudaError_t launch_noise(gld_ctx* c, cudaStream_t s)
 {
-    return launch_noise_block(c->P, c->B.ctrl, c->W, c->Acp, c->la, c->B.frblock, c->prm.seed, c->num_sms, s);
+    return launch_noise_block(c->P, c->B.ctrl, c->W, c->Acp, c->la, c->B.frblock, c->prm.seed, c->d_int2ext, s);
 }
 
 cudaError_t launch_one_step(gld_ctx* c, cudaStream_t s)
@@ -249,12 +255,7 @@ bool capture_graph(gld_ctx* c)
     return ok;
 }
 
-int clamp_block(int t)
-{
-    if (t <= 16) return 16;
-    if (t <= 32) return 32;
-    return kMaxNoiseBlock;
-}
+int clamp_block(int) { return kMaxNoiseBlock; }  // the filter produces 64-step blocks
 
 }  // namespace
 
@@ -283,7 +284,8 @@ gld_status gld_create(const gld_params* p, const double* pos, const double* vel,
     if (p->n < 1 || p->m_max < 2 || p->m_max > 4096 || !(p->box > 0) || !(p->mass > 0) || !(p->dt > 0) ||
         !(p->r_c > 0) || p->r_c > 0.5 * p->box || p->kT < 0 || p->r_c_min < 0 || p->skin < 0 ||
         (p->hist_dtype != GLD_HIST_F32 && p->hist_dtype != GLD_HIST_BF16) || p->vacf_len < 0 ||
-        (p->vacf_len > 0 && p->vacf_stride < 1))
+        (p->vacf_len > 0 && p->vacf_stride < 1) ||
+        (p->vacf_len > 0 && (p->vacf_len + p->vacf_stride - 1) / p->vacf_stride > 32))
         return GLD_E_INVAL;
     gld_ctx* c = new gld_ctx();
     c->prm = *p;
@@ -347,6 +349,46 @@ gld_status gld_create(const gld_params* p, const double* pos, const double* vel,
 
     const size_t np = P.n_pad, n3 = 3 * np;
     const int ncells = nc * nc * nc;
+    // Internal order: the caller's, or the Morton order of the cells at R_0
+    // (ties by the caller's index), so that neighbours are close in memory.
+    c->int2ext.resize(p->n);
+    if (p->order) {
+        std::vector<char> seen(p->n, 0);
+        for (int k = 0; k < p->n; ++k) {
+            const int e = p->order[k];
+            if (e < 0 || e >= p->n || seen[e]) {
+                cudaStreamDestroy(c->cap);
+                delete c;
+                return GLD_E_INVAL;
+            }
+            seen[e] = 1;
+            c->int2ext[k] = e;
+        }
+    } else {
+        auto spread = [](uint64_t v) {  // 21 bits -> every third bit
+            v &= 0x1fffff;
+            v = (v | v << 32) & 0x1f00000000ffffULL;
+            v = (v | v << 16) & 0x1f0000ff0000ffULL;
+            v = (v | v << 8) & 0x100f00f00f00f00fULL;
+            v = (v | v << 4) & 0x10c30c30c30c30c3ULL;
+            v = (v | v << 2) & 0x1249249249249249ULL;
+            return v;
+        };
+        const int g = std::max(nc, 1);
+        std::vector<std::pair<uint64_t, int>> key(p->n);
+        for (int e = 0; e < p->n; ++e) {
+            uint64_t cc[3];
+            for (int d = 0; d < 3; ++d) {
+                const double x = wrap_host(pos[3 * e + d], p->box);
+                long long ci = (long long)std::floor(x / p->box * g);
+                ci = ci < 0 ? 0 : (ci >= g ? g - 1 : ci);
+                cc[d] = (uint64_t)ci;
+            }
+            key[e] = {spread(cc[0]) | spread(cc[1]) << 1 | spread(cc[2]) << 2, e};
+        }
+        std::sort(key.begin(), key.end());
+        for (int k = 0; k < p->n; ++k) c->int2ext[k] = key[k].second;
+    }
     const int chunks = (ncells + 511) / 512;
     ParticleBuffers& B = c->B;
     bool ok = true;
@@ -382,8 +424,8 @@ gld_status gld_create(const gld_params* p, const double* pos, const double* vel,
     B.ccnt = alloc_n<long long>(c, std::max(P.vacf_len, 1), ok);
     B.norig = alloc_n<long long>(c, 1, ok);
     B.vdone = alloc_n<unsigned>(c, 1, ok);
-    c->la = fir_copy_len(P.T, P.H);
-    c->Acp = alloc_n<float>(c, 4 * (size_t)c->la, ok);
+    c->la = fir_taps_len(P.H);
+    c->Acp = alloc_n<float>(c, (size_t)c->la, ok);
     c->coef = alloc_n<float>(c, (size_t)kMaxAcc * P.m_max, ok);
     c->g0 = alloc_n<float>(c, 2 * kMaxQ, ok);
     c->d_Kd = alloc_n<double>(c, P.m_max, ok);
@@ -393,6 +435,7 @@ gld_status gld_create(const gld_params* p, const double* pos, const double* vel,
     c->d_scal = alloc_n<double>(c, 4, ok);
     c->d_status = alloc_n<int>(c, 1, ok);
     c->d_in = alloc_n<double>(c, (size_t)(1 + 2 * kMaxQ) * P.m_max, ok);
+    c->d_int2ext = alloc_n<int>(c, np, ok);
     B.g0 = c->g0;
     if (!ok) {
         gld_destroy(c);
@@ -406,6 +449,9 @@ gld_status gld_create(const gld_params* p, const double* pos, const double* vel,
     if (s == GLD_OK && cudaMemcpyAsync(B.ctrl, &h, sizeof(h), cudaMemcpyHostToDevice, c->st) != cudaSuccess) s = GLD_E_CUDA;
     const int total = P.n;
     if (s == GLD_OK && cudaMemcpyAsync(B.cell_start + ncells, &total, sizeof(int), cudaMemcpyHostToDevice, c->st) != cudaSuccess)
+        s = GLD_E_CUDA;
+    if (s == GLD_OK && cudaMemcpyAsync(c->d_int2ext, c->int2ext.data(), sizeof(int) * P.n, cudaMemcpyHostToDevice,
+                                       c->st) != cudaSuccess)
         s = GLD_E_CUDA;
     if (s == GLD_OK) s = upload_vec(c, B.pos, pos, true);
     if (s == GLD_OK) s = upload_vec(c, B.pos_next, pos, true);
@@ -606,7 +652,7 @@ gld_status gld_get_array(gld_ctx* c, int32_t which, double* out)
                     } else {
                         std::memcpy(&v, h.data() + 4 * idx, 4);
                     }
-                    out[((size_t)(m - 1) * n + i) * 3 + k] = v;
+                    out[((size_t)(m - 1) * n + c->int2ext[i]) * 3 + k] = v;
                 }
         }
         return GLD_OK;
@@ -648,7 +694,7 @@ gld_status gld_set_array(gld_ctx* c, int32_t which, const double* in)
             for (int k = 0; k < 3; ++k)
                 for (int i = 0; i < n; ++i) {
                     const size_t idx = ((size_t)slot * 3 + k) * np + i;
-                    const float v = (float)in[((size_t)(m - 1) * n + i) * 3 + k];
+                    const float v = (float)in[((size_t)(m - 1) * n + c->int2ext[i]) * 3 + k];
                     if (P.hist_bf16) {
                         const __nv_bfloat16 b = __float2bfloat16_rn(v);
                         std::memcpy(h.data() + 2 * idx, &b, 2);
@@ -662,6 +708,13 @@ gld_status gld_set_array(gld_ctx* c, int32_t which, const double* in)
     }
     default: return fail(c, GLD_E_INVAL, "gld_set_array: array is read-only or unknown");
     }
+}
+
+gld_status gld_get_order(gld_ctx* c, int32_t* int2ext)
+{
+    if (!c || !int2ext) return GLD_E_INVAL;
+    std::memcpy(int2ext, c->int2ext.data(), sizeof(int32_t) * c->P.n);
+    return GLD_OK;
 }
 
 gld_status gld_get_step(gld_ctx* c, int64_t* step)
@@ -716,9 +769,15 @@ gld_status gld_get_pairs(gld_ctx* c, int32_t* pairs, int64_t cap, int64_t* count
     unsigned long long cnt = 0;
     if (s == GLD_OK) s = cuda_check(c, cudaStreamSynchronize(c->st), "sync");
     if (s == GLD_OK) s = cuda_check(c, cudaMemcpy(&cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost), "copy");
-    if (s == GLD_OK && cap > 0)
-        s = cuda_check(c, cudaMemcpy(pairs, d_pairs, sizeof(int) * 2 * (size_t)std::min<long long>(cap, (long long)cnt),
-                                     cudaMemcpyDeviceToHost), "copy");
+    if (s == GLD_OK && cap > 0) {
+        const size_t m = (size_t)std::min<long long>(cap, (long long)cnt);
+        s = cuda_check(c, cudaMemcpy(pairs, d_pairs, sizeof(int) * 2 * m, cudaMemcpyDeviceToHost), "copy");
+        for (size_t q = 0; s == GLD_OK && q < m; ++q) {  // caller's indices, i < j
+            const int a = c->int2ext[pairs[2 * q]], b = c->int2ext[pairs[2 * q + 1]];
+            pairs[2 * q] = std::min(a, b);
+            pairs[2 * q + 1] = std::max(a, b);
+        }
+    }
     if (count) *count = (int64_t)cnt;
     cudaStreamSynchronize(c->st);
     dfree(c, d_pairs);

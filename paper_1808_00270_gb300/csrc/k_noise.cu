@@ -8,10 +8,10 @@
 // wgen: white noise W_{i,k} from Philox4x32-10 into a ring of times, each
 //   (particle, time) drawn exactly once over the whole run.
 // fir:  F^R_{i,n+t} = sum_{s=-(m_max-1)}^{m_max-1} A_s W_{i,n+t+s} for a block
-//   of T steps at once (the windowed generation remarked on in Sec. II C):
-//   one thread per (particle, component) keeps T outputs in registers and
-//   streams its W window once; the taps come from shared memory as 16-byte
-//   broadcasts out of four shifted, zero-padded copies of A.
+//   of T = 64 steps at once (the windowed generation remarked on in Sec. II C),
+//   from a shared-memory tile of W with a sliding register window.
+#include <algorithm>
+
 #include "launch.h"
 
 namespace gld {
@@ -111,18 +111,15 @@ __global__ void __launch_bounds__(kPrepThreads) prep(const PrepArgs a)
         a.scal[3] = negsum / (double)L;
         *a.status = anybad > 0.0 ? -3 : 0;
     }
-    // Four copies of the zero-padded taps, copy r shifted right by r entries:
-    // Apad[u] = A_{u - T - H} for T <= u <= T + 2H, else 0.
-    for (int idx = threadIdx.x; idx < 4 * a.la; idx += blockDim.x) {
-        const int r = idx / a.la, u = idx % a.la - r;
-        a.Acp[idx] = (u >= a.T && u <= a.T + 2 * H) ? (float)a.A[u - a.T] : 0.0f;
-    }
+    // Filter taps in FP32: Acp[sigma] = A_{sigma - H}, zero past sigma = 2H.
+    for (int idx = threadIdx.x; idx < a.la; idx += blockDim.x) a.Acp[idx] = idx <= 2 * H ? (float)a.A[idx] : 0.0f;
 }
 
 constexpr int kGenThreads = 256;
 
 __global__ void __launch_bounds__(kGenThreads)
-    wgen(const StepParams P, const Ctrl* __restrict__ ctrl, float* __restrict__ W, uint32_t k0, uint32_t k1)
+    wgen(const StepParams P, const Ctrl* __restrict__ ctrl, float* __restrict__ W, uint32_t k0, uint32_t k1,
+         const int* __restrict__ int2ext)
 {
     const long long n0 = ctrl->step;
     const long long need_lo = n0 - P.H, hi = n0 + P.T + P.H;
@@ -137,7 +134,7 @@ __global__ void __launch_bounds__(kGenThreads)
         const long long time = lo + kk;
         long long slot = time % P.lw;
         if (slot < 0) slot += P.lw;
-        const float3 z = gauss3(k0, k1, (uint32_t)i, time, 0u);
+        const float3 z = gauss3(k0, k1, (uint32_t)__ldg(int2ext + i), time, 0u);
         float* w = W + (size_t)slot * 3 * np + i;
         w[0] = z.x;
         w[np] = z.y;
@@ -145,49 +142,72 @@ __global__ void __launch_bounds__(kGenThreads)
     }
 }
 
-constexpr int kFirThreads = 128;
+constexpr int kFirThreads = 128;  // 4 warps x 16 outputs = one 64-step block
+constexpr int kFirR = 16;         // outputs per thread (register window)
+constexpr int kFirStreams = 32;   // streams per CTA (one per lane)
 
-template <int T>
+// F^R[t][j] = sum_{sigma=0}^{2H} A_{sigma-H} W[n0 - H + t + sigma][j], t < 64.
+// The taps are taken in chunks of `chunk` (a multiple of 16): the CTA stages
+// the chunk's taps and the W rows they touch for its 32 streams in shared
+// memory; warp w produces outputs 16 w .. 16 w + 15 with a 16-deep window of
+// W rows in registers that slides by one row per tap, so each tap costs one
+// shared load of W, one broadcast tap load and 16 FMAs.
 __global__ void __launch_bounds__(kFirThreads)
-    fir(const StepParams P, Ctrl* __restrict__ ctrl, const float* __restrict__ W, const float* __restrict__ Acp,
-        int la, float* __restrict__ out)
+    fir(const StepParams P, Ctrl* __restrict__ ctrl, const float* __restrict__ W, const float* __restrict__ taps,
+        int ntaps, int chunk, float* __restrict__ out)
 {
-    extern __shared__ float4 As4[];
-    float* As = (float*)As4;
-    for (int idx = threadIdx.x; idx < 4 * la; idx += blockDim.x) As[idx] = Acp[idx];
-    __syncthreads();
+    extern __shared__ float4 sm4[];
+    float* At = (float*)sm4;               // [chunk]
+    float* Wt = At + chunk;                // [chunk + 64][32]
     const long long n0 = ctrl->step;
     const long long np = P.n_pad, nstreams = 3 * np;
-    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < nstreams) {
-        float acc[T];
+    const long long j = (long long)blockIdx.x * kFirStreams + (threadIdx.x & 31);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    (void)lane;
+    const int nk = 64 + 2 * P.H;           // rows holding real W
+    const int t0 = warp * kFirR;
+    float acc[kFirR], win[kFirR];
 #pragma unroll
-        for (int t = 0; t < T; ++t) acc[t] = 0.f;
-        const int nk = T + 2 * P.H;
-        const int nk4 = (nk + 3) & ~3;
-        long long slot = (n0 - P.H) % P.lw;
-        if (slot < 0) slot += P.lw;
-        for (int kk0 = 0; kk0 < nk4; kk0 += 4) {
+    for (int r = 0; r < kFirR; ++r) acc[r] = 0.f;
+    for (int c0 = 0; c0 < ntaps; c0 += chunk) {
+        const int cn = min(chunk, ntaps - c0);
+        __syncthreads();  // the previous chunk is consumed
+        for (int k = threadIdx.x; k < cn; k += blockDim.x) At[k] = taps[c0 + k];
+        // W rows of this chunk: 8 threads copy one 128-byte row as 16-byte
+        // asynchronous copies, all in flight together; rows past the window
+        // are zero-filled.
+        const long long jb = (long long)blockIdx.x * kFirStreams;
+        for (int idx = threadIdx.x; idx < (cn + 64) * 8; idx += blockDim.x) {
+            const int k = idx >> 3, part = idx & 7;
+            const int row = c0 + k;
+            const bool real = row < nk && jb + 4 * part < nstreams;
+            long long slot = real ? (n0 - P.H + row) % P.lw : 0;
+            if (slot < 0) slot += P.lw;
+            const float* src = W + (size_t)slot * nstreams + jb + 4 * part;
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(Wt + k * 32 + 4 * part);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(real ? 16 : 0)
+                         : "memory");
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncthreads();
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int kk = kk0 + e;
-                const float w = kk < nk ? __ldcs(W + (size_t)slot * nstreams + j) : 0.f;
-                slot = slot + 1 == P.lw ? 0 : slot + 1;
-                const int r = 3 - e;  // copy whose shift makes the 16-byte loads aligned
+        for (int r = 0; r < kFirR - 1; ++r) win[r] = Wt[(t0 + r) * 32 + lane];
+        const float* wp = Wt + (t0 + kFirR - 1) * 32 + lane;  // next row to enter the window
+        for (int sg = 0; sg < cn; sg += kFirR) {
 #pragma unroll
-                for (int j4 = 0; j4 < T / 4; ++j4) {
-                    // taps for t = 4 j4 + 3 .. 4 j4 at Apad[kk + T - t]
-                    const float4 a4 = *(const float4*)(As + r * la + (kk - e) + T - 4 * j4);
-                    acc[4 * j4 + 3] = fmaf(a4.x, w, acc[4 * j4 + 3]);
-                    acc[4 * j4 + 2] = fmaf(a4.y, w, acc[4 * j4 + 2]);
-                    acc[4 * j4 + 1] = fmaf(a4.z, w, acc[4 * j4 + 1]);
-                    acc[4 * j4 + 0] = fmaf(a4.w, w, acc[4 * j4 + 0]);
-                }
+            for (int u = 0; u < kFirR; ++u) {
+                // window holds rows t0 + sigma .. t0 + sigma + 15, sigma = sg + u (chunk-local)
+                win[(u + kFirR - 1) % kFirR] = wp[0];
+                wp += 32;
+                const float a = At[sg + u];
+#pragma unroll
+                for (int r = 0; r < kFirR; ++r) acc[r] = fmaf(a, win[(u + r) % kFirR], acc[r]);
             }
         }
-#pragma unroll
-        for (int t = 0; t < T; ++t) out[(size_t)t * nstreams + j] = acc[t];
     }
+    if (j < nstreams)
+#pragma unroll
+        for (int r = 0; r < kFirR; ++r) out[(size_t)(t0 + r) * nstreams + j] = acc[r];
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -225,6 +245,7 @@ __global__ void gauss3_k(uint32_t k0, uint32_t k1, const uint32_t* __restrict__ 
 }  // namespace
 
 int fir_copy_len(int T, int H) { return (2 * T + 2 * H + 4 + 3) & ~3; }
+int fir_taps_len(int H) { return (2 * H + 1 + 15) & ~15; }
 
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t st)
 {
@@ -235,30 +256,21 @@ cudaError_t launch_prep(const PrepArgs& a, cudaStream_t st)
 }
 
 cudaError_t launch_noise_block(const StepParams& P, Ctrl* ctrl, float* W, const float* Acp, int la, float* frblock,
-                               unsigned long long seed, int num_sms, cudaStream_t st)
+                               unsigned long long seed, const int* int2ext, cudaStream_t st)
 {
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     dim3 g((P.n + kGenThreads - 1) / kGenThreads, (unsigned)P.T);
-    wgen<<<g, kGenThreads, 0, st>>>(P, ctrl, W, k0, k1);
+    wgen<<<g, kGenThreads, 0, st>>>(P, ctrl, W, k0, k1, int2ext);
     const long long streams = 3LL * P.n_pad;
-    const unsigned grid = (unsigned)((streams + kFirThreads - 1) / kFirThreads);
-    const size_t smem = sizeof(float) * 4 * (size_t)la;
-    (void)num_sms;
-    switch (P.T) {
-    case 16:
-        if (smem > 48 * 1024) cudaFuncSetAttribute(fir<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        fir<16><<<grid, kFirThreads, smem, st>>>(P, ctrl, W, Acp, la, frblock);
-        break;
-    case 32:
-        if (smem > 48 * 1024) cudaFuncSetAttribute(fir<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        fir<32><<<grid, kFirThreads, smem, st>>>(P, ctrl, W, Acp, la, frblock);
-        break;
-    case 64:
-        if (smem > 48 * 1024) cudaFuncSetAttribute(fir<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        fir<64><<<grid, kFirThreads, smem, st>>>(P, ctrl, W, Acp, la, frblock);
-        break;
-    default: return cudaErrorInvalidValue;
-    }
+    (void)la;
+    if (P.T != 64) return cudaErrorInvalidValue;
+    const int ntaps = fir_taps_len(P.H);
+    const int chunk = std::min(ntaps, 768);  // 110 KB of shared memory: two CTAs per SM
+    const size_t smem = sizeof(float) * ((size_t)chunk + (size_t)(64 + chunk) * kFirStreams);
+    cudaError_t e = cudaFuncSetAttribute(fir, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)((streams + kFirStreams - 1) / kFirStreams);
+    fir<<<grid, kFirThreads, smem, st>>>(P, ctrl, W, Acp, ntaps, chunk, frblock);
     return cudaGetLastError();
 }
 

@@ -18,9 +18,10 @@
 // Every neighbour sum runs over a Verlet list with the exact FP32 r < r_c test
 // of the cell traversal, so the pair set is the same; lists are sorted by
 // neighbour id, so the order of every sum does not depend on when the list was
-// built.  Particles are visited in the cell order of the last build; all
-// per-particle arrays stay indexed by the particle id, which never changes, so
-// the displacement history is never permuted.
+// built.  Particles are stored in the Morton order of their cells at creation
+// and a thread handles one particle id, so own loads are coalesced and
+// neighbours lie close in memory; ids never change, so the displacement
+// history is never permuted.
 #include <cuda_bf16.h>
 
 #include "launch.h"
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(kPairThreads)
     if (k >= P.n) return;
     const long long n = ctrl->step;
     const long long np = P.n_pad;
-    const int id = perm[k];
+    const int id = k;  // particles in storage (Morton) order; lists are by id
     const float4 pi = pos[id];
     const float4 vi = vel[id];
 
@@ -71,7 +72,7 @@ __global__ void __launch_bounds__(kPairThreads)
     float f0x = 0.f, f0y = 0.f, f0z = 0.f;  // instantaneous (m = 0) pair terms
     float fhx = 0.f, fhy = 0.f, fhz = 0.f;  // history pair terms (times -1, before 1/dt)
     if (P.Q + P.Qs > 0) {
-        for_each_listed(pi, k, nbr, nbr_cnt[k], P.n_pad, pos, P, [&](int jd, float dx, float dy, float dz, float r2) {
+        for_each_listed(pi, id, nbr, nbr_cnt[id], P.n_pad, pos, P, [&](int jd, float dx, float dy, float dz, float r2) {
             const float r = sqrtf(r2);
             const float inv_r = 1.0f / r;
             const float ex = dx * inv_r, ey = dy * inv_r, ez = dz * inv_r;
@@ -267,15 +268,15 @@ __global__ void __launch_bounds__(kThreads)
     int c = 0;
     for_each_in_stencil(pi, id, pos_sorted, cell_start, P, P.rl2, [&](int jd, float, float, float, float) {
         if (c < cap) {
-            // insertion by id
+            // insertion by id into the list of particle id
             int p = c;
             while (p > 0) {
-                const int q = nbr[(size_t)(p - 1) * stride + k];
+                const int q = nbr[(size_t)(p - 1) * stride + id];
                 if (q < jd) break;
-                nbr[(size_t)p * stride + k] = q;
+                nbr[(size_t)p * stride + id] = q;
                 --p;
             }
-            nbr[(size_t)p * stride + k] = jd;
+            nbr[(size_t)p * stride + id] = jd;
         }
         ++c;
     });
@@ -283,7 +284,7 @@ __global__ void __launch_bounds__(kThreads)
         atomicOr(&ctrl->err, kErrNbrOverflow);
         c = cap;
     }
-    nbr_cnt[k] = c;
+    nbr_cnt[id] = c;
     perm[k] = id;
     disp_build[id] = disp[id];
 }
@@ -301,11 +302,11 @@ __global__ void __launch_bounds__(kThreads)
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k == 0) ctrl->rebuild = 0;  // the lists are current for R_{n+1}
     if (k < P.n) {
-        const int id = perm[k];
+        const int id = k;
         const float4 pi = pos_next[id];
         pos[id] = pi;
         float fx = 0.f, fy = 0.f, fz = 0.f;
-        for_each_listed(pi, k, nbr, nbr_cnt[k], P.n_pad, pos_next, P, [&](int, float dx, float dy, float dz, float r2) {
+        for_each_listed(pi, id, nbr, nbr_cnt[id], P.n_pad, pos_next, P, [&](int, float dx, float dy, float dz, float r2) {
             const float r = sqrtf(r2);
             // -dU/dr e_ij with U = A (1 - r/r_c)^2, e_ij = (R_i - R_j)/r
             const float s = P.fc_mag * (1.0f - r * P.inv_rc) / r;
@@ -333,18 +334,20 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // ---- velocity autocorrelation ------------------------------------------------
-constexpr int kVacfGroup = 8;  // origins accumulated per pass over V
+constexpr int kVacfMaxOrigins = 32;  // origins in flight (vacf_len / vacf_stride)
 
-__device__ __forceinline__ double warp_sum(double v)
+__device__ __forceinline__ float warp_sum_f(float v)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
-// Block b reads each velocity once and dots it with every active origin's
-// stored velocity (origin j = age 0 is the newest); per-block FP64 partials,
-// reduced in a fixed order by the last block to finish.
+// Each thread dots its particles' velocities with every active origin's
+// stored velocity (age j = 0 is the newest) into per-origin registers; warp
+// sums in FP32, block and grid sums in FP64 in a fixed order (the last block
+// to finish adds the per-block partials).
+template <int NO>
 __global__ void __launch_bounds__(kThreads)
     vacf(const StepParams P, const Ctrl* __restrict__ ctrl, const float4* __restrict__ vel,
          float4* __restrict__ vorig, double* __restrict__ partial, double* __restrict__ csum,
@@ -355,45 +358,45 @@ __global__ void __launch_bounds__(kThreads)
     const long long rel = t - P.vacf_burnin;
     const long long o_now = rel / P.vacf_stride;
     const bool is_origin = (rel % P.vacf_stride) == 0;
-    // active ages j: o = o_now - j >= 0 and lag = rel - o stride < vacf_len
     int n_act = 0;
     for (int jj = 0; jj < P.n_os; ++jj) {
         const long long o = o_now - jj;
         if (o >= 0 && rel - o * (long long)P.vacf_stride < P.vacf_len) n_act = jj + 1;
     }
-    __shared__ double wsum[kThreads / 32][kVacfGroup];
+    // slot of age j: (o_now - j) mod n_os
+    const int slot0 = (int)(o_now % P.n_os);
+    float acc[NO];
+#pragma unroll
+    for (int q = 0; q < NO; ++q) acc[q] = 0.f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+        const float4 v = vel[i];
+        float4 w[NO];
+#pragma unroll
+        for (int q = 0; q < NO; ++q) {
+            int sl = slot0 - q;
+            sl = sl < 0 ? sl + P.n_os : sl;
+            w[q] = (q < n_act && !(q == 0 && is_origin)) ? __ldcs(vorig + (size_t)sl * P.n + i) : v;
+        }
+#pragma unroll
+        for (int q = 0; q < NO; ++q)
+            if (q < n_act) acc[q] = fmaf(v.x, w[q].x, fmaf(v.y, w[q].y, fmaf(v.z, w[q].z, acc[q])));
+        if (is_origin) vorig[(size_t)slot0 * P.n + i] = v;
+    }
+    __shared__ double wsum[kThreads / 32][NO];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int g0 = 0; g0 < n_act; g0 += kVacfGroup) {
-        float acc[kVacfGroup];
 #pragma unroll
-        for (int q = 0; q < kVacfGroup; ++q) acc[q] = 0.f;
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
-            const float4 v = vel[i];
-#pragma unroll
-            for (int q = 0; q < kVacfGroup; ++q) {
-                const int jj = g0 + q;
-                if (jj >= n_act) break;
-                const long long o = o_now - jj;
-                const float4* v0 = vorig + (size_t)(o % P.n_os) * P.n;
-                const float4 w = (jj == 0 && is_origin) ? v : v0[i];
-                acc[q] += dot3(v.x, v.y, v.z, w.x, w.y, w.z);
-            }
-            if (g0 == 0 && is_origin) vorig[(size_t)(o_now % P.n_os) * P.n + i] = v;
-        }
-#pragma unroll
-        for (int q = 0; q < kVacfGroup; ++q) {
-            const double s = warp_sum((double)acc[q]);
-            if (lane == 0) wsum[warp][q] = s;
-        }
-        __syncthreads();
-        if (threadIdx.x < kVacfGroup && g0 + (int)threadIdx.x < n_act) {
-            double s = 0.0;
-            for (int w = 0; w < kThreads / 32; ++w) s += wsum[w][threadIdx.x];
-            partial[(size_t)(g0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
-        }
-        __syncthreads();
+    for (int q = 0; q < NO; ++q) {
+        const float sq = warp_sum_f(acc[q]);
+        if (lane == 0) wsum[warp][q] = (double)sq;
+    }
+    __syncthreads();
+    if (threadIdx.x < NO && (int)threadIdx.x < n_act) {
+        double sb = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) sb += wsum[w][threadIdx.x];
+        partial[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = sb;
     }
     __shared__ bool last;
+    __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         last = atomicAdd(done, 1u) == gridDim.x - 1;
@@ -401,15 +404,30 @@ __global__ void __launch_bounds__(kThreads)
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int jj = warp; jj < n_act; jj += kThreads / 32) {
+    // all partials of all origins loaded together, then a fixed-order tree
+    double sg[NO];
+#pragma unroll
+    for (int q = 0; q < NO; ++q) sg[q] = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+#pragma unroll
+        for (int q = 0; q < NO; ++q)
+            if (q < n_act) sg[q] += __ldcg(partial + (size_t)q * gridDim.x + b);
+#pragma unroll
+    for (int q = 0; q < NO; ++q) {
+        double v = sg[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) wsum[warp][q] = v;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < n_act) {
+        const int jj = threadIdx.x;
         const long long o = o_now - jj;
         const long long lg = rel - o * (long long)P.vacf_stride;
-        if (o < 0 || lg >= P.vacf_len) continue;
-        double v = 0.0;
-        for (int b = lane; b < (int)gridDim.x; b += 32) v += ((volatile double*)partial)[(size_t)jj * gridDim.x + b];
-        v = warp_sum(v);
-        if (lane == 0) {
-            csum[lg] += v;
+        double t = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) t += wsum[w][jj];
+        if (o >= 0 && lg < P.vacf_len) {
+            csum[lg] += t;
             ccnt[lg] += 1;
         }
     }
@@ -439,8 +457,8 @@ __global__ void list_pair_list(const StepParams P, const float4* __restrict__ po
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= P.n) return;
-    const int id = perm[k];
-    for_each_listed(pos[id], k, nbr, nbr_cnt[k], P.n_pad, pos, P,
+    const int id = k;
+    for_each_listed(pos[id], id, nbr, nbr_cnt[id], P.n_pad, pos, P,
                     [&](int jd, float, float, float, float) { emit_pair(id, jd, pairs, cap, count); });
 }
 
@@ -529,7 +547,16 @@ cudaError_t launch_cforce(const StepParams& P, const ParticleBuffers& B, int mod
 cudaError_t launch_vacf(const StepParams& P, const ParticleBuffers& B, cudaStream_t st)
 {
     if (P.vacf_len <= 0) return cudaSuccess;
-    vacf<<<B.vacf_gx, kThreads, 0, st>>>(P, B.ctrl, B.vel, B.vorig, B.vpartial, B.csum, B.ccnt, B.norig, B.vdone);
+    if (P.n_os <= 4)
+        vacf<4><<<B.vacf_gx, kThreads, 0, st>>>(P, B.ctrl, B.vel, B.vorig, B.vpartial, B.csum, B.ccnt, B.norig, B.vdone);
+    else if (P.n_os <= 8)
+        vacf<8><<<B.vacf_gx, kThreads, 0, st>>>(P, B.ctrl, B.vel, B.vorig, B.vpartial, B.csum, B.ccnt, B.norig, B.vdone);
+    else if (P.n_os <= 16)
+        vacf<16><<<B.vacf_gx, kThreads, 0, st>>>(P, B.ctrl, B.vel, B.vorig, B.vpartial, B.csum, B.ccnt, B.norig, B.vdone);
+    else if (P.n_os <= kVacfMaxOrigins)
+        vacf<32><<<B.vacf_gx, kThreads, 0, st>>>(P, B.ctrl, B.vel, B.vorig, B.vpartial, B.csum, B.ccnt, B.norig, B.vdone);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

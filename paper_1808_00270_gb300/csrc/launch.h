@@ -74,14 +74,17 @@ struct PrepArgs {
     int* status;        // 0 or -3
     float* coef;        // [1+Q+Qs][m_max] discrete weights for the convolution
     float* g0;          // [Q+Qs] discrete m = 0 weights
-    float* Acp;         // [4][la] shifted zero-padded copies of A for the FIR
+    float* Acp;         // [la] FP32 filter taps A_{sigma-H}, zero padded
     int la;
 };
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t st);
 int fir_copy_len(int T, int H);
+// Padded length of the FP32 tap array (2H + 1 rounded up to 16).
+int fir_taps_len(int H);
 
+// int2ext maps the internal index to the caller's index, which keys the noise.
 cudaError_t launch_noise_block(const StepParams& P, Ctrl* ctrl, float* W, const float* Acp, int la,
-                               float* frblock, unsigned long long seed, int num_sms, cudaStream_t st);
+                               float* frblock, unsigned long long seed, const int* int2ext, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out, long long n,
                           cudaStream_t st);
 cudaError_t launch_gauss3(uint32_t k0, uint32_t k1, const uint32_t* particle, const long long* time,

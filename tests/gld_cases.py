@@ -29,8 +29,8 @@ def make_gpu(w: inputs.Workload, pos=None, vel=None, pair=True, **over):
     from paper_1808_00270_gb300 import GLD
     if pos is None:
         pos, vel = inputs.initial_state(w)
-    gkw = {k: over.pop(k) for k in list(over) if k in ("hist_dtype", "kahan", "noise_block",
-                                                        "use_graphs", "psd_clamp", "torch_allocator")}
+    gkw = {k: over.pop(k) for k in list(over) if k in ("hist_dtype", "kahan", "noise_block", "use_graphs",
+                                                        "psd_clamp", "torch_allocator", "order", "skin")}
     sys_ = GLD(pos=pos, vel=vel, **common_kwargs(w, **over), **gkw)
     ks, g, f, dr = kernels(w)
     if pair:

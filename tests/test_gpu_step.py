@@ -47,6 +47,21 @@ def test_one_step_forces(wname, warm):
     assert rel_l2(v, ref.get(oracle.VEL)) < 1e-5
 
 
+def test_long_memory_one_step():
+    """m_max = 1000: the noise filter runs over several tap chunks and the
+    convolution over 999 slots; one step against the oracle at 1e-5."""
+    from paper_1808_00270_gb300 import ARR_FD, ARR_FR, inputs
+    w = inputs.Workload("gld_n500_m1000", n=500, box=inputs.box_for_density(500, 0.1), m_max=1000, dt=0.005,
+                        r_c=2.0, tau_s=0.5, tau_p=0.3, steps=1, tail=True)
+    gpu = make_gpu(w)
+    gpu.step(1100)
+    ref = oracle_from_gpu(w, gpu)
+    gpu.step(1)
+    ref.step(1)
+    assert rel_l2(gpu.get(ARR_FD), ref.get(oracle.FD)) < 1e-5
+    assert rel_l2(gpu.get(ARR_FR), ref.get(oracle.FR)) < 1e-5
+
+
 @pytest.mark.parametrize("wname", ["gld_n64_m32", "gld_n4096_m200"])
 def test_trajectory_100_steps(wname):
     """Independent integrations from the same initial state and noise stream:
@@ -83,15 +98,16 @@ def test_graph_and_eager_paths_identical():
 
 
 def test_checkpoint_resume_is_bit_identical():
-    """State saved through the array API and loaded into a fresh context
-    continues exactly as the uninterrupted run (noise is counter-based)."""
+    """State saved through the array API (with the internal order) and loaded
+    into a fresh context created from the snapshot continues exactly as the
+    uninterrupted run (noise is counter-based)."""
     from paper_1808_00270_gb300 import ARR_DISP, ARR_FC, ARR_HIST, ARR_POS, ARR_VEL
     w = _w("gld_n4096_m200")
     a = make_gpu(w)
     a.step(77)
     snap = {k: a.get(k) for k in (ARR_POS, ARR_VEL, ARR_FC, ARR_HIST, ARR_DISP)}
     step = a.step_index
-    b = make_gpu(w)
+    b = make_gpu(w, pos=snap[ARR_POS], vel=snap[ARR_VEL], order=a.order())
     b.set_step(step)
     b.set(ARR_POS, snap[ARR_POS])
     b.set(ARR_VEL, snap[ARR_VEL])
@@ -103,6 +119,22 @@ def test_checkpoint_resume_is_bit_identical():
     pa, va = a.get_state()
     pb, vb = b.get_state()
     assert np.array_equal(pa, pb) and np.array_equal(va, vb)
+
+
+def test_any_internal_order_matches_oracle():
+    """The internal storage order is invisible: a random order gives the same
+    one-step forces (to rounding) in the caller's order."""
+    from paper_1808_00270_gb300 import ARR_FD, ARR_FR
+    w = _w("gld_n4096_m200")
+    perm = np.random.default_rng(5).permutation(w.n).astype(np.int32)
+    gpu = make_gpu(w, order=perm)
+    assert np.array_equal(gpu.order(), perm)
+    gpu.step(70)
+    ref = oracle_from_gpu(w, gpu)
+    gpu.step(1)
+    ref.step(1)
+    assert rel_l2(gpu.get(ARR_FD), ref.get(oracle.FD)) < 1e-5
+    assert rel_l2(gpu.get(ARR_FR), ref.get(oracle.FR)) < 1e-5
 
 
 def test_edge_cases():
