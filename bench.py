@@ -228,6 +228,7 @@ def main():
                 "avg_launch_ms": avg_s * 1e3,
                 "kernel_share": {k: v[0] / total_ms for k, v in prof.items() if total_ms > 0}}
 
+    diag = sim.diag()
     e2e = None
     if not args.no_e2e:
         torch.cuda.synchronize()
@@ -257,7 +258,7 @@ def main():
                           "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True,
                           "scaling": "weak", "vs_baseline": None, "dtype": "bf16-history" if args.hist == "bf16" else "f32",
                           "data": "synthetic", "config": cfg, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                          "clocks": clk, "gpu_launches": launches, "profile": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items()}}))
+                          "clocks": clk, "gpu_launches": launches, "diag": diag, "profile": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items()}}))
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0

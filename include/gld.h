@@ -175,6 +175,12 @@ gld_status gld_set_array(gld_ctx* ctx, int32_t which, const double* in);
  * the particle stored at position k; pass it as gld_params.order. */
 gld_status gld_get_order(gld_ctx* ctx, int32_t* int2ext);
 
+/* Diagnostics, out[count] (count <= 4 filled): {graph form of gld_step (0: not
+ * captured yet, 1: rebuild kernels gated on the device, 2: rebuild in a
+ * conditional graph node), neighbour-list builds so far, list capacity per
+ * particle, cells per box edge}.  Synchronizes. */
+gld_status gld_get_diag(gld_ctx* ctx, int64_t* out, int32_t count);
+
 /* Step counter n (the time index of R_n) and its setter (n >= 0, else
  * GLD_E_INVAL); setting it invalidates the noise window, which is rebuilt
  * from the counters. */

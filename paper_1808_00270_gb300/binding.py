@@ -72,6 +72,7 @@ def lib():
             "gld_get_coefs": (i32, [vp, vp, vp, vp, vp]),
             "gld_get_pairs": (i32, [vp, vp, i64, C.POINTER(i64)]),
             "gld_get_order": (i32, [vp, vp]),
+            "gld_get_diag": (i32, [vp, vp, i32]),
             "gld_profile_steps": (i32, [vp, i64, vp, vp]),
             "gld_last_error": (C.c_char_p, [vp]),
             "gld_destroy": (i32, [vp]),
@@ -92,7 +93,7 @@ def exported_symbols() -> list[str]:
     """Names of the C entry points the binding expects the library to export."""
     return ["gld_params_default", "gld_create", "gld_set_kernels", "gld_step", "gld_sync", "gld_vacf",
             "gld_get_state", "gld_get_array", "gld_set_array", "gld_get_step", "gld_set_step",
-            "gld_get_coefs", "gld_get_pairs", "gld_get_order", "gld_profile_steps", "gld_last_error", "gld_destroy", "gld_philox_dev",
+            "gld_get_coefs", "gld_get_pairs", "gld_get_order", "gld_get_diag", "gld_profile_steps", "gld_last_error", "gld_destroy", "gld_philox_dev",
             "gld_gauss3_dev", "gld_hist_conv_dev", "gld_pairs_noalloc"]
 
 
@@ -249,6 +250,11 @@ class GLD:
 
     def set_step(self, step: int) -> None:
         self._check(lib().gld_set_step(self._h, int(step)))
+
+    def diag(self) -> dict:
+        out = np.zeros(4, dtype=np.int64)
+        self._check(lib().gld_get_diag(self._h, _ptr(out), 4))
+        return dict(graph_mode=int(out[0]), rebuilds=int(out[1]), maxnb=int(out[2]), cells_per_edge=int(out[3]))
 
     def order(self) -> np.ndarray:
         """Internal storage order: entry k is the caller's index stored at k."""

@@ -28,6 +28,7 @@ struct gld_ctx {
     int device = 0, num_sms = 0;
     cudaStream_t st = nullptr;   // the caller's stream
     cudaStream_t cap = nullptr;  // private stream used only to capture graphs
+    cudaStream_t cap2 = nullptr; // fills the bodies of conditional graph nodes
     std::vector<void*> allocs;
     ParticleBuffers B{};
     float* W = nullptr;
@@ -45,6 +46,7 @@ struct gld_ctx {
     double a = 1.0, b = 1.0, spec_min = 0.0, clamped = 0.0;
     cudaGraphExec_t gexec = nullptr;
     bool graph_failed = false;
+    int graph_mode = 0;  // 0 none, 1 gated rebuild kernels, 2 conditional rebuild node
     std::string msg;
     gld_status latched = GLD_OK;
     std::vector<int> int2ext;  // caller's index of the particle stored at k
@@ -233,15 +235,55 @@ cudaError_t launch_one_step(gld_ctx* c, cudaStream_t s)
     return launch_vacf(c->P, c->B, s);
 }
 
-bool capture_graph(gld_ctx* c)
+// One step captured with the rebuild kernels in the body of a conditional
+// (IF) node whose condition a one-thread kernel sets from ctrl->rebuild, so
+// steps without a rebuild launch none of them.
+cudaError_t capture_step_conditional(gld_ctx* c, cudaStream_t s)
 {
-    if (c->gexec) return true;
-    if (c->graph_failed) return false;
+    cudaError_t e = launch_hist_conv(c->B.ring, c->P.hist_bf16, c->P.n_pad, c->P.m_max, c->B.ctrl, 0, c->coef,
+                                     c->P.nacc, c->B.conv, c->prm.kahan, s);
+    if (e == cudaSuccess) e = launch_pair_force_integrate(c->P, c->B, s);
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd);
+    cudaGraphConditionalHandle h{};
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) e = launch_rebuild_decide(h, c->B.ctrl, s);
+    if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd);
+    cudaGraphNodeParams np{};
+    cudaGraphNode_t node = nullptr;
+    if (e == cudaSuccess) {
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeIf;
+        np.conditional.size = 1;
+        e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &np);
+    }
+    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess)
+        e = cudaStreamBeginCaptureToGraph(c->cap2, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        const cudaError_t eb = launch_rebuild(c->P, c->B, c->cap2);
+        cudaGraph_t body = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(c->cap2, &body);
+        e = eb != cudaSuccess ? eb : ee;
+    }
+    if (e == cudaSuccess) e = launch_cforce(c->P, c->B, 1, s);
+    if (e == cudaSuccess) e = launch_vacf(c->P, c->B, s);
+    return e;
+}
+
+bool capture_graph_mode(gld_ctx* c, bool conditional)
+{
     cudaGraph_t g = nullptr;
     bool ok = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
         cudaError_t e = launch_noise(c, c->cap);
-        for (int t = 0; t < c->P.T && e == cudaSuccess; ++t) e = launch_one_step(c, c->cap);
+        for (int t = 0; t < c->P.T && e == cudaSuccess; ++t)
+            e = conditional ? capture_step_conditional(c, c->cap) : launch_one_step(c, c->cap);
         const cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
         ok = e == cudaSuccess && e2 == cudaSuccess && g != nullptr;
     }
@@ -249,10 +291,26 @@ bool capture_graph(gld_ctx* c)
     if (g) cudaGraphDestroy(g);
     if (!ok) {
         c->gexec = nullptr;
-        c->graph_failed = true;
         cudaGetLastError();
     }
     return ok;
+}
+
+bool capture_graph(gld_ctx* c)
+{
+    if (c->gexec) return true;
+    if (c->graph_failed) return false;
+    // conditional rebuild first; the gated kernels are the fallback
+    if (capture_graph_mode(c, true)) {
+        c->graph_mode = 2;
+        return true;
+    }
+    if (capture_graph_mode(c, false)) {
+        c->graph_mode = 1;
+        return true;
+    }
+    c->graph_failed = true;
+    return false;
 }
 
 int clamp_block(int) { return kMaxNoiseBlock; }  // the filter produces 64-step blocks
@@ -292,7 +350,8 @@ gld_status gld_create(const gld_params* p, const double* pos, const double* vel,
     c->st = (cudaStream_t)p->stream;
     if (cudaGetDevice(&c->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking) != cudaSuccess) {
         delete c;
         return GLD_E_CUDA;
     }
@@ -358,6 +417,7 @@ gld_status gld_create(const gld_params* p, const double* pos, const double* vel,
             const int e = p->order[k];
             if (e < 0 || e >= p->n || seen[e]) {
                 cudaStreamDestroy(c->cap);
+                cudaStreamDestroy(c->cap2);
                 delete c;
                 return GLD_E_INVAL;
             }
@@ -710,6 +770,17 @@ gld_status gld_set_array(gld_ctx* c, int32_t which, const double* in)
     }
 }
 
+gld_status gld_get_diag(gld_ctx* c, int64_t* out, int32_t count)
+{
+    if (!c || !out || count < 0) return GLD_E_INVAL;
+    GLD_TRY(sync_and_check(c));
+    long long rebuilds = 0;
+    GLD_CUDA(c, cudaMemcpy(&rebuilds, &c->B.ctrl->rebuilds, sizeof(rebuilds), cudaMemcpyDeviceToHost));
+    const int64_t v[4] = {c->graph_mode, rebuilds, c->P.maxnb, c->P.nc};
+    for (int k = 0; k < count; ++k) out[k] = k < 4 ? v[k] : 0;
+    return GLD_OK;
+}
+
 gld_status gld_get_order(gld_ctx* c, int32_t* int2ext)
 {
     if (!c || !int2ext) return GLD_E_INVAL;
@@ -870,6 +941,7 @@ gld_status gld_destroy(gld_ctx* c)
         else cudaFree(p);
     }
     if (c->cap) cudaStreamDestroy(c->cap);
+    if (c->cap2) cudaStreamDestroy(c->cap2);
     delete c;
     return GLD_OK;
 }

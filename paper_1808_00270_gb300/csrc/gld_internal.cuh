@@ -33,6 +33,7 @@ struct Ctrl {
     unsigned done_fir;
     int rebuild;           // != 0: rebuild cells and neighbour lists after this step's move
     int pad_;
+    long long rebuilds;    // neighbour-list builds so far
 };
 
 // Everything a step kernel needs, passed by value.

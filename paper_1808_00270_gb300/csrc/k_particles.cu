@@ -261,6 +261,7 @@ __global__ void __launch_bounds__(kThreads)
 {
     if (ctrl->rebuild == 0) return;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0) ctrl->rebuilds += 1;
     if (k >= P.n) return;
     const float4 pi = pos_sorted[k];
     const int id = __float_as_int(pi.w);
@@ -481,6 +482,12 @@ __global__ void pair_list(const StepParams P, const float4* __restrict__ pos_sor
     });
 }
 
+// Sets the graph condition that guards the rebuild kernels.
+__global__ void rebuild_decide(cudaGraphConditionalHandle h, const Ctrl* __restrict__ ctrl)
+{
+    cudaGraphSetConditional(h, ctrl->rebuild != 0 ? 1u : 0u);
+}
+
 // A bounded idle wait of one thread (lets the host run ahead of the device
 // before a timed sequence of launches).
 __global__ void delay_kernel(unsigned long long ns)
@@ -494,6 +501,12 @@ __global__ void delay_kernel(unsigned long long ns)
 }
 
 }  // namespace
+
+cudaError_t launch_rebuild_decide(cudaGraphConditionalHandle h, const Ctrl* ctrl, cudaStream_t st)
+{
+    rebuild_decide<<<1, 1, 0, st>>>(h, ctrl);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_delay(unsigned long long ns, cudaStream_t st)
 {

@@ -48,6 +48,8 @@ cudaError_t launch_cell_build(const StepParams& P, const ParticleBuffers& B, con
                               cudaStream_t st);
 // Cell list and neighbour lists at R_{n+1} (pos_next), when ctrl->rebuild != 0.
 cudaError_t launch_rebuild(const StepParams& P, const ParticleBuffers& B, cudaStream_t st);
+// Inside a captured graph: sets conditional handle h to (ctrl->rebuild != 0).
+cudaError_t launch_rebuild_decide(cudaGraphConditionalHandle h, const Ctrl* ctrl, cudaStream_t st);
 // mode 0: F^C only (initialisation); mode 1: F^C_{n+1}, V_{n+1}, step += 1.
 // Both copy pos_next into pos and clear ctrl->rebuild.
 cudaError_t launch_cforce(const StepParams& P, const ParticleBuffers& B, int mode, cudaStream_t st);
