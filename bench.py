@@ -49,6 +49,41 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def init_replicas(world: int, local: int, backend: str):
+    """One process per GPU, each stepping an independent replica: the process
+    group only carries the barrier and the max of the timings (no data-path
+    collective)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if backend == "nccl":
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group(backend)
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(value: float, world: int, device: str = "cpu") -> float:
+    """The slowest rank's value (whole-job time is set by the last replica)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(n_per_rank: int, steps: int, world: int, ms_max: float) -> float:
+    """Whole-job particle-steps/s: all ranks' particles over the slowest time."""
+    return world * n_per_rank * steps / (ms_max / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
 
@@ -166,9 +201,7 @@ def main():
     import numpy as np
     import torch
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    init_replicas(world, local, "nccl")
     from paper_1808_00270_gb300 import GLD, build as gbuild
     gbuild.build()
 
@@ -190,24 +223,19 @@ def main():
     clocks = ClockSampler(gpu_index, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv"))
     time.sleep(0.5)
     stream = torch.cuda.current_stream()
-    if world > 1:
-        torch.distributed.barrier()
+    barrier(world)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     sim.step(K)
     ev1.record(stream)
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    barrier(world)
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
     sim.sync()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * w.n * K / (ms / 1e3)
+    ms = max_over_ranks(ms, world, "cuda")
+    value = replica_value(w.n, K, world, ms)
     blocks = (K + T - 1) // T
     launches = K * (7 if w.m_max > 0 else 6) + 2 * blocks
 
