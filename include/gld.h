@@ -222,6 +222,33 @@ gld_status gld_profile_steps(gld_ctx* ctx, int64_t nsteps, double* ms, int64_t* 
 const char* gld_last_error(const gld_ctx* ctx);
 gld_status gld_destroy(gld_ctx* ctx);
 
+/* ---- batches of independent systems -------------------------------------
+ * Many GLD systems of different sizes, densities and memory lengths stepped
+ * together: every kernel family runs as ONE launch over a tile list of
+ * (member, block) for all members, and a 64-step block of the whole batch is
+ * one captured CUDA graph.  Members remain ordinary contexts (their arrays,
+ * VACF and state are read through the gld_* calls above); a member must have
+ * its kernels set, use the batch's stream, sit at a 64-step boundary, and
+ * share the number of kernel terms, the history type and compensation with
+ * the other members.  Results of a member do not depend on the other members.
+ * The convolution's tile schedule is picked by timing four candidates on the
+ * current composition (256- or 128-column tiles, longest memory first, member
+ * order, or one block per member). */
+typedef struct gld_batch gld_batch;
+gld_status gld_batch_create(void* stream, gld_batch** out);
+gld_status gld_batch_add(gld_batch* batch, gld_ctx* member);
+gld_status gld_batch_remove(gld_batch* batch, gld_ctx* member);
+/* Steps every member by nsteps (a multiple of 64); returns without waiting. */
+gld_status gld_batch_step(gld_batch* batch, int64_t nsteps);
+/* Waits, then returns the first latched error of the members. */
+gld_status gld_batch_sync(gld_batch* batch);
+/* members, chosen convolution schedule (-1 before the first step), and the
+ * timed milliseconds of the four schedules; pointers may be NULL. */
+gld_status gld_batch_info(gld_batch* batch, int32_t* members, int32_t* schedule, double* schedule_ms);
+const char* gld_batch_last_error(const gld_batch* batch);
+/* Frees the batch; the members stay valid. */
+gld_status gld_batch_destroy(gld_batch* batch);
+
 /* ---- single kernels on caller-owned device memory ----------------------- */
 
 /* Philox4x32-10 (Salmon et al., SC'11) on n counters: ctr [n][4] uint32,

@@ -80,6 +80,14 @@ def lib():
             "gld_gauss3_dev": (i32, [u64, vp, vp, u32, vp, i64, vp]),
             "gld_hist_conv_dev": (i32, [vp, i32, i32, i32, i64, vp, i32, vp, i32, vp]),
             "gld_pairs_noalloc": (i32, [vp, i32, d, d, vp, i64, vp, vp]),
+            "gld_batch_create": (i32, [vp, C.POINTER(vp)]),
+            "gld_batch_add": (i32, [vp, vp]),
+            "gld_batch_remove": (i32, [vp, vp]),
+            "gld_batch_step": (i32, [vp, i64]),
+            "gld_batch_sync": (i32, [vp]),
+            "gld_batch_info": (i32, [vp, C.POINTER(i32), C.POINTER(i32), vp]),
+            "gld_batch_last_error": (C.c_char_p, [vp]),
+            "gld_batch_destroy": (i32, [vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -94,7 +102,9 @@ def exported_symbols() -> list[str]:
     return ["gld_params_default", "gld_create", "gld_set_kernels", "gld_step", "gld_sync", "gld_vacf",
             "gld_get_state", "gld_get_array", "gld_set_array", "gld_get_step", "gld_set_step",
             "gld_get_coefs", "gld_get_pairs", "gld_get_order", "gld_get_diag", "gld_profile_steps", "gld_last_error", "gld_destroy", "gld_philox_dev",
-            "gld_gauss3_dev", "gld_hist_conv_dev", "gld_pairs_noalloc"]
+            "gld_gauss3_dev", "gld_hist_conv_dev", "gld_pairs_noalloc", "gld_batch_create", "gld_batch_add",
+            "gld_batch_remove", "gld_batch_step", "gld_batch_sync", "gld_batch_info", "gld_batch_last_error",
+            "gld_batch_destroy"]
 
 
 def _ptr(a: np.ndarray):
@@ -291,6 +301,60 @@ def _dptr(t) -> int:
     if not t.is_cuda:
         raise ValueError("expected a CUDA tensor")
     return int(t.data_ptr())
+
+
+class Batch:
+    """Independent GLD systems stepped together (wraps a gld_batch): each kernel
+    family is one launch over all members, a 64-step block of the whole batch
+    is one CUDA graph.  Members stay ordinary GLD objects."""
+
+    def __init__(self, stream=None):
+        self.stream = _current_stream() if stream is None else int(stream)
+        h = C.c_void_p()
+        st = lib().gld_batch_create(C.c_void_p(self.stream), C.byref(h))
+        if st != OK:
+            raise GLDError(st, "gld_batch_create failed")
+        self._h = h
+        self.members = []
+
+    def _check(self, st: int):
+        if st != OK:
+            raise GLDError(st, lib().gld_batch_last_error(self._h).decode())
+
+    def add(self, g: "GLD"):
+        self._check(lib().gld_batch_add(self._h, g._h))
+        self.members.append(g)
+
+    def remove(self, g: "GLD"):
+        self._check(lib().gld_batch_remove(self._h, g._h))
+        self.members.remove(g)
+
+    def step(self, nsteps: int):
+        """Steps every member by nsteps (a multiple of 64) without waiting."""
+        self._check(lib().gld_batch_step(self._h, int(nsteps)))
+
+    def sync(self):
+        st = lib().gld_batch_sync(self._h)
+        if st != OK:
+            raise GLDError(st, lib().gld_batch_last_error(self._h).decode())
+
+    def info(self) -> dict:
+        m, sc = C.c_int32(), C.c_int32()
+        ms = np.zeros(4)
+        self._check(lib().gld_batch_info(self._h, C.byref(m), C.byref(sc), _ptr(ms)))
+        return {"members": m.value, "schedule": sc.value, "schedule_ms": ms.tolist()}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().gld_batch_destroy(self._h)
+            self._h = None
+        self.members = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def philox_dev(ctr, key, out, stream=None):

@@ -974,4 +974,316 @@ gld_status gld_hist_conv_dev(const void* ring, int32_t bf16, int32_t n_pad, int3
                : GLD_E_CUDA;
 }
 
+// ---- batches of independent systems ----------------------------------------
+
+struct gld_batch {
+    cudaStream_t st = nullptr, cap = nullptr;
+    std::vector<gld_ctx*> members;
+    SysDesc* d_desc = nullptr;
+    Tile* d_tiles = nullptr;
+    size_t desc_cap = 0, tiles_cap = 0;
+    BatchPlan plan{};
+    bool dirty = true;
+    int schedule = -1;  // chosen convolution schedule (autotuned), -1: not yet
+    double schedule_ms[4] = {0, 0, 0, 0};
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<SysDesc> snap;  // member descriptors the plan was built from
+    std::string msg;
+};
+
+namespace {
+
+gld_status bfail(gld_batch* b, gld_status s, const std::string& m)
+{
+    if (b) b->msg = m;
+    return s;
+}
+
+void batch_drop_graph(gld_batch* b)
+{
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+}
+
+// Convolution schedules: 0 tiles of 256 columns, longest memories first;
+// 1 tiles of 128 columns, longest first; 2 tiles of 256 in member order;
+// 3 one CTA of 256 per member (block-per-replica).
+void conv_tiles(const std::vector<gld_ctx*>& ms, int schedule, std::vector<Tile>& out, int* block)
+{
+    *block = schedule == 1 ? 128 : 256;
+    std::vector<int> idx(ms.size());
+    for (size_t k = 0; k < ms.size(); ++k) idx[k] = (int)k;
+    if (schedule == 0 || schedule == 1)
+        std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return ms[a]->P.H > ms[b]->P.H; });
+    for (int m : idx) {
+        const long long cols = 3LL * ms[m]->P.n_pad / (ms[m]->P.hist_bf16 ? 8 : 4);
+        const int nb = schedule == 3 ? 1 : (int)((cols + *block - 1) / *block);
+        for (int b = 0; b < nb; ++b) out.push_back(Tile{m, b, nb, 0});
+    }
+}
+
+gld_status batch_plan(gld_batch* b, int schedule)
+{
+    const auto& ms = b->members;
+    std::vector<SysDesc> desc(ms.size());
+    std::vector<Tile> pair, part, cell, vacf, conv, fir;
+    BatchPlan& P = b->plan;
+    P = BatchPlan{};
+    for (size_t m = 0; m < ms.size(); ++m) {
+        gld_ctx* c = ms[m];
+        SysDesc& d = desc[m];
+        d.P = c->P;
+        d.B = c->B;
+        d.coef = c->coef;
+        d.W = c->W;
+        d.taps = c->Acp;
+        d.ntaps = fir_taps_len(c->P.H);
+        d.k0 = (uint32_t)c->prm.seed;
+        d.k1 = (uint32_t)(c->prm.seed >> 32);
+        d.int2ext = c->d_int2ext;
+        d.nb_pair = (c->P.n + kBatchPairBlock - 1) / kBatchPairBlock;
+        d.nb_part = (c->P.n + kBatchPartBlock - 1) / kBatchPartBlock;
+        d.nb_cell = (c->B.ncells + kBatchCellChunk - 1) / kBatchCellChunk;
+        d.nb_vacf = c->P.vacf_len > 0 ? c->B.vacf_gx : 0;
+        d.nb_conv = 0;
+        d.nb_fir = (int)((3LL * c->P.n_pad + kBatchFirStreams - 1) / kBatchFirStreams);
+        for (int k = 0; k < d.nb_pair; ++k) pair.push_back(Tile{(int)m, k, d.nb_pair, 0});
+        for (int k = 0; k < d.nb_part; ++k) part.push_back(Tile{(int)m, k, d.nb_part, 0});
+        for (int k = 0; k < d.nb_cell; ++k) cell.push_back(Tile{(int)m, k, d.nb_cell, 0});
+        for (int k = 0; k < d.nb_vacf; ++k) vacf.push_back(Tile{(int)m, k, d.nb_vacf, 0});
+        for (int k = 0; k < d.nb_fir; ++k) fir.push_back(Tile{(int)m, k, d.nb_fir, 0});
+        P.max_H = std::max(P.max_H, c->P.H);
+        P.max_n = std::max(P.max_n, c->P.n);
+        P.max_ntaps = std::max(P.max_ntaps, d.ntaps);
+        P.vacf_no = std::max(P.vacf_no, c->P.n_os);
+    }
+    conv_tiles(ms, schedule < 0 ? 0 : schedule, conv, &P.conv_block);
+    if (!ms.empty()) {
+        P.nacc = ms[0]->P.nacc;
+        P.bf16 = ms[0]->P.hist_bf16;
+        P.kahan = ms[0]->prm.kahan;
+    }
+    std::vector<Tile> all;
+    auto append = [&](std::vector<Tile>& v, int* n) {
+        *n = (int)v.size();
+        const size_t off = all.size();
+        all.insert(all.end(), v.begin(), v.end());
+        return off;
+    };
+    const size_t o_pair = append(pair, &P.n_pair), o_part = append(part, &P.n_part), o_cell = append(cell, &P.n_cell),
+                 o_vacf = append(vacf, &P.n_vacf), o_conv = append(conv, &P.n_conv), o_fir = append(fir, &P.n_fir);
+    b->snap = desc;
+    if (desc.size() > b->desc_cap) {
+        if (b->d_desc) cudaFree(b->d_desc);
+        b->d_desc = nullptr;
+        b->desc_cap = std::max<size_t>(desc.size(), 2 * b->desc_cap);
+        if (cudaMalloc(&b->d_desc, sizeof(SysDesc) * b->desc_cap) != cudaSuccess)
+            return bfail(b, GLD_E_NOMEM, "batch descriptors");
+    }
+    if (all.size() > b->tiles_cap) {
+        if (b->d_tiles) cudaFree(b->d_tiles);
+        b->d_tiles = nullptr;
+        b->tiles_cap = std::max<size_t>(all.size(), 2 * b->tiles_cap);
+        if (cudaMalloc(&b->d_tiles, sizeof(Tile) * b->tiles_cap) != cudaSuccess)
+            return bfail(b, GLD_E_NOMEM, "batch tiles");
+    }
+    if (!desc.empty() &&
+        (cudaMemcpyAsync(b->d_desc, desc.data(), sizeof(SysDesc) * desc.size(), cudaMemcpyHostToDevice, b->st) !=
+             cudaSuccess ||
+         cudaMemcpyAsync(b->d_tiles, all.data(), sizeof(Tile) * all.size(), cudaMemcpyHostToDevice, b->st) !=
+             cudaSuccess ||
+         cudaStreamSynchronize(b->st) != cudaSuccess))
+        return bfail(b, GLD_E_CUDA, "batch plan upload");
+    P.desc = b->d_desc;
+    P.pair = b->d_tiles + o_pair;
+    P.part = b->d_tiles + o_part;
+    P.cell = b->d_tiles + o_cell;
+    P.vacf = b->d_tiles + o_vacf;
+    P.conv = b->d_tiles + o_conv;
+    P.fir = b->d_tiles + o_fir;
+    return GLD_OK;
+}
+
+cudaError_t batch_launch_block(gld_batch* b, cudaStream_t s)
+{
+    cudaError_t e = launch_batch_noise(b->plan, s);
+    for (int t = 0; t < kMaxNoiseBlock && e == cudaSuccess; ++t) {
+        e = launch_batch_conv(b->plan, s);
+        if (e == cudaSuccess) e = launch_batch_particles(b->plan, s);
+    }
+    return e;
+}
+
+// Times each convolution schedule on the current composition (the
+// convolution only reads the rings and rewrites the projections, so repeating
+// it leaves the state unchanged) and keeps the fastest.
+gld_status batch_autotune(gld_batch* b)
+{
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return bfail(b, GLD_E_CUDA, "autotune events");
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int sc = 0; sc < 4; ++sc) {
+        GLD_TRY(batch_plan(b, sc));
+        float ms = 0.f;
+        bool ok = launch_batch_conv(b->plan, b->st) == cudaSuccess && cudaEventRecord(e0, b->st) == cudaSuccess;
+        for (int r = 0; r < 5 && ok; ++r) ok = launch_batch_conv(b->plan, b->st) == cudaSuccess;
+        ok = ok && cudaEventRecord(e1, b->st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+             cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+        if (!ok) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return bfail(b, GLD_E_CUDA, "autotune launch");
+        }
+        b->schedule_ms[sc] = ms / 5.0;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = sc;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->schedule = best;
+    return batch_plan(b, best);
+}
+
+gld_status batch_prepare(gld_batch* b)
+{
+    if (!b->dirty) return GLD_OK;
+    batch_drop_graph(b);
+    if (b->schedule < 0) GLD_TRY(batch_autotune(b));
+    else GLD_TRY(batch_plan(b, b->schedule));
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        const cudaError_t e = batch_launch_block(b, b->cap);
+        const cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
+        ok = e == cudaSuccess && e2 == cudaSuccess && g;
+    }
+    if (ok) ok = cudaGraphInstantiate(&b->gexec, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+        cudaGetLastError();
+        b->gexec = nullptr;  // eager launches below
+    }
+    b->dirty = false;
+    return GLD_OK;
+}
+
+}  // namespace
+
+gld_status gld_batch_create(void* stream, gld_batch** out)
+{
+    if (!out) return GLD_E_INVAL;
+    gld_batch* b = new gld_batch();
+    b->st = (cudaStream_t)stream;
+    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        delete b;
+        return GLD_E_CUDA;
+    }
+    *out = b;
+    return GLD_OK;
+}
+
+gld_status gld_batch_add(gld_batch* b, gld_ctx* c)
+{
+    if (!b || !c) return GLD_E_INVAL;
+    if (!c->have_kernels) return bfail(b, GLD_E_STATE, "gld_batch_add: the member has no kernels set");
+    if (c->st != b->st) return bfail(b, GLD_E_INVAL, "gld_batch_add: the member must use the batch's stream");
+    if (c->P.T != kMaxNoiseBlock) return bfail(b, GLD_E_INVAL, "gld_batch_add: the member's noise block must be 64");
+    if (c->noise_valid && c->host_step != c->noise_end)
+        return bfail(b, GLD_E_STATE, "gld_batch_add: the member is inside a noise block (step a multiple of 64)");
+    for (gld_ctx* m : b->members)
+        if (m == c) return bfail(b, GLD_E_INVAL, "gld_batch_add: already a member");
+    if (!b->members.empty()) {
+        const gld_ctx* f = b->members[0];
+        if (f->P.nacc != c->P.nacc || f->P.hist_bf16 != c->P.hist_bf16 || f->prm.kahan != c->prm.kahan)
+            return bfail(b, GLD_E_INVAL, "gld_batch_add: members must share kernel terms, history type and Kahan");
+    }
+    b->members.push_back(c);
+    b->dirty = true;
+    b->schedule = -1;
+    return GLD_OK;
+}
+
+gld_status gld_batch_remove(gld_batch* b, gld_ctx* c)
+{
+    if (!b || !c) return GLD_E_INVAL;
+    for (size_t k = 0; k < b->members.size(); ++k)
+        if (b->members[k] == c) {
+            b->members.erase(b->members.begin() + (long)k);
+            b->dirty = true;
+            b->schedule = -1;
+            return GLD_OK;
+        }
+    return bfail(b, GLD_E_INVAL, "gld_batch_remove: not a member");
+}
+
+gld_status gld_batch_step(gld_batch* b, int64_t nsteps)
+{
+    if (!b || nsteps < 0) return GLD_E_INVAL;
+    if (nsteps % kMaxNoiseBlock) return bfail(b, GLD_E_INVAL, "gld_batch_step: steps must be a multiple of 64");
+    if (b->members.empty() || nsteps == 0) return GLD_OK;
+    for (gld_ctx* c : b->members) {
+        if (c->latched != GLD_OK) return bfail(b, c->latched, "gld_batch_step: a member has a latched error");
+        if (c->noise_valid && c->host_step != c->noise_end)
+            return bfail(b, GLD_E_STATE, "gld_batch_step: a member left its noise-block boundary");
+    }
+    for (size_t m = 0; m < b->members.size() && !b->dirty; ++m)  // kernels reset since the plan
+        if (m >= b->snap.size() || std::memcmp(&b->snap[m].P, &b->members[m]->P, sizeof(StepParams)) != 0 ||
+            std::memcmp(&b->snap[m].B, &b->members[m]->B, sizeof(ParticleBuffers)) != 0 ||
+            b->snap[m].coef != b->members[m]->coef)
+            b->dirty = true;
+    GLD_TRY(batch_prepare(b));
+    for (int64_t k = 0; k < nsteps; k += kMaxNoiseBlock) {
+        const cudaError_t e = b->gexec ? cudaGraphLaunch(b->gexec, b->st) : batch_launch_block(b, b->st);
+        if (e != cudaSuccess) return bfail(b, GLD_E_CUDA, std::string("gld_batch_step: ") + cudaGetErrorString(e));
+        for (gld_ctx* c : b->members) {
+            c->block_start = c->host_step;
+            c->host_step += kMaxNoiseBlock;
+            c->noise_end = c->host_step;
+            c->noise_valid = true;
+            c->last_fr_row = kMaxNoiseBlock - 1;
+        }
+    }
+    return GLD_OK;
+}
+
+gld_status gld_batch_sync(gld_batch* b)
+{
+    if (!b) return GLD_E_INVAL;
+    if (cudaStreamSynchronize(b->st) != cudaSuccess) return bfail(b, GLD_E_CUDA, "gld_batch_sync");
+    gld_status s = GLD_OK;
+    for (gld_ctx* c : b->members) {
+        const gld_status t = sync_and_check(c);
+        if (s == GLD_OK) s = t;
+    }
+    return s;
+}
+
+gld_status gld_batch_info(gld_batch* b, int32_t* members, int32_t* schedule, double* schedule_ms)
+{
+    if (!b) return GLD_E_INVAL;
+    if (members) *members = (int32_t)b->members.size();
+    if (schedule) *schedule = b->schedule;
+    if (schedule_ms)
+        for (int k = 0; k < 4; ++k) schedule_ms[k] = b->schedule_ms[k];
+    return GLD_OK;
+}
+
+const char* gld_batch_last_error(const gld_batch* b) { return b ? b->msg.c_str() : "null batch"; }
+
+gld_status gld_batch_destroy(gld_batch* b)
+{
+    if (!b) return GLD_E_INVAL;
+    cudaStreamSynchronize(b->st);
+    batch_drop_graph(b);
+    if (b->d_desc) cudaFree(b->d_desc);
+    if (b->d_tiles) cudaFree(b->d_tiles);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+    return GLD_OK;
+}
+
 }  // extern "C"

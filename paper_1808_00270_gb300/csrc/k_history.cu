@@ -398,7 +398,104 @@ cudaError_t dispatch(int nacc, const void* ring, int bf16, int n_pad, int M, con
     }
 }
 
+// Batch convolution: tile (member, 256-column block); the member's
+// coefficients are staged for its own step and memory length.
+template <int NACC, bool KAHAN, bool BF16>
+__global__ void __launch_bounds__(kBatchConvCols)
+    b_conv(const SysDesc* __restrict__ D, const Tile* __restrict__ tiles)
+{
+    using V = typename Col<BF16>::V;
+    constexpr int VW = Col<BF16>::W;
+    extern __shared__ float cs[];
+    const Tile t = tiles[blockIdx.x];
+    const SysDesc& d = D[t.m];
+    const int H = d.P.H, M = d.P.m_max;
+    stage_coefs<NACC>(cs, d.coef, M, H, d.B.ctrl->step);
+    const long long cols = 3LL * d.P.n_pad / VW;
+    // columns b*bd + tid, then strided by the member's tiles in this schedule
+    for (long long q = (long long)t.b * blockDim.x + threadIdx.x; q < cols; q += (long long)t.nb * blockDim.x) {
+    const V* p = (const V*)d.B.ring + q;
+    float acc[NACC][VW];
+    float cmp[KAHAN ? NACC : 1][VW];
+#pragma unroll
+    for (int a = 0; a < NACC; ++a)
+#pragma unroll
+        for (int e = 0; e < VW; ++e) acc[a][e] = 0.f;
+#pragma unroll
+    for (int a = 0; a < (KAHAN ? NACC : 1); ++a)
+#pragma unroll
+        for (int e = 0; e < VW; ++e) cmp[a][e] = 0.f;
+    int s = 0;
+    for (; s + kUnroll <= H; s += kUnroll) {
+        V v[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) v[u] = __ldcs(p + (long long)(s + u) * cols);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            float x[VW];
+            unpack<BF16>(v[u], x);
+#pragma unroll
+            for (int a = 0; a < NACC; ++a) {
+                const float cf = cs[(s + u) * NACC + a];
+#pragma unroll
+                for (int e = 0; e < VW; ++e) acc1<KAHAN>(acc[a][e], cmp[KAHAN ? a : 0][e], cf, x[e]);
+            }
+        }
+    }
+    for (; s < H; ++s) {
+        float x[VW];
+        unpack<BF16>(__ldcs(p + (long long)s * cols), x);
+#pragma unroll
+        for (int a = 0; a < NACC; ++a) {
+            const float cf = cs[s * NACC + a];
+#pragma unroll
+            for (int e = 0; e < VW; ++e) acc1<KAHAN>(acc[a][e], cmp[KAHAN ? a : 0][e], cf, x[e]);
+        }
+    }
+    float4* o = (float4*)d.B.conv;
+    const long long cols4 = cols * (VW / 4);
+#pragma unroll
+    for (int a = 0; a < NACC; ++a)
+#pragma unroll
+        for (int h = 0; h < VW / 4; ++h) {
+            float r[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                r[e] = KAHAN ? acc[a][4 * h + e] - cmp[KAHAN ? a : 0][4 * h + e] : acc[a][4 * h + e];
+            o[a * cols4 + q * (VW / 4) + h] = make_float4(r[0], r[1], r[2], r[3]);
+        }
+    }
+}
+
+template <int NACC, bool KAHAN>
+cudaError_t launch_b_conv_t(const BatchPlan& bp, cudaStream_t st)
+{
+    const size_t smem = sizeof(float) * (size_t)bp.max_H * NACC;
+    auto k = bp.bf16 ? b_conv<NACC, KAHAN, true> : b_conv<NACC, KAHAN, false>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<bp.n_conv, bp.conv_block, smem, st>>>(bp.desc, bp.conv);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_batch_conv(const BatchPlan& bp, cudaStream_t st)
+{
+    if (!bp.n_conv) return cudaSuccess;
+    const bool k = bp.kahan != 0;
+    switch (bp.nacc) {
+    case 1: return k ? launch_b_conv_t<1, true>(bp, st) : launch_b_conv_t<1, false>(bp, st);
+    case 2: return k ? launch_b_conv_t<2, true>(bp, st) : launch_b_conv_t<2, false>(bp, st);
+    case 3: return k ? launch_b_conv_t<3, true>(bp, st) : launch_b_conv_t<3, false>(bp, st);
+    case 4: return k ? launch_b_conv_t<4, true>(bp, st) : launch_b_conv_t<4, false>(bp, st);
+    case 5: return k ? launch_b_conv_t<5, true>(bp, st) : launch_b_conv_t<5, false>(bp, st);
+    case 6: return k ? launch_b_conv_t<6, true>(bp, st) : launch_b_conv_t<6, false>(bp, st);
+    case 7: return k ? launch_b_conv_t<7, true>(bp, st) : launch_b_conv_t<7, false>(bp, st);
+    case 8: return k ? launch_b_conv_t<8, true>(bp, st) : launch_b_conv_t<8, false>(bp, st);
+    case 9: return k ? launch_b_conv_t<9, true>(bp, st) : launch_b_conv_t<9, false>(bp, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_hist_conv(const void* ring, int bf16, int n_pad, int m_max, const Ctrl* ctrl,
                              long long step, const float* coef, int nacc, float* out, int kahan,

@@ -117,9 +117,8 @@ __global__ void __launch_bounds__(kPrepThreads) prep(const PrepArgs a)
 
 constexpr int kGenThreads = 256;
 
-__global__ void __launch_bounds__(kGenThreads)
-    wgen(const StepParams P, const Ctrl* __restrict__ ctrl, float* __restrict__ W, uint32_t k0, uint32_t k1,
-         const int* __restrict__ int2ext)
+__device__ __forceinline__ void wgen_body(const StepParams& P, const Ctrl* __restrict__ ctrl, float* __restrict__ W,
+                                          uint32_t k0, uint32_t k1, const int* __restrict__ int2ext, int blk)
 {
     const long long n0 = ctrl->step;
     const long long need_lo = n0 - P.H, hi = n0 + P.T + P.H;
@@ -128,7 +127,7 @@ __global__ void __launch_bounds__(kGenThreads)
     const long long lo = valid ? wh : need_lo;
     const long long count = hi - lo;
     const long long np = P.n_pad;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blk * blockDim.x + threadIdx.x;
     if (i >= P.n) return;
     for (long long kk = blockIdx.y; kk < count; kk += gridDim.y) {
         const long long time = lo + kk;
@@ -142,6 +141,13 @@ __global__ void __launch_bounds__(kGenThreads)
     }
 }
 
+__global__ void __launch_bounds__(kGenThreads)
+    wgen(const StepParams P, const Ctrl* __restrict__ ctrl, float* __restrict__ W, uint32_t k0, uint32_t k1,
+         const int* __restrict__ int2ext)
+{
+    wgen_body(P, ctrl, W, k0, k1, int2ext, blockIdx.x);
+}
+
 constexpr int kFirThreads = 128;  // 4 warps x 16 outputs = one 64-step block
 constexpr int kFirR = 16;         // outputs per thread (register window)
 constexpr int kFirStreams = 32;   // streams per CTA (one per lane)
@@ -152,16 +158,16 @@ constexpr int kFirStreams = 32;   // streams per CTA (one per lane)
 // memory; warp w produces outputs 16 w .. 16 w + 15 with a 16-deep window of
 // W rows in registers that slides by one row per tap, so each tap costs one
 // shared load of W, one broadcast tap load and 16 FMAs.
-__global__ void __launch_bounds__(kFirThreads)
-    fir(const StepParams P, Ctrl* __restrict__ ctrl, const float* __restrict__ W, const float* __restrict__ taps,
-        int ntaps, int chunk, float* __restrict__ out)
+__device__ __forceinline__ void fir_body(const StepParams& P, Ctrl* __restrict__ ctrl, const float* __restrict__ W,
+                                         const float* __restrict__ taps, int ntaps, int chunk, float* __restrict__ out,
+                                         int blk, int nblk)
 {
     extern __shared__ float4 sm4[];
     float* At = (float*)sm4;               // [chunk]
     float* Wt = At + chunk;                // [chunk + 64][32]
     const long long n0 = ctrl->step;
     const long long np = P.n_pad, nstreams = 3 * np;
-    const long long j = (long long)blockIdx.x * kFirStreams + (threadIdx.x & 31);
+    const long long j = (long long)blk * kFirStreams + (threadIdx.x & 31);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     (void)lane;
     const int nk = 64 + 2 * P.H;           // rows holding real W
@@ -176,7 +182,7 @@ __global__ void __launch_bounds__(kFirThreads)
         // W rows of this chunk: 8 threads copy one 128-byte row as 16-byte
         // asynchronous copies, all in flight together; rows past the window
         // are zero-filled.
-        const long long jb = (long long)blockIdx.x * kFirStreams;
+        const long long jb = (long long)blk * kFirStreams;
         for (int idx = threadIdx.x; idx < (cn + 64) * 8; idx += blockDim.x) {
             const int k = idx >> 3, part = idx & 7;
             const int row = c0 + k;
@@ -211,7 +217,7 @@ __global__ void __launch_bounds__(kFirThreads)
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        if (atomicAdd(&ctrl->done_fir, 1u) == gridDim.x - 1) {
+        if (atomicAdd(&ctrl->done_fir, 1u) == nblk - 1) {
             ctrl->noise_n0 = n0;
             ctrl->w_lo = n0 - P.H;
             ctrl->w_hi = n0 + P.T + P.H;
@@ -219,6 +225,28 @@ __global__ void __launch_bounds__(kFirThreads)
             __threadfence();
         }
     }
+}
+
+__global__ void __launch_bounds__(kFirThreads)
+    fir(const StepParams P, Ctrl* __restrict__ ctrl, const float* __restrict__ W, const float* __restrict__ taps,
+        int ntaps, int chunk, float* __restrict__ out)
+{
+    fir_body(P, ctrl, W, taps, ntaps, chunk, out, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(kGenThreads) b_wgen(const SysDesc* __restrict__ D, const Tile* __restrict__ tiles)
+{
+    const Tile t = tiles[blockIdx.x];
+    const SysDesc& d = D[t.m];
+    wgen_body(d.P, d.B.ctrl, d.W, d.k0, d.k1, d.int2ext, t.b);
+}
+
+__global__ void __launch_bounds__(kFirThreads)
+    b_fir(const SysDesc* __restrict__ D, const Tile* __restrict__ tiles, int chunk)
+{
+    const Tile t = tiles[blockIdx.x];
+    const SysDesc& d = D[t.m];
+    fir_body(d.P, d.B.ctrl, d.W, d.taps, d.ntaps, chunk, d.B.frblock, t.b, d.nb_fir);
 }
 
 __global__ void philox_k(const uint4* __restrict__ ctr, uint32_t k0, uint32_t k1, uint4* __restrict__ out, long long n)
@@ -271,6 +299,21 @@ cudaError_t launch_noise_block(const StepParams& P, Ctrl* ctrl, float* W, const 
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)((streams + kFirStreams - 1) / kFirStreams);
     fir<<<grid, kFirThreads, smem, st>>>(P, ctrl, W, Acp, ntaps, chunk, frblock);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_noise(const BatchPlan& bp, cudaStream_t st)
+{
+    static_assert(kGenThreads == kBatchPartBlock, "white-noise tiles use the particle tiles");
+    static_assert(kFirStreams == kBatchFirStreams, "filter tiles");
+    if (!bp.n_part || !bp.n_fir) return cudaSuccess;
+    dim3 g((unsigned)bp.n_part, 64u);
+    b_wgen<<<g, kGenThreads, 0, st>>>(bp.desc, bp.part);
+    const int chunk = std::min(bp.max_ntaps, 768);
+    const size_t smem = sizeof(float) * ((size_t)chunk + (size_t)(64 + chunk) * kFirStreams);
+    cudaError_t e = cudaFuncSetAttribute(b_fir, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    b_fir<<<bp.n_fir, kFirThreads, smem, st>>>(bp.desc, bp.fir, chunk);
     return cudaGetLastError();
 }
 

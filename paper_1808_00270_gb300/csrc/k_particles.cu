@@ -30,26 +30,26 @@ namespace gld {
 
 namespace {
 
-constexpr int kPairThreads = 128;
-constexpr int kCellThreads = 512;
-constexpr int kThreads = 256;
+constexpr int kPairThreads = kBatchPairBlock;
+constexpr int kCellThreads = kBatchCellChunk;
+constexpr int kThreads = kBatchPartBlock;
+static_assert(kBatchVacfBlock == kThreads, "vacf blocks share the particle block size");
 
 __device__ __forceinline__ float dot3(float ax, float ay, float az, float bx, float by, float bz)
 {
     return fmaf(ax, bx, fmaf(ay, by, az * bz));
 }
 
-__global__ void __launch_bounds__(kPairThreads)
-    pair_force_integrate(const StepParams P, Ctrl* __restrict__ ctrl, const float4* __restrict__ pos,
+__device__ __forceinline__ void pair_force_integrate_body(const StepParams& P, Ctrl* __restrict__ ctrl, const float4* __restrict__ pos,
                          const int* __restrict__ perm, const int* __restrict__ nbr, const int* __restrict__ nbr_cnt,
                          const float4* __restrict__ vel, const float4* __restrict__ fc, const float* __restrict__ conv,
                          const float* __restrict__ frblock, const float* __restrict__ ftab,
                          const float* __restrict__ g0, void* __restrict__ ring, float4* __restrict__ pos_next,
                          float4* __restrict__ vhalf, float4* __restrict__ fd_out, float4* __restrict__ disp,
-                         const float4* __restrict__ disp_build)
+                         const float4* __restrict__ disp_build, int blk, int nblk)
 {
     unsigned* err = &ctrl->err;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blk * blockDim.x + threadIdx.x;
     if (k >= P.n) return;
     const long long n = ctrl->step;
     const long long np = P.n_pad;
@@ -150,16 +150,33 @@ __global__ void __launch_bounds__(kPairThreads)
     }
 }
 
+__global__ void __launch_bounds__(kPairThreads) pair_force_integrate(const StepParams P, Ctrl* __restrict__ ctrl, const float4* __restrict__ pos,
+                         const int* __restrict__ perm, const int* __restrict__ nbr, const int* __restrict__ nbr_cnt,
+                         const float4* __restrict__ vel, const float4* __restrict__ fc, const float* __restrict__ conv,
+                         const float* __restrict__ frblock, const float* __restrict__ ftab,
+                         const float* __restrict__ g0, void* __restrict__ ring, float4* __restrict__ pos_next,
+                         float4* __restrict__ vhalf, float4* __restrict__ fd_out, float4* __restrict__ disp,
+                         const float4* __restrict__ disp_build)
+{
+    pair_force_integrate_body(P, ctrl, pos, perm, nbr, nbr_cnt, vel, fc, conv, frblock, ftab, g0, ring, pos_next, vhalf, fd_out, disp, disp_build, blockIdx.x, gridDim.x);
+}
+
 // ---- cell list --------------------------------------------------------------
-__global__ void cell_assign(const StepParams P, const int* __restrict__ gate, const float4* __restrict__ pos,
-                            int* __restrict__ head, int* __restrict__ next, int* __restrict__ count)
+__device__ __forceinline__ void cell_assign_body(const StepParams& P, const int* __restrict__ gate, const float4* __restrict__ pos,
+                            int* __restrict__ head, int* __restrict__ next, int* __restrict__ count, int blk, int nblk)
 {
     if (gate && *gate == 0) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blk * blockDim.x + threadIdx.x;
     if (i >= P.n) return;
     const int c = cell_of(pos[i], P);
     atomicAdd(count + c, 1);
     next[i] = atomicExch(head + c, i);
+}
+
+__global__ void cell_assign(const StepParams P, const int* __restrict__ gate, const float4* __restrict__ pos,
+                            int* __restrict__ head, int* __restrict__ next, int* __restrict__ count)
+{
+    cell_assign_body(P, gate, pos, head, next, count, blockIdx.x, gridDim.x);
 }
 
 // Exclusive block scan of one int per thread; returns the block total.
@@ -194,48 +211,52 @@ __device__ int block_exclusive_scan(int v, int* out_excl)
 }
 
 // Chunk sums of the cell counts; the last block to finish scans them.
-__global__ void __launch_bounds__(kCellThreads)
-    cell_scan(const int* __restrict__ gate, const int* __restrict__ count, int ncells, int* __restrict__ chunk_sum,
-              int* __restrict__ chunk_off, unsigned* __restrict__ done)
+__device__ __forceinline__ void cell_scan_body(const int* __restrict__ gate, const int* __restrict__ count, int ncells, int* __restrict__ chunk_sum,
+              int* __restrict__ chunk_off, unsigned* __restrict__ done, int blk, int nblk)
 {
     if (gate && *gate == 0) return;  // uniform over the grid
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blk * blockDim.x + threadIdx.x;
     int excl;
     const int tot = block_exclusive_scan(c < ncells ? count[c] : 0, &excl);
     __shared__ bool last;
     if (threadIdx.x == 0) {
-        chunk_sum[blockIdx.x] = tot;
+        chunk_sum[blk] = tot;
         __threadfence();
-        last = atomicAdd(done, 1u) == gridDim.x - 1;
+        last = atomicAdd(done, 1u) == nblk - 1;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
     int carry = 0;
-    for (int base = 0; base < (int)gridDim.x; base += blockDim.x) {
+    for (int base = 0; base < (int)nblk; base += blockDim.x) {
         const int b = base + threadIdx.x;
-        const int v = b < (int)gridDim.x ? ((volatile int*)chunk_sum)[b] : 0;
+        const int v = b < (int)nblk ? ((volatile int*)chunk_sum)[b] : 0;
         int e;
         const int t = block_exclusive_scan(v, &e);
-        if (b < (int)gridDim.x) chunk_off[b] = carry + e;
+        if (b < (int)nblk) chunk_off[b] = carry + e;
         carry += t;
     }
     if (threadIdx.x == 0) *done = 0u;
 }
 
+__global__ void __launch_bounds__(kCellThreads) cell_scan(const int* __restrict__ gate, const int* __restrict__ count, int ncells, int* __restrict__ chunk_sum,
+              int* __restrict__ chunk_off, unsigned* __restrict__ done)
+{
+    cell_scan_body(gate, count, ncells, chunk_sum, chunk_off, done, blockIdx.x, gridDim.x);
+}
+
 // Cell starts, and each cell's particles in increasing id order.
-__global__ void __launch_bounds__(kCellThreads)
-    cell_fill(const StepParams P, const int* __restrict__ gate, int ncells, const float4* __restrict__ pos,
+__device__ __forceinline__ void cell_fill_body(const StepParams& P, const int* __restrict__ gate, int ncells, const float4* __restrict__ pos,
               int* __restrict__ count, int* __restrict__ head, const int* __restrict__ next,
-              const int* __restrict__ chunk_off, int* __restrict__ cell_start, float4* __restrict__ pos_sorted)
+              const int* __restrict__ chunk_off, int* __restrict__ cell_start, float4* __restrict__ pos_sorted, int blk, int nblk)
 {
     if (gate && *gate == 0) return;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blk * blockDim.x + threadIdx.x;
     const int cnt = c < ncells ? count[c] : 0;
     int excl;
     block_exclusive_scan(cnt, &excl);
     if (c >= ncells) return;
-    const int start = chunk_off[blockIdx.x] + excl;
+    const int start = chunk_off[blk] + excl;
     cell_start[c] = start;
     int j = head[c];
     for (int r = 0; r < cnt && j >= 0; ++r) {
@@ -253,14 +274,20 @@ __global__ void __launch_bounds__(kCellThreads)
     count[c] = 0;
 }
 
+__global__ void __launch_bounds__(kCellThreads) cell_fill(const StepParams P, const int* __restrict__ gate, int ncells, const float4* __restrict__ pos,
+              int* __restrict__ count, int* __restrict__ head, const int* __restrict__ next,
+              const int* __restrict__ chunk_off, int* __restrict__ cell_start, float4* __restrict__ pos_sorted)
+{
+    cell_fill_body(P, gate, ncells, pos, count, head, next, chunk_off, cell_start, pos_sorted, blockIdx.x, gridDim.x);
+}
+
 // Per particle, in cell order: the ids within r_c + skin, sorted by id.
-__global__ void __launch_bounds__(kThreads)
-    nbr_build(const StepParams P, Ctrl* __restrict__ ctrl, const float4* __restrict__ pos_sorted,
+__device__ __forceinline__ void nbr_build_body(const StepParams& P, Ctrl* __restrict__ ctrl, const float4* __restrict__ pos_sorted,
               const int* __restrict__ cell_start, int* __restrict__ nbr, int* __restrict__ nbr_cnt,
-              int* __restrict__ perm, const float4* __restrict__ disp, float4* __restrict__ disp_build)
+              int* __restrict__ perm, const float4* __restrict__ disp, float4* __restrict__ disp_build, int blk, int nblk)
 {
     if (ctrl->rebuild == 0) return;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blk * blockDim.x + threadIdx.x;
     if (k == 0) ctrl->rebuilds += 1;
     if (k >= P.n) return;
     const float4 pi = pos_sorted[k];
@@ -290,17 +317,23 @@ __global__ void __launch_bounds__(kThreads)
     disp_build[id] = disp[id];
 }
 
+__global__ void __launch_bounds__(kThreads) nbr_build(const StepParams P, Ctrl* __restrict__ ctrl, const float4* __restrict__ pos_sorted,
+              const int* __restrict__ cell_start, int* __restrict__ nbr, int* __restrict__ nbr_cnt,
+              int* __restrict__ perm, const float4* __restrict__ disp, float4* __restrict__ disp_build)
+{
+    nbr_build_body(P, ctrl, pos_sorted, cell_start, nbr, nbr_cnt, perm, disp, disp_build, blockIdx.x, gridDim.x);
+}
+
 // ---- conservative force and velocity finish --------------------------------
 // R_{n+1} is read from pos_next (every thread reads neighbours there) and
 // copied into pos for the next step.
 template <bool STEP>
-__global__ void __launch_bounds__(kThreads)
-    cforce(const StepParams P, Ctrl* __restrict__ ctrl, const float4* __restrict__ pos_next,
+__device__ __forceinline__ void cforce_body(const StepParams& P, Ctrl* __restrict__ ctrl, const float4* __restrict__ pos_next,
            float4* __restrict__ pos, const int* __restrict__ perm, const int* __restrict__ nbr,
            const int* __restrict__ nbr_cnt, const float4* __restrict__ vhalf, float4* __restrict__ vel,
-           float4* __restrict__ fc)
+           float4* __restrict__ fc, int blk, int nblk)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blk * blockDim.x + threadIdx.x;
     if (k == 0) ctrl->rebuild = 0;  // the lists are current for R_{n+1}
     if (k < P.n) {
         const int id = k;
@@ -325,13 +358,22 @@ __global__ void __launch_bounds__(kThreads)
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
-            if (atomicAdd(&ctrl->done_cforce, 1u) == gridDim.x - 1) {
+            if (atomicAdd(&ctrl->done_cforce, 1u) == nblk - 1) {
                 ctrl->step += 1;
                 ctrl->done_cforce = 0u;
                 __threadfence();
             }
         }
     }
+}
+
+template <bool STEP>
+__global__ void __launch_bounds__(kThreads) cforce(const StepParams P, Ctrl* __restrict__ ctrl, const float4* __restrict__ pos_next,
+           float4* __restrict__ pos, const int* __restrict__ perm, const int* __restrict__ nbr,
+           const int* __restrict__ nbr_cnt, const float4* __restrict__ vhalf, float4* __restrict__ vel,
+           float4* __restrict__ fc)
+{
+    cforce_body<STEP>(P, ctrl, pos_next, pos, perm, nbr, nbr_cnt, vhalf, vel, fc, blockIdx.x, gridDim.x);
 }
 
 // ---- velocity autocorrelation ------------------------------------------------
@@ -349,10 +391,9 @@ __device__ __forceinline__ float warp_sum_f(float v)
 // sums in FP32, block and grid sums in FP64 in a fixed order (the last block
 // to finish adds the per-block partials).
 template <int NO>
-__global__ void __launch_bounds__(kThreads)
-    vacf(const StepParams P, const Ctrl* __restrict__ ctrl, const float4* __restrict__ vel,
+__device__ __forceinline__ void vacf_body(const StepParams& P, const Ctrl* __restrict__ ctrl, const float4* __restrict__ vel,
          float4* __restrict__ vorig, double* __restrict__ partial, double* __restrict__ csum,
-         long long* __restrict__ ccnt, long long* __restrict__ norig, unsigned* __restrict__ done)
+         long long* __restrict__ ccnt, long long* __restrict__ norig, unsigned* __restrict__ done, int blk, int nblk)
 {
     const long long t = ctrl->step;  // V_t was completed by the previous kernel
     if (t < P.vacf_burnin) return;  // uniform over the grid
@@ -369,7 +410,7 @@ __global__ void __launch_bounds__(kThreads)
     float acc[NO];
 #pragma unroll
     for (int q = 0; q < NO; ++q) acc[q] = 0.f;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+    for (int i = blk * blockDim.x + threadIdx.x; i < P.n; i += nblk * blockDim.x) {
         const float4 v = vel[i];
         float4 w[NO];
 #pragma unroll
@@ -394,13 +435,13 @@ __global__ void __launch_bounds__(kThreads)
     if (threadIdx.x < NO && (int)threadIdx.x < n_act) {
         double sb = 0.0;
         for (int w = 0; w < kThreads / 32; ++w) sb += wsum[w][threadIdx.x];
-        partial[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = sb;
+        partial[(size_t)threadIdx.x * nblk + blk] = sb;
     }
     __shared__ bool last;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        last = atomicAdd(done, 1u) == gridDim.x - 1;
+        last = atomicAdd(done, 1u) == nblk - 1;
     }
     __syncthreads();
     if (!last) return;
@@ -409,10 +450,10 @@ __global__ void __launch_bounds__(kThreads)
     double sg[NO];
 #pragma unroll
     for (int q = 0; q < NO; ++q) sg[q] = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+    for (int b = threadIdx.x; b < (int)nblk; b += blockDim.x)
 #pragma unroll
         for (int q = 0; q < NO; ++q)
-            if (q < n_act) sg[q] += __ldcg(partial + (size_t)q * gridDim.x + b);
+            if (q < n_act) sg[q] += __ldcg(partial + (size_t)q * nblk + b);
 #pragma unroll
     for (int q = 0; q < NO; ++q) {
         double v = sg[q];
@@ -436,6 +477,14 @@ __global__ void __launch_bounds__(kThreads)
         if (is_origin) *norig += 1;
         *done = 0u;
     }
+}
+
+template <int NO>
+__global__ void __launch_bounds__(kThreads) vacf(const StepParams P, const Ctrl* __restrict__ ctrl, const float4* __restrict__ vel,
+         float4* __restrict__ vorig, double* __restrict__ partial, double* __restrict__ csum,
+         long long* __restrict__ ccnt, long long* __restrict__ norig, unsigned* __restrict__ done)
+{
+    vacf_body<NO>(P, ctrl, vel, vorig, partial, csum, ccnt, norig, done, blockIdx.x, gridDim.x);
 }
 
 // ---- explicit pair lists (checks of the traversals) -------------------------
@@ -500,7 +549,86 @@ __global__ void delay_kernel(unsigned long long ns)
     } while (t1 - t0 < ns);
 }
 
+// ---- batch kernels: tile -> member descriptor -> the bodies above ----------
+__global__ void __launch_bounds__(kPairThreads) b_pair(const SysDesc* __restrict__ D, const Tile* __restrict__ tiles)
+{
+    const Tile t = tiles[blockIdx.x];
+    const SysDesc& d = D[t.m];
+    const ParticleBuffers& B = d.B;
+    pair_force_integrate_body(d.P, B.ctrl, B.pos, B.perm, B.nbr, B.nbr_cnt, B.vel, B.fc, B.conv, B.frblock, B.ftab,
+                              B.g0, B.ring, B.pos_next, B.vhalf, B.fd, B.disp, B.disp_build, t.b, d.nb_pair);
+}
+
+__global__ void b_cell_assign(const SysDesc* __restrict__ D, const Tile* __restrict__ tiles)
+{
+    const Tile t = tiles[blockIdx.x];
+    const SysDesc& d = D[t.m];
+    const ParticleBuffers& B = d.B;
+    cell_assign_body(d.P, &B.ctrl->rebuild, B.pos_next, B.cell_head, B.cell_next, B.cell_count, t.b, d.nb_part);
+}
+
+__global__ void __launch_bounds__(kCellThreads) b_cell_scan(const SysDesc* __restrict__ D, const Tile* __restrict__ tiles)
+{
+    const Tile t = tiles[blockIdx.x];
+    const SysDesc& d = D[t.m];
+    const ParticleBuffers& B = d.B;
+    cell_scan_body(&B.ctrl->rebuild, B.cell_count, B.ncells, B.chunk_sum, B.chunk_off, &B.ctrl->done_scan, t.b,
+                   d.nb_cell);
+}
+
+__global__ void __launch_bounds__(kCellThreads) b_cell_fill(const SysDesc* __restrict__ D, const Tile* __restrict__ tiles)
+{
+    const Tile t = tiles[blockIdx.x];
+    const SysDesc& d = D[t.m];
+    const ParticleBuffers& B = d.B;
+    cell_fill_body(d.P, &B.ctrl->rebuild, B.ncells, B.pos_next, B.cell_count, B.cell_head, B.cell_next, B.chunk_off,
+                   B.cell_start, B.pos_sorted, t.b, d.nb_cell);
+}
+
+__global__ void __launch_bounds__(kThreads) b_nbr_build(const SysDesc* __restrict__ D, const Tile* __restrict__ tiles)
+{
+    const Tile t = tiles[blockIdx.x];
+    const SysDesc& d = D[t.m];
+    const ParticleBuffers& B = d.B;
+    nbr_build_body(d.P, B.ctrl, B.pos_sorted, B.cell_start, B.nbr, B.nbr_cnt, B.perm, B.disp, B.disp_build, t.b,
+                   d.nb_part);
+}
+
+__global__ void __launch_bounds__(kThreads) b_cforce(const SysDesc* __restrict__ D, const Tile* __restrict__ tiles)
+{
+    const Tile t = tiles[blockIdx.x];
+    const SysDesc& d = D[t.m];
+    const ParticleBuffers& B = d.B;
+    cforce_body<true>(d.P, B.ctrl, B.pos_next, B.pos, B.perm, B.nbr, B.nbr_cnt, B.vhalf, B.vel, B.fc, t.b, d.nb_part);
+}
+
+template <int NO>
+__global__ void __launch_bounds__(kThreads) b_vacf(const SysDesc* __restrict__ D, const Tile* __restrict__ tiles)
+{
+    const Tile t = tiles[blockIdx.x];
+    const SysDesc& d = D[t.m];
+    const ParticleBuffers& B = d.B;
+    vacf_body<NO>(d.P, B.ctrl, B.vel, B.vorig, B.vpartial, B.csum, B.ccnt, B.norig, B.vdone, t.b, d.nb_vacf);
+}
+
 }  // namespace
+
+cudaError_t launch_batch_particles(const BatchPlan& bp, cudaStream_t st)
+{
+    if (bp.n_pair) b_pair<<<bp.n_pair, kPairThreads, 0, st>>>(bp.desc, bp.pair);
+    if (bp.n_part) b_cell_assign<<<bp.n_part, kThreads, 0, st>>>(bp.desc, bp.part);
+    if (bp.n_cell) b_cell_scan<<<bp.n_cell, kCellThreads, 0, st>>>(bp.desc, bp.cell);
+    if (bp.n_cell) b_cell_fill<<<bp.n_cell, kCellThreads, 0, st>>>(bp.desc, bp.cell);
+    if (bp.n_part) b_nbr_build<<<bp.n_part, kThreads, 0, st>>>(bp.desc, bp.part);
+    if (bp.n_part) b_cforce<<<bp.n_part, kThreads, 0, st>>>(bp.desc, bp.part);
+    if (bp.n_vacf) {
+        if (bp.vacf_no <= 4) b_vacf<4><<<bp.n_vacf, kThreads, 0, st>>>(bp.desc, bp.vacf);
+        else if (bp.vacf_no <= 8) b_vacf<8><<<bp.n_vacf, kThreads, 0, st>>>(bp.desc, bp.vacf);
+        else if (bp.vacf_no <= 16) b_vacf<16><<<bp.n_vacf, kThreads, 0, st>>>(bp.desc, bp.vacf);
+        else b_vacf<32><<<bp.n_vacf, kThreads, 0, st>>>(bp.desc, bp.vacf);
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_rebuild_decide(cudaGraphConditionalHandle h, const Ctrl* ctrl, cudaStream_t st)
 {

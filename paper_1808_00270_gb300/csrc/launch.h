@@ -61,6 +61,40 @@ cudaError_t launch_pair_list(const StepParams& P, const ParticleBuffers& B, int*
 cudaError_t launch_list_pair_list(const StepParams& P, const ParticleBuffers& B, int* pairs,
                                   long long cap, unsigned long long* count, cudaStream_t st);
 
+// ---- batches of independent systems -------------------------------------
+// Every member keeps its own buffers; one launch per kernel family covers all
+// members through a tile list of (member, block within member).  Members share
+// the accumulator count, history type and compensation; block counts per
+// member drive the per-member last-block logic.
+struct SysDesc {
+    StepParams P;
+    ParticleBuffers B;
+    const float* coef;       // convolution coefficients [nacc][m_max]
+    float* W;                // white-noise ring
+    const float* taps;       // FP32 filter taps
+    int ntaps;
+    uint32_t k0, k1;         // Philox key
+    const int* int2ext;
+    int nb_pair, nb_part, nb_cell, nb_vacf, nb_conv, nb_fir;
+};
+struct Tile {
+    int m, b;   // member, block within member
+    int nb, r;  // blocks of the member in this schedule (convolution), unused
+};
+struct BatchPlan {
+    const SysDesc* desc;
+    const Tile *pair, *part, *cell, *vacf, *conv, *fir;
+    int n_pair, n_part, n_cell, n_vacf, n_conv, n_fir;
+    int max_H, max_n, max_ntaps, nacc, bf16, kahan, vacf_no;
+    int conv_block;  // threads per convolution tile (128 or 256)
+};
+cudaError_t launch_batch_conv(const BatchPlan& bp, cudaStream_t st);      // k_history.cu
+cudaError_t launch_batch_particles(const BatchPlan& bp, cudaStream_t st); // k_particles.cu
+cudaError_t launch_batch_noise(const BatchPlan& bp, cudaStream_t st);     // k_noise.cu
+// Block sizes of the tile schedules.
+constexpr int kBatchPairBlock = 128, kBatchPartBlock = 256, kBatchCellChunk = 512, kBatchConvCols = 256,
+              kBatchFirStreams = 32, kBatchVacfBlock = 256;
+
 // Noise and kernel preparation (k_noise.cu).
 struct PrepArgs {
     int m_max, Q, Qs, discrete, clamp, T;
