@@ -219,6 +219,16 @@ enum {
 };
 gld_status gld_profile_steps(gld_ctx* ctx, int64_t nsteps, double* ms, int64_t* launches);
 
+/* Device bytes the context holds (all of its buffers, 256-byte granules). */
+gld_status gld_get_bytes(gld_ctx* ctx, int64_t* bytes);
+/* Device bytes a context with these parameters will hold after gld_create
+ * and a gld_set_kernels with Q pair terms, Qs self-difference terms and nr
+ * table points: exactly what gld_get_bytes then reports.  Needs a current
+ * device (the VACF partial sums scale with its SM count); no device memory
+ * is touched.  The history ring is (m_max-1)*3*n_pad*{4,2} bytes of it, the
+ * white-noise window (64 + 2(m_max-1))*3*n_pad*4 bytes. */
+gld_status gld_bytes_needed(const gld_params* params, int32_t Q, int32_t Qs, int32_t nr, int64_t* bytes);
+
 const char* gld_last_error(const gld_ctx* ctx);
 gld_status gld_destroy(gld_ctx* ctx);
 
@@ -245,9 +255,81 @@ gld_status gld_batch_sync(gld_batch* batch);
 /* members, chosen convolution schedule (-1 before the first step), and the
  * timed milliseconds of the four schedules; pointers may be NULL. */
 gld_status gld_batch_info(gld_batch* batch, int32_t* members, int32_t* schedule, double* schedule_ms);
+/* policy 0 (default): re-time the schedules whenever the members change;
+ * 1: re-time only when the total number of convolution columns has moved by
+ * more than 2x since the last timing (for batches that change every block). */
+gld_status gld_batch_set_tuning(gld_batch* batch, int32_t policy);
 const char* gld_batch_last_error(const gld_batch* batch);
 /* Frees the batch; the members stay valid. */
 gld_status gld_batch_destroy(gld_batch* batch);
+
+/* ---- serving: continuous batching of simulation requests ----------------
+ * A request is a whole simulation (system, kernels, number of steps) whose
+ * result is its VACF (and, on request, its final state).  Requests that have
+ * arrived are admitted in arrival order while the device bytes of their
+ * systems (gld_bytes_needed) fit the server's budget and a member slot is
+ * free; a request that does not fit waits (no overtaking), one larger than
+ * the whole budget fails with GLD_E_NOMEM.  Admitted systems live on the
+ * device until they finish and are stepped together as one batch in 64-step
+ * blocks (gld_batch_*); the composition changes at block boundaries while
+ * the next block is already queued, so admission, retirement and result
+ * read-back overlap the device work.  Steps beyond the last whole block run
+ * alone on the server's stream.  A request's result does not depend on the
+ * other requests.  Not thread-safe: one thread drives a server. */
+typedef struct gld_server gld_server;
+typedef struct {
+    int64_t hbm_budget;   /* device bytes for admitted systems; 0: 85% of the free memory at creation */
+    int32_t max_members;  /* systems stepped together at most; 0: no limit */
+    int32_t in_flight;    /* blocks queued ahead of the device (default 2) */
+    int32_t tuning;       /* gld_batch_set_tuning policy of the batch (default 1) */
+    void* stream;         /* cudaStream_t of the batched work; NULL: the server creates one */
+} gld_server_params;
+typedef struct {
+    gld_params params;    /* the system; stream, alloc, free, order and use_graphs are the server's */
+    const double* pos;    /* [n][3], copied at submission */
+    const double* vel;    /* [n][3] */
+    const double* Ks;     /* kernels as for gld_set_kernels, copied at submission */
+    int32_t Q;
+    const double* g;
+    const double* f;
+    int32_t nr;
+    double dr;
+    const double* dKs_g;
+    const double* dKs_f;
+    int32_t Qs;
+    int32_t kernel_convention;
+    int64_t steps;        /* steps to run (>= 0) */
+    double arrival;       /* server clock (s) before which it is not admitted; non-decreasing */
+    int32_t keep_state;   /* also return the final positions and velocities */
+} gld_request;
+enum {  /* gld_server_stats slots */
+    GLD_SRV_QUEUED = 0, GLD_SRV_ACTIVE = 1, GLD_SRV_RETIRING = 2, GLD_SRV_DONE = 3, GLD_SRV_FAILED = 4,
+    GLD_SRV_BLOCKS = 5, GLD_SRV_PARTICLE_STEPS = 6, GLD_SRV_BYTES = 7, GLD_SRV_BYTES_PEAK = 8,
+    GLD_SRV_MEMBERS_PEAK = 9, GLD_SRV_BUDGET = 10, GLD_SRV_N = 11
+};
+void gld_server_params_default(gld_server_params* params);
+gld_status gld_server_create(const gld_server_params* params, gld_server** out);
+/* Queues a request (inputs copied); *id numbers requests from 0. */
+gld_status gld_server_submit(gld_server* server, const gld_request* request, int64_t* id);
+/* One scheduling round: collects finished results, admits arrived requests,
+ * queues one 64-step block of the batch (waiting only while `in_flight`
+ * blocks are ahead of the device).  *active: systems in the batch. */
+gld_status gld_server_pump(gld_server* server, int32_t* active);
+/* Pumps until every submitted request has finished (timeout_s <= 0: none). */
+gld_status gld_server_drain(gld_server* server, double timeout_s);
+/* Seconds since the server was created (the clock of arrivals and results). */
+gld_status gld_server_clock(const gld_server* server, double* t);
+/* Result of request id: vacf[vacf_len], *n_origins, pos/vel [n][3] (only
+ * with keep_state; else pass NULL), times[3] = {arrival, admission, done}
+ * (-1 where not reached; filled whatever the status).  GLD_E_STATE while it
+ * has not finished; the request's error if it failed.  Any pointer may be NULL. */
+gld_status gld_server_result(gld_server* server, int64_t id, double* vacf, int64_t* n_origins, double* pos,
+                             double* vel, double* times);
+/* out[k] for the GLD_SRV_* slots k < count. */
+gld_status gld_server_stats(gld_server* server, int64_t* out, int32_t count);
+const char* gld_server_last_error(const gld_server* server);
+/* Waits for the device, frees every system and the server. */
+gld_status gld_server_destroy(gld_server* server);
 
 /* ---- single kernels on caller-owned device memory ----------------------- */
 

@@ -43,6 +43,22 @@ class Params(C.Structure):
                 ("free", FREE_FN), ("alloc_user", C.c_void_p)]
 
 
+class ServerParams(C.Structure):
+    _fields_ = [("hbm_budget", C.c_int64), ("max_members", C.c_int32), ("in_flight", C.c_int32),
+                ("tuning", C.c_int32), ("stream", C.c_void_p)]
+
+
+class Request(C.Structure):
+    _fields_ = [("params", Params), ("pos", C.c_void_p), ("vel", C.c_void_p), ("Ks", C.c_void_p),
+                ("Q", C.c_int32), ("g", C.c_void_p), ("f", C.c_void_p), ("nr", C.c_int32), ("dr", C.c_double),
+                ("dKs_g", C.c_void_p), ("dKs_f", C.c_void_p), ("Qs", C.c_int32),
+                ("kernel_convention", C.c_int32), ("steps", C.c_int64), ("arrival", C.c_double),
+                ("keep_state", C.c_int32)]
+
+
+SRV_STATS = ["queued", "active", "retiring", "done", "failed", "blocks", "particle_steps", "bytes", "bytes_peak",
+             "members_peak", "budget"]
+
 _lib = None
 
 
@@ -80,6 +96,19 @@ def lib():
             "gld_gauss3_dev": (i32, [u64, vp, vp, u32, vp, i64, vp]),
             "gld_hist_conv_dev": (i32, [vp, i32, i32, i32, i64, vp, i32, vp, i32, vp]),
             "gld_pairs_noalloc": (i32, [vp, i32, d, d, vp, i64, vp, vp]),
+            "gld_get_bytes": (i32, [vp, C.POINTER(i64)]),
+            "gld_bytes_needed": (i32, [C.POINTER(Params), i32, i32, i32, C.POINTER(i64)]),
+            "gld_batch_set_tuning": (i32, [vp, i32]),
+            "gld_server_params_default": (None, [C.POINTER(ServerParams)]),
+            "gld_server_create": (i32, [C.POINTER(ServerParams), C.POINTER(vp)]),
+            "gld_server_submit": (i32, [vp, C.POINTER(Request), C.POINTER(i64)]),
+            "gld_server_pump": (i32, [vp, C.POINTER(i32)]),
+            "gld_server_drain": (i32, [vp, d]),
+            "gld_server_clock": (i32, [vp, C.POINTER(d)]),
+            "gld_server_result": (i32, [vp, i64, vp, C.POINTER(i64), vp, vp, vp]),
+            "gld_server_stats": (i32, [vp, vp, i32]),
+            "gld_server_last_error": (C.c_char_p, [vp]),
+            "gld_server_destroy": (i32, [vp]),
             "gld_batch_create": (i32, [vp, C.POINTER(vp)]),
             "gld_batch_add": (i32, [vp, vp]),
             "gld_batch_remove": (i32, [vp, vp]),
@@ -104,7 +133,10 @@ def exported_symbols() -> list[str]:
             "gld_get_coefs", "gld_get_pairs", "gld_get_order", "gld_get_diag", "gld_profile_steps", "gld_last_error", "gld_destroy", "gld_philox_dev",
             "gld_gauss3_dev", "gld_hist_conv_dev", "gld_pairs_noalloc", "gld_batch_create", "gld_batch_add",
             "gld_batch_remove", "gld_batch_step", "gld_batch_sync", "gld_batch_info", "gld_batch_last_error",
-            "gld_batch_destroy"]
+            "gld_batch_destroy", "gld_get_bytes", "gld_bytes_needed", "gld_batch_set_tuning",
+            "gld_server_params_default", "gld_server_create", "gld_server_submit", "gld_server_pump",
+            "gld_server_drain", "gld_server_clock", "gld_server_result", "gld_server_stats",
+            "gld_server_last_error", "gld_server_destroy"]
 
 
 def _ptr(a: np.ndarray):
@@ -266,6 +298,12 @@ class GLD:
         self._check(lib().gld_get_diag(self._h, _ptr(out), 4))
         return dict(graph_mode=int(out[0]), rebuilds=int(out[1]), maxnb=int(out[2]), cells_per_edge=int(out[3]))
 
+    def bytes(self) -> int:
+        """Device bytes this system holds."""
+        b = C.c_int64()
+        self._check(lib().gld_get_bytes(self._h, C.byref(b)))
+        return b.value
+
     def order(self) -> np.ndarray:
         """Internal storage order: entry k is the caller's index stored at k."""
         out = np.zeros(self.n, dtype=np.int32)
@@ -303,6 +341,22 @@ def _dptr(t) -> int:
     return int(t.data_ptr())
 
 
+def bytes_needed(*, n, box, m_max, r_c, dt=0.005, skin=0.0, hist_dtype="f32", vacf_len=0, vacf_stride=1,
+                 Q=1, Qs=0, nr=1024) -> int:
+    """Device bytes a GLD system of these parameters holds once its kernels
+    (Q pair terms, Qs self-difference terms on nr table points) are set."""
+    p = Params()
+    lib().gld_params_default(C.byref(p))
+    p.n, p.box, p.m_max, p.r_c, p.dt, p.skin = int(n), float(box), int(m_max), float(r_c), float(dt), float(skin)
+    p.hist_dtype = HIST_BF16 if hist_dtype in ("bf16", HIST_BF16) else HIST_F32
+    p.vacf_len, p.vacf_stride = int(vacf_len), int(vacf_stride)
+    b = C.c_int64()
+    st = lib().gld_bytes_needed(C.byref(p), int(Q), int(Qs), int(nr), C.byref(b))
+    if st != OK:
+        raise GLDError(st, "gld_bytes_needed")
+    return b.value
+
+
 class Batch:
     """Independent GLD systems stepped together (wraps a gld_batch): each kernel
     family is one launch over all members, a 64-step block of the whole batch
@@ -338,6 +392,11 @@ class Batch:
         if st != OK:
             raise GLDError(st, lib().gld_batch_last_error(self._h).decode())
 
+    def set_tuning(self, policy: int):
+        """0: re-time the convolution schedules at every composition change;
+        1: only when the total column count moved by more than 2x."""
+        self._check(lib().gld_batch_set_tuning(self._h, int(policy)))
+
     def info(self) -> dict:
         m, sc = C.c_int32(), C.c_int32()
         ms = np.zeros(4)
@@ -349,6 +408,118 @@ class Batch:
             lib().gld_batch_destroy(self._h)
             self._h = None
         self.members = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Serving loop over GLD simulation requests (wraps a gld_server):
+    admission by device bytes, continuous batching in 64-step blocks,
+    results (VACF, optionally the final state) per request."""
+
+    def __init__(self, *, hbm_budget=0, max_members=0, in_flight=2, tuning=1, stream=None):
+        L = lib()
+        p = ServerParams()
+        L.gld_server_params_default(C.byref(p))
+        p.hbm_budget, p.max_members, p.in_flight, p.tuning = int(hbm_budget), int(max_members), int(in_flight), int(tuning)
+        p.stream = None if stream is None else int(stream)
+        h = C.c_void_p()
+        st = L.gld_server_create(C.byref(p), C.byref(h))
+        if st != OK:
+            raise GLDError(st, "gld_server_create failed")
+        self._h = h
+        self._meta = {}
+
+    def _check(self, st: int):
+        if st != OK:
+            raise GLDError(st, lib().gld_server_last_error(self._h).decode())
+
+    def submit(self, *, n, box, dt, m_max, r_c, pos, vel, Ks, g=None, f=None, dr=1.0, gs=None, fs=None,
+               discrete=False, steps, arrival=0.0, keep_state=False, mass=1.0, kT=1.0, r_c_min=0.0, A_cons=0.0,
+               skin=0.0, seed=1, hist_dtype="f32", kahan=False, vacf_len=0, vacf_stride=1, vacf_burnin=-1) -> int:
+        L = lib()
+        r = Request()
+        p = r.params
+        L.gld_params_default(C.byref(p))
+        p.n, p.box, p.mass, p.kT, p.dt = int(n), float(box), float(mass), float(kT), float(dt)
+        p.m_max, p.r_c, p.r_c_min, p.A_cons, p.skin = int(m_max), float(r_c), float(r_c_min), float(A_cons), float(skin)
+        p.seed = int(seed)
+        p.hist_dtype = HIST_BF16 if hist_dtype in ("bf16", HIST_BF16) else HIST_F32
+        p.kahan = int(bool(kahan))
+        p.vacf_len, p.vacf_stride, p.vacf_burnin = int(vacf_len), int(vacf_stride), int(vacf_burnin)
+        M = int(m_max)
+        pos, vel, Ks = _f64(pos).reshape(-1, 3), _f64(vel).reshape(-1, 3), _f64(Ks)
+        g = None if g is None else _f64(g).reshape(-1, M)
+        gs = None if gs is None else _f64(gs).reshape(-1, M)
+        Q = 0 if g is None else g.shape[0]
+        Qs = 0 if gs is None else gs.shape[0]
+        nr = 2
+        if f is not None:
+            f = _f64(f).reshape(Q, -1)
+            nr = f.shape[1]
+        if fs is not None:
+            fs = _f64(fs).reshape(Qs, -1)
+            nr = fs.shape[1]
+        keep = (pos, vel, Ks, g, f, gs, fs)
+        r.pos, r.vel, r.Ks = pos.ctypes.data, vel.ctypes.data, Ks.ctypes.data
+        r.Q, r.Qs, r.nr, r.dr = Q, Qs, nr, float(dr)
+        r.g = None if g is None else g.ctypes.data
+        r.f = None if f is None else f.ctypes.data
+        r.dKs_g = None if gs is None else gs.ctypes.data
+        r.dKs_f = None if fs is None else fs.ctypes.data
+        r.kernel_convention = KDISCRETE if discrete else KCONT
+        r.steps, r.arrival, r.keep_state = int(steps), float(arrival), int(bool(keep_state))
+        rid = C.c_int64()
+        st = L.gld_server_submit(self._h, C.byref(r), C.byref(rid))
+        del keep
+        self._check(st)
+        self._meta[rid.value] = (int(n), int(vacf_len), bool(keep_state))
+        return rid.value
+
+    def pump(self) -> int:
+        a = C.c_int32()
+        self._check(lib().gld_server_pump(self._h, C.byref(a)))
+        return a.value
+
+    def drain(self, timeout: float = 0.0):
+        self._check(lib().gld_server_drain(self._h, float(timeout)))
+
+    def clock(self) -> float:
+        t = C.c_double()
+        self._check(lib().gld_server_clock(self._h, C.byref(t)))
+        return t.value
+
+    def result(self, rid: int) -> dict:
+        """{'status', 'vacf', 'n_origins', 'arrival', 'admitted', 'done'[, 'pos', 'vel']};
+        status is 0 when finished, E_STATE while pending, else the error."""
+        n, L, keep_state = self._meta[rid]
+        vacf = np.zeros(max(L, 1))
+        no = C.c_int64()
+        times = np.full(3, -1.0)
+        pos = np.zeros((n, 3)) if keep_state else None
+        vel = np.zeros((n, 3)) if keep_state else None
+        st = lib().gld_server_result(self._h, int(rid), _ptr(vacf), C.byref(no),
+                                     None if pos is None else _ptr(pos), None if vel is None else _ptr(vel),
+                                     _ptr(times))
+        out = {"status": st, "vacf": vacf[:L], "n_origins": no.value, "arrival": times[0], "admitted": times[1],
+               "done": times[2]}
+        if keep_state:
+            out["pos"], out["vel"] = pos, vel
+        return out
+
+    def stats(self) -> dict:
+        out = np.zeros(len(SRV_STATS), dtype=np.int64)
+        self._check(lib().gld_server_stats(self._h, _ptr(out), len(SRV_STATS)))
+        return dict(zip(SRV_STATS, out.tolist()))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().gld_server_destroy(self._h)
+            self._h = None
 
     def __del__(self):
         try:

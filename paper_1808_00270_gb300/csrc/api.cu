@@ -17,41 +17,9 @@
 
 #include <cuda_bf16.h>
 
-#include "gld.h"
-#include "launch.h"
+#include "ctx.h"
 
 using namespace gld;
-
-struct gld_ctx {
-    gld_params prm{};
-    StepParams P{};
-    int device = 0, num_sms = 0;
-    cudaStream_t st = nullptr;   // the caller's stream
-    cudaStream_t cap = nullptr;  // private stream used only to capture graphs
-    cudaStream_t cap2 = nullptr; // fills the bodies of conditional graph nodes
-    std::vector<void*> allocs;
-    ParticleBuffers B{};
-    float* W = nullptr;
-    float* Acp = nullptr;
-    int la = 0;
-    float* coef = nullptr;
-    float* g0 = nullptr;
-    float* ftab = nullptr;
-    double *d_Kd = nullptr, *d_C = nullptr, *d_Chat = nullptr, *d_A = nullptr, *d_scal = nullptr, *d_in = nullptr;
-    int* d_status = nullptr;
-    size_t ring_elem = 4;
-    long long host_step = 0, block_start = 0, noise_end = 0, last_fr_row = -1;
-    bool noise_valid = false, have_kernels = false;
-    std::vector<double> Kd, A;
-    double a = 1.0, b = 1.0, spec_min = 0.0, clamped = 0.0;
-    cudaGraphExec_t gexec = nullptr;
-    bool graph_failed = false;
-    int graph_mode = 0;  // 0 none, 1 gated rebuild kernels, 2 conditional rebuild node
-    std::string msg;
-    gld_status latched = GLD_OK;
-    std::vector<int> int2ext;  // caller's index of the particle stored at k
-    int* d_int2ext = nullptr;
-};
 
 namespace {
 
@@ -90,6 +58,8 @@ void* dalloc(gld_ctx* c, size_t bytes)
     else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
     if (p) {
         c->allocs.push_back(p);
+        c->alloc_sizes.push_back(bytes);
+        c->bytes += bytes;
         cudaMemsetAsync(p, 0, bytes, c->st);
     }
     return p;
@@ -100,7 +70,9 @@ void dfree(gld_ctx* c, void* p)
     if (!p) return;
     for (size_t k = 0; k < c->allocs.size(); ++k)
         if (c->allocs[k] == p) {
+            c->bytes -= c->alloc_sizes[k];
             c->allocs.erase(c->allocs.begin() + (long)k);
+            c->alloc_sizes.erase(c->alloc_sizes.begin() + (long)k);
             break;
         }
     if (c->prm.free) c->prm.free(p, c->prm.stream, c->prm.alloc_user);
@@ -156,12 +128,7 @@ gld_status download_vec(gld_ctx* c, const float4* src, double* dst)
     std::vector<float4> h((size_t)n);
     GLD_CUDA(c, cudaMemcpyAsync(h.data(), src, sizeof(float4) * n, cudaMemcpyDeviceToHost, c->st));
     GLD_CUDA(c, cudaStreamSynchronize(c->st));
-    for (int i = 0; i < n; ++i) {
-        const size_t e = (size_t)c->int2ext[i];
-        dst[3 * e] = h[i].x;
-        dst[3 * e + 1] = h[i].y;
-        dst[3 * e + 2] = h[i].z;
-    }
+    ctx_to_caller(c, h.data(), dst);
     return GLD_OK;
 }
 
@@ -184,14 +151,7 @@ gld_status sync_and_check(gld_ctx* c)
     GLD_CUDA(c, cudaStreamSynchronize(c->st));
     unsigned err = 0;
     GLD_CUDA(c, cudaMemcpy(&err, &c->B.ctrl->err, sizeof(unsigned), cudaMemcpyDeviceToHost));
-    if (err & kErrNonFinite) fail(c, GLD_E_NONFINITE, "non-finite displacement produced on the device");
-    else if (err & kErrNbrOverflow) {
-        c->msg = "a neighbour list exceeded its capacity (density far above the one at creation)";
-        if (c->latched == GLD_OK) c->latched = GLD_E_STATE;
-    }
-    else if (err & kErrTimeout) fail(c, GLD_E_TIMEOUT, "a bounded device wait gave up");
-    else if (err & kErrNoise) fail(c, GLD_E_CUDA, "a step ran outside its noise block");
-    return c->latched;
+    return ctx_check_err(c, err);
 }
 
 void invalidate_graph(gld_ctx* c)
@@ -317,45 +277,32 @@ int clamp_block(int) { return kMaxNoiseBlock; }  // the filter produces 64-step 
 
 }  // namespace
 
-extern "C" {
+namespace gld {
 
-void gld_params_default(gld_params* p)
+gld_status ctx_check_err(gld_ctx* c, unsigned err)
 {
-    if (!p) return;
-    std::memset(p, 0, sizeof(*p));
-    p->mass = 1.0;
-    p->kT = 1.0;
-    p->dt = 0.005;
-    p->m_max = 2;
-    p->hist_dtype = GLD_HIST_F32;
-    p->vacf_stride = 1;
-    p->vacf_burnin = -1;
-    p->noise_block = kMaxNoiseBlock;
-    p->use_graphs = 1;
+    if (err & kErrNonFinite) fail(c, GLD_E_NONFINITE, "non-finite displacement produced on the device");
+    else if (err & kErrNbrOverflow) {
+        c->msg = "a neighbour list exceeded its capacity (density far above the one at creation)";
+        if (c->latched == GLD_OK) c->latched = GLD_E_STATE;
+    }
+    else if (err & kErrTimeout) fail(c, GLD_E_TIMEOUT, "a bounded device wait gave up");
+    else if (err & kErrNoise) fail(c, GLD_E_CUDA, "a step ran outside its noise block");
+    return c->latched;
 }
 
-gld_status gld_create(const gld_params* p, const double* pos, const double* vel, gld_ctx** out)
+void ctx_to_caller(const gld_ctx* c, const float4* h, double* dst)
 {
-    if (!out) return GLD_E_INVAL;
-    *out = nullptr;
-    if (!p || !pos || !vel) return GLD_E_INVAL;
-    if (p->n < 1 || p->m_max < 2 || p->m_max > 4096 || !(p->box > 0) || !(p->mass > 0) || !(p->dt > 0) ||
-        !(p->r_c > 0) || p->r_c > 0.5 * p->box || p->kT < 0 || p->r_c_min < 0 || p->skin < 0 ||
-        (p->hist_dtype != GLD_HIST_F32 && p->hist_dtype != GLD_HIST_BF16) || p->vacf_len < 0 ||
-        (p->vacf_len > 0 && p->vacf_stride < 1) ||
-        (p->vacf_len > 0 && (p->vacf_len + p->vacf_stride - 1) / p->vacf_stride > 32))
-        return GLD_E_INVAL;
-    gld_ctx* c = new gld_ctx();
-    c->prm = *p;
-    c->st = (cudaStream_t)p->stream;
-    if (cudaGetDevice(&c->device) != cudaSuccess ||
-        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking) != cudaSuccess) {
-        delete c;
-        return GLD_E_CUDA;
+    for (int i = 0; i < c->P.n; ++i) {
+        const size_t e = (size_t)c->int2ext[i];
+        dst[3 * e] = h[i].x;
+        dst[3 * e + 1] = h[i].y;
+        dst[3 * e + 2] = h[i].z;
     }
-    StepParams& P = c->P;
+}
+
+void ctx_derive(const gld_params* p, StepParams& P, int& ncells)
+{
     P.n = p->n;
     P.n_pad = (p->n + 31) & ~31;
     P.m_max = p->m_max;
@@ -404,10 +351,83 @@ gld_status gld_create(const gld_params* p, const double* pos, const double* vel,
     P.vacf_stride = p->vacf_stride > 0 ? p->vacf_stride : 1;
     P.n_os = p->vacf_len > 0 ? (p->vacf_len + P.vacf_stride - 1) / P.vacf_stride : 0;
     P.vacf_burnin = p->vacf_burnin < 0 ? 2LL * p->m_max : p->vacf_burnin;
+    ncells = P.nc * P.nc * P.nc;
+}
+
+// Mirrors the allocations of gld_create and gld_set_kernels (each rounded to
+// 256 bytes); a test compares it with the bytes a context really holds.
+size_t ctx_bytes_needed(const gld_params* p, int Q, int Qs, int nr, int num_sms)
+{
+    StepParams P{};
+    int ncells = 0;
+    ctx_derive(p, P, ncells);
+    const size_t np = P.n_pad, n3 = 3 * np;
+    const size_t elem = P.hist_bf16 ? 2 : 4;
+    const int chunks = (ncells + 511) / 512;
+    const int vacf_gx = std::max(1, std::min((P.n + 255) / 256, 2 * num_sms));
+    const int nt = Q + Qs, nrr = nt > 0 ? nr : 2;
+    const size_t sizes[] = {
+        sizeof(Ctrl), 16 * np, 16 * np, 16 * np, 16 * np, 4 * (size_t)P.maxnb * np, 4 * np, 4 * np,
+        16 * np, 16 * np, 16 * np, 16 * np, 16 * np, elem * n3 * P.H, 4 * (size_t)kMaxAcc * n3,
+        4 * (size_t)P.T * n3, 4 * (size_t)P.lw * n3, 4 * ((size_t)ncells + 1), 4 * (size_t)ncells,
+        4 * (size_t)ncells, 4 * np, 4 * (size_t)chunks, 4 * (size_t)chunks,
+        16 * (size_t)std::max(P.n_os, 1) * P.n, 8 * (size_t)std::max(P.n_os, 1) * vacf_gx,
+        8 * (size_t)std::max(P.vacf_len, 1), 8 * (size_t)std::max(P.vacf_len, 1), 8, 4,
+        4 * (size_t)fir_taps_len(P.H), 4 * (size_t)kMaxAcc * P.m_max, 4 * 2 * (size_t)kMaxQ,
+        8 * (size_t)P.m_max, 8 * (size_t)P.m_max, 8 * (size_t)P.m_max, 8 * 2 * (size_t)P.m_max, 8 * 4, 4,
+        8 * (size_t)(1 + 2 * kMaxQ) * P.m_max, 4 * np, 4 * (size_t)std::max(nt, 1) * nrr};
+    size_t total = 0;
+    for (size_t b : sizes) total += b == 0 ? 256 : (b + 255) & ~(size_t)255;
+    return total;
+}
+
+}  // namespace gld
+
+extern "C" {
+
+void gld_params_default(gld_params* p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->mass = 1.0;
+    p->kT = 1.0;
+    p->dt = 0.005;
+    p->m_max = 2;
+    p->hist_dtype = GLD_HIST_F32;
+    p->vacf_stride = 1;
+    p->vacf_burnin = -1;
+    p->noise_block = kMaxNoiseBlock;
+    p->use_graphs = 1;
+}
+
+gld_status gld_create(const gld_params* p, const double* pos, const double* vel, gld_ctx** out)
+{
+    if (!out) return GLD_E_INVAL;
+    *out = nullptr;
+    if (!p || !pos || !vel) return GLD_E_INVAL;
+    if (p->n < 1 || p->m_max < 2 || p->m_max > 4096 || !(p->box > 0) || !(p->mass > 0) || !(p->dt > 0) ||
+        !(p->r_c > 0) || p->r_c > 0.5 * p->box || p->kT < 0 || p->r_c_min < 0 || p->skin < 0 ||
+        (p->hist_dtype != GLD_HIST_F32 && p->hist_dtype != GLD_HIST_BF16) || p->vacf_len < 0 ||
+        (p->vacf_len > 0 && p->vacf_stride < 1) ||
+        (p->vacf_len > 0 && (p->vacf_len + p->vacf_stride - 1) / p->vacf_stride > 32))
+        return GLD_E_INVAL;
+    gld_ctx* c = new gld_ctx();
+    c->prm = *p;
+    c->st = (cudaStream_t)p->stream;
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking) != cudaSuccess) {
+        delete c;
+        return GLD_E_CUDA;
+    }
+    StepParams& P = c->P;
+    int ncells = 0;
+    ctx_derive(p, P, ncells);
     c->ring_elem = P.hist_bf16 ? 2 : 4;
 
     const size_t np = P.n_pad, n3 = 3 * np;
-    const int ncells = nc * nc * nc;
+    const int nc = P.nc;
     // Internal order: the caller's, or the Morton order of the cells at R_0
     // (ties by the caller's index), so that neighbours are close in memory.
     c->int2ext.resize(p->n);
@@ -946,6 +966,23 @@ gld_status gld_destroy(gld_ctx* c)
     return GLD_OK;
 }
 
+gld_status gld_get_bytes(gld_ctx* c, int64_t* bytes)
+{
+    if (!c || !bytes) return GLD_E_INVAL;
+    *bytes = (int64_t)c->bytes;
+    return GLD_OK;
+}
+
+gld_status gld_bytes_needed(const gld_params* p, int32_t Q, int32_t Qs, int32_t nr, int64_t* bytes)
+{
+    if (!p || !bytes || p->n < 1 || p->m_max < 2 || !(p->box > 0) || !(p->r_c > 0) || Q < 0 || Qs < 0) return GLD_E_INVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return GLD_E_CUDA;
+    *bytes = (int64_t)ctx_bytes_needed(p, Q, Qs, nr, sms);
+    return GLD_OK;
+}
+
 gld_status gld_philox_dev(const uint32_t* ctr, const uint32_t key[2], uint32_t* out, int64_t n, void* stream)
 {
     if (!key || n < 0 || (n > 0 && (!ctr || !out))) return GLD_E_INVAL;
@@ -976,20 +1013,6 @@ gld_status gld_hist_conv_dev(const void* ring, int32_t bf16, int32_t n_pad, int3
 
 // ---- batches of independent systems ----------------------------------------
 
-struct gld_batch {
-    cudaStream_t st = nullptr, cap = nullptr;
-    std::vector<gld_ctx*> members;
-    SysDesc* d_desc = nullptr;
-    Tile* d_tiles = nullptr;
-    size_t desc_cap = 0, tiles_cap = 0;
-    BatchPlan plan{};
-    bool dirty = true;
-    int schedule = -1;  // chosen convolution schedule (autotuned), -1: not yet
-    double schedule_ms[4] = {0, 0, 0, 0};
-    cudaGraphExec_t gexec = nullptr;
-    std::vector<SysDesc> snap;  // member descriptors the plan was built from
-    std::string msg;
-};
 
 namespace {
 
@@ -999,10 +1022,37 @@ gld_status bfail(gld_batch* b, gld_status s, const std::string& m)
     return s;
 }
 
+// Executable graphs are destroyed only after their last launch finished.
+void batch_reap(gld_batch* b, bool all)
+{
+    size_t keep = 0;
+    for (auto& r : b->retired) {
+        if (all || cudaEventQuery(r.second) == cudaSuccess) {
+            if (all) cudaEventSynchronize(r.second);
+            cudaGraphExecDestroy(r.first);
+            cudaEventDestroy(r.second);
+        } else {
+            b->retired[keep++] = r;
+        }
+    }
+    b->retired.resize(keep);
+}
+
 void batch_drop_graph(gld_batch* b)
 {
-    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->gexec) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventRecord(e, b->st) == cudaSuccess) {
+            b->retired.push_back({b->gexec, e});
+        } else {  // cannot track it: wait
+            if (e) cudaEventDestroy(e);
+            cudaStreamSynchronize(b->st);
+            cudaGraphExecDestroy(b->gexec);
+        }
+    }
     b->gexec = nullptr;
+    batch_reap(b, false);
 }
 
 // Convolution schedules: 0 tiles of 256 columns, longest memories first;
@@ -1073,34 +1123,47 @@ gld_status batch_plan(gld_batch* b, int schedule)
     const size_t o_pair = append(pair, &P.n_pair), o_part = append(part, &P.n_part), o_cell = append(cell, &P.n_cell),
                  o_vacf = append(vacf, &P.n_vacf), o_conv = append(conv, &P.n_conv), o_fir = append(fir, &P.n_fir);
     b->snap = desc;
-    if (desc.size() > b->desc_cap) {
-        if (b->d_desc) cudaFree(b->d_desc);
-        b->d_desc = nullptr;
-        b->desc_cap = std::max<size_t>(desc.size(), 2 * b->desc_cap);
-        if (cudaMalloc(&b->d_desc, sizeof(SysDesc) * b->desc_cap) != cudaSuccess)
-            return bfail(b, GLD_E_NOMEM, "batch descriptors");
+    // One upload of descriptors and tiles through pinned staging, ordered on
+    // the batch's stream after the blocks already queued (which keep reading
+    // the previous plan until they finish); no host synchronisation.
+    const size_t desc_bytes = (sizeof(SysDesc) * desc.size() + 255) & ~(size_t)255;
+    const size_t bytes = desc_bytes + sizeof(Tile) * all.size();
+    if (bytes > b->plan_cap) {
+        if (b->d_plan) cudaFreeAsync(b->d_plan, b->st);
+        b->d_plan = nullptr;
+        b->plan_cap = std::max(bytes, 2 * b->plan_cap);
+        if (cudaMallocAsync((void**)&b->d_plan, b->plan_cap, b->st) != cudaSuccess) {
+            b->plan_cap = 0;
+            return bfail(b, GLD_E_NOMEM, "batch plan allocation");
+        }
     }
-    if (all.size() > b->tiles_cap) {
-        if (b->d_tiles) cudaFree(b->d_tiles);
-        b->d_tiles = nullptr;
-        b->tiles_cap = std::max<size_t>(all.size(), 2 * b->tiles_cap);
-        if (cudaMalloc(&b->d_tiles, sizeof(Tile) * b->tiles_cap) != cudaSuccess)
-            return bfail(b, GLD_E_NOMEM, "batch tiles");
+    const int k = b->stage_k ^= 1;
+    if (b->stage_ev[k] && cudaEventSynchronize(b->stage_ev[k]) != cudaSuccess)
+        return bfail(b, GLD_E_CUDA, "batch plan staging");
+    if (bytes > b->stage_cap[k]) {
+        if (b->h_stage[k]) cudaFreeHost(b->h_stage[k]);
+        b->h_stage[k] = nullptr;
+        b->stage_cap[k] = std::max(bytes, 2 * b->stage_cap[k]);
+        if (cudaHostAlloc((void**)&b->h_stage[k], b->stage_cap[k], cudaHostAllocDefault) != cudaSuccess) {
+            b->stage_cap[k] = 0;
+            return bfail(b, GLD_E_NOMEM, "batch plan staging allocation");
+        }
     }
-    if (!desc.empty() &&
-        (cudaMemcpyAsync(b->d_desc, desc.data(), sizeof(SysDesc) * desc.size(), cudaMemcpyHostToDevice, b->st) !=
-             cudaSuccess ||
-         cudaMemcpyAsync(b->d_tiles, all.data(), sizeof(Tile) * all.size(), cudaMemcpyHostToDevice, b->st) !=
-             cudaSuccess ||
-         cudaStreamSynchronize(b->st) != cudaSuccess))
+    if (!b->stage_ev[k] && cudaEventCreateWithFlags(&b->stage_ev[k], cudaEventDisableTiming) != cudaSuccess)
+        return bfail(b, GLD_E_CUDA, "batch plan event");
+    std::memcpy(b->h_stage[k], desc.data(), sizeof(SysDesc) * desc.size());
+    std::memcpy(b->h_stage[k] + desc_bytes, all.data(), sizeof(Tile) * all.size());
+    if (cudaMemcpyAsync(b->d_plan, b->h_stage[k], bytes, cudaMemcpyHostToDevice, b->st) != cudaSuccess ||
+        cudaEventRecord(b->stage_ev[k], b->st) != cudaSuccess)
         return bfail(b, GLD_E_CUDA, "batch plan upload");
-    P.desc = b->d_desc;
-    P.pair = b->d_tiles + o_pair;
-    P.part = b->d_tiles + o_part;
-    P.cell = b->d_tiles + o_cell;
-    P.vacf = b->d_tiles + o_vacf;
-    P.conv = b->d_tiles + o_conv;
-    P.fir = b->d_tiles + o_fir;
+    const Tile* t0 = (const Tile*)(b->d_plan + desc_bytes);
+    P.desc = (const SysDesc*)b->d_plan;
+    P.pair = t0 + o_pair;
+    P.part = t0 + o_part;
+    P.cell = t0 + o_cell;
+    P.vacf = t0 + o_vacf;
+    P.conv = t0 + o_conv;
+    P.fir = t0 + o_fir;
     return GLD_OK;
 }
 
@@ -1152,8 +1215,14 @@ gld_status batch_prepare(gld_batch* b)
 {
     if (!b->dirty) return GLD_OK;
     batch_drop_graph(b);
-    if (b->schedule < 0) GLD_TRY(batch_autotune(b));
-    else GLD_TRY(batch_plan(b, b->schedule));
+    long long cols = 0;
+    for (const gld_ctx* c : b->members) cols += 3LL * c->P.n_pad / (c->P.hist_bf16 ? 8 : 4);
+    if (b->tuning == 1 && b->schedule >= 0 && cols <= 2 * b->tuned_cols && 2 * cols >= b->tuned_cols) {
+        GLD_TRY(batch_plan(b, b->schedule));
+    } else {
+        GLD_TRY(batch_autotune(b));
+        b->tuned_cols = cols;
+    }
     cudaGraph_t g = nullptr;
     bool ok = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
@@ -1203,7 +1272,6 @@ gld_status gld_batch_add(gld_batch* b, gld_ctx* c)
     }
     b->members.push_back(c);
     b->dirty = true;
-    b->schedule = -1;
     return GLD_OK;
 }
 
@@ -1214,7 +1282,6 @@ gld_status gld_batch_remove(gld_batch* b, gld_ctx* c)
         if (b->members[k] == c) {
             b->members.erase(b->members.begin() + (long)k);
             b->dirty = true;
-            b->schedule = -1;
             return GLD_OK;
         }
     return bfail(b, GLD_E_INVAL, "gld_batch_remove: not a member");
@@ -1272,6 +1339,13 @@ gld_status gld_batch_info(gld_batch* b, int32_t* members, int32_t* schedule, dou
     return GLD_OK;
 }
 
+gld_status gld_batch_set_tuning(gld_batch* b, int32_t policy)
+{
+    if (!b || policy < 0 || policy > 1) return GLD_E_INVAL;
+    b->tuning = policy;
+    return GLD_OK;
+}
+
 const char* gld_batch_last_error(const gld_batch* b) { return b ? b->msg.c_str() : "null batch"; }
 
 gld_status gld_batch_destroy(gld_batch* b)
@@ -1279,8 +1353,13 @@ gld_status gld_batch_destroy(gld_batch* b)
     if (!b) return GLD_E_INVAL;
     cudaStreamSynchronize(b->st);
     batch_drop_graph(b);
-    if (b->d_desc) cudaFree(b->d_desc);
-    if (b->d_tiles) cudaFree(b->d_tiles);
+    batch_reap(b, true);
+    if (b->d_plan) cudaFreeAsync(b->d_plan, b->st);
+    cudaStreamSynchronize(b->st);
+    for (int k = 0; k < 2; ++k) {
+        if (b->h_stage[k]) cudaFreeHost(b->h_stage[k]);
+        if (b->stage_ev[k]) cudaEventDestroy(b->stage_ev[k]);
+    }
     if (b->cap) cudaStreamDestroy(b->cap);
     delete b;
     return GLD_OK;

@@ -40,3 +40,18 @@ def test_params_struct_layout_matches_header():
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
     fields = re.findall(r"\b([a-zA-Z_0-9]+)\s*[,;]", body)
     assert [f for f, _ in binding.Params._fields_] == fields
+
+
+def _fields(name):
+    text = open(HEADER).read()
+    end = text.index("} %s;" % name)
+    body = text[text.rindex("typedef struct", 0, end): end]
+    body = body[body.index("{") + 1:]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    return re.findall(r"\b([a-zA-Z_0-9]+)\s*[,;]", body)
+
+
+def test_server_struct_layouts_match_header():
+    assert [f for f, _ in binding.Request._fields_] == _fields("gld_request")
+    assert [f for f, _ in binding.ServerParams._fields_] == _fields("gld_server_params")
+    assert len(binding.SRV_STATS) == 11  # GLD_SRV_N
