@@ -9,6 +9,14 @@ update, VACF accumulation, and the colored-noise block every 64 steps.
 Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead.
 Under torchrun each rank steps an independent replica (different seed); there
 is no data-path collective, only a barrier and a max over ranks of the time.
+
+The headline line also summarises the first requests of the serving trace
+(`served`).  Two more workloads print their own line:
+  --workload batch512  512 uneven independent systems stepped as one batch,
+                       against the same systems stepped one at a time;
+  --workload serve     the seeded 1000-request Poisson trace (50/s) served
+                       with continuous batching, against the same requests
+                       run one at a time (`--requests R` keeps the first R).
 """
 from __future__ import annotations
 
@@ -39,9 +47,17 @@ def parse():
     ap.add_argument("--profile-steps", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=60,
+                    help="requests of the serving trace summarised in the headline line (0: none)")
     ap.add_argument("--hist", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--kahan", action="store_true")
     ap.add_argument("--reference-seconds", type=float, default=120.0)
+    ap.add_argument("--systems", type=int, default=512, help="batch512: number of systems")
+    ap.add_argument("--requests", type=int, default=1000, help="serve: requests of the trace (its first R)")
+    ap.add_argument("--max-members", type=int, default=0, help="serve: systems stepped together at most")
+    ap.add_argument("--hbm-budget", type=float, default=0.0, help="serve: device GB for admitted systems")
+    ap.add_argument("--sequential", type=int, default=-1,
+                    help="serve: requests also run one at a time with plain gld_step (-1: all)")
     return ap.parse_args()
 
 
@@ -171,9 +187,210 @@ def run_oracle(w, pos, vel, ks, g, f, dr, steps: int, seconds: float):
     return w.n * done / el, done, el, oracle.threads()
 
 
+def pctl(xs, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(xs, dtype=float), q)) if len(xs) else None
+
+
+def batch_leg(args, rank: int, world: int, local: int):
+    """Independent uneven systems stepped as one batch (one launch per kernel
+    family per step, 64-step blocks as one graph) against the same systems
+    stepped one at a time with plain gld_step."""
+    import numpy as np
+    import torch
+    from paper_1808_00270_gb300 import GLD, Batch, inputs
+    torch.cuda.set_device(local)
+    ws = inputs.batch_systems(args.systems, seed=4 + 1000 * rank)
+    vacf = dict(vacf_len=100, vacf_stride=10)
+    systems = []
+    for w in ws:
+        pos, vel = inputs.initial_state(w)
+        g = GLD(pos=pos, vel=vel, n=w.n, box=w.box, mass=w.mass, kT=w.kT, dt=w.dt, m_max=w.m_max, r_c=w.r_c,
+                A_cons=w.A_cons, seed=w.seed, hist_dtype=args.hist, kahan=args.kahan, **vacf)
+        gk, f, dr = inputs.pair_kernel_tables(w)
+        g.set_kernels(inputs.self_kernel_samples(w), g=gk, f=f, dr=dr)
+        systems.append(g)
+    n_tot = sum(w.n for w in ws)
+    b = Batch()
+    for g in systems:
+        b.add(g)
+    T = 64
+    K = max(T, (args.steps + T - 1) // T * T)
+    b.step(T * max(1, (args.warmup + T - 1) // T))  # schedule timing, graph capture
+    b.sync()
+    stream = torch.cuda.current_stream()
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]
+    clocks = ClockSampler(gpu_index, os.path.join(ROOT, "gpurun_out", f"clocks_batch_rank{rank}.csv"))
+    time.sleep(0.5)
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    b.step(K)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    b.sync()
+    ms = max_over_ranks(ms, world, "cuda")
+    value = world * n_tot * K / (ms / 1e3)
+    info = b.info()
+    for g in systems:  # members stay usable alone
+        b.remove(g)
+    # the same systems one at a time (each replays its own captured 64-step graph)
+    for g in systems:
+        g.step(T)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for g in systems:
+        g.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
+    seq = world * n_tot * K / (ms_seq / 1e3)
+    elem = 2 if args.hist == "bf16" else 4
+    alg = sum((elem * 3 * (w.m_max - 1) + 4 * 3 * 2) * w.n for w in ws)
+    conv_ms = info["schedule_ms"][info["schedule"]]
+    peak, peak_kind = peaks()
+    hist_bytes = sum(elem * 3 * (w.m_max - 1) * ((w.n + 31) // 32 * 32) for w in ws)
+    out = {"metric": f"GLD particle-steps/s, {len(ws)} batched uneven systems", "value": value,
+           "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": ms / K,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "bf16-history" + ("+kahan" if args.kahan else "") if args.hist == "bf16" else
+           ("f32+kahan" if args.kahan else "f32"), "data": "synthetic",
+           "config": {"workload": f"batch{len(ws)}", "systems": len(ws), "particles": n_tot,
+                      "n_range": [min(w.n for w in ws), max(w.n for w in ws)],
+                      "m_max_set": sorted({w.m_max for w in ws}), "history_bytes": hist_bytes,
+                      "parallelism": f"replicas{world}",
+                      "l2": f"inputs larger than L2: {hist_bytes / 1e9:.2f} GB of history rings streamed every step"},
+           "sequential": {"value": seq, "unit": UNIT, "ms_per_step": ms_seq / K,
+                          "what": "the same systems one after another, each gld_step(K) replaying its own graph"},
+           "speedup_vs_sequential": value / seq,
+           "autotune": {"schedule": info["schedule"], "schedule_ms": info["schedule_ms"],
+                        "schedules": ["256-column tiles, longest memory first", "128-column tiles, longest first",
+                                      "256-column tiles, member order", "one block per system"]},
+           "roofline": {"bound": "hbm", "kernel": "b_conv (batched history convolution)",
+                        "achieved": alg / (conv_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                        "frac": alg / (conv_ms / 1e3) / 1e9 / peak, "peak_source": f"{peak_kind} hbm_gbs",
+                        "traffic": None, "algorithmic_bytes_per_launch": alg, "avg_launch_ms": conv_ms},
+           "clocks": clk, "gpu_launches": (K // T) * (2 + T * 8)}
+    if rank == 0:
+        print(json.dumps(out))
+    for g in systems:
+        g.close()
+    b.close()
+    return 0
+
+
+def request_inputs(trace, vacf):
+    """Host inputs of each request of a trace (drawn before the clock starts)."""
+    from paper_1808_00270_gb300 import inputs
+    out = []
+    for r in trace:
+        w = r.w
+        pos, vel = inputs.initial_state(w)
+        gk, f, dr = inputs.pair_kernel_tables(w)
+        out.append(dict(n=w.n, box=w.box, dt=w.dt, m_max=w.m_max, r_c=w.r_c, pos=pos, vel=vel,
+                        Ks=inputs.self_kernel_samples(w), g=gk, f=f, dr=dr, steps=r.steps, mass=w.mass, kT=w.kT,
+                        A_cons=w.A_cons, seed=w.seed, **vacf))
+    return out
+
+
+def serve_requests(srv, trace, reqs, t0):
+    return [srv.submit(arrival=t0 + r.arrival, **q) for r, q in zip(trace, reqs)]
+
+
+def serve_leg(args, rank: int, world: int, local: int, quiet: bool = False):
+    """The seeded Poisson trace served with continuous batching, against the
+    same requests run one at a time with plain gld_step (FIFO queue)."""
+    import numpy as np
+    import torch
+    from paper_1808_00270_gb300 import GLD, Server, inputs
+    torch.cuda.set_device(local)
+    trace = inputs.serve_trace(1000, seed=5 + 1000 * rank)[: args.requests]
+    vacf = dict(vacf_len=100, vacf_stride=10)
+    budget = int(args.hbm_budget * 1e9)
+    # warm-up: module load, schedule timing and capture paths on a throw-away server
+    warm = Server(hbm_budget=budget, max_members=args.max_members)
+    wt = inputs.serve_trace(4, seed=99)
+    serve_requests(warm, wt, request_inputs(wt, vacf), 0.0)
+    warm.drain(600)
+    warm.close()
+    reqs = request_inputs(trace, vacf)
+    srv = Server(hbm_budget=budget, max_members=args.max_members)
+    t_sub = time.perf_counter()
+    t0 = srv.clock() + 0.5 + 0.002 * len(trace)  # submission ends before the first arrival
+    ids = serve_requests(srv, trace, reqs, t0)
+    sub_s = time.perf_counter() - t_sub
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]
+    clocks = ClockSampler(gpu_index, os.path.join(ROOT, "gpurun_out", f"clocks_serve_rank{rank}.csv"))
+    srv.drain(3600)
+    clk = clocks.stop()
+    res = [srv.result(i) for i in ids]
+    st = srv.stats()
+    ok = [r for r in res if r["status"] == 0]
+    lat = [r["done"] - r["arrival"] for r in ok]
+    t_end = max(r["done"] for r in ok)
+    work = sum(r.w.n * r.steps for r, x in zip(trace, res) if x["status"] == 0)
+    t_end = float(t_end)
+    served = {"p50_s": pctl(lat, 50), "p99_s": pctl(lat, 99), "mean_s": float(np.mean(lat)),
+              "throughput": work / (t_end - t0), "unit": UNIT, "makespan_s": t_end - t0,
+              "done": len(ok), "failed": len(res) - len(ok), "blocks": st["blocks"],
+              "members_peak": st["members_peak"], "bytes_peak": st["bytes_peak"], "budget": st["budget"],
+              "queue_wait_p50_s": pctl([r["admitted"] - r["arrival"] for r in ok], 50)}
+    srv.close()
+    # sequential plain runs of the same requests, FIFO in arrival order
+    nseq = len(trace) if args.sequential < 0 else min(args.sequential, len(trace))
+    seq = None
+    if nseq > 0:
+        svc = []
+        for r, q in zip(trace[:nseq], reqs):
+            w = r.w
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            g = GLD(pos=q["pos"], vel=q["vel"], n=w.n, box=w.box, mass=w.mass, kT=w.kT, dt=w.dt, m_max=w.m_max,
+                    r_c=w.r_c, A_cons=w.A_cons, seed=w.seed, **vacf)
+            g.set_kernels(q["Ks"], g=q["g"], f=q["f"], dr=q["dr"])
+            g.step(r.steps)
+            g.vacf()
+            svc.append(time.perf_counter() - a)
+            g.close()
+        done_t, lat_s = 0.0, []
+        for r, sv in zip(trace[:nseq], svc):
+            start = max(r.arrival, done_t)
+            done_t = start + sv
+            lat_s.append(done_t - r.arrival)
+        wseq = sum(r.w.n * r.steps for r in trace[:nseq])
+        seq = {"requests": nseq, "p50_s": pctl(lat_s, 50), "p99_s": pctl(lat_s, 99), "throughput": wseq / sum(svc),
+               "unit": UNIT, "what": "each request alone: gld_create + gld_set_kernels + gld_step + gld_vacf, "
+                                     "FIFO in arrival order (latency from the measured service times)"}
+    mean_work = work / max(len(ok), 1)
+    out = {"metric": f"GLD served p99 latency ({len(trace)}-request Poisson trace, 50/s)",
+           "value": served["p99_s"], "unit": "s", "n_gpus": world, "steps": int(sum(r.steps for r in trace)),
+           "warmup": 4, "ms_per_step": None, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"serve{len(trace)}", "requests": len(trace), "rate_per_s": 50.0,
+                      "n_range": [512, 65536], "m_max_range": [64, 400], "step_range": [2000, 20000],
+                      "density_range": [0.02, 0.2], "vacf": vacf, "max_members": args.max_members,
+                      "parallelism": f"replicas{world}", "submission_s": sub_s},
+           "served": served, "sequential": seq,
+           "throughput_vs_sequential": served["throughput"] / seq["throughput"] if seq else None,
+           "max_sustainable_rate_per_s": served["throughput"] / mean_work,
+           "clocks": clk, "gpu_launches": st["blocks"] * (2 + 64 * 8)}
+    if rank == 0 and not quiet:
+        print(json.dumps(out))
+    return out
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.workload.startswith("batch") and args.impl == "gld":
+        return batch_leg(args, rank, world, local)
+    if args.workload.startswith("serve") and args.impl == "gld":
+        serve_leg(args, rank, world, local)
+        return 0
     from paper_1808_00270_gb300 import inputs
     w = inputs.WORKLOADS[args.workload]
     ks = inputs.self_kernel_samples(w)
@@ -218,6 +435,7 @@ def main():
     sim.sync()
 
     K = args.steps
+    d0 = sim.diag()  # before the clock: graph form and list builds so far
     gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local] if os.environ.get("CUDA_VISIBLE_DEVICES") else str(local)
     os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
     clocks = ClockSampler(gpu_index, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv"))
@@ -234,10 +452,10 @@ def main():
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
     sim.sync()
+    d1 = sim.diag()
     ms = max_over_ranks(ms, world, "cuda")
     value = replica_value(w.n, K, world, ms)
     blocks = (K + T - 1) // T
-    launches = K * (7 if w.m_max > 0 else 6) + 2 * blocks
 
     # per-kernel device time with CUDA events on the same stream
     prof = sim.profile_steps(args.profile_steps)
@@ -257,6 +475,11 @@ def main():
                 "kernel_share": {k: v[0] / total_ms for k, v in prof.items() if total_ms > 0}}
 
     diag = sim.diag()
+    T_blocks = (K + T - 1) // T
+    if d0["graph_mode"] == 2:  # rebuild kernels only on the steps that rebuild
+        launches = K * 5 + 4 * (d1["rebuilds"] - d0["rebuilds"]) + 2 * T_blocks
+    else:
+        launches = K * 8 + 2 * T_blocks
     e2e = None
     if not args.no_e2e:
         torch.cuda.synchronize()
@@ -281,12 +504,28 @@ def main():
                "sample": f"{done} full FP64 oracle steps of the same {w.n}-particle workload after one untimed "
                          f"step ({el:.1f} s)"}
 
+    served = None
+    if rank == 0 and world == 1 and args.serve_requests > 0:
+        sargs = argparse.Namespace(**vars(args))
+        sargs.requests, sargs.sequential = args.serve_requests, args.serve_requests
+        sargs.max_members, sargs.hbm_budget = 0, 0.0
+        o = serve_leg(sargs, rank, world, local, quiet=True)
+        served = {"requests": o["config"]["requests"],
+                  "trace": "first requests of the seeded 1000-request Poisson trace (50/s; N 512-65536, "
+                           "m_max 64-400, 2000-20000 steps, VACF returned)",
+                  "p50_s": o["served"]["p50_s"], "p99_s": o["served"]["p99_s"],
+                  "throughput": o["served"]["throughput"], "unit": UNIT,
+                  "sequential_p50_s": o["sequential"]["p50_s"], "sequential_p99_s": o["sequential"]["p99_s"],
+                  "sequential_throughput": o["sequential"]["throughput"],
+                  "throughput_vs_sequential": o["throughput_vs_sequential"],
+                  "max_sustainable_rate_per_s": o["max_sustainable_rate_per_s"], "gpu_launches": o["gpu_launches"]}
+
     if rank == 0:
         print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
                           "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True,
                           "scaling": "weak", "vs_baseline": None, "dtype": "bf16-history" if args.hist == "bf16" else "f32",
                           "data": "synthetic", "config": cfg, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                          "clocks": clk, "gpu_launches": launches, "diag": diag, "profile": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items()}}))
+                          "clocks": clk, "gpu_launches": launches, "served": served, "diag": diag, "profile": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items()}}))
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0

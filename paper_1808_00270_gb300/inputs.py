@@ -106,3 +106,46 @@ def random_history(n: int, m_max: int, scale: float = 0.005, seed: int = 7) -> n
     """A random displacement history [m_max-1, n, 3] (index m-1 holds dR_{n-m})."""
     rng = np.random.default_rng(seed)
     return rng.normal(0.0, scale, size=(m_max - 1, n, 3))
+
+
+def batch_systems(count: int = 512, seed: int = 4, n_range=(256, 16384), density_range=(0.02, 0.2),
+                  m_choices=(100, 200, 400)) -> list:
+    """Uneven independent systems: N = round(exp U(ln 256, ln 16384)), density
+    exp U(ln 0.02, ln 0.2), m_max drawn from {100, 200, 400}; kernels as the
+    4096-particle workload (tau_s = 0.5, tau_p = 0.3, dt = 0.005, r_c = 2);
+    seed of system k is seed * 100000 + k."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        n = int(round(math.exp(rng.uniform(math.log(n_range[0]), math.log(n_range[1])))))
+        rho = math.exp(rng.uniform(math.log(density_range[0]), math.log(density_range[1])))
+        m = int(rng.choice(m_choices))
+        out.append(Workload(f"batch{k}_n{n}_m{m}", n=n, box=box_for_density(n, rho), m_max=m, dt=0.005,
+                            r_c=2.0, tau_s=0.5, tau_p=0.3, steps=1, seed=seed * 100000 + k))
+    return out
+
+
+@dataclasses.dataclass(frozen=True)
+class Request:
+    arrival: float  # seconds after the start of the trace
+    w: Workload
+    steps: int
+
+
+def serve_trace(count: int = 1000, rate: float = 50.0, seed: int = 5, n_range=(512, 65536),
+                density_range=(0.02, 0.2), m_range=(64, 400), step_range=(2000, 20000)) -> list:
+    """Poisson arrivals at `rate` per second of requests with N log-uniform in
+    [512, 65536], density log-uniform in [0.02, 0.2], m_max uniform in
+    [64, 400], steps uniform in [2000, 20000]; kernels as batch_systems."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    for k in range(count):
+        t += rng.exponential(1.0 / rate)
+        n = int(round(math.exp(rng.uniform(math.log(n_range[0]), math.log(n_range[1])))))
+        rho = math.exp(rng.uniform(math.log(density_range[0]), math.log(density_range[1])))
+        m = int(rng.integers(m_range[0], m_range[1] + 1))
+        steps = int(rng.integers(step_range[0], step_range[1] + 1))
+        w = Workload(f"req{k}_n{n}_m{m}", n=n, box=box_for_density(n, rho), m_max=m, dt=0.005, r_c=2.0,
+                     tau_s=0.5, tau_p=0.3, steps=steps, seed=seed * 100000 + k)
+        out.append(Request(t, w, steps))
+    return out
