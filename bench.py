@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=60,
                     help="requests of the serving trace summarised in the headline line (0: none)")
+    ap.add_argument("--graph-form", default="conditional", choices=["conditional", "gated"],
+                    help="gated: rebuild kernels gated on the device instead of a conditional graph node "
+                         "(every graph node a plain kernel, which per-kernel profilers can capture)")
     ap.add_argument("--hist", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--kahan", action="store_true")
     ap.add_argument("--reference-seconds", type=float, default=120.0)
@@ -425,7 +428,8 @@ def main():
     pos, vel = inputs.initial_state(w, seed=w.seed + rank)
     vacf = dict(vacf_len=w.m_max, vacf_stride=max(1, w.m_max // 10), vacf_burnin=2 * w.m_max)
     common = dict(n=w.n, box=w.box, mass=w.mass, kT=w.kT, dt=w.dt, m_max=w.m_max, r_c=w.r_c, A_cons=w.A_cons,
-                  seed=w.seed + rank, hist_dtype=args.hist, kahan=args.kahan, **vacf)
+                  seed=w.seed + rank, hist_dtype=args.hist, kahan=args.kahan,
+                  use_graphs=2 if args.graph_form == "gated" else 1, **vacf)
     sim = GLD(pos=pos, vel=vel, **common)
     sim.set_kernels(ks, g=g, f=f, dr=dr)
     T = 64

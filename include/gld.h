@@ -84,7 +84,11 @@ typedef struct gld_params {
     int64_t vacf_burnin; /* first origin time; < 0 selects 2 m_max                  */
     int32_t noise_block; /* steps of F^R produced per noise launch (0 = 64)          */
     int32_t psd_clamp;   /* 1: clamp negative noise modes to 0 instead of failing    */
-    int32_t use_graphs;  /* 1 (default): replay steps from a captured CUDA graph     */
+    int32_t use_graphs;  /* 1 (default): replay steps from a captured CUDA graph
+                          * whose list rebuild is a conditional node; 2: the same
+                          * graph with device-gated rebuild kernels instead (every
+                          * node a plain kernel, e.g. for per-kernel profilers);
+                          * 0: launch every kernel from the host              */
     const int32_t* order; /* optional [n]: internal storage order (see gld_get_order) */
     void* stream;        /* cudaStream_t for all work of this context                */
     gld_alloc_fn alloc;  /* optional device allocator (NULL: cudaMalloc)             */

@@ -192,7 +192,8 @@ class GLD:
         p.hist_dtype = HIST_BF16 if hist_dtype in ("bf16", HIST_BF16) else HIST_F32
         p.kahan = int(bool(kahan))
         p.vacf_len, p.vacf_stride, p.vacf_burnin = int(vacf_len), int(vacf_stride), int(vacf_burnin)
-        p.noise_block, p.psd_clamp, p.use_graphs = int(noise_block), int(bool(psd_clamp)), int(bool(use_graphs))
+        p.noise_block, p.psd_clamp = int(noise_block), int(bool(psd_clamp))
+        p.use_graphs = int(use_graphs) if not isinstance(use_graphs, bool) else int(use_graphs)
         self.stream = _current_stream() if stream is None else int(stream)
         p.stream = self.stream
         self._alloc = _TorchAllocator() if torch_allocator else None

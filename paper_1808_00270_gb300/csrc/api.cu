@@ -261,7 +261,7 @@ bool capture_graph(gld_ctx* c)
     if (c->gexec) return true;
     if (c->graph_failed) return false;
     // conditional rebuild first; the gated kernels are the fallback
-    if (capture_graph_mode(c, true)) {
+    if (c->prm.use_graphs != 2 && capture_graph_mode(c, true)) {
         c->graph_mode = 2;
         return true;
     }
@@ -274,6 +274,9 @@ bool capture_graph(gld_ctx* c)
 }
 
 int clamp_block(int) { return kMaxNoiseBlock; }  // the filter produces 64-step blocks
+
+// Particle blocks of the VACF grid (each of its rows of origin groups).
+int vacf_blocks(int n, int) { return std::max(1, std::min((n + 255) / 256, kVacfMaxBlocks)); }
 
 }  // namespace
 
@@ -364,14 +367,14 @@ size_t ctx_bytes_needed(const gld_params* p, int Q, int Qs, int nr, int num_sms)
     const size_t np = P.n_pad, n3 = 3 * np;
     const size_t elem = P.hist_bf16 ? 2 : 4;
     const int chunks = (ncells + 511) / 512;
-    const int vacf_gx = std::max(1, std::min((P.n + 255) / 256, 2 * num_sms));
+    const int vacf_gx = vacf_blocks(P.n, num_sms);
     const int nt = Q + Qs, nrr = nt > 0 ? nr : 2;
     const size_t sizes[] = {
         sizeof(Ctrl), 16 * np, 16 * np, 16 * np, 16 * np, 4 * (size_t)P.maxnb * np, 4 * np, 4 * np,
         16 * np, 16 * np, 16 * np, 16 * np, 16 * np, elem * n3 * P.H, 4 * (size_t)kMaxAcc * n3,
         4 * (size_t)P.T * n3, 4 * (size_t)P.lw * n3, 4 * ((size_t)ncells + 1), 4 * (size_t)ncells,
         4 * (size_t)ncells, 4 * np, 4 * (size_t)chunks, 4 * (size_t)chunks,
-        16 * (size_t)std::max(P.n_os, 1) * P.n, 8 * (size_t)std::max(P.n_os, 1) * vacf_gx,
+        16 * (size_t)std::max(P.n_os, 1) * P.n, 4 * (size_t)std::max(P.n_os, 1) * vacf_gx,
         8 * (size_t)std::max(P.vacf_len, 1), 8 * (size_t)std::max(P.vacf_len, 1), 8, 4,
         4 * (size_t)fir_taps_len(P.H), 4 * (size_t)kMaxAcc * P.m_max, 4 * 2 * (size_t)kMaxQ,
         8 * (size_t)P.m_max, 8 * (size_t)P.m_max, 8 * (size_t)P.m_max, 8 * 2 * (size_t)P.m_max, 8 * 4, 4,
@@ -405,6 +408,7 @@ gld_status gld_create(const gld_params* p, const double* pos, const double* vel,
     if (!out) return GLD_E_INVAL;
     *out = nullptr;
     if (!p || !pos || !vel) return GLD_E_INVAL;
+    if (p->use_graphs < 0 || p->use_graphs > 2) return GLD_E_INVAL;
     if (p->n < 1 || p->m_max < 2 || p->m_max > 4096 || !(p->box > 0) || !(p->mass > 0) || !(p->dt > 0) ||
         !(p->r_c > 0) || p->r_c > 0.5 * p->box || p->kT < 0 || p->r_c_min < 0 || p->skin < 0 ||
         (p->hist_dtype != GLD_HIST_F32 && p->hist_dtype != GLD_HIST_BF16) || p->vacf_len < 0 ||
@@ -497,9 +501,9 @@ gld_status gld_create(const gld_params* p, const double* pos, const double* vel,
     B.cell_next = alloc_n<int>(c, np, ok);
     B.chunk_sum = alloc_n<int>(c, chunks, ok);
     B.chunk_off = alloc_n<int>(c, chunks, ok);
-    B.vacf_gx = std::max(1, std::min((P.n + 255) / 256, 2 * c->num_sms));
+    B.vacf_gx = vacf_blocks(P.n, c->num_sms);
     B.vorig = alloc_n<float4>(c, (size_t)std::max(P.n_os, 1) * P.n, ok);
-    B.vpartial = alloc_n<double>(c, (size_t)std::max(P.n_os, 1) * B.vacf_gx, ok);
+    B.vpartial = alloc_n<float>(c, (size_t)std::max(P.n_os, 1) * B.vacf_gx, ok);
     B.csum = alloc_n<double>(c, std::max(P.vacf_len, 1), ok);
     B.ccnt = alloc_n<long long>(c, std::max(P.vacf_len, 1), ok);
     B.norig = alloc_n<long long>(c, 1, ok);
@@ -820,8 +824,9 @@ gld_status gld_set_step(gld_ctx* c, int64_t step)
     if (!c || step < 0) return GLD_E_INVAL;
     GLD_TRY(sync_and_check(c));
     c->host_step = step;
-    long long s = step;
-    GLD_CUDA(c, cudaMemcpyAsync(&c->B.ctrl->step, &s, sizeof(s), cudaMemcpyHostToDevice, c->st));
+    long long s[2] = {step, step % c->P.H};
+    GLD_CUDA(c, cudaMemcpyAsync(&c->B.ctrl->step, &s[0], sizeof(long long), cudaMemcpyHostToDevice, c->st));
+    GLD_CUDA(c, cudaMemcpyAsync(&c->B.ctrl->hslot, &s[1], sizeof(long long), cudaMemcpyHostToDevice, c->st));
     GLD_TRY(invalidate_noise(c));
     c->last_fr_row = -1;
     return sync_and_check(c);
@@ -1076,9 +1081,12 @@ gld_status batch_plan(gld_batch* b, int schedule)
 {
     const auto& ms = b->members;
     std::vector<SysDesc> desc(ms.size());
-    std::vector<Tile> pair, part, cell, vacf, conv, fir;
+    std::vector<Tile> pair, part, cell, vacf, conv, fir, cf;
     BatchPlan& P = b->plan;
     P = BatchPlan{};
+    P.pair_fast = 1;
+    for (const gld_ctx* c : ms) P.pair_fast &= (c->P.Q == 1 && c->P.Qs == 0) ? 1 : 0;
+    const int pair_per_block = P.pair_fast ? kBatchPairBlock / kBatchPairLanes : kBatchPairBlock;
     for (size_t m = 0; m < ms.size(); ++m) {
         gld_ctx* c = ms[m];
         SysDesc& d = desc[m];
@@ -1091,14 +1099,16 @@ gld_status batch_plan(gld_batch* b, int schedule)
         d.k0 = (uint32_t)c->prm.seed;
         d.k1 = (uint32_t)(c->prm.seed >> 32);
         d.int2ext = c->d_int2ext;
-        d.nb_pair = (c->P.n + kBatchPairBlock - 1) / kBatchPairBlock;
+        d.nb_pair = (c->P.n + pair_per_block - 1) / pair_per_block;
         d.nb_part = (c->P.n + kBatchPartBlock - 1) / kBatchPartBlock;
+        d.nb_cf = (int)(((long long)c->P.n * kBatchCforceLanes + kBatchCforceBlock - 1) / kBatchCforceBlock);
         d.nb_cell = (c->B.ncells + kBatchCellChunk - 1) / kBatchCellChunk;
         d.nb_vacf = c->P.vacf_len > 0 ? c->B.vacf_gx : 0;
         d.nb_conv = 0;
         d.nb_fir = (int)((3LL * c->P.n_pad + kBatchFirStreams - 1) / kBatchFirStreams);
         for (int k = 0; k < d.nb_pair; ++k) pair.push_back(Tile{(int)m, k, d.nb_pair, 0});
         for (int k = 0; k < d.nb_part; ++k) part.push_back(Tile{(int)m, k, d.nb_part, 0});
+        for (int k = 0; k < d.nb_cf; ++k) cf.push_back(Tile{(int)m, k, d.nb_cf, 0});
         for (int k = 0; k < d.nb_cell; ++k) cell.push_back(Tile{(int)m, k, d.nb_cell, 0});
         for (int k = 0; k < d.nb_vacf; ++k) vacf.push_back(Tile{(int)m, k, d.nb_vacf, 0});
         for (int k = 0; k < d.nb_fir; ++k) fir.push_back(Tile{(int)m, k, d.nb_fir, 0});
@@ -1108,6 +1118,7 @@ gld_status batch_plan(gld_batch* b, int schedule)
         P.vacf_no = std::max(P.vacf_no, c->P.n_os);
     }
     conv_tiles(ms, schedule < 0 ? 0 : schedule, conv, &P.conv_block);
+
     if (!ms.empty()) {
         P.nacc = ms[0]->P.nacc;
         P.bf16 = ms[0]->P.hist_bf16;
@@ -1121,7 +1132,8 @@ gld_status batch_plan(gld_batch* b, int schedule)
         return off;
     };
     const size_t o_pair = append(pair, &P.n_pair), o_part = append(part, &P.n_part), o_cell = append(cell, &P.n_cell),
-                 o_vacf = append(vacf, &P.n_vacf), o_conv = append(conv, &P.n_conv), o_fir = append(fir, &P.n_fir);
+                 o_vacf = append(vacf, &P.n_vacf), o_conv = append(conv, &P.n_conv), o_fir = append(fir, &P.n_fir),
+                 o_cf = append(cf, &P.n_cf);
     b->snap = desc;
     // One upload of descriptors and tiles through pinned staging, ordered on
     // the batch's stream after the blocks already queued (which keep reading
@@ -1164,6 +1176,7 @@ gld_status batch_plan(gld_batch* b, int schedule)
     P.vacf = t0 + o_vacf;
     P.conv = t0 + o_conv;
     P.fir = t0 + o_fir;
+    P.cf = t0 + o_cf;
     return GLD_OK;
 }
 

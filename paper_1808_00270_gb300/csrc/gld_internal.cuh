@@ -15,6 +15,7 @@ namespace gld {
 
 constexpr int kMaxQ = 4;            // separable terms per pair-kernel family
 constexpr int kMaxAcc = 1 + 2 * kMaxQ;
+constexpr int kVacfMaxBlocks = 256;  // particle blocks of the VACF grid at most
 constexpr int kMaxNoiseBlock = 64;  // register-resident outputs per FIR thread
 
 // Latched device error bits.
@@ -34,6 +35,11 @@ struct Ctrl {
     int rebuild;           // != 0: rebuild cells and neighbour lists after this step's move
     int pad_;
     long long rebuilds;    // neighbour-list builds so far
+    long long hslot;       // step mod H: the history slot this step writes
+    // VACF schedule at the step the next VACF kernel sees (written by the
+    // pair kernel): active, origins in flight, slot of the newest origin, a
+    // new origin at this step, lag of the newest origin
+    int vacf_on, vacf_nact, vacf_slot0, vacf_origin, vacf_lag0, pad2_;
 };
 
 // Everything a step kernel needs, passed by value.
@@ -177,7 +183,7 @@ __device__ inline void for_each_in_stencil(const float4 pi, const int id, const 
 }
 
 // Visits every j != i with r_ij < r_c from i's neighbour list (a superset built
-// with r_c + skin, sorted by id): f(j, dx, dy, dz, r2) with d = R_i - R_j.
+// with r_c + skin, in stencil order): f(j, dx, dy, dz, r2) with d = R_i - R_j.
 // The distance test is the same as the stencil's, so the pairs are the same.
 template <class F>
 __device__ inline void for_each_listed(const float4 pi, const int k, const int* __restrict__ nbr,

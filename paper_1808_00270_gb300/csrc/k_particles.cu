@@ -10,7 +10,7 @@
 //   cell build + nbr_build (only when a rebuild was requested): cell list at
 //                         R_{n+1} (per-cell linked lists, chunked scan, cells
 //                         filled in id order), then per particle the ids within
-//                         r_c + skin, sorted by id.
+//                         r_c + skin in the (fixed) stencil traversal order.
 //   cforce                F^C_{n+1} = sum_j 2A/r_c (1 - r/r_c) e_ij and the
 //                         rest of the velocity update; advances n.
 //   vacf                  FP64 accumulation of <V(t0+tau) V(t0)> (Sec. III A).
@@ -31,6 +31,8 @@ namespace gld {
 namespace {
 
 constexpr int kPairThreads = kBatchPairBlock;
+constexpr int kPairLanes = kBatchPairLanes;  // lanes per particle in the one-term pair kernel
+constexpr int kCforceLanes = kBatchCforceLanes;  // lanes per particle in the F^C kernel
 constexpr int kCellThreads = kBatchCellChunk;
 constexpr int kThreads = kBatchPartBlock;
 static_assert(kBatchVacfBlock == kThreads, "vacf blocks share the particle block size");
@@ -40,6 +42,30 @@ __device__ __forceinline__ float dot3(float ax, float ay, float az, float bx, fl
     return fmaf(ax, bx, fmaf(ay, by, az * bz));
 }
 
+// The VACF kernel's view of step t (once per step, by one thread): origins
+// start at vacf_burnin and every vacf_stride steps; the origin of age j is
+// active while its lag t - t_j is below vacf_len.
+__device__ __forceinline__ void vacf_schedule(const StepParams& P, Ctrl* __restrict__ ctrl, long long t)
+{
+    if (t < P.vacf_burnin) {
+        ctrl->vacf_on = 0;
+        return;
+    }
+    const long long rel = t - P.vacf_burnin;
+    const long long o_now = rel / P.vacf_stride;
+    const int lag0 = (int)(rel - o_now * P.vacf_stride);
+    int n_act = 0;
+    for (int j = 0; j < P.n_os; ++j)
+        if (o_now - j >= 0 && lag0 + (long long)j * P.vacf_stride < P.vacf_len) n_act = j + 1;
+    ctrl->vacf_on = 1;
+    ctrl->vacf_nact = n_act;
+    ctrl->vacf_slot0 = (int)(o_now % P.n_os);
+    ctrl->vacf_origin = lag0 == 0;
+    ctrl->vacf_lag0 = lag0;
+}
+
+// FAST: exactly one separable pair term and no self-difference term.
+template <bool FAST>
 __device__ __forceinline__ void pair_force_integrate_body(const StepParams& P, Ctrl* __restrict__ ctrl, const float4* __restrict__ pos,
                          const int* __restrict__ perm, const int* __restrict__ nbr, const int* __restrict__ nbr_cnt,
                          const float4* __restrict__ vel, const float4* __restrict__ fc, const float* __restrict__ conv,
@@ -49,17 +75,21 @@ __device__ __forceinline__ void pair_force_integrate_body(const StepParams& P, C
                          const float4* __restrict__ disp_build, int blk, int nblk)
 {
     unsigned* err = &ctrl->err;
-    const int k = blk * blockDim.x + threadIdx.x;
-    if (k >= P.n) return;
+    // FAST: kPairLanes consecutive lanes share a particle and split its list
+    constexpr int LANES = FAST ? kPairLanes : 1;
+    const int k = (blk * blockDim.x + threadIdx.x) / LANES;
+    const int lr = threadIdx.x & (LANES - 1);
+    if (k >= P.n) return;  // uniform over the lanes of a particle
     const long long n = ctrl->step;
     const long long np = P.n_pad;
     const int id = k;  // particles in storage (Morton) order; lists are by id
+    if (blk == 0 && threadIdx.x == 0 && P.vacf_len > 0) vacf_schedule(P, ctrl, n + 1);
     const float4 pi = pos[id];
     const float4 vi = vel[id];
 
-    float ps[kMaxQ][3];
+    float ps[FAST ? 1 : kMaxQ][3];
 #pragma unroll
-    for (int q = 0; q < kMaxQ; ++q) {
+    for (int q = 0; q < (FAST ? 1 : kMaxQ); ++q) {
         if (q < P.Qs) {
             const float* p = conv + (size_t)(1 + P.Q + q) * 3 * np + id;
             ps[q][0] = p[0];
@@ -71,7 +101,67 @@ __device__ __forceinline__ void pair_force_integrate_body(const StepParams& P, C
     }
     float f0x = 0.f, f0y = 0.f, f0z = 0.f;  // instantaneous (m = 0) pair terms
     float fhx = 0.f, fhy = 0.f, fhz = 0.f;  // history pair terms (times -1, before 1/dt)
-    if (P.Q + P.Qs > 0) {
+    if (FAST) {
+        // one separable pair term (the common case): the neighbour's V_j and
+        // P_j are fetched together with its position, four candidates at a
+        // time, so that one memory latency covers the whole batch; the
+        // arithmetic is the general loop's below, term for term
+        const float* pj0 = conv + 3 * (size_t)np;
+        const float g00 = __ldg(g0);
+        const int cnt = nbr_cnt[id];
+        auto term = [&](int jd, float4 pj, float4 vj, float qx, float qy, float qz) {
+            const float dx = min_image(pi.x, pj.x, P.box, P.half_box);
+            const float dy = min_image(pi.y, pj.y, P.box, P.half_box);
+            const float dz = min_image(pi.z, pj.z, P.box, P.half_box);
+            const float r2 = dist2(dx, dy, dz);
+            if (!(r2 < P.rc2)) return;
+            const float r = sqrtf(r2);
+            const float inv_r = 1.0f / r;
+            const float ex = dx * inv_r, ey = dy * inv_r, ez = dz * inv_r;
+            const float x = fmaxf(r, P.rc_min) * P.inv_dr;
+            const float evj = dot3(ex, ey, ez, vj.x, vj.y, vj.z);
+            const float fq = table_at(ftab, P.nr, x);
+            const float epj = dot3(ex, ey, ez, qx, qy, qz);
+            const float inst = fmaf(fq * g00, evj, 0.f);
+            const float hist = fmaf(fq, epj, 0.f);
+            f0x = fmaf(-inst, ex, f0x); f0y = fmaf(-inst, ey, f0y); f0z = fmaf(-inst, ez, f0z);
+            fhx = fmaf(-hist, ex, fhx); fhy = fmaf(-hist, ey, fhy); fhz = fmaf(-hist, ez, fhz);
+        };
+        // lane lr takes the entries lr, lr + LANES, ...: four of them per
+        // round with all their loads in flight together
+        int base = lr;
+        for (; base + 3 * LANES < cnt; base += 4 * LANES) {
+            int j[4];
+            float4 pj[4], vj[4];
+            float qx[4], qy[4], qz[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) j[u] = __ldg(nbr + (size_t)(base + u * LANES) * P.n_pad + id);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                pj[u] = __ldg(pos + j[u]);
+                vj[u] = __ldg(vel + j[u]);
+                qx[u] = __ldg(pj0 + j[u]);
+                qy[u] = __ldg(pj0 + np + j[u]);
+                qz[u] = __ldg(pj0 + 2 * np + j[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) term(j[u], pj[u], vj[u], qx[u], qy[u], qz[u]);
+        }
+        for (; base < cnt; base += LANES) {
+            const int jd = __ldg(nbr + (size_t)base * P.n_pad + id);
+            term(jd, __ldg(pos + jd), __ldg(vel + jd), __ldg(pj0 + jd), __ldg(pj0 + np + jd), __ldg(pj0 + 2 * np + jd));
+        }
+        if (LANES > 1) {  // sum over the lanes of the particle (same result in each)
+            const unsigned grp = ((1u << LANES) - 1u) << ((threadIdx.x & 31) & ~(LANES - 1));
+#pragma unroll
+            for (int o = 1; o < LANES; o <<= 1) {
+                f0x += __shfl_xor_sync(grp, f0x, o); f0y += __shfl_xor_sync(grp, f0y, o);
+                f0z += __shfl_xor_sync(grp, f0z, o); fhx += __shfl_xor_sync(grp, fhx, o);
+                fhy += __shfl_xor_sync(grp, fhy, o); fhz += __shfl_xor_sync(grp, fhz, o);
+            }
+        }
+        if (lr != 0) return;  // one lane finishes the particle
+    } else if (!FAST && P.Q + P.Qs > 0) {
         for_each_listed(pi, id, nbr, nbr_cnt[id], P.n_pad, pos, P, [&](int jd, float dx, float dy, float dz, float r2) {
             const float r = sqrtf(r2);
             const float inv_r = 1.0f / r;
@@ -118,7 +208,7 @@ __device__ __forceinline__ void pair_force_integrate_body(const StepParams& P, C
     const float dRx = fmaf(P.pos_f, fci.x + fdx + frx, P.pos_v * vi.x);
     const float dRy = fmaf(P.pos_f, fci.y + fdy + fry, P.pos_v * vi.y);
     const float dRz = fmaf(P.pos_f, fci.z + fdz + frz, P.pos_v * vi.z);
-    const long long slot = n % P.H;
+    const long long slot = ctrl->hslot;  // n mod H
     if (P.hist_bf16) {
         __nv_bfloat16* h = (__nv_bfloat16*)ring + (size_t)slot * 3 * np + id;
         h[0] = __float2bfloat16_rn(dRx);
@@ -150,6 +240,7 @@ __device__ __forceinline__ void pair_force_integrate_body(const StepParams& P, C
     }
 }
 
+template <bool FAST>
 __global__ void __launch_bounds__(kPairThreads) pair_force_integrate(const StepParams P, Ctrl* __restrict__ ctrl, const float4* __restrict__ pos,
                          const int* __restrict__ perm, const int* __restrict__ nbr, const int* __restrict__ nbr_cnt,
                          const float4* __restrict__ vel, const float4* __restrict__ fc, const float* __restrict__ conv,
@@ -158,7 +249,7 @@ __global__ void __launch_bounds__(kPairThreads) pair_force_integrate(const StepP
                          float4* __restrict__ vhalf, float4* __restrict__ fd_out, float4* __restrict__ disp,
                          const float4* __restrict__ disp_build)
 {
-    pair_force_integrate_body(P, ctrl, pos, perm, nbr, nbr_cnt, vel, fc, conv, frblock, ftab, g0, ring, pos_next, vhalf, fd_out, disp, disp_build, blockIdx.x, gridDim.x);
+    pair_force_integrate_body<FAST>(P, ctrl, pos, perm, nbr, nbr_cnt, vel, fc, conv, frblock, ftab, g0, ring, pos_next, vhalf, fd_out, disp, disp_build, blockIdx.x, gridDim.x);
 }
 
 // ---- cell list --------------------------------------------------------------
@@ -281,7 +372,7 @@ __global__ void __launch_bounds__(kCellThreads) cell_fill(const StepParams P, co
     cell_fill_body(P, gate, ncells, pos, count, head, next, chunk_off, cell_start, pos_sorted, blockIdx.x, gridDim.x);
 }
 
-// Per particle, in cell order: the ids within r_c + skin, sorted by id.
+// Per particle, in cell order: the ids within r_c + skin in traversal order.
 __device__ __forceinline__ void nbr_build_body(const StepParams& P, Ctrl* __restrict__ ctrl, const float4* __restrict__ pos_sorted,
               const int* __restrict__ cell_start, int* __restrict__ nbr, int* __restrict__ nbr_cnt,
               int* __restrict__ perm, const float4* __restrict__ disp, float4* __restrict__ disp_build, int blk, int nblk)
@@ -294,18 +385,11 @@ __device__ __forceinline__ void nbr_build_body(const StepParams& P, Ctrl* __rest
     const int id = __float_as_int(pi.w);
     const int stride = P.n_pad, cap = P.maxnb;
     int c = 0;
+    // the traversal order is fixed (stencil cells in order, each cell's
+    // particles by increasing id), so the lists and every sum over them are
+    // reproducible without sorting
     for_each_in_stencil(pi, id, pos_sorted, cell_start, P, P.rl2, [&](int jd, float, float, float, float) {
-        if (c < cap) {
-            // insertion by id into the list of particle id
-            int p = c;
-            while (p > 0) {
-                const int q = nbr[(size_t)(p - 1) * stride + id];
-                if (q < jd) break;
-                nbr[(size_t)p * stride + id] = q;
-                --p;
-            }
-            nbr[(size_t)p * stride + id] = jd;
-        }
+        if (c < cap) nbr[(size_t)c * stride + id] = jd;
         ++c;
     });
     if (c > cap) {
@@ -333,25 +417,55 @@ __device__ __forceinline__ void cforce_body(const StepParams& P, Ctrl* __restric
            const int* __restrict__ nbr_cnt, const float4* __restrict__ vhalf, float4* __restrict__ vel,
            float4* __restrict__ fc, int blk, int nblk)
 {
-    const int k = blk * blockDim.x + threadIdx.x;
-    if (k == 0) ctrl->rebuild = 0;  // the lists are current for R_{n+1}
-    if (k < P.n) {
+    // kCforceLanes consecutive lanes share a particle and split its list
+    const int k = (blk * blockDim.x + threadIdx.x) / kCforceLanes;
+    const int lr = threadIdx.x & (kCforceLanes - 1);
+    if (blk == 0 && threadIdx.x == 0) ctrl->rebuild = 0;  // the lists are current for R_{n+1}
+    if (k < P.n) {  // uniform over the lanes of a particle
         const int id = k;
         const float4 pi = pos_next[id];
-        pos[id] = pi;
+        const int cnt = nbr_cnt[id];
         float fx = 0.f, fy = 0.f, fz = 0.f;
-        for_each_listed(pi, id, nbr, nbr_cnt[id], P.n_pad, pos_next, P, [&](int, float dx, float dy, float dz, float r2) {
-            const float r = sqrtf(r2);
-            // -dU/dr e_ij with U = A (1 - r/r_c)^2, e_ij = (R_i - R_j)/r
-            const float s = P.fc_mag * (1.0f - r * P.inv_rc) / r;
-            fx = fmaf(s, dx, fx);
-            fy = fmaf(s, dy, fy);
-            fz = fmaf(s, dz, fz);
-        });
-        fc[id] = make_float4(fx, fy, fz, 0.f);
-        if (STEP) {
-            const float4 vh = vhalf[id];
-            vel[id] = make_float4(fmaf(P.vf_fc, fx, vh.x), fmaf(P.vf_fc, fy, vh.y), fmaf(P.vf_fc, fz, vh.z), 0.f);
+        for (int base = lr; base < cnt; base += 4 * kCforceLanes) {
+            int j[4];
+            float4 pj[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int s = base + u * kCforceLanes;
+                j[u] = s < cnt ? __ldg(nbr + (size_t)s * P.n_pad + id) : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) pj[u] = __ldg(pos_next + (j[u] < 0 ? id : j[u]));
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float dx = min_image(pi.x, pj[u].x, P.box, P.half_box);
+                const float dy = min_image(pi.y, pj[u].y, P.box, P.half_box);
+                const float dz = min_image(pi.z, pj[u].z, P.box, P.half_box);
+                const float r2 = dist2(dx, dy, dz);
+                if (j[u] >= 0 && r2 < P.rc2) {
+                    const float r = sqrtf(r2);
+                    // -dU/dr e_ij with U = A (1 - r/r_c)^2, e_ij = (R_i - R_j)/r
+                    const float sc = P.fc_mag * (1.0f - r * P.inv_rc) / r;
+                    fx = fmaf(sc, dx, fx);
+                    fy = fmaf(sc, dy, fy);
+                    fz = fmaf(sc, dz, fz);
+                }
+            }
+        }
+        const unsigned grp = ((1u << kCforceLanes) - 1u) << ((threadIdx.x & 31) & ~(kCforceLanes - 1));
+#pragma unroll
+        for (int o = 1; o < kCforceLanes; o <<= 1) {
+            fx += __shfl_xor_sync(grp, fx, o);
+            fy += __shfl_xor_sync(grp, fy, o);
+            fz += __shfl_xor_sync(grp, fz, o);
+        }
+        if (lr == 0) {
+            pos[id] = pi;
+            fc[id] = make_float4(fx, fy, fz, 0.f);
+            if (STEP) {
+                const float4 vh = vhalf[id];
+                vel[id] = make_float4(fmaf(P.vf_fc, fx, vh.x), fmaf(P.vf_fc, fy, vh.y), fmaf(P.vf_fc, fz, vh.z), 0.f);
+            }
         }
     }
     if (STEP) {
@@ -360,6 +474,7 @@ __device__ __forceinline__ void cforce_body(const StepParams& P, Ctrl* __restric
             __threadfence();
             if (atomicAdd(&ctrl->done_cforce, 1u) == nblk - 1) {
                 ctrl->step += 1;
+                ctrl->hslot = ctrl->hslot + 1 == P.H ? 0 : ctrl->hslot + 1;
                 ctrl->done_cforce = 0u;
                 __threadfence();
             }
@@ -378,6 +493,8 @@ __global__ void __launch_bounds__(kThreads) cforce(const StepParams P, Ctrl* __r
 
 // ---- velocity autocorrelation ------------------------------------------------
 constexpr int kVacfMaxOrigins = 32;  // origins in flight (vacf_len / vacf_stride)
+constexpr int kVacfGroup = 4;        // origins per block row of the VACF grid
+static_assert(kVacfMaxBlocks % 32 == 0, "VACF block count");
 
 __device__ __forceinline__ float warp_sum_f(float v)
 {
@@ -386,90 +503,108 @@ __device__ __forceinline__ float warp_sum_f(float v)
     return v;
 }
 
-// Each thread dots its particles' velocities with every active origin's
-// stored velocity (age j = 0 is the newest) into per-origin registers; warp
-// sums in FP32, block and grid sums in FP64 in a fixed order (the last block
-// to finish adds the per-block partials).
-template <int NO>
-__device__ __forceinline__ void vacf_body(const StepParams& P, const Ctrl* __restrict__ ctrl, const float4* __restrict__ vel,
-         float4* __restrict__ vorig, double* __restrict__ partial, double* __restrict__ csum,
-         long long* __restrict__ ccnt, long long* __restrict__ norig, unsigned* __restrict__ done, int blk, int nblk)
+// Knuth's two-sum: s + e equals a + b exactly (no contraction: additions only).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
 {
-    const long long t = ctrl->step;  // V_t was completed by the previous kernel
-    if (t < P.vacf_burnin) return;  // uniform over the grid
-    const long long rel = t - P.vacf_burnin;
-    const long long o_now = rel / P.vacf_stride;
-    const bool is_origin = (rel % P.vacf_stride) == 0;
-    int n_act = 0;
-    for (int jj = 0; jj < P.n_os; ++jj) {
-        const long long o = o_now - jj;
-        if (o >= 0 && rel - o * (long long)P.vacf_stride < P.vacf_len) n_act = jj + 1;
-    }
-    // slot of age j: (o_now - j) mod n_os
-    const int slot0 = (int)(o_now % P.n_os);
-    float acc[NO];
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// (hi, lo) += (bhi, blo) in double-float arithmetic on the FP32 pipes.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float bhi, float blo)
+{
+    float s, e;
+    two_sum(hi, bhi, s, e);
+    e += lo + blo;
+    hi = s + e;
+    lo = e - (hi - s);
+}
+
+// Block (x, y) of the grid (gx <= 256) takes the particles x*256 + tid,
+// x*256 + tid + gx*256, ... and
+// the origins of ages 4y .. 4y+3 (age j = 0 is the newest): dot products in
+// FP32 registers, warp and block sums in FP32 (at most 256 x a few terms);
+// the last block to finish adds the per-block partials of every origin in
+// double-float in a fixed order and accumulates C(lag) in FP64 (GB300's FP64
+// pipes are slow, so FP64 is kept to one addition per origin and step).
+__device__ __forceinline__ void vacf_body(const StepParams& P, const Ctrl* __restrict__ ctrl,
+                                          const float4* __restrict__ vel, float4* __restrict__ vorig,
+                                          float* __restrict__ partial, double* __restrict__ csum,
+                                          long long* __restrict__ ccnt, long long* __restrict__ norig,
+                                          unsigned* __restrict__ done, int blk, int nblk, int grp, int ngrp)
+{
+    // V_t was completed by the previous kernel; the pair kernel of this step
+    // wrote the schedule of t
+    if (!ctrl->vacf_on) return;  // uniform over the grid
+    const int n_act = ctrl->vacf_nact;
+    const bool is_origin = ctrl->vacf_origin != 0;
+    const int slot0 = ctrl->vacf_slot0;  // slot of age j: (slot0 - j) mod n_os
+    const int lag0 = ctrl->vacf_lag0;
+    const int q0 = grp * kVacfGroup;
+    float acc[kVacfGroup];
 #pragma unroll
-    for (int q = 0; q < NO; ++q) acc[q] = 0.f;
-    for (int i = blk * blockDim.x + threadIdx.x; i < P.n; i += nblk * blockDim.x) {
-        const float4 v = vel[i];
-        float4 w[NO];
+    for (int q = 0; q < kVacfGroup; ++q) acc[q] = 0.f;
+    if (q0 < n_act || (grp == 0 && is_origin)) {
+        for (int i = blk * blockDim.x + threadIdx.x; i < P.n; i += nblk * blockDim.x) {
+            const float4 v = vel[i];
+            float4 w[kVacfGroup];
 #pragma unroll
-        for (int q = 0; q < NO; ++q) {
-            int sl = slot0 - q;
-            sl = sl < 0 ? sl + P.n_os : sl;
-            w[q] = (q < n_act && !(q == 0 && is_origin)) ? __ldcs(vorig + (size_t)sl * P.n + i) : v;
+            for (int q = 0; q < kVacfGroup; ++q) {
+                const int j = q0 + q;
+                int sl = slot0 - j;
+                sl = sl < 0 ? sl + P.n_os : sl;
+                w[q] = (j < n_act && !(j == 0 && is_origin)) ? __ldcs(vorig + (size_t)sl * P.n + i) : v;
+            }
+#pragma unroll
+            for (int q = 0; q < kVacfGroup; ++q)
+                if (q0 + q < n_act) acc[q] = fmaf(v.x, w[q].x, fmaf(v.y, w[q].y, fmaf(v.z, w[q].z, acc[q])));
+            if (grp == 0 && is_origin) vorig[(size_t)slot0 * P.n + i] = v;
         }
-#pragma unroll
-        for (int q = 0; q < NO; ++q)
-            if (q < n_act) acc[q] = fmaf(v.x, w[q].x, fmaf(v.y, w[q].y, fmaf(v.z, w[q].z, acc[q])));
-        if (is_origin) vorig[(size_t)slot0 * P.n + i] = v;
     }
-    __shared__ double wsum[kThreads / 32][NO];
+    __shared__ float wsum[kThreads / 32][kVacfGroup];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int q = 0; q < NO; ++q) {
+    for (int q = 0; q < kVacfGroup; ++q) {
         const float sq = warp_sum_f(acc[q]);
-        if (lane == 0) wsum[warp][q] = (double)sq;
+        if (lane == 0) wsum[warp][q] = sq;
     }
     __syncthreads();
-    if (threadIdx.x < NO && (int)threadIdx.x < n_act) {
-        double sb = 0.0;
+    if (threadIdx.x < kVacfGroup && q0 + (int)threadIdx.x < n_act) {
+        float sb = 0.f;
         for (int w = 0; w < kThreads / 32; ++w) sb += wsum[w][threadIdx.x];
-        partial[(size_t)threadIdx.x * nblk + blk] = sb;
+        partial[(size_t)(q0 + threadIdx.x) * nblk + blk] = sb;
     }
     __shared__ bool last;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        last = atomicAdd(done, 1u) == nblk - 1;
+        last = atomicAdd(done, 1u) == (unsigned)(nblk * ngrp) - 1u;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    // all partials of all origins loaded together, then a fixed-order tree
-    double sg[NO];
+    // warp w takes the origins w, w + 8, ...; lane l the blocks l, l + 32, ...
+    // (all of its loads issued before the first addition)
+    for (int q = warp; q < n_act; q += kThreads / 32) {
+        float v[kVacfMaxBlocks / 32];
 #pragma unroll
-    for (int q = 0; q < NO; ++q) sg[q] = 0.0;
-    for (int b = threadIdx.x; b < (int)nblk; b += blockDim.x)
+        for (int k = 0; k < kVacfMaxBlocks / 32; ++k) {
+            const int b = lane + 32 * k;
+            v[k] = b < nblk ? __ldcg(partial + (size_t)q * nblk + b) : 0.f;
+        }
+        float hi = 0.f, lo = 0.f;
 #pragma unroll
-        for (int q = 0; q < NO; ++q)
-            if (q < n_act) sg[q] += __ldcg(partial + (size_t)q * nblk + b);
+        for (int k = 0; k < kVacfMaxBlocks / 32; ++k)
+            if (lane + 32 * k < nblk) df_add(hi, lo, v[k], 0.f);
 #pragma unroll
-    for (int q = 0; q < NO; ++q) {
-        double v = sg[q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) wsum[warp][q] = v;
-    }
-    __syncthreads();
-    if ((int)threadIdx.x < n_act) {
-        const int jj = threadIdx.x;
-        const long long o = o_now - jj;
-        const long long lg = rel - o * (long long)P.vacf_stride;
-        double t = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) t += wsum[w][jj];
-        if (o >= 0 && lg < P.vacf_len) {
-            csum[lg] += t;
+        for (int o = 16; o > 0; o >>= 1) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, hi, o), l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+            df_add(hi, lo, h2, l2);
+        }
+        if (lane == 0) {
+            const int lg = lag0 + q * P.vacf_stride;  // < vacf_len for q < n_act
+            csum[lg] += (double)hi + (double)lo;
             ccnt[lg] += 1;
         }
     }
@@ -479,12 +614,11 @@ __device__ __forceinline__ void vacf_body(const StepParams& P, const Ctrl* __res
     }
 }
 
-template <int NO>
 __global__ void __launch_bounds__(kThreads) vacf(const StepParams P, const Ctrl* __restrict__ ctrl, const float4* __restrict__ vel,
-         float4* __restrict__ vorig, double* __restrict__ partial, double* __restrict__ csum,
+         float4* __restrict__ vorig, float* __restrict__ partial, double* __restrict__ csum,
          long long* __restrict__ ccnt, long long* __restrict__ norig, unsigned* __restrict__ done)
 {
-    vacf_body<NO>(P, ctrl, vel, vorig, partial, csum, ccnt, norig, done, blockIdx.x, gridDim.x);
+    vacf_body(P, ctrl, vel, vorig, partial, csum, ccnt, norig, done, blockIdx.x, gridDim.x, blockIdx.y, gridDim.y);
 }
 
 // ---- explicit pair lists (checks of the traversals) -------------------------
@@ -550,12 +684,13 @@ __global__ void delay_kernel(unsigned long long ns)
 }
 
 // ---- batch kernels: tile -> member descriptor -> the bodies above ----------
+template <bool FAST>
 __global__ void __launch_bounds__(kPairThreads) b_pair(const SysDesc* __restrict__ D, const Tile* __restrict__ tiles)
 {
     const Tile t = tiles[blockIdx.x];
     const SysDesc& d = D[t.m];
     const ParticleBuffers& B = d.B;
-    pair_force_integrate_body(d.P, B.ctrl, B.pos, B.perm, B.nbr, B.nbr_cnt, B.vel, B.fc, B.conv, B.frblock, B.ftab,
+    pair_force_integrate_body<FAST>(d.P, B.ctrl, B.pos, B.perm, B.nbr, B.nbr_cnt, B.vel, B.fc, B.conv, B.frblock, B.ftab,
                               B.g0, B.ring, B.pos_next, B.vhalf, B.fd, B.disp, B.disp_build, t.b, d.nb_pair);
 }
 
@@ -599,33 +734,34 @@ __global__ void __launch_bounds__(kThreads) b_cforce(const SysDesc* __restrict__
     const Tile t = tiles[blockIdx.x];
     const SysDesc& d = D[t.m];
     const ParticleBuffers& B = d.B;
-    cforce_body<true>(d.P, B.ctrl, B.pos_next, B.pos, B.perm, B.nbr, B.nbr_cnt, B.vhalf, B.vel, B.fc, t.b, d.nb_part);
+    cforce_body<true>(d.P, B.ctrl, B.pos_next, B.pos, B.perm, B.nbr, B.nbr_cnt, B.vhalf, B.vel, B.fc, t.b, d.nb_cf);
 }
 
-template <int NO>
 __global__ void __launch_bounds__(kThreads) b_vacf(const SysDesc* __restrict__ D, const Tile* __restrict__ tiles)
 {
     const Tile t = tiles[blockIdx.x];
     const SysDesc& d = D[t.m];
     const ParticleBuffers& B = d.B;
-    vacf_body<NO>(d.P, B.ctrl, B.vel, B.vorig, B.vpartial, B.csum, B.ccnt, B.norig, B.vdone, t.b, d.nb_vacf);
+    vacf_body(d.P, B.ctrl, B.vel, B.vorig, B.vpartial, B.csum, B.ccnt, B.norig, B.vdone, t.b, d.nb_vacf, blockIdx.y,
+              gridDim.y);
 }
 
 }  // namespace
 
 cudaError_t launch_batch_particles(const BatchPlan& bp, cudaStream_t st)
 {
-    if (bp.n_pair) b_pair<<<bp.n_pair, kPairThreads, 0, st>>>(bp.desc, bp.pair);
+    if (bp.n_pair) {
+        if (bp.pair_fast) b_pair<true><<<bp.n_pair, kPairThreads, 0, st>>>(bp.desc, bp.pair);
+        else b_pair<false><<<bp.n_pair, kPairThreads, 0, st>>>(bp.desc, bp.pair);
+    }
     if (bp.n_part) b_cell_assign<<<bp.n_part, kThreads, 0, st>>>(bp.desc, bp.part);
     if (bp.n_cell) b_cell_scan<<<bp.n_cell, kCellThreads, 0, st>>>(bp.desc, bp.cell);
     if (bp.n_cell) b_cell_fill<<<bp.n_cell, kCellThreads, 0, st>>>(bp.desc, bp.cell);
     if (bp.n_part) b_nbr_build<<<bp.n_part, kThreads, 0, st>>>(bp.desc, bp.part);
-    if (bp.n_part) b_cforce<<<bp.n_part, kThreads, 0, st>>>(bp.desc, bp.part);
+    if (bp.n_cf) b_cforce<<<bp.n_cf, kBatchCforceBlock, 0, st>>>(bp.desc, bp.cf);
     if (bp.n_vacf) {
-        if (bp.vacf_no <= 4) b_vacf<4><<<bp.n_vacf, kThreads, 0, st>>>(bp.desc, bp.vacf);
-        else if (bp.vacf_no <= 8) b_vacf<8><<<bp.n_vacf, kThreads, 0, st>>>(bp.desc, bp.vacf);
-        else if (bp.vacf_no <= 16) b_vacf<16><<<bp.n_vacf, kThreads, 0, st>>>(bp.desc, bp.vacf);
-        else b_vacf<32><<<bp.n_vacf, kThreads, 0, st>>>(bp.desc, bp.vacf);
+        const dim3 g((unsigned)bp.n_vacf, (unsigned)((bp.vacf_no + kVacfGroup - 1) / kVacfGroup));
+        b_vacf<<<g, kThreads, 0, st>>>(bp.desc, bp.vacf);
     }
     return cudaGetLastError();
 }
@@ -645,7 +781,10 @@ cudaError_t launch_delay(unsigned long long ns, cudaStream_t st)
 cudaError_t launch_pair_force_integrate(const StepParams& P, const ParticleBuffers& B, cudaStream_t st)
 {
     const unsigned grid = (unsigned)((P.n + kPairThreads - 1) / kPairThreads);
-    pair_force_integrate<<<grid, kPairThreads, 0, st>>>(P, B.ctrl, B.pos, B.perm, B.nbr, B.nbr_cnt, B.vel, B.fc,
+    const bool fast = P.Q == 1 && P.Qs == 0;
+    auto k = fast ? pair_force_integrate<true> : pair_force_integrate<false>;
+    const unsigned pgrid = fast ? (unsigned)(((long long)P.n * kPairLanes + kPairThreads - 1) / kPairThreads) : grid;
+    k<<<pgrid, kPairThreads, 0, st>>>(P, B.ctrl, B.pos, B.perm, B.nbr, B.nbr_cnt, B.vel, B.fc,
                                                         B.conv, B.frblock, B.ftab, B.g0, B.ring, B.pos_next,
                                                         B.vhalf, B.fd, B.disp, B.disp_build);
     return cudaGetLastError();
@@ -675,7 +814,7 @@ cudaError_t launch_rebuild(const StepParams& P, const ParticleBuffers& B, cudaSt
 
 cudaError_t launch_cforce(const StepParams& P, const ParticleBuffers& B, int mode, cudaStream_t st)
 {
-    const unsigned grid = (unsigned)((P.n + kThreads - 1) / kThreads);
+    const unsigned grid = (unsigned)(((long long)P.n * kCforceLanes + kThreads - 1) / kThreads);
     if (mode)
         cforce<true><<<grid, kThreads, 0, st>>>(P, B.ctrl, B.pos_next, B.pos, B.perm, B.nbr, B.nbr_cnt, B.vhalf,
                                                 B.vel, B.fc);
@@ -688,16 +827,9 @@ cudaError_t launch_cforce(const StepParams& P, const ParticleBuffers& B, int mod
 cudaError_t launch_vacf(const StepParams& P, const ParticleBuffers& B, cudaStream_t st)
 {
     if (P.vacf_len <= 0) return cudaSuccess;
-    if (P.n_os <= 4)
-        vacf<4><<<B.vacf_gx, kThreads, 0, st>>>(P, B.ctrl, B.vel, B.vorig, B.vpartial, B.csum, B.ccnt, B.norig, B.vdone);
-    else if (P.n_os <= 8)
-        vacf<8><<<B.vacf_gx, kThreads, 0, st>>>(P, B.ctrl, B.vel, B.vorig, B.vpartial, B.csum, B.ccnt, B.norig, B.vdone);
-    else if (P.n_os <= 16)
-        vacf<16><<<B.vacf_gx, kThreads, 0, st>>>(P, B.ctrl, B.vel, B.vorig, B.vpartial, B.csum, B.ccnt, B.norig, B.vdone);
-    else if (P.n_os <= kVacfMaxOrigins)
-        vacf<32><<<B.vacf_gx, kThreads, 0, st>>>(P, B.ctrl, B.vel, B.vorig, B.vpartial, B.csum, B.ccnt, B.norig, B.vdone);
-    else
-        return cudaErrorInvalidValue;
+    if (P.n_os > kVacfMaxOrigins) return cudaErrorInvalidValue;
+    const dim3 g((unsigned)B.vacf_gx, (unsigned)((P.n_os + kVacfGroup - 1) / kVacfGroup));
+    vacf<<<g, kThreads, 0, st>>>(P, B.ctrl, B.vel, B.vorig, B.vpartial, B.csum, B.ccnt, B.norig, B.vdone);
     return cudaGetLastError();
 }
 

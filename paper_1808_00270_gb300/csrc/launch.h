@@ -31,7 +31,7 @@ struct ParticleBuffers {
     int ncells;
     // VACF
     float4* vorig;
-    double* vpartial;
+    float* vpartial;      // per-block VACF partials [n_os][vacf_gx]
     double* csum;
     long long* ccnt;
     long long* norig;
@@ -75,7 +75,7 @@ struct SysDesc {
     int ntaps;
     uint32_t k0, k1;         // Philox key
     const int* int2ext;
-    int nb_pair, nb_part, nb_cell, nb_vacf, nb_conv, nb_fir;
+    int nb_pair, nb_part, nb_cell, nb_vacf, nb_conv, nb_fir, nb_cf;
 };
 struct Tile {
     int m, b;   // member, block within member
@@ -83,15 +83,19 @@ struct Tile {
 };
 struct BatchPlan {
     const SysDesc* desc;
-    const Tile *pair, *part, *cell, *vacf, *conv, *fir;
-    int n_pair, n_part, n_cell, n_vacf, n_conv, n_fir;
+    const Tile *pair, *part, *cell, *vacf, *conv, *fir, *cf;
+    int n_pair, n_part, n_cell, n_vacf, n_conv, n_fir, n_cf;
     int max_H, max_n, max_ntaps, nacc, bf16, kahan, vacf_no;
     int conv_block;  // threads per convolution tile (128 or 256)
+    int pair_fast;   // every member has one pair term and no self-difference term
 };
 cudaError_t launch_batch_conv(const BatchPlan& bp, cudaStream_t st);      // k_history.cu
 cudaError_t launch_batch_particles(const BatchPlan& bp, cudaStream_t st); // k_particles.cu
 cudaError_t launch_batch_noise(const BatchPlan& bp, cudaStream_t st);     // k_noise.cu
 // Block sizes of the tile schedules.
+constexpr int kBatchPairLanes = 1;    // lanes per particle of the one-term pair kernel
+constexpr int kBatchCforceLanes = 1;  // lanes per particle of the F^C kernel
+constexpr int kBatchCforceBlock = 128; // threads per F^C tile of a batch
 constexpr int kBatchPairBlock = 128, kBatchPartBlock = 256, kBatchCellChunk = 512, kBatchConvCols = 256,
               kBatchFirStreams = 32, kBatchVacfBlock = 256;
 

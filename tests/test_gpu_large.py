@@ -35,12 +35,13 @@ def test_large_suspension_sampled_forces():
     assert rel_l2(fr, fr_ref) < 1e-5
 
 
-def test_vacf_accumulator_definition():
-    """The FP64 VACF accumulator equals the definition evaluated on the
-    recorded velocities with the same origin schedule."""
+@pytest.mark.parametrize("wname,L,stride,burn", [("gld_n64_m32", 12, 3, 5), ("gld_n4096_m200", 40, 3, 2)])
+def test_vacf_accumulator_definition(wname, L, stride, burn):
+    """The VACF accumulator equals the definition evaluated on the recorded
+    velocities with the same origin schedule (one or several particle blocks,
+    one or several groups of origins)."""
     from paper_1808_00270_gb300 import inputs
-    w = inputs.SMALL
-    L, stride, burn = 12, 3, 5
+    w = inputs.WORKLOADS[wname]
     gpu = make_gpu(w, vacf_len=L, vacf_stride=stride, vacf_burnin=burn)
     V = {0: gpu.get_state()[1]}
     for t in range(1, 60):

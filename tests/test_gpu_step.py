@@ -85,15 +85,20 @@ def test_graph_and_eager_paths_identical():
     a = make_gpu(w, use_graphs=True)
     b = make_gpu(w, use_graphs=False)
     c = make_gpu(w, use_graphs=True)
+    d = make_gpu(w, use_graphs=2)  # gated rebuild kernels instead of a conditional node
     a.step(150)
     b.step(150)
+    d.step(150)
     for k in (1, 63, 2, 64, 20):
         c.step(k)
     pa, va = a.get_state()
     pb, vb = b.get_state()
     pc, vc = c.get_state()
+    pd, vd = d.get_state()
+    assert a.diag()["graph_mode"] in (1, 2) and d.diag()["graph_mode"] == 1
     assert np.array_equal(pa, pb) and np.array_equal(va, vb)
     assert np.array_equal(pa, pc) and np.array_equal(va, vc)
+    assert np.array_equal(pa, pd) and np.array_equal(va, vd)
     assert np.array_equal(a.get(ARR_DISP), c.get(ARR_DISP))
 
 
