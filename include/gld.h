@@ -52,8 +52,9 @@ typedef enum {
     GLD_E_NOT_PSD = -3,   /* noise spectrum has a negative mode (Sec. II B)   */
     GLD_E_CUDA = -4,      /* a CUDA runtime call or launch failed             */
     GLD_E_NONFINITE = -5, /* a non-finite displacement was produced           */
-    GLD_E_TIMEOUT = -6,   /* a bounded device wait gave up                     */
-    GLD_E_STATE = -7      /* call out of order (e.g. gld_step before kernels) */
+    GLD_E_TIMEOUT = -6,   /* a bounded wait gave up (device, or gld_server_drain) */
+    GLD_E_STATE = -7,     /* call out of order (e.g. gld_step before kernels) */
+    GLD_E_CANCELLED = -8  /* a served request was cancelled                   */
 } gld_status;
 
 enum { GLD_HIST_F32 = 0, GLD_HIST_BF16 = 1 };
@@ -329,6 +330,11 @@ gld_status gld_server_clock(const gld_server* server, double* t);
  * has not finished; the request's error if it failed.  Any pointer may be NULL. */
 gld_status gld_server_result(gld_server* server, int64_t id, double* vacf, int64_t* n_origins, double* pos,
                              double* vel, double* times);
+/* Cancels request id: a queued request is dropped, an admitted one leaves the
+ * batch at once and its system is freed once the device has finished the
+ * blocks already queued for it.  Its result then reports GLD_E_CANCELLED.
+ * GLD_E_STATE if it has already finished or is being read back. */
+gld_status gld_server_cancel(gld_server* server, int64_t id);
 /* out[k] for the GLD_SRV_* slots k < count. */
 gld_status gld_server_stats(gld_server* server, int64_t* out, int32_t count);
 const char* gld_server_last_error(const gld_server* server);

@@ -14,13 +14,13 @@ import numpy as np
 
 from . import build as _build
 
-OK, E_INVAL, E_NOMEM, E_NOT_PSD, E_CUDA, E_NONFINITE, E_TIMEOUT, E_STATE = 0, -1, -2, -3, -4, -5, -6, -7
+OK, E_INVAL, E_NOMEM, E_NOT_PSD, E_CUDA, E_NONFINITE, E_TIMEOUT, E_STATE, E_CANCELLED = 0, -1, -2, -3, -4, -5, -6, -7, -8
 HIST_F32, HIST_BF16 = 0, 1
 KCONT, KDISCRETE = 0, 1
 ARR_POS, ARR_VEL, ARR_FC, ARR_FD, ARR_FR, ARR_DISP, ARR_HIST, ARR_CONV = range(8)
 _NAMES = {OK: "GLD_OK", E_INVAL: "GLD_E_INVAL", E_NOMEM: "GLD_E_NOMEM", E_NOT_PSD: "GLD_E_NOT_PSD",
           E_CUDA: "GLD_E_CUDA", E_NONFINITE: "GLD_E_NONFINITE", E_TIMEOUT: "GLD_E_TIMEOUT",
-          E_STATE: "GLD_E_STATE"}
+          E_STATE: "GLD_E_STATE", E_CANCELLED: "GLD_E_CANCELLED"}
 
 
 class GLDError(RuntimeError):
@@ -107,6 +107,7 @@ def lib():
             "gld_server_clock": (i32, [vp, C.POINTER(d)]),
             "gld_server_result": (i32, [vp, i64, vp, C.POINTER(i64), vp, vp, vp]),
             "gld_server_stats": (i32, [vp, vp, i32]),
+            "gld_server_cancel": (i32, [vp, i64]),
             "gld_server_last_error": (C.c_char_p, [vp]),
             "gld_server_destroy": (i32, [vp]),
             "gld_batch_create": (i32, [vp, C.POINTER(vp)]),
@@ -136,7 +137,7 @@ def exported_symbols() -> list[str]:
             "gld_batch_destroy", "gld_get_bytes", "gld_bytes_needed", "gld_batch_set_tuning",
             "gld_server_params_default", "gld_server_create", "gld_server_submit", "gld_server_pump",
             "gld_server_drain", "gld_server_clock", "gld_server_result", "gld_server_stats",
-            "gld_server_last_error", "gld_server_destroy"]
+            "gld_server_last_error", "gld_server_destroy", "gld_server_cancel"]
 
 
 def _ptr(a: np.ndarray):
@@ -511,6 +512,9 @@ class Server:
         if keep_state:
             out["pos"], out["vel"] = pos, vel
         return out
+
+    def cancel(self, rid: int):
+        self._check(lib().gld_server_cancel(self._h, int(rid)))
 
     def stats(self) -> dict:
         out = np.zeros(len(SRV_STATS), dtype=np.int64)

@@ -374,7 +374,7 @@ size_t ctx_bytes_needed(const gld_params* p, int Q, int Qs, int nr, int num_sms)
         16 * np, 16 * np, 16 * np, 16 * np, 16 * np, elem * n3 * P.H, 4 * (size_t)kMaxAcc * n3,
         4 * (size_t)P.T * n3, 4 * (size_t)P.lw * n3, 4 * ((size_t)ncells + 1), 4 * (size_t)ncells,
         4 * (size_t)ncells, 4 * np, 4 * (size_t)chunks, 4 * (size_t)chunks,
-        16 * (size_t)std::max(P.n_os, 1) * P.n, 4 * (size_t)std::max(P.n_os, 1) * vacf_gx,
+        16 * (size_t)std::max(P.n_os, 1) * P.n, 8 * (size_t)std::max(P.n_os, 1) * vacf_gx,
         8 * (size_t)std::max(P.vacf_len, 1), 8 * (size_t)std::max(P.vacf_len, 1), 8, 4,
         4 * (size_t)fir_taps_len(P.H), 4 * (size_t)kMaxAcc * P.m_max, 4 * 2 * (size_t)kMaxQ,
         8 * (size_t)P.m_max, 8 * (size_t)P.m_max, 8 * (size_t)P.m_max, 8 * 2 * (size_t)P.m_max, 8 * 4, 4,
@@ -503,7 +503,7 @@ gld_status gld_create(const gld_params* p, const double* pos, const double* vel,
     B.chunk_off = alloc_n<int>(c, chunks, ok);
     B.vacf_gx = vacf_blocks(P.n, c->num_sms);
     B.vorig = alloc_n<float4>(c, (size_t)std::max(P.n_os, 1) * P.n, ok);
-    B.vpartial = alloc_n<float>(c, (size_t)std::max(P.n_os, 1) * B.vacf_gx, ok);
+    B.vpartial = alloc_n<float>(c, 2 * (size_t)std::max(P.n_os, 1) * B.vacf_gx, ok);
     B.csum = alloc_n<double>(c, std::max(P.vacf_len, 1), ok);
     B.ccnt = alloc_n<long long>(c, std::max(P.vacf_len, 1), ok);
     B.norig = alloc_n<long long>(c, 1, ok);
@@ -676,6 +676,7 @@ gld_status gld_sync(gld_ctx* c)
 gld_status gld_vacf(gld_ctx* c, double* out, int64_t* n_origins)
 {
     if (!c) return GLD_E_INVAL;
+    if (c->latched == GLD_OK) GLD_CUDA(c, launch_vacf_flush(c->P, c->B, c->st));
     GLD_TRY(sync_and_check(c));
     const int L = c->P.vacf_len;
     long long no = 0;

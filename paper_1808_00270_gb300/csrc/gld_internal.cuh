@@ -38,8 +38,13 @@ struct Ctrl {
     long long hslot;       // step mod H: the history slot this step writes
     // VACF schedule at the step the next VACF kernel sees (written by the
     // pair kernel): active, origins in flight, slot of the newest origin, a
-    // new origin at this step, lag of the newest origin
-    int vacf_on, vacf_nact, vacf_slot0, vacf_origin, vacf_lag0, pad2_;
+    // new origin at this step, lag of the newest origin, partial buffer
+    int vacf_on, vacf_nact, vacf_slot0, vacf_origin, vacf_lag0, vacf_buf;
+    // partials of an earlier VACF launch not yet added to the sums: set by
+    // the VACF kernel, consumed by the next VACF kernel or by a flush
+    int vacf_pending;
+    // the previous launch's schedule as the next VACF kernel must fold it
+    int pv_nact, pv_lag0, pv_buf;
 };
 
 // Everything a step kernel needs, passed by value.

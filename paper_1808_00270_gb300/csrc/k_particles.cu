@@ -47,6 +47,12 @@ __device__ __forceinline__ float dot3(float ax, float ay, float az, float bx, fl
 // active while its lag t - t_j is below vacf_len.
 __device__ __forceinline__ void vacf_schedule(const StepParams& P, Ctrl* __restrict__ ctrl, long long t)
 {
+    // the partials of the last VACF launch are folded by the next one
+    ctrl->pv_nact = ctrl->vacf_pending ? ctrl->vacf_nact : 0;
+    ctrl->pv_lag0 = ctrl->vacf_lag0;
+    ctrl->pv_buf = ctrl->vacf_buf;
+    ctrl->vacf_pending = 0;
+    ctrl->vacf_buf ^= 1;
     if (t < P.vacf_burnin) {
         ctrl->vacf_on = 0;
         return;
@@ -494,7 +500,7 @@ __global__ void __launch_bounds__(kThreads) cforce(const StepParams P, Ctrl* __r
 // ---- velocity autocorrelation ------------------------------------------------
 constexpr int kVacfMaxOrigins = 32;  // origins in flight (vacf_len / vacf_stride)
 constexpr int kVacfGroup = 4;        // origins per block row of the VACF grid
-static_assert(kVacfMaxBlocks % 32 == 0, "VACF block count");
+static_assert(kVacfMaxBlocks % 32 == 0 && kVacfMaxBlocks <= kThreads, "VACF partials are folded one per thread");
 
 __device__ __forceinline__ float warp_sum_f(float v)
 {
@@ -521,26 +527,66 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float bhi, float bl
     lo = e - (hi - s);
 }
 
-// Block (x, y) of the grid (gx <= 256) takes the particles x*256 + tid,
-// x*256 + tid + gx*256, ... and
-// the origins of ages 4y .. 4y+3 (age j = 0 is the newest): dot products in
-// FP32 registers, warp and block sums in FP32 (at most 256 x a few terms);
-// the last block to finish adds the per-block partials of every origin in
-// double-float in a fixed order and accumulates C(lag) in FP64 (GB300's FP64
-// pipes are slow, so FP64 is kept to one addition per origin and step).
-__device__ __forceinline__ void vacf_body(const StepParams& P, const Ctrl* __restrict__ ctrl,
+// Adds the block partials of origins q = first, first + step, ... (buffer
+// buf, nblk partials each) to C(lag0 + q*stride): double-float sums on the
+// FP32 pipes in a fixed order, one FP64 addition per origin.
+__device__ __forceinline__ void vacf_fold(const StepParams& P, const float* __restrict__ partial, double* __restrict__ csum,
+                                          long long* __restrict__ ccnt, int buf, int nact, int lag0, int nblk, int first,
+                                          int step)
+{
+    __shared__ float sh[kThreads / 32][2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float* base = partial + (size_t)buf * P.n_os * nblk;
+    for (int q = first; q < nact; q += step) {
+        float hi = 0.f, lo = 0.f;
+        if ((int)threadIdx.x < nblk) hi = __ldcg(base + (size_t)q * nblk + threadIdx.x);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, hi, o), l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+            df_add(hi, lo, h2, l2);
+        }
+        if (lane == 0) {
+            sh[warp][0] = hi;
+            sh[warp][1] = lo;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float h = 0.f, l = 0.f;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) df_add(h, l, sh[w][0], sh[w][1]);
+            const int lg = lag0 + q * P.vacf_stride;  // < vacf_len for q < nact
+            csum[lg] += (double)h + (double)l;
+            ccnt[lg] += 1;
+        }
+        __syncthreads();
+    }
+}
+
+// Block (x, y) of the grid (gx <= 256 = blockDim) takes the particles
+// x*256 + tid, x*256 + tid + gx*256, ... and the origins of ages 4y .. 4y+3
+// (age j = 0 is the newest): dot products in FP32 registers, warp and block
+// sums in FP32 (at most 256 x a few terms) written as per-block partials.
+// The partials of a step are added to C(lag) by the next VACF launch (blocks
+// (x < origins, 0) fold the previous step's buffer while the rest of the grid
+// streams) or by vacf_flush before the sums are read: no grid-wide wait.
+// GB300's FP64 pipes are slow, so FP64 is one addition per origin and step.
+__device__ __forceinline__ void vacf_body(const StepParams& P, Ctrl* __restrict__ ctrl,
                                           const float4* __restrict__ vel, float4* __restrict__ vorig,
                                           float* __restrict__ partial, double* __restrict__ csum,
-                                          long long* __restrict__ ccnt, long long* __restrict__ norig,
-                                          unsigned* __restrict__ done, int blk, int nblk, int grp, int ngrp)
+                                          long long* __restrict__ ccnt, long long* __restrict__ norig, int blk,
+                                          int nblk, int grp)
 {
     // V_t was completed by the previous kernel; the pair kernel of this step
-    // wrote the schedule of t
+    // wrote the schedule of t and moved the last one to pv_*
+    if (grp == 0 && ctrl->pv_nact > 0)
+        vacf_fold(P, partial, csum, ccnt, ctrl->pv_buf, ctrl->pv_nact, ctrl->pv_lag0, nblk, blk, nblk);
     if (!ctrl->vacf_on) return;  // uniform over the grid
     const int n_act = ctrl->vacf_nact;
     const bool is_origin = ctrl->vacf_origin != 0;
     const int slot0 = ctrl->vacf_slot0;  // slot of age j: (slot0 - j) mod n_os
-    const int lag0 = ctrl->vacf_lag0;
+    if (blk == 0 && grp == 0 && threadIdx.x == 0) {
+        ctrl->vacf_pending = 1;
+        if (is_origin) *norig += 1;
+    }
     const int q0 = grp * kVacfGroup;
     float acc[kVacfGroup];
 #pragma unroll
@@ -572,53 +618,26 @@ __device__ __forceinline__ void vacf_body(const StepParams& P, const Ctrl* __res
     __syncthreads();
     if (threadIdx.x < kVacfGroup && q0 + (int)threadIdx.x < n_act) {
         float sb = 0.f;
-        for (int w = 0; w < kThreads / 32; ++w) sb += wsum[w][threadIdx.x];
-        partial[(size_t)(q0 + threadIdx.x) * nblk + blk] = sb;
-    }
-    __shared__ bool last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        last = atomicAdd(done, 1u) == (unsigned)(nblk * ngrp) - 1u;
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    // warp w takes the origins w, w + 8, ...; lane l the blocks l, l + 32, ...
-    // (all of its loads issued before the first addition)
-    for (int q = warp; q < n_act; q += kThreads / 32) {
-        float v[kVacfMaxBlocks / 32];
-#pragma unroll
-        for (int k = 0; k < kVacfMaxBlocks / 32; ++k) {
-            const int b = lane + 32 * k;
-            v[k] = b < nblk ? __ldcg(partial + (size_t)q * nblk + b) : 0.f;
-        }
-        float hi = 0.f, lo = 0.f;
-#pragma unroll
-        for (int k = 0; k < kVacfMaxBlocks / 32; ++k)
-            if (lane + 32 * k < nblk) df_add(hi, lo, v[k], 0.f);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float h2 = __shfl_xor_sync(0xffffffffu, hi, o), l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-            df_add(hi, lo, h2, l2);
-        }
-        if (lane == 0) {
-            const int lg = lag0 + q * P.vacf_stride;  // < vacf_len for q < n_act
-            csum[lg] += (double)hi + (double)lo;
-            ccnt[lg] += 1;
-        }
-    }
-    if (threadIdx.x == 0) {
-        if (is_origin) *norig += 1;
-        *done = 0u;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sb += wsum[w][threadIdx.x];
+        partial[((size_t)ctrl->vacf_buf * P.n_os + q0 + threadIdx.x) * nblk + blk] = sb;
     }
 }
 
-__global__ void __launch_bounds__(kThreads) vacf(const StepParams P, const Ctrl* __restrict__ ctrl, const float4* __restrict__ vel,
+__global__ void __launch_bounds__(kThreads) vacf(const StepParams P, Ctrl* __restrict__ ctrl, const float4* __restrict__ vel,
          float4* __restrict__ vorig, float* __restrict__ partial, double* __restrict__ csum,
-         long long* __restrict__ ccnt, long long* __restrict__ norig, unsigned* __restrict__ done)
+         long long* __restrict__ ccnt, long long* __restrict__ norig)
 {
-    vacf_body(P, ctrl, vel, vorig, partial, csum, ccnt, norig, done, blockIdx.x, gridDim.x, blockIdx.y, gridDim.y);
+    vacf_body(P, ctrl, vel, vorig, partial, csum, ccnt, norig, blockIdx.x, gridDim.x, blockIdx.y);
+}
+
+// Adds the partials of the last VACF launch to the sums (before a read).
+__global__ void __launch_bounds__(kThreads) vacf_flush(const StepParams P, Ctrl* __restrict__ ctrl,
+                                                       const float* __restrict__ partial, double* __restrict__ csum,
+                                                       long long* __restrict__ ccnt, int nblk)
+{
+    if (!ctrl->vacf_pending) return;
+    vacf_fold(P, partial, csum, ccnt, ctrl->vacf_buf, ctrl->vacf_nact, ctrl->vacf_lag0, nblk, 0, 1);
+    if (threadIdx.x == 0) ctrl->vacf_pending = 0;
 }
 
 // ---- explicit pair lists (checks of the traversals) -------------------------
@@ -742,8 +761,7 @@ __global__ void __launch_bounds__(kThreads) b_vacf(const SysDesc* __restrict__ D
     const Tile t = tiles[blockIdx.x];
     const SysDesc& d = D[t.m];
     const ParticleBuffers& B = d.B;
-    vacf_body(d.P, B.ctrl, B.vel, B.vorig, B.vpartial, B.csum, B.ccnt, B.norig, B.vdone, t.b, d.nb_vacf, blockIdx.y,
-              gridDim.y);
+    vacf_body(d.P, B.ctrl, B.vel, B.vorig, B.vpartial, B.csum, B.ccnt, B.norig, t.b, d.nb_vacf, blockIdx.y);
 }
 
 }  // namespace
@@ -829,7 +847,14 @@ cudaError_t launch_vacf(const StepParams& P, const ParticleBuffers& B, cudaStrea
     if (P.vacf_len <= 0) return cudaSuccess;
     if (P.n_os > kVacfMaxOrigins) return cudaErrorInvalidValue;
     const dim3 g((unsigned)B.vacf_gx, (unsigned)((P.n_os + kVacfGroup - 1) / kVacfGroup));
-    vacf<<<g, kThreads, 0, st>>>(P, B.ctrl, B.vel, B.vorig, B.vpartial, B.csum, B.ccnt, B.norig, B.vdone);
+    vacf<<<g, kThreads, 0, st>>>(P, B.ctrl, B.vel, B.vorig, B.vpartial, B.csum, B.ccnt, B.norig);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vacf_flush(const StepParams& P, const ParticleBuffers& B, cudaStream_t st)
+{
+    if (P.vacf_len <= 0) return cudaSuccess;
+    vacf_flush<<<1, kThreads, 0, st>>>(P, B.ctrl, B.vpartial, B.csum, B.ccnt, B.vacf_gx);
     return cudaGetLastError();
 }
 

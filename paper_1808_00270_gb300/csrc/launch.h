@@ -31,7 +31,7 @@ struct ParticleBuffers {
     int ncells;
     // VACF
     float4* vorig;
-    float* vpartial;      // per-block VACF partials [n_os][vacf_gx]
+    float* vpartial;      // per-block VACF partials [2][n_os][vacf_gx] (two steps)
     double* csum;
     long long* ccnt;
     long long* norig;
@@ -54,6 +54,8 @@ cudaError_t launch_rebuild_decide(cudaGraphConditionalHandle h, const Ctrl* ctrl
 // Both copy pos_next into pos and clear ctrl->rebuild.
 cudaError_t launch_cforce(const StepParams& P, const ParticleBuffers& B, int mode, cudaStream_t st);
 cudaError_t launch_vacf(const StepParams& P, const ParticleBuffers& B, cudaStream_t st);
+// Adds the last VACF launch's partials to the FP64 sums (before reading them).
+cudaError_t launch_vacf_flush(const StepParams& P, const ParticleBuffers& B, cudaStream_t st);
 // Pairs from a fresh cell traversal of pos_sorted / cell_start.
 cudaError_t launch_pair_list(const StepParams& P, const ParticleBuffers& B, int* pairs,
                              long long cap, unsigned long long* count, cudaStream_t st);

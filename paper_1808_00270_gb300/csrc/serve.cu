@@ -21,7 +21,7 @@
 
 namespace {
 
-enum ReqState { kQueued = 0, kActive = 1, kRetiring = 2, kDone = 3, kFailed = 4 };
+enum ReqState { kQueued = 0, kActive = 1, kRetiring = 2, kDone = 3, kFailed = 4, kCancelling = 5 };
 
 struct Slab {  // pinned host memory for a result in flight
     char* p = nullptr;
@@ -59,6 +59,7 @@ struct gld_server {
     std::deque<Req*> queue;     // arrival order
     std::vector<Req*> active;   // members of the batch
     std::vector<Req*> retiring; // results in flight
+    std::vector<Req*> cancelling; // cancelled members waiting for their queued blocks
     std::deque<cudaEvent_t> inflight;
     std::vector<cudaEvent_t> spare_ev;
     std::vector<Slab> spare_slab;
@@ -181,7 +182,8 @@ gld_status retire(gld_server* s, Req* r)
     const size_t need = 64 + 16 * (size_t)std::max(L, 1) + (r->keep_state ? 32 * n : 0);
     if (!take_slab(s, need, r->slab)) return GLD_E_NOMEM;
     char* h = r->slab.p;
-    cudaError_t e = cudaMemcpyAsync(h, &c->B.ctrl->err, sizeof(unsigned), cudaMemcpyDeviceToHost, s->S);
+    cudaError_t e = launch_vacf_flush(c->P, c->B, s->S);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, &c->B.ctrl->err, sizeof(unsigned), cudaMemcpyDeviceToHost, s->S);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h + 8, c->B.norig, 8, cudaMemcpyDeviceToHost, s->S);
     if (e == cudaSuccess && L > 0) e = cudaMemcpyAsync(h + 64, c->B.csum, 8 * (size_t)L, cudaMemcpyDeviceToHost, s->S);
     if (e == cudaSuccess && L > 0)
@@ -252,6 +254,18 @@ void reap(gld_server* s)
         else s->retiring[keep++] = r;
     }
     s->retiring.resize(keep);
+    keep = 0;
+    for (Req* r : s->cancelling) {
+        if (cudaEventQuery(r->ev) == cudaSuccess) {
+            s->spare_ev.push_back(r->ev);
+            r->ev = nullptr;
+            release_ctx(s, r);
+            fail_req(s, r, GLD_E_CANCELLED, "cancelled");
+        } else {
+            s->cancelling[keep++] = r;
+        }
+    }
+    s->cancelling.resize(keep);
 }
 
 void drop_active(gld_server* s, Req* r, gld_status st, const std::string& m)
@@ -449,7 +463,7 @@ gld_status gld_server_drain(gld_server* s, double timeout_s)
     for (;;) {
         const gld_status st = gld_server_pump(s, nullptr);
         if (st != GLD_OK) return st;
-        if (s->queue.empty() && s->active.empty() && s->retiring.empty()) break;
+        if (s->queue.empty() && s->active.empty() && s->retiring.empty() && s->cancelling.empty()) break;
         const double now = now_s(s);
         if (now > t_end) {
             s->msg = "gld_server_drain: timeout";
@@ -457,7 +471,8 @@ gld_status gld_server_drain(gld_server* s, double timeout_s)
         }
         if (s->active.empty()) {  // idle until the next arrival or result
             double wait = 5e-5;
-            if (s->retiring.empty() && !s->queue.empty()) wait = std::min(1e-3, std::max(0.0, s->queue.front()->arrival - now));
+            if (s->retiring.empty() && s->cancelling.empty() && !s->queue.empty())
+                wait = std::min(1e-3, std::max(0.0, s->queue.front()->arrival - now));
             std::this_thread::sleep_for(std::chrono::duration<double>(wait));
         }
     }
@@ -495,6 +510,35 @@ gld_status gld_server_result(gld_server* s, int64_t id, double* vacf, int64_t* n
         s->msg = "gld_server_result: the request did not keep its state";
         return GLD_E_STATE;
     }
+    return GLD_OK;
+}
+
+gld_status gld_server_cancel(gld_server* s, int64_t id)
+{
+    if (!s || id < 0 || id >= (int64_t)s->reqs.size()) return GLD_E_INVAL;
+    Req* r = s->reqs[(size_t)id];
+    if (r->state == kQueued) {
+        s->queue.erase(std::find(s->queue.begin(), s->queue.end(), r));
+        fail_req(s, r, GLD_E_CANCELLED, "cancelled");
+        return GLD_OK;
+    }
+    if (r->state != kActive) {
+        s->msg = "gld_server_cancel: the request has finished or is being read back";
+        return GLD_E_STATE;
+    }
+    s->active.erase(std::find(s->active.begin(), s->active.end(), r));
+    gld_batch_remove(s->batch, r->ctx);
+    r->ev = take_event(s);
+    if (!r->ev || cudaEventRecord(r->ev, s->S) != cudaSuccess) {  // cannot track it: wait
+        cudaStreamSynchronize(s->S);
+        if (r->ev) s->spare_ev.push_back(r->ev);
+        r->ev = nullptr;
+        release_ctx(s, r);
+        fail_req(s, r, GLD_E_CANCELLED, "cancelled");
+        return GLD_OK;
+    }
+    r->state = kCancelling;
+    s->cancelling.push_back(r);
     return GLD_OK;
 }
 

@@ -140,3 +140,29 @@ def test_requests_wait_for_their_arrival():
     r0, r1 = s.result(i0), s.result(i1)
     assert r1["admitted"] >= t0 + 0.3 and r0["done"] > r0["admitted"] >= r0["arrival"]
     assert np.array_equal(r0["vacf"], r1["vacf"])  # same system, same result
+
+
+def test_cancel_and_forced_drain_timeout():
+    """Host-side failure paths: a drain that runs out of time returns
+    GLD_E_TIMEOUT and leaves the server usable; a queued and an admitted
+    request are cancelled (their memory returns to the budget) while the
+    others complete."""
+    from paper_1808_00270_gb300 import GLDError, Server
+    from paper_1808_00270_gb300.binding import E_CANCELLED, E_TIMEOUT
+    s = Server()
+    a = _submit(s, _workload("long", 3000, 0.1, 200, 60), 64 * 400, keep_state=False)
+    b = _submit(s, _workload("short", 500, 0.1, 64, 61), 256, keep_state=False)
+    c = _submit(s, _workload("later", 500, 0.1, 64, 62), 128, arrival=s.clock() + 30.0, keep_state=False)
+    with pytest.raises(GLDError) as e:
+        s.drain(0.05)
+    assert e.value.status == E_TIMEOUT
+    assert s.stats()["active"] >= 1
+    s.cancel(a)  # admitted
+    s.cancel(c)  # still queued
+    s.drain(60)
+    assert s.result(a)["status"] == E_CANCELLED and s.result(c)["status"] == E_CANCELLED
+    assert s.result(b)["status"] == 0
+    st = s.stats()
+    assert st["bytes"] == 0 and st["failed"] == 2 and st["done"] == 1
+    with pytest.raises(GLDError):
+        s.cancel(b)  # already finished
