@@ -82,7 +82,8 @@ typedef struct gld_params {
     int32_t vacf_len;    /* VACF lags kept (0 = no VACF)                             */
     int32_t vacf_stride; /* steps between VACF time origins (>= 1); at most 32      */
                          /* origins in flight: ceil(vacf_len / vacf_stride) <= 32   */
-    int64_t vacf_burnin; /* first origin time; < 0 selects 2 m_max                  */
+    int64_t vacf_burnin; /* first origin time, >= 1 (samples follow steps); < 0
+                          * selects 2 m_max                                    */
     int32_t noise_block; /* steps of F^R produced per noise launch (0 = 64)          */
     int32_t psd_clamp;   /* 1: clamp negative noise modes to 0 instead of failing    */
     int32_t use_graphs;  /* 1 (default): replay steps from a captured CUDA graph

@@ -90,6 +90,9 @@ def lib(variant: int = 0):
             L.or_get_coefs.argtypes = [vp, vp, vp, vp, vp, vp, vp]
             L.or_get_vacf.argtypes = [vp, vp]
             L.or_get_vacf.restype = i64
+            L.or_set_paircorr.argtypes = [vp, i32, C.c_double]
+            L.or_set_paircorr.restype = i32
+            L.or_get_paircorr.argtypes = [vp, vp, vp, vp]
             L.or_set_threads.argtypes = [i32]
             L.or_get_threads.restype = i32
             _libs[variant] = L
@@ -175,12 +178,13 @@ class System:
     """An oracle GLD system (FP64).  Mirrors the CUDA library's model API."""
 
     def __init__(self, *, n, box, mass, kT, dt, m_max, r_c, r_c_min=0.0, A_cons=0.0, seed=1,
-                 vacf_len=0, vacf_stride=1, vacf_burnin=0, pos, vel, variant=0):
+                 vacf_len=0, vacf_stride=1, vacf_burnin=-1, pos, vel, variant=0):
         self._L = lib(variant)
         self.n, self.m_max = int(n), int(m_max)
         pos, vel = _f64(pos).reshape(n, 3), _f64(vel).reshape(n, 3)
         self._h = self._L.or_create(self.n, box, mass, kT, dt, self.m_max, r_c, r_c_min, A_cons,
-                                    int(seed), int(vacf_len), int(vacf_stride), int(vacf_burnin),
+                                    int(seed), int(vacf_len), int(vacf_stride),
+                                    int(vacf_burnin) if vacf_burnin >= 0 else 2 * int(m_max),
                                     _p(pos), _p(vel))
         if not self._h:
             raise ValueError("oracle: invalid parameters")
@@ -246,6 +250,22 @@ class System:
         mass = C.c_double()
         self._L.or_get_coefs(self._h, _p(Kd), _p(A), _p(Cm), _p(Ch), _p(ab), C.byref(mass))
         return dict(Kd=Kd, A=A, C=Cm, Chat=Ch, a=ab[0], b=ab[1], clamped_mass=mass.value)
+
+    def set_paircorr(self, nbins: int, rmax: float) -> int:
+        """Enables C^a(R, t), C^c(R, t) (Sec. III A) on nbins distance bins of
+        [0, rmax), sampled with the VACF's origins; rmax <= r_c."""
+        st = self._L.or_set_paircorr(self._h, int(nbins), float(rmax))
+        if st == 0:
+            self._pc_nbins = int(nbins)
+        return st
+
+    def paircorr(self):
+        """(C^a, C^c, counts), each [vacf_len, nbins]."""
+        L, nb = self.vacf_len, self._pc_nbins
+        ca, cc = np.zeros((L, nb)), np.zeros((L, nb))
+        cnt = np.zeros((L, nb), dtype=np.int64)
+        self._L.or_get_paircorr(self._h, _p(ca), _p(cc), _p(cnt))
+        return ca, cc, cnt
 
     def vacf(self):
         out = np.zeros(max(self.vacf_len, 1))

@@ -56,7 +56,7 @@
  *   3 sign of the pair history term flipped
  *   4 inverse transform scaled by 1/m_max   5 history read one step late
  *   6 a_0 = 1 in the noise target           7 V_i in place of V_j at m = 0
- *   8 sign of F^C flipped */
+ *   8 sign of F^C flipped                  9 auto and cross pair terms swapped */
 #ifndef OR_PLANT
 #define OR_PLANT 0
 #endif
@@ -364,6 +364,12 @@ typedef struct {
     double *vorig, *csum;
     int64_t *ccnt, n_origins;
     int n_os;
+    /* distance-binned auto- and cross-correlations C^a(R,t), C^c(R,t) (Sec.
+     * III A): sums [vacf_len][pc_nbins] over unordered pairs and origins */
+    int pc_nbins;
+    double pc_rmax;
+    double *pc_a, *pc_c;
+    int64_t* pc_n;
     or_nblist nl;
 } or_sys;
 
@@ -375,7 +381,9 @@ or_sys* or_create(int n, double L, double mass, double kT, double dt, int m_max,
                   double rc_min, double A_cons, uint64_t seed, int vacf_len, int vacf_stride,
                   int64_t vacf_burnin, const double* pos, const double* vel)
 {
-    if (n < 0 || m_max < 2 || !(L > 0) || !(rc > 0) || rc > 0.5 * L || !(mass > 0) || !(dt > 0))
+    /* VACF samples are taken after each step: the first origin is t = 1 */
+    if (n < 0 || m_max < 2 || !(L > 0) || !(rc > 0) || rc > 0.5 * L || !(mass > 0) || !(dt > 0) ||
+        (vacf_len > 0 && vacf_burnin < 1))
         return NULL;
     or_sys* s = (or_sys*)calloc(1, sizeof(or_sys));
     s->n = n; s->L = L; s->mass = mass; s->kT = kT; s->dt = dt; s->m_max = m_max;
@@ -406,9 +414,9 @@ void or_destroy(or_sys* s)
 {
     if (!s) return;
     double* arrs[] = { s->Kd, s->gd, s->f, s->gsd, s->fs, s->C, s->Chat, s->A, s->pos, s->vel,
-                       s->fc, s->fd, s->fr, s->disp, s->hist, s->W, s->vorig, s->csum };
+                       s->fc, s->fd, s->fr, s->disp, s->hist, s->W, s->vorig, s->csum, s->pc_a, s->pc_c };
     for (size_t k = 0; k < sizeof(arrs) / sizeof(arrs[0]); ++k) free(arrs[k]);
-    free(s->wtime); free(s->ccnt); free(s->nl.start); free(s->nl.list);
+    free(s->wtime); free(s->ccnt); free(s->nl.start); free(s->nl.list); free(s->pc_n);
     free(s);
 }
 
@@ -561,6 +569,8 @@ static void random_force_i(const or_sys* s, int i, double F[3], int direct)
     }
 }
 
+static void paircorr_sample(or_sys* s, int64_t o_now);
+
 static void vacf_sample(or_sys* s)
 {
     /* V at time t = step (after the step that produced it). */
@@ -574,6 +584,7 @@ static void vacf_sample(or_sys* s)
         memcpy(s->vorig + (size_t)(o_now % s->n_os) * n3, s->vel, sizeof(double) * n3);
         s->n_origins++;
     }
+    paircorr_sample(s, o_now);
     for (int64_t o = o_now; o >= 0 && o > o_now - s->n_os; --o) {
         int64_t t0 = s->vacf_burnin + o * s->vacf_stride;
         int64_t lag = t - t0;
@@ -583,6 +594,79 @@ static void vacf_sample(or_sys* s)
         for (size_t k = 0; k < n3; ++k) acc += s->vel[k] * v0[k];
         s->csum[lag] += acc;
         s->ccnt[lag] += 1;
+    }
+}
+
+/* The pair part of the sample at time t = step: for every unordered pair
+ * i < j with r_ij(t) < r_max (distance at time t, bins of width r_max/nbins)
+ * and every active origin t0, with e = (R_i - R_j)/r at time t and the
+ * velocity components along e,
+ *   a = v_i(t) v_i(t0) + v_j(t) v_j(t0),   c = v_i(t) v_j(t0) + v_j(t) v_i(t0).
+ * C^a, C^c are the sums over i, j != i of these terms divided by twice the
+ * number of ordered pairs: per bin and lag, sum over unordered pairs / (2 n). */
+static void paircorr_sample(or_sys* s, int64_t o_now)
+{
+    if (s->pc_nbins <= 0) return;
+    const size_t n3 = (size_t)3 * s->n;
+    const double dr = s->pc_rmax / s->pc_nbins;
+    for (int i = 0; i < s->n; ++i) {
+        for (int64_t k = s->nl.start[i]; k < s->nl.start[i + 1]; ++k) {
+            const int j = s->nl.list[k];
+            if (j <= i) continue;
+            double d[3], r2 = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                d[c] = min_image(s->pos[3 * i + c] - s->pos[3 * j + c], s->L);
+                r2 += d[c] * d[c];
+            }
+            const double r = sqrt(r2);
+            if (!(r < s->pc_rmax)) continue;
+            int b = (int)(r / dr);
+            if (b >= s->pc_nbins) b = s->pc_nbins - 1;
+            double vit = 0.0, vjt = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                vit += s->vel[3 * i + c] * d[c] / r;
+                vjt += s->vel[3 * j + c] * d[c] / r;
+            }
+            for (int64_t o = o_now; o >= 0 && o > o_now - s->n_os; --o) {
+                const int64_t lag = s->step - (s->vacf_burnin + o * s->vacf_stride);
+                if (lag < 0 || lag >= s->vacf_len) continue;
+                const double* v0 = s->vorig + (size_t)(o % s->n_os) * n3;
+                double vi0 = 0.0, vj0 = 0.0;
+                for (int c = 0; c < 3; ++c) {
+                    vi0 += v0[3 * i + c] * d[c] / r;
+                    vj0 += v0[3 * j + c] * d[c] / r;
+                }
+                const size_t at = (size_t)lag * s->pc_nbins + b;
+                const double ta = vit * vi0 + vjt * vj0, tc = vit * vj0 + vjt * vi0;
+                s->pc_a[at] += OR_PLANT == 9 ? tc : ta;
+                s->pc_c[at] += OR_PLANT == 9 ? ta : tc;
+                s->pc_n[at] += 1;
+            }
+        }
+    }
+}
+
+int or_set_paircorr(or_sys* s, int nbins, double rmax)
+{
+    if (s->vacf_len <= 0 || nbins < 1 || !(rmax > 0) || rmax > s->rc) return -1;
+    free(s->pc_a); free(s->pc_c); free(s->pc_n);
+    const size_t cnt = (size_t)s->vacf_len * nbins;
+    s->pc_nbins = nbins;
+    s->pc_rmax = rmax;
+    s->pc_a = zalloc(cnt);
+    s->pc_c = zalloc(cnt);
+    s->pc_n = (int64_t*)calloc(cnt, sizeof(int64_t));
+    return 0;
+}
+
+/* ca, cc [vacf_len][nbins] (0 where no pair was seen), counts of pair samples. */
+void or_get_paircorr(const or_sys* s, double* ca, double* cc, int64_t* counts)
+{
+    const size_t cnt = (size_t)s->vacf_len * s->pc_nbins;
+    for (size_t k = 0; k < cnt; ++k) {
+        ca[k] = s->pc_n[k] > 0 ? s->pc_a[k] / (2.0 * (double)s->pc_n[k]) : 0.0;
+        cc[k] = s->pc_n[k] > 0 ? s->pc_c[k] / (2.0 * (double)s->pc_n[k]) : 0.0;
+        counts[k] = s->pc_n[k];
     }
 }
 

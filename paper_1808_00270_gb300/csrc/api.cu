@@ -412,7 +412,7 @@ gld_status gld_create(const gld_params* p, const double* pos, const double* vel,
     if (p->n < 1 || p->m_max < 2 || p->m_max > 4096 || !(p->box > 0) || !(p->mass > 0) || !(p->dt > 0) ||
         !(p->r_c > 0) || p->r_c > 0.5 * p->box || p->kT < 0 || p->r_c_min < 0 || p->skin < 0 ||
         (p->hist_dtype != GLD_HIST_F32 && p->hist_dtype != GLD_HIST_BF16) || p->vacf_len < 0 ||
-        (p->vacf_len > 0 && p->vacf_stride < 1) ||
+        (p->vacf_len > 0 && p->vacf_stride < 1) || (p->vacf_len > 0 && p->vacf_burnin == 0) ||
         (p->vacf_len > 0 && (p->vacf_len + p->vacf_stride - 1) / p->vacf_stride > 32))
         return GLD_E_INVAL;
     gld_ctx* c = new gld_ctx();

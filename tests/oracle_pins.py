@@ -394,6 +394,99 @@ def pin_vacf_accumulator(variant=0):
     return err < 1e-12 and n0 == len(range(burn, 60, stride)), f"max err {err:.1e}, origins {n0}"
 
 
+def _run_pair_corr(dt, Ks0, Kp0, Kds0, tau, T, variant):
+    m_max = int(round(2.0 / dt))
+    steps = int(round(T / dt))
+    s = oracle.System(n=2, box=100.0, mass=1.0, kT=0.0, dt=dt, m_max=m_max, r_c=10.0,
+                      vacf_len=steps, vacf_stride=steps + 1, vacf_burnin=1,
+                      pos=[[50, 50, 50], [53, 50, 50]], vel=[[1.0, 0, 0], [0, 0, 0]], variant=variant)
+    t = np.arange(m_max) * dt
+    g = np.exp(-t / tau)[None]
+    f = np.ones((1, 64))
+    if s.set_kernels(Ks0 * np.exp(-t / tau), g=Kp0 * g, f=f, dr=10.0 / 63, gs=Kds0 * g, fs=f) != 0:
+        return np.inf, np.inf
+    if s.set_paircorr(1, 10.0) != 0:
+        return np.inf, np.inf
+    s.step(steps)
+    ca, cc, cnt = s.paircorr()
+    tt = np.arange(steps + 1) * dt
+    phip = closed_form_vacf(tt, Ks0 + Kds0 + Kp0, tau)
+    phim = closed_form_vacf(tt, Ks0 + Kds0 - Kp0, tau)
+    # one origin at t0 = dt: C = (phi_+(t) phi_+(t0) +- phi_-(t) phi_-(t0)) / 4, t = t0 + lag
+    wa = (phip[1:] * phip[1] + phim[1:] * phim[1]) / 4
+    wc = (phip[1:] * phip[1] - phim[1:] * phim[1]) / 4
+    if not np.all(cnt[:, 0] == 1):
+        return np.inf, np.inf
+    return float(np.max(np.abs(ca[:, 0] - wa))), float(np.max(np.abs(cc[:, 0] - wc)))
+
+
+def pin_paircorr_closed_form(variant=0):
+    """Two particles on a line with flat pair kernels (Sec. III A), V_1(0) = 1,
+    V_2(0) = 0, kT = 0: V_+- = (V_1 +- V_2)/sqrt 2 follow the closed forms
+    phi_+-/sqrt 2 of K^s + dK^s +- K^p, so with one origin t0 the
+    distance-binned correlations are C^a = (phi_+(t) phi_+(t0) + phi_-(t)
+    phi_-(t0))/4 and C^c = (phi_+(t) phi_+(t0) - phi_-(t) phi_-(t0))/4."""
+    errs = [_run_pair_corr(dt, 20.0, 8.0, 3.0, 0.1, 1.0, variant) for dt in (0.01, 0.005, 0.0025)]
+    ea = [e[0] for e in errs]
+    ec = [e[1] for e in errs]
+    ok = max(ea[2], ec[2]) < 5e-5 and 3.5 < ea[1] / ea[2] < 4.5 and 3.5 < ec[1] / ec[2] < 4.5
+    return ok, f"C^a errors {ea}, C^c errors {ec}"
+
+
+def paircorr_definition(P, V, box, rmax, nbins, L, stride, burn):
+    """C^a, C^c and counts [L, nbins] from recorded positions P[t] and
+    velocities V[t] (all pairs, brute force)."""
+    T = len(P)
+    n = P[0].shape[0]
+    sa, sc = np.zeros((L, nbins)), np.zeros((L, nbins))
+    cnt = np.zeros((L, nbins), dtype=np.int64)
+    iu, ju = np.triu_indices(n, 1)
+    for t in range(T):
+        d = P[t][iu] - P[t][ju]
+        d -= box * np.round(d / box)
+        r = np.sqrt((d * d).sum(1))
+        sel = r < rmax
+        e = d[sel] / r[sel][:, None]
+        b = np.minimum((r[sel] / (rmax / nbins)).astype(int), nbins - 1)
+        i, j = iu[sel], ju[sel]
+        vit, vjt = (V[t][i] * e).sum(1), (V[t][j] * e).sum(1)
+        for t0 in range(burn, t + 1, stride):
+            lag = t - t0
+            if lag >= L:
+                continue
+            vi0, vj0 = (V[t0][i] * e).sum(1), (V[t0][j] * e).sum(1)
+            np.add.at(sa[lag], b, vit * vi0 + vjt * vj0)
+            np.add.at(sc[lag], b, vit * vj0 + vjt * vi0)
+            np.add.at(cnt[lag], b, 1)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return (np.where(cnt > 0, sa / (2 * np.maximum(cnt, 1)), 0.0),
+                np.where(cnt > 0, sc / (2 * np.maximum(cnt, 1)), 0.0), cnt)
+
+
+def pin_paircorr_definition(variant=0):
+    """The distance-binned accumulators equal the definition evaluated by brute
+    force over all pairs of the recorded trajectory (several bins and origins)."""
+    w = inputs.SMALL
+    pos, vel = inputs.initial_state(w, seed=6)
+    L, stride, burn, nbins = 10, 3, 4, 5
+    s = oracle.System(n=w.n, box=w.box, mass=1.0, kT=1.0, dt=w.dt, m_max=w.m_max, r_c=w.r_c,
+                      A_cons=w.A_cons, seed=5, vacf_len=L, vacf_stride=stride, vacf_burnin=burn,
+                      pos=pos, vel=vel, variant=variant)
+    g, f, dr = inputs.pair_kernel_tables(w)
+    s.set_kernels(inputs.self_kernel_samples(w), g=g, f=f, dr=dr)
+    if s.set_paircorr(nbins, w.r_c) != 0:
+        return False, "set_paircorr failed"
+    P, V = [s.get(oracle.POS)], [s.get(oracle.VEL)]
+    for _ in range(1, 40):
+        s.step(1)
+        P.append(s.get(oracle.POS))
+        V.append(s.get(oracle.VEL))
+    wa, wc, wn = paircorr_definition(P, V, w.box, w.r_c, nbins, L, stride, burn)
+    ca, cc, cnt = s.paircorr()
+    err = max(np.max(np.abs(ca - wa)), np.max(np.abs(cc - wc)))
+    return bool(np.array_equal(cnt, wn) and err < 1e-12 and wn.sum() > 0), f"max err {err:.1e}, samples {wn.sum()}"
+
+
 ALL = {
     "philox_kat": pin_philox_kat,
     "gauss_moments": pin_gauss_moments,
@@ -410,4 +503,6 @@ ALL = {
     "noise_autocorrelation": pin_noise_autocorrelation,
     "vacf_closed_form": pin_vacf_closed_form,
     "vacf_accumulator": pin_vacf_accumulator,
+    "paircorr_closed_form": pin_paircorr_closed_form,
+    "paircorr_definition": pin_paircorr_definition,
 }

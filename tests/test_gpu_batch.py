@@ -113,8 +113,8 @@ def test_batch_vacf_matches_single_system():
     stepped alone (to FP32 rounding of the trajectory)."""
     from paper_1808_00270_gb300 import Batch
     w = _mixed()[2]
-    a = make_gpu(w, vacf_len=100, vacf_stride=20, vacf_burnin=0)
-    g = make_gpu(w, vacf_len=100, vacf_stride=20, vacf_burnin=0)
+    a = make_gpu(w, vacf_len=100, vacf_stride=20, vacf_burnin=1)
+    g = make_gpu(w, vacf_len=100, vacf_stride=20, vacf_burnin=1)
     other = make_gpu(_mixed()[1], vacf_len=50, vacf_stride=50, vacf_burnin=10)
     b = Batch()
     b.add(g)

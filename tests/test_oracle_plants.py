@@ -14,6 +14,7 @@ PLANTS = {
     6: "a_0 = 1 in the noise target",
     7: "V_i in place of V_j in the instantaneous pair term",
     8: "conservative force with the wrong sign",
+    9: "auto and cross pair correlation terms swapped",
 }
 
 
