@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--graph-form", default="conditional", choices=["conditional", "gated"],
                     help="gated: rebuild kernels gated on the device instead of a conditional graph node "
                          "(every graph node a plain kernel, which per-kernel profilers can capture)")
+    ap.add_argument("--pcorr", type=int, default=0,
+                    help="also accumulate the distance-binned pair correlations on this many bins of [0, r_c)")
     ap.add_argument("--hist", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--kahan", action="store_true")
     ap.add_argument("--reference-seconds", type=float, default=120.0)
@@ -399,6 +401,8 @@ def main():
     ks = inputs.self_kernel_samples(w)
     g, f, dr = inputs.pair_kernel_tables(w)
     cfg = dict(w.describe())
+    if args.pcorr > 0:
+        cfg["pair_correlation_bins"] = args.pcorr
     cfg.update({"global_batch": w.n * world, "parallelism": f"replicas{world}",
                 "l2": "inputs larger than L2: 1.26 GB FP32 history ring streamed every step"})
 
@@ -432,6 +436,8 @@ def main():
                   use_graphs=2 if args.graph_form == "gated" else 1, **vacf)
     sim = GLD(pos=pos, vel=vel, **common)
     sim.set_kernels(ks, g=g, f=f, dr=dr)
+    if args.pcorr > 0:
+        sim.set_pair_correlation(args.pcorr, w.r_c)
     T = 64
     # warm-up: at least W steps, then up to a noise-block boundary and one graph replay
     sim.step(max(args.warmup, 3))
@@ -484,6 +490,8 @@ def main():
         launches = K * 5 + 4 * (d1["rebuilds"] - d0["rebuilds"]) + 2 * T_blocks
     else:
         launches = K * 8 + 2 * T_blocks
+    if args.pcorr > 0:
+        launches += K
     e2e = None
     if not args.no_e2e:
         torch.cuda.synchronize()

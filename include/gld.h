@@ -221,9 +221,28 @@ enum {
     GLD_PROF_CELL = 3,   /* cell + neighbour-list rebuild (4 kernels, gated)  */
     GLD_PROF_CFORCE = 4, /* F^C_{n+1} and velocity update                     */
     GLD_PROF_VACF = 5,   /* velocity autocorrelation                          */
-    GLD_PROF_N = 6
+    GLD_PROF_PCORR = 6,  /* distance-binned pair correlations (when enabled)  */
+    GLD_PROF_N = 7
 };
 gld_status gld_profile_steps(gld_ctx* ctx, int64_t nsteps, double* ms, int64_t* launches);
+
+/* Distance-binned velocity auto- and cross-correlations of pairs (Sec. III A,
+ * the functions C^a(R,t) and C^c(R,t) from which the paper reconstructs the
+ * pair memory kernels), sampled with the VACF's origins: for every unordered
+ * pair i < j with r_ij(t) < r_max in bins of width r_max/nbins (distance at
+ * the later time t), with e = (R_i - R_j)/r_ij(t) and the velocity components
+ * along e,
+ *   C^a(bin, lag) = < v_i(t) v_i(t0) + v_j(t) v_j(t0) > / 2,
+ *   C^c(bin, lag) = < v_i(t) v_j(t0) + v_j(t) v_i(t0) > / 2,  lag = t - t0,
+ * averaged over the pairs and origins of the bin.  Needs vacf_len > 0 and
+ * 0 < r_max <= r_c; origins in flight x nbins <= 2048 (else GLD_E_INVAL).
+ * Per-step sums are kept in 2^-28 fixed point (order-independent, so results
+ * are reproducible bit for bit), accumulated in FP64.  Setting it again
+ * clears the sums; contexts with it cannot join a batch. */
+gld_status gld_set_pair_correlation(gld_ctx* ctx, int32_t nbins, double r_max);
+/* ca, cc [vacf_len][nbins] (0 where the bin saw no pair), counts [vacf_len]
+ * [nbins] pair samples; any pointer may be NULL.  Synchronizes. */
+gld_status gld_pair_correlation(gld_ctx* ctx, double* ca, double* cc, int64_t* counts);
 
 /* Device bytes the context holds (all of its buffers, 256-byte granules). */
 gld_status gld_get_bytes(gld_ctx* ctx, int64_t* bytes);

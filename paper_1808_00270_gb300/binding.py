@@ -97,6 +97,8 @@ def lib():
             "gld_hist_conv_dev": (i32, [vp, i32, i32, i32, i64, vp, i32, vp, i32, vp]),
             "gld_pairs_noalloc": (i32, [vp, i32, d, d, vp, i64, vp, vp]),
             "gld_get_bytes": (i32, [vp, C.POINTER(i64)]),
+            "gld_set_pair_correlation": (i32, [vp, i32, d]),
+            "gld_pair_correlation": (i32, [vp, vp, vp, vp]),
             "gld_bytes_needed": (i32, [C.POINTER(Params), i32, i32, i32, C.POINTER(i64)]),
             "gld_batch_set_tuning": (i32, [vp, i32]),
             "gld_server_params_default": (None, [C.POINTER(ServerParams)]),
@@ -137,7 +139,8 @@ def exported_symbols() -> list[str]:
             "gld_batch_destroy", "gld_get_bytes", "gld_bytes_needed", "gld_batch_set_tuning",
             "gld_server_params_default", "gld_server_create", "gld_server_submit", "gld_server_pump",
             "gld_server_drain", "gld_server_clock", "gld_server_result", "gld_server_stats",
-            "gld_server_last_error", "gld_server_destroy", "gld_server_cancel"]
+            "gld_server_last_error", "gld_server_destroy", "gld_server_cancel", "gld_set_pair_correlation",
+            "gld_pair_correlation"]
 
 
 def _ptr(a: np.ndarray):
@@ -300,6 +303,19 @@ class GLD:
         self._check(lib().gld_get_diag(self._h, _ptr(out), 4))
         return dict(graph_mode=int(out[0]), rebuilds=int(out[1]), maxnb=int(out[2]), cells_per_edge=int(out[3]))
 
+    def set_pair_correlation(self, nbins: int, r_max: float):
+        """Enables C^a(R, t), C^c(R, t) on nbins distance bins of [0, r_max)."""
+        self._check(lib().gld_set_pair_correlation(self._h, int(nbins), float(r_max)))
+        self._pc_nbins = int(nbins)
+
+    def pair_correlation(self):
+        """(C^a, C^c, counts), each [vacf_len, nbins]."""
+        L, nb = self.vacf_len, self._pc_nbins
+        ca, cc = np.zeros((L, nb)), np.zeros((L, nb))
+        cnt = np.zeros((L, nb), dtype=np.int64)
+        self._check(lib().gld_pair_correlation(self._h, _ptr(ca), _ptr(cc), _ptr(cnt)))
+        return ca, cc, cnt
+
     def bytes(self) -> int:
         """Device bytes this system holds."""
         b = C.c_int64()
@@ -318,12 +334,12 @@ class GLD:
         self._check(lib().gld_get_coefs(self._h, _ptr(Kd), _ptr(A), _ptr(ab), _ptr(spec)))
         return dict(Kd=Kd, A=A, a=ab[0], b=ab[1], spec_min=spec[0], clamped_mass=spec[1])
 
-    PROF_NAMES = ("noise", "hist_conv", "pair_force_integrate", "cell_build", "cforce", "vacf")
+    PROF_NAMES = ("noise", "hist_conv", "pair_force_integrate", "cell_build", "cforce", "vacf", "pcorr")
 
     def profile_steps(self, nsteps: int):
         """Runs nsteps steps with per-kernel CUDA-event timing; returns
         {family: (milliseconds, launches)}."""
-        ms, n = np.zeros(6), np.zeros(6, dtype=np.int64)
+        ms, n = np.zeros(len(self.PROF_NAMES)), np.zeros(len(self.PROF_NAMES), dtype=np.int64)
         self._check(lib().gld_profile_steps(self._h, int(nsteps), _ptr(ms), _ptr(n)))
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.PROF_NAMES)}
 

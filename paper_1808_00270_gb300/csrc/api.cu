@@ -192,7 +192,8 @@ cudaError_t launch_one_step(gld_ctx* c, cudaStream_t s)
     if ((e = launch_pair_force_integrate(c->P, c->B, s)) != cudaSuccess) return e;
     if ((e = launch_rebuild(c->P, c->B, s)) != cudaSuccess) return e;
     if ((e = launch_cforce(c->P, c->B, 1, s)) != cudaSuccess) return e;
-    return launch_vacf(c->P, c->B, s);
+    if ((e = launch_vacf(c->P, c->B, s)) != cudaSuccess) return e;
+    return launch_pcorr(c->P, c->B, s);
 }
 
 // One step captured with the rebuild kernels in the body of a conditional
@@ -233,6 +234,7 @@ cudaError_t capture_step_conditional(gld_ctx* c, cudaStream_t s)
     }
     if (e == cudaSuccess) e = launch_cforce(c->P, c->B, 1, s);
     if (e == cudaSuccess) e = launch_vacf(c->P, c->B, s);
+    if (e == cudaSuccess) e = launch_pcorr(c->P, c->B, s);
     return e;
 }
 
@@ -896,7 +898,8 @@ gld_status gld_profile_steps(gld_ctx* c, int64_t nsteps, double* ms, int64_t* la
     // block ahead of the device, then every kernel family is bracketed by an
     // event pair, so the device times contain no host launch gaps.
     const bool vac = c->P.vacf_len > 0;
-    const size_t nk = 1 + (size_t)T * (vac ? 5 : 4);
+    const bool pcor = vac && c->P.pc_nbins > 0;
+    const size_t nk = 1 + (size_t)T * (4 + (vac ? 1 : 0) + (pcor ? 1 : 0));
     std::vector<cudaEvent_t> ev(2 * nk, nullptr);
     std::vector<int> fam(nk);
     gld_status s = GLD_OK;
@@ -931,6 +934,7 @@ gld_status gld_profile_steps(gld_ctx* c, int64_t nsteps, double* ms, int64_t* la
             timed(GLD_PROF_CELL, [&] { return launch_rebuild(c->P, c->B, c->st); });
             timed(GLD_PROF_CFORCE, [&] { return launch_cforce(c->P, c->B, 1, c->st); });
             if (vac) timed(GLD_PROF_VACF, [&] { return launch_vacf(c->P, c->B, c->st); });
+            if (pcor) timed(GLD_PROF_PCORR, [&] { return launch_pcorr(c->P, c->B, c->st); });
             c->last_fr_row = t;
             ++c->host_step;
         }
@@ -953,6 +957,62 @@ gld_status gld_profile_steps(gld_ctx* c, int64_t nsteps, double* ms, int64_t* la
     }
     if (s != GLD_OK) return s;
     return sync_and_check(c);
+}
+
+gld_status gld_set_pair_correlation(gld_ctx* c, int32_t nbins, double r_max)
+{
+    if (!c) return GLD_E_INVAL;
+    StepParams& P = c->P;
+    if (P.vacf_len <= 0) return fail(c, GLD_E_INVAL, "gld_set_pair_correlation: the VACF (vacf_len > 0) is off");
+    if (nbins < 1 || !(r_max > 0) || r_max > c->prm.r_c)
+        return fail(c, GLD_E_INVAL, "gld_set_pair_correlation: need nbins >= 1 and 0 < r_max <= r_c");
+    if ((long long)P.n_os * nbins > kPcMaxOriginBins)
+        return fail(c, GLD_E_INVAL, "gld_set_pair_correlation: origins in flight x bins exceeds 2048");
+    GLD_TRY(sync_and_check(c));
+    dfree(c, c->B.pc_step);
+    dfree(c, c->B.pc_sa);
+    dfree(c, c->B.pc_sc);
+    dfree(c, c->B.pc_n);
+    c->B.pc_step = nullptr;
+    c->B.pc_sa = c->B.pc_sc = nullptr;
+    c->B.pc_n = nullptr;
+    P.pc_nbins = 0;
+    bool ok = true;
+    const size_t cells = (size_t)P.vacf_len * nbins;
+    c->B.pc_step = alloc_n<long long>(c, 2 * 3 * (size_t)P.n_os * nbins, ok);
+    c->B.pc_sa = alloc_n<double>(c, cells, ok);
+    c->B.pc_sc = alloc_n<double>(c, cells, ok);
+    c->B.pc_n = alloc_n<long long>(c, cells, ok);
+    if (!ok) return fail(c, GLD_E_NOMEM, "gld_set_pair_correlation: allocation failed");
+    P.pc_nbins = nbins;
+    P.pc_rmax2 = (float)(r_max * r_max);
+    P.pc_inv_dr = (float)(nbins / r_max);
+    const int zero[2] = {0, 0};  // no sums pending from an earlier setting
+    GLD_CUDA(c, cudaMemcpyAsync(&c->B.ctrl->pc_pending, zero, sizeof(int), cudaMemcpyHostToDevice, c->st));
+    GLD_CUDA(c, cudaMemcpyAsync(&c->B.ctrl->pc_pv_nact, zero, sizeof(int), cudaMemcpyHostToDevice, c->st));
+    invalidate_graph(c);  // the step now has one more kernel
+    return sync_and_check(c);
+}
+
+gld_status gld_pair_correlation(gld_ctx* c, double* ca, double* cc, int64_t* counts)
+{
+    if (!c) return GLD_E_INVAL;
+    const StepParams& P = c->P;
+    if (P.pc_nbins <= 0) return fail(c, GLD_E_STATE, "gld_pair_correlation: not enabled");
+    if (c->latched == GLD_OK) GLD_CUDA(c, launch_pcorr_flush(P, c->B, c->st));
+    GLD_TRY(sync_and_check(c));
+    const size_t cells = (size_t)P.vacf_len * P.pc_nbins;
+    std::vector<double> sa(cells), sc(cells);
+    std::vector<long long> sn(cells);
+    GLD_CUDA(c, cudaMemcpy(sa.data(), c->B.pc_sa, sizeof(double) * cells, cudaMemcpyDeviceToHost));
+    GLD_CUDA(c, cudaMemcpy(sc.data(), c->B.pc_sc, sizeof(double) * cells, cudaMemcpyDeviceToHost));
+    GLD_CUDA(c, cudaMemcpy(sn.data(), c->B.pc_n, sizeof(long long) * cells, cudaMemcpyDeviceToHost));
+    for (size_t k = 0; k < cells; ++k) {
+        if (ca) ca[k] = sn[k] > 0 ? sa[k] / (2.0 * (double)sn[k]) : 0.0;
+        if (cc) cc[k] = sn[k] > 0 ? sc[k] / (2.0 * (double)sn[k]) : 0.0;
+        if (counts) counts[k] = sn[k];
+    }
+    return GLD_OK;
 }
 
 const char* gld_last_error(const gld_ctx* c) { return c ? c->msg.c_str() : "null context"; }
@@ -1275,6 +1335,8 @@ gld_status gld_batch_add(gld_batch* b, gld_ctx* c)
     if (!c->have_kernels) return bfail(b, GLD_E_STATE, "gld_batch_add: the member has no kernels set");
     if (c->st != b->st) return bfail(b, GLD_E_INVAL, "gld_batch_add: the member must use the batch's stream");
     if (c->P.T != kMaxNoiseBlock) return bfail(b, GLD_E_INVAL, "gld_batch_add: the member's noise block must be 64");
+    if (c->P.pc_nbins > 0)
+        return bfail(b, GLD_E_INVAL, "gld_batch_add: pair correlations are accumulated by single contexts only");
     if (c->noise_valid && c->host_step != c->noise_end)
         return bfail(b, GLD_E_STATE, "gld_batch_add: the member is inside a noise block (step a multiple of 64)");
     for (gld_ctx* m : b->members)

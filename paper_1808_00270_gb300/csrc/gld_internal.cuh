@@ -15,6 +15,7 @@ namespace gld {
 
 constexpr int kMaxQ = 4;            // separable terms per pair-kernel family
 constexpr int kMaxAcc = 1 + 2 * kMaxQ;
+constexpr int kPcMaxOriginBins = 2048;  // origins x bins of the pair correlations (48 KB of shared sums)
 constexpr int kVacfMaxBlocks = 256;  // particle blocks of the VACF grid at most
 constexpr int kMaxNoiseBlock = 64;  // register-resident outputs per FIR thread
 
@@ -45,6 +46,8 @@ struct Ctrl {
     int vacf_pending;
     // the previous launch's schedule as the next VACF kernel must fold it
     int pv_nact, pv_lag0, pv_buf;
+    // the same bookkeeping for the distance-binned pair correlations
+    int pc_pending, pc_buf, pc_pv_nact, pc_pv_lag0, pc_pv_buf, pad3_;
 };
 
 // Everything a step kernel needs, passed by value.
@@ -66,6 +69,9 @@ struct StepParams {
     // VACF
     int vacf_len, vacf_stride, n_os;
     long long vacf_burnin;
+    // distance-binned pair correlations (0 bins: off)
+    int pc_nbins;
+    float pc_rmax2, pc_inv_dr;  // r_max^2, nbins / r_max
 };
 
 // ---------------------------------------------------------------- Philox --

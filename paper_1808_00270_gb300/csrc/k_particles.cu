@@ -22,6 +22,8 @@
 // and a thread handles one particle id, so own loads are coalesced and
 // neighbours lie close in memory; ids never change, so the displacement
 // history is never permuted.
+#include <algorithm>
+
 #include <cuda_bf16.h>
 
 #include "launch.h"
@@ -47,7 +49,13 @@ __device__ __forceinline__ float dot3(float ax, float ay, float az, float bx, fl
 // active while its lag t - t_j is below vacf_len.
 __device__ __forceinline__ void vacf_schedule(const StepParams& P, Ctrl* __restrict__ ctrl, long long t)
 {
-    // the partials of the last VACF launch are folded by the next one
+    // the partials of the last VACF launch are folded by the next one; the
+    // same for the pair correlations' per-step sums
+    ctrl->pc_pv_nact = ctrl->pc_pending ? ctrl->vacf_nact : 0;
+    ctrl->pc_pv_lag0 = ctrl->vacf_lag0;
+    ctrl->pc_pv_buf = ctrl->pc_buf;
+    ctrl->pc_pending = 0;
+    ctrl->pc_buf ^= 1;
     ctrl->pv_nact = ctrl->vacf_pending ? ctrl->vacf_nact : 0;
     ctrl->pv_lag0 = ctrl->vacf_lag0;
     ctrl->pv_buf = ctrl->vacf_buf;
@@ -640,6 +648,109 @@ __global__ void __launch_bounds__(kThreads) vacf_flush(const StepParams P, Ctrl*
     if (threadIdx.x == 0) ctrl->vacf_pending = 0;
 }
 
+// ---- distance-binned pair correlations C^a(R,t), C^c(R,t) (Sec. III A) -----
+constexpr float kPcScale = 268435456.0f;       // 2^28: fixed point of the per-step sums
+constexpr double kPcUnscale = 1.0 / 268435456.0;
+
+__device__ __forceinline__ long long pc_fixed(float x) { return __float2ll_rn(x * kPcScale); }
+
+// Adds per-step sums (buffer buf, origins q < nact) to the FP64 sums of their
+// lags and clears them; entry k of the grid-wide range by one thread each.
+__device__ __forceinline__ void pcorr_fold(const StepParams& P, long long* __restrict__ step_sums, int buf, int nact,
+                                           int lag0, double* __restrict__ sa, double* __restrict__ sc,
+                                           long long* __restrict__ sn, long long k0, long long kstep)
+{
+    long long* b = step_sums + (size_t)buf * P.n_os * P.pc_nbins * 3;
+    for (long long k = k0; k < (long long)nact * P.pc_nbins; k += kstep) {
+        const int q = (int)(k / P.pc_nbins), bin = (int)(k - (long long)q * P.pc_nbins);
+        long long* e = b + 3 * k;
+        const size_t at = (size_t)(lag0 + q * P.vacf_stride) * P.pc_nbins + bin;
+        sa[at] += (double)e[0] * kPcUnscale;
+        sc[at] += (double)e[1] * kPcUnscale;
+        sn[at] += e[2];
+        e[0] = e[1] = e[2] = 0;
+    }
+}
+
+// At time t (after the VACF kernel stored this step's origin): for every
+// unordered pair i < j of the neighbour lists with r_ij(t) < r_max and every
+// active origin t0, with e = (R_i - R_j)/r and velocity components along e,
+// a = v_i(t) v_i(t0) + v_j(t) v_j(t0) and c = v_i(t) v_j(t0) + v_j(t) v_i(t0)
+// are added to the bin of r_ij(t) in 2^-28 fixed point (integer sums do not
+// depend on the order of the atomics, so results are reproducible bit for
+// bit).  The previous launch's sums are folded into the FP64 sums meanwhile.
+__global__ void __launch_bounds__(kThreads) pcorr(const StepParams P, Ctrl* __restrict__ ctrl,
+                                                  const float4* __restrict__ pos, const float4* __restrict__ vel,
+                                                  const float4* __restrict__ vorig, const int* __restrict__ nbr,
+                                                  const int* __restrict__ nbr_cnt, long long* __restrict__ step_sums,
+                                                  double* __restrict__ sa, double* __restrict__ sc,
+                                                  long long* __restrict__ sn)
+{
+    if (ctrl->pc_pv_nact > 0)
+        pcorr_fold(P, step_sums, ctrl->pc_pv_buf, ctrl->pc_pv_nact, ctrl->pc_pv_lag0, sa, sc, sn,
+                   (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+    if (!ctrl->vacf_on) return;  // uniform over the grid
+    const int n_act = ctrl->vacf_nact;
+    const bool is_origin = ctrl->vacf_origin != 0;
+    const int slot0 = ctrl->vacf_slot0;
+    const int nb = P.pc_nbins;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->pc_pending = 1;
+    extern __shared__ long long hs[];  // [n_act][nbins][3]
+    for (int k = threadIdx.x; k < n_act * nb * 3; k += blockDim.x) hs[k] = 0;
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < P.n) {
+        const float4 pi = pos[i], vi = vel[i];
+        const int cnt = nbr_cnt[i];
+        for (int s = 0; s < cnt; ++s) {
+            const int j = __ldg(nbr + (size_t)s * P.n_pad + i);
+            if (j <= i) continue;
+            const float4 pj = __ldg(pos + j);
+            const float dx = min_image(pi.x, pj.x, P.box, P.half_box);
+            const float dy = min_image(pi.y, pj.y, P.box, P.half_box);
+            const float dz = min_image(pi.z, pj.z, P.box, P.half_box);
+            const float r2 = dist2(dx, dy, dz);
+            if (!(r2 < P.pc_rmax2)) continue;
+            const float r = sqrtf(r2);
+            const float inv = 1.0f / r;
+            const float ex = dx * inv, ey = dy * inv, ez = dz * inv;
+            const int bin = min((int)(r * P.pc_inv_dr), nb - 1);
+            const float4 vj = __ldg(vel + j);
+            const float vit = vi.x * ex + vi.y * ey + vi.z * ez;
+            const float vjt = vj.x * ex + vj.y * ey + vj.z * ez;
+            for (int q = 0; q < n_act; ++q) {
+                float vi0 = vit, vj0 = vjt;
+                if (!(q == 0 && is_origin)) {
+                    int sl = slot0 - q;
+                    sl = sl < 0 ? sl + P.n_os : sl;
+                    const float4 oi = __ldg(vorig + (size_t)sl * P.n + i), oj = __ldg(vorig + (size_t)sl * P.n + j);
+                    vi0 = oi.x * ex + oi.y * ey + oi.z * ez;
+                    vj0 = oj.x * ex + oj.y * ey + oj.z * ez;
+                }
+                long long* h = hs + 3 * (q * nb + bin);
+                atomicAdd((unsigned long long*)h, (unsigned long long)pc_fixed(vit * vi0 + vjt * vj0));
+                atomicAdd((unsigned long long*)(h + 1), (unsigned long long)pc_fixed(vit * vj0 + vjt * vi0));
+                atomicAdd((unsigned long long*)(h + 2), 1ull);
+            }
+        }
+    }
+    __syncthreads();
+    long long* out = step_sums + (size_t)ctrl->pc_buf * P.n_os * nb * 3;
+    for (int k = threadIdx.x; k < n_act * nb * 3; k += blockDim.x)
+        if (hs[k] != 0) atomicAdd((unsigned long long*)(out + k), (unsigned long long)hs[k]);
+}
+
+// Folds the last launch's sums (before they are read).
+__global__ void __launch_bounds__(kThreads) pcorr_flush(const StepParams P, Ctrl* __restrict__ ctrl,
+                                                        long long* __restrict__ step_sums, double* __restrict__ sa,
+                                                        double* __restrict__ sc, long long* __restrict__ sn)
+{
+    if (!ctrl->pc_pending) return;
+    pcorr_fold(P, step_sums, ctrl->pc_buf, ctrl->vacf_nact, ctrl->vacf_lag0, sa, sc, sn, threadIdx.x, blockDim.x);
+    __syncthreads();
+    if (threadIdx.x == 0) ctrl->pc_pending = 0;
+}
+
 // ---- explicit pair lists (checks of the traversals) -------------------------
 __device__ __forceinline__ void emit_pair(int id, int jd, int* __restrict__ pairs, long long cap,
                                           unsigned long long* __restrict__ count)
@@ -855,6 +966,23 @@ cudaError_t launch_vacf_flush(const StepParams& P, const ParticleBuffers& B, cud
 {
     if (P.vacf_len <= 0) return cudaSuccess;
     vacf_flush<<<1, kThreads, 0, st>>>(P, B.ctrl, B.vpartial, B.csum, B.ccnt, B.vacf_gx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pcorr(const StepParams& P, const ParticleBuffers& B, cudaStream_t st)
+{
+    if (P.pc_nbins <= 0 || P.vacf_len <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)std::max(1, (P.n + kThreads - 1) / kThreads);
+    const size_t smem = sizeof(long long) * 3 * (size_t)P.n_os * P.pc_nbins;
+    pcorr<<<grid, kThreads, smem, st>>>(P, B.ctrl, B.pos, B.vel, B.vorig, B.nbr, B.nbr_cnt, B.pc_step, B.pc_sa,
+                                        B.pc_sc, B.pc_n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pcorr_flush(const StepParams& P, const ParticleBuffers& B, cudaStream_t st)
+{
+    if (P.pc_nbins <= 0 || P.vacf_len <= 0) return cudaSuccess;
+    pcorr_flush<<<1, kThreads, 0, st>>>(P, B.ctrl, B.pc_step, B.pc_sa, B.pc_sc, B.pc_n);
     return cudaGetLastError();
 }
 

@@ -37,6 +37,11 @@ struct ParticleBuffers {
     long long* norig;
     unsigned* vdone;
     int vacf_gx;
+    // pair correlations: per-step fixed-point sums [2][n_os][nbins][3] (a, c,
+    // count) and the FP64 sums [vacf_len][nbins] with their counts
+    long long* pc_step;
+    double *pc_sa, *pc_sc;
+    long long* pc_n;
 };
 
 cudaError_t launch_pair_force_integrate(const StepParams& P, const ParticleBuffers& B, cudaStream_t st);
@@ -56,6 +61,10 @@ cudaError_t launch_cforce(const StepParams& P, const ParticleBuffers& B, int mod
 cudaError_t launch_vacf(const StepParams& P, const ParticleBuffers& B, cudaStream_t st);
 // Adds the last VACF launch's partials to the FP64 sums (before reading them).
 cudaError_t launch_vacf_flush(const StepParams& P, const ParticleBuffers& B, cudaStream_t st);
+// Distance-binned pair correlations at the current step (after vacf), and the
+// fold of the last launch's sums before they are read.
+cudaError_t launch_pcorr(const StepParams& P, const ParticleBuffers& B, cudaStream_t st);
+cudaError_t launch_pcorr_flush(const StepParams& P, const ParticleBuffers& B, cudaStream_t st);
 // Pairs from a fresh cell traversal of pos_sorted / cell_start.
 cudaError_t launch_pair_list(const StepParams& P, const ParticleBuffers& B, int* pairs,
                              long long cap, unsigned long long* count, cudaStream_t st);

@@ -55,3 +55,9 @@ def test_server_struct_layouts_match_header():
     assert [f for f, _ in binding.Request._fields_] == _fields("gld_request")
     assert [f for f, _ in binding.ServerParams._fields_] == _fields("gld_server_params")
     assert len(binding.SRV_STATS) == 11  # GLD_SRV_N
+
+
+def test_profile_families_match_header():
+    text = open(HEADER).read()
+    n = int(re.search(r"GLD_PROF_N\s*=\s*(\d+)", text).group(1))
+    assert len(binding.GLD.PROF_NAMES) == n
