@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--graph-form", default="conditional", choices=["conditional", "gated"],
                     help="gated: rebuild kernels gated on the device instead of a conditional graph node "
                          "(every graph node a plain kernel, which per-kernel profilers can capture)")
+    ap.add_argument("--modes", action="store_true",
+                    help="memory sums in auxiliary-variable form (the workload's kernels are sums of damped modes) "
+                         "instead of the history-ring convolution")
     ap.add_argument("--pcorr", type=int, default=0,
                     help="also accumulate the distance-binned pair correlations on this many bins of [0, r_c)")
     ap.add_argument("--hist", default="f32", choices=["f32", "bf16"])
@@ -403,6 +406,8 @@ def main():
     cfg = dict(w.describe())
     if args.pcorr > 0:
         cfg["pair_correlation_bins"] = args.pcorr
+    if args.modes:
+        cfg["memory"] = "auxiliary-variable modes (O(1) per particle-step in m_max)"
     cfg.update({"global_batch": w.n * world, "parallelism": f"replicas{world}",
                 "l2": "inputs larger than L2: 1.26 GB FP32 history ring streamed every step"})
 
@@ -438,6 +443,8 @@ def main():
     sim.set_kernels(ks, g=g, f=f, dr=dr)
     if args.pcorr > 0:
         sim.set_pair_correlation(args.pcorr, w.r_c)
+    if args.modes:
+        sim.set_memory_modes(*inputs.memory_modes(w))
     T = 64
     # warm-up: at least W steps, then up to a noise-block boundary and one graph replay
     sim.step(max(args.warmup, 3))
@@ -474,13 +481,19 @@ def main():
     alg_bytes = (4 * 3 * (w.m_max - 1) + 4 * 3 * nacc) * w.n * (0.5 if args.hist == "bf16" else 1.0)
     if args.hist == "bf16":
         alg_bytes = (2 * 3 * (w.m_max - 1) + 4 * 3 * nacc) * w.n
+    kname, traffic = "hist_conv", measured_traffic(args.workload)
+    if args.modes:  # per column: Y' of every mode read and written, two ring values, the projections
+        nm = len(inputs.memory_modes(w)[0])
+        elem = 2 if args.hist == "bf16" else 4
+        alg_bytes = 3 * ((w.n + 31) // 32 * 32) * (16 * nm + 2 * elem + 4 * nacc)
+        kname, traffic = "modes_step", None
     avg_s = h_ms / 1e3 / max(h_n, 1)
     achieved = alg_bytes / avg_s / 1e9
     peak, peak_kind = peaks()
     total_ms = sum(v[0] for v in prof.values())
-    roofline = {"bound": "hbm", "kernel": "hist_conv", "achieved": achieved, "peak": peak, "unit": "GB/s",
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
-                "traffic": measured_traffic(args.workload), "algorithmic_bytes_per_launch": alg_bytes,
+                "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes,
                 "avg_launch_ms": avg_s * 1e3,
                 "kernel_share": {k: v[0] / total_ms for k, v in prof.items() if total_ms > 0}}
 

@@ -226,6 +226,24 @@ enum {
 };
 gld_status gld_profile_steps(gld_ctx* ctx, int64_t nsteps, double* ms, int64_t* launches);
 
+/* Memory sums in auxiliary-variable form (App. C discusses auxiliary-variable
+ * expansions as the alternative to a stored history).  When every kernel
+ * given to gld_set_kernels is, for m >= 1, a combination of the modes
+ *   z_k^m = exp((-rate_k + i omega_k) m dt)   (real and imaginary parts),
+ * the projections S, P, Ps of Eq. dissipative_force2 are carried as
+ * per-particle sums Y_k(n) = sum_{m=1}^{m_max-1} z_k^m dR_{n-m}, updated in
+ * O(1) per step as Y_k(n+1) = z_k (dR_n + Y_k(n) - z_k^{m_max-1} dR_{n-m_max+1}):
+ * the same truncated convolution without streaming the ring every step (the
+ * ring still holds the term that leaves the window).  The combination
+ * coefficients are fitted in FP64 to the discrete weights; GLD_E_INVAL when
+ * the relative residual exceeds 1e-9 (the kernels are not sums of these
+ * modes), rate_k <= 0, omega_k < 0 or nmodes > 8.  Sums are FP32 (the Kahan
+ * option does not apply).  The sums are rebuilt from the ring before the next
+ * step (and after gld_set_step or a history write).  nmodes = 0, or a new
+ * gld_set_kernels, returns to the ring convolution.  Single contexts only:
+ * such a context cannot join a batch.  Synchronizes. */
+gld_status gld_set_memory_modes(gld_ctx* ctx, int32_t nmodes, const double* rate, const double* omega);
+
 /* Distance-binned velocity auto- and cross-correlations of pairs (Sec. III A,
  * the functions C^a(R,t) and C^c(R,t) from which the paper reconstructs the
  * pair memory kernels), sampled with the VACF's origins: for every unordered

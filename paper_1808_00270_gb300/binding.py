@@ -98,6 +98,7 @@ def lib():
             "gld_pairs_noalloc": (i32, [vp, i32, d, d, vp, i64, vp, vp]),
             "gld_get_bytes": (i32, [vp, C.POINTER(i64)]),
             "gld_set_pair_correlation": (i32, [vp, i32, d]),
+            "gld_set_memory_modes": (i32, [vp, i32, vp, vp]),
             "gld_pair_correlation": (i32, [vp, vp, vp, vp]),
             "gld_bytes_needed": (i32, [C.POINTER(Params), i32, i32, i32, C.POINTER(i64)]),
             "gld_batch_set_tuning": (i32, [vp, i32]),
@@ -140,7 +141,7 @@ def exported_symbols() -> list[str]:
             "gld_server_params_default", "gld_server_create", "gld_server_submit", "gld_server_pump",
             "gld_server_drain", "gld_server_clock", "gld_server_result", "gld_server_stats",
             "gld_server_last_error", "gld_server_destroy", "gld_server_cancel", "gld_set_pair_correlation",
-            "gld_pair_correlation"]
+            "gld_pair_correlation", "gld_set_memory_modes"]
 
 
 def _ptr(a: np.ndarray):
@@ -302,6 +303,12 @@ class GLD:
         out = np.zeros(4, dtype=np.int64)
         self._check(lib().gld_get_diag(self._h, _ptr(out), 4))
         return dict(graph_mode=int(out[0]), rebuilds=int(out[1]), maxnb=int(out[2]), cells_per_edge=int(out[3]))
+
+    def set_memory_modes(self, rates, omegas):
+        """Carries the memory sums in auxiliary-variable form for kernels that
+        are sums of the modes exp((-rate + i omega) t); empty: the ring."""
+        r, o = _f64(rates).ravel(), _f64(omegas).ravel()
+        self._check(lib().gld_set_memory_modes(self._h, int(r.size), _ptr(r), _ptr(o)))
 
     def set_pair_correlation(self, nbins: int, r_max: float):
         """Enables C^a(R, t), C^c(R, t) on nbins distance bins of [0, r_max)."""

@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -184,10 +185,30 @@ cudaError_t launch_noise(gld_ctx* c, cudaStream_t s)
     return launch_noise_block(c->P, c->B.ctrl, c->W, c->Acp, c->la, c->B.frblock, c->prm.seed, c->d_int2ext, s);
 }
 
+// The memory sums of step n: the history convolution, or its recursive form
+// when memory modes are set.
+cudaError_t launch_memory(gld_ctx* c, cudaStream_t s)
+{
+    if (c->P.nmodes > 0)
+        return launch_modes_step(c->P, c->B.ctrl, c->B.ring, c->d_mcoef, c->d_mw, c->d_Y, c->B.conv, s);
+    return launch_hist_conv(c->B.ring, c->P.hist_bf16, c->P.n_pad, c->P.m_max, c->B.ctrl, 0, c->coef, c->P.nacc,
+                            c->B.conv, c->prm.kahan, s);
+}
+
+// Rebuilds the auxiliary sums of the recursive form from the ring when the
+// history or the step index was replaced.
+gld_status refresh_modes(gld_ctx* c)
+{
+    if (c->P.nmodes > 0 && c->modes_dirty) {
+        GLD_CUDA(c, launch_modes_init(c->P, c->B.ctrl, c->B.ring, c->d_mz, c->d_Y, c->st));
+        c->modes_dirty = false;
+    }
+    return GLD_OK;
+}
+
 cudaError_t launch_one_step(gld_ctx* c, cudaStream_t s)
 {
-    cudaError_t e = launch_hist_conv(c->B.ring, c->P.hist_bf16, c->P.n_pad, c->P.m_max, c->B.ctrl, 0, c->coef,
-                                     c->P.nacc, c->B.conv, c->prm.kahan, s);
+    cudaError_t e = launch_memory(c, s);
     if (e != cudaSuccess) return e;
     if ((e = launch_pair_force_integrate(c->P, c->B, s)) != cudaSuccess) return e;
     if ((e = launch_rebuild(c->P, c->B, s)) != cudaSuccess) return e;
@@ -201,8 +222,7 @@ cudaError_t launch_one_step(gld_ctx* c, cudaStream_t s)
 // steps without a rebuild launch none of them.
 cudaError_t capture_step_conditional(gld_ctx* c, cudaStream_t s)
 {
-    cudaError_t e = launch_hist_conv(c->B.ring, c->P.hist_bf16, c->P.n_pad, c->P.m_max, c->B.ctrl, 0, c->coef,
-                                     c->P.nacc, c->B.conv, c->prm.kahan, s);
+    cudaError_t e = launch_memory(c, s);
     if (e == cudaSuccess) e = launch_pair_force_integrate(c->P, c->B, s);
     cudaStreamCaptureStatus cs;
     cudaGraph_t g = nullptr;
@@ -633,6 +653,15 @@ gld_status gld_set_kernels(gld_ctx* c, const double* Ks, int32_t Q, const double
     P.vh_f = (float)(c->b * dt / c->prm.mass);
     P.vf_fc = (float)(dt / M2);
     c->B.ftab = c->ftab;
+    // FP64 discrete weights of every accumulator (m >= 1), for the recursive form
+    c->wts.assign((size_t)P.nacc * P.m_max, 0.0);
+    for (int a = 0; a < P.nacc; ++a)
+        for (int m = 1; m < P.m_max; ++m) {
+            const double sm = in[(size_t)a * P.m_max + m];  // rows: K^s, g_1..g_Q, gs_1..gs_Qs
+            c->wts[(size_t)a * P.m_max + m] = conv == GLD_KDISCRETE ? sm : dt * sm;
+        }
+    P.nmodes = 0;  // new kernels: back to the ring convolution until modes are set again
+    c->modes_dirty = false;
     c->have_kernels = true;
     GLD_TRY(invalidate_noise(c));
     return sync_and_check(c);
@@ -644,6 +673,7 @@ gld_status gld_step(gld_ctx* c, int64_t nsteps)
     if (!c->have_kernels) return fail(c, GLD_E_STATE, "gld_step: gld_set_kernels has not succeeded");
     if (c->latched != GLD_OK) return c->latched;
     const int T = c->P.T;
+    if (nsteps > 0) GLD_TRY(refresh_modes(c));
     while (nsteps > 0) {
         if (!c->noise_valid || c->host_step >= c->noise_end) {
             if (c->prm.use_graphs && nsteps >= T && capture_graph(c)) {
@@ -791,6 +821,7 @@ gld_status gld_set_array(gld_ctx* c, int32_t which, const double* in)
                 }
         }
         GLD_CUDA(c, cudaMemcpy(c->B.ring, h.data(), h.size(), cudaMemcpyHostToDevice));
+        c->modes_dirty = true;
         return GLD_OK;
     }
     default: return fail(c, GLD_E_INVAL, "gld_set_array: array is read-only or unknown");
@@ -832,6 +863,7 @@ gld_status gld_set_step(gld_ctx* c, int64_t step)
     GLD_CUDA(c, cudaMemcpyAsync(&c->B.ctrl->hslot, &s[1], sizeof(long long), cudaMemcpyHostToDevice, c->st));
     GLD_TRY(invalidate_noise(c));
     c->last_fr_row = -1;
+    c->modes_dirty = true;  // the ring's slots now stand for other times
     return sync_and_check(c);
 }
 
@@ -891,6 +923,7 @@ gld_status gld_profile_steps(gld_ctx* c, int64_t nsteps, double* ms, int64_t* la
     if (c->latched != GLD_OK) return c->latched;
     // untimed steps up to the next noise-block boundary
     if (c->noise_valid && c->host_step < c->noise_end) GLD_TRY(gld_step(c, c->noise_end - c->host_step));
+    GLD_TRY(refresh_modes(c));
     GLD_TRY(sync_and_check(c));
     const int T = c->P.T;
     const int64_t blocks = (nsteps + T - 1) / T;
@@ -927,8 +960,7 @@ gld_status gld_profile_steps(gld_ctx* c, int64_t nsteps, double* ms, int64_t* la
         c->noise_valid = true;
         for (int t = 0; t < T; ++t) {
             timed(GLD_PROF_HIST, [&] {
-                return launch_hist_conv(c->B.ring, c->P.hist_bf16, c->P.n_pad, c->P.m_max, c->B.ctrl, 0, c->coef,
-                                        c->P.nacc, c->B.conv, c->prm.kahan, c->st);
+                return launch_memory(c, c->st);
             });
             timed(GLD_PROF_PAIR, [&] { return launch_pair_force_integrate(c->P, c->B, c->st); });
             timed(GLD_PROF_CELL, [&] { return launch_rebuild(c->P, c->B, c->st); });
@@ -956,6 +988,119 @@ gld_status gld_profile_steps(gld_ctx* c, int64_t nsteps, double* ms, int64_t* la
         if (launches) launches[f] += cnt[f];
     }
     if (s != GLD_OK) return s;
+    return sync_and_check(c);
+}
+
+gld_status gld_set_memory_modes(gld_ctx* c, int32_t nmodes, const double* rate, const double* omega)
+{
+    if (!c) return GLD_E_INVAL;
+    if (!c->have_kernels) return fail(c, GLD_E_STATE, "gld_set_memory_modes: set the kernels first");
+    StepParams& P = c->P;
+    if (nmodes == 0) {  // back to the ring convolution
+        GLD_TRY(sync_and_check(c));
+        P.nmodes = 0;
+        invalidate_graph(c);
+        return GLD_OK;
+    }
+    if (nmodes < 0 || nmodes > kMaxModes || !rate || !omega)
+        return fail(c, GLD_E_INVAL, "gld_set_memory_modes: 1..8 modes with rates and frequencies");
+    for (int k = 0; k < nmodes; ++k)
+        if (!(rate[k] > 0) || !std::isfinite(rate[k]) || !std::isfinite(omega[k]) || omega[k] < 0)
+            return fail(c, GLD_E_INVAL, "gld_set_memory_modes: need rate > 0 and omega >= 0");
+    const int H = P.H, M = P.m_max, na = P.nacc;
+    const double dt = c->prm.dt;
+    // basis functions Re z_k^m (and Im z_k^m for omega_k != 0), m = 1..H
+    std::vector<std::vector<double>> cols;
+    std::vector<int> col_mode, col_im;
+    for (int k = 0; k < nmodes; ++k)
+        for (int im = 0; im < (omega[k] != 0.0 ? 2 : 1); ++im) {
+            std::vector<double> v(H);
+            for (int m = 1; m <= H; ++m) {
+                const double mag = std::exp(-rate[k] * dt * m), ph = omega[k] * dt * m;
+                v[m - 1] = mag * (im ? std::sin(ph) : std::cos(ph));
+            }
+            cols.push_back(v);
+            col_mode.push_back(k);
+            col_im.push_back(im);
+        }
+    // least squares through modified Gram-Schmidt: Phi = Q R
+    const int nb = (int)cols.size();
+    std::vector<std::vector<double>> Qm = cols;
+    std::vector<double> R((size_t)nb * nb, 0.0);
+    for (int j = 0; j < nb; ++j) {
+        const double n0 = std::sqrt(std::inner_product(cols[j].begin(), cols[j].end(), cols[j].begin(), 0.0));
+        for (int i = 0; i < j; ++i) {
+            const double r = std::inner_product(Qm[i].begin(), Qm[i].end(), Qm[j].begin(), 0.0);
+            R[(size_t)i * nb + j] = r;
+            for (int m = 0; m < H; ++m) Qm[j][m] -= r * Qm[i][m];
+        }
+        const double nj = std::sqrt(std::inner_product(Qm[j].begin(), Qm[j].end(), Qm[j].begin(), 0.0));
+        if (!(nj > 1e-10 * n0)) return fail(c, GLD_E_INVAL, "gld_set_memory_modes: modes are not independent");
+        R[(size_t)j * nb + j] = nj;
+        for (int m = 0; m < H; ++m) Qm[j][m] /= nj;
+    }
+    std::vector<float2> hw((size_t)na * nmodes, make_float2(0.f, 0.f));
+    double worst = 0.0;
+    for (int a = 0; a < na; ++a) {
+        const double* w = c->wts.data() + (size_t)a * M + 1;
+        std::vector<double> x(nb, 0.0);
+        for (int j = 0; j < nb; ++j) x[j] = std::inner_product(Qm[j].begin(), Qm[j].end(), w, 0.0);
+        for (int j = nb - 1; j >= 0; --j) {
+            for (int i = j + 1; i < nb; ++i) x[j] -= R[(size_t)j * nb + i] * x[i];
+            x[j] /= R[(size_t)j * nb + j];
+        }
+        double wmax = 0.0, res = 0.0;
+        for (int m = 0; m < H; ++m) {
+            double f = 0.0;
+            for (int j = 0; j < nb; ++j) f += x[j] * cols[j][m];
+            res = std::max(res, std::fabs(f - w[m]));
+            wmax = std::max(wmax, std::fabs(w[m]));
+        }
+        const double rel = wmax > 0 ? res / wmax : res;
+        worst = std::max(worst, rel);
+        for (int j = 0; j < nb; ++j) {
+            float2& e = hw[(size_t)a * nmodes + col_mode[j]];
+            (col_im[j] ? e.y : e.x) = (float)x[j];
+        }
+    }
+    if (worst > 1e-9) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf,
+                      "gld_set_memory_modes: the kernels are not sums of these modes (relative residual %.3g)", worst);
+        return fail(c, GLD_E_INVAL, buf);
+    }
+    std::vector<float4> hc(nmodes);
+    std::vector<double> hz(2 * (size_t)nmodes);
+    for (int k = 0; k < nmodes; ++k) {
+        const double mag = std::exp(-rate[k] * dt), ph = omega[k] * dt;
+        const double magH = std::exp(-rate[k] * dt * H), phH = omega[k] * dt * H;
+        hz[2 * k] = mag * std::cos(ph);
+        hz[2 * k + 1] = mag * std::sin(ph);
+        hc[k] = make_float4((float)hz[2 * k], (float)hz[2 * k + 1], (float)(magH * std::cos(phH)),
+                            (float)(magH * std::sin(phH)));
+    }
+    GLD_TRY(sync_and_check(c));
+    dfree(c, c->d_mcoef);
+    dfree(c, c->d_mw);
+    dfree(c, c->d_Y);
+    dfree(c, c->d_mz);
+    c->d_mcoef = nullptr;
+    c->d_mw = nullptr;
+    c->d_Y = nullptr;
+    c->d_mz = nullptr;
+    P.nmodes = 0;
+    bool ok = true;
+    c->d_mcoef = alloc_n<float4>(c, (size_t)nmodes, ok);
+    c->d_mw = alloc_n<float2>(c, hw.size(), ok);
+    c->d_Y = alloc_n<float2>(c, (size_t)nmodes * 3 * P.n_pad, ok);
+    c->d_mz = alloc_n<double>(c, hz.size(), ok);
+    if (!ok) return fail(c, GLD_E_NOMEM, "gld_set_memory_modes: allocation failed");
+    GLD_CUDA(c, cudaMemcpyAsync(c->d_mcoef, hc.data(), sizeof(float4) * hc.size(), cudaMemcpyHostToDevice, c->st));
+    GLD_CUDA(c, cudaMemcpyAsync(c->d_mw, hw.data(), sizeof(float2) * hw.size(), cudaMemcpyHostToDevice, c->st));
+    GLD_CUDA(c, cudaMemcpyAsync(c->d_mz, hz.data(), sizeof(double) * hz.size(), cudaMemcpyHostToDevice, c->st));
+    P.nmodes = nmodes;
+    c->modes_dirty = true;  // the sums are built from the ring before the next step
+    invalidate_graph(c);
     return sync_and_check(c);
 }
 
@@ -1335,8 +1480,9 @@ gld_status gld_batch_add(gld_batch* b, gld_ctx* c)
     if (!c->have_kernels) return bfail(b, GLD_E_STATE, "gld_batch_add: the member has no kernels set");
     if (c->st != b->st) return bfail(b, GLD_E_INVAL, "gld_batch_add: the member must use the batch's stream");
     if (c->P.T != kMaxNoiseBlock) return bfail(b, GLD_E_INVAL, "gld_batch_add: the member's noise block must be 64");
-    if (c->P.pc_nbins > 0)
-        return bfail(b, GLD_E_INVAL, "gld_batch_add: pair correlations are accumulated by single contexts only");
+    if (c->P.pc_nbins > 0 || c->P.nmodes > 0)
+        return bfail(b, GLD_E_INVAL,
+                     "gld_batch_add: pair correlations and memory modes are single-context features");
     if (c->noise_valid && c->host_step != c->noise_end)
         return bfail(b, GLD_E_STATE, "gld_batch_add: the member is inside a noise block (step a multiple of 64)");
     for (gld_ctx* m : b->members)

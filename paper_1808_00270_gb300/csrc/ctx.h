@@ -44,6 +44,15 @@ struct gld_ctx {
     gld_status latched = GLD_OK;
     std::vector<int> int2ext;  // caller's index of the particle stored at k
     int* d_int2ext = nullptr;
+    // recursive memory form: FP64 discrete weights w_a[m] of every
+    // accumulator (kept from gld_set_kernels for the fit), mode tables, the
+    // auxiliary sums, and whether they must be rebuilt from the ring
+    std::vector<double> wts;
+    float4* d_mcoef = nullptr;
+    float2* d_mw = nullptr;
+    float2* d_Y = nullptr;
+    double* d_mz = nullptr;
+    bool modes_dirty = false;
 };
 
 struct gld_batch {

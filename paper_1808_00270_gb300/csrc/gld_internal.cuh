@@ -15,6 +15,7 @@ namespace gld {
 
 constexpr int kMaxQ = 4;            // separable terms per pair-kernel family
 constexpr int kMaxAcc = 1 + 2 * kMaxQ;
+constexpr int kMaxModes = 8;         // damped-exponential modes of the recursive memory form
 constexpr int kPcMaxOriginBins = 2048;  // origins x bins of the pair correlations (48 KB of shared sums)
 constexpr int kVacfMaxBlocks = 256;  // particle blocks of the VACF grid at most
 constexpr int kMaxNoiseBlock = 64;  // register-resident outputs per FIR thread
@@ -69,6 +70,8 @@ struct StepParams {
     // VACF
     int vacf_len, vacf_stride, n_os;
     long long vacf_burnin;
+    // memory sums in recursive (auxiliary-variable) form: modes (0: ring convolution)
+    int nmodes;
     // distance-binned pair correlations (0 bins: off)
     int pc_nbins;
     float pc_rmax2, pc_inv_dr;  // r_max^2, nbins / r_max

@@ -695,8 +695,10 @@ __global__ void __launch_bounds__(kThreads) pcorr(const StepParams P, Ctrl* __re
     const int slot0 = ctrl->vacf_slot0;
     const int nb = P.pc_nbins;
     if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->pc_pending = 1;
-    extern __shared__ long long hs[];  // [n_act][nbins][3]
+    extern __shared__ long long hs[];  // [n_act][nbins][3] (a, c, unused) then [nbins] pair counts
+    long long* hn = hs + 3 * P.n_os * nb;
     for (int k = threadIdx.x; k < n_act * nb * 3; k += blockDim.x) hs[k] = 0;
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) hn[k] = 0;
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < P.n) {
@@ -718,6 +720,7 @@ __global__ void __launch_bounds__(kThreads) pcorr(const StepParams P, Ctrl* __re
             const float4 vj = __ldg(vel + j);
             const float vit = vi.x * ex + vi.y * ey + vi.z * ez;
             const float vjt = vj.x * ex + vj.y * ey + vj.z * ez;
+            atomicAdd((unsigned long long*)(hn + bin), 1ull);  // the same pairs for every origin
             for (int q = 0; q < n_act; ++q) {
                 float vi0 = vit, vj0 = vjt;
                 if (!(q == 0 && is_origin)) {
@@ -730,14 +733,15 @@ __global__ void __launch_bounds__(kThreads) pcorr(const StepParams P, Ctrl* __re
                 long long* h = hs + 3 * (q * nb + bin);
                 atomicAdd((unsigned long long*)h, (unsigned long long)pc_fixed(vit * vi0 + vjt * vj0));
                 atomicAdd((unsigned long long*)(h + 1), (unsigned long long)pc_fixed(vit * vj0 + vjt * vi0));
-                atomicAdd((unsigned long long*)(h + 2), 1ull);
             }
         }
     }
     __syncthreads();
     long long* out = step_sums + (size_t)ctrl->pc_buf * P.n_os * nb * 3;
-    for (int k = threadIdx.x; k < n_act * nb * 3; k += blockDim.x)
-        if (hs[k] != 0) atomicAdd((unsigned long long*)(out + k), (unsigned long long)hs[k]);
+    for (int k = threadIdx.x; k < n_act * nb * 3; k += blockDim.x) {
+        const long long v = (k % 3 == 2) ? hn[(k / 3) % nb] : hs[k];
+        if (v != 0) atomicAdd((unsigned long long*)(out + k), (unsigned long long)v);
+    }
 }
 
 // Folds the last launch's sums (before they are read).
@@ -973,7 +977,11 @@ cudaError_t launch_pcorr(const StepParams& P, const ParticleBuffers& B, cudaStre
 {
     if (P.pc_nbins <= 0 || P.vacf_len <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)std::max(1, (P.n + kThreads - 1) / kThreads);
-    const size_t smem = sizeof(long long) * 3 * (size_t)P.n_os * P.pc_nbins;
+    const size_t smem = sizeof(long long) * (3 * (size_t)P.n_os * P.pc_nbins + P.pc_nbins);
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(pcorr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
     pcorr<<<grid, kThreads, smem, st>>>(P, B.ctrl, B.pos, B.vel, B.vorig, B.nbr, B.nbr_cnt, B.pc_step, B.pc_sa,
                                         B.pc_sc, B.pc_n);
     return cudaGetLastError();

@@ -110,6 +110,13 @@ constexpr int kBatchCforceBlock = 128; // threads per F^C tile of a batch
 constexpr int kBatchPairBlock = 128, kBatchPartBlock = 256, kBatchCellChunk = 512, kBatchConvCols = 256,
               kBatchFirStreams = 32, kBatchVacfBlock = 256;
 
+// Memory sums in auxiliary-variable form (k_modes.cu): coef[k] = {Re z, Im z,
+// Re z^H, Im z^H}, w[a * nmodes + k] = {x_ak, y_ak}, Y[nmodes][3 n_pad].
+cudaError_t launch_modes_step(const StepParams& P, const Ctrl* ctrl, const void* ring, const float4* coef,
+                              const float2* w, float2* Y, float* conv, cudaStream_t st);
+cudaError_t launch_modes_init(const StepParams& P, const Ctrl* ctrl, const void* ring, const double* zd, float2* Y,
+                              cudaStream_t st);
+
 // Noise and kernel preparation (k_noise.cu).
 struct PrepArgs {
     int m_max, Q, Qs, discrete, clamp, T;

@@ -92,6 +92,19 @@ def self_kernel_samples(w: Workload) -> np.ndarray:
     return ks
 
 
+def memory_modes(w: Workload):
+    """The damped modes exp((-rate + i omega) t) the workload's kernels are
+    made of: K^s (rate 1/tau_s, omega 3), its slow tail (rate 1/2), the pair
+    kernel's time factor (rate 1/tau_p).  Returns (rates, omegas)."""
+    rates, omegas = [1.0 / w.tau_s], [3.0]
+    if w.tail:
+        rates.append(0.5)
+        omegas.append(0.0)
+    rates.append(1.0 / w.tau_p)
+    omegas.append(0.0)
+    return np.array(rates), np.array(omegas)
+
+
 def pair_kernel_tables(w: Workload):
     """Separable pair kernel: g[1, m_max] = exp(-m dt/tau_p), f[1, nr] = 2 (1 - r/r_c)^2."""
     t = np.arange(w.m_max) * w.dt
