@@ -721,7 +721,11 @@ __global__ void __launch_bounds__(kThreads) pcorr(const StepParams P, Ctrl* __re
             const float vit = vi.x * ex + vi.y * ey + vi.z * ez;
             const float vjt = vj.x * ex + vj.y * ey + vj.z * ez;
             atomicAdd((unsigned long long*)(hn + bin), 1ull);  // the same pairs for every origin
-            for (int q = 0; q < n_act; ++q) {
+            // lanes start at different origins, so that the shared-memory
+            // atomics of one instruction seldom meet on the same (origin, bin)
+            const int q0 = (threadIdx.x & 31) % n_act;
+            for (int qq = 0; qq < n_act; ++qq) {
+                const int q = qq + q0 < n_act ? qq + q0 : qq + q0 - n_act;
                 float vi0 = vit, vj0 = vjt;
                 if (!(q == 0 && is_origin)) {
                     int sl = slot0 - q;
