@@ -167,7 +167,9 @@ enum {
     GLD_ARR_FR = 4,   /* F^R of the last completed step (r)                       */
     GLD_ARR_DISP = 5, /* unwrapped displacement since creation, sum of dR (rw)    */
     GLD_ARR_HIST = 6, /* [m_max-1][n][3]: entry m-1 holds dR_{n-m} (rw)           */
-    GLD_ARR_CONV = 7  /* [1+Q+Qs][n][3]: history projections of the last step (r) */
+    GLD_ARR_CONV = 7  /* [1+Q+Qs][n][3]: history projections as last computed (r):
+                       * of the last step, or of the next one after a
+                       * replayed graph block, which computes them early */
 };
 gld_status gld_get_array(gld_ctx* ctx, int32_t which, double* out);
 gld_status gld_set_array(gld_ctx* ctx, int32_t which, const double* in);

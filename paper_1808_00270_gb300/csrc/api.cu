@@ -160,11 +160,13 @@ void invalidate_graph(gld_ctx* c)
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     c->gexec = nullptr;
     c->graph_failed = false;
+    c->conv_valid_step = -1;
 }
 
 gld_status invalidate_noise(gld_ctx* c)
 {
     c->noise_valid = false;
+    c->conv_valid_step = -1;
     long long w[2] = {0, 1};  // {w_hi, w_lo}: w_hi < w_lo marks the W ring empty
     GLD_CUDA(c, cudaMemcpyAsync(&c->B.ctrl->w_hi, w, sizeof(w), cudaMemcpyHostToDevice, c->st));
     return GLD_OK;
@@ -220,10 +222,40 @@ cudaError_t launch_one_step(gld_ctx* c, cudaStream_t s)
 // One step captured with the rebuild kernels in the body of a conditional
 // (IF) node whose condition a one-thread kernel sets from ctrl->rebuild, so
 // steps without a rebuild launch none of them.
-cudaError_t capture_step_conditional(gld_ctx* c, cudaStream_t s)
+// With `overlap`, the step's own convolution is not captured (the previous
+// step computed it) and the next step's convolution is forked onto a second
+// capture stream right after the pair kernel: it reads only the ring the pair
+// kernel has just written, so it runs beside the rebuild, F^C, VACF and pair
+// correlation kernels and is joined before the next pair kernel.
+cudaError_t capture_fork_next(gld_ctx* c, cudaStream_t s)
 {
-    cudaError_t e = launch_memory(c, s);
+    cudaError_t e = cudaEventRecord(c->ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->cap3, c->ev_fork, 0);
+    if (e == cudaSuccess)
+        e = launch_hist_conv_next(c->B.ring, c->P.hist_bf16, c->P.n_pad, c->P.m_max, c->B.ctrl, c->coef, c->P.nacc,
+                                  c->B.conv, c->prm.kahan, c->cap3);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->cap3);
+    return e;
+}
+
+cudaError_t capture_step_gated(gld_ctx* c, cudaStream_t s, bool overlap)
+{
+    if (!overlap) return launch_one_step(c, s);
+    cudaError_t e = launch_pair_force_integrate(c->P, c->B, s);
+    if (e == cudaSuccess) e = capture_fork_next(c, s);
+    if (e == cudaSuccess) e = launch_rebuild(c->P, c->B, s);
+    if (e == cudaSuccess) e = launch_cforce(c->P, c->B, 1, s);
+    if (e == cudaSuccess) e = launch_vacf(c->P, c->B, s);
+    if (e == cudaSuccess) e = launch_pcorr(c->P, c->B, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join, 0);
+    return e;
+}
+
+cudaError_t capture_step_conditional(gld_ctx* c, cudaStream_t s, bool overlap)
+{
+    cudaError_t e = overlap ? cudaSuccess : launch_memory(c, s);
     if (e == cudaSuccess) e = launch_pair_force_integrate(c->P, c->B, s);
+    if (overlap && e == cudaSuccess) e = capture_fork_next(c, s);
     cudaStreamCaptureStatus cs;
     cudaGraph_t g = nullptr;
     const cudaGraphNode_t* deps = nullptr;
@@ -255,17 +287,28 @@ cudaError_t capture_step_conditional(gld_ctx* c, cudaStream_t s)
     if (e == cudaSuccess) e = launch_cforce(c->P, c->B, 1, s);
     if (e == cudaSuccess) e = launch_vacf(c->P, c->B, s);
     if (e == cudaSuccess) e = launch_pcorr(c->P, c->B, s);
+    if (overlap && e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join, 0);
     return e;
 }
 
 bool capture_graph_mode(gld_ctx* c, bool conditional)
 {
+    // the overlapped form needs an idempotent convolution (not the recursive
+    // memory form, whose kernel advances its auxiliary sums)
+    bool overlap = c->P.nmodes == 0;
+    if (overlap && !c->cap3 &&
+        (cudaStreamCreateWithFlags(&c->cap3, cudaStreamNonBlocking) != cudaSuccess ||
+         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)) {
+        cudaGetLastError();
+        overlap = false;
+    }
     cudaGraph_t g = nullptr;
     bool ok = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
         cudaError_t e = launch_noise(c, c->cap);
         for (int t = 0; t < c->P.T && e == cudaSuccess; ++t)
-            e = conditional ? capture_step_conditional(c, c->cap) : launch_one_step(c, c->cap);
+            e = conditional ? capture_step_conditional(c, c->cap, overlap) : capture_step_gated(c, c->cap, overlap);
         const cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
         ok = e == cudaSuccess && e2 == cudaSuccess && g != nullptr;
     }
@@ -275,6 +318,7 @@ bool capture_graph_mode(gld_ctx* c, bool conditional)
         c->gexec = nullptr;
         cudaGetLastError();
     }
+    c->overlap_graph = ok && overlap;
     return ok;
 }
 
@@ -677,9 +721,12 @@ gld_status gld_step(gld_ctx* c, int64_t nsteps)
     while (nsteps > 0) {
         if (!c->noise_valid || c->host_step >= c->noise_end) {
             if (c->prm.use_graphs && nsteps >= T && capture_graph(c)) {
+                // the overlapped graph starts from the projections of its first step
+                if (c->overlap_graph && c->conv_valid_step != c->host_step) GLD_CUDA(c, launch_memory(c, c->st));
                 GLD_CUDA(c, cudaGraphLaunch(c->gexec, c->st));
                 c->block_start = c->host_step;
                 c->host_step += T;
+                c->conv_valid_step = c->overlap_graph ? c->host_step : -1;
                 c->noise_end = c->host_step;
                 c->noise_valid = true;
                 c->last_fr_row = T - 1;
@@ -692,6 +739,7 @@ gld_status gld_step(gld_ctx* c, int64_t nsteps)
             c->noise_valid = true;
         }
         GLD_CUDA(c, launch_one_step(c, c->st));
+        c->conv_valid_step = -1;
         c->last_fr_row = c->host_step - c->block_start;
         ++c->host_step;
         --nsteps;
@@ -780,6 +828,7 @@ gld_status gld_get_array(gld_ctx* c, int32_t which, double* out)
 
 gld_status gld_set_array(gld_ctx* c, int32_t which, const double* in)
 {
+    if (c) c->conv_valid_step = -1;
     if (!c || !in) return GLD_E_INVAL;
     GLD_TRY(sync_and_check(c));
     const StepParams& P = c->P;
@@ -925,6 +974,7 @@ gld_status gld_profile_steps(gld_ctx* c, int64_t nsteps, double* ms, int64_t* la
     if (c->noise_valid && c->host_step < c->noise_end) GLD_TRY(gld_step(c, c->noise_end - c->host_step));
     GLD_TRY(refresh_modes(c));
     GLD_TRY(sync_and_check(c));
+    c->conv_valid_step = -1;  // the eager steps below leave no next-step projections
     const int T = c->P.T;
     const int64_t blocks = (nsteps + T - 1) / T;
     // Per noise block: a short delay kernel lets the host enqueue the whole
@@ -1173,6 +1223,9 @@ gld_status gld_destroy(gld_ctx* c)
     }
     if (c->cap) cudaStreamDestroy(c->cap);
     if (c->cap2) cudaStreamDestroy(c->cap2);
+    if (c->cap3) cudaStreamDestroy(c->cap3);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     delete c;
     return GLD_OK;
 }
@@ -1529,6 +1582,7 @@ gld_status gld_batch_step(gld_batch* b, int64_t nsteps)
         const cudaError_t e = b->gexec ? cudaGraphLaunch(b->gexec, b->st) : batch_launch_block(b, b->st);
         if (e != cudaSuccess) return bfail(b, GLD_E_CUDA, std::string("gld_batch_step: ") + cudaGetErrorString(e));
         for (gld_ctx* c : b->members) {
+            c->conv_valid_step = -1;
             c->block_start = c->host_step;
             c->host_step += kMaxNoiseBlock;
             c->noise_end = c->host_step;

@@ -20,6 +20,10 @@ struct gld_ctx {
     cudaStream_t st = nullptr;   // the caller's stream
     cudaStream_t cap = nullptr;  // private stream used only to capture graphs
     cudaStream_t cap2 = nullptr; // fills the bodies of conditional graph nodes
+    cudaStream_t cap3 = nullptr; // the overlapped next-step convolution of the graph
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool overlap_graph = false;  // the graph computes each step's successor convolution
+    long long conv_valid_step = -1;  // the step whose projections `conv` already holds
     std::vector<void*> allocs;
     std::vector<size_t> alloc_sizes;
     size_t bytes = 0;  // device bytes held

@@ -38,6 +38,7 @@ struct Ctrl {
     int pad_;
     long long rebuilds;    // neighbour-list builds so far
     long long hslot;       // step mod H: the history slot this step writes
+    long long conv_step;   // n + 1, written by the pair kernel of step n
     // VACF schedule at the step the next VACF kernel sees (written by the
     // pair kernel): active, origins in flight, slot of the newest origin, a
     // new origin at this step, lag of the newest origin, partial buffer

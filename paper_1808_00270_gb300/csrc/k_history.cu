@@ -95,13 +95,13 @@ __device__ __forceinline__ void unpack(const typename Col<BF16>::V v, float (&x)
 template <int NACC, bool KAHAN, bool BF16>
 __global__ void __launch_bounds__(kThreads, (NACC * Col<BF16>::W * (KAHAN ? 2 : 1) <= 8) ? 6 : 1)
     hist_conv_col(const typename Col<BF16>::V* __restrict__ ring, long long cols, int H,
-                  const float* __restrict__ coef, int M, const Ctrl* __restrict__ ctrl, long long step,
+                  const float* __restrict__ coef, int M, const long long* __restrict__ nstep, long long step,
                   float* __restrict__ out)
 {
     using V = typename Col<BF16>::V;
     constexpr int VW = Col<BF16>::W;
     extern __shared__ float cs[];
-    const long long n = ctrl ? ctrl->step : step;
+    const long long n = nstep ? *nstep : step;
     stage_coefs<NACC>(cs, coef, M, H, n);
     const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= cols) return;
@@ -164,13 +164,13 @@ __global__ void __launch_bounds__(kThreads, (NACC * Col<BF16>::W * (KAHAN ? 2 : 
 template <int NACC, bool KAHAN, bool BF16>
 __global__ void __launch_bounds__(kThreads)
     hist_conv(const typename Col<BF16>::V* __restrict__ ring, long long cols, int H, const float* __restrict__ coef,
-              int M, const Ctrl* __restrict__ ctrl, long long step, float* __restrict__ out, int G)
+              int M, const long long* __restrict__ nstep, long long step, float* __restrict__ out, int G)
 {
     using V = typename Col<BF16>::V;
     constexpr int VW = Col<BF16>::W;
     extern __shared__ float cs[];
     __shared__ float4 red[kThreads * (BF16 ? 2 : 1)];
-    const long long n = ctrl ? ctrl->step : step;
+    const long long n = nstep ? *nstep : step;
     stage_coefs<NACC>(cs, coef, M, H, n);
     const int per = blockDim.x / G;  // columns per block
     const int g = threadIdx.x / per, c = threadIdx.x - g * per;
@@ -297,7 +297,7 @@ template <int NACC, bool KAHAN, bool BF16>
 cudaError_t choose_shape(long long cols, int H, size_t smem, Shape* out);
 
 template <int NACC, bool KAHAN, bool BF16>
-cudaError_t launch_tb(const void* ring, int n_pad, int M, const Ctrl* ctrl, long long step, const float* coef,
+cudaError_t launch_tb(const void* ring, int n_pad, int M, const long long* nstep, long long step, const float* coef,
                       float* out, cudaStream_t st)
 {
     using V = typename Col<BF16>::V;
@@ -321,10 +321,10 @@ cudaError_t launch_tb(const void* ring, int n_pad, int M, const Ctrl* ctrl, long
         }
     }
     if (sh.kind == 0)
-        hist_conv_col<NACC, KAHAN, BF16><<<sh.grid, sh.block, smem, st>>>((const V*)ring, cols, H, coef, M, ctrl, step,
+        hist_conv_col<NACC, KAHAN, BF16><<<sh.grid, sh.block, smem, st>>>((const V*)ring, cols, H, coef, M, nstep, step,
                                                                           out);
     else
-        hist_conv<NACC, KAHAN, BF16><<<sh.grid, sh.block, smem, st>>>((const V*)ring, cols, H, coef, M, ctrl, step,
+        hist_conv<NACC, KAHAN, BF16><<<sh.grid, sh.block, smem, st>>>((const V*)ring, cols, H, coef, M, nstep, step,
                                                                       out, sh.G);
     return cudaGetLastError();
 }
@@ -373,27 +373,27 @@ cudaError_t choose_shape(long long cols, int H, size_t smem, Shape* out)
 }
 
 template <int NACC, bool KAHAN>
-cudaError_t launch_t(const void* ring, int bf16, int n_pad, int M, const Ctrl* ctrl, long long step,
+cudaError_t launch_t(const void* ring, int bf16, int n_pad, int M, const long long* nstep, long long step,
                      const float* coef, float* out, cudaStream_t st)
 {
-    return bf16 ? launch_tb<NACC, KAHAN, true>(ring, n_pad, M, ctrl, step, coef, out, st)
-                : launch_tb<NACC, KAHAN, false>(ring, n_pad, M, ctrl, step, coef, out, st);
+    return bf16 ? launch_tb<NACC, KAHAN, true>(ring, n_pad, M, nstep, step, coef, out, st)
+                : launch_tb<NACC, KAHAN, false>(ring, n_pad, M, nstep, step, coef, out, st);
 }
 
 template <bool KAHAN>
-cudaError_t dispatch(int nacc, const void* ring, int bf16, int n_pad, int M, const Ctrl* ctrl,
+cudaError_t dispatch(int nacc, const void* ring, int bf16, int n_pad, int M, const long long* nstep,
                      long long step, const float* coef, float* out, cudaStream_t st)
 {
     switch (nacc) {
-    case 1: return launch_t<1, KAHAN>(ring, bf16, n_pad, M, ctrl, step, coef, out, st);
-    case 2: return launch_t<2, KAHAN>(ring, bf16, n_pad, M, ctrl, step, coef, out, st);
-    case 3: return launch_t<3, KAHAN>(ring, bf16, n_pad, M, ctrl, step, coef, out, st);
-    case 4: return launch_t<4, KAHAN>(ring, bf16, n_pad, M, ctrl, step, coef, out, st);
-    case 5: return launch_t<5, KAHAN>(ring, bf16, n_pad, M, ctrl, step, coef, out, st);
-    case 6: return launch_t<6, KAHAN>(ring, bf16, n_pad, M, ctrl, step, coef, out, st);
-    case 7: return launch_t<7, KAHAN>(ring, bf16, n_pad, M, ctrl, step, coef, out, st);
-    case 8: return launch_t<8, KAHAN>(ring, bf16, n_pad, M, ctrl, step, coef, out, st);
-    case 9: return launch_t<9, KAHAN>(ring, bf16, n_pad, M, ctrl, step, coef, out, st);
+    case 1: return launch_t<1, KAHAN>(ring, bf16, n_pad, M, nstep, step, coef, out, st);
+    case 2: return launch_t<2, KAHAN>(ring, bf16, n_pad, M, nstep, step, coef, out, st);
+    case 3: return launch_t<3, KAHAN>(ring, bf16, n_pad, M, nstep, step, coef, out, st);
+    case 4: return launch_t<4, KAHAN>(ring, bf16, n_pad, M, nstep, step, coef, out, st);
+    case 5: return launch_t<5, KAHAN>(ring, bf16, n_pad, M, nstep, step, coef, out, st);
+    case 6: return launch_t<6, KAHAN>(ring, bf16, n_pad, M, nstep, step, coef, out, st);
+    case 7: return launch_t<7, KAHAN>(ring, bf16, n_pad, M, nstep, step, coef, out, st);
+    case 8: return launch_t<8, KAHAN>(ring, bf16, n_pad, M, nstep, step, coef, out, st);
+    case 9: return launch_t<9, KAHAN>(ring, bf16, n_pad, M, nstep, step, coef, out, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -502,8 +502,17 @@ cudaError_t launch_hist_conv(const void* ring, int bf16, int n_pad, int m_max, c
                              cudaStream_t st)
 {
     if (m_max < 2 || n_pad <= 0 || n_pad % 32 != 0 || nacc < 1 || nacc > kMaxAcc) return cudaErrorInvalidValue;
-    return kahan ? dispatch<true>(nacc, ring, bf16, n_pad, m_max, ctrl, step, coef, out, st)
-                 : dispatch<false>(nacc, ring, bf16, n_pad, m_max, ctrl, step, coef, out, st);
+    const long long* nstep = ctrl ? &ctrl->step : nullptr;
+    return kahan ? dispatch<true>(nacc, ring, bf16, n_pad, m_max, nstep, step, coef, out, st)
+                 : dispatch<false>(nacc, ring, bf16, n_pad, m_max, nstep, step, coef, out, st);
+}
+
+cudaError_t launch_hist_conv_next(const void* ring, int bf16, int n_pad, int m_max, const Ctrl* ctrl,
+                                  const float* coef, int nacc, float* out, int kahan, cudaStream_t st)
+{
+    if (m_max < 2 || n_pad <= 0 || n_pad % 32 != 0 || nacc < 1 || nacc > kMaxAcc || !ctrl) return cudaErrorInvalidValue;
+    return kahan ? dispatch<true>(nacc, ring, bf16, n_pad, m_max, &ctrl->conv_step, 0, coef, out, st)
+                 : dispatch<false>(nacc, ring, bf16, n_pad, m_max, &ctrl->conv_step, 0, coef, out, st);
 }
 
 }  // namespace gld

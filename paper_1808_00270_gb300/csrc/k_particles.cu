@@ -97,7 +97,10 @@ __device__ __forceinline__ void pair_force_integrate_body(const StepParams& P, C
     const long long n = ctrl->step;
     const long long np = P.n_pad;
     const int id = k;  // particles in storage (Morton) order; lists are by id
-    if (blk == 0 && threadIdx.x == 0 && P.vacf_len > 0) vacf_schedule(P, ctrl, n + 1);
+    if (blk == 0 && threadIdx.x == 0) {
+        ctrl->conv_step = n + 1;  // for a convolution of the next step that overlaps this one's tail
+        if (P.vacf_len > 0) vacf_schedule(P, ctrl, n + 1);
+    }
     const float4 pi = pos[id];
     const float4 vi = vel[id];
 

@@ -15,6 +15,12 @@ cudaError_t launch_hist_conv(const void* ring, int bf16, int n_pad, int m_max, c
                              long long step, const float* coef, int nacc, float* out, int kahan,
                              cudaStream_t st);
 
+// The convolution of the step after the current one (its index read from
+// ctrl->conv_step, written by the pair kernel), so that it can run beside the
+// current step's F^C and VACF kernels.
+cudaError_t launch_hist_conv_next(const void* ring, int bf16, int n_pad, int m_max, const Ctrl* ctrl,
+                                  const float* coef, int nacc, float* out, int kahan, cudaStream_t st);
+
 // Particle kernels (k_particles.cu).
 struct ParticleBuffers {
     Ctrl* ctrl;
