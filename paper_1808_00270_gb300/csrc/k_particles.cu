@@ -603,20 +603,40 @@ __device__ __forceinline__ void vacf_body(const StepParams& P, Ctrl* __restrict_
 #pragma unroll
     for (int q = 0; q < kVacfGroup; ++q) acc[q] = 0.f;
     if (q0 < n_act || (grp == 0 && is_origin)) {
-        for (int i = blk * blockDim.x + threadIdx.x; i < P.n; i += nblk * blockDim.x) {
+        // two particles per round, all their loads issued before the sums (the
+        // particles are still summed in the order i, i + stride, ...)
+        const int stride = nblk * blockDim.x;
+        int sl[kVacfGroup];
+        bool use[kVacfGroup];
+#pragma unroll
+        for (int q = 0; q < kVacfGroup; ++q) {
+            const int j = q0 + q;
+            sl[q] = slot0 - j < 0 ? slot0 - j + P.n_os : slot0 - j;
+            use[q] = j < n_act && !(j == 0 && is_origin);
+        }
+        for (int i = blk * blockDim.x + threadIdx.x; i < P.n; i += 2 * stride) {
+            const int i2 = i + stride;
+            const bool two = i2 < P.n;
             const float4 v = vel[i];
-            float4 w[kVacfGroup];
+            const float4 v2 = two ? vel[i2] : v;
+            float4 w[kVacfGroup], w2[kVacfGroup];
 #pragma unroll
             for (int q = 0; q < kVacfGroup; ++q) {
-                const int j = q0 + q;
-                int sl = slot0 - j;
-                sl = sl < 0 ? sl + P.n_os : sl;
-                w[q] = (j < n_act && !(j == 0 && is_origin)) ? __ldcs(vorig + (size_t)sl * P.n + i) : v;
+                w[q] = use[q] ? __ldcs(vorig + (size_t)sl[q] * P.n + i) : v;
+                w2[q] = use[q] && two ? __ldcs(vorig + (size_t)sl[q] * P.n + i2) : v2;
             }
 #pragma unroll
             for (int q = 0; q < kVacfGroup; ++q)
                 if (q0 + q < n_act) acc[q] = fmaf(v.x, w[q].x, fmaf(v.y, w[q].y, fmaf(v.z, w[q].z, acc[q])));
-            if (grp == 0 && is_origin) vorig[(size_t)slot0 * P.n + i] = v;
+            if (two)
+#pragma unroll
+                for (int q = 0; q < kVacfGroup; ++q)
+                    if (q0 + q < n_act)
+                        acc[q] = fmaf(v2.x, w2[q].x, fmaf(v2.y, w2[q].y, fmaf(v2.z, w2[q].z, acc[q])));
+            if (grp == 0 && is_origin) {
+                vorig[(size_t)slot0 * P.n + i] = v;
+                if (two) vorig[(size_t)slot0 * P.n + i2] = v2;
+            }
         }
     }
     __shared__ float wsum[kThreads / 32][kVacfGroup];
