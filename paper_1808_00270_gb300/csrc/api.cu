@@ -441,7 +441,7 @@ size_t ctx_bytes_needed(const gld_params* p, int Q, int Qs, int nr, int num_sms)
         4 * (size_t)P.T * n3, 4 * (size_t)P.lw * n3, 4 * ((size_t)ncells + 1), 4 * (size_t)ncells,
         4 * (size_t)ncells, 4 * np, 4 * (size_t)chunks, 4 * (size_t)chunks,
         16 * (size_t)std::max(P.n_os, 1) * P.n, 8 * (size_t)std::max(P.n_os, 1) * vacf_gx,
-        8 * (size_t)std::max(P.vacf_len, 1), 8 * (size_t)std::max(P.vacf_len, 1), 8, 4,
+        8 * (size_t)std::max(P.vacf_len, 1), 8 * (size_t)std::max(P.vacf_len, 1), 8,
         4 * (size_t)fir_taps_len(P.H), 4 * (size_t)kMaxAcc * P.m_max, 4 * 2 * (size_t)kMaxQ,
         8 * (size_t)P.m_max, 8 * (size_t)P.m_max, 8 * (size_t)P.m_max, 8 * 2 * (size_t)P.m_max, 8 * 4, 4,
         8 * (size_t)(1 + 2 * kMaxQ) * P.m_max, 4 * np, 4 * (size_t)std::max(nt, 1) * nrr};
@@ -573,7 +573,6 @@ gld_status gld_create(const gld_params* p, const double* pos, const double* vel,
     B.csum = alloc_n<double>(c, std::max(P.vacf_len, 1), ok);
     B.ccnt = alloc_n<long long>(c, std::max(P.vacf_len, 1), ok);
     B.norig = alloc_n<long long>(c, 1, ok);
-    B.vdone = alloc_n<unsigned>(c, 1, ok);
     c->la = fir_taps_len(P.H);
     c->Acp = alloc_n<float>(c, (size_t)c->la, ok);
     c->coef = alloc_n<float>(c, (size_t)kMaxAcc * P.m_max, ok);

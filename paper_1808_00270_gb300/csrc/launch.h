@@ -41,7 +41,6 @@ struct ParticleBuffers {
     double* csum;
     long long* ccnt;
     long long* norig;
-    unsigned* vdone;
     int vacf_gx;
     // pair correlations: per-step fixed-point sums [2][n_os][nbins][3] (a, c,
     // count) and the FP64 sums [vacf_len][nbins] with their counts
