@@ -28,9 +28,12 @@
  *               the length-(2 m_max - 1) Fourier transform (Eq. FT), the
  *               self-kernel-only case named at the end of that section.
  *   App. A      derivation of the integrator; position update uses b.
- *   Sec. III A  velocity autocorrelation (the self part of C^a).
+ *   Sec. III A  velocity autocorrelation (the self part of C^a) and the
+ *               distance-binned auto and cross correlations C^a(R,t), C^c(R,t)
+ *               (velocity components along e_ij at the later time t, pairs
+ *               binned by their distance at t).
  *
- * Readings of the paper that this file takes (each is listed in the design doc):
+ * Readings of the paper that this file takes:
  *   - position update uses b V_n (App. A) and not a V_n (Sec. II B);
  *   - kernels given as continuous samples K(m dt) become K_m = dt K(m dt),
  *     K_0 = dt K(0) / 2 (trapezoid weights of the delta comb, consistent with
