@@ -90,6 +90,10 @@ def lib(variant: int = 0):
             L.or_get_coefs.argtypes = [vp, vp, vp, vp, vp, vp, vp]
             L.or_get_vacf.argtypes = [vp, vp]
             L.or_get_vacf.restype = i64
+            L.or_set_fc_table.argtypes = [vp, vp, i32, C.c_double]
+            L.or_set_fc_table.restype = i32
+            L.or_set_pair_table.argtypes = [vp, vp, i32, C.c_double, i32]
+            L.or_set_pair_table.restype = i32
             L.or_set_paircorr.argtypes = [vp, i32, C.c_double]
             L.or_set_paircorr.restype = i32
             L.or_get_paircorr.argtypes = [vp, vp, vp, vp]
@@ -250,6 +254,21 @@ class System:
         mass = C.c_double()
         self._L.or_get_coefs(self._h, _p(Kd), _p(A), _p(Cm), _p(Ch), _p(ab), C.byref(mass))
         return dict(Kd=Kd, A=A, C=Cm, Chat=Ch, a=ab[0], b=ab[1], clamped_mass=mass.value)
+
+    def set_fc_table(self, f, dr: float) -> int:
+        """Conservative force magnitude -dU/dr tabulated on r = k dr (None: the
+        soft repulsion); F^C is recomputed."""
+        if f is None:
+            return self._L.or_set_fc_table(self._h, None, 0, 1.0)
+        f = _f64(f)
+        return self._L.or_set_fc_table(self._h, _p(f), int(f.size), float(dr))
+
+    def set_pair_table(self, Kp, dr: float, discrete: bool = False) -> int:
+        """A general pair kernel Kp[k, m] = K^p(k dr, m dt) (None: off)."""
+        if Kp is None:
+            return self._L.or_set_pair_table(self._h, None, 0, 1.0, 0)
+        Kp = _f64(Kp).reshape(-1, self.m_max)
+        return self._L.or_set_pair_table(self._h, _p(Kp), int(Kp.shape[0]), float(dr), int(bool(discrete)))
 
     def set_paircorr(self, nbins: int, rmax: float) -> int:
         """Enables C^a(R, t), C^c(R, t) (Sec. III A) on nbins distance bins of

@@ -59,7 +59,8 @@
  *   3 sign of the pair history term flipped
  *   4 inverse transform scaled by 1/m_max   5 history read one step late
  *   6 a_0 = 1 in the noise target           7 V_i in place of V_j at m = 0
- *   8 sign of F^C flipped                  9 auto and cross pair terms swapped */
+ *   8 sign of F^C flipped                  9 auto and cross pair terms swapped
+ *  10 pair-kernel table read at the lower row, not interpolated */
 #ifndef OR_PLANT
 #define OR_PLANT 0
 #endif
@@ -373,6 +374,16 @@ typedef struct {
     double pc_rmax;
     double *pc_a, *pc_c;
     int64_t* pc_n;
+    /* tabulated conservative force magnitude f(r) on r = k fc_dr (0 rows: the
+     * soft repulsion) */
+    double* fct;
+    int fc_nr;
+    double fc_dr;
+    /* a general pair-kernel table: discrete weights kpt[k][m] of K^p_m(r_k),
+     * r_k = k kp_dr, linear in r between rows (0 rows: the separable terms) */
+    double* kpt;
+    int kp_nr;
+    double kp_dr;
     or_nblist nl;
 } or_sys;
 
@@ -417,7 +428,8 @@ void or_destroy(or_sys* s)
 {
     if (!s) return;
     double* arrs[] = { s->Kd, s->gd, s->f, s->gsd, s->fs, s->C, s->Chat, s->A, s->pos, s->vel,
-                       s->fc, s->fd, s->fr, s->disp, s->hist, s->W, s->vorig, s->csum, s->pc_a, s->pc_c };
+                       s->fc, s->fd, s->fr, s->disp, s->hist, s->W, s->vorig, s->csum, s->pc_a, s->pc_c,
+                       s->fct, s->kpt };
     for (size_t k = 0; k < sizeof(arrs) / sizeof(arrs[0]); ++k) free(arrs[k]);
     free(s->wtime); free(s->ccnt); free(s->nl.start); free(s->nl.list); free(s->pc_n);
     free(s);
@@ -463,6 +475,42 @@ int or_set_kernels(or_sys* s, const double* Ks, int Q, const double* g, const do
     return st;
 }
 
+/* -dU/dr on r = k dr, k < nr (nr = 0: back to the soft repulsion); F^C is
+ * recomputed at the current positions. */
+int or_set_fc_table(or_sys* s, const double* f, int nr, double dr)
+{
+    if (nr < 0 || (nr > 0 && (nr < 2 || !(dr > 0) || !f))) return -1;
+    free(s->fct);
+    s->fct = NULL;
+    s->fc_nr = nr;
+    s->fc_dr = dr;
+    if (nr > 0) {
+        s->fct = zalloc((size_t)nr);
+        memcpy(s->fct, f, sizeof(double) * nr);
+    }
+    conservative_forces(s);
+    return 0;
+}
+
+/* A general (not separable) pair kernel: samples Kp[k][m] of K^p(r_k, m)
+ * (continuous samples or discrete weights as for or_set_kernels), added to
+ * the separable terms (set Q = 0 to use the table alone); the self kernel and
+ * the noise are set by or_set_kernels as before (call this after it). */
+int or_set_pair_table(or_sys* s, const double* Kp, int nr, double dr, int discrete)
+{
+    const int M = s->m_max;
+    if (nr < 0 || (nr > 0 && (nr < 2 || !(dr > 0) || !Kp))) return -1;
+    free(s->kpt);
+    s->kpt = NULL;
+    s->kp_nr = nr;
+    s->kp_dr = dr;
+    if (nr > 0) {
+        s->kpt = zalloc((size_t)nr * M);
+        for (int k = 0; k < nr; ++k) discretize(Kp + (size_t)k * M, M, s->dt, discrete, s->kpt + (size_t)k * M);
+    }
+    return 0;
+}
+
 static void ensure_noise(or_sys* s, int64_t n)
 {
     const int M = s->m_max, LW = 2 * M - 1;
@@ -489,7 +537,9 @@ static const double* dR_at(const or_sys* s, int64_t k)
     return s->hist + (size_t)(((k % H) + H) % H) * 3 * s->n;
 }
 
-/* F^C_i = sum_j -dU/dr e_ij with U = A (1 - r/rc)^2, at the current positions. */
+/* F^C_i = sum_j -dU/dr e_ij with U = A (1 - r/rc)^2, or with -dU/dr = f(r)
+ * read from a table (the form iterative Boltzmann inversion produces), at the
+ * current positions. */
 static void conservative_forces(or_sys* s)
 {
     build_neighbors(s->pos, s->n, s->L, s->rc, &s->nl);
@@ -502,7 +552,8 @@ static void conservative_forces(or_sys* s)
             double d[3];
             for (int c = 0; c < 3; ++c) d[c] = min_image(s->pos[3 * i + c] - s->pos[3 * j + c], L);
             double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-            double mag = (OR_PLANT == 8 ? -2.0 : 2.0) * A / rc * (1.0 - r / rc);
+            double mag = s->fc_nr > 0 ? table_at(s->fct, s->fc_nr, s->fc_dr, r)
+                                      : (OR_PLANT == 8 ? -2.0 : 2.0) * A / rc * (1.0 - r / rc);
             for (int c = 0; c < 3; ++c) F[c] += mag * d[c] / r;
         }
         for (int c = 0; c < 3; ++c) s->fc[3 * i + c] = F[c];
@@ -531,9 +582,21 @@ static void dissipative_force_i(const or_sys* s, int i, const int32_t* nb, int64
         double fq[8], fsq[8]; /* radial factors f_q(r), fs_q(r) (Q, Qs <= 8) */
         for (int q = 0; q < Q; ++q) fq[q] = table_at(s->f + (size_t)q * s->nr, s->nr, s->dr, rt);
         for (int q = 0; q < Qs; ++q) fsq[q] = table_at(s->fs + (size_t)q * s->nr, s->nr, s->dr, rt);
+        /* rows and weight of a general table at rt (the interpolation of table_at) */
+        int kr0 = 0, kr1 = 0;
+        double kw = 0.0;
+        if (s->kp_nr > 0) {
+            const double x = rt / s->kp_dr;
+            kr0 = x <= 0.0 ? 0 : (int)floor(x);
+            if (kr0 >= s->kp_nr - 1) { kr0 = kr1 = s->kp_nr - 1; }
+            else { kr1 = kr0 + 1; kw = (x <= 0.0 || OR_PLANT == 10) ? 0.0 : x - kr0; }
+        }
         for (int m = 0; m < M; ++m) {
-            /* K^p_m(r) = sum_q f_q(r) g_q[m],  dK^s_m(r) = sum_q fs_q(r) gs_q[m] */
+            /* K^p_m(r) = sum_q f_q(r) g_q[m] (or the general table),
+             * dK^s_m(r) = sum_q fs_q(r) gs_q[m] */
             double kp = 0.0, kds = 0.0;
+            if (s->kp_nr > 0)
+                kp = s->kpt[(size_t)kr0 * M + m] * (1.0 - kw) + s->kpt[(size_t)kr1 * M + m] * kw;
             for (int q = 0; q < Q; ++q) kp += fq[q] * s->gd[(size_t)q * M + m];
             for (int q = 0; q < Qs; ++q) kds += fsq[q] * s->gsd[(size_t)q * M + m];
             const double *xj, *xi;

@@ -182,6 +182,83 @@ def pin_fc_fd(variant=0):
     return err < 1e-6 and net < 1e-10, f"rel err {err:.2e}, |sum F| {net:.1e}"
 
 
+def _fc_table_f(r, rc):
+    """A smooth, non-monotonic force table: repulsive core plus an attractive
+    well, zero at r_c (the kind of curve iterative Boltzmann inversion gives)."""
+    x = np.clip(1 - r / rc, 0, None)
+    return 30 * x ** 3 - 8 * np.sin(2.5 * r) * x
+
+
+def _table_potential(pos, box, rc, f, dr):
+    """U = sum_pairs int_r^rc f_lin(s) ds with f_lin the linear interpolation of
+    the table: each segment contributes a trapezoid, exactly."""
+    d = pos[:, None, :] - pos[None, :, :]
+    d -= box * np.round(d / box)
+    r = np.sqrt((d ** 2).sum(-1))[np.triu_indices(len(pos), 1)]
+    r = r[r < rc]
+    nodes = np.arange(f.size) * dr
+    tail = np.concatenate([np.cumsum(((f[1:] + f[:-1]) * dr / 2)[::-1])[::-1], [0.0]])  # int_{node k}^{end}
+    U = 0.0
+    for x in r:
+        k = min(int(x // dr), f.size - 2)
+        fx = np.interp(x, nodes, f)
+        U += (fx + f[k + 1]) * (nodes[k + 1] - x) / 2 + tail[k + 1]
+    return float(U)
+
+
+def pin_fc_table(variant=0):
+    """Tabulated F^C: the table of the soft repulsion's force reproduces the
+    analytic F^C exactly (linear interpolation of a linear function), and for a
+    non-linear table F^C = -grad U with U the exact integral of the
+    interpolated table; sum_i F^C_i = 0."""
+    rng = np.random.default_rng(15)
+    n, box, rc, A = 24, 5.0, 2.0, 25.0
+    pos = rng.uniform(0, box, (n, 3))
+    s = oracle.System(n=n, box=box, mass=1.0, kT=0.0, dt=0.01, m_max=4, r_c=rc, A_cons=A,
+                      pos=pos, vel=np.zeros((n, 3)), variant=variant)
+    F0 = s.get(oracle.FC)
+    nr = 65
+    dr = rc / (nr - 1)
+    r = np.arange(nr) * dr
+    s.set_fc_table(2 * A / rc * (1 - r / rc), dr)
+    e_lin = np.abs(s.get(oracle.FC) - F0).max() / np.abs(F0).max()
+    f = _fc_table_f(r, rc)
+    s.set_fc_table(f, dr)
+    F = s.get(oracle.FC)
+    h = 1e-6
+    Ffd = np.zeros_like(F)
+    for i in range(n):
+        for c in range(3):
+            pp, pm = pos.copy(), pos.copy()
+            pp[i, c] += h
+            pm[i, c] -= h
+            Ffd[i, c] = -(_table_potential(pp, box, rc, f, dr) - _table_potential(pm, box, rc, f, dr)) / (2 * h)
+    err = np.abs(F - Ffd).max() / np.abs(Ffd).max()
+    net = np.abs(F.sum(0)).max()
+    return bool(e_lin < 1e-12 and err < 1e-6 and net < 1e-10), f"linear table {e_lin:.1e}, FD {err:.2e}, |sum F| {net:.1e}"
+
+
+def pin_pair_table(variant=0):
+    """A general pair-kernel table equal to f(r) g(m) (rank one) integrates the
+    same trajectory as the separable term f, g: displacement and F^D after 30
+    steps agree to rounding."""
+    w = inputs.SMALL
+    pos, vel = inputs.initial_state(w, seed=9)
+    g, f, dr = inputs.pair_kernel_tables(w)
+    ks = inputs.self_kernel_samples(w)
+    kw = dict(n=w.n, box=w.box, mass=1.0, kT=1.0, dt=w.dt, m_max=w.m_max, r_c=w.r_c, A_cons=w.A_cons,
+              seed=4, pos=pos, vel=vel, variant=variant)
+    a, b = oracle.System(**kw), oracle.System(**kw)
+    a.set_kernels(ks, g=g, f=f, dr=dr)
+    b.set_kernels(ks)
+    b.set_pair_table(np.outer(f[0], g[0]), dr)
+    a.step(30)
+    b.step(30)
+    e_d = np.abs(a.get(oracle.DISP) - b.get(oracle.DISP)).max() / np.abs(a.get(oracle.DISP)).max()
+    e_f = np.abs(a.get(oracle.FD) - b.get(oracle.FD)).max() / np.abs(a.get(oracle.FD)).max()
+    return bool(e_d < 1e-10 and e_f < 1e-10), f"displacement {e_d:.1e}, F^D {e_f:.1e}"
+
+
 # ----------------------------------------------------------------- integrator --
 def _soft_system(variant, n=64, box=8.0, seed=11, steps_kernel_zero=True, **kw):
     w = inputs.SMALL
@@ -503,6 +580,8 @@ ALL = {
     "noise_autocorrelation": pin_noise_autocorrelation,
     "vacf_closed_form": pin_vacf_closed_form,
     "vacf_accumulator": pin_vacf_accumulator,
+    "fc_table": pin_fc_table,
+    "pair_table": pin_pair_table,
     "paircorr_closed_form": pin_paircorr_closed_form,
     "paircorr_definition": pin_paircorr_definition,
 }

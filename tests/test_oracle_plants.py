@@ -15,6 +15,7 @@ PLANTS = {
     7: "V_i in place of V_j in the instantaneous pair term",
     8: "conservative force with the wrong sign",
     9: "auto and cross pair correlation terms swapped",
+    10: "pair-kernel table not interpolated",
 }
 
 
