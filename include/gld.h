@@ -228,6 +228,26 @@ enum {
 };
 gld_status gld_profile_steps(gld_ctx* ctx, int64_t nsteps, double* ms, int64_t* launches);
 
+/* Tabulated conservative force (the form iterative Boltzmann inversion gives,
+ * Sec. III): F^C_ij = f(r_ij) e_ij with f = -dU/dr sampled on r = k dr,
+ * k < nr, linear between samples and constant past the last (pairs are taken
+ * within r_c).  Replaces the soft repulsion A (1 - r/r_c)^2; nr = 0 returns to
+ * it.  F^C is recomputed at the current positions.  Synchronizes. */
+gld_status gld_set_conservative_table(gld_ctx* ctx, const double* f, int32_t nr, double dr);
+/* A general, not separable, pair kernel given as samples Kp[k][m] =
+ * K^p(k dr, m dt) (k < nr, m < m_max; the parallel component of Eq.
+ * dissipative_force2): its best rank-Q approximation (SVD in FP64, 1 <= Q <= 4)
+ * becomes Q separable terms f_q(r) g_q[m], set with gld_set_kernels together
+ * with the self kernel Ks (kernel_convention as there).  *trunc receives the
+ * relative Frobenius norm of the discarded part (NULL allowed). */
+gld_status gld_set_kernels_table(gld_ctx* ctx, const double* Ks, const double* Kp, int32_t nr, double dr,
+                                 int32_t Q, int32_t kernel_convention, double* trunc);
+/* The separation itself, on the host (no device needed): f[Q][nr], g[Q][m]
+ * with table ~ sum_q f_q g_q^T, f_q carrying the singular value; *trunc as
+ * above.  GLD_E_INVAL unless 1 <= Q <= min(nr, m). */
+gld_status gld_separable_terms(const double* table, int32_t nr, int32_t m, int32_t Q, double* f, double* g,
+                               double* trunc);
+
 /* Memory sums in auxiliary-variable form (App. C discusses auxiliary-variable
  * expansions as the alternative to a stored history).  When every kernel
  * given to gld_set_kernels is, for m >= 1, a combination of the modes
@@ -285,7 +305,9 @@ gld_status gld_destroy(gld_ctx* ctx);
  * VACF and state are read through the gld_* calls above); a member must have
  * its kernels set, use the batch's stream, sit at a 64-step boundary, and
  * share the number of kernel terms, the history type and compensation with
- * the other members.  Results of a member do not depend on the other members.
+ * the other members.  A member's kernels, tables and parameters are read when
+ * it joins: change them only while it is out of the batch.  Results of a
+ * member do not depend on the other members.
  * The convolution's tile schedule is picked by timing four candidates on the
  * current composition (256- or 128-column tiles, longest memory first, member
  * order, or one block per member). */

@@ -99,6 +99,9 @@ def lib():
             "gld_get_bytes": (i32, [vp, C.POINTER(i64)]),
             "gld_set_pair_correlation": (i32, [vp, i32, d]),
             "gld_set_memory_modes": (i32, [vp, i32, vp, vp]),
+            "gld_set_conservative_table": (i32, [vp, vp, i32, C.c_double]),
+            "gld_set_kernels_table": (i32, [vp, vp, vp, i32, C.c_double, i32, i32, C.POINTER(C.c_double)]),
+            "gld_separable_terms": (i32, [vp, i32, i32, i32, vp, vp, C.POINTER(C.c_double)]),
             "gld_pair_correlation": (i32, [vp, vp, vp, vp]),
             "gld_bytes_needed": (i32, [C.POINTER(Params), i32, i32, i32, C.POINTER(i64)]),
             "gld_batch_set_tuning": (i32, [vp, i32]),
@@ -141,7 +144,8 @@ def exported_symbols() -> list[str]:
             "gld_server_params_default", "gld_server_create", "gld_server_submit", "gld_server_pump",
             "gld_server_drain", "gld_server_clock", "gld_server_result", "gld_server_stats",
             "gld_server_last_error", "gld_server_destroy", "gld_server_cancel", "gld_set_pair_correlation",
-            "gld_pair_correlation", "gld_set_memory_modes"]
+            "gld_pair_correlation", "gld_set_memory_modes", "gld_set_conservative_table",
+            "gld_set_kernels_table", "gld_separable_terms"]
 
 
 def _ptr(a: np.ndarray):
@@ -309,6 +313,25 @@ class GLD:
         are sums of the modes exp((-rate + i omega) t); empty: the ring."""
         r, o = _f64(rates).ravel(), _f64(omegas).ravel()
         self._check(lib().gld_set_memory_modes(self._h, int(r.size), _ptr(r), _ptr(o)))
+
+    def set_conservative_table(self, f, dr: float = 1.0):
+        """F^C from a tabulated -dU/dr on r = k dr (None: the soft repulsion)."""
+        if f is None:
+            self._check(lib().gld_set_conservative_table(self._h, None, 0, 1.0))
+            return
+        f = _f64(f).ravel()
+        self._check(lib().gld_set_conservative_table(self._h, _ptr(f), int(f.size), float(dr)))
+
+    def set_kernels_table(self, Ks, Kp, dr: float, Q: int = 4, discrete: bool = False) -> float:
+        """Self kernel Ks and a general pair kernel Kp[k, m] = K^p(k dr, m dt),
+        reduced to its best rank-Q separable form; returns the relative
+        Frobenius norm of the discarded part."""
+        Ks, Kp = _f64(Ks), _f64(Kp).reshape(-1, self.m_max)
+        tr = C.c_double()
+        self._check(lib().gld_set_kernels_table(self._h, _ptr(Ks), _ptr(Kp), int(Kp.shape[0]), float(dr), int(Q),
+                                                KDISCRETE if discrete else KCONT, C.byref(tr)))
+        self.nacc = 1 + min(int(Q), Kp.shape[0], self.m_max)
+        return float(tr.value)
 
     def set_pair_correlation(self, nbins: int, r_max: float):
         """Enables C^a(R, t), C^c(R, t) on nbins distance bins of [0, r_max)."""
@@ -593,3 +616,15 @@ def pairs_noalloc(pos4, box, r_c, pairs, count, stream=None):
                                  _current_stream() if stream is None else stream)
     if st != OK:
         raise GLDError(st, "gld_pairs_noalloc")
+
+
+def separable_terms(table, Q: int):
+    """Host-side rank-Q separation of table[nr, m] ~ f^T g: (f[Q, nr], g[Q, m],
+    relative Frobenius norm of the remainder)."""
+    t = _f64(table)
+    nr, m = t.shape
+    f, g, tr = np.zeros((Q, nr)), np.zeros((Q, m)), C.c_double()
+    st = lib().gld_separable_terms(_ptr(t), nr, m, int(Q), _ptr(f), _ptr(g), C.byref(tr))
+    if st != 0:
+        raise GLDError(st, "gld_separable_terms failed")
+    return f, g, float(tr.value)

@@ -1040,6 +1040,129 @@ gld_status gld_profile_steps(gld_ctx* c, int64_t nsteps, double* ms, int64_t* la
     return sync_and_check(c);
 }
 
+gld_status gld_set_conservative_table(gld_ctx* c, const double* f, int32_t nr, double dr)
+{
+    if (!c) return GLD_E_INVAL;
+    if (nr != 0 && (nr < 2 || !f || !(dr > 0)))
+        return fail(c, GLD_E_INVAL, "gld_set_conservative_table: need nr >= 2 points and dr > 0 (or nr = 0)");
+    GLD_TRY(sync_and_check(c));
+    StepParams& P = c->P;
+    float* old = (float*)c->B.fctab;
+    c->B.fctab = nullptr;
+    P.fc_nr = 0;
+    if (old) dfree(c, old);
+    if (nr > 0) {
+        std::vector<float> h((size_t)nr);
+        for (int k = 0; k < nr; ++k) h[(size_t)k] = (float)f[k];
+        float* d = (float*)dalloc(c, sizeof(float) * h.size());
+        if (!d) return fail(c, GLD_E_NOMEM, "gld_set_conservative_table: allocation failed");
+        GLD_CUDA(c, cudaMemcpyAsync(d, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice, c->st));
+        c->B.fctab = d;
+        P.fc_nr = nr;
+        P.fc_inv_dr = (float)(1.0 / dr);
+    }
+    invalidate_graph(c);
+    GLD_CUDA(c, launch_cforce(P, c->B, 0, c->st));  // F^C_n at the current positions
+    return sync_and_check(c);
+}
+
+gld_status gld_separable_terms(const double* table, int32_t nr, int32_t m, int32_t Q, double* f, double* g,
+                               double* trunc)
+{
+    if (!table || nr < 1 || m < 1 || Q < 1 || Q > std::min(nr, m) || !f || !g) return GLD_E_INVAL;
+    // Gram matrix of the smaller side, eigenvectors by cyclic Jacobi rotations
+    const bool rows = nr <= m;  // G = T T^T (nr x nr) or T^T T (m x m)
+    const int d = rows ? nr : m;
+    auto at = [&](int k, int j) { return table[(size_t)k * m + j]; };
+    std::vector<double> G((size_t)d * d, 0.0), E((size_t)d * d, 0.0);
+    for (int a = 0; a < d; ++a)
+        for (int b = a; b < d; ++b) {
+            double acc = 0.0;
+            if (rows)
+                for (int j = 0; j < m; ++j) acc += at(a, j) * at(b, j);
+            else
+                for (int k = 0; k < nr; ++k) acc += at(k, a) * at(k, b);
+            G[(size_t)a * d + b] = G[(size_t)b * d + a] = acc;
+        }
+    for (int a = 0; a < d; ++a) E[(size_t)a * d + a] = 1.0;
+    double total = 0.0;
+    for (int a = 0; a < d; ++a) total += G[(size_t)a * d + a];
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < d; ++p)
+            for (int q = p + 1; q < d; ++q) off += G[(size_t)p * d + q] * G[(size_t)p * d + q];
+        if (off <= 1e-30 * total * total) break;
+        for (int p = 0; p < d; ++p)
+            for (int q = p + 1; q < d; ++q) {
+                const double apq = G[(size_t)p * d + q];
+                if (apq == 0.0) continue;
+                const double theta = (G[(size_t)q * d + q] - G[(size_t)p * d + p]) / (2.0 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double cs = 1.0 / std::sqrt(t * t + 1.0), sn = t * cs;
+                for (int k = 0; k < d; ++k) {  // columns p, q
+                    const double gp = G[(size_t)k * d + p], gq = G[(size_t)k * d + q];
+                    G[(size_t)k * d + p] = cs * gp - sn * gq;
+                    G[(size_t)k * d + q] = sn * gp + cs * gq;
+                }
+                for (int k = 0; k < d; ++k) {  // rows p, q
+                    const double gp = G[(size_t)p * d + k], gq = G[(size_t)q * d + k];
+                    G[(size_t)p * d + k] = cs * gp - sn * gq;
+                    G[(size_t)q * d + k] = sn * gp + cs * gq;
+                }
+                for (int k = 0; k < d; ++k) {
+                    const double ep = E[(size_t)k * d + p], eq = E[(size_t)k * d + q];
+                    E[(size_t)k * d + p] = cs * ep - sn * eq;
+                    E[(size_t)k * d + q] = sn * ep + cs * eq;
+                }
+            }
+    }
+    std::vector<int> order(d);
+    for (int a = 0; a < d; ++a) order[a] = a;
+    std::sort(order.begin(), order.end(),
+              [&](int x, int y) { return G[(size_t)x * d + x] > G[(size_t)y * d + y]; });
+    double kept = 0.0;
+    for (int q = 0; q < Q; ++q) {
+        const int e = order[q];
+        const double lam = std::max(G[(size_t)e * d + e], 0.0), sig = std::sqrt(lam);
+        kept += lam;
+        // one side is the eigenvector, the other the table applied to it over sigma
+        for (int k = 0; k < nr; ++k) f[(size_t)q * nr + k] = 0.0;
+        for (int j = 0; j < m; ++j) g[(size_t)q * m + j] = 0.0;
+        if (rows) {
+            for (int k = 0; k < nr; ++k) f[(size_t)q * nr + k] = sig * E[(size_t)k * d + e];
+            for (int j = 0; j < m && sig > 0; ++j) {
+                double acc = 0.0;
+                for (int k = 0; k < nr; ++k) acc += at(k, j) * E[(size_t)k * d + e];
+                g[(size_t)q * m + j] = acc / sig;
+            }
+        } else {
+            for (int j = 0; j < m; ++j) g[(size_t)q * m + j] = E[(size_t)j * d + e];
+            for (int k = 0; k < nr; ++k) {
+                double acc = 0.0;
+                for (int j = 0; j < m; ++j) acc += at(k, j) * E[(size_t)j * d + e];
+                f[(size_t)q * nr + k] = acc;
+            }
+        }
+    }
+    if (trunc) *trunc = total > 0 ? std::sqrt(std::max(total - kept, 0.0) / total) : 0.0;
+    return GLD_OK;
+}
+
+gld_status gld_set_kernels_table(gld_ctx* c, const double* Ks, const double* Kp, int32_t nr, double dr, int32_t Q,
+                                 int32_t conv, double* trunc)
+{
+    if (!c) return GLD_E_INVAL;
+    const int M = c->P.m_max;
+    if (!Kp || nr < 2 || !(dr > 0) || Q < 1 || Q > kMaxQ)
+        return fail(c, GLD_E_INVAL, "gld_set_kernels_table: need a table of nr >= 2 rows and 1 <= Q <= 4");
+    std::vector<double> f((size_t)Q * nr), g((size_t)Q * M);
+    double tr = 0.0;
+    if (gld_separable_terms(Kp, nr, M, std::min(Q, std::min(nr, M)), f.data(), g.data(), &tr) != GLD_OK)
+        return fail(c, GLD_E_INVAL, "gld_set_kernels_table: invalid table");
+    if (trunc) *trunc = tr;
+    return gld_set_kernels(c, Ks, std::min(Q, std::min(nr, M)), g.data(), f.data(), nr, dr, nullptr, nullptr, 0, conv);
+}
+
 gld_status gld_set_memory_modes(gld_ctx* c, int32_t nmodes, const double* rate, const double* omega)
 {
     if (!c) return GLD_E_INVAL;

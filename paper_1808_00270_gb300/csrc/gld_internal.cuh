@@ -73,6 +73,9 @@ struct StepParams {
     long long vacf_burnin;
     // memory sums in recursive (auxiliary-variable) form: modes (0: ring convolution)
     int nmodes;
+    // tabulated conservative force -dU/dr on r = k / fc_inv_dr (0 rows: soft repulsion)
+    int fc_nr;
+    float fc_inv_dr;
     // distance-binned pair correlations (0 bins: off)
     int pc_nbins;
     float pc_rmax2, pc_inv_dr;  // r_max^2, nbins / r_max

@@ -432,7 +432,7 @@ template <bool STEP>
 __device__ __forceinline__ void cforce_body(const StepParams& P, Ctrl* __restrict__ ctrl, const float4* __restrict__ pos_next,
            float4* __restrict__ pos, const int* __restrict__ perm, const int* __restrict__ nbr,
            const int* __restrict__ nbr_cnt, const float4* __restrict__ vhalf, float4* __restrict__ vel,
-           float4* __restrict__ fc, int blk, int nblk)
+           float4* __restrict__ fc, const float* __restrict__ fctab, int blk, int nblk)
 {
     // kCforceLanes consecutive lanes share a particle and split its list
     const int k = (blk * blockDim.x + threadIdx.x) / kCforceLanes;
@@ -462,7 +462,9 @@ __device__ __forceinline__ void cforce_body(const StepParams& P, Ctrl* __restric
                 if (j[u] >= 0 && r2 < P.rc2) {
                     const float r = sqrtf(r2);
                     // -dU/dr e_ij with U = A (1 - r/r_c)^2, e_ij = (R_i - R_j)/r
-                    const float sc = P.fc_mag * (1.0f - r * P.inv_rc) / r;
+                    // -dU/dr: a table (P.fc_nr > 0) or the soft repulsion A (1 - r/r_c)^2
+                    const float sc = (P.fc_nr > 0 ? table_at(fctab, P.fc_nr, r * P.fc_inv_dr)
+                                                   : P.fc_mag * (1.0f - r * P.inv_rc)) / r;
                     fx = fmaf(sc, dx, fx);
                     fy = fmaf(sc, dy, fy);
                     fz = fmaf(sc, dz, fz);
@@ -503,9 +505,9 @@ template <bool STEP>
 __global__ void __launch_bounds__(kThreads) cforce(const StepParams P, Ctrl* __restrict__ ctrl, const float4* __restrict__ pos_next,
            float4* __restrict__ pos, const int* __restrict__ perm, const int* __restrict__ nbr,
            const int* __restrict__ nbr_cnt, const float4* __restrict__ vhalf, float4* __restrict__ vel,
-           float4* __restrict__ fc)
+           float4* __restrict__ fc, const float* __restrict__ fctab)
 {
-    cforce_body<STEP>(P, ctrl, pos_next, pos, perm, nbr, nbr_cnt, vhalf, vel, fc, blockIdx.x, gridDim.x);
+    cforce_body<STEP>(P, ctrl, pos_next, pos, perm, nbr, nbr_cnt, vhalf, vel, fc, fctab, blockIdx.x, gridDim.x);
 }
 
 // ---- velocity autocorrelation ------------------------------------------------
@@ -895,7 +897,8 @@ __global__ void __launch_bounds__(kThreads) b_cforce(const SysDesc* __restrict__
     const Tile t = tiles[blockIdx.x];
     const SysDesc& d = D[t.m];
     const ParticleBuffers& B = d.B;
-    cforce_body<true>(d.P, B.ctrl, B.pos_next, B.pos, B.perm, B.nbr, B.nbr_cnt, B.vhalf, B.vel, B.fc, t.b, d.nb_cf);
+    cforce_body<true>(d.P, B.ctrl, B.pos_next, B.pos, B.perm, B.nbr, B.nbr_cnt, B.vhalf, B.vel, B.fc, B.fctab, t.b,
+                      d.nb_cf);
 }
 
 __global__ void __launch_bounds__(kThreads) b_vacf(const SysDesc* __restrict__ D, const Tile* __restrict__ tiles)
@@ -977,10 +980,10 @@ cudaError_t launch_cforce(const StepParams& P, const ParticleBuffers& B, int mod
     const unsigned grid = (unsigned)(((long long)P.n * kCforceLanes + kThreads - 1) / kThreads);
     if (mode)
         cforce<true><<<grid, kThreads, 0, st>>>(P, B.ctrl, B.pos_next, B.pos, B.perm, B.nbr, B.nbr_cnt, B.vhalf,
-                                                B.vel, B.fc);
+                                                B.vel, B.fc, B.fctab);
     else
         cforce<false><<<grid, kThreads, 0, st>>>(P, B.ctrl, B.pos_next, B.pos, B.perm, B.nbr, B.nbr_cnt, B.vhalf,
-                                                 B.vel, B.fc);
+                                                 B.vel, B.fc, B.fctab);
     return cudaGetLastError();
 }
 
