@@ -4,8 +4,9 @@ This package is the slow, plain reference that the CUDA path is checked
 against.  Only the test-suite, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import it; the
 product path never does.  The arithmetic lives in ``gldref.c`` (plain C,
-double precision, OpenMP over particles); this module only compiles it and
-marshals arrays through ctypes.
+double precision, OpenMP over particles) and, for the pair-correlated noise
+with its dense matrix square roots, in ``pairnoise.py`` (numpy); this module
+compiles the C part and marshals arrays through ctypes.
 
 Paper: Jung, Hanke & Schmid, arXiv:1808.00270.  Sections followed are listed
 in the header of ``gldref.c``.
@@ -97,6 +98,8 @@ def lib(variant: int = 0):
             L.or_set_paircorr.argtypes = [vp, i32, C.c_double]
             L.or_set_paircorr.restype = i32
             L.or_get_paircorr.argtypes = [vp, vp, vp, vp]
+            L.or_white_window.argtypes = [vp, i64, vp]
+            L.or_set_fr_override.argtypes = [vp, vp]
             L.or_set_threads.argtypes = [i32]
             L.or_get_threads.restype = i32
             _libs[variant] = L
@@ -193,6 +196,9 @@ class System:
         if not self._h:
             raise ValueError("oracle: invalid parameters")
         self.vacf_len = int(vacf_len)
+        self._geom = dict(box=float(box), rc=float(r_c), rc_min=float(r_c_min), kT=float(kT), dt=float(dt))
+        self._variant = int(variant)
+        self._kern = None
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -208,8 +214,35 @@ class System:
         nr = (f.shape[-1] if f is not None else (fs.shape[-1] if fs is not None else 2))
         f = np.zeros((0, nr)) if f is None else _f64(f).reshape(-1, nr)
         fs = np.zeros((0, nr)) if fs is None else _f64(fs).reshape(-1, nr)
+        self._kern = dict(Ks=Ks, g=g, f=f, dr=float(dr), gs=gs, fs=fs, discrete=bool(discrete))
         return int(self._L.or_set_kernels(self._h, _p(Ks), g.shape[0], _p(g), _p(f), nr, dr,
                                           gs.shape[0], _p(gs), _p(fs), int(discrete), int(clamp)))
+
+    def white_window(self, step=None) -> np.ndarray:
+        """W_{i,n+s} for s = -(m_max-1) .. m_max-1: [2 m_max - 1, N, 3]."""
+        n = self.step_index if step is None else int(step)
+        out = np.zeros((2 * self.m_max - 1, self.n, 3))
+        self._L.or_white_window(self._h, n, _p(out))
+        return out
+
+    def pair_random_force(self, clamp: bool = False) -> np.ndarray:
+        """F^R of the coming step with the pair-correlated noise (Sec. II C,
+        Algorithm 1 evaluated exactly; see pairnoise.py)."""
+        from . import pairnoise
+        k, G = self._kern, self._geom
+        terms = pairnoise.matrix_terms(self.get(POS), G["box"], G["rc"], G["rc_min"], self.m_max, G["dt"],
+                                       k["Ks"], k["g"], k["f"], k["dr"], k["gs"], k["fs"], k["discrete"],
+                                       variant=self._variant)
+        return pairnoise.random_force(terms, G["kT"], G["dt"], self.m_max, self.white_window(), clamp=clamp,
+                                      variant=self._variant)
+
+    def step_pair_noise(self, nsteps: int = 1, clamp: bool = False) -> None:
+        """Steps with the pair-correlated random force instead of the
+        self-kernel noise."""
+        for _ in range(int(nsteps)):
+            F = _f64(self.pair_random_force(clamp))
+            self._L.or_set_fr_override(self._h, _p(F))
+            self.step(1)
 
     def step(self, nsteps: int = 1) -> None:
         st = self._L.or_step(self._h, int(nsteps))

@@ -39,7 +39,8 @@
  *     K_0 = dt K(0) / 2 (trapezoid weights of the delta comb, consistent with
  *     a_0 = 2), unless the caller passes discrete K_m directly;
  *   - the noise is generated from the self kernel only (Sec. II C, last
- *     remark); pair dissipation is applied without pair noise;
+ *     remark) unless the caller supplies F^R for the step (the
+ *     pair-correlated noise of Algorithm 1, evaluated by pairnoise.py);
  *   - the inverse transform for A_s uses 1/(2 m_max - 1);
  *   - history and noise before t = 0: Delta R = 0, W from the same counters.
  */
@@ -60,7 +61,8 @@
  *   4 inverse transform scaled by 1/m_max   5 history read one step late
  *   6 a_0 = 1 in the noise target           7 V_i in place of V_j at m = 0
  *   8 sign of F^C flipped                  9 auto and cross pair terms swapped
- *  10 pair-kernel table read at the lower row, not interpolated */
+ *  10 pair-kernel table read at the lower row, not interpolated
+ *  (11 and 12 are planted in pairnoise.py; this file builds unchanged) */
 #ifndef OR_PLANT
 #define OR_PLANT 0
 #endif
@@ -384,6 +386,10 @@ typedef struct {
     double* kpt;
     int kp_nr;
     double kp_dr;
+    /* F^R supplied by the caller for the next step only (the pair-correlated
+     * noise of Algorithm 1 is evaluated outside this file) */
+    double* fr_ovr;
+    int fr_ovr_on;
     or_nblist nl;
 } or_sys;
 
@@ -429,7 +435,7 @@ void or_destroy(or_sys* s)
     if (!s) return;
     double* arrs[] = { s->Kd, s->gd, s->f, s->gsd, s->fs, s->C, s->Chat, s->A, s->pos, s->vel,
                        s->fc, s->fd, s->fr, s->disp, s->hist, s->W, s->vorig, s->csum, s->pc_a, s->pc_c,
-                       s->fct, s->kpt };
+                       s->fct, s->kpt, s->fr_ovr };
     for (size_t k = 0; k < sizeof(arrs) / sizeof(arrs[0]); ++k) free(arrs[k]);
     free(s->wtime); free(s->ccnt); free(s->nl.start); free(s->nl.list); free(s->pc_n);
     free(s);
@@ -754,7 +760,8 @@ int or_step(or_sys* s, int64_t nsteps)
         for (int i = 0; i < n; ++i) {
             double FD[3], FR[3];
             dissipative_force_i(s, i, s->nl.list + s->nl.start[i], s->nl.start[i + 1] - s->nl.start[i], FD);
-            random_force_i(s, i, FR, 0);
+            if (s->fr_ovr_on) for (int c = 0; c < 3; ++c) FR[c] = s->fr_ovr[3 * i + c];
+            else random_force_i(s, i, FR, 0);
             for (int c = 0; c < 3; ++c) {
                 double v = s->vel[3 * i + c];
                 double Ft = s->fc[3 * i + c] + FD[c] + FR[c];
@@ -770,6 +777,7 @@ int or_step(or_sys* s, int64_t nsteps)
             s->pos[i] = wrap(s->pos[i] + dRtmp[i], s->L);
         }
         free(dRtmp);
+        s->fr_ovr_on = 0;
         conservative_forces(s); /* F^C_{n+1} at R_{n+1}; rebuilds the lists */
         for (int i = 0; i < 3 * n; ++i) s->vel[i] = vhalf[i] + dt / (2.0 * M) * s->fc[i];
         s->step++;
@@ -777,6 +785,25 @@ int or_step(or_sys* s, int64_t nsteps)
     }
     free(vhalf);
     return 0;
+}
+
+/* The white noise of the window of step n: out[s + m_max - 1][i][c] =
+ * W_{i,n+s}, s = -(m_max-1) .. m_max-1 (the counters of or_gauss3). */
+void or_white_window(const or_sys* s, int64_t n, double* out)
+{
+    const int M = s->m_max;
+#pragma omp parallel for schedule(static)
+    for (int sh = -(M - 1); sh <= M - 1; ++sh)
+        for (int i = 0; i < s->n; ++i)
+            or_gauss3(s->seed, (uint32_t)i, n + sh, 0u, out + ((size_t)(sh + M - 1) * s->n + i) * 3);
+}
+
+/* Uses fr[i][c] as F^R of the next step (one step only). */
+void or_set_fr_override(or_sys* s, const double* fr)
+{
+    if (!s->fr_ovr) s->fr_ovr = zalloc((size_t)3 * s->n);
+    memcpy(s->fr_ovr, fr, sizeof(double) * 3 * (size_t)s->n);
+    s->fr_ovr_on = 1;
 }
 
 /* Forces of the coming step n for a subset of particles (neighbours by

@@ -564,6 +564,99 @@ def pin_paircorr_definition(variant=0):
     return bool(np.array_equal(cnt, wn) and err < 1e-12 and wn.sum() > 0), f"max err {err:.1e}, samples {wn.sum()}"
 
 
+# ---------------------------------------------------------- pair-correlated noise --
+def _pn_kernels(m_max, dt, nr=41, rc=2.0):
+    t = np.arange(m_max) * dt
+    dr = rc / (nr - 1)
+    r = np.arange(nr) * dr
+    return (10.0 * np.exp(-t / 0.2), np.exp(-t / 0.3)[None, :], (2.0 * (1 - r / rc) ** 2)[None, :], dr)
+
+
+def pin_pair_noise_self_limit(variant=0):
+    """Without pair kernels the matrix square roots of Algorithm 1 reduce to
+    the scalar moving average of the self-kernel noise: the dense
+    frequency-domain evaluation equals sum_s A_s W_{n+s} of the oracle's own
+    generator for every particle."""
+    rng = np.random.default_rng(21)
+    n, box, M, dt = 12, 6.0, 12, 0.02
+    s = oracle.System(n=n, box=box, mass=1.0, kT=1.3, dt=dt, m_max=M, r_c=2.0, pos=rng.uniform(0, box, (n, 3)),
+                      vel=np.zeros((n, 3)), seed=5, variant=variant)
+    Ks = _pn_kernels(M, dt)[0]
+    s.set_kernels(Ks)
+    s.set_step(37)
+    F = s.pair_random_force()
+    fd, fr = np.zeros((n, 3)), np.zeros((n, 3))
+    idx = np.arange(n, dtype=np.int32)
+    s._L.or_forces_subset(s._h, oracle._p(idx), n, oracle._p(fd), oracle._p(fr))
+    err = np.abs(F - fr).max() / np.abs(fr).max()
+    return bool(err < 1e-12), f"dense evaluation vs scalar generator {err:.1e}"
+
+
+def pin_pair_noise_two_particles(variant=0):
+    """Two particles at distance r (Sec. III A): the noise decouples into the
+    modes (F_1 +- F_2).e / sqrt 2 with kernels K^s +- f(r) g, and the
+    perpendicular modes with K^s alone -- each must equal the scalar generator
+    (A_s of the oracle, Eq. noise_production) for that kernel applied to the
+    same projection of W."""
+    M, dt, kT = 10, 0.02, 0.7
+    Ks, g, f, dr = _pn_kernels(M, dt)
+    rng = np.random.default_rng(8)
+    e = rng.normal(size=3)
+    e /= np.linalg.norm(e)
+    u = np.cross(e, [0.3, -0.5, 0.8])
+    u /= np.linalg.norm(u)
+    r = 1.2
+    pos = np.array([[4.0, 4.0, 4.0], [4.0, 4.0, 4.0]]) + np.array([0.5 * r * e, -0.5 * r * e])
+    s = oracle.System(n=2, box=10.0, mass=1.0, kT=kT, dt=dt, m_max=M, r_c=2.0, pos=pos, vel=np.zeros((2, 3)),
+                      seed=3, variant=variant)
+    s.set_kernels(Ks, g=g, f=f, dr=dr)
+    s.set_step(11)
+    F = s.pair_random_force()
+    W = s.white_window()
+    fr = np.interp(r, np.arange(f.shape[1]) * dr, f[0])
+    Kd = Ks * dt
+    Kd[0] *= 0.5
+    gd = g[0] * dt
+    gd[0] *= 0.5
+    worst = 0.0
+    for sign in (1.0, -1.0):
+        for v, kern in ((e, Kd + sign * fr * gd), (u, Kd)):
+            st, _, _, A, _ = oracle.noise_coefs(kern, kT, dt)
+            Wp = (W[:, 0, :] + sign * W[:, 1, :]) @ v / np.sqrt(2)
+            want = float(A @ Wp)
+            got = float((F[0] + sign * F[1]) @ v / np.sqrt(2))
+            worst = max(worst, abs(got - want) / max(abs(want), 1e-3))
+    return bool(worst < 1e-10), f"mode projections vs scalar generator {worst:.1e}"
+
+
+def pin_pair_noise_covariance(variant=0):
+    """Eq. noise_ansatz for the full matrix kernel: the generator is linear in
+    W, F_n = sum_s B_s W_{n+s}; its impulse responses B_s (one unit W at a
+    time) must satisfy sum_s B_s B_{s+m}^T = K_m (indices wrapped with period
+    2 m_max - 1) for the 3N x 3N correlation matrices of a 5-particle cluster
+    with pair and self-difference terms."""
+    from oracle import pairnoise
+    M, dt, kT = 6, 0.05, 1.1
+    Ks, g, f, dr = _pn_kernels(M, dt)
+    rng = np.random.default_rng(2)
+    pos = 3.0 + rng.uniform(0, 1.6, (5, 3))
+    terms = pairnoise.matrix_terms(pos, 8.0, 2.0, 0.3, M, dt, Ks, g, f, dr, gs=0.5 * g, fs=0.3 * f,
+                                   variant=variant)
+    L, n3 = 2 * M - 1, 15
+    B = np.zeros((L, n3, n3))
+    for sh in range(L):
+        for J in range(n3):
+            Wwin = np.zeros((L, 5, 3))
+            Wwin[sh, J // 3, J % 3] = 1.0
+            B[sh, :, J] = pairnoise.random_force(terms, kT, dt, M, Wwin, variant=variant).reshape(n3)
+    worst = 0.0
+    for m in range(M):
+        Cm = sum(B[sh] @ B[(sh + m) % L].T for sh in range(L))
+        Km = pairnoise.correlation_matrix(terms, kT, dt, m)
+        worst = max(worst, np.abs(Cm - Km).max() / np.abs(pairnoise.correlation_matrix(terms, kT, dt, 0)).max())
+    return bool(worst < 1e-10), f"sum_s B_s B_(s+m)^T vs K_m {worst:.1e}"
+
+
 ALL = {
     "philox_kat": pin_philox_kat,
     "gauss_moments": pin_gauss_moments,
@@ -584,4 +677,7 @@ ALL = {
     "pair_table": pin_pair_table,
     "paircorr_closed_form": pin_paircorr_closed_form,
     "paircorr_definition": pin_paircorr_definition,
+    "pair_noise_self_limit": pin_pair_noise_self_limit,
+    "pair_noise_two_particles": pin_pair_noise_two_particles,
+    "pair_noise_covariance": pin_pair_noise_covariance,
 }

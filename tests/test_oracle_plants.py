@@ -1,6 +1,7 @@
 """A pin set is only trusted if it fails for plausible mistakes: each of these
-oracle builds carries one planted error (OR_PLANT in oracle/gldref.c), and at
-least one pin must reject it.  The mistakes are planted on the CPU only."""
+oracle builds carries one planted error (OR_PLANT in oracle/gldref.c, or the
+``variant`` of oracle/pairnoise.py for 11 and 12), and at least one pin must
+reject it.  The mistakes are planted on the CPU only."""
 import pytest
 
 import oracle_pins as P
@@ -16,6 +17,8 @@ PLANTS = {
     8: "conservative force with the wrong sign",
     9: "auto and cross pair correlation terms swapped",
     10: "pair-kernel table not interpolated",
+    11: "pair blocks of the noise correlation matrix with the wrong sign",
+    12: "pair-noise inverse transform scaled by 1/m_max",
 }
 
 
