@@ -248,6 +248,27 @@ gld_status gld_set_kernels_table(gld_ctx* ctx, const double* Ks, const double* K
 gld_status gld_separable_terms(const double* table, int32_t nr, int32_t m, int32_t Q, double* f, double* g,
                                double* trunc);
 
+/* Pair-correlated random force (Sec. II C, Eqs. stochastic_force2,
+ * correlation_matrix, noise_ansatz; the matrix square root that Algorithm 1
+ * applies by a Lanczos iteration per frequency), under the time-scale
+ * separation remarked on after Algorithm 1 (kernels at the current R_n).  With
+ * one separable pair term f(r) g(t) the transformed correlation matrices are
+ * hat K_w = h_w 1 + g_w M, M the pair matrix with blocks f(r_ij) e_ij e_ij^T,
+ * so every sqrt(hat K_w) is one function of M: it is replaced by its
+ * Chebyshev interpolant of `degree` (1..16) on [-lambda, lambda], giving
+ * F_n = sum_k T_k(M / lambda) Z_k with Z_k moving averages of the same white
+ * noise (degree + 1 filters per 64-step block, `degree` neighbour sweeps per
+ * step).  *lambda: in, a bound on the spectrum of M (<= 0 or NULL: 1.25 x
+ * the largest Gershgorin row sum at the current positions); out, the bound
+ * used.  Every step checks the Gershgorin bound and latches GLD_E_NOT_PSD if
+ * a row sum exceeds lambda.  *cheb_err: the largest interpolation error
+ * relative to the largest square root (NULL allowed).  Needs Q = 1 and
+ * Qs = 0; GLD_E_NOT_PSD if h_w < |g_w| lambda for some w (positive
+ * semi-definiteness not guaranteed) unless psd_clamp.  degree = 0 returns to
+ * the self-kernel noise; gld_set_kernels does too.  Such a context cannot join
+ * a batch.  Synchronizes. */
+gld_status gld_set_pair_noise(gld_ctx* ctx, int32_t degree, double* lambda, double* cheb_err);
+
 /* Memory sums in auxiliary-variable form (App. C discusses auxiliary-variable
  * expansions as the alternative to a stored history).  When every kernel
  * given to gld_set_kernels is, for m >= 1, a combination of the modes

@@ -100,6 +100,7 @@ def lib():
             "gld_set_pair_correlation": (i32, [vp, i32, d]),
             "gld_set_memory_modes": (i32, [vp, i32, vp, vp]),
             "gld_set_conservative_table": (i32, [vp, vp, i32, C.c_double]),
+            "gld_set_pair_noise": (i32, [vp, i32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "gld_set_kernels_table": (i32, [vp, vp, vp, i32, C.c_double, i32, i32, C.POINTER(C.c_double)]),
             "gld_separable_terms": (i32, [vp, i32, i32, i32, vp, vp, C.POINTER(C.c_double)]),
             "gld_pair_correlation": (i32, [vp, vp, vp, vp]),
@@ -145,7 +146,7 @@ def exported_symbols() -> list[str]:
             "gld_server_drain", "gld_server_clock", "gld_server_result", "gld_server_stats",
             "gld_server_last_error", "gld_server_destroy", "gld_server_cancel", "gld_set_pair_correlation",
             "gld_pair_correlation", "gld_set_memory_modes", "gld_set_conservative_table",
-            "gld_set_kernels_table", "gld_separable_terms"]
+            "gld_set_kernels_table", "gld_separable_terms", "gld_set_pair_noise"]
 
 
 def _ptr(a: np.ndarray):
@@ -332,6 +333,15 @@ class GLD:
                                                 KDISCRETE if discrete else KCONT, C.byref(tr)))
         self.nacc = 1 + min(int(Q), Kp.shape[0], self.m_max)
         return float(tr.value)
+
+    def set_pair_noise(self, degree: int = 12, lam: float = 0.0):
+        """Pair-correlated random force by a degree-`degree` Chebyshev form of
+        the matrix square root (0: self-kernel noise only).  lam: bound on the
+        pair matrix's spectrum (<= 0: automatic).  Returns (lam used,
+        relative interpolation error)."""
+        lv, err = C.c_double(float(lam)), C.c_double()
+        self._check(lib().gld_set_pair_noise(self._h, int(degree), C.byref(lv), C.byref(err)))
+        return float(lv.value), float(err.value)
 
     def set_pair_correlation(self, nbins: int, r_max: float):
         """Enables C^a(R, t), C^c(R, t) on nbins distance bins of [0, r_max)."""

@@ -184,7 +184,16 @@ gld_status rebuild_cells_and_fc(gld_ctx* c)
 
 cudaError_t launch_noise(gld_ctx* c, cudaStream_t s)
 {
-    return launch_noise_block(c->P, c->B.ctrl, c->W, c->Acp, c->la, c->B.frblock, c->prm.seed, c->d_int2ext, s);
+    const StepParams& P = c->P;
+    if (P.pn_deg <= 0)
+        return launch_noise_block(P, c->B.ctrl, c->W, c->Acp, c->la, c->B.frblock, c->prm.seed, c->d_int2ext, s);
+    // pair-correlated noise: Z_0 .. Z_deg from one white-noise window
+    cudaError_t e = launch_noise_block(P, c->B.ctrl, c->W, c->d_pntaps, c->la, c->B.frblock, c->prm.seed,
+                                       c->d_int2ext, s);
+    for (int k = 1; k <= P.pn_deg && e == cudaSuccess; ++k)
+        e = launch_noise_filter(P, c->B.ctrl, c->W, c->d_pntaps + (size_t)k * c->la,
+                                c->d_zblk + (size_t)(k - 1) * P.T * 3 * P.n_pad, s);
+    return e;
 }
 
 // The memory sums of step n: the history convolution, or its recursive form
@@ -212,6 +221,7 @@ cudaError_t launch_one_step(gld_ctx* c, cudaStream_t s)
 {
     cudaError_t e = launch_memory(c, s);
     if (e != cudaSuccess) return e;
+    if ((e = launch_pair_noise(c->P, c->B, c->d_zblk, c->d_bvec, s)) != cudaSuccess) return e;
     if ((e = launch_pair_force_integrate(c->P, c->B, s)) != cudaSuccess) return e;
     if ((e = launch_rebuild(c->P, c->B, s)) != cudaSuccess) return e;
     if ((e = launch_cforce(c->P, c->B, 1, s)) != cudaSuccess) return e;
@@ -241,7 +251,8 @@ cudaError_t capture_fork_next(gld_ctx* c, cudaStream_t s)
 cudaError_t capture_step_gated(gld_ctx* c, cudaStream_t s, bool overlap)
 {
     if (!overlap) return launch_one_step(c, s);
-    cudaError_t e = launch_pair_force_integrate(c->P, c->B, s);
+    cudaError_t e = launch_pair_noise(c->P, c->B, c->d_zblk, c->d_bvec, s);
+    if (e == cudaSuccess) e = launch_pair_force_integrate(c->P, c->B, s);
     if (e == cudaSuccess) e = capture_fork_next(c, s);
     if (e == cudaSuccess) e = launch_rebuild(c->P, c->B, s);
     if (e == cudaSuccess) e = launch_cforce(c->P, c->B, 1, s);
@@ -254,6 +265,7 @@ cudaError_t capture_step_gated(gld_ctx* c, cudaStream_t s, bool overlap)
 cudaError_t capture_step_conditional(gld_ctx* c, cudaStream_t s, bool overlap)
 {
     cudaError_t e = overlap ? cudaSuccess : launch_memory(c, s);
+    if (e == cudaSuccess) e = launch_pair_noise(c->P, c->B, c->d_zblk, c->d_bvec, s);
     if (e == cudaSuccess) e = launch_pair_force_integrate(c->P, c->B, s);
     if (overlap && e == cudaSuccess) e = capture_fork_next(c, s);
     cudaStreamCaptureStatus cs;
@@ -357,6 +369,10 @@ gld_status ctx_check_err(gld_ctx* c, unsigned err)
     }
     else if (err & kErrTimeout) fail(c, GLD_E_TIMEOUT, "a bounded device wait gave up");
     else if (err & kErrNoise) fail(c, GLD_E_CUDA, "a step ran outside its noise block");
+    else if (err & kErrPnBound) {
+        c->msg = "pair noise: a Gershgorin row sum of the pair matrix exceeded lambda (set a larger one)";
+        if (c->latched == GLD_OK) c->latched = GLD_E_NOT_PSD;
+    }
     return c->latched;
 }
 
@@ -699,11 +715,12 @@ gld_status gld_set_kernels(gld_ctx* c, const double* Ks, int32_t Q, const double
     // FP64 discrete weights of every accumulator (m >= 1), for the recursive form
     c->wts.assign((size_t)P.nacc * P.m_max, 0.0);
     for (int a = 0; a < P.nacc; ++a)
-        for (int m = 1; m < P.m_max; ++m) {
+        for (int m = 0; m < P.m_max; ++m) {
             const double sm = in[(size_t)a * P.m_max + m];  // rows: K^s, g_1..g_Q, gs_1..gs_Qs
-            c->wts[(size_t)a * P.m_max + m] = conv == GLD_KDISCRETE ? sm : dt * sm;
+            c->wts[(size_t)a * P.m_max + m] = conv == GLD_KDISCRETE ? sm : (m == 0 ? 0.5 : 1.0) * dt * sm;
         }
     P.nmodes = 0;  // new kernels: back to the ring convolution until modes are set again
+    P.pn_deg = 0;  // and to the self-kernel noise until the pair noise is set again
     c->modes_dirty = false;
     c->have_kernels = true;
     GLD_TRY(invalidate_noise(c));
@@ -1161,6 +1178,112 @@ gld_status gld_set_kernels_table(gld_ctx* c, const double* Ks, const double* Kp,
         return fail(c, GLD_E_INVAL, "gld_set_kernels_table: invalid table");
     if (trunc) *trunc = tr;
     return gld_set_kernels(c, Ks, std::min(Q, std::min(nr, M)), g.data(), f.data(), nr, dr, nullptr, nullptr, 0, conv);
+}
+
+gld_status gld_set_pair_noise(gld_ctx* c, int32_t degree, double* lambda, double* cheb_err)
+{
+    if (!c) return GLD_E_INVAL;
+    StepParams& P = c->P;
+    if (degree < 0 || degree > kMaxPnDegree) return fail(c, GLD_E_INVAL, "gld_set_pair_noise: degree outside [0, 16]");
+    if (degree > 0 && !c->have_kernels) return fail(c, GLD_E_STATE, "gld_set_pair_noise: set the kernels first");
+    if (degree > 0 && (P.Q != 1 || P.Qs != 0))
+        return fail(c, GLD_E_INVAL, "gld_set_pair_noise: needs exactly one separable pair term and no self-difference term");
+    GLD_TRY(sync_and_check(c));
+    for (float** p : {&c->d_pntaps, &c->d_zblk, &c->d_bvec}) {
+        dfree(c, *p);
+        *p = nullptr;
+    }
+    dfree(c, c->d_rowsum);
+    c->d_rowsum = nullptr;
+    P.pn_deg = 0;
+    invalidate_graph(c);
+    GLD_TRY(invalidate_noise(c));
+    if (degree == 0) return sync_and_check(c);
+    const int M = P.m_max, K = degree;
+    const long long L = 2LL * M - 1;
+    // the bound on the spectrum of the pair matrix: given, or 1.25 x the
+    // largest Gershgorin row sum at the current positions
+    double lam = lambda ? *lambda : 0.0;
+    if (!(lam > 0)) {
+        c->d_rowsum = (unsigned*)dalloc(c, sizeof(unsigned));
+        if (!c->d_rowsum) return fail(c, GLD_E_NOMEM, "gld_set_pair_noise: allocation failed");
+        GLD_CUDA(c, launch_pn_rowsum(P, c->B, c->d_rowsum, c->st));
+        unsigned bits = 0;
+        GLD_CUDA(c, cudaMemcpyAsync(&bits, c->d_rowsum, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));
+        GLD_TRY(sync_and_check(c));
+        float mx;
+        std::memcpy(&mx, &bits, sizeof(float));
+        lam = std::max(1.25 * (double)mx, 1e-6);
+    }
+    if (lambda) *lambda = lam;
+    // transforms (Eq. FT) of the noise targets kT a_m K_m / dt of the self
+    // kernel and of the pair term's time factor, in FP64
+    const double* ws = c->wts.data();
+    const double* wg = c->wts.data() + M;
+    std::vector<double> hh(M), gh(M);
+    double hmax = 0.0, worst = 0.0;
+    for (int w = 0; w < M; ++w) {
+        double a = 2.0 * ws[0], b = 2.0 * wg[0];
+        for (int m = 1; m < M; ++m) {
+            const double cs = std::cos(2.0 * M_PI * (double)(((long long)w * m) % L) / (double)L);
+            a += 2.0 * ws[m] * cs;
+            b += 2.0 * wg[m] * cs;
+        }
+        hh[w] = c->prm.kT / c->prm.dt * a;
+        gh[w] = c->prm.kT / c->prm.dt * b;
+        hmax = std::max(hmax, std::fabs(hh[w]) + std::fabs(gh[w]) * lam);
+        worst = std::min(worst, hh[w] - std::fabs(gh[w]) * lam);
+    }
+    if (worst < -1e-12 * hmax && !c->prm.psd_clamp)
+        return fail(c, GLD_E_NOT_PSD,
+                    "gld_set_pair_noise: h_w - |g_w| lambda < 0 for some frequency: positive semi-definiteness of the "
+                    "correlation matrices is not guaranteed over the spectral bound (psd_clamp clamps)");
+    // Chebyshev interpolation of phi_w(x) = sqrt(h_w + g_w lambda x) on
+    // [-1, 1] at degree K, its error on a fine grid, and the filter taps
+    // a_k[s] = (c_0k + 2 sum_{w>=1} c_wk cos(2 pi w s / L)) / L
+    auto phi = [&](int w, double x) { return std::sqrt(std::max(hh[w] + gh[w] * lam * x, 0.0)); };
+    const int nc = K + 1;
+    std::vector<double> cw((size_t)M * nc);
+    double err = 0.0;
+    for (int w = 0; w < M; ++w) {
+        for (int k = 0; k < nc; ++k) {
+            double acc = 0.0;
+            for (int j = 0; j < nc; ++j) {
+                const double th = M_PI * (j + 0.5) / nc;
+                acc += phi(w, std::cos(th)) * std::cos(k * th);
+            }
+            cw[(size_t)w * nc + k] = (k == 0 ? 1.0 : 2.0) * acc / nc;
+        }
+        for (int t = 0; t <= 256; ++t) {
+            const double x = -1.0 + 2.0 * t / 256.0, th = std::acos(std::min(1.0, std::max(-1.0, x)));
+            double p = 0.0;
+            for (int k = 0; k < nc; ++k) p += cw[(size_t)w * nc + k] * std::cos(k * th);
+            err = std::max(err, std::fabs(p - phi(w, x)));
+        }
+    }
+    double smax = 0.0;  // the largest square root over frequencies and the interval
+    for (int w = 0; w < M; ++w) smax = std::max(smax, std::max(phi(w, 1.0), phi(w, -1.0)));
+    if (cheb_err) *cheb_err = smax > 0 ? err / smax : 0.0;
+    const int H = M - 1;
+    std::vector<float> taps((size_t)nc * c->la, 0.0f);
+    for (int k = 0; k < nc; ++k)
+        for (int sg = 0; sg <= 2 * H; ++sg) {
+            const long long sh = sg - H;
+            double v = cw[k];
+            for (int w = 1; w < M; ++w)
+                v += 2.0 * cw[(size_t)w * nc + k] *
+                     std::cos(2.0 * M_PI * (double)((((long long)w * sh) % L + L) % L) / (double)L);
+            taps[(size_t)k * c->la + sg] = (float)(v / (double)L);
+        }
+    c->d_pntaps = (float*)dalloc(c, sizeof(float) * taps.size());
+    c->d_zblk = (float*)dalloc(c, sizeof(float) * (size_t)K * P.T * 3 * P.n_pad);
+    c->d_bvec = (float*)dalloc(c, sizeof(float) * 3 * 3 * (size_t)P.n_pad);
+    if (!c->d_pntaps || !c->d_zblk || !c->d_bvec) return fail(c, GLD_E_NOMEM, "gld_set_pair_noise: allocation failed");
+    GLD_CUDA(c, cudaMemcpyAsync(c->d_pntaps, taps.data(), sizeof(float) * taps.size(), cudaMemcpyHostToDevice, c->st));
+    P.pn_deg = K;
+    P.pn_lambda = (float)lam;
+    P.pn_inv_lambda = (float)(1.0 / lam);
+    return sync_and_check(c);
 }
 
 gld_status gld_set_memory_modes(gld_ctx* c, int32_t nmodes, const double* rate, const double* omega)
@@ -1655,9 +1778,9 @@ gld_status gld_batch_add(gld_batch* b, gld_ctx* c)
     if (!c->have_kernels) return bfail(b, GLD_E_STATE, "gld_batch_add: the member has no kernels set");
     if (c->st != b->st) return bfail(b, GLD_E_INVAL, "gld_batch_add: the member must use the batch's stream");
     if (c->P.T != kMaxNoiseBlock) return bfail(b, GLD_E_INVAL, "gld_batch_add: the member's noise block must be 64");
-    if (c->P.pc_nbins > 0 || c->P.nmodes > 0)
+    if (c->P.pc_nbins > 0 || c->P.nmodes > 0 || c->P.pn_deg > 0)
         return bfail(b, GLD_E_INVAL,
-                     "gld_batch_add: pair correlations and memory modes are single-context features");
+                     "gld_batch_add: pair correlations, memory modes and pair noise are single-context features");
     if (c->noise_valid && c->host_step != c->noise_end)
         return bfail(b, GLD_E_STATE, "gld_batch_add: the member is inside a noise block (step a multiple of 64)");
     for (gld_ctx* m : b->members)

@@ -57,6 +57,12 @@ struct gld_ctx {
     float2* d_Y = nullptr;
     double* d_mz = nullptr;
     bool modes_dirty = false;
+    // pair-correlated noise: filter taps [deg + 1][la], the blocks Z_1..Z_deg,
+    // three Clenshaw vectors, and a word for the Gershgorin bound
+    float* d_pntaps = nullptr;
+    float* d_zblk = nullptr;
+    float* d_bvec = nullptr;
+    unsigned* d_rowsum = nullptr;
 };
 
 struct gld_batch {

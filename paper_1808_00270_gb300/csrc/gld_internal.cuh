@@ -19,9 +19,10 @@ constexpr int kMaxModes = 8;         // damped-exponential modes of the recursiv
 constexpr int kPcMaxOriginBins = 2048;  // origins x bins of the pair correlations (48 KB of shared sums)
 constexpr int kVacfMaxBlocks = 256;  // particle blocks of the VACF grid at most
 constexpr int kMaxNoiseBlock = 64;  // register-resident outputs per FIR thread
+constexpr int kMaxPnDegree = 16;    // Chebyshev degree of the pair-correlated noise
 
 // Latched device error bits.
-enum : unsigned { kErrNonFinite = 1u, kErrTimeout = 2u, kErrNoise = 4u, kErrNbrOverflow = 8u };
+enum : unsigned { kErrNonFinite = 1u, kErrTimeout = 2u, kErrNoise = 4u, kErrNbrOverflow = 8u, kErrPnBound = 16u };
 
 // Device control block: the step counter lives on the device so that a
 // captured graph of several steps can be replayed without new arguments.
@@ -79,6 +80,10 @@ struct StepParams {
     // distance-binned pair correlations (0 bins: off)
     int pc_nbins;
     float pc_rmax2, pc_inv_dr;  // r_max^2, nbins / r_max
+    // pair-correlated noise: Chebyshev degree (0: self-kernel noise only) and
+    // the bound lambda on the spectrum of the pair matrix, with 1 / lambda
+    int pn_deg;
+    float pn_lambda, pn_inv_lambda;
 };
 
 // ---------------------------------------------------------------- Philox --

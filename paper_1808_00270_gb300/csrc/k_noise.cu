@@ -302,6 +302,20 @@ cudaError_t launch_noise_block(const StepParams& P, Ctrl* ctrl, float* W, const 
     return cudaGetLastError();
 }
 
+cudaError_t launch_noise_filter(const StepParams& P, Ctrl* ctrl, const float* W, const float* taps, float* out,
+                                cudaStream_t st)
+{
+    if (P.T != 64) return cudaErrorInvalidValue;
+    const int ntaps = fir_taps_len(P.H);
+    const int chunk = std::min(ntaps, 768);
+    const size_t smem = sizeof(float) * ((size_t)chunk + (size_t)(64 + chunk) * kFirStreams);
+    cudaError_t e = cudaFuncSetAttribute(fir, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)((3LL * P.n_pad + kFirStreams - 1) / kFirStreams);
+    fir<<<grid, kFirThreads, smem, st>>>(P, ctrl, W, taps, ntaps, chunk, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_batch_noise(const BatchPlan& bp, cudaStream_t st)
 {
     static_assert(kGenThreads == kBatchPartBlock, "white-noise tiles use the particle tiles");

@@ -909,6 +909,75 @@ __global__ void __launch_bounds__(kThreads) b_vacf(const SysDesc* __restrict__ D
     vacf_body(d.P, B.ctrl, B.vel, B.vorig, B.vpartial, B.csum, B.ccnt, B.norig, t.b, d.nb_vacf, blockIdx.y);
 }
 
+// ---- pair-correlated noise (Sec. II C, Algorithm 1's matrix square root) --
+// With one separable pair term the transformed correlation matrix of every
+// frequency w is hat K_w = h_w 1 + g_w M, M the 3N x 3N pair matrix with
+// blocks f(r_ij) e_ij e_ij^T; its square root is the same function of M for
+// all w, so sqrt(hat K_w) ~ sum_k c_wk T_k(M / lambda) (Chebyshev), and after
+// the inverse transform F_n = sum_k T_k(M / lambda) Z_k with Z_k moving
+// averages of W (filters built on the host).  One stage of Clenshaw's
+// recurrence:  out = Z_k + coef (M / lambda) b1 - b2  (coef 2; 1 for the last).
+struct PnStage {
+    const float* z;    // Z_k block [T][3][n_pad]
+    const float* b1;   // b_{k+1}: a Z block (rows) or a vector [3][n_pad]
+    const float* b2;   // b_{k+2} likewise, or null
+    float* out;        // b_k vector, or (last stage) the Z_0 block rows
+    int b1_rows, b2_rows, out_rows, last;
+};
+
+__global__ void __launch_bounds__(kThreads)
+    pn_stage(const StepParams P, Ctrl* __restrict__ ctrl, const float4* __restrict__ pos, const int* __restrict__ nbr,
+             const int* __restrict__ nbr_cnt, const float* __restrict__ ftab, const PnStage S)
+{
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= P.n) return;
+    const long long np = P.n_pad;
+    const long long row = ctrl->step - ctrl->noise_n0;
+    if (row < 0 || row >= P.T) {
+        if (id == 0) atomicOr(&ctrl->err, kErrNoise);
+        return;
+    }
+    const size_t roff = (size_t)row * 3 * np;
+    const float* b1 = S.b1 + (S.b1_rows ? roff : 0);
+    const float* b2 = S.b2 ? S.b2 + (S.b2_rows ? roff : 0) : nullptr;
+    float* out = S.out + (S.out_rows ? roff : 0);
+    const float* z = S.z + roff;
+    const float4 pi = pos[id];
+    float mx = 0.f, my = 0.f, mz = 0.f, rowsum = 0.f;
+    for_each_listed(pi, id, nbr, nbr_cnt[id], P.n_pad, pos, P, [&](int jd, float dx, float dy, float dz, float r2) {
+        const float r = sqrtf(r2);
+        const float inv_r = 1.0f / r;
+        const float ex = dx * inv_r, ey = dy * inv_r, ez = dz * inv_r;
+        const float f = table_at(ftab, P.nr, fmaxf(r, P.rc_min) * P.inv_dr);
+        const float eb = f * dot3(ex, ey, ez, __ldg(b1 + jd), __ldg(b1 + np + jd), __ldg(b1 + 2 * np + jd));
+        mx = fmaf(eb, ex, mx);
+        my = fmaf(eb, ey, my);
+        mz = fmaf(eb, ez, mz);
+        rowsum += fabsf(f);
+    });
+    const float c = (S.last ? 1.0f : 2.0f) * P.pn_inv_lambda;
+    const float ox = fmaf(c, mx, z[id]) - (b2 ? b2[id] : 0.f);
+    const float oy = fmaf(c, my, z[np + id]) - (b2 ? b2[np + id] : 0.f);
+    const float oz = fmaf(c, mz, z[2 * np + id]) - (b2 ? b2[2 * np + id] : 0.f);
+    out[id] = ox;
+    out[np + id] = oy;
+    out[2 * np + id] = oz;
+    if (S.last && rowsum > P.pn_lambda) atomicOr(&ctrl->err, kErrPnBound);
+}
+
+__global__ void __launch_bounds__(kThreads)
+    pn_rowsum(const StepParams P, const float4* __restrict__ pos, const int* __restrict__ nbr,
+              const int* __restrict__ nbr_cnt, const float* __restrict__ ftab, unsigned* __restrict__ out)
+{
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= P.n) return;
+    float rowsum = 0.f;
+    for_each_listed(pos[id], id, nbr, nbr_cnt[id], P.n_pad, pos, P, [&](int, float, float, float, float r2) {
+        rowsum += fabsf(table_at(ftab, P.nr, fmaxf(sqrtf(r2), P.rc_min) * P.inv_dr));
+    });
+    atomicMax(out, __float_as_uint(rowsum));  // non-negative floats order as their bits
+}
+
 }  // namespace
 
 cudaError_t launch_batch_particles(const BatchPlan& bp, cudaStream_t st)
@@ -1021,6 +1090,38 @@ cudaError_t launch_pcorr_flush(const StepParams& P, const ParticleBuffers& B, cu
 {
     if (P.pc_nbins <= 0 || P.vacf_len <= 0) return cudaSuccess;
     pcorr_flush<<<1, kThreads, 0, st>>>(P, B.ctrl, B.pc_step, B.pc_sa, B.pc_sc, B.pc_n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_noise(const StepParams& P, const ParticleBuffers& B, const float* zblk, float* bvec,
+                              cudaStream_t st)
+{
+    const int K = P.pn_deg;
+    if (K <= 0) return cudaSuccess;
+    const size_t blk = (size_t)P.T * 3 * P.n_pad, vec = (size_t)3 * P.n_pad;
+    auto zk = [&](int k) -> const float* { return k == 0 ? B.frblock : zblk + (size_t)(k - 1) * blk; };
+    const unsigned grid = (unsigned)((P.n + kThreads - 1) / kThreads);
+    // b_K = Z_K (read in place); b_k for K > k >= 1 in bvec[k % 3]
+    for (int k = K - 1; k >= 0; --k) {
+        PnStage S{};
+        S.z = zk(k);
+        S.last = k == 0;
+        if (k + 1 == K) { S.b1 = zk(K); S.b1_rows = 1; }
+        else { S.b1 = bvec + (size_t)((k + 1) % 3) * vec; }
+        if (k + 2 == K) { S.b2 = zk(K); S.b2_rows = 1; }
+        else if (k + 2 < K) { S.b2 = bvec + (size_t)((k + 2) % 3) * vec; }
+        if (k == 0) { S.out = B.frblock; S.out_rows = 1; }
+        else { S.out = bvec + (size_t)(k % 3) * vec; }
+        pn_stage<<<grid, kThreads, 0, st>>>(P, B.ctrl, B.pos, B.nbr, B.nbr_cnt, B.ftab, S);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_pn_rowsum(const StepParams& P, const ParticleBuffers& B, unsigned* out, cudaStream_t st)
+{
+    pn_rowsum<<<(P.n + kThreads - 1) / kThreads, kThreads, 0, st>>>(P, B.pos, B.nbr, B.nbr_cnt, B.ftab, out);
     return cudaGetLastError();
 }
 

@@ -71,6 +71,15 @@ cudaError_t launch_vacf_flush(const StepParams& P, const ParticleBuffers& B, cud
 // fold of the last launch's sums before they are read.
 cudaError_t launch_pcorr(const StepParams& P, const ParticleBuffers& B, cudaStream_t st);
 cudaError_t launch_pcorr_flush(const StepParams& P, const ParticleBuffers& B, cudaStream_t st);
+// Pair-correlated noise of step n: F = sum_k T_k(M / lambda) Z_k by Clenshaw's
+// recurrence (pn_deg neighbour sweeps); Z_0 rows are frblock's, Z_k (k >= 1)
+// rows of zblk[k - 1]; bvec holds three vectors [3][n_pad]; F replaces the
+// Z_0 row of step n in frblock.
+cudaError_t launch_pair_noise(const StepParams& P, const ParticleBuffers& B, const float* zblk, float* bvec,
+                              cudaStream_t st);
+// Largest Gershgorin row sum sum_j |f(r_ij)| of the pair matrix at the
+// current positions (as the bit pattern of a non-negative float).
+cudaError_t launch_pn_rowsum(const StepParams& P, const ParticleBuffers& B, unsigned* out, cudaStream_t st);
 // Pairs from a fresh cell traversal of pos_sorted / cell_start.
 cudaError_t launch_pair_list(const StepParams& P, const ParticleBuffers& B, int* pairs,
                              long long cap, unsigned long long* count, cudaStream_t st);
@@ -149,6 +158,10 @@ int fir_taps_len(int H);
 // int2ext maps the internal index to the caller's index, which keys the noise.
 cudaError_t launch_noise_block(const StepParams& P, Ctrl* ctrl, float* W, const float* Acp, int la,
                                float* frblock, unsigned long long seed, const int* int2ext, cudaStream_t st);
+// One more moving-average pass over the white noise already in the ring of
+// the current block (after launch_noise_block): out[t] = sum_s taps W.
+cudaError_t launch_noise_filter(const StepParams& P, Ctrl* ctrl, const float* W, const float* taps, float* out,
+                                cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out, long long n,
                           cudaStream_t st);
 cudaError_t launch_gauss3(uint32_t k0, uint32_t k1, const uint32_t* particle, const long long* time,

@@ -1,0 +1,182 @@
+"""Pair-correlated random force (needs a GPU): the Chebyshev form of the
+matrix square root of Sec. II C against the FP64 oracle, which takes the
+square roots of the dense 3N x 3N transformed correlation matrices
+(Algorithm 1's target) -- one step's F^R, the whole step, the self-kernel
+limit -- plus the fluctuation-dissipation balance it restores (uncorrelated
+velocities of different particles despite the pair friction), bit-identical
+graph forms and the argument checks."""
+import numpy as np
+import pytest
+
+import oracle
+from gld_cases import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def _workload(n=128, seed=31):
+    from paper_1808_00270_gb300 import inputs
+    return inputs.Workload(f"pairnoise_n{n}", n=n, box=inputs.box_for_density(n, 0.1), m_max=200, dt=0.005,
+                           r_c=2.0, tau_s=0.5, tau_p=0.3, steps=1, seed=seed, nr=129)
+
+
+def _kernels(w, strength=0.3):
+    """The workload's kernels with the pair term scaled by `strength` (0.3:
+    h_w >= |g_w| lambda holds for the Gershgorin bound, so the correlation
+    matrices are positive semi-definite for every configuration)."""
+    from paper_1808_00270_gb300 import inputs
+    g, f, dr = inputs.pair_kernel_tables(w)
+    return inputs.self_kernel_samples(w), g, strength * f, dr
+
+
+def _pair(w, strength=0.3, **gkw):
+    from paper_1808_00270_gb300 import GLD, inputs
+    pos, vel = inputs.initial_state(w)
+    ks, g, f, dr = _kernels(w, strength)
+    gpu = GLD(n=w.n, box=w.box, mass=w.mass, kT=w.kT, dt=w.dt, m_max=w.m_max, r_c=w.r_c, A_cons=w.A_cons,
+              seed=w.seed, pos=pos, vel=vel, **gkw)
+    gpu.set_kernels(ks, g=g, f=f, dr=dr)
+    return gpu
+
+
+def _oracle_from(w, gpu, strength=0.3):
+    from paper_1808_00270_gb300 import ARR_FC, ARR_HIST
+    pos, vel = gpu.get_state()
+    s = oracle.System(n=w.n, box=w.box, mass=w.mass, kT=w.kT, dt=w.dt, m_max=w.m_max, r_c=w.r_c,
+                      A_cons=w.A_cons, seed=w.seed, pos=pos, vel=vel)
+    ks, g, f, dr = _kernels(w, strength)
+    assert s.set_kernels(ks, g=g, f=f, dr=dr) == 0
+    s.set_state(step=gpu.step_index, pos=pos, vel=vel, fc=gpu.get(ARR_FC), hist=gpu.get(ARR_HIST))
+    return s
+
+
+@pytest.mark.parametrize("warm", [0, 81])
+def test_pair_noise_matches_dense_square_roots(warm):
+    """F^R of one step (at the start of a noise block and inside one) within
+    2e-6 of the oracle's dense evaluation; degree 12 interpolates to < 1e-9."""
+    from paper_1808_00270_gb300 import ARR_FR
+    w = _workload()
+    gpu = _pair(w)
+    lam, err = gpu.set_pair_noise(12)
+    assert lam > 0 and err < 1e-9, (lam, err)
+    gpu.step(warm)
+    ref = _oracle_from(w, gpu)
+    want = ref.pair_random_force()
+    gpu.step(1)
+    e = rel_l2(gpu.get(ARR_FR), want)
+    print(f"pair noise after {warm} steps: lambda {lam:.3f}, interpolation {err:.1e}, F^R {e:.2e}")
+    assert e < 2e-6
+
+
+def test_pair_noise_step_matches_oracle():
+    """The whole step with the pair noise: F^R, F^D and V_{n+1} within 1e-5."""
+    from paper_1808_00270_gb300 import ARR_FD, ARR_FR
+    w = _workload(seed=32)
+    gpu = _pair(w)
+    gpu.set_pair_noise(12)
+    gpu.step(100)
+    ref = _oracle_from(w, gpu)
+    gpu.step(1)
+    ref.step_pair_noise(1)
+    errs = {"fr": rel_l2(gpu.get(ARR_FR), ref.get(oracle.FR)), "fd": rel_l2(gpu.get(ARR_FD), ref.get(oracle.FD)),
+            "vel": rel_l2(gpu.get_state()[1], ref.get(oracle.VEL))}
+    assert max(errs.values()) < 1e-5, errs
+
+
+def test_zero_pair_kernel_gives_the_self_noise():
+    """f = 0: the pair matrix vanishes and the random force is the
+    self-kernel noise of the same counters."""
+    from paper_1808_00270_gb300 import ARR_FR
+    w = _workload(seed=33)
+    a, b = _pair(w, strength=0.0), _pair(w, strength=0.0)
+    b.set_pair_noise(8)
+    a.step(70)
+    b.step(70)
+    assert rel_l2(b.get(ARR_FR), a.get(ARR_FR)) < 1e-6
+    assert rel_l2(b.get_state()[1], a.get_state()[1]) < 1e-5
+
+
+def test_pair_noise_restores_the_canonical_velocity_distribution():
+    """Fluctuation-dissipation balance with pair friction (Eq.
+    stochastic_force2): in equilibrium the velocities of different particles
+    are uncorrelated, C^c(R, 0) = 0, and <V_x^2> = kT/M.  Ideal gas of 4096
+    particles, K^s = 20 exp(-t / 0.05) (memory short against the motion, the
+    time-scale separation under which the noise is built), K^p = 0.03 K^s
+    within r_c, lambda = 24 (above any neighbour count the run reaches; 0.03 x
+    24 < 1 keeps every correlation matrix positive definite).  With the
+    self-kernel noise alone the pair friction leaves C^c(R, 0) / kT near
+    -0.015 in both distance bins; with the pair noise it is below 0.004 in
+    magnitude (statistical and time-scale-separation residue), and the
+    temperature stays within 1 %."""
+    from paper_1808_00270_gb300 import GLD, inputs
+    w = inputs.WORKLOADS["gld_n4096_m200"]
+    M = 64
+    ks = 20.0 * np.exp(-np.arange(M) * w.dt / 0.05)
+    res = {}
+    for on in (False, True):
+        pos, vel = inputs.initial_state(w)
+        s = GLD(n=w.n, box=w.box, mass=1.0, kT=1.0, dt=w.dt, m_max=M, r_c=w.r_c, A_cons=0.0, seed=w.seed,
+                pos=pos, vel=vel, vacf_len=1, vacf_stride=1, vacf_burnin=2048)
+        s.set_kernels(ks, g=0.03 * ks[None, :], f=np.ones((1, 2)), dr=w.r_c)
+        s.set_pair_correlation(2, w.r_c)
+        if on:
+            lam, err = s.set_pair_noise(16, lam=24.0)
+            assert lam == 24.0 and err < 1e-5
+        s.step(2048 + 32768)
+        c, _ = s.vacf()
+        _, cc, cnt = s.pair_correlation()
+        assert cnt[0].min() > 10 ** 7
+        res[on] = (c[0], cc[0])
+    print("(<V_x^2>, C^c(R, 0)) without / with pair noise:", res)
+    assert np.all(res[False][1] < -0.01), res
+    assert np.all(np.abs(res[True][1]) < 0.004), res
+    assert abs(res[True][0] - 1.0) < 0.01, res
+
+
+def test_pair_noise_graph_forms_bit_identical():
+    from paper_1808_00270_gb300 import ARR_FR
+    w = _workload(seed=34)
+    outs = []
+    for ug in (0, 1, 2):
+        g = _pair(w, use_graphs=ug)
+        g.set_pair_noise(6)
+        g.step(128)
+        outs.append((g.get_state()[0], g.get(ARR_FR)))
+    for p, fr in outs[1:]:
+        assert np.array_equal(p, outs[0][0]) and np.array_equal(fr, outs[0][1])
+
+
+def test_pair_noise_bound_and_arguments():
+    from paper_1808_00270_gb300 import Batch, GLDError
+    from paper_1808_00270_gb300.binding import E_INVAL, E_NOT_PSD
+    w = _workload(seed=35)
+    g = _pair(w)
+    # a bound far below the Gershgorin row sums: the step's check latches
+    g.set_pair_noise(4, lam=1e-3)
+    with pytest.raises(GLDError) as e:
+        g.step(1)
+        g.sync()
+    assert e.value.status == E_NOT_PSD
+    g2 = _pair(w)
+    for deg in (-1, 17):
+        with pytest.raises(GLDError) as e:
+            g2.set_pair_noise(deg)
+        assert e.value.status == E_INVAL
+    # the full-strength pair kernel does not keep h_w >= |g_w| lambda
+    with pytest.raises(GLDError) as e:
+        _pair(w, strength=1.0).set_pair_noise(8)
+    assert e.value.status == E_NOT_PSD
+    g2.set_pair_noise(4)
+    with pytest.raises(GLDError):
+        Batch().add(g2)
+    g2.set_pair_noise(0)
+    Batch().add(g2)
