@@ -57,6 +57,9 @@ def parse():
                          "instead of the history-ring convolution")
     ap.add_argument("--pcorr", type=int, default=0,
                     help="also accumulate the distance-binned pair correlations on this many bins of [0, r_c)")
+    ap.add_argument("--pair-noise", type=int, default=0,
+                    help="pair-correlated random force with a Chebyshev form of this degree (the pair kernel scaled "
+                         "by 0.3 so that positive definiteness is guaranteed over the Gershgorin bound)")
     ap.add_argument("--hist", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--kahan", action="store_true")
     ap.add_argument("--reference-seconds", type=float, default=120.0)
@@ -408,6 +411,9 @@ def main():
         cfg["pair_correlation_bins"] = args.pcorr
     if args.modes:
         cfg["memory"] = "auxiliary-variable modes (O(1) per particle-step in m_max)"
+    if args.pair_noise > 0:
+        f = 0.3 * f
+        cfg["pair_noise"] = {"degree": args.pair_noise, "pair_kernel_scale": 0.3}
     cfg.update({"global_batch": w.n * world, "parallelism": f"replicas{world}",
                 "l2": "inputs larger than L2: 1.26 GB FP32 history ring streamed every step"})
 
@@ -445,6 +451,9 @@ def main():
         sim.set_pair_correlation(args.pcorr, w.r_c)
     if args.modes:
         sim.set_memory_modes(*inputs.memory_modes(w))
+    if args.pair_noise > 0:
+        lam, cheb = sim.set_pair_noise(args.pair_noise)
+        cfg["pair_noise"].update({"lambda": lam, "interpolation_error": cheb})
     T = 64
     # warm-up: at least W steps, then up to a noise-block boundary and one graph replay
     sim.step(max(args.warmup, 3))
@@ -505,12 +514,19 @@ def main():
         launches = K * 8 + 2 * T_blocks
     if args.pcorr > 0:
         launches += K
+    launches += args.pair_noise * (K + T_blocks)  # Clenshaw sweeps per step, filters per block
     e2e = None
     if not args.no_e2e:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         e = GLD(pos=pos, vel=vel, **common)
         e.set_kernels(ks, g=g, f=f, dr=dr)
+        if args.pcorr > 0:
+            e.set_pair_correlation(args.pcorr, w.r_c)
+        if args.modes:
+            e.set_memory_modes(*inputs.memory_modes(w))
+        if args.pair_noise > 0:
+            e.set_pair_noise(args.pair_noise)
         e.step(K)
         cv, _ = e.vacf()
         p_out, v_out = e.get_state()

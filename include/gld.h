@@ -224,7 +224,8 @@ enum {
     GLD_PROF_CFORCE = 4, /* F^C_{n+1} and velocity update                     */
     GLD_PROF_VACF = 5,   /* velocity autocorrelation                          */
     GLD_PROF_PCORR = 6,  /* distance-binned pair correlations (when enabled)  */
-    GLD_PROF_N = 7
+    GLD_PROF_PNOISE = 7, /* Clenshaw sweeps of the pair-correlated noise      */
+    GLD_PROF_N = 8
 };
 gld_status gld_profile_steps(gld_ctx* ctx, int64_t nsteps, double* ms, int64_t* launches);
 

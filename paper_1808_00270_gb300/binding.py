@@ -374,7 +374,8 @@ class GLD:
         self._check(lib().gld_get_coefs(self._h, _ptr(Kd), _ptr(A), _ptr(ab), _ptr(spec)))
         return dict(Kd=Kd, A=A, a=ab[0], b=ab[1], spec_min=spec[0], clamped_mass=spec[1])
 
-    PROF_NAMES = ("noise", "hist_conv", "pair_force_integrate", "cell_build", "cforce", "vacf", "pcorr")
+    PROF_NAMES = ("noise", "hist_conv", "pair_force_integrate", "cell_build", "cforce", "vacf", "pcorr",
+                  "pair_noise")
 
     def profile_steps(self, nsteps: int):
         """Runs nsteps steps with per-kernel CUDA-event timing; returns

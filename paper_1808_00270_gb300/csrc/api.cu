@@ -998,7 +998,8 @@ gld_status gld_profile_steps(gld_ctx* c, int64_t nsteps, double* ms, int64_t* la
     // event pair, so the device times contain no host launch gaps.
     const bool vac = c->P.vacf_len > 0;
     const bool pcor = vac && c->P.pc_nbins > 0;
-    const size_t nk = 1 + (size_t)T * (4 + (vac ? 1 : 0) + (pcor ? 1 : 0));
+    const bool pnoise = c->P.pn_deg > 0;
+    const size_t nk = 1 + (size_t)T * (4 + (vac ? 1 : 0) + (pcor ? 1 : 0) + (pnoise ? 1 : 0));
     std::vector<cudaEvent_t> ev(2 * nk, nullptr);
     std::vector<int> fam(nk);
     gld_status s = GLD_OK;
@@ -1028,6 +1029,7 @@ gld_status gld_profile_steps(gld_ctx* c, int64_t nsteps, double* ms, int64_t* la
             timed(GLD_PROF_HIST, [&] {
                 return launch_memory(c, c->st);
             });
+            if (pnoise) timed(GLD_PROF_PNOISE, [&] { return launch_pair_noise(c->P, c->B, c->d_zblk, c->d_bvec, c->st); });
             timed(GLD_PROF_PAIR, [&] { return launch_pair_force_integrate(c->P, c->B, c->st); });
             timed(GLD_PROF_CELL, [&] { return launch_rebuild(c->P, c->B, c->st); });
             timed(GLD_PROF_CFORCE, [&] { return launch_cforce(c->P, c->B, 1, c->st); });
@@ -1044,7 +1046,11 @@ gld_status gld_profile_steps(gld_ctx* c, int64_t nsteps, double* ms, int64_t* la
                 break;
             }
             acc[fam[q]] += t;
-            cnt[fam[q]] += fam[q] == GLD_PROF_CELL ? 4 : (fam[q] == GLD_PROF_NOISE ? 2 : 1);
+            const int pd = c->P.pn_deg;
+            cnt[fam[q]] += fam[q] == GLD_PROF_CELL     ? 4
+                           : fam[q] == GLD_PROF_NOISE  ? 2 + pd
+                           : fam[q] == GLD_PROF_PNOISE ? pd
+                                                       : 1;
         }
     }
     for (auto& e : ev)
