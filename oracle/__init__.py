@@ -99,6 +99,8 @@ def lib(variant: int = 0):
             L.or_set_paircorr.restype = i32
             L.or_get_paircorr.argtypes = [vp, vp, vp, vp]
             L.or_white_window.argtypes = [vp, i64, vp]
+            L.or_set_perp.argtypes = [vp, vp, vp]
+            L.or_set_perp.restype = i32
             L.or_set_fr_override.argtypes = [vp, vp]
             L.or_set_threads.argtypes = [i32]
             L.or_get_threads.restype = i32
@@ -214,9 +216,18 @@ class System:
         nr = (f.shape[-1] if f is not None else (fs.shape[-1] if fs is not None else 2))
         f = np.zeros((0, nr)) if f is None else _f64(f).reshape(-1, nr)
         fs = np.zeros((0, nr)) if fs is None else _f64(fs).reshape(-1, nr)
-        self._kern = dict(Ks=Ks, g=g, f=f, dr=float(dr), gs=gs, fs=fs, discrete=bool(discrete))
+        self._kern = dict(Ks=Ks, g=g, f=f, dr=float(dr), gs=gs, fs=fs, discrete=bool(discrete), fp=None, fsp=None)
         return int(self._L.or_set_kernels(self._h, _p(Ks), g.shape[0], _p(g), _p(f), nr, dr,
                                           gs.shape[0], _p(gs), _p(fs), int(discrete), int(clamp)))
+
+    def set_perp(self, fp=None, fsp=None) -> int:
+        """Perpendicular radial factors fp[Q, nr], fsp[Qs, nr] of the kernel
+        terms already set (None: zero)."""
+        k = self._kern
+        fp = None if fp is None else _f64(fp).reshape(k["g"].shape[0], -1)
+        fsp = None if fsp is None else _f64(fsp).reshape(k["gs"].shape[0], -1)
+        k["fp"], k["fsp"] = fp, fsp
+        return int(self._L.or_set_perp(self._h, None if fp is None else _p(fp), None if fsp is None else _p(fsp)))
 
     def white_window(self, step=None) -> np.ndarray:
         """W_{i,n+s} for s = -(m_max-1) .. m_max-1: [2 m_max - 1, N, 3]."""
@@ -232,7 +243,7 @@ class System:
         k, G = self._kern, self._geom
         terms = pairnoise.matrix_terms(self.get(POS), G["box"], G["rc"], G["rc_min"], self.m_max, G["dt"],
                                        k["Ks"], k["g"], k["f"], k["dr"], k["gs"], k["fs"], k["discrete"],
-                                       variant=self._variant)
+                                       variant=self._variant, fp=k["fp"], fsp=k["fsp"])
         return pairnoise.random_force(terms, G["kT"], G["dt"], self.m_max, self.white_window(), clamp=clamp,
                                       variant=self._variant)
 

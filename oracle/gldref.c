@@ -62,7 +62,8 @@
  *   6 a_0 = 1 in the noise target           7 V_i in place of V_j at m = 0
  *   8 sign of F^C flipped                  9 auto and cross pair terms swapped
  *  10 pair-kernel table read at the lower row, not interpolated
- *  (11 and 12 are planted in pairnoise.py; this file builds unchanged) */
+ *  (11 and 12 are planted in pairnoise.py; this file builds unchanged)
+ *  13 perpendicular pair terms without the projection 1 - e e^T */
 #ifndef OR_PLANT
 #define OR_PLANT 0
 #endif
@@ -358,6 +359,9 @@ typedef struct {
     int64_t vacf_burnin;
     /* discrete kernels (Eq. k-discrete) */
     double *Kd, *gd, *f, *gsd, *fs;
+    /* perpendicular radial factors of the same terms (Sec. II A: the part
+     * acting through 1 - e e^T), sharing g_q, gs_q and the r grid; NULL: 0 */
+    double *fp, *fsp;
     double *C, *Chat, *A, clamped_mass;
     double a, b;
     /* state at step `step`: R_n, V_n, F^C_n, ring of Delta R_{n-1..n-m_max+1} */
@@ -435,7 +439,7 @@ void or_destroy(or_sys* s)
     if (!s) return;
     double* arrs[] = { s->Kd, s->gd, s->f, s->gsd, s->fs, s->C, s->Chat, s->A, s->pos, s->vel,
                        s->fc, s->fd, s->fr, s->disp, s->hist, s->W, s->vorig, s->csum, s->pc_a, s->pc_c,
-                       s->fct, s->kpt, s->fr_ovr };
+                       s->fct, s->kpt, s->fr_ovr, s->fp, s->fsp };
     for (size_t k = 0; k < sizeof(arrs) / sizeof(arrs[0]); ++k) free(arrs[k]);
     free(s->wtime); free(s->ccnt); free(s->nl.start); free(s->nl.list); free(s->pc_n);
     free(s);
@@ -461,6 +465,8 @@ int or_set_kernels(or_sys* s, const double* Ks, int Q, const double* g, const do
     int M = s->m_max;
     if (Q < 0 || Qs < 0 || Q > 8 || Qs > 8 || (Q + Qs > 0 && (nr < 2 || !(dr > 0)))) return -1;
     free(s->Kd); free(s->gd); free(s->f); free(s->gsd); free(s->fs);
+    free(s->fp); free(s->fsp);
+    s->fp = s->fsp = NULL;
     free(s->C); free(s->Chat); free(s->A);
     s->Q = Q; s->Qs = Qs; s->nr = nr; s->dr = dr; s->clamp = clamp;
     s->Kd = zalloc(M); s->gd = zalloc((size_t)Q * M); s->f = zalloc((size_t)Q * nr);
@@ -479,6 +485,25 @@ int or_set_kernels(or_sys* s, const double* Ks, int Q, const double* g, const do
     int st = or_noise_coefs(M, s->kT, s->dt, s->Kd, clamp, s->C, s->Chat, s->A, &s->clamped_mass);
     s->have_kernels = (st == 0);
     return st;
+}
+
+/* Perpendicular radial factors fp[Q][nr], fsp[Qs][nr] of the terms set by
+ * or_set_kernels (either may be NULL: zero): K^p_m(r) = sum_q g_q[m]
+ * (f_q(r) e e^T + fp_q(r) (1 - e e^T)), likewise dK^s with gs_q, fsp_q. */
+int or_set_perp(or_sys* s, const double* fp, const double* fsp)
+{
+    if (!s->have_kernels) return -7;
+    free(s->fp); free(s->fsp);
+    s->fp = s->fsp = NULL;
+    if (fp && s->Q > 0) {
+        s->fp = zalloc((size_t)s->Q * s->nr);
+        memcpy(s->fp, fp, sizeof(double) * (size_t)s->Q * s->nr);
+    }
+    if (fsp && s->Qs > 0) {
+        s->fsp = zalloc((size_t)s->Qs * s->nr);
+        memcpy(s->fsp, fsp, sizeof(double) * (size_t)s->Qs * s->nr);
+    }
+    return 0;
 }
 
 /* -dU/dr on r = k dr, k < nr (nr = 0: back to the soft repulsion); F^C is
@@ -585,9 +610,16 @@ static void dissipative_force_i(const or_sys* s, int i, const int32_t* nb, int64
         double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         double e[3] = { d[0] / r, d[1] / r, d[2] / r };
         double rt = r < s->rc_min ? s->rc_min : r;
-        double fq[8], fsq[8]; /* radial factors f_q(r), fs_q(r) (Q, Qs <= 8) */
-        for (int q = 0; q < Q; ++q) fq[q] = table_at(s->f + (size_t)q * s->nr, s->nr, s->dr, rt);
-        for (int q = 0; q < Qs; ++q) fsq[q] = table_at(s->fs + (size_t)q * s->nr, s->nr, s->dr, rt);
+        double fq[8], fsq[8], fpq[8], fspq[8]; /* radial factors f_q, fs_q and their
+                                                  perpendicular parts (Q, Qs <= 8) */
+        for (int q = 0; q < Q; ++q) {
+            fq[q] = table_at(s->f + (size_t)q * s->nr, s->nr, s->dr, rt);
+            fpq[q] = s->fp ? table_at(s->fp + (size_t)q * s->nr, s->nr, s->dr, rt) : 0.0;
+        }
+        for (int q = 0; q < Qs; ++q) {
+            fsq[q] = table_at(s->fs + (size_t)q * s->nr, s->nr, s->dr, rt);
+            fspq[q] = s->fsp ? table_at(s->fsp + (size_t)q * s->nr, s->nr, s->dr, rt) : 0.0;
+        }
         /* rows and weight of a general table at rt (the interpolation of table_at) */
         int kr0 = 0, kr1 = 0;
         double kw = 0.0;
@@ -600,11 +632,13 @@ static void dissipative_force_i(const or_sys* s, int i, const int32_t* nb, int64
         for (int m = 0; m < M; ++m) {
             /* K^p_m(r) = sum_q f_q(r) g_q[m] (or the general table),
              * dK^s_m(r) = sum_q fs_q(r) gs_q[m] */
-            double kp = 0.0, kds = 0.0;
+            double kp = 0.0, kds = 0.0, kpp = 0.0, kdsp = 0.0;
             if (s->kp_nr > 0)
                 kp = s->kpt[(size_t)kr0 * M + m] * (1.0 - kw) + s->kpt[(size_t)kr1 * M + m] * kw;
             for (int q = 0; q < Q; ++q) kp += fq[q] * s->gd[(size_t)q * M + m];
             for (int q = 0; q < Qs; ++q) kds += fsq[q] * s->gsd[(size_t)q * M + m];
+            for (int q = 0; q < Q; ++q) kpp += fpq[q] * s->gd[(size_t)q * M + m];
+            for (int q = 0; q < Qs; ++q) kdsp += fspq[q] * s->gsd[(size_t)q * M + m];
             const double *xj, *xi;
             double scale;
             if (m == 0) { xj = s->vel + 3 * (OR_PLANT == 7 ? i : j); xi = s->vel + 3 * i; scale = 1.0; }
@@ -615,7 +649,12 @@ static void dissipative_force_i(const or_sys* s, int i, const int32_t* nb, int64
             if (m > 0 && OR_PLANT == 3) kp = -kp;
             double pj = e[0] * xj[0] + e[1] * xj[1] + e[2] * xj[2];
             double pi = e[0] * xi[0] + e[1] * xi[1] + e[2] * xi[2];
-            for (int c = 0; c < 3; ++c) F[c] -= scale * (kp * pj + kds * pi) * e[c];
+            /* parallel parts through e e^T, perpendicular ones through 1 - e e^T */
+            for (int c = 0; c < 3; ++c) {
+                const double xjp = OR_PLANT == 13 ? xj[c] : xj[c] - pj * e[c];
+                const double xip = OR_PLANT == 13 ? xi[c] : xi[c] - pi * e[c];
+                F[c] -= scale * ((kp * pj + kds * pi) * e[c] + kpp * xjp + kdsp * xip);
+            }
         }
     }
     for (int m = 1; m < M; ++m) {

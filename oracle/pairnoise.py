@@ -9,9 +9,10 @@ frequency, by its plain definition with dense matrices:
     the right-hand side of Eq. stochastic_force2 under the time-scale
     separation remarked on after Algorithm 1 (all kernels at the current
     configuration R_n):  K_m = kT a_m / dt * ( K^s_m 1
-        + blocks (i, j != i): K^p_m(R_ij) e_ij e_ij^T
-        + blocks (i, i):      sum_k dK^s_m(R_ik) e_ik e_ik^T ),
-    a_0 = 2, a_m = 1 (Eq. FDT_discretized), parallel components only;
+        + blocks (i, j != i): K^p_m(R_ij)
+        + blocks (i, i):      sum_k dK^s_m(R_ik) ),
+    each pair tensor K(R) = K_par(R) e e^T + K_perp(R) (1 - e e^T) (Sec. II A),
+    a_0 = 2, a_m = 1 (Eq. FDT_discretized);
   * their transform over the 2 m_max - 1 points of Eq. FT,
     hat K_w = K_0 + 2 sum_{m>=1} K_m cos(2 pi w m / (2 m_max - 1));
   * hat F_w = sqrt(hat K_w) hat W_w with the symmetric square root taken from
@@ -64,19 +65,22 @@ def pair_geometry(pos, box: float, rc: float):
 
 
 def matrix_terms(pos, box, rc, rc_min, m_max, dt, Ks, g=None, f=None, dr=1.0, gs=None, fs=None,
-                 discrete=False, variant=0):
+                 discrete=False, variant=0, fp=None, fsp=None):
     """The memory kernel as a list of (time weights w[m], 3N x 3N matrix X),
-    K_m = sum w[m] X (before the factor kT a_m / dt)."""
+    K_m = sum w[m] X (before the factor kT a_m / dt).  Each pair block is
+    f(r) e e^T + fp(r) (1 - e e^T) (perpendicular factors fp, fsp: None = 0)."""
     n = np.asarray(pos).shape[0]
     terms = [(discretize(Ks, dt, discrete), np.eye(3 * n))]
     i, j, r, e = pair_geometry(pos, box, rc)
     rt = np.maximum(r, rc_min)
     ee = e[:, :, None] * e[:, None, :]
+    perp = np.eye(3)[None] - ee
     g = np.zeros((0, m_max)) if g is None else np.reshape(g, (-1, m_max))
     f = np.zeros((0, 2)) if f is None or g.shape[0] == 0 else np.reshape(f, (g.shape[0], -1))
-    for gq, fq in zip(g, f):
+    fp = np.zeros_like(f) if fp is None else np.reshape(fp, f.shape)
+    for gq, fq, fpq in zip(g, f, fp):
         X = np.zeros((n, 3, n, 3))
-        w = radial(fq, dr, rt)[:, None, None] * ee
+        w = radial(fq, dr, rt)[:, None, None] * ee + radial(fpq, dr, rt)[:, None, None] * perp
         if variant == 11:
             w = -w
         X[i, :, j, :] = w
@@ -84,9 +88,11 @@ def matrix_terms(pos, box, rc, rc_min, m_max, dt, Ks, g=None, f=None, dr=1.0, gs
         terms.append((discretize(gq, dt, discrete), X.reshape(3 * n, 3 * n)))
     if gs is not None and fs is not None and np.size(gs) > 0:
         gs = np.reshape(gs, (-1, m_max))
-        for gq, fq in zip(gs, np.reshape(fs, (gs.shape[0], -1))):
+        fs = np.reshape(fs, (gs.shape[0], -1))
+        fsp = np.zeros_like(fs) if fsp is None else np.reshape(fsp, fs.shape)
+        for gq, fq, fpq in zip(gs, fs, fsp):
             X = np.zeros((n, 3, n, 3))
-            w = radial(fq, dr, rt)[:, None, None] * ee
+            w = radial(fq, dr, rt)[:, None, None] * ee + radial(fpq, dr, rt)[:, None, None] * perp
             np.add.at(X, (i, slice(None), i, slice(None)), w)
             np.add.at(X, (j, slice(None), j, slice(None)), w)
             terms.append((discretize(gq, dt, discrete), X.reshape(3 * n, 3 * n)))

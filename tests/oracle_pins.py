@@ -383,6 +383,86 @@ def _run_pair(dt, Ks0, Kp0, Kds0, tau, T, variant):
     return float(np.max(np.abs(vp - cp))), float(np.max(np.abs(vm - cm)))
 
 
+def _run_pair_oblique(dt, Ks0, K_par, K_perp, Kds_par, Kds_perp, tau, T, variant):
+    """Two particles on the x axis, V_1(0) = (1, 0.7, 0), V_2(0) = (0, 0.7, 0),
+    kT = 0, flat parallel and perpendicular kernels (the relative motion stays
+    on the x axis, so e_12 is fixed): the largest deviation of V_+-,x and
+    V_+,y from their closed forms, and of V_-,y and V_z from zero."""
+    m_max = int(round(2.0 / dt))
+    s = oracle.System(n=2, box=100.0, mass=1.0, kT=0.0, dt=dt, m_max=m_max, r_c=10.0,
+                      pos=[[50, 50, 50], [53, 50, 50]], vel=[[1.0, 0.7, 0], [0, 0.7, 0]], variant=variant)
+    t = np.arange(m_max) * dt
+    g = np.exp(-t / tau)[None]
+    one = np.ones((1, 64))
+    if s.set_kernels(Ks0 * np.exp(-t / tau), g=g, f=K_par * one, dr=10.0 / 63, gs=g, fs=Kds_par * one) != 0:
+        return np.inf
+    s.set_perp(K_perp * one, Kds_perp * one)
+    steps = int(round(T / dt))
+    V = [s.get(oracle.VEL)]
+    for _ in range(steps):
+        s.step(1)
+        V.append(s.get(oracle.VEL))
+    V = np.array(V)
+    tt = np.arange(steps + 1) * dt
+    worst = max(float(np.abs(V[:, :, 2]).max()), float(np.abs(V[:, 0, 1] - V[:, 1, 1]).max()))
+    for c, amp, sign, kp, kd in ((0, 1.0, 1.0, K_par, Kds_par), (0, 1.0, -1.0, K_par, Kds_par),
+                                 (1, 1.4, 1.0, K_perp, Kds_perp)):
+        got = (V[:, 0, c] + sign * V[:, 1, c]) / math.sqrt(2)
+        want = amp * closed_form_vacf(tt, Ks0 + kd + sign * kp, tau) / math.sqrt(2)
+        worst = max(worst, float(np.abs(got - want).max()))
+    return worst
+
+
+def _perp_mirror_forces(variant, a, b, c, d, along):
+    """F^D of the coming step for two particles on the x axis with velocities
+    and a random displacement history all along `along`, parallel factors
+    (a, c), perpendicular ones (b, d) for the pair and self-difference terms."""
+    rng = np.random.default_rng(12)
+    M, dt = 8, 0.01
+    vx = rng.normal(size=2)
+    hx = rng.normal(0, 0.01, size=(M - 1, 2))
+    vel = np.zeros((2, 3))
+    hist = np.zeros((M - 1, 2, 3))
+    vel[:, along] = vx
+    hist[:, :, along] = hx
+    s = oracle.System(n=2, box=20.0, mass=1.0, kT=0.0, dt=dt, m_max=M, r_c=5.0,
+                      pos=[[8.0, 9.0, 10.0], [10.5, 9.0, 10.0]], vel=vel, variant=variant)
+    t = np.arange(M) * dt
+    g, gs = np.exp(-t / 0.05)[None], np.cos(20 * t)[None]
+    r = np.linspace(0, 5, 11)[None]
+    s.set_kernels(10 * np.exp(-t / 0.05), g=g, f=a(r), dr=0.5, gs=gs, fs=c(r))
+    s.set_perp(b(r), d(r))
+    s.set_state(step=M + 3, pos=s.get(oracle.POS), vel=vel, hist=hist)
+    fd, fr = np.zeros((2, 3)), np.zeros((2, 3))
+    idx = np.arange(2, dtype=np.int32)
+    s._L.or_forces_subset(s._h, oracle._p(idx), 2, oracle._p(fd), oracle._p(fr))
+    return fd
+
+
+def pin_perpendicular_decoupling(variant=0):
+    """Parallel and perpendicular pair kernels (Sec. II A).  (i) Two particles
+    on the x axis: the x components of V_+- follow the closed form with
+    K^s + dK^s_par +- K^p_par, the common y motion the one with
+    K^s + dK^s_perp + K^p_perp, at second order in dt.  (ii) Mirror
+    symmetry: with velocities and history along e the force from factors
+    (par a, perp b) equals, turned by 90 degrees, the force with velocities
+    and history across e and the factors exchanged (par b, perp a) -- so the
+    perpendicular terms reproduce the closed-form-pinned parallel ones,
+    including which particle's motion each term reads."""
+    errs = [_run_pair_oblique(dt, 20.0, 8.0, 5.0, 3.0, 2.0, 0.1, 1.0, variant) for dt in (0.01, 0.005, 0.0025)]
+    ok = errs[2] < 5e-5 and 3.5 < errs[1] / errs[2] < 4.5
+    fa = lambda r: 2.0 * (1 - r / 5.0) ** 2
+    fb = lambda r: 0.7 - 0.1 * r
+    fc = lambda r: 0.5 * np.exp(-r)
+    fdd = lambda r: 0.3 + 0.0 * r
+    A = _perp_mirror_forces(variant, fa, fb, fc, fdd, 0)
+    B = _perp_mirror_forces(variant, fb, fa, fdd, fc, 1)
+    mirror = float(np.abs(A[:, 0] - B[:, 1]).max() / np.abs(A[:, 0]).max())
+    rest = float(max(np.abs(A[:, 1:]).max(), np.abs(B[:, [0, 2]]).max()))
+    ok = ok and mirror < 1e-12 and rest < 1e-12
+    return ok, f"closed-form errors {errs}, mirror {mirror:.1e}, off-axis {rest:.1e}"
+
+
 def pin_pair_decoupling(variant=0):
     """Two particles on a line with flat parallel pair kernels (Sec. III A,
     Eqs. gle1-gle2): V_+- = (V_1 +- V_2)/sqrt 2 obey single-particle GLEs with
@@ -680,4 +760,5 @@ ALL = {
     "pair_noise_self_limit": pin_pair_noise_self_limit,
     "pair_noise_two_particles": pin_pair_noise_two_particles,
     "pair_noise_covariance": pin_pair_noise_covariance,
+    "perpendicular_decoupling": pin_perpendicular_decoupling,
 }

@@ -19,6 +19,7 @@ PLANTS = {
     10: "pair-kernel table not interpolated",
     11: "pair blocks of the noise correlation matrix with the wrong sign",
     12: "pair-noise inverse transform scaled by 1/m_max",
+    13: "perpendicular pair terms without the projection 1 - e e^T",
 }
 
 
