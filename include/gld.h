@@ -249,12 +249,21 @@ gld_status gld_set_kernels_table(gld_ctx* ctx, const double* Ks, const double* K
 gld_status gld_separable_terms(const double* table, int32_t nr, int32_t m, int32_t Q, double* f, double* g,
                                double* trunc);
 
+/* Perpendicular components of the pair and self-difference kernels (Sec.
+ * II A: each two-particle tensor is K_par(r) e e^T + K_perp(r) (1 - e e^T)):
+ * fp[Q][nr] and fsp[Qs][nr] are the perpendicular radial factors of the terms
+ * set by gld_set_kernels, sharing their time factors g_q, gs_q and r grid
+ * (NULL or all zero: none; gld_set_kernels clears them).  They enter F^D and,
+ * when set, the pair-correlated noise.  Synchronizes. */
+gld_status gld_set_perpendicular(gld_ctx* ctx, const double* fp, const double* fsp);
+
 /* Pair-correlated random force (Sec. II C, Eqs. stochastic_force2,
  * correlation_matrix, noise_ansatz; the matrix square root that Algorithm 1
  * applies by a Lanczos iteration per frequency), under the time-scale
  * separation remarked on after Algorithm 1 (kernels at the current R_n).  With
  * one separable pair term f(r) g(t) the transformed correlation matrices are
- * hat K_w = h_w 1 + g_w M, M the pair matrix with blocks f(r_ij) e_ij e_ij^T,
+ * hat K_w = h_w 1 + g_w M, M the pair matrix with blocks f(r_ij) e_ij e_ij^T
+ * (+ fp(r_ij) (1 - e_ij e_ij^T) with perpendicular factors),
  * so every sqrt(hat K_w) is one function of M: it is replaced by its
  * Chebyshev interpolant of `degree` (1..16) on [-lambda, lambda], giving
  * F_n = sum_k T_k(M / lambda) Z_k with Z_k moving averages of the same white

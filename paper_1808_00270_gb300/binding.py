@@ -101,6 +101,7 @@ def lib():
             "gld_set_memory_modes": (i32, [vp, i32, vp, vp]),
             "gld_set_conservative_table": (i32, [vp, vp, i32, C.c_double]),
             "gld_set_pair_noise": (i32, [vp, i32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+            "gld_set_perpendicular": (i32, [vp, vp, vp]),
             "gld_set_kernels_table": (i32, [vp, vp, vp, i32, C.c_double, i32, i32, C.POINTER(C.c_double)]),
             "gld_separable_terms": (i32, [vp, i32, i32, i32, vp, vp, C.POINTER(C.c_double)]),
             "gld_pair_correlation": (i32, [vp, vp, vp, vp]),
@@ -146,7 +147,8 @@ def exported_symbols() -> list[str]:
             "gld_server_drain", "gld_server_clock", "gld_server_result", "gld_server_stats",
             "gld_server_last_error", "gld_server_destroy", "gld_server_cancel", "gld_set_pair_correlation",
             "gld_pair_correlation", "gld_set_memory_modes", "gld_set_conservative_table",
-            "gld_set_kernels_table", "gld_separable_terms", "gld_set_pair_noise"]
+            "gld_set_kernels_table", "gld_separable_terms", "gld_set_pair_noise",
+            "gld_set_perpendicular"]
 
 
 def _ptr(a: np.ndarray):
@@ -333,6 +335,16 @@ class GLD:
                                                 KDISCRETE if discrete else KCONT, C.byref(tr)))
         self.nacc = 1 + min(int(Q), Kp.shape[0], self.m_max)
         return float(tr.value)
+
+    def set_perpendicular(self, fp=None, fs=None):
+        """Perpendicular radial factors fp[Q, nr], fs[Qs, nr] of the kernel
+        terms already set (acting through 1 - e e^T); None: zero."""
+        fp = None if fp is None else _f64(fp).ravel()
+        fs = None if fs is None else _f64(fs).ravel()
+        keep = (fp, fs)
+        self._check(lib().gld_set_perpendicular(self._h, None if fp is None else _ptr(fp),
+                                                None if fs is None else _ptr(fs)))
+        del keep
 
     def set_pair_noise(self, degree: int = 12, lam: float = 0.0):
         """Pair-correlated random force by a degree-`degree` Chebyshev form of

@@ -721,6 +721,7 @@ gld_status gld_set_kernels(gld_ctx* c, const double* Ks, int32_t Q, const double
         }
     P.nmodes = 0;  // new kernels: back to the ring convolution until modes are set again
     P.pn_deg = 0;  // and to the self-kernel noise until the pair noise is set again
+    P.perp = 0;    // and to parallel components only
     c->modes_dirty = false;
     c->have_kernels = true;
     GLD_TRY(invalidate_noise(c));
@@ -1186,6 +1187,40 @@ gld_status gld_set_kernels_table(gld_ctx* c, const double* Ks, const double* Kp,
     return gld_set_kernels(c, Ks, std::min(Q, std::min(nr, M)), g.data(), f.data(), nr, dr, nullptr, nullptr, 0, conv);
 }
 
+gld_status gld_set_perpendicular(gld_ctx* c, const double* fp, const double* fsp)
+{
+    if (!c) return GLD_E_INVAL;
+    if (!c->have_kernels) return fail(c, GLD_E_STATE, "gld_set_perpendicular: set the kernels first");
+    StepParams& P = c->P;
+    GLD_TRY(sync_and_check(c));
+    const int nt = P.Q + P.Qs;
+    std::vector<float> tab((size_t)std::max(nt, 1) * P.nr, 0.f);
+    bool any = false;
+    for (int q = 0; q < P.Q && fp; ++q)
+        for (int k = 0; k < P.nr; ++k) {
+            tab[(size_t)q * P.nr + k] = (float)fp[(size_t)q * P.nr + k];
+            any = any || fp[(size_t)q * P.nr + k] != 0.0;
+        }
+    for (int q = 0; q < P.Qs && fsp; ++q)
+        for (int k = 0; k < P.nr; ++k) {
+            tab[(size_t)(P.Q + q) * P.nr + k] = (float)fsp[(size_t)q * P.nr + k];
+            any = any || fsp[(size_t)q * P.nr + k] != 0.0;
+        }
+    dfree(c, c->fptab);
+    c->fptab = nullptr;
+    c->B.fptab = nullptr;
+    P.perp = 0;
+    if (any) {
+        c->fptab = (float*)dalloc(c, sizeof(float) * tab.size());
+        if (!c->fptab) return fail(c, GLD_E_NOMEM, "gld_set_perpendicular: allocation failed");
+        GLD_CUDA(c, cudaMemcpyAsync(c->fptab, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice, c->st));
+        c->B.fptab = c->fptab;
+        P.perp = 1;
+    }
+    invalidate_graph(c);
+    return sync_and_check(c);
+}
+
 gld_status gld_set_pair_noise(gld_ctx* c, int32_t degree, double* lambda, double* cheb_err)
 {
     if (!c) return GLD_E_INVAL;
@@ -1595,7 +1630,7 @@ gld_status batch_plan(gld_batch* b, int schedule)
     BatchPlan& P = b->plan;
     P = BatchPlan{};
     P.pair_fast = 1;
-    for (const gld_ctx* c : ms) P.pair_fast &= (c->P.Q == 1 && c->P.Qs == 0) ? 1 : 0;
+    for (const gld_ctx* c : ms) P.pair_fast &= (c->P.Q == 1 && c->P.Qs == 0 && !c->P.perp) ? 1 : 0;
     const int pair_per_block = P.pair_fast ? kBatchPairBlock / kBatchPairLanes : kBatchPairBlock;
     for (size_t m = 0; m < ms.size(); ++m) {
         gld_ctx* c = ms[m];

@@ -34,6 +34,7 @@ struct gld_ctx {
     float* coef = nullptr;
     float* g0 = nullptr;
     float* ftab = nullptr;
+    float* fptab = nullptr;
     double *d_Kd = nullptr, *d_C = nullptr, *d_Chat = nullptr, *d_A = nullptr, *d_scal = nullptr, *d_in = nullptr;
     int* d_status = nullptr;
     size_t ring_elem = 4;

@@ -84,6 +84,7 @@ __device__ __forceinline__ void pair_force_integrate_body(const StepParams& P, C
                          const int* __restrict__ perm, const int* __restrict__ nbr, const int* __restrict__ nbr_cnt,
                          const float4* __restrict__ vel, const float4* __restrict__ fc, const float* __restrict__ conv,
                          const float* __restrict__ frblock, const float* __restrict__ ftab,
+                         const float* __restrict__ fptab,
                          const float* __restrict__ g0, void* __restrict__ ring, float4* __restrict__ pos_next,
                          float4* __restrict__ vhalf, float4* __restrict__ fd_out, float4* __restrict__ disp,
                          const float4* __restrict__ disp_build, int blk, int nblk)
@@ -203,6 +204,30 @@ __device__ __forceinline__ void pair_force_integrate_body(const StepParams& P, C
             }
             f0x = fmaf(-inst, ex, f0x); f0y = fmaf(-inst, ey, f0y); f0z = fmaf(-inst, ez, f0z);
             fhx = fmaf(-hist, ex, fhx); fhy = fmaf(-hist, ey, fhy); fhz = fmaf(-hist, ez, fhz);
+            if (P.perp) {
+                // perpendicular parts act through 1 - e e^T: on X they give
+                // fp (X - (e.X) e), X = V_j, P_j (pair) or V_i, P_i (self-difference)
+                float cvj = 0.f, cvi = 0.f, hpe = 0.f, hpx = 0.f, hpy = 0.f, hpz = 0.f;
+                for (int q = 0; q < P.Q; ++q) {
+                    const float fp = table_at(fptab + q * P.nr, P.nr, x);
+                    const float* pj = conv + (size_t)(1 + q) * 3 * np + jd;
+                    const float px = __ldg(pj), py = __ldg(pj + np), pz = __ldg(pj + 2 * np);
+                    cvj = fmaf(fp, __ldg(g0 + q), cvj);
+                    hpe = fmaf(fp, dot3(ex, ey, ez, px, py, pz), hpe);
+                    hpx = fmaf(fp, px, hpx); hpy = fmaf(fp, py, hpy); hpz = fmaf(fp, pz, hpz);
+                }
+                for (int q = 0; q < P.Qs; ++q) {
+                    const float fp = table_at(fptab + (P.Q + q) * P.nr, P.nr, x);
+                    cvi = fmaf(fp, __ldg(g0 + P.Q + q), cvi);
+                    hpe = fmaf(fp, dot3(ex, ey, ez, ps[q][0], ps[q][1], ps[q][2]), hpe);
+                    hpx = fmaf(fp, ps[q][0], hpx); hpy = fmaf(fp, ps[q][1], hpy); hpz = fmaf(fp, ps[q][2], hpz);
+                }
+                const float ipe = fmaf(cvj, evj, cvi * evi);
+                f0x += fmaf(ipe, ex, -fmaf(cvj, vj.x, cvi * vi.x));
+                f0y += fmaf(ipe, ey, -fmaf(cvj, vj.y, cvi * vi.y));
+                f0z += fmaf(ipe, ez, -fmaf(cvj, vj.z, cvi * vi.z));
+                fhx += fmaf(hpe, ex, -hpx); fhy += fmaf(hpe, ey, -hpy); fhz += fmaf(hpe, ez, -hpz);
+            }
         });
     }
     // F^D = -sum_j (K^p_0 V_j + dK^s_0 V_i) - (1/dt) (S_i + sum_j ...)
@@ -262,11 +287,12 @@ __global__ void __launch_bounds__(kPairThreads) pair_force_integrate(const StepP
                          const int* __restrict__ perm, const int* __restrict__ nbr, const int* __restrict__ nbr_cnt,
                          const float4* __restrict__ vel, const float4* __restrict__ fc, const float* __restrict__ conv,
                          const float* __restrict__ frblock, const float* __restrict__ ftab,
+                         const float* __restrict__ fptab,
                          const float* __restrict__ g0, void* __restrict__ ring, float4* __restrict__ pos_next,
                          float4* __restrict__ vhalf, float4* __restrict__ fd_out, float4* __restrict__ disp,
                          const float4* __restrict__ disp_build)
 {
-    pair_force_integrate_body<FAST>(P, ctrl, pos, perm, nbr, nbr_cnt, vel, fc, conv, frblock, ftab, g0, ring, pos_next, vhalf, fd_out, disp, disp_build, blockIdx.x, gridDim.x);
+    pair_force_integrate_body<FAST>(P, ctrl, pos, perm, nbr, nbr_cnt, vel, fc, conv, frblock, ftab, fptab, g0, ring, pos_next, vhalf, fd_out, disp, disp_build, blockIdx.x, gridDim.x);
 }
 
 // ---- cell list --------------------------------------------------------------
@@ -854,7 +880,7 @@ __global__ void __launch_bounds__(kPairThreads) b_pair(const SysDesc* __restrict
     const SysDesc& d = D[t.m];
     const ParticleBuffers& B = d.B;
     pair_force_integrate_body<FAST>(d.P, B.ctrl, B.pos, B.perm, B.nbr, B.nbr_cnt, B.vel, B.fc, B.conv, B.frblock, B.ftab,
-                              B.g0, B.ring, B.pos_next, B.vhalf, B.fd, B.disp, B.disp_build, t.b, d.nb_pair);
+                              B.fptab, B.g0, B.ring, B.pos_next, B.vhalf, B.fd, B.disp, B.disp_build, t.b, d.nb_pair);
 }
 
 __global__ void b_cell_assign(const SysDesc* __restrict__ D, const Tile* __restrict__ tiles)
@@ -927,7 +953,8 @@ struct PnStage {
 
 __global__ void __launch_bounds__(kThreads)
     pn_stage(const StepParams P, Ctrl* __restrict__ ctrl, const float4* __restrict__ pos, const int* __restrict__ nbr,
-             const int* __restrict__ nbr_cnt, const float* __restrict__ ftab, const PnStage S)
+             const int* __restrict__ nbr_cnt, const float* __restrict__ ftab, const float* __restrict__ fptab,
+             const PnStage S)
 {
     const int id = blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= P.n) return;
@@ -948,12 +975,15 @@ __global__ void __launch_bounds__(kThreads)
         const float r = sqrtf(r2);
         const float inv_r = 1.0f / r;
         const float ex = dx * inv_r, ey = dy * inv_r, ez = dz * inv_r;
-        const float f = table_at(ftab, P.nr, fmaxf(r, P.rc_min) * P.inv_dr);
-        const float eb = f * dot3(ex, ey, ez, __ldg(b1 + jd), __ldg(b1 + np + jd), __ldg(b1 + 2 * np + jd));
-        mx = fmaf(eb, ex, mx);
-        my = fmaf(eb, ey, my);
-        mz = fmaf(eb, ez, mz);
-        rowsum += fabsf(f);
+        const float xr = fmaxf(r, P.rc_min) * P.inv_dr;
+        const float f = table_at(ftab, P.nr, xr);
+        const float fp = P.perp ? table_at(fptab, P.nr, xr) : 0.f;  // block f e e^T + fp (1 - e e^T)
+        const float bx = __ldg(b1 + jd), by = __ldg(b1 + np + jd), bz = __ldg(b1 + 2 * np + jd);
+        const float eb = (f - fp) * dot3(ex, ey, ez, bx, by, bz);
+        mx = fmaf(eb, ex, fmaf(fp, bx, mx));
+        my = fmaf(eb, ey, fmaf(fp, by, my));
+        mz = fmaf(eb, ez, fmaf(fp, bz, mz));
+        rowsum += fmaxf(fabsf(f), fabsf(fp));  // the block's spectral norm
     });
     const float c = (S.last ? 1.0f : 2.0f) * P.pn_inv_lambda;
     const float ox = fmaf(c, mx, z[id]) - (b2 ? b2[id] : 0.f);
@@ -967,13 +997,15 @@ __global__ void __launch_bounds__(kThreads)
 
 __global__ void __launch_bounds__(kThreads)
     pn_rowsum(const StepParams P, const float4* __restrict__ pos, const int* __restrict__ nbr,
-              const int* __restrict__ nbr_cnt, const float* __restrict__ ftab, unsigned* __restrict__ out)
+              const int* __restrict__ nbr_cnt, const float* __restrict__ ftab, const float* __restrict__ fptab,
+              unsigned* __restrict__ out)
 {
     const int id = blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= P.n) return;
     float rowsum = 0.f;
     for_each_listed(pos[id], id, nbr, nbr_cnt[id], P.n_pad, pos, P, [&](int, float, float, float, float r2) {
-        rowsum += fabsf(table_at(ftab, P.nr, fmaxf(sqrtf(r2), P.rc_min) * P.inv_dr));
+        const float xr = fmaxf(sqrtf(r2), P.rc_min) * P.inv_dr;
+        rowsum += fmaxf(fabsf(table_at(ftab, P.nr, xr)), P.perp ? fabsf(table_at(fptab, P.nr, xr)) : 0.f);
     });
     atomicMax(out, __float_as_uint(rowsum));  // non-negative floats order as their bits
 }
@@ -1013,11 +1045,12 @@ cudaError_t launch_delay(unsigned long long ns, cudaStream_t st)
 cudaError_t launch_pair_force_integrate(const StepParams& P, const ParticleBuffers& B, cudaStream_t st)
 {
     const unsigned grid = (unsigned)((P.n + kPairThreads - 1) / kPairThreads);
-    const bool fast = P.Q == 1 && P.Qs == 0;
+    const bool fast = P.Q == 1 && P.Qs == 0 && !P.perp;
     auto k = fast ? pair_force_integrate<true> : pair_force_integrate<false>;
     const unsigned pgrid = fast ? (unsigned)(((long long)P.n * kPairLanes + kPairThreads - 1) / kPairThreads) : grid;
     k<<<pgrid, kPairThreads, 0, st>>>(P, B.ctrl, B.pos, B.perm, B.nbr, B.nbr_cnt, B.vel, B.fc,
-                                                        B.conv, B.frblock, B.ftab, B.g0, B.ring, B.pos_next,
+                                                        B.conv, B.frblock, B.ftab, B.fptab, B.g0, B.ring,
+                                                        B.pos_next,
                                                         B.vhalf, B.fd, B.disp, B.disp_build);
     return cudaGetLastError();
 }
@@ -1112,7 +1145,7 @@ cudaError_t launch_pair_noise(const StepParams& P, const ParticleBuffers& B, con
         else if (k + 2 < K) { S.b2 = bvec + (size_t)((k + 2) % 3) * vec; }
         if (k == 0) { S.out = B.frblock; S.out_rows = 1; }
         else { S.out = bvec + (size_t)(k % 3) * vec; }
-        pn_stage<<<grid, kThreads, 0, st>>>(P, B.ctrl, B.pos, B.nbr, B.nbr_cnt, B.ftab, S);
+        pn_stage<<<grid, kThreads, 0, st>>>(P, B.ctrl, B.pos, B.nbr, B.nbr_cnt, B.ftab, B.fptab, S);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -1121,7 +1154,8 @@ cudaError_t launch_pair_noise(const StepParams& P, const ParticleBuffers& B, con
 
 cudaError_t launch_pn_rowsum(const StepParams& P, const ParticleBuffers& B, unsigned* out, cudaStream_t st)
 {
-    pn_rowsum<<<(P.n + kThreads - 1) / kThreads, kThreads, 0, st>>>(P, B.pos, B.nbr, B.nbr_cnt, B.ftab, out);
+    pn_rowsum<<<(P.n + kThreads - 1) / kThreads, kThreads, 0, st>>>(P, B.pos, B.nbr, B.nbr_cnt, B.ftab, B.fptab,
+                                                                      out);
     return cudaGetLastError();
 }
 

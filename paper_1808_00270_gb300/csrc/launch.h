@@ -32,6 +32,7 @@ struct ParticleBuffers {
     float* conv;
     float* frblock;
     const float* ftab;
+    const float* fptab;   // perpendicular factors [Q + Qs][nr] (StepParams::perp) or null
     const float* fctab;   // tabulated -dU/dr (StepParams::fc_nr rows) or null
     const float* g0;
     int *cell_start, *cell_count, *cell_head, *cell_next, *chunk_sum, *chunk_off;
