@@ -160,9 +160,9 @@ constexpr int kFirChunk = 256;
 // F^R[t][j] = sum_{sigma=0}^{2H} A_{sigma-H} W[n0 - H + t + sigma][j], t < 64.
 // The taps are taken in chunks of `chunk` (a multiple of 16): the CTA stages
 // the chunk's taps and the W rows they touch for its 32 streams in shared
-// memory; warp w produces outputs 16 w .. 16 w + 15 with a 16-deep window of
-// W rows in registers that slides by one row per tap, so each tap costs one
-// shared load of W, one broadcast tap load and 16 FMAs.
+// memory; warp w produces outputs 16 w .. 16 w + 15, 16 taps at a time from
+// 31 W rows and 16 taps held in registers (256 FMAs per 31 + 4 shared loads,
+// taps in the same order as a plain loop over sigma).
 __device__ __forceinline__ void fir_body(const StepParams& P, Ctrl* __restrict__ ctrl, const float* __restrict__ W,
                                          const float* __restrict__ taps, int ntaps, int chunk, float* __restrict__ out,
                                          int blk, int nblk)
@@ -177,7 +177,7 @@ __device__ __forceinline__ void fir_body(const StepParams& P, Ctrl* __restrict__
     (void)lane;
     const int nk = 64 + 2 * P.H;           // rows holding real W
     const int t0 = warp * kFirR;
-    float acc[kFirR], win[kFirR];
+    float acc[kFirR];
 #pragma unroll
     for (int r = 0; r < kFirR; ++r) acc[r] = 0.f;
     for (int c0 = 0; c0 < ntaps; c0 += chunk) {
@@ -201,19 +201,22 @@ __device__ __forceinline__ void fir_body(const StepParams& P, Ctrl* __restrict__
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
         __syncthreads();
-#pragma unroll
-        for (int r = 0; r < kFirR - 1; ++r) win[r] = Wt[(t0 + r) * 32 + lane];
-        const float* wp = Wt + (t0 + kFirR - 1) * 32 + lane;  // next row to enter the window
+        // 16 taps at a time: the 31 W rows they touch and the taps are loaded
+        // into registers, so every index below is static (no window to rotate)
+        const float* wl = Wt + t0 * 32 + lane;
         for (int sg = 0; sg < cn; sg += kFirR) {
+            float win[2 * kFirR - 1], tap[kFirR];
 #pragma unroll
-            for (int u = 0; u < kFirR; ++u) {
-                // window holds rows t0 + sigma .. t0 + sigma + 15, sigma = sg + u (chunk-local)
-                win[(u + kFirR - 1) % kFirR] = wp[0];
-                wp += 32;
-                const float a = At[sg + u];
+            for (int k = 0; k < 2 * kFirR - 1; ++k) win[k] = wl[(sg + k) * 32];
 #pragma unroll
-                for (int r = 0; r < kFirR; ++r) acc[r] = fmaf(a, win[(u + r) % kFirR], acc[r]);
+            for (int u = 0; u < kFirR; u += 4) {
+                const float4 t4 = *(const float4*)(At + sg + u);
+                tap[u] = t4.x; tap[u + 1] = t4.y; tap[u + 2] = t4.z; tap[u + 3] = t4.w;
             }
+#pragma unroll
+            for (int u = 0; u < kFirR; ++u)
+#pragma unroll
+                for (int r = 0; r < kFirR; ++r) acc[r] = fmaf(tap[u], win[u + r], acc[r]);
         }
     }
     if (j < nstreams)
