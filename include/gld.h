@@ -273,7 +273,9 @@ gld_status gld_set_perpendicular(gld_ctx* ctx, const double* fp, const double* f
  * used.  Every step checks the Gershgorin bound and latches GLD_E_NOT_PSD if
  * a row sum exceeds lambda.  *cheb_err: the largest interpolation error
  * relative to the largest square root (NULL allowed).  Needs Q = 1 and
- * Qs = 0; GLD_E_NOT_PSD if h_w < |g_w| lambda for some w (positive
+ * Qs <= 1, a self-difference term having the pair term's time factor
+ * (gs = c g: its blocks c fs(r) e e^T join M on the diagonal; GLD_E_INVAL
+ * otherwise); GLD_E_NOT_PSD if h_w < |g_w| lambda for some w (positive
  * semi-definiteness not guaranteed) unless psd_clamp.  degree = 0 returns to
  * the self-kernel noise; gld_set_kernels does too.  Such a context cannot join
  * a batch.  Synchronizes. */

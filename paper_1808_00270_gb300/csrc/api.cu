@@ -1227,8 +1227,28 @@ gld_status gld_set_pair_noise(gld_ctx* c, int32_t degree, double* lambda, double
     StepParams& P = c->P;
     if (degree < 0 || degree > kMaxPnDegree) return fail(c, GLD_E_INVAL, "gld_set_pair_noise: degree outside [0, 16]");
     if (degree > 0 && !c->have_kernels) return fail(c, GLD_E_STATE, "gld_set_pair_noise: set the kernels first");
-    if (degree > 0 && (P.Q != 1 || P.Qs != 0))
-        return fail(c, GLD_E_INVAL, "gld_set_pair_noise: needs exactly one separable pair term and no self-difference term");
+    if (degree > 0 && (P.Q != 1 || P.Qs > 1))
+        return fail(c, GLD_E_INVAL, "gld_set_pair_noise: needs one separable pair term and at most one self-difference term");
+    // a self-difference term must share the pair term's time factor (gs = c g):
+    // then every transformed matrix is h_w 1 + g_w (M_pair + c D_self)
+    double cs_ratio = 0.0;
+    if (degree > 0 && P.Qs == 1) {
+        const int M = P.m_max;
+        const double* g = c->wts.data() + M;
+        const double* gs = c->wts.data() + 2 * (size_t)M;
+        double gg = 0.0, sg = 0.0, smax = 0.0;
+        for (int m = 0; m < M; ++m) {
+            gg += g[m] * g[m];
+            sg += gs[m] * g[m];
+            smax = std::max(smax, std::fabs(gs[m]));
+        }
+        cs_ratio = gg > 0 ? sg / gg : 0.0;
+        double dev = 0.0;
+        for (int m = 0; m < M; ++m) dev = std::max(dev, std::fabs(gs[m] - cs_ratio * g[m]));
+        if (dev > 1e-9 * smax)
+            return fail(c, GLD_E_INVAL,
+                        "gld_set_pair_noise: the self-difference term must have the pair term's time factor (gs = c g)");
+    }
     GLD_TRY(sync_and_check(c));
     for (float** p : {&c->d_pntaps, &c->d_zblk, &c->d_bvec}) {
         dfree(c, *p);
@@ -1245,6 +1265,7 @@ gld_status gld_set_pair_noise(gld_ctx* c, int32_t degree, double* lambda, double
     // the bound on the spectrum of the pair matrix: given, or 1.25 x the
     // largest Gershgorin row sum at the current positions
     double lam = lambda ? *lambda : 0.0;
+    P.pn_cs = (float)cs_ratio;  // the row sums include the self-difference blocks
     if (!(lam > 0)) {
         c->d_rowsum = (unsigned*)dalloc(c, sizeof(unsigned));
         if (!c->d_rowsum) return fail(c, GLD_E_NOMEM, "gld_set_pair_noise: allocation failed");
@@ -1322,6 +1343,7 @@ gld_status gld_set_pair_noise(gld_ctx* c, int32_t degree, double* lambda, double
     if (!c->d_pntaps || !c->d_zblk || !c->d_bvec) return fail(c, GLD_E_NOMEM, "gld_set_pair_noise: allocation failed");
     GLD_CUDA(c, cudaMemcpyAsync(c->d_pntaps, taps.data(), sizeof(float) * taps.size(), cudaMemcpyHostToDevice, c->st));
     P.pn_deg = K;
+    P.pn_cs = (float)cs_ratio;
     P.pn_lambda = (float)lam;
     P.pn_inv_lambda = (float)(1.0 / lam);
     return sync_and_check(c);

@@ -84,6 +84,7 @@ struct StepParams {
     // the bound lambda on the spectrum of the pair matrix, with 1 / lambda
     int pn_deg;
     float pn_lambda, pn_inv_lambda;
+    float pn_cs;  // self-difference time factor = pn_cs x the pair term's (when Qs = 1)
     // perpendicular factors of the pair and self-difference terms are set
     // (rows of ParticleBuffers::fptab)
     int perp;

@@ -938,7 +938,9 @@ __global__ void __launch_bounds__(kThreads) b_vacf(const SysDesc* __restrict__ D
 // ---- pair-correlated noise (Sec. II C, Algorithm 1's matrix square root) --
 // With one separable pair term the transformed correlation matrix of every
 // frequency w is hat K_w = h_w 1 + g_w M, M the 3N x 3N pair matrix with
-// blocks f(r_ij) e_ij e_ij^T; its square root is the same function of M for
+// off-diagonal blocks f(r_ij) e_ij e_ij^T (+ fp(r_ij) (1 - e_ij e_ij^T)) and,
+// with a self-difference term of time factor c g, diagonal blocks
+// c sum_k fs(r_ik) e_ik e_ik^T (+ perpendicular part); its square root is the same function of M for
 // all w, so sqrt(hat K_w) ~ sum_k c_wk T_k(M / lambda) (Chebyshev), and after
 // the inverse transform F_n = sum_k T_k(M / lambda) Z_k with Z_k moving
 // averages of W (filters built on the host).  One stage of Clenshaw's
@@ -970,6 +972,7 @@ __global__ void __launch_bounds__(kThreads)
     float* out = S.out + (S.out_rows ? roff : 0);
     const float* z = S.z + roff;
     const float4 pi = pos[id];
+    const float bix = b1[id], biy = b1[np + id], biz = b1[2 * np + id];  // own entry, for the self-difference blocks
     float mx = 0.f, my = 0.f, mz = 0.f, rowsum = 0.f;
     for_each_listed(pi, id, nbr, nbr_cnt[id], P.n_pad, pos, P, [&](int jd, float dx, float dy, float dz, float r2) {
         const float r = sqrtf(r2);
@@ -984,6 +987,16 @@ __global__ void __launch_bounds__(kThreads)
         my = fmaf(eb, ey, fmaf(fp, by, my));
         mz = fmaf(eb, ez, fmaf(fp, bz, mz));
         rowsum += fmaxf(fabsf(f), fabsf(fp));  // the block's spectral norm
+        if (P.Qs > 0) {
+            // self-difference term pn_cs (fs e e^T + fsp (1 - e e^T)) on the own entry b_i
+            const float fs = P.pn_cs * table_at(ftab + P.Q * P.nr, P.nr, xr);
+            const float fsp = P.perp ? P.pn_cs * table_at(fptab + P.Q * P.nr, P.nr, xr) : 0.f;
+            const float ei = (fs - fsp) * dot3(ex, ey, ez, bix, biy, biz);
+            mx = fmaf(ei, ex, fmaf(fsp, bix, mx));
+            my = fmaf(ei, ey, fmaf(fsp, biy, my));
+            mz = fmaf(ei, ez, fmaf(fsp, biz, mz));
+            rowsum += fmaxf(fabsf(fs), fabsf(fsp));
+        }
     });
     const float c = (S.last ? 1.0f : 2.0f) * P.pn_inv_lambda;
     const float ox = fmaf(c, mx, z[id]) - (b2 ? b2[id] : 0.f);
@@ -1006,6 +1019,9 @@ __global__ void __launch_bounds__(kThreads)
     for_each_listed(pos[id], id, nbr, nbr_cnt[id], P.n_pad, pos, P, [&](int, float, float, float, float r2) {
         const float xr = fmaxf(sqrtf(r2), P.rc_min) * P.inv_dr;
         rowsum += fmaxf(fabsf(table_at(ftab, P.nr, xr)), P.perp ? fabsf(table_at(fptab, P.nr, xr)) : 0.f);
+        if (P.Qs > 0)
+            rowsum += fabsf(P.pn_cs) * fmaxf(fabsf(table_at(ftab + P.Q * P.nr, P.nr, xr)),
+                                             P.perp ? fabsf(table_at(fptab + P.Q * P.nr, P.nr, xr)) : 0.f);
     });
     atomicMax(out, __float_as_uint(rowsum));  // non-negative floats order as their bits
 }

@@ -92,6 +92,41 @@ def test_pair_noise_step_matches_oracle():
     assert max(errs.values()) < 1e-5, errs
 
 
+def test_pair_noise_with_self_difference_term():
+    """A self-difference term dK^s = 0.3 f(r) x 0.5 g(t) (the pair term's time
+    factor) joins the pair matrix on its diagonal blocks: F^R of one step
+    within 2e-6 of the oracle's dense square roots (which take the term as
+    written); a self-difference term with another time factor is rejected."""
+    from paper_1808_00270_gb300 import ARR_FR, GLD, GLDError, inputs
+    from paper_1808_00270_gb300.binding import E_INVAL
+    w = _workload(seed=36)
+    ks, g, f, dr = _kernels(w)
+    pos, vel = inputs.initial_state(w)
+    kw = dict(n=w.n, box=w.box, mass=w.mass, kT=w.kT, dt=w.dt, m_max=w.m_max, r_c=w.r_c, A_cons=w.A_cons,
+              seed=w.seed)
+    gpu = GLD(pos=pos, vel=vel, **kw)
+    gpu.set_kernels(ks, g=g, f=f, dr=dr, gs=0.5 * g, fs=0.3 * f)
+    lam, err = gpu.set_pair_noise(12)
+    assert err < 1e-8
+    gpu.step(45)
+    from paper_1808_00270_gb300 import ARR_FC, ARR_HIST
+    p, v = gpu.get_state()
+    ref = oracle.System(pos=p, vel=v, **kw)
+    assert ref.set_kernels(ks, g=g, f=f, dr=dr, gs=0.5 * g, fs=0.3 * f) == 0
+    ref.set_state(step=gpu.step_index, pos=p, vel=v, fc=gpu.get(ARR_FC), hist=gpu.get(ARR_HIST))
+    want = ref.pair_random_force()
+    gpu.step(1)
+    e = rel_l2(gpu.get(ARR_FR), want)
+    print(f"pair noise with self-difference term: lambda {lam:.3f}, F^R {e:.2e}")
+    assert e < 2e-6
+    other = GLD(pos=pos, vel=vel, **kw)
+    t = np.arange(w.m_max) * w.dt
+    other.set_kernels(ks, g=g, f=f, dr=dr, gs=np.exp(-t / 0.1)[None], fs=0.3 * f)
+    with pytest.raises(GLDError) as exc:
+        other.set_pair_noise(8)
+    assert exc.value.status == E_INVAL
+
+
 def test_zero_pair_kernel_gives_the_self_noise():
     """f = 0: the pair matrix vanishes and the random force is the
     self-kernel noise of the same counters."""
