@@ -280,6 +280,15 @@ gld_status gld_set_perpendicular(gld_ctx* ctx, const double* fp, const double* f
  * the self-kernel noise; gld_set_kernels does too.  Such a context cannot join
  * a batch.  Synchronizes. */
 gld_status gld_set_pair_noise(gld_ctx* ctx, int32_t degree, double* lambda, double* cheb_err);
+/* The filters of gld_set_pair_noise, on the host (no device needed): from the
+ * discrete weights ks[m_max] of the self kernel and g[m_max] of the pair
+ * term's time factor (K_0 already halved, as gld_set_kernels derives them),
+ * taps[(degree + 1)][2 m_max - 1]: Z_k = sum_s taps[k][s + m_max - 1]
+ * W_{n+s}, so that F_n = sum_k T_k(M / lambda) Z_k.  *cheb_err as there.
+ * GLD_E_NOT_PSD if h_w < |g_w| lambda for some w and !psd_clamp;
+ * GLD_E_INVAL for m_max < 2, degree outside [1, 16], lambda <= 0, dt <= 0. */
+gld_status gld_pair_noise_filters(const double* ks, const double* g, int32_t m_max, double kT, double dt,
+                                  double lambda, int32_t degree, int32_t psd_clamp, double* taps, double* cheb_err);
 
 /* Memory sums in auxiliary-variable form (App. C discusses auxiliary-variable
  * expansions as the alternative to a stored history).  When every kernel

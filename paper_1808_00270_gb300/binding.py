@@ -102,6 +102,8 @@ def lib():
             "gld_set_conservative_table": (i32, [vp, vp, i32, C.c_double]),
             "gld_set_pair_noise": (i32, [vp, i32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "gld_set_perpendicular": (i32, [vp, vp, vp]),
+            "gld_pair_noise_filters": (i32, [vp, vp, i32, C.c_double, C.c_double, C.c_double, i32, i32, vp,
+                                             C.POINTER(C.c_double)]),
             "gld_set_kernels_table": (i32, [vp, vp, vp, i32, C.c_double, i32, i32, C.POINTER(C.c_double)]),
             "gld_separable_terms": (i32, [vp, i32, i32, i32, vp, vp, C.POINTER(C.c_double)]),
             "gld_pair_correlation": (i32, [vp, vp, vp, vp]),
@@ -148,7 +150,7 @@ def exported_symbols() -> list[str]:
             "gld_server_last_error", "gld_server_destroy", "gld_server_cancel", "gld_set_pair_correlation",
             "gld_pair_correlation", "gld_set_memory_modes", "gld_set_conservative_table",
             "gld_set_kernels_table", "gld_separable_terms", "gld_set_pair_noise",
-            "gld_set_perpendicular"]
+            "gld_set_perpendicular", "gld_pair_noise_filters"]
 
 
 def _ptr(a: np.ndarray):
@@ -651,3 +653,16 @@ def separable_terms(table, Q: int):
     if st != 0:
         raise GLDError(st, "gld_separable_terms failed")
     return f, g, float(tr.value)
+
+
+def pair_noise_filters(ks_weights, g_weights, kT: float, dt: float, lam: float, degree: int, psd_clamp=False):
+    """Host-side filters of the pair-correlated noise: (taps[degree + 1,
+    2 m_max - 1], relative interpolation error) from discrete weights."""
+    ks, g = _f64(ks_weights).ravel(), _f64(g_weights).ravel()
+    M = ks.size
+    taps, err = np.zeros((int(degree) + 1, 2 * M - 1)), C.c_double()
+    st = lib().gld_pair_noise_filters(_ptr(ks), _ptr(g), M, float(kT), float(dt), float(lam), int(degree),
+                                      int(bool(psd_clamp)), _ptr(taps), C.byref(err))
+    if st != 0:
+        raise GLDError(st, "gld_pair_noise_filters failed")
+    return taps, float(err.value)

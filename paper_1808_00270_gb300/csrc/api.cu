@@ -1221,6 +1221,68 @@ gld_status gld_set_perpendicular(gld_ctx* c, const double* fp, const double* fsp
     return sync_and_check(c);
 }
 
+gld_status gld_pair_noise_filters(const double* ks, const double* g, int32_t m_max, double kT, double dt,
+                                  double lambda, int32_t degree, int32_t psd_clamp, double* taps, double* cheb_err)
+{
+    if (!ks || !g || !taps || m_max < 2 || degree < 1 || degree > kMaxPnDegree || !(lambda > 0) || !(dt > 0))
+        return GLD_E_INVAL;
+    const int M = m_max, K = degree, H = M - 1;
+    const long long L = 2LL * M - 1;
+    // transforms (Eq. FT) of the noise targets kT a_m K_m / dt (a_0 = 2) of
+    // the self kernel and of the pair term's time factor, in FP64
+    std::vector<double> hh(M), gh(M);
+    double hmax = 0.0, worst = 0.0;
+    for (int w = 0; w < M; ++w) {
+        double a = 2.0 * ks[0], b = 2.0 * g[0];
+        for (int m = 1; m < M; ++m) {
+            const double cs = std::cos(2.0 * M_PI * (double)(((long long)w * m) % L) / (double)L);
+            a += 2.0 * ks[m] * cs;
+            b += 2.0 * g[m] * cs;
+        }
+        hh[w] = kT / dt * a;
+        gh[w] = kT / dt * b;
+        hmax = std::max(hmax, std::fabs(hh[w]) + std::fabs(gh[w]) * lambda);
+        worst = std::min(worst, hh[w] - std::fabs(gh[w]) * lambda);
+    }
+    if (worst < -1e-12 * hmax && !psd_clamp) return GLD_E_NOT_PSD;
+    // Chebyshev interpolation of phi_w(x) = sqrt(h_w + g_w lambda x) on
+    // [-1, 1] at degree K, its error on a fine grid, and the filter taps
+    // a_k[s] = (c_0k + 2 sum_{w>=1} c_wk cos(2 pi w s / L)) / L
+    auto phi = [&](int w, double x) { return std::sqrt(std::max(hh[w] + gh[w] * lambda * x, 0.0)); };
+    const int nc = K + 1;
+    std::vector<double> cw((size_t)M * nc);
+    double err = 0.0;
+    for (int w = 0; w < M; ++w) {
+        for (int k = 0; k < nc; ++k) {
+            double acc = 0.0;
+            for (int j = 0; j < nc; ++j) {
+                const double th = M_PI * (j + 0.5) / nc;
+                acc += phi(w, std::cos(th)) * std::cos(k * th);
+            }
+            cw[(size_t)w * nc + k] = (k == 0 ? 1.0 : 2.0) * acc / nc;
+        }
+        for (int t = 0; t <= 256; ++t) {
+            const double x = -1.0 + 2.0 * t / 256.0, th = std::acos(std::min(1.0, std::max(-1.0, x)));
+            double p = 0.0;
+            for (int k = 0; k < nc; ++k) p += cw[(size_t)w * nc + k] * std::cos(k * th);
+            err = std::max(err, std::fabs(p - phi(w, x)));
+        }
+    }
+    double smax = 0.0;  // the largest square root over frequencies and the interval
+    for (int w = 0; w < M; ++w) smax = std::max(smax, std::max(phi(w, 1.0), phi(w, -1.0)));
+    if (cheb_err) *cheb_err = smax > 0 ? err / smax : 0.0;
+    for (int k = 0; k < nc; ++k)
+        for (int sg = 0; sg <= 2 * H; ++sg) {
+            const long long sh = sg - H;
+            double v = cw[k];
+            for (int w = 1; w < M; ++w)
+                v += 2.0 * cw[(size_t)w * nc + k] *
+                     std::cos(2.0 * M_PI * (double)((((long long)w * sh) % L + L) % L) / (double)L);
+            taps[(size_t)k * (2 * H + 1) + sg] = v / (double)L;
+        }
+    return GLD_OK;
+}
+
 gld_status gld_set_pair_noise(gld_ctx* c, int32_t degree, double* lambda, double* cheb_err)
 {
     if (!c) return GLD_E_INVAL;
@@ -1261,7 +1323,6 @@ gld_status gld_set_pair_noise(gld_ctx* c, int32_t degree, double* lambda, double
     GLD_TRY(invalidate_noise(c));
     if (degree == 0) return sync_and_check(c);
     const int M = P.m_max, K = degree;
-    const long long L = 2LL * M - 1;
     // the bound on the spectrum of the pair matrix: given, or 1.25 x the
     // largest Gershgorin row sum at the current positions
     double lam = lambda ? *lambda : 0.0;
@@ -1278,65 +1339,18 @@ gld_status gld_set_pair_noise(gld_ctx* c, int32_t degree, double* lambda, double
         lam = std::max(1.25 * (double)mx, 1e-6);
     }
     if (lambda) *lambda = lam;
-    // transforms (Eq. FT) of the noise targets kT a_m K_m / dt of the self
-    // kernel and of the pair term's time factor, in FP64
-    const double* ws = c->wts.data();
-    const double* wg = c->wts.data() + M;
-    std::vector<double> hh(M), gh(M);
-    double hmax = 0.0, worst = 0.0;
-    for (int w = 0; w < M; ++w) {
-        double a = 2.0 * ws[0], b = 2.0 * wg[0];
-        for (int m = 1; m < M; ++m) {
-            const double cs = std::cos(2.0 * M_PI * (double)(((long long)w * m) % L) / (double)L);
-            a += 2.0 * ws[m] * cs;
-            b += 2.0 * wg[m] * cs;
-        }
-        hh[w] = c->prm.kT / c->prm.dt * a;
-        gh[w] = c->prm.kT / c->prm.dt * b;
-        hmax = std::max(hmax, std::fabs(hh[w]) + std::fabs(gh[w]) * lam);
-        worst = std::min(worst, hh[w] - std::fabs(gh[w]) * lam);
-    }
-    if (worst < -1e-12 * hmax && !c->prm.psd_clamp)
+    const int H = M - 1;
+    std::vector<double> td((size_t)(K + 1) * (2 * H + 1));
+    const gld_status fs = gld_pair_noise_filters(c->wts.data(), c->wts.data() + M, M, c->prm.kT, c->prm.dt, lam, K,
+                                                 c->prm.psd_clamp, td.data(), cheb_err);
+    if (fs == GLD_E_NOT_PSD)
         return fail(c, GLD_E_NOT_PSD,
                     "gld_set_pair_noise: h_w - |g_w| lambda < 0 for some frequency: positive semi-definiteness of the "
                     "correlation matrices is not guaranteed over the spectral bound (psd_clamp clamps)");
-    // Chebyshev interpolation of phi_w(x) = sqrt(h_w + g_w lambda x) on
-    // [-1, 1] at degree K, its error on a fine grid, and the filter taps
-    // a_k[s] = (c_0k + 2 sum_{w>=1} c_wk cos(2 pi w s / L)) / L
-    auto phi = [&](int w, double x) { return std::sqrt(std::max(hh[w] + gh[w] * lam * x, 0.0)); };
-    const int nc = K + 1;
-    std::vector<double> cw((size_t)M * nc);
-    double err = 0.0;
-    for (int w = 0; w < M; ++w) {
-        for (int k = 0; k < nc; ++k) {
-            double acc = 0.0;
-            for (int j = 0; j < nc; ++j) {
-                const double th = M_PI * (j + 0.5) / nc;
-                acc += phi(w, std::cos(th)) * std::cos(k * th);
-            }
-            cw[(size_t)w * nc + k] = (k == 0 ? 1.0 : 2.0) * acc / nc;
-        }
-        for (int t = 0; t <= 256; ++t) {
-            const double x = -1.0 + 2.0 * t / 256.0, th = std::acos(std::min(1.0, std::max(-1.0, x)));
-            double p = 0.0;
-            for (int k = 0; k < nc; ++k) p += cw[(size_t)w * nc + k] * std::cos(k * th);
-            err = std::max(err, std::fabs(p - phi(w, x)));
-        }
-    }
-    double smax = 0.0;  // the largest square root over frequencies and the interval
-    for (int w = 0; w < M; ++w) smax = std::max(smax, std::max(phi(w, 1.0), phi(w, -1.0)));
-    if (cheb_err) *cheb_err = smax > 0 ? err / smax : 0.0;
-    const int H = M - 1;
-    std::vector<float> taps((size_t)nc * c->la, 0.0f);
-    for (int k = 0; k < nc; ++k)
-        for (int sg = 0; sg <= 2 * H; ++sg) {
-            const long long sh = sg - H;
-            double v = cw[k];
-            for (int w = 1; w < M; ++w)
-                v += 2.0 * cw[(size_t)w * nc + k] *
-                     std::cos(2.0 * M_PI * (double)((((long long)w * sh) % L + L) % L) / (double)L);
-            taps[(size_t)k * c->la + sg] = (float)(v / (double)L);
-        }
+    if (fs != GLD_OK) return fail(c, fs, "gld_set_pair_noise: invalid filter arguments");
+    std::vector<float> taps((size_t)(K + 1) * c->la, 0.0f);
+    for (int k = 0; k <= K; ++k)
+        for (int sg = 0; sg <= 2 * H; ++sg) taps[(size_t)k * c->la + sg] = (float)td[(size_t)k * (2 * H + 1) + sg];
     c->d_pntaps = (float*)dalloc(c, sizeof(float) * taps.size());
     c->d_zblk = (float*)dalloc(c, sizeof(float) * (size_t)K * P.T * 3 * P.n_pad);
     c->d_bvec = (float*)dalloc(c, sizeof(float) * 3 * 3 * (size_t)P.n_pad);
