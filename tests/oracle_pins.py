@@ -677,7 +677,8 @@ def pin_pair_noise_two_particles(variant=0):
     modes (F_1 +- F_2).e / sqrt 2 with kernels K^s +- f(r) g, and the
     perpendicular modes with K^s alone -- each must equal the scalar generator
     (A_s of the oracle, Eq. noise_production) for that kernel applied to the
-    same projection of W."""
+    same projection of W.  Then with a self-difference term and perpendicular
+    factors: K^s + fs gs +- f g along e, K^s + fsp gs +- fp g across it."""
     M, dt, kT = 10, 0.02, 0.7
     Ks, g, f, dr = _pn_kernels(M, dt)
     rng = np.random.default_rng(8)
@@ -698,15 +699,31 @@ def pin_pair_noise_two_particles(variant=0):
     Kd[0] *= 0.5
     gd = g[0] * dt
     gd[0] *= 0.5
+    worst = _two_particle_modes(F, W, e, u, [(e, Kd, fr * gd), (u, Kd, 0.0 * gd)], kT, dt)
+    # with a self-difference term (diagonal blocks) and perpendicular factors
+    # (1 - e e^T parts): along e K^s + fs gs +- f g, across e K^s + fsp gs +- fp g
+    fp, fs, fsp = 0.5 * f, 0.3 * f, 0.2 * f
+    s.set_kernels(Ks, g=g, f=f, dr=dr, gs=0.5 * g, fs=fs)
+    s.set_perp(fp, fsp)
+    F2 = s.pair_random_force()
+    at = lambda t: float(np.interp(r, np.arange(t.shape[1]) * dr, t[0]))
+    worst = max(worst, _two_particle_modes(F2, W, e, u, [(e, Kd + at(fs) * 0.5 * gd, at(f) * gd),
+                                                         (u, Kd + at(fsp) * 0.5 * gd, at(fp) * gd)], kT, dt))
+    return bool(worst < 1e-10), f"mode projections vs scalar generator {worst:.1e}"
+
+
+def _two_particle_modes(F, W, e, u, modes, kT, dt):
+    """Largest relative deviation of (F_1 +- F_2).v / sqrt 2 from the scalar
+    generator with kernel base +- pair for each (v, base, pair)."""
     worst = 0.0
     for sign in (1.0, -1.0):
-        for v, kern in ((e, Kd + sign * fr * gd), (u, Kd)):
-            st, _, _, A, _ = oracle.noise_coefs(kern, kT, dt)
+        for v, base, pair in modes:
+            st, _, _, A, _ = oracle.noise_coefs(base + sign * pair, kT, dt)
             Wp = (W[:, 0, :] + sign * W[:, 1, :]) @ v / np.sqrt(2)
             want = float(A @ Wp)
             got = float((F[0] + sign * F[1]) @ v / np.sqrt(2))
             worst = max(worst, abs(got - want) / max(abs(want), 1e-3))
-    return bool(worst < 1e-10), f"mode projections vs scalar generator {worst:.1e}"
+    return worst
 
 
 def pin_pair_noise_covariance(variant=0):
