@@ -638,6 +638,18 @@ gld_status gld_set_kernels(gld_ctx* c, const double* Ks, int32_t Q, const double
     if (!Ks || Q < 0 || Q > kMaxQ || Qs < 0 || Qs > kMaxQ || (Q > 0 && (!g || !f)) || (Qs > 0 && (!dKs_g || !dKs_f)) ||
         (Q + Qs > 0 && (nr < 2 || !(dr > 0))) || (conv != GLD_KCONT && conv != GLD_KDISCRETE))
         return fail(c, GLD_E_INVAL, "gld_set_kernels: invalid kernel description");
+    // the pair noise and the perpendicular factors belong to the previous
+    // kernels: off, and their buffers released (stream-ordered like ftab's)
+    c->P.pn_deg = 0;
+    c->P.perp = 0;
+    invalidate_graph(c);
+    for (float** p : {&c->d_pntaps, &c->d_zblk, &c->d_bvec, &c->fptab}) {
+        dfree(c, *p);
+        *p = nullptr;
+    }
+    dfree(c, c->d_rowsum);
+    c->d_rowsum = nullptr;
+    c->B.fptab = nullptr;
     const int M = c->P.m_max;
     std::vector<double> in((size_t)(1 + 2 * kMaxQ) * M, 0.0);
     std::memcpy(in.data(), Ks, sizeof(double) * M);

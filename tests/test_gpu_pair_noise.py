@@ -190,6 +190,23 @@ def test_pair_noise_graph_forms_bit_identical():
         assert np.array_equal(p, outs[0][0]) and np.array_equal(fr, outs[0][1])
 
 
+def test_set_kernels_releases_the_pair_noise():
+    """gld_set_kernels switches the pair noise off and frees its buffers: the
+    context's device bytes return to what they were, and the following steps
+    are those of a context that never had it, bit for bit."""
+    w = _workload(seed=37)
+    g, h = _pair(w), _pair(w)
+    b0 = g.bytes()
+    g.set_pair_noise(8)
+    assert g.bytes() > b0
+    ks, gg, f, dr = _kernels(w)
+    g.set_kernels(ks, g=gg, f=f, dr=dr)
+    assert g.bytes() == b0
+    g.step(96)
+    h.step(96)
+    assert np.array_equal(g.get_state()[0], h.get_state()[0])
+
+
 def test_pair_noise_bound_and_arguments():
     from paper_1808_00270_gb300 import Batch, GLDError
     from paper_1808_00270_gb300.binding import E_INVAL, E_NOT_PSD
