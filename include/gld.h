@@ -18,9 +18,11 @@
  *
  * Conventions shared by every call:
  *   - All pointers passed to gld_create / gld_set_kernels / gld_get_* /
- *     gld_set_* / gld_vacf are HOST pointers owned by the caller; the library
- *     copies from or into them and keeps no reference.  Arrays of particle
- *     vectors are row-major [n][3] doubles.
+ *     gld_set_* / gld_vacf / gld_pair_correlation and the host-only helpers
+ *     gld_separable_terms / gld_pair_noise_filters are HOST pointers owned by
+ *     the caller; the library copies from or into them and keeps no
+ *     reference.  Arrays of particle vectors are row-major [n][3] doubles;
+ *     tables are row-major as written ([rows][columns]).
  *   - The library owns all device memory of a context.  It allocates through
  *     gld_params.alloc / .free when given (e.g. a framework's caching
  *     allocator), else with cudaMalloc / cudaFree.
