@@ -1,6 +1,7 @@
 """Parity at the full sizes (needs a GPU): the 262144-particle, m_max = 400
 suspension on sampled particles in the launch configuration bench.py times
-(graphs, 64-step noise blocks), and the VACF of the 4096-particle system over
+(graphs, 64-step noise blocks) -- with the benchmark's kernels and with the
+general pair kernel -- and the VACF of the 4096-particle system over
 10^4 steps against an independent oracle run."""
 import numpy as np
 import pytest
@@ -33,6 +34,34 @@ def test_large_suspension_sampled_forces():
     fd, fr = gpu.get(ARR_FD)[idx], gpu.get(ARR_FR)[idx]
     assert rel_l2(fd, fd_ref) < 1e-5
     assert rel_l2(fr, fr_ref) < 1e-5
+
+
+def test_large_suspension_general_pair_kernel_sampled_forces():
+    """The same at full size with the general pair kernel: a self-difference
+    term and perpendicular factors on top of the pair term (Sec. II A)."""
+    from paper_1808_00270_gb300 import ARR_FC, ARR_FD, ARR_FR, ARR_HIST, GLD, inputs
+    w = inputs.LARGE
+    g, f, dr = inputs.pair_kernel_tables(w)
+    r = np.arange(f.shape[1]) * dr
+    fp = (0.8 * np.clip(1 - r / w.r_c, 0, None) * (1 + np.cos(2 * r)))[None]
+    ks = inputs.self_kernel_samples(w)
+    pos, vel = inputs.initial_state(w)
+    kw = dict(n=w.n, box=w.box, mass=w.mass, kT=w.kT, dt=w.dt, m_max=w.m_max, r_c=w.r_c, A_cons=w.A_cons,
+              seed=w.seed)
+    gpu = GLD(pos=pos, vel=vel, **kw)
+    gpu.set_kernels(ks, g=g, f=f, dr=dr, gs=0.5 * g, fs=0.3 * f)
+    gpu.set_perpendicular(fp, 0.25 * fp)
+    gpu.step(448)
+    p, v = gpu.get_state()
+    ref = oracle.System(pos=p, vel=v, **kw)
+    assert ref.set_kernels(ks, g=g, f=f, dr=dr, gs=0.5 * g, fs=0.3 * f) == 0
+    assert ref.set_perp(fp, 0.25 * fp) == 0
+    ref.set_state(step=gpu.step_index, pos=p, vel=v, fc=gpu.get(ARR_FC), hist=gpu.get(ARR_HIST))
+    idx = np.sort(np.random.default_rng(12).choice(w.n, size=1500, replace=False)).astype(np.int32)
+    fd_ref, fr_ref = ref.forces_subset(idx)
+    gpu.step(1)
+    assert rel_l2(gpu.get(ARR_FD)[idx], fd_ref) < 1e-5
+    assert rel_l2(gpu.get(ARR_FR)[idx], fr_ref) < 1e-5
 
 
 @pytest.mark.parametrize("wname,L,stride,burn", [("gld_n64_m32", 12, 3, 5), ("gld_n4096_m200", 40, 3, 2)])
