@@ -27,6 +27,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -69,6 +70,10 @@ def parse():
     ap.add_argument("--hbm-budget", type=float, default=0.0, help="serve: device GB for admitted systems")
     ap.add_argument("--sequential", type=int, default=-1,
                     help="serve: requests also run one at a time with plain gld_step (-1: all)")
+    ap.add_argument("--batch-systems", type=int, default=512,
+                    help="systems of the batched workload summarised in the headline line (0: none)")
+    ap.add_argument("--clock-log", default=None,
+                    help="file for the nvidia-smi clock samples of the timed region (default: a temporary file)")
     return ap.parse_args()
 
 
@@ -112,14 +117,19 @@ def replica_value(n_per_rank: int, steps: int, world: int, ms_max: float) -> flo
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi samples of SM clock and throttle reasons during the timed
+    region (a read-only query), kept in a temporary file or in `path`."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: str, path: str):
-        self.path, self.proc = path, None
+    def __init__(self, gpu_index: str, path: str | None = None):
+        self.proc, self.tmp = None, path is None
+        if path is None:
+            fd, path = tempfile.mkstemp(prefix="gld_clocks_", suffix=".csv")
+            os.close(fd)
+        self.path = path
         try:
             self.fh = open(path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
@@ -149,6 +159,8 @@ class ClockSampler:
             for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), parts[4:8]):
                 if val.lower().startswith("active"):
                     reasons.add(name)
+        if self.tmp:
+            os.remove(self.path)
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
@@ -203,7 +215,7 @@ def pctl(xs, q):
     return float(np.percentile(np.asarray(xs, dtype=float), q)) if len(xs) else None
 
 
-def batch_leg(args, rank: int, world: int, local: int):
+def batch_leg(args, rank: int, world: int, local: int, quiet: bool = False):
     """Independent uneven systems stepped as one batch (one launch per kernel
     family per step, 64-step blocks as one graph) against the same systems
     stepped one at a time with plain gld_step."""
@@ -231,7 +243,7 @@ def batch_leg(args, rank: int, world: int, local: int):
     b.sync()
     stream = torch.cuda.current_stream()
     gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]
-    clocks = ClockSampler(gpu_index, os.path.join(ROOT, "gpurun_out", f"clocks_batch_rank{rank}.csv"))
+    clocks = ClockSampler(gpu_index, args.clock_log)
     time.sleep(0.5)
     barrier(world)
     torch.cuda.synchronize()
@@ -286,12 +298,12 @@ def batch_leg(args, rank: int, world: int, local: int):
                         "frac": alg / (conv_ms / 1e3) / 1e9 / peak, "peak_source": f"{peak_kind} hbm_gbs",
                         "traffic": None, "algorithmic_bytes_per_launch": alg, "avg_launch_ms": conv_ms},
            "clocks": clk, "gpu_launches": (K // T) * (2 + T * 8)}
-    if rank == 0:
+    if rank == 0 and not quiet:
         print(json.dumps(out))
     for g in systems:
         g.close()
     b.close()
-    return 0
+    return out
 
 
 def request_inputs(trace, vacf):
@@ -335,7 +347,7 @@ def serve_leg(args, rank: int, world: int, local: int, quiet: bool = False):
     ids = serve_requests(srv, trace, reqs, t0)
     sub_s = time.perf_counter() - t_sub
     gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]
-    clocks = ClockSampler(gpu_index, os.path.join(ROOT, "gpurun_out", f"clocks_serve_rank{rank}.csv"))
+    clocks = ClockSampler(gpu_index, args.clock_log)
     srv.drain(3600)
     clk = clocks.stop()
     res = [srv.result(i) for i in ids]
@@ -398,7 +410,8 @@ def main():
     args = parse()
     rank, world, local = dist_env()
     if args.workload.startswith("batch") and args.impl == "gld":
-        return batch_leg(args, rank, world, local)
+        batch_leg(args, rank, world, local)
+        return 0
     if args.workload.startswith("serve") and args.impl == "gld":
         serve_leg(args, rank, world, local)
         return 0
@@ -455,16 +468,21 @@ def main():
         lam, cheb = sim.set_pair_noise(args.pair_noise)
         cfg["pair_noise"].update({"lambda": lam, "interpolation_error": cheb})
     T = 64
-    # warm-up: at least W steps, then up to a noise-block boundary and one graph replay
-    sim.step(max(args.warmup, 3))
+    # warm-up: at least W steps and until the VACF runs with every origin in
+    # flight (burn-in + vacf_len steps), so the clock sees its full cost; then
+    # up to a noise-block boundary (the timed region starts with a whole
+    # block's noise) and one graph replay
+    warm = max(args.warmup, 3, vacf["vacf_burnin"] + vacf["vacf_len"])
+    sim.step(warm)
     sim.step((-sim.step_index) % T + T)
     sim.sync()
+    warm_steps = sim.step_index
 
     K = args.steps
     d0 = sim.diag()  # before the clock: graph form and list builds so far
+    _, orig0 = sim.vacf()
     gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local] if os.environ.get("CUDA_VISIBLE_DEVICES") else str(local)
-    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-    clocks = ClockSampler(gpu_index, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv"))
+    clocks = ClockSampler(gpu_index, args.clock_log)
     time.sleep(0.5)
     stream = torch.cuda.current_stream()
     barrier(world)
@@ -479,6 +497,7 @@ def main():
     clk = clocks.stop()
     sim.sync()
     d1 = sim.diag()
+    _, orig1 = sim.vacf()
     ms = max_over_ranks(ms, world, "cuda")
     value = replica_value(w.n, K, world, ms)
     blocks = (K + T - 1) // T
@@ -507,6 +526,9 @@ def main():
                 "kernel_share": {k: v[0] / total_ms for k, v in prof.items() if total_ms > 0}}
 
     diag = sim.diag()
+    diag.update({"untimed_steps_before_clock": warm_steps, "vacf_origins_before": int(orig0),
+                 "vacf_origins_after": int(orig1), "vacf_origins_in_flight": (vacf["vacf_len"] + vacf["vacf_stride"] - 1)
+                 // vacf["vacf_stride"]})
     T_blocks = (K + T - 1) // T
     if d0["graph_mode"] == 2:  # rebuild kernels only on the steps that rebuild
         launches = K * 5 + 4 * (d1["rebuilds"] - d0["rebuilds"]) + 2 * T_blocks
@@ -561,12 +583,25 @@ def main():
                   "throughput_vs_sequential": o["throughput_vs_sequential"],
                   "max_sustainable_rate_per_s": o["max_sustainable_rate_per_s"], "gpu_launches": o["gpu_launches"]}
 
+    batched = None
+    if rank == 0 and world == 1 and args.batch_systems > 0:
+        bargs = argparse.Namespace(**vars(args))
+        bargs.systems, bargs.steps, bargs.warmup = args.batch_systems, 128, 64
+        o = batch_leg(bargs, rank, world, local, quiet=True)
+        batched = {"systems": o["config"]["systems"], "particles": o["config"]["particles"],
+                   "workload": "uneven independent systems (N log-uniform 256-16384, densities 0.02-0.2, "
+                               "m_max in {100, 200, 400}) stepped as one batch",
+                   "value": o["value"], "unit": UNIT, "ms_per_step": o["ms_per_step"], "steps": o["steps"],
+                   "sequential_value": o["sequential"]["value"], "speedup_vs_sequential": o["speedup_vs_sequential"],
+                   "autotuned_schedule": o["autotune"]["schedules"][o["autotune"]["schedule"]],
+                   "conv_roofline_frac": o["roofline"]["frac"], "gpu_launches": o["gpu_launches"]}
+
     if rank == 0:
         print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
                           "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True,
                           "scaling": "weak", "vs_baseline": None, "dtype": "bf16-history" if args.hist == "bf16" else "f32",
                           "data": "synthetic", "config": cfg, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                          "clocks": clk, "gpu_launches": launches, "served": served, "diag": diag, "profile": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items()}}))
+                          "clocks": clk, "gpu_launches": launches, "served": served, "batched": batched, "diag": diag, "profile": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items()}}))
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0

@@ -63,7 +63,11 @@
  *   8 sign of F^C flipped                  9 auto and cross pair terms swapped
  *  10 pair-kernel table read at the lower row, not interpolated
  *  (11 and 12 are planted in pairnoise.py; this file builds unchanged)
- *  13 perpendicular pair terms without the projection 1 - e e^T */
+ *  13 perpendicular pair terms without the projection 1 - e e^T
+ *  14 pairs closer than r_c,min dropped instead of clamped
+ *  15 perpendicular factors read at the unclamped distance
+ *  16 the clamped distance used for the unit vector e as well
+ *  (17 is planted in pairnoise.py) */
 #ifndef OR_PLANT
 #define OR_PLANT 0
 #endif
@@ -608,17 +612,19 @@ static void dissipative_force_i(const or_sys* s, int i, const int32_t* nb, int64
         double d[3];
         for (int c = 0; c < 3; ++c) d[c] = min_image(s->pos[3 * i + c] - s->pos[3 * j + c], s->L);
         double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        double e[3] = { d[0] / r, d[1] / r, d[2] / r };
         double rt = r < s->rc_min ? s->rc_min : r;
+        if (OR_PLANT == 14 && r < s->rc_min) continue;
+        const double re = OR_PLANT == 16 ? rt : r;
+        double e[3] = { d[0] / re, d[1] / re, d[2] / re };
         double fq[8], fsq[8], fpq[8], fspq[8]; /* radial factors f_q, fs_q and their
                                                   perpendicular parts (Q, Qs <= 8) */
         for (int q = 0; q < Q; ++q) {
             fq[q] = table_at(s->f + (size_t)q * s->nr, s->nr, s->dr, rt);
-            fpq[q] = s->fp ? table_at(s->fp + (size_t)q * s->nr, s->nr, s->dr, rt) : 0.0;
+            fpq[q] = s->fp ? table_at(s->fp + (size_t)q * s->nr, s->nr, s->dr, OR_PLANT == 15 ? r : rt) : 0.0;
         }
         for (int q = 0; q < Qs; ++q) {
             fsq[q] = table_at(s->fs + (size_t)q * s->nr, s->nr, s->dr, rt);
-            fspq[q] = s->fsp ? table_at(s->fsp + (size_t)q * s->nr, s->nr, s->dr, rt) : 0.0;
+            fspq[q] = s->fsp ? table_at(s->fsp + (size_t)q * s->nr, s->nr, s->dr, OR_PLANT == 15 ? r : rt) : 0.0;
         }
         /* rows and weight of a general table at rt (the interpolation of table_at) */
         int kr0 = 0, kr1 = 0;

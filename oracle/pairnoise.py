@@ -29,7 +29,8 @@ the last value held (as the dissipative force of the oracle); pairs are those
 with r < r_c.
 
 Deliberate mistakes for the pin test (``variant``): 11 the sign of the pair
-blocks flipped; 12 the inverse transform scaled by 1 / m_max.
+blocks flipped; 12 the inverse transform scaled by 1 / m_max; 17 the radial
+factors read at the unclamped distance (r_c,min ignored).
 """
 from __future__ import annotations
 
@@ -72,7 +73,7 @@ def matrix_terms(pos, box, rc, rc_min, m_max, dt, Ks, g=None, f=None, dr=1.0, gs
     n = np.asarray(pos).shape[0]
     terms = [(discretize(Ks, dt, discrete), np.eye(3 * n))]
     i, j, r, e = pair_geometry(pos, box, rc)
-    rt = np.maximum(r, rc_min)
+    rt = r if variant == 17 else np.maximum(r, rc_min)
     ee = e[:, :, None] * e[:, None, :]
     perp = np.eye(3)[None] - ee
     g = np.zeros((0, m_max)) if g is None else np.reshape(g, (-1, m_max))

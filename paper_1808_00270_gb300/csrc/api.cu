@@ -638,6 +638,12 @@ gld_status gld_set_kernels(gld_ctx* c, const double* Ks, int32_t Q, const double
     if (!Ks || Q < 0 || Q > kMaxQ || Qs < 0 || Qs > kMaxQ || (Q > 0 && (!g || !f)) || (Qs > 0 && (!dKs_g || !dKs_f)) ||
         (Q + Qs > 0 && (nr < 2 || !(dr > 0))) || (conv != GLD_KCONT && conv != GLD_KDISCRETE))
         return fail(c, GLD_E_INVAL, "gld_set_kernels: invalid kernel description");
+    // From here until the new kernels are in place the context has none: the
+    // old tables are released below, so a failure on the way (an allocation,
+    // a CUDA call, a rejected spectrum) leaves a context that refuses to step
+    // rather than one whose step would read freed tables.
+    c->have_kernels = false;
+    c->B.ftab = nullptr;
     // the pair noise and the perpendicular factors belong to the previous
     // kernels: off, and their buffers released (stream-ordered like ftab's)
     c->P.pn_deg = 0;
@@ -663,7 +669,7 @@ gld_status gld_set_kernels(gld_ctx* c, const double* Ks, int32_t Q, const double
         for (int k = 0; k < nr; ++k) tab[(size_t)q * nr + k] = (float)f[(size_t)q * nr + k];
     for (int q = 0; q < Qs; ++q)
         for (int k = 0; k < nr; ++k) tab[(size_t)(Q + q) * nr + k] = (float)dKs_f[(size_t)q * nr + k];
-    if (c->ftab) dfree(c, c->ftab);
+    dfree(c, c->ftab);
     c->ftab = (float*)dalloc(c, sizeof(float) * tab.size());
     if (!c->ftab) return fail(c, GLD_E_NOMEM, "gld_set_kernels: table allocation failed");
     GLD_CUDA(c, cudaMemcpyAsync(c->ftab, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice, c->st));
@@ -1903,6 +1909,7 @@ gld_status gld_batch_step(gld_batch* b, int64_t nsteps)
     if (b->members.empty() || nsteps == 0) return GLD_OK;
     for (gld_ctx* c : b->members) {
         if (c->latched != GLD_OK) return bfail(b, c->latched, "gld_batch_step: a member has a latched error");
+        if (!c->have_kernels) return bfail(b, GLD_E_STATE, "gld_batch_step: a member has no kernels set");
         if (c->noise_valid && c->host_step != c->noise_end)
             return bfail(b, GLD_E_STATE, "gld_batch_step: a member left its noise-block boundary");
     }

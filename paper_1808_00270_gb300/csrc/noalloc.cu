@@ -20,7 +20,9 @@ namespace {
 constexpr int kMaxN = GLD_NOALLOC_MAX_N;
 constexpr int kMaxCellsPerSide = 64;
 constexpr int kMaxCells = kMaxCellsPerSide * kMaxCellsPerSide * kMaxCellsPerSide;
-constexpr int kChunk = 512;  // cells per block of the cell-list scan
+// cells per block of the cell-list scan: the chunk sums below are sized by
+// the block size that launch_cell_build uses
+constexpr int kChunk = kBatchCellChunk;
 constexpr int kMaxChunks = (kMaxCells + kChunk - 1) / kChunk;
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }

@@ -474,6 +474,69 @@ def pin_pair_decoupling(variant=0):
     return ok, f"V+ errors {ep}, V- errors {em}"
 
 
+def _run_pair_below_rc_min(dt, variant):
+    """Two particles 1.0 apart on the x axis, with r_c = 4 and the lower
+    cutoff r_c,min = 2 (Sec. III B: kernels below r_c,min take their value at
+    r_c,min).  Every radial factor varies below r_c,min, so only a kernel
+    read at r_c,min (not at the true distance) gives constant kernels.  The
+    particles move apart but stay below r_c,min, and the relative motion stays
+    on the axis, so V_+- along x follow the closed forms with
+    K^s + dK^s_par(r_c,min) +- K^p_par(r_c,min) and the common y motion the
+    one with K^s + dK^s_perp(r_c,min) + K^p_perp(r_c,min).  Returns the
+    largest deviation, the smallest and largest separation seen."""
+    m_max = int(round(2.0 / dt))
+    rc, rc_min, nr = 4.0, 2.0, 65
+    dr = rc / (nr - 1)                     # r_c,min is grid point 32
+    r = np.arange(nr) * dr
+    f_par = (8.0 * (1 - r / rc) ** 2)[None]       # 2.0 at r_c,min, 4.5 at r = 1
+    f_perp = (3.0 - 0.5 * r)[None]                # 2.0 at r_c,min, 2.5 at r = 1
+    fs_par = (1.0 + 2.0 * (1 - r / rc))[None]     # 2.0 at r_c,min, 2.5 at r = 1
+    fs_perp = (0.5 * np.exp(2.0 - r))[None]       # 0.5 at r_c,min, 1.36 at r = 1
+    tau, Ks0 = 0.1, 20.0
+    s = oracle.System(n=2, box=100.0, mass=1.0, kT=0.0, dt=dt, m_max=m_max, r_c=rc, r_c_min=rc_min,
+                      pos=[[50, 50, 50], [49, 50, 50]], vel=[[1.0, 0.7, 0], [0, 0.7, 0]], variant=variant)
+    t = np.arange(m_max) * dt
+    g = np.exp(-t / tau)[None]
+    if s.set_kernels(Ks0 * np.exp(-t / tau), g=g, f=f_par, dr=dr, gs=g, fs=fs_par) != 0:
+        return np.inf, 0.0, 0.0
+    s.set_perp(f_perp, fs_perp)
+    at = lambda tab: float(tab[0, 32])
+    steps = int(round(T_RCMIN / dt))
+    V, sep = [s.get(oracle.VEL)], []
+    for _ in range(steps):
+        s.step(1)
+        V.append(s.get(oracle.VEL))
+        p = s.get(oracle.POS)
+        sep.append(float(np.linalg.norm(p[0] - p[1])))
+    V = np.array(V)
+    tt = np.arange(steps + 1) * dt
+    worst = max(float(np.abs(V[:, :, 2]).max()), float(np.abs(V[:, 0, 1] - V[:, 1, 1]).max()))
+    for c, amp, sign, kp, kd in ((0, 1.0, 1.0, at(f_par), at(fs_par)), (0, 1.0, -1.0, at(f_par), at(fs_par)),
+                                 (1, 1.4, 1.0, at(f_perp), at(fs_perp))):
+        got = (V[:, 0, c] + sign * V[:, 1, c]) / math.sqrt(2)
+        want = amp * closed_form_vacf(tt, Ks0 + kd + sign * kp, tau) / math.sqrt(2)
+        worst = max(worst, float(np.abs(got - want).max()))
+    return worst, min(sep), max(sep)
+
+
+T_RCMIN = 1.0
+
+
+def pin_rc_min_clamp(variant=0):
+    """The lower cutoff r_c,min of the pair kernels (Sec. III B): two
+    particles closer than r_c,min with parallel, perpendicular and
+    self-difference factors that all vary below it must follow the
+    two-particle closed forms of the kernels evaluated at r_c,min (with the
+    true direction e), at second order in dt.  Dropping the close pair,
+    reading any factor at the true distance, or normalising e by the clamped
+    distance changes a mode's kernel and fails."""
+    res = [_run_pair_below_rc_min(dt, variant) for dt in (0.01, 0.005, 0.0025)]
+    errs = [x[0] for x in res]
+    lo, hi = min(x[1] for x in res), max(x[2] for x in res)
+    ok = errs[2] < 5e-5 and 3.5 < errs[1] / errs[2] < 4.5 and 1.0 <= lo and hi < 2.0
+    return bool(ok), f"closed-form errors {errs}, separation in [{lo:.3f}, {hi:.3f}] (r_c,min 2)"
+
+
 def pin_noise_autocorrelation(variant=0):
     """The generated F^R has <F_{n+m} F_n> = kT a_m K_m / dt (Eq.
     stochastic_force2, self part) up to the wrap-around terms of the finite
@@ -709,6 +772,17 @@ def pin_pair_noise_two_particles(variant=0):
     at = lambda t: float(np.interp(r, np.arange(t.shape[1]) * dr, t[0]))
     worst = max(worst, _two_particle_modes(F2, W, e, u, [(e, Kd + at(fs) * 0.5 * gd, at(f) * gd),
                                                          (u, Kd + at(fsp) * 0.5 * gd, at(fp) * gd)], kT, dt))
+    # the same pair closer than the lower cutoff r_c,min = 1.5 (Sec. III B):
+    # every factor is read at r_c,min, the direction stays e
+    s3 = oracle.System(n=2, box=10.0, mass=1.0, kT=kT, dt=dt, m_max=M, r_c=2.0, r_c_min=1.5, pos=pos,
+                       vel=np.zeros((2, 3)), seed=3, variant=variant)
+    s3.set_kernels(Ks, g=g, f=f, dr=dr, gs=0.5 * g, fs=fs)
+    s3.set_perp(fp, fsp)
+    s3.set_step(11)
+    F3 = s3.pair_random_force()
+    cut = lambda t: float(np.interp(1.5, np.arange(t.shape[1]) * dr, t[0]))
+    worst = max(worst, _two_particle_modes(F3, W, e, u, [(e, Kd + cut(fs) * 0.5 * gd, cut(f) * gd),
+                                                         (u, Kd + cut(fsp) * 0.5 * gd, cut(fp) * gd)], kT, dt))
     return bool(worst < 1e-10), f"mode projections vs scalar generator {worst:.1e}"
 
 
@@ -778,4 +852,5 @@ ALL = {
     "pair_noise_two_particles": pin_pair_noise_two_particles,
     "pair_noise_covariance": pin_pair_noise_covariance,
     "perpendicular_decoupling": pin_perpendicular_decoupling,
+    "rc_min_clamp": pin_rc_min_clamp,
 }

@@ -1,6 +1,6 @@
 """A pin set is only trusted if it fails for plausible mistakes: each of these
 oracle builds carries one planted error (OR_PLANT in oracle/gldref.c, or the
-``variant`` of oracle/pairnoise.py for 11 and 12), and at least one pin must
+``variant`` of oracle/pairnoise.py for 11, 12 and 17), and at least one pin must
 reject it.  The mistakes are planted on the CPU only."""
 import pytest
 
@@ -20,6 +20,10 @@ PLANTS = {
     11: "pair blocks of the noise correlation matrix with the wrong sign",
     12: "pair-noise inverse transform scaled by 1/m_max",
     13: "perpendicular pair terms without the projection 1 - e e^T",
+    14: "pairs closer than r_c,min dropped instead of clamped",
+    15: "perpendicular factors read at the unclamped distance",
+    16: "the clamped distance used for the unit vector e",
+    17: "pair-noise radial factors read at the unclamped distance",
 }
 
 

@@ -1,7 +1,9 @@
 """The allocation-free neighbour search (gld_pairs_noalloc) returns the same
-pairs as the context-based gld_get_pairs, on two calls in a row.  It exists
-for callers that cannot allocate device memory; its scratch is a static
-device array shared by every call.  Collected last on purpose."""
+pairs as the context-based gld_get_pairs and as the oracle's FP32 brute force
+(same FP32 positions, the single-precision distance test of gld.h), on two
+calls in a row, for ragged sizes and with particles on the periodic faces.
+It exists for callers that cannot allocate device memory; its scratch is a
+static device array shared by every call.  Collected last on purpose."""
 import numpy as np
 import pytest
 
@@ -26,11 +28,28 @@ def _reference_pairs(pos, box, rc):
     return p32, want
 
 
-@pytest.mark.parametrize("n,box,rc", [(4096, 34.47, 2.0), (64, 8.0, 2.0), (20000, 60.0, 2.5)])
-def test_noalloc_pairs_match_context_pairs(n, box, rc):
+def _positions(n, box, faces, seed):
+    """Uniform FP32 positions in [0, box); with `faces`, a quarter of the
+    particles get one coordinate on a periodic face (0 or the largest FP32
+    value below box)."""
+    rng = np.random.default_rng(seed)
+    p = rng.uniform(0, box, (n, 3)).astype(np.float32)
+    if faces:
+        top = np.nextafter(np.float32(box), np.float32(0))
+        k = np.arange(0, n, 4)
+        p[k, rng.integers(0, 3, k.size)] = np.where(rng.random(k.size) < 0.5, np.float32(0), top)
+    return p.astype(np.float64)
+
+
+@pytest.mark.parametrize("n,box,rc,faces", [(4096, 34.47, 2.0, False), (64, 8.0, 2.0, False),
+                                            (20000, 60.0, 2.5, False), (77, 9.0, 2.0, True),
+                                            (20001, 60.0, 2.5, True)])
+def test_noalloc_pairs_match_context_pairs(n, box, rc, faces):
+    import oracle
     from paper_1808_00270_gb300.binding import pairs_noalloc
-    rng = np.random.default_rng(n)
-    p32, want = _reference_pairs(rng.uniform(0, box, (n, 3)), box, rc)
+    p32, want = _reference_pairs(_positions(n, box, faces, n), box, rc)
+    brute = oracle.pairs_brute_f32(p32.astype(np.float32), box, np.float32(rc * rc))
+    assert {(min(a, b), max(a, b)) for a, b in brute.tolist()} == want
     pos4 = torch.zeros((n, 4), dtype=torch.float32, device="cuda")
     pos4[:, :3] = torch.from_numpy(p32.astype(np.float32)).cuda()
     cap = 16 * n
