@@ -35,7 +35,8 @@ def test_nonfinite_velocity_latches():
     """A NaN in one velocity gives a non-finite displacement at the next step:
     the synchronizing call returns GLD_E_NONFINITE, and so does every later
     call that would launch work (the error is latched)."""
-    from paper_1808_00270_gb300 import ARR_VEL, E_NONFINITE, inputs
+    from paper_1808_00270_gb300 import ARR_VEL, inputs
+    from paper_1808_00270_gb300.binding import E_NONFINITE
     w = inputs.MEDIUM
     g = make_gpu(w)
     g.step(3)
@@ -54,7 +55,8 @@ def test_neighbour_list_overflow_latches():
     each, far above the list capacity sized for the creation density: the
     rebuild that follows the new positions reports GLD_E_STATE, and the
     context refuses to step from then on."""
-    from paper_1808_00270_gb300 import ARR_POS, E_STATE, inputs
+    from paper_1808_00270_gb300 import ARR_POS, inputs
+    from paper_1808_00270_gb300.binding import E_STATE
     w = inputs.MEDIUM
     g = make_gpu(w)
     assert g.diag()["maxnb"] < 199
@@ -91,7 +93,8 @@ def test_set_kernels_allocation_failure_leaves_no_kernels():
     GLD_E_NOMEM; the old tables are already released, so the context must
     then refuse to step (GLD_E_STATE) instead of reading them.  Setting the
     kernels again with the allocator back restores a working context."""
-    from paper_1808_00270_gb300 import E_NOMEM, E_STATE, inputs
+    from paper_1808_00270_gb300 import inputs
+    from paper_1808_00270_gb300.binding import E_NOMEM, E_STATE
     from gld_cases import kernels
     w = inputs.MEDIUM
     g = make_gpu(w)
