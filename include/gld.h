@@ -328,6 +328,23 @@ gld_status gld_set_pair_correlation(gld_ctx* ctx, int32_t nbins, double r_max);
  * [nbins] pair samples; any pointer may be NULL.  Synchronizes. */
 gld_status gld_pair_correlation(gld_ctx* ctx, double* ca, double* cc, int64_t* counts);
 
+/* Checkpoint of the observables (Sec. III A: the VACF and the pair
+ * correlations C^a, C^c accumulate over time origins, so a resumed run needs
+ * their sums and the velocities of the origins still in flight).  The blob
+ * holds the VACF sums, counts and origin count, the origin velocities (in
+ * the caller's particle order) and, when enabled, the pair-correlation sums;
+ * partials not yet added are added first.  gld_save_observables: *size
+ * receives the blob's byte size; with buf != NULL (cap >= *size, else
+ * GLD_E_INVAL) it is written.  gld_load_observables restores a blob into a
+ * context of the same n, VACF settings and pair-correlation bins (else
+ * GLD_E_INVAL) whose step index is the checkpoint's (gld_set_step first; else
+ * GLD_E_STATE).  With the rest of the state restored through gld_set_array
+ * and the same particle order, the resumed VACF and pair correlations are
+ * those of the uninterrupted run bit for bit.  Both synchronize; the caller
+ * owns buf. */
+gld_status gld_save_observables(gld_ctx* ctx, void* buf, int64_t cap, int64_t* size);
+gld_status gld_load_observables(gld_ctx* ctx, const void* buf, int64_t size);
+
 /* Device bytes the context holds (all of its buffers, 256-byte granules). */
 gld_status gld_get_bytes(gld_ctx* ctx, int64_t* bytes);
 /* Device bytes a context with these parameters will hold after gld_create

@@ -107,6 +107,8 @@ def lib():
             "gld_set_kernels_table": (i32, [vp, vp, vp, i32, C.c_double, i32, i32, C.POINTER(C.c_double)]),
             "gld_separable_terms": (i32, [vp, i32, i32, i32, vp, vp, C.POINTER(C.c_double)]),
             "gld_pair_correlation": (i32, [vp, vp, vp, vp]),
+            "gld_save_observables": (i32, [vp, vp, i64, C.POINTER(i64)]),
+            "gld_load_observables": (i32, [vp, vp, i64]),
             "gld_bytes_needed": (i32, [C.POINTER(Params), i32, i32, i32, C.POINTER(i64)]),
             "gld_batch_set_tuning": (i32, [vp, i32]),
             "gld_server_params_default": (None, [C.POINTER(ServerParams)]),
@@ -369,6 +371,18 @@ class GLD:
         cnt = np.zeros((L, nb), dtype=np.int64)
         self._check(lib().gld_pair_correlation(self._h, _ptr(ca), _ptr(cc), _ptr(cnt)))
         return ca, cc, cnt
+
+    def save_observables(self) -> bytes:
+        """The VACF and pair-correlation accumulators as an opaque blob."""
+        size = C.c_int64()
+        self._check(lib().gld_save_observables(self._h, None, 0, C.byref(size)))
+        buf = C.create_string_buffer(int(size.value))
+        self._check(lib().gld_save_observables(self._h, buf, int(size.value), C.byref(size)))
+        return buf.raw[: int(size.value)]
+
+    def load_observables(self, blob: bytes) -> None:
+        buf = C.create_string_buffer(bytes(blob), len(blob))
+        self._check(lib().gld_load_observables(self._h, buf, len(blob)))
 
     def bytes(self) -> int:
         """Device bytes this system holds."""

@@ -370,6 +370,7 @@ gld_status ctx_check_err(gld_ctx* c, unsigned err)
         if (c->latched == GLD_OK) c->latched = GLD_E_STATE;
     }
     else if (err & kErrTimeout) fail(c, GLD_E_TIMEOUT, "a bounded device wait gave up");
+    else if (err & kErrCheck) fail(c, GLD_E_CUDA, "a kernel's own bounds or alignment check failed");
     else if (err & kErrNoise) fail(c, GLD_E_CUDA, "a step ran outside its noise block");
     else if (err & kErrPnBound) {
         c->msg = "pair noise: a Gershgorin row sum of the pair matrix exceeded lambda (set a larger one)";
@@ -1556,6 +1557,113 @@ gld_status gld_pair_correlation(gld_ctx* c, double* ca, double* cc, int64_t* cou
         if (counts) counts[k] = sn[k];
     }
     return GLD_OK;
+}
+
+// Checkpoint of the observables.  Layout of the blob (native byte order):
+// header, VACF sums [L] f64, counts [L] i64, origins so far (i64), origin
+// velocities [n_os][n][4] f32 in the caller's particle order, then, when the
+// pair correlations are on, their sums a and c [L][nbins] f64 and counts
+// [L][nbins] i64.  Pending per-step partials are folded in first (the same
+// additions, in the same order, as the next VACF launch would make).
+namespace {
+struct ObsHeader {
+    uint64_t magic;
+    int32_t version, n, vacf_len, vacf_stride, n_os, pc_nbins;
+    int64_t vacf_burnin, step;
+};
+constexpr uint64_t kObsMagic = 0x31534256444C47ull;  // "GLDVBS1"
+
+size_t obs_bytes(const StepParams& P)
+{
+    const size_t L = (size_t)std::max(P.vacf_len, 0), cells = L * (size_t)std::max(P.pc_nbins, 0);
+    return sizeof(ObsHeader) + 16 * L + 8 + 16 * (size_t)P.n_os * P.n + 24 * cells;
+}
+}  // namespace
+
+gld_status gld_save_observables(gld_ctx* c, void* buf, int64_t cap, int64_t* size)
+{
+    if (!c || !size || cap < 0) return GLD_E_INVAL;
+    const StepParams& P = c->P;
+    const size_t need = obs_bytes(P);
+    *size = (int64_t)need;
+    if (!buf) return GLD_OK;
+    if ((size_t)cap < need) return fail(c, GLD_E_INVAL, "gld_save_observables: buffer smaller than *size");
+    if (c->latched == GLD_OK && P.vacf_len > 0) GLD_CUDA(c, launch_vacf_flush(P, c->B, c->st));
+    if (c->latched == GLD_OK && P.pc_nbins > 0) GLD_CUDA(c, launch_pcorr_flush(P, c->B, c->st));
+    GLD_TRY(sync_and_check(c));
+    unsigned char* o = (unsigned char*)buf;
+    ObsHeader h{kObsMagic, 1, P.n, P.vacf_len, P.vacf_stride, P.n_os, P.pc_nbins, P.vacf_burnin, c->host_step};
+    std::memcpy(o, &h, sizeof(h));
+    o += sizeof(h);
+    const size_t L = (size_t)std::max(P.vacf_len, 0);
+    if (L > 0) {
+        GLD_CUDA(c, cudaMemcpy(o, c->B.csum, 8 * L, cudaMemcpyDeviceToHost));
+        GLD_CUDA(c, cudaMemcpy(o + 8 * L, c->B.ccnt, 8 * L, cudaMemcpyDeviceToHost));
+        GLD_CUDA(c, cudaMemcpy(o + 16 * L, c->B.norig, 8, cudaMemcpyDeviceToHost));
+    } else {
+        std::memset(o + 16 * L, 0, 8);
+    }
+    o += 16 * L + 8;
+    if (P.n_os > 0) {
+        std::vector<float4> v((size_t)P.n_os * P.n);
+        GLD_CUDA(c, cudaMemcpy(v.data(), c->B.vorig, sizeof(float4) * v.size(), cudaMemcpyDeviceToHost));
+        float4* dst = (float4*)o;  // caller's order
+        for (int q = 0; q < P.n_os; ++q)
+            for (int i = 0; i < P.n; ++i) std::memcpy(dst + (size_t)q * P.n + c->int2ext[i], &v[(size_t)q * P.n + i], 16);
+        o += 16 * v.size();
+    }
+    if (P.pc_nbins > 0) {
+        const size_t cells = L * P.pc_nbins;
+        GLD_CUDA(c, cudaMemcpy(o, c->B.pc_sa, 8 * cells, cudaMemcpyDeviceToHost));
+        GLD_CUDA(c, cudaMemcpy(o + 8 * cells, c->B.pc_sc, 8 * cells, cudaMemcpyDeviceToHost));
+        GLD_CUDA(c, cudaMemcpy(o + 16 * cells, c->B.pc_n, 8 * cells, cudaMemcpyDeviceToHost));
+    }
+    return GLD_OK;
+}
+
+gld_status gld_load_observables(gld_ctx* c, const void* buf, int64_t size)
+{
+    if (!c || !buf || size < (int64_t)sizeof(ObsHeader)) return GLD_E_INVAL;
+    const StepParams& P = c->P;
+    ObsHeader h{};
+    std::memcpy(&h, buf, sizeof(h));
+    if (h.magic != kObsMagic || h.version != 1 || (size_t)size != obs_bytes(P) || h.n != P.n ||
+        h.vacf_len != P.vacf_len || h.vacf_stride != P.vacf_stride || h.n_os != P.n_os ||
+        h.pc_nbins != P.pc_nbins || h.vacf_burnin != P.vacf_burnin)
+        return fail(c, GLD_E_INVAL, "gld_load_observables: the blob belongs to another configuration");
+    if (h.step != c->host_step)
+        return fail(c, GLD_E_STATE, "gld_load_observables: set the step index of the checkpoint first");
+    GLD_TRY(sync_and_check(c));
+    const unsigned char* o = (const unsigned char*)buf + sizeof(h);
+    const size_t L = (size_t)std::max(P.vacf_len, 0);
+    if (L > 0) {
+        GLD_CUDA(c, cudaMemcpy(c->B.csum, o, 8 * L, cudaMemcpyHostToDevice));
+        GLD_CUDA(c, cudaMemcpy(c->B.ccnt, o + 8 * L, 8 * L, cudaMemcpyHostToDevice));
+        GLD_CUDA(c, cudaMemcpy(c->B.norig, o + 16 * L, 8, cudaMemcpyHostToDevice));
+    }
+    o += 16 * L + 8;
+    if (P.n_os > 0) {
+        std::vector<float4> v((size_t)P.n_os * P.n);
+        const float4* src = (const float4*)o;
+        for (int q = 0; q < P.n_os; ++q)
+            for (int i = 0; i < P.n; ++i) std::memcpy(&v[(size_t)q * P.n + i], src + (size_t)q * P.n + c->int2ext[i], 16);
+        GLD_CUDA(c, cudaMemcpy(c->B.vorig, v.data(), sizeof(float4) * v.size(), cudaMemcpyHostToDevice));
+        o += 16 * v.size();
+    }
+    if (P.pc_nbins > 0) {
+        const size_t cells = L * P.pc_nbins;
+        GLD_CUDA(c, cudaMemcpy(c->B.pc_sa, o, 8 * cells, cudaMemcpyHostToDevice));
+        GLD_CUDA(c, cudaMemcpy(c->B.pc_sc, o + 8 * cells, 8 * cells, cudaMemcpyHostToDevice));
+        GLD_CUDA(c, cudaMemcpy(c->B.pc_n, o + 16 * cells, 8 * cells, cudaMemcpyHostToDevice));
+        GLD_CUDA(c, cudaMemsetAsync(c->B.pc_step, 0, sizeof(long long) * 2 * 3 * (size_t)P.n_os * P.pc_nbins, c->st));
+    }
+    // nothing pending from before the checkpoint
+    const int zero = 0;
+    GLD_CUDA(c, cudaMemcpyAsync(&c->B.ctrl->vacf_pending, &zero, sizeof(int), cudaMemcpyHostToDevice, c->st));
+    GLD_CUDA(c, cudaMemcpyAsync(&c->B.ctrl->pv_nact, &zero, sizeof(int), cudaMemcpyHostToDevice, c->st));
+    GLD_CUDA(c, cudaMemcpyAsync(&c->B.ctrl->pc_pending, &zero, sizeof(int), cudaMemcpyHostToDevice, c->st));
+    GLD_CUDA(c, cudaMemcpyAsync(&c->B.ctrl->pc_pv_nact, &zero, sizeof(int), cudaMemcpyHostToDevice, c->st));
+    return sync_and_check(c);
 }
 
 const char* gld_last_error(const gld_ctx* c) { return c ? c->msg.c_str() : "null context"; }

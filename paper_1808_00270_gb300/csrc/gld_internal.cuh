@@ -22,7 +22,8 @@ constexpr int kMaxNoiseBlock = 64;  // register-resident outputs per FIR thread
 constexpr int kMaxPnDegree = 16;    // Chebyshev degree of the pair-correlated noise
 
 // Latched device error bits.
-enum : unsigned { kErrNonFinite = 1u, kErrTimeout = 2u, kErrNoise = 4u, kErrNbrOverflow = 8u, kErrPnBound = 16u };
+enum : unsigned { kErrNonFinite = 1u, kErrTimeout = 2u, kErrNoise = 4u, kErrNbrOverflow = 8u, kErrPnBound = 16u,
+                  kErrCheck = 32u };
 
 // Device control block: the step counter lives on the device so that a
 // captured graph of several steps can be replayed without new arguments.

@@ -178,6 +178,16 @@ __global__ void __launch_bounds__(kTcThreads) fir_tc(const __grid_constant__ CUt
     uint32_t* misc = (uint32_t*)(mdone + 2);                     // TMEM base
 
     const int tid = threadIdx.x, warp = tid >> 5;
+    {
+        // the layout below must fit the dynamic shared memory of the launch
+        uint32_t dyn;
+        asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+        const size_t used = (size_t)(sm - sm_raw) + (size_t)kTcStages * kTcStageBytes + 32 * (size_t)nrows + 64;
+        if (used > dyn) {
+            if (tid == 0) atomicOr(&ctrl->err, kErrCheck);
+            return;  // uniform: before any barrier or tensor-memory use
+        }
+    }
     const int H = P.H, T = P.T;
     const long long n0 = ctrl->step;
     const long long np3 = 3LL * P.n_pad;
@@ -205,6 +215,7 @@ __global__ void __launch_bounds__(kTcThreads) fir_tc(const __grid_constant__ CUt
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the taps, for the tensor cores
+    __syncwarp();  // .sync.aligned tcgen05 instructions need the whole warp converged
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&misc[0])),
                      "r"(kTcCols)
@@ -215,6 +226,8 @@ __global__ void __launch_bounds__(kTcThreads) fir_tc(const __grid_constant__ CUt
     __syncthreads();
     tc_fence_after();
     const uint32_t tm = misc[0];
+    // the allocation must be lane 0 and leave room for the 192 columns used
+    const bool tm_ok = (tm >> 16) == 0 && (tm & 0xFFFFu) + 192u <= 512u;
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     const uint32_t rhi = smem_u32(Rhi), rlo = smem_u32(Rlo);
 
@@ -226,8 +239,14 @@ __global__ void __launch_bounds__(kTcThreads) fir_tc(const __grid_constant__ CUt
         const int st = (int)(g % kTcStages);
         long long slot = (t_lo + (long long)kTcChunk * c) % P.lw;
         if (slot < 0) slot += P.lw;
+        const long long x = (long long)tile * 128;
+        if (x >= np3 || (slot & 31) || slot + kTcChunk > P.lw) {  // never for a valid launch
+            atomicOr(&ctrl->err, kErrCheck);
+            mbar_expect_tx(&full[st], 0);  // completes the phase without a copy
+            return;
+        }
         mbar_expect_tx(&full[st], kTcStageBytes);
-        tma_load_2d(stage + (size_t)st * kTcStageFloats, &wmap, tile * 128, (int)slot, &full[st]);
+        tma_load_2d(stage + (size_t)st * kTcStageFloats, &wmap, (int)x, (int)slot, &full[st]);
     };
     if (tid == 0)
         for (; issued < G && issued < kTcStages - 1; ++issued) issue(issued);
@@ -235,8 +254,9 @@ __global__ void __launch_bounds__(kTcThreads) fir_tc(const __grid_constant__ CUt
     // A wait that runs out makes this thread `bad`; the CTA learns of it at the
     // next barrier (__syncthreads_or: the same answer in every thread) and
     // stops streaming.
-    bool bad = false, aborted = false;
+    bool bad = !tm_ok, aborted = false;
     long long g_stop = G;
+    if (!tm_ok && tid == 0) atomicOr(&ctrl->err, kErrCheck);
     for (long long g = 0; g < G; ++g) {
         const int i = (int)(g / nch), c = (int)(g - (long long)i * nch);
         const int tile = (int)blockIdx.x + i * (int)gridDim.x;
@@ -245,7 +265,7 @@ __global__ void __launch_bounds__(kTcThreads) fir_tc(const __grid_constant__ CUt
         if (!mbar_wait(&full[st], (uint32_t)((g / kTcStages) & 1))) bad = true;
         if (g >= 2 && !mbar_wait(&mdone[ab], (uint32_t)(((g - 2) >> 1) & 1))) bad = true;
         // this thread's stream: 32 window rows, zero outside the real window
-        {
+        if (tm_ok) {
             uint32_t hv[32], lv[32];
             const float* sp = stage + (size_t)st * kTcStageFloats + tid;
 #pragma unroll
@@ -257,6 +277,7 @@ __global__ void __launch_bounds__(kTcThreads) fir_tc(const __grid_constant__ CUt
                 lv[r] = __float_as_uint(v - __uint_as_float(hv[r]));
             }
             const uint32_t ta = tm + lane_base + 64u + 64u * (uint32_t)ab;
+            __syncwarp();  // lanes leave the waits above at different times
             tmem_st32(ta, hv);
             tmem_st32(ta + 32u, lv);
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
@@ -273,6 +294,10 @@ __global__ void __launch_bounds__(kTcThreads) fir_tc(const __grid_constant__ CUt
             for (int s = 0; s < 4; ++s) {
                 const int k0 = kTcChunk * c + 8 * s;
                 const uint32_t u0 = (uint32_t)(k0 - a - 63 + kTcRowOff);
+                if (u0 + 68u > (uint32_t)nrows) {  // never for a valid launch
+                    atomicOr(&ctrl->err, kErrCheck);
+                    continue;
+                }
                 const uint64_t dh = smem_desc(rhi + 16u * u0, 64u, 128u);
                 const uint64_t dl = smem_desc(rlo + 16u * u0, 64u, 128u);
                 const uint32_t ah = tm + 64u + 64u * (uint32_t)ab + 8u * (uint32_t)s, al = ah + 32u;
@@ -285,11 +310,13 @@ __global__ void __launch_bounds__(kTcThreads) fir_tc(const __grid_constant__ CUt
         }
         if (c == nch - 1) {  // the tile is complete: D to F^R (column n is t = 63 - n)
             if (!mbar_wait(&mdone[ab], (uint32_t)((g >> 1) & 1))) bad = true;
+            __syncwarp();  // thread 0 issued the MMAs alone; lanes leave the wait at different times
             tc_fence_after();
             const long long j = (long long)tile * 128 + tid;
 #pragma unroll
             for (int half = 0; half < 2; ++half) {
                 uint32_t d[32];
+                __syncwarp();
                 tmem_ld32(tm + lane_base + 32u * (uint32_t)half, d);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 if (j < np3)
@@ -311,6 +338,7 @@ __global__ void __launch_bounds__(kTcThreads) fir_tc(const __grid_constant__ CUt
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
+        __syncwarp();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(kTcCols) : "memory");
     }
     if (tid == 0) {

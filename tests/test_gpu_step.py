@@ -126,6 +126,67 @@ def test_checkpoint_resume_is_bit_identical():
     assert np.array_equal(pa, pb) and np.array_equal(va, vb)
 
 
+def test_checkpoint_of_observables_resumes_bit_identical():
+    """A checkpoint taken after the VACF burn-in, with ten origins in flight
+    and the pair correlations on: the run resumed from the state arrays plus
+    gld_save_observables / gld_load_observables returns the VACF and C^a, C^c
+    of the uninterrupted run bit for bit; without the observables blob the
+    resumed sums differ (they restart at zero)."""
+    from paper_1808_00270_gb300 import ARR_DISP, ARR_FC, ARR_HIST, ARR_POS, ARR_VEL
+    w = _w("gld_n4096_m200")
+    kw = dict(vacf_len=100, vacf_stride=10, vacf_burnin=50)
+    a = make_gpu(w, **kw)
+    a.set_pair_correlation(8, w.r_c)
+    a.step(237)
+    snap = {k: a.get(k) for k in (ARR_POS, ARR_VEL, ARR_FC, ARR_HIST, ARR_DISP)}
+    blob = a.save_observables()
+    _, n_orig = a.vacf()
+    assert n_orig == 19  # origins at 50, 60, ..., 230; the last ten in flight
+    step = a.step_index
+
+    def resumed(load):
+        b = make_gpu(w, pos=snap[ARR_POS], vel=snap[ARR_VEL], order=a.order(), **kw)
+        b.set_pair_correlation(8, w.r_c)
+        b.set_step(step)
+        for k in (ARR_POS, ARR_VEL, ARR_FC, ARR_HIST, ARR_DISP):
+            b.set(k, snap[k])
+        if load:
+            b.load_observables(blob)
+        b.step(150)
+        return b
+
+    b, c = resumed(True), resumed(False)
+    a.step(150)
+    (ca, na), (cb, nb), (cc_, nc) = a.vacf(), b.vacf(), c.vacf()
+    assert na == nb == 34 and nc == 15
+    assert np.array_equal(ca, cb, equal_nan=True)
+    assert not np.array_equal(ca, cc_, equal_nan=True)
+    for x, y in zip(a.pair_correlation(), b.pair_correlation()):
+        assert np.array_equal(x, y, equal_nan=True)
+    assert not np.array_equal(a.pair_correlation()[2], c.pair_correlation()[2])
+
+
+def test_observables_blob_checks_its_configuration():
+    from paper_1808_00270_gb300 import GLDError
+    from paper_1808_00270_gb300.binding import E_INVAL, E_STATE
+    w = _w("gld_n4096_m200")
+    a = make_gpu(w, vacf_len=100, vacf_stride=10, vacf_burnin=50)
+    a.step(120)
+    blob = a.save_observables()
+    other = make_gpu(w, vacf_len=50, vacf_stride=10, vacf_burnin=50)
+    other.set_step(120)
+    with pytest.raises(GLDError) as e:
+        other.load_observables(blob)
+    assert e.value.status == E_INVAL
+    same = make_gpu(w, vacf_len=100, vacf_stride=10, vacf_burnin=50)
+    with pytest.raises(GLDError) as e:
+        same.load_observables(blob)  # step index not restored first
+    assert e.value.status == E_STATE
+    same.set_step(120)
+    same.load_observables(blob)
+    assert same.vacf()[1] == a.vacf()[1]
+
+
 def test_any_internal_order_matches_oracle():
     """The internal storage order is invisible: a random order gives the same
     one-step forces (to rounding) in the caller's order."""
