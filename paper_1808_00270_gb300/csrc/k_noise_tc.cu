@@ -12,24 +12,31 @@
 //
 // Precision: the tensor cores read FP32 operands as TF32 (the low 13 mantissa
 // bits dropped).  Each operand is split into a TF32 part and the FP32
-// remainder, and three products are accumulated in FP32,
-//     W_hi A_hi + W_hi A_lo + W_lo A_hi,
-// which keeps the result within about 3e-7 of the FP32 sum (the dropped
-// W_lo A_lo term and the remainders' own truncation are below 2^-21).
+// remainder, and three products are accumulated,
+//     W_hi A_hi + W_hi A_lo + W_lo A_hi
+// (the dropped W_lo A_lo term and the remainders' own truncation are below
+// 2^-21 of each product).  The tensor cores' FP32 accumulation rounds toward
+// zero; summed over a whole window (up to 750 MMAs at m_max = 1000) that bias
+// reached 1.2e-5 of F^R, so each 32-row chunk accumulates into a fresh TMEM
+// accumulator and the chunks are added on the FP32 pipes with round-to-
+// nearest: about 4e-7 of the FP32 sum at any m_max (measured, and emulated
+// on the CPU).
 //
 // Layout, per CTA (128 threads, one stream per thread and TMEM lane):
 //   * W tiles [32 rows][128 streams] arrive by TMA (cp.async.bulk.tensor,
 //     three stages, mbarrier completion); rows outside the real window are
 //     replaced by zero, the rest split into hi / lo and stored into TMEM
-//     (two A buffers of 64 columns: hi in the first 32, lo in the last 32).
+//     (A buffers of 64 columns at 128 and 192: hi in the first 32, lo in the
+//     last 32).
 //   * B is never materialised per K step: shared memory holds the taps as
 //     overlapping rows R[u] = (Acp[u - 94 + e], e < 4) (hi and lo copies),
 //     and the K-major descriptor of K step k0 starts at row k0 - a + 31, with
 //     8-row groups 128 bytes apart (SBO) and the second 4-column group 64
 //     bytes on (LBO).  With output column n standing for t = 63 - n, both
 //     offsets are positive.
-//   * The accumulator D [128 lanes][64 columns] FP32 lives in TMEM; one
-//     elected thread issues the MMAs and commits them to an mbarrier.
+//   * Chunk g accumulates into D[g & 1] [128 lanes][64 columns] FP32 in TMEM
+//     (columns 0 and 64); one thread issues the MMAs and commits them to an
+//     mbarrier; two chunks later the threads add D into registers.
 // CTAs are persistent over tiles (two per SM: 256 TMEM columns each).
 // Every wait is bounded: a wait that runs out sets kErrTimeout, and the CTA
 // drains its copies and MMAs (bounded again), frees its TMEM and returns.
@@ -49,7 +56,7 @@ constexpr int kTcStages = 3;
 constexpr int kTcChunk = 32;                               // window rows per stage (4 K steps)
 constexpr int kTcStageFloats = kTcChunk * 128;
 constexpr int kTcStageBytes = kTcStageFloats * 4;          // 16 KB
-constexpr uint32_t kTcCols = 256;                          // D [0, 64), A buffers [64, 128), [128, 192)
+constexpr uint32_t kTcCols = 256;                          // D buffers [0, 128), A buffers [128, 256)
 constexpr int kTcRowOff = 94;                              // R[u] holds Acp[u - kTcRowOff + e]
 constexpr long long kTcWaitCycles = 2000000000LL;          // about one second
 
@@ -226,8 +233,8 @@ __global__ void __launch_bounds__(kTcThreads) fir_tc(const __grid_constant__ CUt
     __syncthreads();
     tc_fence_after();
     const uint32_t tm = misc[0];
-    // the allocation must be lane 0 and leave room for the 192 columns used
-    const bool tm_ok = (tm >> 16) == 0 && (tm & 0xFFFFu) + 192u <= 512u;
+    // the allocation must start at lane 0 and hold the columns used
+    const bool tm_ok = (tm >> 16) == 0 && (tm & 0xFFFFu) + kTcCols <= 512u;
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     const uint32_t rhi = smem_u32(Rhi), rlo = smem_u32(Rlo);
 
@@ -251,6 +258,36 @@ __global__ void __launch_bounds__(kTcThreads) fir_tc(const __grid_constant__ CUt
     if (tid == 0)
         for (; issued < G && issued < kTcStages - 1; ++issued) issue(issued);
 
+    // Chunk g accumulates into a fresh D[g & 1] from A[g & 1]; two iterations
+    // later (when both buffers are needed again) the threads add D into FP32
+    // registers with round-to-nearest.  The tensor cores' own accumulation
+    // rounds toward zero, and over the ~100-750 MMAs of a whole window that
+    // bias reaches 1e-5 of the result; per chunk it stays near 4e-7.
+    float acc[64];
+#pragma unroll
+    for (int q = 0; q < 64; ++q) acc[q] = 0.f;
+    auto fold = [&](long long gg) {  // all threads; D[gg & 1] holds chunk gg
+        const int fi = (int)(gg / nch), fc = (int)(gg - (long long)fi * nch);
+        __syncwarp();
+        tc_fence_after();
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            uint32_t d[32];
+            tmem_ld32(tm + lane_base + 64u * (uint32_t)(gg & 1) + 32u * (uint32_t)half, d);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int q = 0; q < 32; ++q) acc[32 * half + q] = __fadd_rn(acc[32 * half + q], __uint_as_float(d[q]));
+        }
+        if (fc == nch - 1) {  // the tile is complete: to F^R (column n is t = 63 - n)
+            const long long j = ((long long)blockIdx.x + (long long)fi * gridDim.x) * 128 + tid;
+            if (j < np3)
+#pragma unroll
+                for (int q = 0; q < 64; ++q) out[(size_t)(63 - q) * np3 + j] = acc[q];
+#pragma unroll
+            for (int q = 0; q < 64; ++q) acc[q] = 0.f;
+        }
+    };
+
     // A wait that runs out makes this thread `bad`; the CTA learns of it at the
     // next barrier (__syncthreads_or: the same answer in every thread) and
     // stops streaming.
@@ -259,11 +296,15 @@ __global__ void __launch_bounds__(kTcThreads) fir_tc(const __grid_constant__ CUt
     if (!tm_ok && tid == 0) atomicOr(&ctrl->err, kErrCheck);
     for (long long g = 0; g < G; ++g) {
         const int i = (int)(g / nch), c = (int)(g - (long long)i * nch);
-        const int tile = (int)blockIdx.x + i * (int)gridDim.x;
         const int st = (int)(g % kTcStages), ab = (int)(g & 1);
+        (void)i;
         if (tid == 0 && issued < G && issued <= g + kTcStages - 1) issue(issued++);
         if (!mbar_wait(&full[st], (uint32_t)((g / kTcStages) & 1))) bad = true;
-        if (g >= 2 && !mbar_wait(&mdone[ab], (uint32_t)(((g - 2) >> 1) & 1))) bad = true;
+        // A[ab] and D[ab] are free once the MMAs of chunk g - 2 are done
+        if (g >= 2) {
+            if (!mbar_wait(&mdone[ab], (uint32_t)(((g - 2) >> 1) & 1))) bad = true;
+            if (tm_ok) fold(g - 2);
+        }
         // this thread's stream: 32 window rows, zero outside the real window
         if (tm_ok) {
             uint32_t hv[32], lv[32];
@@ -276,7 +317,7 @@ __global__ void __launch_bounds__(kTcThreads) fir_tc(const __grid_constant__ CUt
                 hv[r] = tf32_rna(v);
                 lv[r] = __float_as_uint(v - __uint_as_float(hv[r]));
             }
-            const uint32_t ta = tm + lane_base + 64u + 64u * (uint32_t)ab;
+            const uint32_t ta = tm + lane_base + 128u + 64u * (uint32_t)ab;
             __syncwarp();  // lanes leave the waits above at different times
             tmem_st32(ta, hv);
             tmem_st32(ta + 32u, lv);
@@ -290,6 +331,7 @@ __global__ void __launch_bounds__(kTcThreads) fir_tc(const __grid_constant__ CUt
         }
         if (tid == 0) {
             tc_fence_after();
+            const uint32_t dd = tm + 64u * (uint32_t)ab;
 #pragma unroll
             for (int s = 0; s < 4; ++s) {
                 const int k0 = kTcChunk * c + 8 * s;
@@ -300,33 +342,24 @@ __global__ void __launch_bounds__(kTcThreads) fir_tc(const __grid_constant__ CUt
                 }
                 const uint64_t dh = smem_desc(rhi + 16u * u0, 64u, 128u);
                 const uint64_t dl = smem_desc(rlo + 16u * u0, 64u, 128u);
-                const uint32_t ah = tm + 64u + 64u * (uint32_t)ab + 8u * (uint32_t)s, al = ah + 32u;
-                mma_tf32(tm, ah, dh, (c > 0 || s > 0) ? 1u : 0u);
-                mma_tf32(tm, ah, dl, 1u);
-                mma_tf32(tm, al, dh, 1u);
+                const uint32_t ah = tm + 128u + 64u * (uint32_t)ab + 8u * (uint32_t)s, al = ah + 32u;
+                mma_tf32(dd, ah, dh, s > 0 ? 1u : 0u);
+                mma_tf32(dd, ah, dl, 1u);
+                mma_tf32(dd, al, dh, 1u);
             }
             mma_commit(&mdone[ab]);
             committed = g;
         }
-        if (c == nch - 1) {  // the tile is complete: D to F^R (column n is t = 63 - n)
-            if (!mbar_wait(&mdone[ab], (uint32_t)((g >> 1) & 1))) bad = true;
-            __syncwarp();  // thread 0 issued the MMAs alone; lanes leave the wait at different times
-            tc_fence_after();
-            const long long j = (long long)tile * 128 + tid;
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                uint32_t d[32];
-                __syncwarp();
-                tmem_ld32(tm + lane_base + 32u * (uint32_t)half, d);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (j < np3)
-#pragma unroll
-                    for (int q = 0; q < 32; ++q) out[(size_t)(63 - (32 * half + q)) * np3 + j] = __uint_as_float(d[q]);
-            }
-            tc_fence_before();
-        }
     }
+    // the last two chunks: wait for their MMAs, agree on the outcome, fold
+    const long long g_last0 = G >= 2 ? G - 2 : 0;
+    if (!aborted)
+        for (long long gg = g_last0; gg < G; ++gg)
+            if (!mbar_wait(&mdone[gg & 1], (uint32_t)((gg >> 1) & 1))) bad = true;
     if (__syncthreads_or(bad)) aborted = true;
+    if (!aborted && tm_ok)
+        for (long long gg = g_last0; gg < G; ++gg) fold(gg);
+    tc_fence_before();
     if (aborted && tid == 0) {
         atomicOr(&ctrl->err, kErrTimeout);
         // drain (bounded): tile loads still in flight, then the last MMAs
