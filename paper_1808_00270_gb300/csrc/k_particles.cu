@@ -17,8 +17,8 @@
 //
 // Every neighbour sum runs over a Verlet list with the exact FP32 r < r_c test
 // of the cell traversal, so the pair set is the same; lists are sorted by
-// neighbour id, so the order of every sum does not depend on when the list was
-// built.  Particles are stored in the Morton order of their cells at creation
+// neighbour id at each build, so the order of every sum does not depend on
+// when the list was built.  Particles are stored in the Morton order of their cells at creation
 // and a thread handles one particle id, so own loads are coalesced and
 // neighbours lie close in memory; ids never change, so the displacement
 // history is never permuted.
@@ -37,6 +37,7 @@ constexpr int kPairLanes = kBatchPairLanes;  // lanes per particle in the one-te
 constexpr int kCforceLanes = kBatchCforceLanes;  // lanes per particle in the F^C kernel
 constexpr int kCellThreads = kBatchCellChunk;
 constexpr int kThreads = kBatchPartBlock;
+constexpr int kNbrSortCap = 128;  // list entries sorted by id at each build
 static_assert(kBatchVacfBlock == kThreads, "vacf blocks share the particle block size");
 
 __device__ __forceinline__ float dot3(float ax, float ay, float az, float bx, float by, float bz)
@@ -428,17 +429,30 @@ __device__ __forceinline__ void nbr_build_body(const StepParams& P, Ctrl* __rest
     const int id = __float_as_int(pi.w);
     const int stride = P.n_pad, cap = P.maxnb;
     int c = 0;
-    // the traversal order is fixed (stencil cells in order, each cell's
-    // particles by increasing id), so the lists and every sum over them are
-    // reproducible without sorting
+    // Candidates are collected in traversal order and sorted by id, so the
+    // order of every sum over a list does not depend on the cell layout at
+    // the time the list was built (a run resumed from a checkpoint, which
+    // builds its lists at the resume step, gives the same bits).  Entries
+    // beyond the first kNbrSortCap (far above any workload's lists) keep the
+    // traversal order.
+    int loc[kNbrSortCap];
     for_each_in_stencil(pi, id, pos_sorted, cell_start, P, P.rl2, [&](int jd, float, float, float, float) {
-        if (c < cap) nbr[(size_t)c * stride + id] = jd;
+        if (c < kNbrSortCap) loc[c] = jd;
+        else if (c < cap) nbr[(size_t)c * stride + id] = jd;
         ++c;
     });
     if (c > cap) {
         atomicOr(&ctrl->err, kErrNbrOverflow);
         c = cap;
     }
+    const int ns = c < kNbrSortCap ? c : kNbrSortCap;
+    for (int s = 1; s < ns; ++s) {
+        const int v = loc[s];
+        int q = s;
+        for (; q > 0 && loc[q - 1] > v; --q) loc[q] = loc[q - 1];
+        loc[q] = v;
+    }
+    for (int s = 0; s < ns; ++s) nbr[(size_t)s * stride + id] = loc[s];
     nbr_cnt[id] = c;
     perm[k] = id;
     disp_build[id] = disp[id];
