@@ -4,8 +4,8 @@
 // For a block of T = 64 steps starting at n0, Eq. noise_production gives per
 // stream j (a particle's component) and t < 64
 //     F^R[t][j] = sum_{s=-H}^{H} A_s W[n0 + t + s][j],          H = m_max - 1.
-// Over a window of times t_lo + k (k < 32 nch, t_lo = n0 - H rounded down to a
-// multiple of 32, a = n0 - H - t_lo) this is the product
+// Over a window of times t_lo + k (t_lo = n0 - H rounded down to a multiple
+// of 32, a = n0 - H - t_lo) this is the product
 //     F^R[t][j] = sum_k W[t_lo + k][j] B[k][t],   B[k][t] = A_{k - a - t - H},
 // a GEMM with M = streams (128 per tile), N = 64 outputs and K = window rows,
 // whose B operand is a Toeplitz matrix of the taps (zero outside |s| <= H).
@@ -20,26 +20,32 @@
 // reached 1.2e-5 of F^R, so each 32-row chunk accumulates into a fresh TMEM
 // accumulator and the chunks are added on the FP32 pipes with round-to-
 // nearest: about 4e-7 of the FP32 sum at any m_max (measured, and emulated
-// on the CPU).
+// on the CPU).  Every 32-row chunk starts at a time that is a multiple of 32,
+// so an output's sum does not depend on where its 64-step block started.
 //
-// Layout, per CTA (128 threads, one stream per thread and TMEM lane):
-//   * W tiles [32 rows][128 streams] arrive by TMA (cp.async.bulk.tensor,
-//     three stages, mbarrier completion); rows outside the real window are
-//     replaced by zero, the rest split into hi / lo and stored into TMEM
-//     (A buffers of 64 columns at 128 and 192: hi in the first 32, lo in the
-//     last 32).
-//   * B is never materialised per K step: shared memory holds the taps as
-//     overlapping rows R[u] = (Acp[u - 94 + e], e < 4) (hi and lo copies),
-//     and the K-major descriptor of K step k0 starts at row k0 - a + 31, with
-//     8-row groups 128 bytes apart (SBO) and the second 4-column group 64
-//     bytes on (LBO).  With output column n standing for t = 63 - n, both
-//     offsets are positive.
-//   * Chunk g accumulates into D[g & 1] [128 lanes][64 columns] FP32 in TMEM
-//     (columns 0 and 64); one thread issues the MMAs and commits them to an
-//     mbarrier; two chunks later the threads add D into registers.
-// CTAs are persistent over tiles (two per SM: 256 TMEM columns each).
-// Every wait is bounded: a wait that runs out sets kErrTimeout, and the CTA
-// drains its copies and MMAs (bounded again), frees its TMEM and returns.
+// B is never materialised per K step: shared memory holds the taps as
+// overlapping rows R[u] = (Acp[u - 94 + e], e < 4) (TF32 part and remainder),
+// and the K-major descriptor of K step k0 starts at row k0 - a + 31, with
+// 8-row groups 128 bytes apart (SBO) and the second 4-column group 64 bytes
+// on (LBO).  With output column n standing for t = 63 - n, both offsets are
+// positive.
+//
+// One persistent CTA per SM (all 512 TMEM columns), warp-specialized and
+// linked by mbarriers, so that loads, conversions, MMAs and accumulation of
+// different chunks overlap:
+//   warp 0, one thread  TMA loads of W tiles [32 rows][128 streams] into a
+//                       ring of shared-memory stages;
+//   warp 1, one thread  the MMAs of a chunk (4 K steps x 3 products) into one
+//                       of four TMEM accumulators D, from one of four TMEM A
+//                       buffers; owns the TMEM allocation;
+//   warps 4-7           converters: a stage's rows (zero outside the real
+//                       window) split into TF32 part / remainder and stored
+//                       into an A buffer (thread = stream = TMEM lane);
+//   warps 8-11          accumulators: D read back and added in FP32 registers;
+//                       at the last chunk of a tile, F^R written out.
+// Every wait is bounded: a wait that runs out sets kErrTimeout and a shared
+// abort flag that ends every role's loop; the CTA then lets its copies and
+// MMAs finish (bounded again), frees its TMEM and returns.
 #include <algorithm>
 
 #include <cuda.h>
@@ -51,12 +57,14 @@ namespace gld {
 
 namespace {
 
-constexpr int kTcThreads = 128;
-constexpr int kTcStages = 3;
+constexpr int kTcThreads = 384;                            // 12 warps (roles above)
+constexpr int kTcMaxStages = 8;
 constexpr int kTcChunk = 32;                               // window rows per stage (4 K steps)
 constexpr int kTcStageFloats = kTcChunk * 128;
 constexpr int kTcStageBytes = kTcStageFloats * 4;          // 16 KB
-constexpr uint32_t kTcCols = 256;                          // D buffers [0, 128), A buffers [128, 256)
+constexpr int kTcNA = 4, kTcND = 4;                        // TMEM A buffers and accumulators
+constexpr uint32_t kTcCols = 512;                          // D [0, 256), A [256, 512)
+constexpr uint32_t kTcAcol = 64u * kTcND;
 constexpr int kTcRowOff = 94;                              // R[u] holds Acp[u - kTcRowOff + e]
 constexpr long long kTcWaitCycles = 2000000000LL;          // about one second
 
@@ -100,6 +108,34 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity)
         if (it == 0) t0 = clock64();
         else if (clock64() - t0 > kTcWaitCycles) return false;
     }
+}
+
+// As mbar_wait, but also gives up when another role raised the CTA's abort
+// flag; raises it on a timeout.
+__device__ __forceinline__ bool mbar_wait_ab(uint64_t* b, uint32_t parity, volatile int* abort_flag)
+{
+    const uint32_t a = smem_u32(b);
+    long long t0 = 0;
+    for (int it = 0;; ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(a), "r"(parity)
+                     : "memory");
+        if (done) return true;
+        if (*abort_flag) return false;
+        if (it == 0) t0 = clock64();
+        else if (clock64() - t0 > kTcWaitCycles) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar)
@@ -163,34 +199,48 @@ __host__ __device__ inline int tc_nch_max(int H, int T) { return (31 + 2 * H + T
 // Rows of the overlapping tap array: every K-step tile of any window offset.
 __host__ __device__ inline int tc_rows(int H, int T) { return kTcChunk * tc_nch_max(H, T) + 91; }
 
-size_t tc_smem_bytes(int H, int T)
+constexpr size_t kTcBarBytes = 8 * (2 * kTcMaxStages + 2 * kTcNA + 2 * kTcND) + 16;
+
+// Load stages that fit beside the taps (at most 8, at least 2).
+int tc_stages(int H, int T)
 {
-    const size_t b = 1024 + (size_t)kTcStages * kTcStageBytes + 2 * (size_t)tc_rows(H, T) * 16 + 64;
-    // at least 80 KB: at most two CTAs (2 x 256 TMEM columns) share an SM
-    return b < 80 * 1024 ? 80 * 1024 : b;
+    const long long room = 227LL * 1024 - 1024 - 2LL * tc_rows(H, T) * 16 - (long long)kTcBarBytes;
+    return (int)std::max(0LL, std::min<long long>(kTcMaxStages, room / kTcStageBytes));
 }
 
-__global__ void __launch_bounds__(kTcThreads) fir_tc(const __grid_constant__ CUtensorMap wmap, const StepParams P,
-                                                     Ctrl* __restrict__ ctrl, const float* __restrict__ taps,
-                                                     float* __restrict__ out, int nrows)
+size_t tc_smem_bytes(int H, int T)
+{
+    const size_t b = 1024 + (size_t)tc_stages(H, T) * kTcStageBytes + 2 * (size_t)tc_rows(H, T) * 16 + kTcBarBytes;
+    // at least 116 KB: a second CTA (which would wait for the TMEM) never shares an SM
+    return std::max<size_t>(b, 116 * 1024);
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) fir_tc(const __grid_constant__ CUtensorMap wmap, const StepParams P,
+                                                        Ctrl* __restrict__ ctrl, const float* __restrict__ taps,
+                                                        float* __restrict__ out, int nrows, int nst)
 {
     extern __shared__ unsigned char sm_raw[];
     const uint32_t raw = smem_u32(sm_raw);
     unsigned char* sm = sm_raw + (((raw + 1023u) & ~1023u) - raw);
-    float* stage = (float*)sm;                                   // [kTcStages][32][128]
-    float* Rhi = (float*)(sm + (size_t)kTcStages * kTcStageBytes);  // [nrows][4]
+    float* stage = (float*)sm;                                       // [nst][32][128]
+    float* Rhi = (float*)(sm + (size_t)nst * kTcStageBytes);         // [nrows][4]
     float* Rlo = Rhi + 4 * (size_t)nrows;
-    uint64_t* full = (uint64_t*)(Rlo + 4 * (size_t)nrows);       // [kTcStages]
-    uint64_t* mdone = full + kTcStages;                          // [2]: MMAs of A buffer b done
-    uint32_t* misc = (uint32_t*)(mdone + 2);                     // TMEM base
+    uint64_t* full = (uint64_t*)(Rlo + 4 * (size_t)nrows);           // [nst]  stage loaded
+    uint64_t* empty = full + kTcMaxStages;                           // [nst]  stage read
+    uint64_t* afull = empty + kTcMaxStages;                          // [NA]   A buffer written
+    uint64_t* aempty = afull + kTcNA;                                // [NA]   A buffer read by the MMAs
+    uint64_t* dfull = aempty + kTcNA;                                // [ND]   accumulator complete
+    uint64_t* dempty = dfull + kTcND;                                // [ND]   accumulator read back
+    uint32_t* misc = (uint32_t*)(dempty + kTcND);                    // TMEM base
+    volatile int* abort_flag = (volatile int*)(misc + 1);
 
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     {
-        // the layout below must fit the dynamic shared memory of the launch
+        // the layout must fit the dynamic shared memory of the launch
         uint32_t dyn;
         asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
-        const size_t used = (size_t)(sm - sm_raw) + (size_t)kTcStages * kTcStageBytes + 32 * (size_t)nrows + 64;
-        if (used > dyn) {
+        const size_t used = (size_t)(sm - sm_raw) + (size_t)nst * kTcStageBytes + 32 * (size_t)nrows + kTcBarBytes;
+        if (used > dyn || nst < 2 || nst > kTcMaxStages) {
             if (tid == 0) atomicOr(&ctrl->err, kErrCheck);
             return;  // uniform: before any barrier or tensor-memory use
         }
@@ -216,14 +266,24 @@ __global__ void __launch_bounds__(kTcThreads) fir_tc(const __grid_constant__ CUt
         Rlo[idx] = v - hi;
     }
     if (tid == 0) {
-        for (int s = 0; s < kTcStages; ++s) mbar_init(&full[s], 1);
-        mbar_init(&mdone[0], 1);
-        mbar_init(&mdone[1], 1);
+        for (int s = 0; s < nst; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 4);
+        }
+        for (int b = 0; b < kTcNA; ++b) {
+            mbar_init(&afull[b], 4);
+            mbar_init(&aempty[b], 1);
+        }
+        for (int d = 0; d < kTcND; ++d) {
+            mbar_init(&dfull[d], 1);
+            mbar_init(&dempty[d], 4);
+        }
+        *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the taps, for the tensor cores
     __syncwarp();  // .sync.aligned tcgen05 instructions need the whole warp converged
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&misc[0])),
                      "r"(kTcCols)
                      : "memory");
@@ -233,105 +293,42 @@ __global__ void __launch_bounds__(kTcThreads) fir_tc(const __grid_constant__ CUt
     __syncthreads();
     tc_fence_after();
     const uint32_t tm = misc[0];
-    // the allocation must start at lane 0 and hold the columns used
-    const bool tm_ok = (tm >> 16) == 0 && (tm & 0xFFFFu) + kTcCols <= 512u;
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-    const uint32_t rhi = smem_u32(Rhi), rlo = smem_u32(Rlo);
+    // the allocation must start at lane 0 and column 0 (all 512 columns)
+    if ((tm & 0xFFFF0000u) != 0 || (tm & 0xFFFFu) != 0) {
+        if (tid == 0) atomicOr(&ctrl->err, kErrCheck);
+        *abort_flag = 1;
+    }
+    __syncthreads();
+    const bool ok0 = *abort_flag == 0;
 
-    long long issued = 0;     // chunks whose tile load was issued (thread 0)
-    long long committed = -1; // last chunk whose MMAs were committed (thread 0)
-    auto issue = [&](long long g) {
-        const int i = (int)(g / nch), c = (int)(g - (long long)i * nch);
-        const int tile = (int)blockIdx.x + i * (int)gridDim.x;
-        const int st = (int)(g % kTcStages);
-        long long slot = (t_lo + (long long)kTcChunk * c) % P.lw;
-        if (slot < 0) slot += P.lw;
-        const long long x = (long long)tile * 128;
-        if (x >= np3 || (slot & 31) || slot + kTcChunk > P.lw) {  // never for a valid launch
-            atomicOr(&ctrl->err, kErrCheck);
-            mbar_expect_tx(&full[st], 0);  // completes the phase without a copy
-            return;
-        }
-        mbar_expect_tx(&full[st], kTcStageBytes);
-        tma_load_2d(stage + (size_t)st * kTcStageFloats, &wmap, (int)x, (int)slot, &full[st]);
-    };
-    if (tid == 0)
-        for (; issued < G && issued < kTcStages - 1; ++issued) issue(issued);
-
-    // Chunk g accumulates into a fresh D[g & 1] from A[g & 1]; two iterations
-    // later (when both buffers are needed again) the threads add D into FP32
-    // registers with round-to-nearest.  The tensor cores' own accumulation
-    // rounds toward zero, and over the ~100-750 MMAs of a whole window that
-    // bias reaches 1e-5 of the result; per chunk it stays near 4e-7.
-    float acc[64];
-#pragma unroll
-    for (int q = 0; q < 64; ++q) acc[q] = 0.f;
-    auto fold = [&](long long gg) {  // all threads; D[gg & 1] holds chunk gg
-        const int fi = (int)(gg / nch), fc = (int)(gg - (long long)fi * nch);
-        __syncwarp();
-        tc_fence_after();
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            uint32_t d[32];
-            tmem_ld32(tm + lane_base + 64u * (uint32_t)(gg & 1) + 32u * (uint32_t)half, d);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-            for (int q = 0; q < 32; ++q) acc[32 * half + q] = __fadd_rn(acc[32 * half + q], __uint_as_float(d[q]));
-        }
-        if (fc == nch - 1) {  // the tile is complete: to F^R (column n is t = 63 - n)
-            const long long j = ((long long)blockIdx.x + (long long)fi * gridDim.x) * 128 + tid;
-            if (j < np3)
-#pragma unroll
-                for (int q = 0; q < 64; ++q) out[(size_t)(63 - q) * np3 + j] = acc[q];
-#pragma unroll
-            for (int q = 0; q < 64; ++q) acc[q] = 0.f;
-        }
-    };
-
-    // A wait that runs out makes this thread `bad`; the CTA learns of it at the
-    // next barrier (__syncthreads_or: the same answer in every thread) and
-    // stops streaming.
-    bool bad = !tm_ok, aborted = false;
-    long long g_stop = G;
-    if (!tm_ok && tid == 0) atomicOr(&ctrl->err, kErrCheck);
-    for (long long g = 0; g < G; ++g) {
-        const int i = (int)(g / nch), c = (int)(g - (long long)i * nch);
-        const int st = (int)(g % kTcStages), ab = (int)(g & 1);
-        (void)i;
-        if (tid == 0 && issued < G && issued <= g + kTcStages - 1) issue(issued++);
-        if (!mbar_wait(&full[st], (uint32_t)((g / kTcStages) & 1))) bad = true;
-        // A[ab] and D[ab] are free once the MMAs of chunk g - 2 are done
-        if (g >= 2) {
-            if (!mbar_wait(&mdone[ab], (uint32_t)(((g - 2) >> 1) & 1))) bad = true;
-            if (tm_ok) fold(g - 2);
-        }
-        // this thread's stream: 32 window rows, zero outside the real window
-        if (tm_ok) {
-            uint32_t hv[32], lv[32];
-            const float* sp = stage + (size_t)st * kTcStageFloats + tid;
-#pragma unroll
-            for (int r = 0; r < 32; ++r) {
-                const int k = kTcChunk * c + r;
-                float v = sp[r * 128];
-                v = (k >= a && k < a + nk) ? v : 0.f;
-                hv[r] = tf32_rna(v);
-                lv[r] = __float_as_uint(v - __uint_as_float(hv[r]));
+    long long committed = -1;  // MMA thread: last chunk whose MMAs were committed
+    if (ok0 && warp == 0 && lane == 0) {
+        // ---- producer: TMA loads of the window's 32-row tiles ---------------
+        for (long long g = 0; g < G; ++g) {
+            const int i = (int)(g / nch), c = (int)(g - (long long)i * nch);
+            const int s = (int)(g % nst);
+            if (g >= nst && !mbar_wait_ab(&empty[s], (uint32_t)((g / nst - 1) & 1), abort_flag)) break;
+            long long slot = (t_lo + (long long)kTcChunk * c) % P.lw;
+            if (slot < 0) slot += P.lw;
+            const long long x = ((long long)blockIdx.x + (long long)i * gridDim.x) * 128;
+            if (x >= np3 || (slot & 31) || slot + kTcChunk > P.lw) {  // never for a valid launch
+                atomicOr(&ctrl->err, kErrCheck);
+                *abort_flag = 1;
+                break;
             }
-            const uint32_t ta = tm + lane_base + 128u + 64u * (uint32_t)ab;
-            __syncwarp();  // lanes leave the waits above at different times
-            tmem_st32(ta, hv);
-            tmem_st32(ta + 32u, lv);
-            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            mbar_expect_tx(&full[s], kTcStageBytes);
+            tma_load_2d(stage + (size_t)s * kTcStageFloats, &wmap, (int)x, (int)slot, &full[s]);
         }
-        tc_fence_before();
-        if (__syncthreads_or(bad)) {
-            aborted = true;
-            g_stop = g;
-            break;
-        }
-        if (tid == 0) {
+    } else if (ok0 && warp == 1 && lane == 0) {
+        // ---- MMA issuer ---------------------------------------------------------
+        const uint32_t rhi = smem_u32(Rhi), rlo = smem_u32(Rlo);
+        for (long long g = 0; g < G; ++g) {
+            const int c = (int)(g % nch);
+            const int b = (int)(g % kTcNA), d = (int)(g % kTcND);
+            if (!mbar_wait_ab(&afull[b], (uint32_t)((g / kTcNA) & 1), abort_flag)) break;
+            if (g >= kTcND && !mbar_wait_ab(&dempty[d], (uint32_t)((g / kTcND - 1) & 1), abort_flag)) break;
             tc_fence_after();
-            const uint32_t dd = tm + 64u * (uint32_t)ab;
+            const uint32_t dd = tm + 64u * (uint32_t)d;
 #pragma unroll
             for (int s = 0; s < 4; ++s) {
                 const int k0 = kTcChunk * c + 8 * s;
@@ -342,34 +339,93 @@ __global__ void __launch_bounds__(kTcThreads) fir_tc(const __grid_constant__ CUt
                 }
                 const uint64_t dh = smem_desc(rhi + 16u * u0, 64u, 128u);
                 const uint64_t dl = smem_desc(rlo + 16u * u0, 64u, 128u);
-                const uint32_t ah = tm + 128u + 64u * (uint32_t)ab + 8u * (uint32_t)s, al = ah + 32u;
+                const uint32_t ah = tm + kTcAcol + 64u * (uint32_t)b + 8u * (uint32_t)s, al = ah + 32u;
                 mma_tf32(dd, ah, dh, s > 0 ? 1u : 0u);
                 mma_tf32(dd, ah, dl, 1u);
                 mma_tf32(dd, al, dh, 1u);
             }
-            mma_commit(&mdone[ab]);
+            mma_commit(&aempty[b]);
+            mma_commit(&dfull[d]);
             committed = g;
         }
+    } else if (ok0 && warp >= 4 && warp < 8) {
+        // ---- converters: stage rows -> TF32 part / remainder in TMEM ------------
+        const int ct = tid - 128;  // stream within the tile = TMEM lane
+        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+        for (long long g = 0; g < G; ++g) {
+            const int c = (int)(g % nch);
+            const int s = (int)(g % nst), b = (int)(g % kTcNA);
+            bool okw = mbar_wait_ab(&full[s], (uint32_t)((g / nst) & 1), abort_flag);
+            if (okw && g >= kTcNA) okw = mbar_wait_ab(&aempty[b], (uint32_t)((g / kTcNA - 1) & 1), abort_flag);
+            if (!__all_sync(0xffffffffu, okw)) break;  // the same decision in every lane
+            uint32_t hv[32], lv[32];
+            const float* sp = stage + (size_t)s * kTcStageFloats + ct;
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {
+                const int k = kTcChunk * c + r;
+                const float v = (k >= a && k < a + nk) ? sp[r * 128] : 0.f;
+                hv[r] = tf32_rna(v);
+                lv[r] = __float_as_uint(v - __uint_as_float(hv[r]));
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);  // the stage may be loaded again
+            const uint32_t ta = tm + lane_base + kTcAcol + 64u * (uint32_t)b;
+            tmem_st32(ta, hv);
+            tmem_st32(ta + 32u, lv);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&afull[b]);
+        }
+    } else if (ok0 && warp >= 8) {
+        // ---- accumulators: D -> FP32 registers, F^R at the end of a tile -------
+        const int ft = tid - 256;
+        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+        float acc[64];
+#pragma unroll
+        for (int q = 0; q < 64; ++q) acc[q] = 0.f;
+        for (long long g = 0; g < G; ++g) {
+            const int i = (int)(g / nch), c = (int)(g - (long long)i * nch);
+            const int d = (int)(g % kTcND);
+            const bool okw = mbar_wait_ab(&dfull[d], (uint32_t)((g / kTcND) & 1), abort_flag);
+            if (!__all_sync(0xffffffffu, okw)) break;
+            tc_fence_after();
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                uint32_t dv[32];
+                tmem_ld32(tm + lane_base + 64u * (uint32_t)d + 32u * (uint32_t)half, dv);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int q = 0; q < 32; ++q) acc[32 * half + q] = __fadd_rn(acc[32 * half + q], __uint_as_float(dv[q]));
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&dempty[d]);
+            if (c == nch - 1) {  // the tile is complete: to F^R (column n is t = 63 - n)
+                const long long j = ((long long)blockIdx.x + (long long)i * gridDim.x) * 128 + ft;
+                if (j < np3)
+#pragma unroll
+                    for (int q = 0; q < 64; ++q) out[(size_t)(63 - q) * np3 + j] = acc[q];
+#pragma unroll
+                for (int q = 0; q < 64; ++q) acc[q] = 0.f;
+            }
+        }
     }
-    // the last two chunks: wait for their MMAs, agree on the outcome, fold
-    const long long g_last0 = G >= 2 ? G - 2 : 0;
-    if (!aborted)
-        for (long long gg = g_last0; gg < G; ++gg)
-            if (!mbar_wait(&mdone[gg & 1], (uint32_t)((gg >> 1) & 1))) bad = true;
-    if (__syncthreads_or(bad)) aborted = true;
-    if (!aborted && tm_ok)
-        for (long long gg = g_last0; gg < G; ++gg) fold(gg);
-    tc_fence_before();
-    if (aborted && tid == 0) {
-        atomicOr(&ctrl->err, kErrTimeout);
-        // drain (bounded): tile loads still in flight, then the last MMAs
-        for (long long gg = g_stop; gg < issued; ++gg)
-            mbar_wait(&full[gg % kTcStages], (uint32_t)((gg / kTcStages) & 1));
-        if (committed >= 0) mbar_wait(&mdone[committed & 1], (uint32_t)((committed >> 1) & 1));
+    __syncthreads();
+    if (*abort_flag) {
+        if (tid == 0) atomicOr(&ctrl->err, kErrTimeout);
+        // let copies and MMAs still in flight finish before the memory goes
+        if (warp == 1 && lane == 0 && committed >= 0)
+            mbar_wait(&dfull[committed % kTcND], (uint32_t)((committed / kTcND) & 1));
+        if (tid == 0) {
+            const long long t0 = clock64();
+            while (clock64() - t0 < 200000) {
+            }
+        }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 1) {
         tc_fence_after();
         __syncwarp();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(kTcCols) : "memory");
@@ -390,7 +446,8 @@ __global__ void __launch_bounds__(kTcThreads) fir_tc(const __grid_constant__ CUt
 
 bool noise_filter_tc_ok(const StepParams& P)
 {
-    return P.T == 64 && P.lw % kTcChunk == 0 && P.lw >= 2LL * P.H + P.T + 31 && tc_smem_bytes(P.H, P.T) <= 227 * 1024;
+    return P.T == 64 && P.lw % kTcChunk == 0 && P.lw >= 2LL * P.H + P.T + 31 && tc_stages(P.H, P.T) >= 2 &&
+           tc_smem_bytes(P.H, P.T) <= 227 * 1024;
 }
 
 cudaError_t make_noise_ring_map(void* W, const StepParams& P, CUtensorMap* map)
@@ -421,8 +478,8 @@ cudaError_t launch_noise_filter_tc(const StepParams& P, Ctrl* ctrl, const CUtens
     cudaError_t e = cudaFuncSetAttribute(fir_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const long long ntiles = (3LL * P.n_pad + 127) / 128;
-    const int grid = (int)std::min<long long>(ntiles, 2LL * std::max(num_sms, 1));
-    fir_tc<<<grid, kTcThreads, smem, st>>>(*wmap, P, ctrl, taps, out, tc_rows(P.H, P.T));
+    const int grid = (int)std::min<long long>(ntiles, std::max(num_sms, 1));
+    fir_tc<<<grid, kTcThreads, smem, st>>>(*wmap, P, ctrl, taps, out, tc_rows(P.H, P.T), tc_stages(P.H, P.T));
     return cudaGetLastError();
 }
 
