@@ -10,23 +10,27 @@
 // a GEMM with M = streams (128 per tile), N = 64 outputs and K = window rows,
 // whose B operand is a Toeplitz matrix of the taps (zero outside |s| <= H).
 //
-// Precision: the tensor cores read FP32 operands as TF32 (the low 13 mantissa
-// bits dropped).  Each operand is split into a TF32 part and the FP32
-// remainder, and three products are accumulated,
-//     W_hi A_hi + W_hi A_lo + W_lo A_hi
-// (the dropped W_lo A_lo term and the remainders' own truncation are below
-// 2^-21 of each product).  The tensor cores' FP32 accumulation rounds toward
-// zero; summed over a whole window (up to 750 MMAs at m_max = 1000) that bias
-// reached 1.2e-5 of F^R, so each 32-row chunk accumulates into a fresh TMEM
-// accumulator and the chunks are added on the FP32 pipes with round-to-
-// nearest: about 4e-7 of the FP32 sum at any m_max (measured, and emulated
-// on the CPU).  Every 32-row chunk starts at a time that is a multiple of 32,
-// so an output's sum does not depend on where its 64-step block started.
+// Precision: the products run in FP16 (kind::f16, K = 16 per MMA, FP32
+// accumulation); FP16 keeps 11 significant bits, so each operand is split into
+// an FP16 part and its remainder scaled by 2^11 (again FP16), and
+//     F = D1 + 2^-11 D2,   D1 = W_hi A_hi,   D2 = W_hi A_lo + W_lo A_hi,
+// which drops only W_lo A_lo (2^-22 of a product).  The taps are first scaled
+// by a power of two that puts the largest one in [2^14, 2^15) (FP16 range;
+// undone exactly at the end).  The tensor cores' FP32 accumulation rounds
+// toward zero; summed over a whole window (hundreds of MMAs) that bias reached
+// 1.2e-5 of F^R, so each 32-row chunk accumulates into fresh TMEM accumulators
+// and the chunks are added on the FP32 pipes with round-to-nearest: about
+// 1e-7 to 2e-7 of the FP32 sum at m_max = 200 ... 1000 (measured, and emulated
+// on the CPU).  A 16-bit MMA costs the same tensor-pipe time as a TF32 one
+// with half the K (about 96 cycles for N <= 128, measured), so this takes half
+// the MMAs of a TF32 split.  Every 32-row chunk starts at a time that is a
+// multiple of 32, so an output's sum does not depend on where its 64-step
+// block started.
 //
-// B is never materialised per K step: shared memory holds the taps as
-// overlapping rows R[u] = (Acp[u - 94 + e], e < 4) (TF32 part and remainder),
+// B is never materialised per K step: shared memory holds the scaled taps as
+// overlapping FP16 rows R[u] = (Acp[u - 94 + e], e < 8) (hi and lo parts),
 // and the K-major descriptor of K step k0 starts at row k0 - a + 31, with
-// 8-row groups 128 bytes apart (SBO) and the second 4-column group 64 bytes
+// 8-row groups 128 bytes apart (SBO) and the second 8-column group 128 bytes
 // on (LBO).  With output column n standing for t = 63 - n, both offsets are
 // positive.
 //
@@ -35,12 +39,12 @@
 // different chunks overlap:
 //   warp 0, one thread  TMA loads of W tiles [32 rows][128 streams] into a
 //                       ring of shared-memory stages;
-//   warp 1, one thread  the MMAs of a chunk (4 K steps x 3 products) into one
-//                       of four TMEM accumulators D, from one of four TMEM A
-//                       buffers; owns the TMEM allocation;
+//   warp 1, one thread  the MMAs of a chunk (2 K steps x 3 products) into one
+//                       of three TMEM accumulator pairs (D1, D2), from one of
+//                       four TMEM A buffers; owns the TMEM allocation;
 //   warps 4-7           converters: a stage's rows (zero outside the real
-//                       window) split into TF32 part / remainder and stored
-//                       into an A buffer (thread = stream = TMEM lane);
+//                       window) split into FP16 parts and stored into an A
+//                       buffer (thread = stream = TMEM lane);
 //   warps 8-11          accumulators: D read back and added in FP32 registers;
 //                       at the last chunk of a tile, F^R written out.
 // Every wait is bounded: a wait that runs out sets kErrTimeout and a shared
@@ -49,6 +53,7 @@
 #include <algorithm>
 
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
 #include "launch.h"
@@ -62,24 +67,17 @@ constexpr int kTcMaxStages = 8;
 constexpr int kTcChunk = 32;                               // window rows per stage (4 K steps)
 constexpr int kTcStageFloats = kTcChunk * 128;
 constexpr int kTcStageBytes = kTcStageFloats * 4;          // 16 KB
-constexpr int kTcNA = 4, kTcND = 4;                        // TMEM A buffers and accumulators
-constexpr uint32_t kTcCols = 512;                          // D [0, 256), A [256, 512)
-constexpr uint32_t kTcAcol = 64u * kTcND;
+constexpr int kTcNA = 4, kTcND = 3;                        // TMEM A buffers and accumulator pairs
+constexpr uint32_t kTcCols = 512;                          // D pairs [0, 384), A [384, 512)
+constexpr uint32_t kTcAcol = 128u * kTcND;
 constexpr int kTcRowOff = 94;                              // R[u] holds Acp[u - kTcRowOff + e]
 constexpr long long kTcWaitCycles = 2000000000LL;          // about one second
 
-// Instruction descriptor of tcgen05.mma kind::tf32: D FP32, A and B TF32,
+// Instruction descriptor of tcgen05.mma kind::f16: D FP32, A and B FP16,
 // both K-major, N = 64, M = 128.
-constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t kTcIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint32_t tf32_rna(float v)
-{
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
-    return r;
-}
 
 __device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count)
 {
@@ -152,10 +150,10 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t accumulate)
+__device__ __forceinline__ void mma_f16(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t accumulate)
 {
     asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}"
                  ::"r"(d), "r"(a), "l"(bdesc), "r"(kTcIdesc), "r"(accumulate)
                  : "memory");
 }
@@ -166,27 +164,31 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar)
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32])
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16])
 {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-                 "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};"
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                 "%13, %14, %15, %16};"
                  ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]),
                  "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
-                 "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]),
-                 "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]),
-                 "r"(v[31])
+                 "r"(v[15])
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
+// FP16 part of v and its remainder scaled by 2^11 (as FP16 bit patterns)
+__device__ __forceinline__ void split_f16(float v, uint32_t& hi, uint32_t& lo)
 {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-                 "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+    const __half h = __float2half_rn(v);
+    hi = __half_as_ushort(h);
+    lo = __half_as_ushort(__float2half_rn((v - __half2float(h)) * 2048.0f));
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                 "%13, %14, %15}, [%16];"
                  : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
                    "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                   "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                   "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                   "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                   "=r"(v[15])
                  : "r"(taddr)
                  : "memory");
 }
@@ -223,9 +225,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) fir_tc(const __grid_constant__ 
     const uint32_t raw = smem_u32(sm_raw);
     unsigned char* sm = sm_raw + (((raw + 1023u) & ~1023u) - raw);
     float* stage = (float*)sm;                                       // [nst][32][128]
-    float* Rhi = (float*)(sm + (size_t)nst * kTcStageBytes);         // [nrows][4]
-    float* Rlo = Rhi + 4 * (size_t)nrows;
-    uint64_t* full = (uint64_t*)(Rlo + 4 * (size_t)nrows);           // [nst]  stage loaded
+    __half* Rhi = (__half*)(sm + (size_t)nst * kTcStageBytes);       // [nrows][8]
+    __half* Rlo = Rhi + 8 * (size_t)nrows;
+    uint64_t* full = (uint64_t*)(Rlo + 8 * (size_t)nrows);           // [nst]  stage loaded
     uint64_t* empty = full + kTcMaxStages;                           // [nst]  stage read
     uint64_t* afull = empty + kTcMaxStages;                          // [NA]   A buffer written
     uint64_t* aempty = afull + kTcNA;                                // [NA]   A buffer read by the MMAs
@@ -233,6 +235,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fir_tc(const __grid_constant__ 
     uint64_t* dempty = dfull + kTcND;                                // [ND]   accumulator read back
     uint32_t* misc = (uint32_t*)(dempty + kTcND);                    // TMEM base
     volatile int* abort_flag = (volatile int*)(misc + 1);
+    int* red = (int*)(misc + 2);                                     // largest tap (bit pattern)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     {
@@ -257,13 +260,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) fir_tc(const __grid_constant__ 
     const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const long long G = (long long)my_tiles * nch;  // chunks this CTA streams
 
-    // taps as overlapping rows, TF32 part and remainder
-    for (int idx = tid; idx < 4 * nrows; idx += kTcThreads) {
-        const int sig = (idx >> 2) - kTcRowOff + (idx & 3);
-        const float v = (sig >= 0 && sig <= 2 * H) ? __ldg(taps + sig) : 0.f;
-        const float hi = __uint_as_float(tf32_rna(v));
-        Rhi[idx] = hi;
-        Rlo[idx] = v - hi;
+    // the taps scaled by 2^ks (largest in [2^14, 2^15)) as overlapping FP16
+    // rows, FP16 part and 2^11-scaled remainder
+    if (tid == 0) *red = 0;
+    __syncthreads();
+    {
+        float mx = 0.f;
+        for (int sig = tid; sig <= 2 * H; sig += kTcThreads) mx = fmaxf(mx, fabsf(__ldg(taps + sig)));
+        if (mx > 0.f) atomicMax(red, __float_as_int(mx));  // non-negative floats order as ints
+    }
+    __syncthreads();
+    const float amax = __int_as_float(*red);
+    const int ks = amax > 0.f ? max(-60, min(60, 14 - ilogbf(amax))) : 0;
+    for (int idx = tid; idx < 8 * nrows; idx += kTcThreads) {
+        const int sig = (idx >> 3) - kTcRowOff + (idx & 7);
+        const float v = (sig >= 0 && sig <= 2 * H) ? ldexpf(__ldg(taps + sig), ks) : 0.f;
+        uint32_t hb, lb;
+        split_f16(v, hb, lb);
+        Rhi[idx] = __ushort_as_half((unsigned short)hb);
+        Rlo[idx] = __ushort_as_half((unsigned short)lb);
     }
     if (tid == 0) {
         for (int s = 0; s < nst; ++s) {
@@ -328,21 +343,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) fir_tc(const __grid_constant__ 
             if (!mbar_wait_ab(&afull[b], (uint32_t)((g / kTcNA) & 1), abort_flag)) break;
             if (g >= kTcND && !mbar_wait_ab(&dempty[d], (uint32_t)((g / kTcND - 1) & 1), abort_flag)) break;
             tc_fence_after();
-            const uint32_t dd = tm + 64u * (uint32_t)d;
+            const uint32_t d1 = tm + 128u * (uint32_t)d, d2 = d1 + 64u;
 #pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                const int k0 = kTcChunk * c + 8 * s;
+            for (int s = 0; s < 2; ++s) {
+                const int k0 = kTcChunk * c + 16 * s;
                 const uint32_t u0 = (uint32_t)(k0 - a - 63 + kTcRowOff);
-                if (u0 + 68u > (uint32_t)nrows) {  // never for a valid launch
+                if (u0 + 72u > (uint32_t)nrows) {  // never for a valid launch
                     atomicOr(&ctrl->err, kErrCheck);
                     continue;
                 }
-                const uint64_t dh = smem_desc(rhi + 16u * u0, 64u, 128u);
-                const uint64_t dl = smem_desc(rlo + 16u * u0, 64u, 128u);
-                const uint32_t ah = tm + kTcAcol + 64u * (uint32_t)b + 8u * (uint32_t)s, al = ah + 32u;
-                mma_tf32(dd, ah, dh, s > 0 ? 1u : 0u);
-                mma_tf32(dd, ah, dl, 1u);
-                mma_tf32(dd, al, dh, 1u);
+                const uint64_t dh = smem_desc(rhi + 16u * u0, 128u, 128u);
+                const uint64_t dl = smem_desc(rlo + 16u * u0, 128u, 128u);
+                const uint32_t ah = tm + kTcAcol + 32u * (uint32_t)b + 8u * (uint32_t)s, al = ah + 16u;
+                mma_f16(d1, ah, dh, s > 0 ? 1u : 0u);
+                mma_f16(d2, ah, dl, s > 0 ? 1u : 0u);
+                mma_f16(d2, al, dh, 1u);
             }
             mma_commit(&aempty[b]);
             mma_commit(&dfull[d]);
@@ -358,20 +373,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) fir_tc(const __grid_constant__ 
             bool okw = mbar_wait_ab(&full[s], (uint32_t)((g / nst) & 1), abort_flag);
             if (okw && g >= kTcNA) okw = mbar_wait_ab(&aempty[b], (uint32_t)((g / kTcNA - 1) & 1), abort_flag);
             if (!__all_sync(0xffffffffu, okw)) break;  // the same decision in every lane
-            uint32_t hv[32], lv[32];
+            uint32_t hv[16], lv[16];  // two FP16 per column, the earlier row in the low half
             const float* sp = stage + (size_t)s * kTcStageFloats + ct;
 #pragma unroll
-            for (int r = 0; r < 32; ++r) {
+            for (int r = 0; r < 32; r += 2) {
                 const int k = kTcChunk * c + r;
-                const float v = (k >= a && k < a + nk) ? sp[r * 128] : 0.f;
-                hv[r] = tf32_rna(v);
-                lv[r] = __float_as_uint(v - __uint_as_float(hv[r]));
+                const float v0 = (k >= a && k < a + nk) ? sp[r * 128] : 0.f;
+                const float v1 = (k + 1 >= a && k + 1 < a + nk) ? sp[(r + 1) * 128] : 0.f;
+                uint32_t h0, l0, h1, l1;
+                split_f16(v0, h0, l0);
+                split_f16(v1, h1, l1);
+                hv[r >> 1] = h0 | (h1 << 16);
+                lv[r >> 1] = l0 | (l1 << 16);
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);  // the stage may be loaded again
-            const uint32_t ta = tm + lane_base + kTcAcol + 64u * (uint32_t)b;
-            tmem_st32(ta, hv);
-            tmem_st32(ta + 32u, lv);
+            const uint32_t ta = tm + lane_base + kTcAcol + 32u * (uint32_t)b;
+            tmem_st16(ta, hv);
+            tmem_st16(ta + 16u, lv);
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             tc_fence_before();
             __syncwarp();
@@ -391,12 +410,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) fir_tc(const __grid_constant__ 
             if (!__all_sync(0xffffffffu, okw)) break;
             tc_fence_after();
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                uint32_t dv[32];
-                tmem_ld32(tm + lane_base + 64u * (uint32_t)d + 32u * (uint32_t)half, dv);
+            for (int part = 0; part < 4; ++part) {
+                uint32_t dv1[16], dv2[16];
+                tmem_ld16(tm + lane_base + 128u * (uint32_t)d + 16u * (uint32_t)part, dv1);
+                tmem_ld16(tm + lane_base + 128u * (uint32_t)d + 64u + 16u * (uint32_t)part, dv2);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                for (int q = 0; q < 32; ++q) acc[32 * half + q] = __fadd_rn(acc[32 * half + q], __uint_as_float(dv[q]));
+                for (int q = 0; q < 16; ++q)
+                    acc[16 * part + q] = __fadd_rn(acc[16 * part + q],
+                                                   __fmaf_rn(__uint_as_float(dv2[q]), 1.0f / 2048.0f, __uint_as_float(dv1[q])));
             }
             tc_fence_before();
             __syncwarp();
@@ -405,7 +427,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fir_tc(const __grid_constant__ 
                 const long long j = ((long long)blockIdx.x + (long long)i * gridDim.x) * 128 + ft;
                 if (j < np3)
 #pragma unroll
-                    for (int q = 0; q < 64; ++q) out[(size_t)(63 - q) * np3 + j] = acc[q];
+                    for (int q = 0; q < 64; ++q) out[(size_t)(63 - q) * np3 + j] = ldexpf(acc[q], -ks);
 #pragma unroll
                 for (int q = 0; q < 64; ++q) acc[q] = 0.f;
             }
