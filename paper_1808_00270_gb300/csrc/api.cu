@@ -185,15 +185,16 @@ gld_status rebuild_cells_and_fc(gld_ctx* c)
 cudaError_t launch_noise(gld_ctx* c, cudaStream_t s)
 {
     const StepParams& P = c->P;
+    const CUtensorMap* wmap = c->have_wmap ? &c->wmap : nullptr;
     if (P.pn_deg <= 0)
-        return launch_noise_block(P, c->B.ctrl, c->W, c->Acp, c->la, c->B.frblock, c->prm.seed, c->d_int2ext, true,
+        return launch_noise_block(P, c->B.ctrl, c->W, c->Acp, c->la, c->B.frblock, c->prm.seed, c->d_int2ext, wmap,
                                   c->num_sms, s);
     // pair-correlated noise: Z_0 .. Z_deg from one white-noise window
     cudaError_t e = launch_noise_block(P, c->B.ctrl, c->W, c->d_pntaps, c->la, c->B.frblock, c->prm.seed,
-                                       c->d_int2ext, true, c->num_sms, s);
+                                       c->d_int2ext, wmap, c->num_sms, s);
     for (int k = 1; k <= P.pn_deg && e == cudaSuccess; ++k)
         e = launch_noise_filter(P, c->B.ctrl, c->W, c->d_pntaps + (size_t)k * c->la,
-                                c->d_zblk + (size_t)(k - 1) * P.T * 3 * P.n_pad, true, c->num_sms, s);
+                                c->d_zblk + (size_t)(k - 1) * P.T * 3 * P.n_pad, wmap, c->num_sms, s);
     return e;
 }
 
@@ -610,6 +611,10 @@ gld_status gld_create(const gld_params* p, const double* pos, const double* vel,
         gld_destroy(c);
         return GLD_E_NOMEM;
     }
+    // tensor map of the white-noise ring for the tensor-core filter (the
+    // filter runs on the FP32 pipes when it cannot be made)
+    c->have_wmap = noise_filter_tc_ok(P) && make_noise_ring_map(c->W, P, &c->wmap) == cudaSuccess;
+    cudaGetLastError();
     gld_status s = GLD_OK;
     if (cudaMemsetAsync(B.cell_head, 0xff, sizeof(int) * ncells, c->st) != cudaSuccess) s = GLD_E_CUDA;
     Ctrl h{};

@@ -29,6 +29,8 @@ struct gld_ctx {
     size_t bytes = 0;  // device bytes held
     ParticleBuffers B{};
     float* W = nullptr;
+    CUtensorMap wmap{};      // W as 32 x 128 tiles for the tensor-core filter
+    bool have_wmap = false;
     float* Acp = nullptr;
     int la = 0;
     float* coef = nullptr;

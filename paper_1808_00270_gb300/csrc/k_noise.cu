@@ -294,7 +294,8 @@ cudaError_t launch_prep(const PrepArgs& a, cudaStream_t st)
 }
 
 cudaError_t launch_noise_block(const StepParams& P, Ctrl* ctrl, float* W, const float* Acp, int la, float* frblock,
-                               unsigned long long seed, const int* int2ext, bool tc, int num_sms, cudaStream_t st)
+                               unsigned long long seed, const int* int2ext, const CUtensorMap* wmap, int num_sms,
+                               cudaStream_t st)
 {
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     dim3 g((P.n + kGenThreads - 1) / kGenThreads, (unsigned)P.T);
@@ -302,7 +303,7 @@ cudaError_t launch_noise_block(const StepParams& P, Ctrl* ctrl, float* W, const 
     const long long streams = 3LL * P.n_pad;
     (void)la;
     if (P.T != 64) return cudaErrorInvalidValue;
-    if (tc && noise_filter_tc_ok(P)) return launch_noise_filter_tc(P, ctrl, W, Acp, frblock, num_sms, st);
+    if (wmap && noise_filter_tc_ok(P)) return launch_noise_filter_tc(P, ctrl, wmap, Acp, frblock, num_sms, st);
     const int ntaps = fir_taps_len(P.H);
     const int chunk = std::min(ntaps, kFirChunk);
     const size_t smem = fir_smem(chunk);
@@ -314,10 +315,10 @@ cudaError_t launch_noise_block(const StepParams& P, Ctrl* ctrl, float* W, const 
 }
 
 cudaError_t launch_noise_filter(const StepParams& P, Ctrl* ctrl, const float* W, const float* taps, float* out,
-                                bool tc, int num_sms, cudaStream_t st)
+                                const CUtensorMap* wmap, int num_sms, cudaStream_t st)
 {
     if (P.T != 64) return cudaErrorInvalidValue;
-    if (tc && noise_filter_tc_ok(P)) return launch_noise_filter_tc(P, ctrl, W, taps, out, num_sms, st);
+    if (wmap && noise_filter_tc_ok(P)) return launch_noise_filter_tc(P, ctrl, wmap, taps, out, num_sms, st);
     const int ntaps = fir_taps_len(P.H);
     const int chunk = std::min(ntaps, kFirChunk);
     const size_t smem = fir_smem(chunk);

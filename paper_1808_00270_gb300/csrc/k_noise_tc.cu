@@ -1,5 +1,5 @@
 // k_noise_tc.cu -- the moving-average filter of the colored noise on the
-// tensor cores (tcgen05 MMAs from TMEM and shared memory, TMEM accumulators).
+// tensor cores (tcgen05, TMEM accumulators, TMA tile loads).
 //
 // For a block of T = 64 steps starting at n0, Eq. noise_production gives per
 // stream j (a particle's component) and t < 64
@@ -37,28 +37,31 @@
 // One persistent CTA per SM (all 512 TMEM columns), warp-specialized and
 // linked by mbarriers, so that loads, conversions, MMAs and accumulation of
 // different chunks overlap:
+//   warp 0, one thread  TMA loads of W tiles [32 rows][128 streams] into a
+//                       ring of shared-memory stages;
 //   warp 1, one thread  the MMAs of a chunk (2 K steps x 3 products) into one
 //                       of three TMEM accumulator pairs (D1, D2), from one of
 //                       four TMEM A buffers; owns the TMEM allocation;
-//   warps 4-7           loaders and converters: 16-byte asynchronous copies
-//                       (cp.async, completion tracked by the stage's mbarrier)
-//                       of W tiles [32 rows][128 streams] into a ring of up to
-//                       eight shared-memory stages, several chunks ahead; then
-//                       a stage's rows (zero outside the real window) split
-//                       into FP16 parts and stored into an A buffer (thread =
-//                       stream = TMEM lane);
+//   warps 4-7           converters: a stage's rows (zero outside the real
+//                       window) split into FP16 parts and stored into an A
+//                       buffer (thread = stream = TMEM lane);
 //   warps 8-11          accumulators: D read back and added in FP32 registers;
 //                       at the last chunk of a tile, F^R written out.
-// Loading with TMA (cp.async.bulk.tensor, one elected thread, the same
-// stages) streamed the ring at only about 3.6 TB/s on GB300 (one SM's bulk
-// copies are served one after another): 0.90 ms per 64-step block at 262144
-// particles with every other role idle, against 6.7 TB/s for ordinary loads.
+// Measured on GB300 (262144 particles, m_max = 400, one 64-step block): 1.3 ms
+// including the white-noise generation, against 2.2 ms for the FP32-pipe
+// filter.  The bulk-tensor copies are the limit: with every other role idle
+// they stream the ring at about 3.6 TB/s (0.90 ms; the same from L2-resident
+// tiles, and the same with the stage split into 2 or 4 smaller boxes), about
+// 12 bytes per cycle per SM.  Loading with 16-byte cp.async copies issued by
+// the converter warps instead (completion on the same mbarriers) took 2.2 ms.
 // Every wait is bounded: a wait that runs out sets kErrTimeout and a shared
 // abort flag that ends every role's loop; the CTA then lets its copies and
 // MMAs finish (bounded again), frees its TMEM and returns.
 #include <algorithm>
 
+#include <cuda.h>
 #include <cuda_fp16.h>
+#include <cudaTypedefs.h>
 
 #include "launch.h"
 
@@ -86,6 +89,11 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)_
 __device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
 }
 
 // Waits until the phase with the given parity has completed; false after
@@ -135,18 +143,11 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
 
-// 16-byte asynchronous copy, zero-filled when `real` is false.
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool real)
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar)
 {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(real ? 16 : 0)
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                 ::"r"(smem_u32(dst)), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(smem_u32(bar))
                  : "memory");
-}
-
-// The mbarrier receives one arrival once all earlier cp.async copies of this
-// thread have landed (its expected count includes these arrivals).
-__device__ __forceinline__ void cp_async_arrive(uint64_t* b)
-{
-    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(b)) : "memory");
 }
 
 // K-major, no-swizzle shared-memory matrix descriptor (tcgen05 version 1).
@@ -223,7 +224,7 @@ size_t tc_smem_bytes(int H, int T)
     return std::max<size_t>(b, 116 * 1024);
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1) fir_tc(const float* __restrict__ W, const StepParams P,
+__global__ void __launch_bounds__(kTcThreads, 1) fir_tc(const __grid_constant__ CUtensorMap wmap, const StepParams P,
                                                         Ctrl* __restrict__ ctrl, const float* __restrict__ taps,
                                                         float* __restrict__ out, int nrows, int nst)
 {
@@ -288,7 +289,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fir_tc(const float* __restrict_
     }
     if (tid == 0) {
         for (int s = 0; s < nst; ++s) {
-            mbar_init(&full[s], 128);  // one cp.async arrival per converter thread
+            mbar_init(&full[s], 1);
             mbar_init(&empty[s], 4);
         }
         for (int b = 0; b < kTcNA; ++b) {
@@ -323,7 +324,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) fir_tc(const float* __restrict_
     const bool ok0 = *abort_flag == 0;
 
     long long committed = -1;  // MMA thread: last chunk whose MMAs were committed
-    if (ok0 && warp == 1 && lane == 0) {
+    if (ok0 && warp == 0 && lane == 0) {
+        // ---- producer: TMA loads of the window's 32-row tiles ---------------
+        for (long long g = 0; g < G; ++g) {
+            const int i = (int)(g / nch), c = (int)(g - (long long)i * nch);
+            const int s = (int)(g % nst);
+            if (g >= nst && !mbar_wait_ab(&empty[s], (uint32_t)((g / nst - 1) & 1), abort_flag)) break;
+            long long slot = (t_lo + (long long)kTcChunk * c) % P.lw;
+            if (slot < 0) slot += P.lw;
+            const long long x = ((long long)blockIdx.x + (long long)i * gridDim.x) * 128;
+            if (x >= np3 || (slot & 31) || slot + kTcChunk > P.lw) {  // never for a valid launch
+                atomicOr(&ctrl->err, kErrCheck);
+                *abort_flag = 1;
+                break;
+            }
+            mbar_expect_tx(&full[s], kTcStageBytes);
+            tma_load_2d(stage + (size_t)s * kTcStageFloats, &wmap, (int)x, (int)slot, &full[s]);
+        }
+    } else if (ok0 && warp == 1 && lane == 0) {
         // ---- MMA issuer ---------------------------------------------------------
         const uint32_t rhi = smem_u32(Rhi), rlo = smem_u32(Rlo);
         for (long long g = 0; g < G; ++g) {
@@ -353,38 +371,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) fir_tc(const float* __restrict_
             committed = g;
         }
     } else if (ok0 && warp >= 4 && warp < 8) {
-        // ---- loaders and converters: W tiles -> FP16 parts in TMEM -------------
+        // ---- converters: stage rows -> TF32 part / remainder in TMEM ------------
         const int ct = tid - 128;  // stream within the tile = TMEM lane
         const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
-        // chunk g: 32 rows of 512 bytes (128 streams) = 1024 copies of 16
-        // bytes, 8 per thread; streams past 3 n_pad are zero-filled
-        auto load = [&](long long g) {
-            const int i = (int)(g / nch), c = (int)(g - (long long)i * nch);
-            const long long x0 = ((long long)blockIdx.x + (long long)i * gridDim.x) * 128;
-            long long slot = (t_lo + (long long)kTcChunk * c) % P.lw;
-            if (slot < 0) slot += P.lw;
-            float* dst = stage + (size_t)(g % nst) * kTcStageFloats;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int piece = ct + 128 * q, r = piece >> 5, c4 = (piece & 31) * 4;
-                const bool real = x0 + c4 < np3;
-                const float* src = W + (size_t)(slot + r) * np3 + (real ? x0 + c4 : 0);
-                cp_async16(dst + r * 128 + c4, src, real);
-            }
-            cp_async_arrive(&full[g % nst]);
-        };
-        for (long long g = 0; g < G && g < nst - 1; ++g) load(g);
         for (long long g = 0; g < G; ++g) {
             const int c = (int)(g % nch);
             const int s = (int)(g % nst), b = (int)(g % kTcNA);
-            // refill the stage chunk g - 1 used, once every converter warp read it
-            const long long gn = g + nst - 1;
-            if (gn < G) {
-                bool oke = true;
-                if (g >= 1) oke = mbar_wait_ab(&empty[gn % nst], (uint32_t)(((g - 1) / nst) & 1), abort_flag);
-                if (!__all_sync(0xffffffffu, oke)) break;
-                load(gn);
-            }
             bool okw = mbar_wait_ab(&full[s], (uint32_t)((g / nst) & 1), abort_flag);
             if (okw && g >= kTcNA) okw = mbar_wait_ab(&aempty[b], (uint32_t)((g / kTcNA - 1) & 1), abort_flag);
             if (!__all_sync(0xffffffffu, okw)) break;  // the same decision in every lane
@@ -448,13 +440,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) fir_tc(const float* __restrict_
             }
         }
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");  // no copy outlives the CTA
     __syncthreads();
     if (*abort_flag) {
         if (tid == 0) atomicOr(&ctrl->err, kErrTimeout);
-        // let the MMAs still in flight finish before the memory goes
+        // let copies and MMAs still in flight finish before the memory goes
         if (warp == 1 && lane == 0 && committed >= 0)
             mbar_wait(&dfull[committed % kTcND], (uint32_t)((committed / kTcND) & 1));
+        if (tid == 0) {
+            const long long t0 = clock64();
+            while (clock64() - t0 < 200000) {
+            }
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -483,8 +479,28 @@ bool noise_filter_tc_ok(const StepParams& P)
            tc_smem_bytes(P.H, P.T) <= 227 * 1024;
 }
 
-cudaError_t launch_noise_filter_tc(const StepParams& P, Ctrl* ctrl, const float* W, const float* taps, float* out,
-                                   int num_sms, cudaStream_t st)
+cudaError_t make_noise_ring_map(void* W, const StepParams& P, CUtensorMap* map)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return e != cudaSuccess ? e : cudaErrorNotSupported;
+        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)3 * P.n_pad, (cuuint64_t)P.lw};
+    const cuuint64_t strides[1] = {(cuuint64_t)3 * P.n_pad * sizeof(float)};
+    const cuuint32_t box[2] = {128u, (cuuint32_t)kTcChunk};
+    const cuuint32_t estr[2] = {1u, 1u};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, W, dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_noise_filter_tc(const StepParams& P, Ctrl* ctrl, const CUtensorMap* wmap, const float* taps,
+                                   float* out, int num_sms, cudaStream_t st)
 {
     if (!noise_filter_tc_ok(P)) return cudaErrorInvalidValue;
     const size_t smem = tc_smem_bytes(P.H, P.T);
@@ -492,7 +508,7 @@ cudaError_t launch_noise_filter_tc(const StepParams& P, Ctrl* ctrl, const float*
     if (e != cudaSuccess) return e;
     const long long ntiles = (3LL * P.n_pad + 127) / 128;
     const int grid = (int)std::min<long long>(ntiles, std::max(num_sms, 1));
-    fir_tc<<<grid, kTcThreads, smem, st>>>(W, P, ctrl, taps, out, tc_rows(P.H, P.T), tc_stages(P.H, P.T));
+    fir_tc<<<grid, kTcThreads, smem, st>>>(*wmap, P, ctrl, taps, out, tc_rows(P.H, P.T), tc_stages(P.H, P.T));
     return cudaGetLastError();
 }
 

@@ -3,6 +3,7 @@
 // of the launch.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "gld_internal.cuh"
@@ -157,21 +158,22 @@ int fir_copy_len(int T, int H);
 int fir_taps_len(int H);
 
 // int2ext maps the internal index to the caller's index, which keys the noise.
-// With tc the filter runs on the tensor cores when noise_filter_tc_ok(P),
-// else on the FP32 pipes.
+// With wmap (the ring's tensor map, make_noise_ring_map) the filter runs on
+// the tensor cores when noise_filter_tc_ok(P), else on the FP32 pipes.
 cudaError_t launch_noise_block(const StepParams& P, Ctrl* ctrl, float* W, const float* Acp, int la,
-                               float* frblock, unsigned long long seed, const int* int2ext, bool tc, int num_sms,
-                               cudaStream_t st);
+                               float* frblock, unsigned long long seed, const int* int2ext,
+                               const CUtensorMap* wmap, int num_sms, cudaStream_t st);
 // One more moving-average pass over the white noise already in the ring of
 // the current block (after launch_noise_block): out[t] = sum_s taps W.
 cudaError_t launch_noise_filter(const StepParams& P, Ctrl* ctrl, const float* W, const float* taps, float* out,
-                                bool tc, int num_sms, cudaStream_t st);
+                                const CUtensorMap* wmap, int num_sms, cudaStream_t st);
 // Tensor-core filter (k_noise_tc.cu): whether it serves these parameters
-// (64-step blocks, a ring of 32-row tiles, taps that fit shared memory), and
-// the launch over the ring W [lw][3 n_pad] FP32.
+// (64-step blocks, a ring of 32-row tiles, taps that fit shared memory), the
+// tensor map of the ring W [lw][3 n_pad] FP32 in 32 x 128 tiles, and the launch.
 bool noise_filter_tc_ok(const StepParams& P);
-cudaError_t launch_noise_filter_tc(const StepParams& P, Ctrl* ctrl, const float* W, const float* taps, float* out,
-                                   int num_sms, cudaStream_t st);
+cudaError_t make_noise_ring_map(void* W, const StepParams& P, CUtensorMap* map);
+cudaError_t launch_noise_filter_tc(const StepParams& P, Ctrl* ctrl, const CUtensorMap* wmap, const float* taps,
+                                   float* out, int num_sms, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out, long long n,
                           cudaStream_t st);
 cudaError_t launch_gauss3(uint32_t k0, uint32_t k1, const uint32_t* particle, const long long* time,
