@@ -185,10 +185,12 @@ gld_status gld_set_array(gld_ctx* ctx, int32_t which, const double* in);
  * the particle stored at position k; pass it as gld_params.order. */
 gld_status gld_get_order(gld_ctx* ctx, int32_t* int2ext);
 
-/* Diagnostics, out[count] (count <= 4 filled): {graph form of gld_step (0: not
+/* Diagnostics, out[count] (count <= 5 filled): {graph form of gld_step (0: not
  * captured yet, 1: rebuild kernels gated on the device, 2: rebuild in a
  * conditional graph node), neighbour-list builds so far, list capacity per
- * particle, cells per box edge}.  Synchronizes. */
+ * particle, cells per box edge, Lanczos iterations of the last step's
+ * pair-correlated noise (gld_set_pair_noise_krylov; 0 when off)}.
+ * Synchronizes. */
 gld_status gld_get_diag(gld_ctx* ctx, int64_t* out, int32_t count);
 
 /* Step counter n (the time index of R_n) and its setter (n >= 0, else
@@ -291,6 +293,29 @@ gld_status gld_set_pair_noise(gld_ctx* ctx, int32_t degree, double* lambda, doub
  * GLD_E_INVAL for m_max < 2, degree outside [1, 16], lambda <= 0, dt <= 0. */
 gld_status gld_pair_noise_filters(const double* ks, const double* g, int32_t m_max, double kT, double dt,
                                   double lambda, int32_t degree, int32_t psd_clamp, double* taps, double* cheb_err);
+
+/* Pair-correlated random force by Algorithm 1 of Sec. II C: every step, for
+ * each frequency w = 0 .. m_max - 1, a Lanczos iteration on the transformed
+ * correlation matrix hat K_w (the right-hand side of Eq. stochastic_force2 at
+ * the current configuration, the time-scale separation remarked on after
+ * Algorithm 1) from the transformed white-noise window hat W_w, stopped when
+ * the relative change of |hat W_w| V sqrt(H) e_1 between iterations falls to
+ * tol (Algorithm 1's Delta; the vectors are FP32, so tol of 1e-6 .. 1e-4 is
+ * meaningful), at most kmax iterations; F_n = (x_0 + 2
+ * sum_{w>=1} x_w) / (2 m_max - 1).  It takes every kernel form (any Q, Qs <= 4
+ * with time factors of their own, perpendicular factors, r_c,min) and needs
+ * only that each hat K_w is positive semi-definite at the configuration; a
+ * Ritz value below -1e-6 of the largest latches GLD_E_NOT_PSD, no
+ * convergence within kmax
+ * GLD_E_TIMEOUT.  It replaces the Chebyshev form of gld_set_pair_noise (and
+ * the reverse).  Cost per step: kmax neighbour sweeps over all m_max
+ * frequencies at most, with the host deciding between chunks of four
+ * iterations, so steps run without graphs; device memory (kmax + 2) x 3 n_pad
+ * x m_max floats.  tol <= 0 turns it off; 0 < tol < 1, 2 <= kmax <= 64, else
+ * GLD_E_INVAL; GLD_E_STATE before kernels are set.  Single contexts only (not
+ * in a batch); gld_profile_steps refuses it.  A new gld_set_kernels turns it
+ * off.  Synchronizes. */
+gld_status gld_set_pair_noise_krylov(gld_ctx* ctx, double tol, int32_t kmax);
 
 /* Memory sums in auxiliary-variable form (App. C discusses auxiliary-variable
  * expansions as the alternative to a stored history).  When every kernel

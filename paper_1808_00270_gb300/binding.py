@@ -102,6 +102,7 @@ def lib():
             "gld_set_conservative_table": (i32, [vp, vp, i32, C.c_double]),
             "gld_set_pair_noise": (i32, [vp, i32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "gld_set_perpendicular": (i32, [vp, vp, vp]),
+            "gld_set_pair_noise_krylov": (i32, [vp, C.c_double, i32]),
             "gld_pair_noise_filters": (i32, [vp, vp, i32, C.c_double, C.c_double, C.c_double, i32, i32, vp,
                                              C.POINTER(C.c_double)]),
             "gld_set_kernels_table": (i32, [vp, vp, vp, i32, C.c_double, i32, i32, C.POINTER(C.c_double)]),
@@ -152,7 +153,8 @@ def exported_symbols() -> list[str]:
             "gld_server_last_error", "gld_server_destroy", "gld_server_cancel", "gld_set_pair_correlation",
             "gld_pair_correlation", "gld_set_memory_modes", "gld_set_conservative_table",
             "gld_set_kernels_table", "gld_separable_terms", "gld_set_pair_noise",
-            "gld_set_perpendicular", "gld_pair_noise_filters"]
+            "gld_set_perpendicular", "gld_pair_noise_filters", "gld_save_observables", "gld_load_observables",
+            "gld_set_pair_noise_krylov"]
 
 
 def _ptr(a: np.ndarray):
@@ -311,9 +313,10 @@ class GLD:
         self._check(lib().gld_set_step(self._h, int(step)))
 
     def diag(self) -> dict:
-        out = np.zeros(4, dtype=np.int64)
-        self._check(lib().gld_get_diag(self._h, _ptr(out), 4))
-        return dict(graph_mode=int(out[0]), rebuilds=int(out[1]), maxnb=int(out[2]), cells_per_edge=int(out[3]))
+        out = np.zeros(5, dtype=np.int64)
+        self._check(lib().gld_get_diag(self._h, _ptr(out), 5))
+        return dict(graph_mode=int(out[0]), rebuilds=int(out[1]), maxnb=int(out[2]), cells_per_edge=int(out[3]),
+                    krylov_iterations=int(out[4]))
 
     def set_memory_modes(self, rates, omegas):
         """Carries the memory sums in auxiliary-variable form for kernels that
@@ -358,6 +361,11 @@ class GLD:
         lv, err = C.c_double(float(lam)), C.c_double()
         self._check(lib().gld_set_pair_noise(self._h, int(degree), C.byref(lv), C.byref(err)))
         return float(lv.value), float(err.value)
+
+    def set_pair_noise_krylov(self, tol: float = 1e-6, kmax: int = 32):
+        """Pair-correlated noise by a Lanczos iteration per frequency
+        (Algorithm 1); tol <= 0 turns it off."""
+        self._check(lib().gld_set_pair_noise_krylov(self._h, float(tol), int(kmax)))
 
     def set_pair_correlation(self, nbins: int, r_max: float):
         """Enables C^a(R, t), C^c(R, t) on nbins distance bins of [0, r_max)."""

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libgld.so")
-SOURCES = ["api.cu", "serve.cu", "k_modes.cu", "k_history.cu", "k_particles.cu", "k_noise.cu", "k_noise_tc.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "serve.cu", "k_modes.cu", "k_history.cu", "k_particles.cu", "k_noise.cu", "k_noise_tc.cu", "k_pn_krylov.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--extended-lambda", "-Xcompiler", "-fPIC",
          "-I" + INCLUDE, "-I" + CSRC]

@@ -305,6 +305,199 @@ cudaError_t capture_step_conditional(gld_ctx* c, cudaStream_t s, bool overlap)
     return e;
 }
 
+// ---- pair-correlated noise by a Lanczos iteration per frequency ------------
+void kry_release(gld_ctx* c)
+{
+    auto& K = c->kry;
+    for (float** p : {&K.V, &K.Y, &K.cf}) {
+        dfree(c, *p);
+        *p = nullptr;
+    }
+    for (double** p : {&K.part, &K.alpha, &K.beta, &K.xnorm, &K.wc}) {
+        dfree(c, *p);
+        *p = nullptr;
+    }
+    dfree(c, K.alive);
+    K.alive = nullptr;
+    K.M = K.Mp = K.kmax = 0;
+    K.last_iters = 0;
+    c->P.pn_kry = 0;
+}
+
+// Eigen-decomposition of a small symmetric matrix a (n x n, row-major) by
+// cyclic Jacobi rotations: eigenvalues into th, eigenvectors as the columns
+// of u.  Rotations stop once the off-diagonal part is below 1e-30 of the
+// norm (FP64).
+void jacobi_eig(int n, std::vector<double>& a, std::vector<double>& th, std::vector<double>& u)
+{
+    u.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) u[(size_t)i * n + i] = 1.0;
+    double norm = 0.0;
+    for (double x : a) norm += x * x;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) off += a[(size_t)p * n + q] * a[(size_t)p * n + q];
+        if (off <= 1e-30 * norm) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = a[(size_t)p * n + q];
+                if (apq == 0.0) continue;
+                const double theta = (a[(size_t)q * n + q] - a[(size_t)p * n + p]) / (2.0 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double cs = 1.0 / std::sqrt(t * t + 1.0), sn = t * cs;
+                for (int k = 0; k < n; ++k) {  // columns p, q
+                    const double akp = a[(size_t)k * n + p], akq = a[(size_t)k * n + q];
+                    a[(size_t)k * n + p] = cs * akp - sn * akq;
+                    a[(size_t)k * n + q] = sn * akp + cs * akq;
+                }
+                for (int k = 0; k < n; ++k) {  // rows p, q
+                    const double apk = a[(size_t)p * n + k], aqk = a[(size_t)q * n + k];
+                    a[(size_t)p * n + k] = cs * apk - sn * aqk;
+                    a[(size_t)q * n + k] = sn * apk + cs * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double ukp = u[(size_t)k * n + p], ukq = u[(size_t)k * n + q];
+                    u[(size_t)k * n + p] = cs * ukp - sn * ukq;
+                    u[(size_t)k * n + q] = sn * ukp + cs * ukq;
+                }
+            }
+    }
+    th.resize(n);
+    for (int i = 0; i < n; ++i) th[i] = a[(size_t)i * n + i];
+}
+
+// c = |x| sqrt(H) e_1 for the j x j Lanczos matrix H (diagonal alpha,
+// off-diagonal beta); *neg receives the most negative eigenvalue of H over
+// its largest magnitude (a negative Ritz value means hat K_w is not positive
+// semi-definite).  Negative eigenvalues contribute nothing.
+void tri_sqrt_e1(int j, const double* alpha, const double* beta, double xnorm, std::vector<double>& c, double* neg)
+{
+    std::vector<double> a((size_t)j * j, 0.0), th, u;
+    for (int p = 0; p < j; ++p) {
+        a[(size_t)p * j + p] = alpha[p];
+        if (p + 1 < j) a[(size_t)p * j + p + 1] = a[(size_t)(p + 1) * j + p] = beta[p];
+    }
+    jacobi_eig(j, a, th, u);
+    double mx = 0.0, mn = 0.0;
+    for (double t : th) {
+        mx = std::max(mx, std::fabs(t));
+        mn = std::min(mn, t);
+    }
+    *neg = mx > 0 ? mn / mx : 0.0;
+    c.assign(j, 0.0);
+    for (int i = 0; i < j; ++i) {
+        const double wgt = std::sqrt(std::max(th[i], 0.0)) * u[i];  // sqrt(theta_i) (u_i)_1
+        for (int p = 0; p < j; ++p) c[p] += u[(size_t)p * j + i] * wgt;
+    }
+    for (double& x : c) x *= xnorm;
+}
+
+// F^R of the current step by Algorithm 1, into its row of the F^R block
+// (eager: host decisions between chunks of iterations).
+gld_status pair_noise_krylov(gld_ctx* c, cudaStream_t st)
+{
+    const StepParams& P = c->P;
+    auto& K = c->kry;
+    const int M = K.M, Mp = K.Mp;
+    const size_t vs = 3 * (size_t)P.n_pad * Mp;
+    auto V = [&](int p) { return K.V + (size_t)p * vs; };
+    GLD_CUDA(c, cudaMemsetAsync(K.alive, 1, sizeof(int) * Mp, st));  // nonzero: alive
+    GLD_CUDA(c, kry_ft(P, c->B.ctrl, c->W, M, Mp, V(0), st));
+    GLD_CUDA(c, kry_dot(P, V(0), V(0), Mp, K.part, K.xnorm, 2, nullptr, K.alive, st));
+    GLD_CUDA(c, kry_scale(P, V(0), V(0), Mp, K.xnorm, K.alive, st));
+    GLD_CUDA(c, kry_matvec(P, c->B, K.wc, Mp, V(0), K.Y, st));
+    GLD_CUDA(c, kry_dot(P, V(0), K.Y, Mp, K.part, K.alpha, 0, nullptr, K.alive, st));
+    int k = 1;  // Lanczos vectors so far
+    const int chunk = 4;
+    std::vector<double> ha, hb, hx(Mp);
+    std::vector<std::vector<double>> cprev(M), cfin(M);
+    std::vector<int> done(M, 0), kw(M, 0);
+    int ndone = 0;
+    double worst_change = 0.0, worst_neg = 0.0;
+    while (true) {
+        for (int it = 0; it < chunk && k < K.kmax; ++it, ++k) {
+            GLD_CUDA(c, kry_resid(P, K.Y, V(k - 1), k >= 2 ? V(k - 2) : nullptr, K.alpha + (size_t)(k - 1) * Mp,
+                                  K.beta + (size_t)(k >= 2 ? k - 2 : 0) * Mp, Mp, V(k), st));
+            GLD_CUDA(c, kry_dot(P, V(k), V(k), Mp, K.part, K.beta + (size_t)(k - 1) * Mp, 1, K.alpha, K.alive, st));
+            GLD_CUDA(c, kry_scale(P, V(k), V(k), Mp, K.beta + (size_t)(k - 1) * Mp, K.alive, st));
+            GLD_CUDA(c, kry_matvec(P, c->B, K.wc, Mp, V(k), K.Y, st));
+            GLD_CUDA(c, kry_dot(P, V(k), K.Y, Mp, K.part, K.alpha + (size_t)k * Mp, 0, nullptr, K.alive, st));
+        }
+        ha.resize((size_t)k * Mp);
+        hb.resize((size_t)std::max(k - 1, 1) * Mp);
+        GLD_CUDA(c, cudaMemcpyAsync(ha.data(), K.alpha, sizeof(double) * ha.size(), cudaMemcpyDeviceToHost, st));
+        if (k > 1)
+            GLD_CUDA(c, cudaMemcpyAsync(hb.data(), K.beta, sizeof(double) * (size_t)(k - 1) * Mp, cudaMemcpyDeviceToHost,
+                                        st));
+        GLD_CUDA(c, cudaMemcpyAsync(hx.data(), K.xnorm, sizeof(double) * Mp, cudaMemcpyDeviceToHost, st));
+        GLD_TRY(sync_and_check(c));
+        for (int w = 0; w < M; ++w) {
+            if (done[w]) continue;
+            // the Krylov space of w ends at the first vanished beta (exact result)
+            int j = 1;
+            std::vector<double> al(k), be(std::max(k - 1, 0));
+            for (int p = 0; p < k; ++p) al[p] = ha[(size_t)p * Mp + w];
+            bool exhausted = false;
+            for (int p = 0; p + 1 < k; ++p) {
+                be[p] = hb[(size_t)p * Mp + w];
+                if (!(be[p] > 0.0)) {
+                    exhausted = true;
+                    break;
+                }
+                ++j;
+            }
+            std::vector<double> cj;
+            double neg = 0.0;
+            tri_sqrt_e1(j, al.data(), be.data(), hx[w], cj, &neg);
+            worst_neg = std::min(worst_neg, neg);
+            double change = 0.0, nrm = 0.0;
+            if (j >= 2 || exhausted) {
+                std::vector<double> cm;
+                double neg2 = 0.0;
+                if (j >= 2) tri_sqrt_e1(j - 1, al.data(), be.data(), hx[w], cm, &neg2);
+                cm.resize(j, 0.0);
+                for (int p = 0; p < j; ++p) {
+                    change += (cj[p] - cm[p]) * (cj[p] - cm[p]);
+                    nrm += cj[p] * cj[p];
+                }
+                change = nrm > 0 ? std::sqrt(change / nrm) : 0.0;
+            } else {
+                change = 1.0;
+            }
+            if (exhausted || change <= K.tol) {
+                done[w] = 1;
+                ++ndone;
+                cfin[w] = cj;
+                kw[w] = j;
+                worst_change = std::max(worst_change, exhausted ? 0.0 : change);
+            } else if (k >= K.kmax) {
+                cfin[w] = cj;
+                kw[w] = j;
+                worst_change = std::max(worst_change, change);
+            }
+        }
+        if (ndone == M || k >= K.kmax) break;
+    }
+    K.last_iters = k;
+    K.last_change = worst_change;
+    if (worst_neg < -1e-6) {  // beyond the rounding of FP32 vectors
+        c->msg = "pair noise (Lanczos): a transformed correlation matrix is not positive semi-definite";
+        if (c->latched == GLD_OK) c->latched = GLD_E_NOT_PSD;
+        return GLD_E_NOT_PSD;
+    }
+    if (ndone < M)
+        return fail(c, GLD_E_TIMEOUT, "pair noise (Lanczos): no convergence within the iteration limit");
+    std::vector<float> cf((size_t)M * k, 0.f);
+    for (int w = 0; w < M; ++w)
+        for (int p = 0; p < kw[w]; ++p) cf[(size_t)w * k + p] = (float)cfin[w][p];
+    GLD_CUDA(c, cudaMemcpyAsync(K.cf, cf.data(), sizeof(float) * cf.size(), cudaMemcpyHostToDevice, st));
+    const long long row = c->host_step - c->block_start;
+    GLD_CUDA(c, kry_combine(P, K.V, K.cf, k, M, Mp, c->B.frblock + (size_t)row * 3 * P.n_pad, st));
+    GLD_CUDA(c, cudaStreamSynchronize(st));  // cf is reused by the next step
+    return GLD_OK;
+}
+
 bool capture_graph_mode(gld_ctx* c, bool conditional)
 {
     // the overlapped form needs an idempotent convolution (not the recursive
@@ -339,7 +532,7 @@ bool capture_graph_mode(gld_ctx* c, bool conditional)
 bool capture_graph(gld_ctx* c)
 {
     if (c->gexec) return true;
-    if (c->graph_failed) return false;
+    if (c->graph_failed || c->P.pn_kry) return false;  // the Lanczos noise decides on the host every step
     // conditional rebuild first; the gated kernels are the fallback
     if (c->prm.use_graphs != 2 && capture_graph_mode(c, true)) {
         c->graph_mode = 2;
@@ -665,6 +858,7 @@ gld_status gld_set_kernels(gld_ctx* c, const double* Ks, int32_t Q, const double
     dfree(c, c->d_rowsum);
     c->d_rowsum = nullptr;
     c->B.fptab = nullptr;
+    kry_release(c);
     const int M = c->P.m_max;
     std::vector<double> in((size_t)(1 + 2 * kMaxQ) * M, 0.0);
     std::memcpy(in.data(), Ks, sizeof(double) * M);
@@ -782,6 +976,7 @@ gld_status gld_step(gld_ctx* c, int64_t nsteps)
             c->noise_end = c->host_step + T;
             c->noise_valid = true;
         }
+        if (c->P.pn_kry) GLD_TRY(pair_noise_krylov(c, c->st));
         GLD_CUDA(c, launch_one_step(c, c->st));
         c->conv_valid_step = -1;
         c->last_fr_row = c->host_step - c->block_start;
@@ -927,8 +1122,8 @@ gld_status gld_get_diag(gld_ctx* c, int64_t* out, int32_t count)
     GLD_TRY(sync_and_check(c));
     long long rebuilds = 0;
     GLD_CUDA(c, cudaMemcpy(&rebuilds, &c->B.ctrl->rebuilds, sizeof(rebuilds), cudaMemcpyDeviceToHost));
-    const int64_t v[4] = {c->graph_mode, rebuilds, c->P.maxnb, c->P.nc};
-    for (int k = 0; k < count; ++k) out[k] = k < 4 ? v[k] : 0;
+    const int64_t v[5] = {c->graph_mode, rebuilds, c->P.maxnb, c->P.nc, c->kry.last_iters};
+    for (int k = 0; k < count; ++k) out[k] = k < 5 ? v[k] : 0;
     return GLD_OK;
 }
 
@@ -1014,6 +1209,8 @@ gld_status gld_profile_steps(gld_ctx* c, int64_t nsteps, double* ms, int64_t* la
     if (!c || nsteps < 0) return GLD_E_INVAL;
     if (!c->have_kernels) return fail(c, GLD_E_STATE, "gld_profile_steps: gld_set_kernels has not succeeded");
     if (c->latched != GLD_OK) return c->latched;
+    if (c->P.pn_kry)
+        return fail(c, GLD_E_STATE, "gld_profile_steps: not with the Lanczos pair noise (host decisions every step)");
     // untimed steps up to the next noise-block boundary
     if (c->noise_valid && c->host_step < c->noise_end) GLD_TRY(gld_step(c, c->noise_end - c->host_step));
     GLD_TRY(refresh_modes(c));
@@ -1346,6 +1543,7 @@ gld_status gld_set_pair_noise(gld_ctx* c, int32_t degree, double* lambda, double
     dfree(c, c->d_rowsum);
     c->d_rowsum = nullptr;
     P.pn_deg = 0;
+    kry_release(c);  // one form of pair noise at a time
     invalidate_graph(c);
     GLD_TRY(invalidate_noise(c));
     if (degree == 0) return sync_and_check(c);
@@ -1387,6 +1585,66 @@ gld_status gld_set_pair_noise(gld_ctx* c, int32_t degree, double* lambda, double
     P.pn_cs = (float)cs_ratio;
     P.pn_lambda = (float)lam;
     P.pn_inv_lambda = (float)(1.0 / lam);
+    return sync_and_check(c);
+}
+
+gld_status gld_set_pair_noise_krylov(gld_ctx* c, double tol, int32_t kmax)
+{
+    if (!c) return GLD_E_INVAL;
+    StepParams& P = c->P;
+    if (tol > 0 && !c->have_kernels) return fail(c, GLD_E_STATE, "gld_set_pair_noise_krylov: set the kernels first");
+    if (tol > 0 && (kmax < 2 || kmax > 64 || !(tol < 1.0)))
+        return fail(c, GLD_E_INVAL, "gld_set_pair_noise_krylov: need 0 < tol < 1 and 2 <= kmax <= 64");
+    GLD_TRY(sync_and_check(c));
+    kry_release(c);
+    invalidate_graph(c);
+    if (!(tol > 0)) return sync_and_check(c);
+    // the Chebyshev form is replaced
+    for (float** p : {&c->d_pntaps, &c->d_zblk, &c->d_bvec}) {
+        dfree(c, *p);
+        *p = nullptr;
+    }
+    dfree(c, c->d_rowsum);
+    c->d_rowsum = nullptr;
+    P.pn_deg = 0;
+    auto& K = c->kry;
+    const int M = P.m_max, Mp = (M + 31) & ~31, nacc = P.nacc;
+    const long long L = 2LL * M - 1;
+    // transforms (Eq. FT) of kT a_m / dt times each discrete time factor:
+    // a_w (self), g_qw (pair terms), gs_qw (self-difference terms), FP64
+    std::vector<double> wc((size_t)nacc * Mp, 0.0);
+    const double f0 = c->prm.kT / c->prm.dt;
+    for (int a = 0; a < nacc; ++a) {
+        const double* wt = c->wts.data() + (size_t)a * M;
+        for (int w = 0; w < M; ++w) {
+            double v = 2.0 * wt[0];
+            for (int m = 1; m < M; ++m) v += 2.0 * wt[m] * std::cos(2.0 * M_PI * (double)(((long long)w * m) % L) / (double)L);
+            wc[(size_t)a * Mp + w] = f0 * v;
+        }
+    }
+    const size_t vs = 3 * (size_t)P.n_pad * Mp;
+    bool ok = true;
+    K.V = alloc_n<float>(c, (size_t)(kmax + 1) * vs, ok);
+    K.Y = alloc_n<float>(c, vs, ok);
+    K.cf = alloc_n<float>(c, (size_t)M * (kmax + 1), ok);
+    K.part = alloc_n<double>(c, (size_t)kry_dot_blocks(P) * Mp, ok);
+    K.alpha = alloc_n<double>(c, (size_t)(kmax + 1) * Mp, ok);
+    K.beta = alloc_n<double>(c, (size_t)(kmax + 1) * Mp, ok);
+    K.xnorm = alloc_n<double>(c, Mp, ok);
+    K.wc = alloc_n<double>(c, wc.size(), ok);
+    K.alive = alloc_n<int>(c, Mp, ok);
+    if (!ok) {
+        kry_release(c);
+        return fail(c, GLD_E_NOMEM, "gld_set_pair_noise_krylov: allocation failed");
+    }
+    GLD_CUDA(c, cudaMemcpyAsync(K.wc, wc.data(), sizeof(double) * wc.size(), cudaMemcpyHostToDevice, c->st));
+    K.M = M;
+    K.Mp = Mp;
+    K.kmax = kmax;
+    K.tol = tol;
+    K.last_iters = 0;
+    K.last_change = 0.0;
+    P.pn_kry = 1;
     return sync_and_check(c);
 }
 
@@ -1989,7 +2247,7 @@ gld_status gld_batch_add(gld_batch* b, gld_ctx* c)
     if (!c->have_kernels) return bfail(b, GLD_E_STATE, "gld_batch_add: the member has no kernels set");
     if (c->st != b->st) return bfail(b, GLD_E_INVAL, "gld_batch_add: the member must use the batch's stream");
     if (c->P.T != kMaxNoiseBlock) return bfail(b, GLD_E_INVAL, "gld_batch_add: the member's noise block must be 64");
-    if (c->P.pc_nbins > 0 || c->P.nmodes > 0 || c->P.pn_deg > 0)
+    if (c->P.pc_nbins > 0 || c->P.nmodes > 0 || c->P.pn_deg > 0 || c->P.pn_kry)
         return bfail(b, GLD_E_INVAL,
                      "gld_batch_add: pair correlations, memory modes and pair noise are single-context features");
     if (c->noise_valid && c->host_step != c->noise_end)

@@ -66,6 +66,18 @@ struct gld_ctx {
     float* d_zblk = nullptr;
     float* d_bvec = nullptr;
     unsigned* d_rowsum = nullptr;
+    // pair-correlated noise by a Lanczos iteration per frequency: M
+    // frequencies (Mp padded to 32), at most kmax iterations, the stopping
+    // tolerance, device vectors and scalars, and the last step's statistics
+    struct Krylov {
+        int M = 0, Mp = 0, kmax = 0;
+        double tol = 0.0;
+        float *V = nullptr, *Y = nullptr, *cf = nullptr;
+        double *part = nullptr, *alpha = nullptr, *beta = nullptr, *xnorm = nullptr, *wc = nullptr;
+        int* alive = nullptr;
+        int last_iters = 0;
+        double last_change = 0.0;
+    } kry;
 };
 
 struct gld_batch {

@@ -89,6 +89,8 @@ struct StepParams {
     // perpendicular factors of the pair and self-difference terms are set
     // (rows of ParticleBuffers::fptab)
     int perp;
+    // pair-correlated noise by a Lanczos iteration per frequency (Algorithm 1)
+    int pn_kry;
 };
 
 // ---------------------------------------------------------------- Philox --

@@ -79,6 +79,26 @@ cudaError_t launch_pcorr_flush(const StepParams& P, const ParticleBuffers& B, cu
 // Z_0 row of step n in frblock.
 cudaError_t launch_pair_noise(const StepParams& P, const ParticleBuffers& B, const float* zblk, float* bvec,
                               cudaStream_t st);
+// Pair-correlated noise by Algorithm 1 (k_pn_krylov.cu): vectors [3 n_pad][Mp]
+// (frequency fastest).  kry_ft: the transformed white-noise window of step
+// ctrl->step into V0; kry_dot: per-frequency dot products a.b into out
+// (mode 0), or square roots of the sums (2; 1 also marks exhausted Krylov
+// spaces in alive, relative to ref); kry_scale: dst = src / d; kry_resid:
+// r = Y - alpha v_k - beta v_{k-1}; kry_matvec: Y = hat K_w V for every w
+// (wc: a_w, g_qw, gs_qw rows); kry_combine: out[I] = (sum_w c_w sum_p
+// cf[w][p] V_p[I][w]) / (2 m_max - 1).
+cudaError_t kry_ft(const StepParams& P, const Ctrl* ctrl, const float* W, int M, int Mp, float* V0, cudaStream_t st);
+int kry_dot_blocks(const StepParams& P);
+cudaError_t kry_dot(const StepParams& P, const float* a, const float* b, int Mp, double* part, double* out, int mode,
+                    const double* ref, int* alive, cudaStream_t st);
+cudaError_t kry_scale(const StepParams& P, const float* src, float* dst, int Mp, const double* d, const int* alive,
+                      cudaStream_t st);
+cudaError_t kry_resid(const StepParams& P, const float* Y, const float* vk, const float* vkm1, const double* alpha,
+                      const double* beta, int Mp, float* r, cudaStream_t st);
+cudaError_t kry_matvec(const StepParams& P, const ParticleBuffers& B, const double* wc, int Mp, const float* V,
+                       float* Y, cudaStream_t st);
+cudaError_t kry_combine(const StepParams& P, const float* V, const float* cf, int kp, int M, int Mp, float* out,
+                        cudaStream_t st);
 // Largest Gershgorin row sum sum_j |f(r_ij)| of the pair matrix at the
 // current positions (as the bit pattern of a non-negative float).
 cudaError_t launch_pn_rowsum(const StepParams& P, const ParticleBuffers& B, unsigned* out, cudaStream_t st);
