@@ -188,8 +188,9 @@ gld_status gld_get_order(gld_ctx* ctx, int32_t* int2ext);
 /* Diagnostics, out[count] (count <= 5 filled): {graph form of gld_step (0: not
  * captured yet, 1: rebuild kernels gated on the device, 2: rebuild in a
  * conditional graph node), neighbour-list builds so far, list capacity per
- * particle, cells per box edge, Lanczos iterations of the last step's
- * pair-correlated noise (gld_set_pair_noise_krylov; 0 when off)}.
+ * particle, cells per box edge, the largest Krylov dimension any frequency
+ * used in the last step's pair-correlated noise (gld_set_pair_noise_krylov;
+ * 0 when off)}.
  * Synchronizes. */
 gld_status gld_get_diag(gld_ctx* ctx, int64_t* out, int32_t count);
 

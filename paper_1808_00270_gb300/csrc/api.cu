@@ -479,7 +479,7 @@ gld_status pair_noise_krylov(gld_ctx* c, cudaStream_t st)
         }
         if (ndone == M || k >= K.kmax) break;
     }
-    K.last_iters = k;
+    K.last_iters = *std::max_element(kw.begin(), kw.end());  // the largest Krylov dimension used
     K.last_change = worst_change;
     if (worst_neg < -1e-6) {  // beyond the rounding of FP32 vectors
         c->msg = "pair noise (Lanczos): a transformed correlation matrix is not positive semi-definite";
