@@ -294,6 +294,37 @@ gld_status gld_set_pair_noise(gld_ctx* ctx, int32_t degree, double* lambda, doub
  * GLD_E_INVAL for m_max < 2, degree outside [1, 16], lambda <= 0, dt <= 0. */
 gld_status gld_pair_noise_filters(const double* ks, const double* g, int32_t m_max, double kT, double dt,
                                   double lambda, int32_t degree, int32_t psd_clamp, double* taps, double* cheb_err);
+/* The same on an interval [lo, hi] holding the spectrum of M (lo < hi,
+ * finite): F_n = sum_k T_k((M - c) / rho) Z_k, c = (lo + hi) / 2,
+ * rho = (hi - lo) / 2; GLD_E_NOT_PSD if h_w + g_w mu < 0 at mu = lo or hi for
+ * some w and !psd_clamp (h_w + g_w mu is linear in mu).  gld_pair_noise_filters
+ * is this with [-lambda, lambda], bit for bit. */
+gld_status gld_pair_noise_filters_on(const double* ks, const double* g, int32_t m_max, double kT, double dt,
+                                     double lo, double hi, int32_t degree, int32_t psd_clamp, double* taps,
+                                     double* cheb_err);
+/* The Chebyshev form of gld_set_pair_noise on an interval [lo, hi] of the
+ * spectrum of M rather than a symmetric Gershgorin bound.  The positive
+ * semi-definiteness of hat K_w = h_w 1 + g_w M only needs h_w + g_w mu >= 0
+ * on the actual eigenvalues mu; a Gershgorin bound overestimates them (for
+ * the workloads' pair kernel f = 2 (1 - r/r_c)^2 at density 0.1 it gives 8.2
+ * where the spectrum is [-2.4, 3.8]) and so refuses kernels that are
+ * positive definite.  *lo, *hi: in, the interval (used when *lo < *hi); else
+ * (or NULL) it is estimated by 32 Lanczos steps on M at the current
+ * positions (FP32 vectors, FP64 sums, Sturm bisection of the tridiagonal
+ * matrix) and the Ritz extremes widened by 25 % of their spread on each side
+ * (the extremes are set by the closest pairs and move as pairs meet), each
+ * end kept 5 % of the way from the spectrum to where h_w + g_w mu changes
+ * sign for some w; out, the interval used.  Ritz values approach the extremes from inside, so
+ * the estimate is not a bound: at every 64-step noise block the same Lanczos
+ * run is repeated on the device (inside the captured step graph) and
+ * GLD_E_NOT_PSD latches when a Ritz extreme leaves [lo, hi].  Otherwise as
+ * gld_set_pair_noise (kernel forms, degree, psd_clamp, *cheb_err, exclusions);
+ * it replaces either other form of pair noise.  Synchronizes. */
+gld_status gld_set_pair_noise_on(gld_ctx* ctx, int32_t degree, double* lo, double* hi, double* cheb_err);
+/* out[5]: the smallest and largest Ritz values of the last Lanczos run of
+ * gld_set_pair_noise_on, the Krylov dimension it used, and the interval
+ * [lo, hi].  GLD_E_STATE when that form is off.  Synchronizes. */
+gld_status gld_pair_noise_spectrum(gld_ctx* ctx, double* out);
 
 /* Pair-correlated random force by Algorithm 1 of Sec. II C: every step, for
  * each frequency w = 0 .. m_max - 1, a Lanczos iteration on the transformed

@@ -103,6 +103,11 @@ def lib():
             "gld_set_pair_noise": (i32, [vp, i32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "gld_set_perpendicular": (i32, [vp, vp, vp]),
             "gld_set_pair_noise_krylov": (i32, [vp, C.c_double, i32]),
+            "gld_set_pair_noise_on": (i32, [vp, i32, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                            C.POINTER(C.c_double)]),
+            "gld_pair_noise_spectrum": (i32, [vp, vp]),
+            "gld_pair_noise_filters_on": (i32, [vp, vp, i32, C.c_double, C.c_double, C.c_double, C.c_double, i32,
+                                                i32, vp, C.POINTER(C.c_double)]),
             "gld_pair_noise_filters": (i32, [vp, vp, i32, C.c_double, C.c_double, C.c_double, i32, i32, vp,
                                              C.POINTER(C.c_double)]),
             "gld_set_kernels_table": (i32, [vp, vp, vp, i32, C.c_double, i32, i32, C.POINTER(C.c_double)]),
@@ -154,7 +159,8 @@ def exported_symbols() -> list[str]:
             "gld_pair_correlation", "gld_set_memory_modes", "gld_set_conservative_table",
             "gld_set_kernels_table", "gld_separable_terms", "gld_set_pair_noise",
             "gld_set_perpendicular", "gld_pair_noise_filters", "gld_save_observables", "gld_load_observables",
-            "gld_set_pair_noise_krylov"]
+            "gld_set_pair_noise_krylov", "gld_set_pair_noise_on", "gld_pair_noise_spectrum",
+            "gld_pair_noise_filters_on"]
 
 
 def _ptr(a: np.ndarray):
@@ -361,6 +367,26 @@ class GLD:
         lv, err = C.c_double(float(lam)), C.c_double()
         self._check(lib().gld_set_pair_noise(self._h, int(degree), C.byref(lv), C.byref(err)))
         return float(lv.value), float(err.value)
+
+    def set_pair_noise_on(self, degree: int = 12, lo: float | None = None, hi: float | None = None):
+        """Chebyshev pair noise on an interval [lo, hi] of the pair matrix's
+        spectrum (None: estimated by a Lanczos run, widened by 25 % of its
+        spread each side within the positive semi-definite range; re-checked
+        at every noise block).  Returns (lo, hi,
+        relative interpolation error)."""
+        l = C.c_double(float(lo) if lo is not None else 0.0)
+        h = C.c_double(float(hi) if hi is not None else 0.0)
+        err = C.c_double()
+        self._check(lib().gld_set_pair_noise_on(self._h, int(degree), C.byref(l), C.byref(h), C.byref(err)))
+        return float(l.value), float(h.value), float(err.value)
+
+    def pair_noise_spectrum(self) -> dict:
+        """The last Lanczos run of set_pair_noise_on: Ritz extremes, the
+        Krylov dimension used, and the interval."""
+        out = np.zeros(5)
+        self._check(lib().gld_pair_noise_spectrum(self._h, _ptr(out)))
+        return dict(ritz_min=float(out[0]), ritz_max=float(out[1]), krylov_dim=int(out[2]), lo=float(out[3]),
+                    hi=float(out[4]))
 
     def set_pair_noise_krylov(self, tol: float = 1e-6, kmax: int = 32):
         """Pair-correlated noise by a Lanczos iteration per frequency
@@ -687,4 +713,18 @@ def pair_noise_filters(ks_weights, g_weights, kT: float, dt: float, lam: float, 
                                       int(bool(psd_clamp)), _ptr(taps), C.byref(err))
     if st != 0:
         raise GLDError(st, "gld_pair_noise_filters failed")
+    return taps, float(err.value)
+
+
+def pair_noise_filters_on(ks_weights, g_weights, kT: float, dt: float, lo: float, hi: float, degree: int,
+                          psd_clamp=False):
+    """pair_noise_filters on the spectral interval [lo, hi]:
+    F_n = sum_k T_k((M - c) / rho) Z_k, c and rho its centre and half-width."""
+    ks, g = _f64(ks_weights).ravel(), _f64(g_weights).ravel()
+    M = ks.size
+    taps, err = np.zeros((int(degree) + 1, 2 * M - 1)), C.c_double()
+    st = lib().gld_pair_noise_filters_on(_ptr(ks), _ptr(g), M, float(kT), float(dt), float(lo), float(hi),
+                                         int(degree), int(bool(psd_clamp)), _ptr(taps), C.byref(err))
+    if st != 0:
+        raise GLDError(st, "gld_pair_noise_filters_on failed")
     return taps, float(err.value)

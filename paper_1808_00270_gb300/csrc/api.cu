@@ -195,6 +195,10 @@ cudaError_t launch_noise(gld_ctx* c, cudaStream_t s)
     for (int k = 1; k <= P.pn_deg && e == cudaSuccess; ++k)
         e = launch_noise_filter(P, c->B.ctrl, c->W, c->d_pntaps + (size_t)k * c->la,
                                 c->d_zblk + (size_t)(k - 1) * P.T * 3 * P.n_pad, wmap, c->num_sms, s);
+    // an interval from Ritz values: checked again at R_n of every block
+    if (P.pn_iv && e == cudaSuccess)
+        e = launch_pn_spectrum(P, c->B, c->d_lzv, c->d_lzpart, c->d_lzab, c->pn_lo, c->pn_hi, 1,
+                               c->d_lzab + 2 * kPnLanczosSteps + 1, s);
     return e;
 }
 
@@ -303,6 +307,24 @@ cudaError_t capture_step_conditional(gld_ctx* c, cudaStream_t s, bool overlap)
     if (e == cudaSuccess) e = launch_pcorr(c->P, c->B, s);
     if (overlap && e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join, 0);
     return e;
+}
+
+// Turns the Chebyshev form of the pair noise off and releases its buffers.
+void pn_release(gld_ctx* c)
+{
+    for (float** p : {&c->d_pntaps, &c->d_zblk, &c->d_bvec, &c->d_lzv}) {
+        dfree(c, *p);
+        *p = nullptr;
+    }
+    for (double** p : {&c->d_lzpart, &c->d_lzab}) {
+        dfree(c, *p);
+        *p = nullptr;
+    }
+    dfree(c, c->d_rowsum);
+    c->d_rowsum = nullptr;
+    c->P.pn_deg = 0;
+    c->P.pn_iv = 0;
+    c->P.pn_cen = 0.f;
 }
 
 // ---- pair-correlated noise by a Lanczos iteration per frequency ------------
@@ -566,7 +588,8 @@ gld_status ctx_check_err(gld_ctx* c, unsigned err)
     else if (err & kErrCheck) fail(c, GLD_E_CUDA, "a kernel's own bounds or alignment check failed");
     else if (err & kErrNoise) fail(c, GLD_E_CUDA, "a step ran outside its noise block");
     else if (err & kErrPnBound) {
-        c->msg = "pair noise: a Gershgorin row sum of the pair matrix exceeded lambda (set a larger one)";
+        c->msg = "pair noise: the spectrum of the pair matrix left the interpolation interval (a Gershgorin row "
+                 "sum above lambda, or a Ritz value outside [lo, hi]): set a wider one";
         if (c->latched == GLD_OK) c->latched = GLD_E_NOT_PSD;
     }
     return c->latched;
@@ -848,15 +871,11 @@ gld_status gld_set_kernels(gld_ctx* c, const double* Ks, int32_t Q, const double
     c->B.ftab = nullptr;
     // the pair noise and the perpendicular factors belong to the previous
     // kernels: off, and their buffers released (stream-ordered like ftab's)
-    c->P.pn_deg = 0;
     c->P.perp = 0;
     invalidate_graph(c);
-    for (float** p : {&c->d_pntaps, &c->d_zblk, &c->d_bvec, &c->fptab}) {
-        dfree(c, *p);
-        *p = nullptr;
-    }
-    dfree(c, c->d_rowsum);
-    c->d_rowsum = nullptr;
+    pn_release(c);
+    dfree(c, c->fptab);
+    c->fptab = nullptr;
     c->B.fptab = nullptr;
     kry_release(c);
     const int M = c->P.m_max;
@@ -1445,13 +1464,17 @@ gld_status gld_set_perpendicular(gld_ctx* c, const double* fp, const double* fsp
     return sync_and_check(c);
 }
 
-gld_status gld_pair_noise_filters(const double* ks, const double* g, int32_t m_max, double kT, double dt,
-                                  double lambda, int32_t degree, int32_t psd_clamp, double* taps, double* cheb_err)
+gld_status gld_pair_noise_filters_on(const double* ks, const double* g, int32_t m_max, double kT, double dt,
+                                     double lo, double hi, int32_t degree, int32_t psd_clamp, double* taps,
+                                     double* cheb_err)
 {
-    if (!ks || !g || !taps || m_max < 2 || degree < 1 || degree > kMaxPnDegree || !(lambda > 0) || !(dt > 0))
+    if (!ks || !g || !taps || m_max < 2 || degree < 1 || degree > kMaxPnDegree || !(lo < hi) || !std::isfinite(lo) ||
+        !std::isfinite(hi) || !(dt > 0))
         return GLD_E_INVAL;
     const int M = m_max, K = degree, H = M - 1;
     const long long L = 2LL * M - 1;
+    // the interval [cen - rad, cen + rad]; cen is exactly 0 for a symmetric one
+    const double cen = 0.5 * (lo + hi), rad = 0.5 * (hi - lo);
     // transforms (Eq. FT) of the noise targets kT a_m K_m / dt (a_0 = 2) of
     // the self kernel and of the pair term's time factor, in FP64
     std::vector<double> hh(M), gh(M);
@@ -1465,14 +1488,18 @@ gld_status gld_pair_noise_filters(const double* ks, const double* g, int32_t m_m
         }
         hh[w] = kT / dt * a;
         gh[w] = kT / dt * b;
-        hmax = std::max(hmax, std::fabs(hh[w]) + std::fabs(gh[w]) * lambda);
-        worst = std::min(worst, hh[w] - std::fabs(gh[w]) * lambda);
+        // h_w + g_w mu is linear in mu: its minimum over the interval is at an end
+        hmax = std::max(hmax, std::fabs(hh[w]) + std::fabs(gh[w]) * std::max(std::fabs(lo), std::fabs(hi)));
+        worst = std::min(worst, std::min(hh[w] + gh[w] * lo, hh[w] + gh[w] * hi));
     }
     if (worst < -1e-12 * hmax && !psd_clamp) return GLD_E_NOT_PSD;
-    // Chebyshev interpolation of phi_w(x) = sqrt(h_w + g_w lambda x) on
+    // Chebyshev interpolation of phi_w(x) = sqrt(h_w + g_w (cen + rad x)) on
     // [-1, 1] at degree K, its error on a fine grid, and the filter taps
     // a_k[s] = (c_0k + 2 sum_{w>=1} c_wk cos(2 pi w s / L)) / L
-    auto phi = [&](int w, double x) { return std::sqrt(std::max(hh[w] + gh[w] * lambda * x, 0.0)); };
+    auto phi = [&](int w, double x) {
+        const double gm = cen == 0.0 ? gh[w] * rad * x : gh[w] * (cen + rad * x);
+        return std::sqrt(std::max(hh[w] + gm, 0.0));
+    };
     const int nc = K + 1;
     std::vector<double> cw((size_t)M * nc);
     double err = 0.0;
@@ -1507,17 +1534,55 @@ gld_status gld_pair_noise_filters(const double* ks, const double* g, int32_t m_m
     return GLD_OK;
 }
 
-gld_status gld_set_pair_noise(gld_ctx* c, int32_t degree, double* lambda, double* cheb_err)
+gld_status gld_pair_noise_filters(const double* ks, const double* g, int32_t m_max, double kT, double dt,
+                                  double lambda, int32_t degree, int32_t psd_clamp, double* taps, double* cheb_err)
 {
-    if (!c) return GLD_E_INVAL;
-    StepParams& P = c->P;
-    if (degree < 0 || degree > kMaxPnDegree) return fail(c, GLD_E_INVAL, "gld_set_pair_noise: degree outside [0, 16]");
-    if (degree > 0 && !c->have_kernels) return fail(c, GLD_E_STATE, "gld_set_pair_noise: set the kernels first");
+    if (!(lambda > 0)) return GLD_E_INVAL;
+    return gld_pair_noise_filters_on(ks, g, m_max, kT, dt, -lambda, lambda, degree, psd_clamp, taps, cheb_err);
+}
+
+namespace {
+
+// Ritz extremes of the pair matrix are widened by this fraction of their
+// spread on each side to give the interpolation interval (the extremes are
+// set by the closest pairs, so they move as pairs meet: one pair at contact
+// alone gives +-f(0)); an end is kept this fraction of the way from the
+// spectrum to where h_w + g_w mu changes sign for some frequency.
+constexpr double kPnMargin = 0.25, kPnPsdGap = 0.05;
+
+// The transforms (Eq. FT) h_w, g_w of kT a_m K_m / dt (a_0 = 2) for the
+// self kernel's and the pair term's discrete weights, FP64.
+void pn_transforms(const double* ks, const double* g, int M, double kT, double dt, std::vector<double>& hh,
+                   std::vector<double>& gh)
+{
+    const long long L = 2LL * M - 1;
+    hh.assign(M, 0.0);
+    gh.assign(M, 0.0);
+    for (int w = 0; w < M; ++w) {
+        double a = 2.0 * ks[0], b = 2.0 * g[0];
+        for (int m = 1; m < M; ++m) {
+            const double cs = std::cos(2.0 * M_PI * (double)(((long long)w * m) % L) / (double)L);
+            a += 2.0 * ks[m] * cs;
+            b += 2.0 * g[m] * cs;
+        }
+        hh[w] = kT / dt * a;
+        gh[w] = kT / dt * b;
+    }
+}
+
+// The kernel forms the Chebyshev form takes: one separable pair term and at
+// most one self-difference term, whose time factor must be a multiple c of
+// the pair term's (gs = c g: then every transformed matrix is
+// h_w 1 + g_w (M_pair + c D_self)); c into *cs.
+gld_status pn_check_form(gld_ctx* c, const char* who, int32_t degree, double* cs)
+{
+    const StepParams& P = c->P;
+    *cs = 0.0;
+    if (degree < 0 || degree > kMaxPnDegree) return fail(c, GLD_E_INVAL, std::string(who) + ": degree outside [0, 16]");
+    if (degree > 0 && !c->have_kernels) return fail(c, GLD_E_STATE, std::string(who) + ": set the kernels first");
     if (degree > 0 && (P.Q != 1 || P.Qs > 1))
-        return fail(c, GLD_E_INVAL, "gld_set_pair_noise: needs one separable pair term and at most one self-difference term");
-    // a self-difference term must share the pair term's time factor (gs = c g):
-    // then every transformed matrix is h_w 1 + g_w (M_pair + c D_self)
-    double cs_ratio = 0.0;
+        return fail(c, GLD_E_INVAL,
+                    std::string(who) + ": needs one separable pair term and at most one self-difference term");
     if (degree > 0 && P.Qs == 1) {
         const int M = P.m_max;
         const double* g = c->wts.data() + M;
@@ -1528,26 +1593,62 @@ gld_status gld_set_pair_noise(gld_ctx* c, int32_t degree, double* lambda, double
             sg += gs[m] * g[m];
             smax = std::max(smax, std::fabs(gs[m]));
         }
-        cs_ratio = gg > 0 ? sg / gg : 0.0;
+        const double ratio = gg > 0 ? sg / gg : 0.0;
         double dev = 0.0;
-        for (int m = 0; m < M; ++m) dev = std::max(dev, std::fabs(gs[m] - cs_ratio * g[m]));
+        for (int m = 0; m < M; ++m) dev = std::max(dev, std::fabs(gs[m] - ratio * g[m]));
         if (dev > 1e-9 * smax)
             return fail(c, GLD_E_INVAL,
-                        "gld_set_pair_noise: the self-difference term must have the pair term's time factor (gs = c g)");
+                        std::string(who) + ": the self-difference term must have the pair term's time factor (gs = c g)");
+        *cs = ratio;
     }
+    return GLD_OK;
+}
+
+// Installs the Chebyshev form of degree K on the spectral interval [lo, hi]:
+// the K + 1 filters, the blocks Z_1 .. Z_K and the Clenshaw vectors.
+gld_status pn_install(gld_ctx* c, const char* who, int K, double lo, double hi, double* cheb_err)
+{
+    StepParams& P = c->P;
+    const int M = P.m_max, H = M - 1;
+    std::vector<double> td((size_t)(K + 1) * (2 * H + 1));
+    const gld_status fs = gld_pair_noise_filters_on(c->wts.data(), c->wts.data() + M, M, c->prm.kT, c->prm.dt, lo, hi,
+                                                    K, c->prm.psd_clamp, td.data(), cheb_err);
+    if (fs == GLD_E_NOT_PSD)
+        return fail(c, GLD_E_NOT_PSD,
+                    std::string(who) + ": h_w + g_w mu < 0 for some frequency w and some mu of the spectral interval: "
+                                       "positive semi-definiteness of the correlation matrices is not guaranteed "
+                                       "(psd_clamp clamps)");
+    if (fs != GLD_OK) return fail(c, fs, std::string(who) + ": invalid filter arguments");
+    std::vector<float> taps((size_t)(K + 1) * c->la, 0.0f);
+    for (int k = 0; k <= K; ++k)
+        for (int sg = 0; sg <= 2 * H; ++sg) taps[(size_t)k * c->la + sg] = (float)td[(size_t)k * (2 * H + 1) + sg];
+    c->d_pntaps = (float*)dalloc(c, sizeof(float) * taps.size());
+    c->d_zblk = (float*)dalloc(c, sizeof(float) * (size_t)K * P.T * 3 * P.n_pad);
+    c->d_bvec = (float*)dalloc(c, sizeof(float) * 3 * 3 * (size_t)P.n_pad);
+    if (!c->d_pntaps || !c->d_zblk || !c->d_bvec) return fail(c, GLD_E_NOMEM, std::string(who) + ": allocation failed");
+    GLD_CUDA(c, cudaMemcpyAsync(c->d_pntaps, taps.data(), sizeof(float) * taps.size(), cudaMemcpyHostToDevice, c->st));
+    const double cen = 0.5 * (lo + hi), rad = 0.5 * (hi - lo);
+    P.pn_deg = K;
+    P.pn_cen = (float)cen;  // exactly 0 for the symmetric bound
+    P.pn_lambda = (float)rad;
+    P.pn_inv_lambda = (float)(1.0 / rad);
+    return GLD_OK;
+}
+
+}  // namespace
+
+gld_status gld_set_pair_noise(gld_ctx* c, int32_t degree, double* lambda, double* cheb_err)
+{
+    if (!c) return GLD_E_INVAL;
+    StepParams& P = c->P;
+    double cs_ratio = 0.0;
+    GLD_TRY(pn_check_form(c, "gld_set_pair_noise", degree, &cs_ratio));
     GLD_TRY(sync_and_check(c));
-    for (float** p : {&c->d_pntaps, &c->d_zblk, &c->d_bvec}) {
-        dfree(c, *p);
-        *p = nullptr;
-    }
-    dfree(c, c->d_rowsum);
-    c->d_rowsum = nullptr;
-    P.pn_deg = 0;
+    pn_release(c);
     kry_release(c);  // one form of pair noise at a time
     invalidate_graph(c);
     GLD_TRY(invalidate_noise(c));
     if (degree == 0) return sync_and_check(c);
-    const int M = P.m_max, K = degree;
     // the bound on the spectrum of the pair matrix: given, or 1.25 x the
     // largest Gershgorin row sum at the current positions
     double lam = lambda ? *lambda : 0.0;
@@ -1564,28 +1665,82 @@ gld_status gld_set_pair_noise(gld_ctx* c, int32_t degree, double* lambda, double
         lam = std::max(1.25 * (double)mx, 1e-6);
     }
     if (lambda) *lambda = lam;
-    const int H = M - 1;
-    std::vector<double> td((size_t)(K + 1) * (2 * H + 1));
-    const gld_status fs = gld_pair_noise_filters(c->wts.data(), c->wts.data() + M, M, c->prm.kT, c->prm.dt, lam, K,
-                                                 c->prm.psd_clamp, td.data(), cheb_err);
-    if (fs == GLD_E_NOT_PSD)
-        return fail(c, GLD_E_NOT_PSD,
-                    "gld_set_pair_noise: h_w - |g_w| lambda < 0 for some frequency: positive semi-definiteness of the "
-                    "correlation matrices is not guaranteed over the spectral bound (psd_clamp clamps)");
-    if (fs != GLD_OK) return fail(c, fs, "gld_set_pair_noise: invalid filter arguments");
-    std::vector<float> taps((size_t)(K + 1) * c->la, 0.0f);
-    for (int k = 0; k <= K; ++k)
-        for (int sg = 0; sg <= 2 * H; ++sg) taps[(size_t)k * c->la + sg] = (float)td[(size_t)k * (2 * H + 1) + sg];
-    c->d_pntaps = (float*)dalloc(c, sizeof(float) * taps.size());
-    c->d_zblk = (float*)dalloc(c, sizeof(float) * (size_t)K * P.T * 3 * P.n_pad);
-    c->d_bvec = (float*)dalloc(c, sizeof(float) * 3 * 3 * (size_t)P.n_pad);
-    if (!c->d_pntaps || !c->d_zblk || !c->d_bvec) return fail(c, GLD_E_NOMEM, "gld_set_pair_noise: allocation failed");
-    GLD_CUDA(c, cudaMemcpyAsync(c->d_pntaps, taps.data(), sizeof(float) * taps.size(), cudaMemcpyHostToDevice, c->st));
-    P.pn_deg = K;
-    P.pn_cs = (float)cs_ratio;
-    P.pn_lambda = (float)lam;
-    P.pn_inv_lambda = (float)(1.0 / lam);
+    GLD_TRY(pn_install(c, "gld_set_pair_noise", degree, -lam, lam, cheb_err));
     return sync_and_check(c);
+}
+
+gld_status gld_set_pair_noise_on(gld_ctx* c, int32_t degree, double* lo, double* hi, double* cheb_err)
+{
+    if (!c) return GLD_E_INVAL;
+    StepParams& P = c->P;
+    double cs_ratio = 0.0;
+    GLD_TRY(pn_check_form(c, "gld_set_pair_noise_on", degree, &cs_ratio));
+    GLD_TRY(sync_and_check(c));
+    pn_release(c);
+    kry_release(c);
+    invalidate_graph(c);
+    GLD_TRY(invalidate_noise(c));
+    if (degree == 0) return sync_and_check(c);
+    P.pn_cs = (float)cs_ratio;
+    bool ok = true;
+    c->d_lzv = alloc_n<float>(c, 4 * 3 * (size_t)P.n_pad, ok);
+    c->d_lzpart = alloc_n<double>(c, 2 * (size_t)pn_spectrum_blocks(P), ok);
+    c->d_lzab = alloc_n<double>(c, 2 * kPnLanczosSteps + 1 + 3, ok);
+    if (!ok) {
+        pn_release(c);
+        return fail(c, GLD_E_NOMEM, "gld_set_pair_noise_on: allocation failed");
+    }
+    double l = lo ? *lo : 0.0, h = hi ? *hi : 0.0;
+    if (!(l < h)) {
+        // Ritz extremes at the current positions, widened by kPnMargin of
+        // their spread on each side
+        double th[3];
+        GLD_CUDA(c, launch_pn_spectrum(P, c->B, c->d_lzv, c->d_lzpart, c->d_lzab, 0.0, 0.0, 0,
+                                       c->d_lzab + 2 * kPnLanczosSteps + 1, c->st));
+        GLD_CUDA(c, cudaMemcpyAsync(th, c->d_lzab + 2 * kPnLanczosSteps + 1, sizeof th, cudaMemcpyDeviceToHost, c->st));
+        GLD_TRY(sync_and_check(c));
+        const double wd = std::max({th[1] - th[0], 1e-3 * std::max(std::fabs(th[0]), std::fabs(th[1])), 1e-12});
+        l = th[0] - kPnMargin * wd;
+        h = th[1] + kPnMargin * wd;
+        // h_w + g_w mu >= 0 for mu >= mlo (g_w > 0) and mu <= mhi (g_w < 0)
+        std::vector<double> hw, gw;
+        pn_transforms(c->wts.data(), c->wts.data() + P.m_max, P.m_max, c->prm.kT, c->prm.dt, hw, gw);
+        double mlo = -INFINITY, mhi = INFINITY;
+        for (int w = 0; w < P.m_max; ++w) {
+            if (gw[w] > 0) mlo = std::max(mlo, -hw[w] / gw[w]);
+            if (gw[w] < 0) mhi = std::min(mhi, -hw[w] / gw[w]);
+        }
+        if (th[0] > mlo) l = std::max(l, mlo + kPnPsdGap * (th[0] - mlo));
+        if (th[1] < mhi) h = std::min(h, mhi - kPnPsdGap * (mhi - th[1]));
+    }
+    if (!std::isfinite(l) || !std::isfinite(h)) {
+        pn_release(c);
+        return fail(c, GLD_E_INVAL, "gld_set_pair_noise_on: the spectral interval is not finite");
+    }
+    const gld_status st = pn_install(c, "gld_set_pair_noise_on", degree, l, h, cheb_err);
+    if (st != GLD_OK) {
+        pn_release(c);
+        return st;
+    }
+    P.pn_iv = 1;
+    c->pn_lo = l;
+    c->pn_hi = h;
+    if (lo) *lo = l;
+    if (hi) *hi = h;
+    return sync_and_check(c);
+}
+
+gld_status gld_pair_noise_spectrum(gld_ctx* c, double* out)
+{
+    if (!c || !out) return GLD_E_INVAL;
+    if (!c->P.pn_iv || !c->d_lzab) return fail(c, GLD_E_STATE, "gld_pair_noise_spectrum: gld_set_pair_noise_on is off");
+    GLD_TRY(sync_and_check(c));
+    GLD_CUDA(c, cudaMemcpyAsync(out, c->d_lzab + 2 * kPnLanczosSteps + 1, 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                                c->st));
+    GLD_CUDA(c, cudaStreamSynchronize(c->st));
+    out[3] = c->pn_lo;
+    out[4] = c->pn_hi;
+    return GLD_OK;
 }
 
 gld_status gld_set_pair_noise_krylov(gld_ctx* c, double tol, int32_t kmax)
@@ -1599,14 +1754,7 @@ gld_status gld_set_pair_noise_krylov(gld_ctx* c, double tol, int32_t kmax)
     kry_release(c);
     invalidate_graph(c);
     if (!(tol > 0)) return sync_and_check(c);
-    // the Chebyshev form is replaced
-    for (float** p : {&c->d_pntaps, &c->d_zblk, &c->d_bvec}) {
-        dfree(c, *p);
-        *p = nullptr;
-    }
-    dfree(c, c->d_rowsum);
-    c->d_rowsum = nullptr;
-    P.pn_deg = 0;
+    pn_release(c);  // the Chebyshev form is replaced
     auto& K = c->kry;
     const int M = P.m_max, Mp = (M + 31) & ~31, nacc = P.nacc;
     const long long L = 2LL * M - 1;

@@ -66,6 +66,13 @@ struct gld_ctx {
     float* d_zblk = nullptr;
     float* d_bvec = nullptr;
     unsigned* d_rowsum = nullptr;
+    // the Lanczos run that finds (and at each noise block checks) the
+    // interval of the pair matrix's spectrum: four vectors [3][n_pad], two
+    // sets of block partials, alpha/beta and the Ritz extremes; the interval
+    double* d_lzpart = nullptr;
+    float* d_lzv = nullptr;
+    double* d_lzab = nullptr;
+    double pn_lo = 0.0, pn_hi = 0.0;
     // pair-correlated noise by a Lanczos iteration per frequency: M
     // frequencies (Mp padded to 32), at most kmax iterations, the stopping
     // tolerance, device vectors and scalars, and the last step's statistics

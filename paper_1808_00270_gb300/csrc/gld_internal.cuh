@@ -20,6 +20,7 @@ constexpr int kPcMaxOriginBins = 2048;  // origins x bins of the pair correlatio
 constexpr int kVacfMaxBlocks = 256;  // particle blocks of the VACF grid at most
 constexpr int kMaxNoiseBlock = 64;  // register-resident outputs per FIR thread
 constexpr int kMaxPnDegree = 16;    // Chebyshev degree of the pair-correlated noise
+constexpr int kPnLanczosSteps = 32;  // Lanczos steps for the pair matrix's extreme eigenvalues
 
 // Latched device error bits.
 enum : unsigned { kErrNonFinite = 1u, kErrTimeout = 2u, kErrNoise = 4u, kErrNbrOverflow = 8u, kErrPnBound = 16u,
@@ -82,9 +83,13 @@ struct StepParams {
     int pc_nbins;
     float pc_rmax2, pc_inv_dr;  // r_max^2, nbins / r_max
     // pair-correlated noise: Chebyshev degree (0: self-kernel noise only) and
-    // the bound lambda on the spectrum of the pair matrix, with 1 / lambda
+    // the interval [pn_cen - pn_lambda, pn_cen + pn_lambda] holding the
+    // spectrum of the pair matrix (pn_cen = 0: the symmetric bound lambda),
+    // with 1 / pn_lambda; pn_iv: the interval comes from Ritz values and is
+    // checked by a Lanczos run at each noise block (else Gershgorin, each step)
     int pn_deg;
-    float pn_lambda, pn_inv_lambda;
+    float pn_lambda, pn_inv_lambda, pn_cen;
+    int pn_iv;
     float pn_cs;  // self-difference time factor = pn_cs x the pair term's (when Qs = 1)
     // perpendicular factors of the pair and self-difference terms are set
     // (rows of ParticleBuffers::fptab)

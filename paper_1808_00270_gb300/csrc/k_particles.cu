@@ -967,6 +967,44 @@ struct PnStage {
     int b1_rows, b2_rows, out_rows, last;
 };
 
+// (M b)_i for the vector b [3][n_pad]: the pair blocks f e e^T + fp (1 - e e^T)
+// on the neighbours' entries and, with a self-difference term, the diagonal
+// blocks pn_cs (fs e e^T + fsp (1 - e e^T)) on the own entry; rowsum: the
+// Gershgorin row sum of the blocks' spectral norms.
+__device__ __forceinline__ void pn_apply(const StepParams& P, const float4* __restrict__ pos,
+                                         const int* __restrict__ nbr, const int* __restrict__ nbr_cnt,
+                                         const float* __restrict__ ftab, const float* __restrict__ fptab, int id,
+                                         const float* __restrict__ b, float& mx, float& my, float& mz, float& rowsum)
+{
+    const long long np = P.n_pad;
+    const float4 pi = pos[id];
+    const float bix = b[id], biy = b[np + id], biz = b[2 * np + id];  // own entry, for the self-difference blocks
+    mx = my = mz = rowsum = 0.f;
+    for_each_listed(pi, id, nbr, nbr_cnt[id], P.n_pad, pos, P, [&](int jd, float dx, float dy, float dz, float r2) {
+        const float r = sqrtf(r2);
+        const float inv_r = 1.0f / r;
+        const float ex = dx * inv_r, ey = dy * inv_r, ez = dz * inv_r;
+        const float xr = fmaxf(r, P.rc_min) * P.inv_dr;
+        const float f = table_at(ftab, P.nr, xr);
+        const float fp = P.perp ? table_at(fptab, P.nr, xr) : 0.f;  // block f e e^T + fp (1 - e e^T)
+        const float bx = __ldg(b + jd), by = __ldg(b + np + jd), bz = __ldg(b + 2 * np + jd);
+        const float eb = (f - fp) * dot3(ex, ey, ez, bx, by, bz);
+        mx = fmaf(eb, ex, fmaf(fp, bx, mx));
+        my = fmaf(eb, ey, fmaf(fp, by, my));
+        mz = fmaf(eb, ez, fmaf(fp, bz, mz));
+        rowsum += fmaxf(fabsf(f), fabsf(fp));  // the block's spectral norm
+        if (P.Qs > 0) {
+            const float fs = P.pn_cs * table_at(ftab + P.Q * P.nr, P.nr, xr);
+            const float fsp = P.perp ? P.pn_cs * table_at(fptab + P.Q * P.nr, P.nr, xr) : 0.f;
+            const float ei = (fs - fsp) * dot3(ex, ey, ez, bix, biy, biz);
+            mx = fmaf(ei, ex, fmaf(fsp, bix, mx));
+            my = fmaf(ei, ey, fmaf(fsp, biy, my));
+            mz = fmaf(ei, ez, fmaf(fsp, biz, mz));
+            rowsum += fmaxf(fabsf(fs), fabsf(fsp));
+        }
+    });
+}
+
 __global__ void __launch_bounds__(kThreads)
     pn_stage(const StepParams P, Ctrl* __restrict__ ctrl, const float4* __restrict__ pos, const int* __restrict__ nbr,
              const int* __restrict__ nbr_cnt, const float* __restrict__ ftab, const float* __restrict__ fptab,
@@ -985,33 +1023,13 @@ __global__ void __launch_bounds__(kThreads)
     const float* b2 = S.b2 ? S.b2 + (S.b2_rows ? roff : 0) : nullptr;
     float* out = S.out + (S.out_rows ? roff : 0);
     const float* z = S.z + roff;
-    const float4 pi = pos[id];
-    const float bix = b1[id], biy = b1[np + id], biz = b1[2 * np + id];  // own entry, for the self-difference blocks
-    float mx = 0.f, my = 0.f, mz = 0.f, rowsum = 0.f;
-    for_each_listed(pi, id, nbr, nbr_cnt[id], P.n_pad, pos, P, [&](int jd, float dx, float dy, float dz, float r2) {
-        const float r = sqrtf(r2);
-        const float inv_r = 1.0f / r;
-        const float ex = dx * inv_r, ey = dy * inv_r, ez = dz * inv_r;
-        const float xr = fmaxf(r, P.rc_min) * P.inv_dr;
-        const float f = table_at(ftab, P.nr, xr);
-        const float fp = P.perp ? table_at(fptab, P.nr, xr) : 0.f;  // block f e e^T + fp (1 - e e^T)
-        const float bx = __ldg(b1 + jd), by = __ldg(b1 + np + jd), bz = __ldg(b1 + 2 * np + jd);
-        const float eb = (f - fp) * dot3(ex, ey, ez, bx, by, bz);
-        mx = fmaf(eb, ex, fmaf(fp, bx, mx));
-        my = fmaf(eb, ey, fmaf(fp, by, my));
-        mz = fmaf(eb, ez, fmaf(fp, bz, mz));
-        rowsum += fmaxf(fabsf(f), fabsf(fp));  // the block's spectral norm
-        if (P.Qs > 0) {
-            // self-difference term pn_cs (fs e e^T + fsp (1 - e e^T)) on the own entry b_i
-            const float fs = P.pn_cs * table_at(ftab + P.Q * P.nr, P.nr, xr);
-            const float fsp = P.perp ? P.pn_cs * table_at(fptab + P.Q * P.nr, P.nr, xr) : 0.f;
-            const float ei = (fs - fsp) * dot3(ex, ey, ez, bix, biy, biz);
-            mx = fmaf(ei, ex, fmaf(fsp, bix, mx));
-            my = fmaf(ei, ey, fmaf(fsp, biy, my));
-            mz = fmaf(ei, ez, fmaf(fsp, biz, mz));
-            rowsum += fmaxf(fabsf(fs), fabsf(fsp));
-        }
-    });
+    float mx, my, mz, rowsum;
+    pn_apply(P, pos, nbr, nbr_cnt, ftab, fptab, id, b1, mx, my, mz, rowsum);
+    if (P.pn_cen != 0.f) {  // the interval [cen - rho, cen + rho]: (M - cen) b1
+        mx = fmaf(-P.pn_cen, b1[id], mx);
+        my = fmaf(-P.pn_cen, b1[np + id], my);
+        mz = fmaf(-P.pn_cen, b1[2 * np + id], mz);
+    }
     const float c = (S.last ? 1.0f : 2.0f) * P.pn_inv_lambda;
     const float ox = fmaf(c, mx, z[id]) - (b2 ? b2[id] : 0.f);
     const float oy = fmaf(c, my, z[np + id]) - (b2 ? b2[np + id] : 0.f);
@@ -1019,7 +1037,9 @@ __global__ void __launch_bounds__(kThreads)
     out[id] = ox;
     out[np + id] = oy;
     out[2 * np + id] = oz;
-    if (S.last && rowsum > P.pn_lambda) atomicOr(&ctrl->err, kErrPnBound);
+    // the symmetric bound is checked every step by Gershgorin; an interval
+    // from Ritz values by the Lanczos run at each noise block
+    if (S.last && !P.pn_iv && rowsum > P.pn_lambda) atomicOr(&ctrl->err, kErrPnBound);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -1038,6 +1058,163 @@ __global__ void __launch_bounds__(kThreads)
                                              P.perp ? fabsf(table_at(fptab + P.Q * P.nr, P.nr, xr)) : 0.f);
     });
     atomicMax(out, __float_as_uint(rowsum));  // non-negative floats order as their bits
+}
+
+// ---- extreme eigenvalues of the pair matrix by a Lanczos run ---------------
+// kPnLanczosSteps steps from a fixed +-1 start vector, vectors [3][n_pad] in
+// FP32 kept unnormalised (r_k, v_k = r_k / beta_k), every dot product summed
+// in FP64 as per-block partials that each block of the next kernel folds in
+// the same fixed order, so all blocks (and every run) see the same bits.  The
+// extreme eigenvalues of the tridiagonal matrix (the Ritz values) are found
+// by Sturm-sequence bisection in one thread.  ab: alpha_0 .. alpha_{K-1},
+// then beta_0 .. beta_K.
+__device__ __forceinline__ double block_sum_d(double v, double* red)
+{
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ double fold_partials(const double* __restrict__ part, int nblk, double* red)
+{
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[b];
+    return block_sum_d(s, red);
+}
+
+__global__ void __launch_bounds__(kThreads) lz_start(const StepParams P, float* __restrict__ r0, double* __restrict__ part)
+{
+    __shared__ double red[kThreads];
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long np = P.n_pad;
+    double s = 0.0;
+    if (id < P.n)
+        for (int c = 0; c < 3; ++c) {
+            const uint32_t h = (uint32_t)(c * np + id) * 0x9E3779B1u;  // Fibonacci hash: a fixed sign pattern
+            r0[c * np + id] = (h >> 31) ? -1.f : 1.f;
+            s += 1.0;
+        }
+    else if (id < np)
+        for (int c = 0; c < 3; ++c) r0[c * np + id] = 0.f;
+    const double t = block_sum_d(s, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// y = M v_k, v_k = r_k / beta_k (beta_k from the partials of |r_k|^2); partial
+// sums of v_k . y.
+__global__ void __launch_bounds__(kThreads)
+    lz_matvec(const StepParams P, const float4* __restrict__ pos, const int* __restrict__ nbr,
+              const int* __restrict__ nbr_cnt, const float* __restrict__ ftab, const float* __restrict__ fptab,
+              const float* __restrict__ rk, const double* __restrict__ part_in, int nblk, float* __restrict__ y,
+              double* __restrict__ part_out, double* __restrict__ ab, int k)
+{
+    __shared__ double red[kThreads];
+    const double beta = sqrt(fold_partials(part_in, nblk, red));
+    if (blockIdx.x == 0 && threadIdx.x == 0) ab[kPnLanczosSteps + k] = beta;
+    const float invb = beta > 0.0 ? (float)(1.0 / beta) : 0.f;
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long np = P.n_pad;
+    double a = 0.0;
+    if (id < P.n) {
+        float mx, my, mz, rowsum;
+        pn_apply(P, pos, nbr, nbr_cnt, ftab, fptab, id, rk, mx, my, mz, rowsum);
+        const float yx = invb * mx, yy = invb * my, yz = invb * mz;
+        y[id] = yx;
+        y[np + id] = yy;
+        y[2 * np + id] = yz;
+        a = (double)(invb * rk[id]) * yx + (double)(invb * rk[np + id]) * yy + (double)(invb * rk[2 * np + id]) * yz;
+    } else if (id < np) {
+        y[id] = y[np + id] = y[2 * np + id] = 0.f;
+    }
+    const double t = block_sum_d(a, red);
+    if (threadIdx.x == 0) part_out[blockIdx.x] = t;
+}
+
+// r_{k+1} = y - alpha_k v_k - beta_k v_{k-1}; partial sums of |r_{k+1}|^2.
+__global__ void __launch_bounds__(kThreads)
+    lz_update(const StepParams P, const float* __restrict__ y, const float* __restrict__ rk,
+              const float* __restrict__ rkm1, const double* __restrict__ part_in, int nblk, double* __restrict__ ab,
+              int k, float* __restrict__ rkp1, double* __restrict__ part_out)
+{
+    __shared__ double red[kThreads];
+    const double alpha = fold_partials(part_in, nblk, red);
+    if (blockIdx.x == 0 && threadIdx.x == 0) ab[k] = alpha;
+    const double bk = ab[kPnLanczosSteps + k], bkm1 = k > 0 ? ab[kPnLanczosSteps + k - 1] : 0.0;
+    const float ib = bk > 0.0 ? (float)(1.0 / bk) : 0.f, ibm = (k > 0 && bkm1 > 0.0) ? (float)(1.0 / bkm1) : 0.f;
+    const float a = (float)alpha, b = (float)bk;
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long np = P.n_pad;
+    double s = 0.0;
+    if (id < np)
+        for (int c = 0; c < 3; ++c) {
+            const size_t e = (size_t)c * np + id;
+            float r = fmaf(-a, ib * rk[e], y[e]);
+            if (k > 0) r = fmaf(-b, ibm * rkm1[e], r);
+            rkp1[e] = r;
+            s += (double)r * r;
+        }
+    const double t = block_sum_d(s, red);
+    if (threadIdx.x == 0) part_out[blockIdx.x] = t;
+}
+
+// Number of eigenvalues below x of the j x j tridiagonal matrix (Sturm).
+__device__ int sturm_count(const double* al, const double* be, int j, double x)
+{
+    int cnt = 0;
+    double d = 1.0;
+    for (int i = 0; i < j; ++i) {
+        const double off = i > 0 ? be[i] * be[i] : 0.0;
+        d = al[i] - x - (i > 0 ? off / d : 0.0);
+        if (d == 0.0) d = -1e-300;  // x on an eigenvalue of a leading block: count it
+        cnt += d < 0.0;
+    }
+    return cnt;
+}
+
+// Ritz extremes into out[0] (smallest), out[1] (largest); the Krylov space
+// ends at the first beta_j below 1e-6 of the spectral scale so far.  check:
+// latch kErrPnBound when they leave [lo, hi].
+__global__ void lz_final(const double* __restrict__ ab, double lo, double hi, int check, Ctrl* __restrict__ ctrl,
+                         double* __restrict__ out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double* al = ab;
+    const double* be = ab + kPnLanczosSteps;  // be[i] couples rows i - 1 and i (i >= 1)
+    int j = 1;
+    double scale = fabs(al[0]);
+    while (j < kPnLanczosSteps && be[j] > 1e-6 * scale) {
+        scale = fmax(scale, fabs(al[j]) + be[j]);
+        ++j;
+    }
+    double glo = al[0], ghi = al[0];  // Gershgorin interval of the tridiagonal matrix
+    for (int i = 0; i < j; ++i) {
+        const double rad = (i > 0 ? fabs(be[i]) : 0.0) + (i + 1 < j ? fabs(be[i + 1]) : 0.0);
+        glo = fmin(glo, al[i] - rad);
+        ghi = fmax(ghi, al[i] + rad);
+    }
+    double a = glo, b = ghi;  // smallest: count(x) >= 1 first at it
+    for (int it = 0; it < 200 && b - a > 1e-15 * fmax(fabs(a), fabs(b)); ++it) {
+        const double m = 0.5 * (a + b);
+        if (sturm_count(al, be, j, m) >= 1) b = m; else a = m;
+    }
+    const double tmin = 0.5 * (a + b);
+    a = glo;
+    b = ghi;  // largest: count(x) >= j first at it
+    for (int it = 0; it < 200 && b - a > 1e-15 * fmax(fabs(a), fabs(b)); ++it) {
+        const double m = 0.5 * (a + b);
+        if (sturm_count(al, be, j, m) >= j) b = m; else a = m;
+    }
+    const double tmax = 0.5 * (a + b);
+    out[0] = tmin;
+    out[1] = tmax;
+    out[2] = (double)j;
+    if (check && (tmin < lo || tmax > hi)) atomicOr(&ctrl->err, kErrPnBound);
 }
 
 }  // namespace
@@ -1180,6 +1357,28 @@ cudaError_t launch_pair_noise(const StepParams& P, const ParticleBuffers& B, con
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+int pn_spectrum_blocks(const StepParams& P) { return (int)((P.n_pad + kThreads - 1) / kThreads); }
+
+cudaError_t launch_pn_spectrum(const StepParams& P, const ParticleBuffers& B, float* vec, double* part, double* ab,
+                               double lo, double hi, int check, double* out, cudaStream_t st)
+{
+    const int nblk = pn_spectrum_blocks(P);
+    const size_t vs = (size_t)3 * P.n_pad;
+    float* y = vec + 3 * vs;  // r_k rotate through vec[0..2]
+    double* pa = part;         // |r_k|^2 partials
+    double* pb = part + nblk;  // v_k . y partials
+    lz_start<<<nblk, kThreads, 0, st>>>(P, vec, pa);
+    for (int k = 0; k < kPnLanczosSteps; ++k) {
+        float* rk = vec + (size_t)(k % 3) * vs;
+        const float* rkm1 = vec + (size_t)((k + 2) % 3) * vs;
+        float* rkp1 = vec + (size_t)((k + 1) % 3) * vs;
+        lz_matvec<<<nblk, kThreads, 0, st>>>(P, B.pos, B.nbr, B.nbr_cnt, B.ftab, B.fptab, rk, pa, nblk, y, pb, ab, k);
+        lz_update<<<nblk, kThreads, 0, st>>>(P, y, rk, rkm1, pb, nblk, ab, k, rkp1, pa);
+    }
+    lz_final<<<1, 32, 0, st>>>(ab, lo, hi, check, B.ctrl, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pn_rowsum(const StepParams& P, const ParticleBuffers& B, unsigned* out, cudaStream_t st)

@@ -79,6 +79,14 @@ cudaError_t launch_pcorr_flush(const StepParams& P, const ParticleBuffers& B, cu
 // Z_0 row of step n in frblock.
 cudaError_t launch_pair_noise(const StepParams& P, const ParticleBuffers& B, const float* zblk, float* bvec,
                               cudaStream_t st);
+// Extreme eigenvalues of the pair matrix M (as the Clenshaw sweeps apply it)
+// by kPnLanczosSteps Lanczos steps: vec holds four vectors [3][n_pad], part
+// 2 x ceil(n_pad / 256) doubles, ab 2 kPnLanczosSteps + 1 doubles; out[0],
+// out[1] the smallest and largest Ritz values, out[2] the Krylov dimension
+// used.  check: latch kErrPnBound when they leave [lo, hi].
+cudaError_t launch_pn_spectrum(const StepParams& P, const ParticleBuffers& B, float* vec, double* part, double* ab,
+                               double lo, double hi, int check, double* out, cudaStream_t st);
+int pn_spectrum_blocks(const StepParams& P);
 // Pair-correlated noise by Algorithm 1 (k_pn_krylov.cu): vectors [3 n_pad][Mp]
 // (frequency fastest).  kry_ft: the transformed white-noise window of step
 // ctrl->step into V0; kry_dot: per-frequency dot products a.b into out
