@@ -535,10 +535,12 @@ def main():
                  "vacf_origins_after": int(orig1), "vacf_origins_in_flight": (vacf["vacf_len"] + vacf["vacf_stride"] - 1)
                  // vacf["vacf_stride"]})
     T_blocks = (K + T - 1) // T
+    # per step: convolution, pair kernel, F^C with the VACF terms, and the
+    # rebuild decision (conditional form) or the four gated rebuild kernels
     if d0["graph_mode"] == 2:  # rebuild kernels only on the steps that rebuild
-        launches = K * 5 + 4 * (d1["rebuilds"] - d0["rebuilds"]) + 2 * T_blocks
+        launches = K * 4 + 4 * (d1["rebuilds"] - d0["rebuilds"]) + 2 * T_blocks
     else:
-        launches = K * 8 + 2 * T_blocks
+        launches = K * 7 + 2 * T_blocks
     if args.pcorr > 0:
         launches += K
     if args.pair_noise > 0:  # Clenshaw sweeps per step; filters and the Lanczos check per block

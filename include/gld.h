@@ -226,8 +226,9 @@ enum {
     GLD_PROF_HIST = 1,   /* history convolution                               */
     GLD_PROF_PAIR = 2,   /* F^D, position update, history write               */
     GLD_PROF_CELL = 3,   /* cell + neighbour-list rebuild (4 kernels, gated)  */
-    GLD_PROF_CFORCE = 4, /* F^C_{n+1} and velocity update                     */
-    GLD_PROF_VACF = 5,   /* velocity autocorrelation                          */
+    GLD_PROF_CFORCE = 4, /* F^C_{n+1}, velocity update and the VACF terms     */
+    GLD_PROF_VACF = 5,   /* velocity autocorrelation in batches only (single  */
+                         /* contexts accumulate it inside the F^C kernel: 0)  */
     GLD_PROF_PCORR = 6,  /* distance-binned pair correlations (when enabled)  */
     GLD_PROF_PNOISE = 7, /* Clenshaw sweeps of the pair-correlated noise      */
     GLD_PROF_N = 8

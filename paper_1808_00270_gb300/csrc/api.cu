@@ -3,7 +3,7 @@
 //
 // One step n -> n+1 is five kernels on the context's stream:
 //   hist_conv -> pair_force_integrate -> cell build (3 small kernels)
-//   -> cforce (F^C_{n+1}, V_{n+1}, n += 1) -> vacf (when enabled)
+//   -> cforce (F^C_{n+1}, V_{n+1}, n += 1, and the VACF terms when enabled)
 // and every T steps one noise block (wgen + fir) produces F^R for the next T
 // steps.  The step counter lives on the device, so a graph holding one noise
 // block and T steps is captured once and replayed for as long as the kernels
@@ -230,8 +230,7 @@ cudaError_t launch_one_step(gld_ctx* c, cudaStream_t s)
     if ((e = launch_pair_noise(c->P, c->B, c->d_zblk, c->d_bvec, s)) != cudaSuccess) return e;
     if ((e = launch_pair_force_integrate(c->P, c->B, s)) != cudaSuccess) return e;
     if ((e = launch_rebuild(c->P, c->B, s)) != cudaSuccess) return e;
-    if ((e = launch_cforce(c->P, c->B, 1, s)) != cudaSuccess) return e;
-    if ((e = launch_vacf(c->P, c->B, s)) != cudaSuccess) return e;
+    if ((e = launch_cforce(c->P, c->B, 1, s)) != cudaSuccess) return e;  // with the VACF terms
     return launch_pcorr(c->P, c->B, s);
 }
 
@@ -262,7 +261,6 @@ cudaError_t capture_step_gated(gld_ctx* c, cudaStream_t s, bool overlap)
     if (e == cudaSuccess) e = capture_fork_next(c, s);
     if (e == cudaSuccess) e = launch_rebuild(c->P, c->B, s);
     if (e == cudaSuccess) e = launch_cforce(c->P, c->B, 1, s);
-    if (e == cudaSuccess) e = launch_vacf(c->P, c->B, s);
     if (e == cudaSuccess) e = launch_pcorr(c->P, c->B, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join, 0);
     return e;
@@ -303,7 +301,6 @@ cudaError_t capture_step_conditional(gld_ctx* c, cudaStream_t s, bool overlap)
         e = eb != cudaSuccess ? eb : ee;
     }
     if (e == cudaSuccess) e = launch_cforce(c->P, c->B, 1, s);
-    if (e == cudaSuccess) e = launch_vacf(c->P, c->B, s);
     if (e == cudaSuccess) e = launch_pcorr(c->P, c->B, s);
     if (overlap && e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join, 0);
     return e;
@@ -570,8 +567,9 @@ bool capture_graph(gld_ctx* c)
 
 int clamp_block(int) { return kMaxNoiseBlock; }  // the filter produces 64-step blocks
 
-// Particle blocks of the VACF grid (each of its rows of origin groups).
-int vacf_blocks(int n, int) { return std::max(1, std::min((n + 255) / 256, kVacfMaxBlocks)); }
+// Blocks of VACF partials per origin: one per 256 particles, the F^C
+// kernel's grid (which accumulates them) and the batch VACF grid's width.
+int vacf_blocks(int n, int) { return std::max(1, (n + 255) / 256); }
 
 }  // namespace
 
@@ -1240,10 +1238,9 @@ gld_status gld_profile_steps(gld_ctx* c, int64_t nsteps, double* ms, int64_t* la
     // Per noise block: a short delay kernel lets the host enqueue the whole
     // block ahead of the device, then every kernel family is bracketed by an
     // event pair, so the device times contain no host launch gaps.
-    const bool vac = c->P.vacf_len > 0;
-    const bool pcor = vac && c->P.pc_nbins > 0;
+    const bool pcor = c->P.vacf_len > 0 && c->P.pc_nbins > 0;
     const bool pnoise = c->P.pn_deg > 0;
-    const size_t nk = 1 + (size_t)T * (4 + (vac ? 1 : 0) + (pcor ? 1 : 0) + (pnoise ? 1 : 0));
+    const size_t nk = 1 + (size_t)T * (4 + (pcor ? 1 : 0) + (pnoise ? 1 : 0));
     std::vector<cudaEvent_t> ev(2 * nk, nullptr);
     std::vector<int> fam(nk);
     gld_status s = GLD_OK;
@@ -1276,8 +1273,7 @@ gld_status gld_profile_steps(gld_ctx* c, int64_t nsteps, double* ms, int64_t* la
             if (pnoise) timed(GLD_PROF_PNOISE, [&] { return launch_pair_noise(c->P, c->B, c->d_zblk, c->d_bvec, c->st); });
             timed(GLD_PROF_PAIR, [&] { return launch_pair_force_integrate(c->P, c->B, c->st); });
             timed(GLD_PROF_CELL, [&] { return launch_rebuild(c->P, c->B, c->st); });
-            timed(GLD_PROF_CFORCE, [&] { return launch_cforce(c->P, c->B, 1, c->st); });
-            if (vac) timed(GLD_PROF_VACF, [&] { return launch_vacf(c->P, c->B, c->st); });
+            timed(GLD_PROF_CFORCE, [&] { return launch_cforce(c->P, c->B, 1, c->st); });  // with the VACF terms
             if (pcor) timed(GLD_PROF_PCORR, [&] { return launch_pcorr(c->P, c->B, c->st); });
             c->last_fr_row = t;
             ++c->host_step;

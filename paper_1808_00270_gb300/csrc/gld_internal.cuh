@@ -17,7 +17,6 @@ constexpr int kMaxQ = 4;            // separable terms per pair-kernel family
 constexpr int kMaxAcc = 1 + 2 * kMaxQ;
 constexpr int kMaxModes = 8;         // damped-exponential modes of the recursive memory form
 constexpr int kPcMaxOriginBins = 2048;  // origins x bins of the pair correlations (48 KB of shared sums)
-constexpr int kVacfMaxBlocks = 256;  // particle blocks of the VACF grid at most
 constexpr int kMaxNoiseBlock = 64;  // register-resident outputs per FIR thread
 constexpr int kMaxPnDegree = 16;    // Chebyshev degree of the pair-correlated noise
 constexpr int kPnLanczosSteps = 32;  // Lanczos steps for the pair matrix's extreme eigenvalues

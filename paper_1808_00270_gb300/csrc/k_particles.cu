@@ -465,15 +465,137 @@ __global__ void __launch_bounds__(kThreads) nbr_build(const StepParams P, Ctrl* 
     nbr_build_body(P, ctrl, pos_sorted, cell_start, nbr, nbr_cnt, perm, disp, disp_build, blockIdx.x, gridDim.x);
 }
 
+// ---- velocity autocorrelation ------------------------------------------------
+constexpr int kVacfMaxOrigins = 32;  // origins in flight (vacf_len / vacf_stride)
+constexpr int kVacfGroup = 4;        // origins per block row of the VACF grid
+
+__device__ __forceinline__ float warp_sum_f(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Knuth's two-sum: s + e equals a + b exactly (no contraction: additions only).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// (hi, lo) += (bhi, blo) in double-float arithmetic on the FP32 pipes.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float bhi, float blo)
+{
+    float s, e;
+    two_sum(hi, bhi, s, e);
+    e += lo + blo;
+    hi = s + e;
+    lo = e - (hi - s);
+}
+
+// Adds the block partials of origins q = first, first + step, ... (buffer
+// buf, nblk partials each) to C(lag0 + q*stride): double-float sums on the
+// FP32 pipes in a fixed order, one FP64 addition per origin.
+__device__ __forceinline__ void vacf_fold(const StepParams& P, const float* __restrict__ partial, double* __restrict__ csum,
+                                          long long* __restrict__ ccnt, int buf, int nact, int lag0, int nblk, int first,
+                                          int step)
+{
+    __shared__ float sh[kThreads / 32][2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float* base = partial + (size_t)buf * P.n_os * nblk;
+    for (int q = first; q < nact; q += step) {
+        float hi = 0.f, lo = 0.f;
+        for (int b = threadIdx.x; b < nblk; b += blockDim.x)
+            df_add(hi, lo, __ldcg(base + (size_t)q * nblk + b), 0.f);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, hi, o), l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+            df_add(hi, lo, h2, l2);
+        }
+        if (lane == 0) {
+            sh[warp][0] = hi;
+            sh[warp][1] = lo;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float h = 0.f, l = 0.f;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) df_add(h, l, sh[w][0], sh[w][1]);
+            const int lg = lag0 + q * P.vacf_stride;  // < vacf_len for q < nact
+            csum[lg] += (double)h + (double)l;
+            ccnt[lg] += 1;
+        }
+        __syncthreads();
+    }
+}
+
+// The VACF terms of V_{n+1}, fused into the F^C kernel that computes it:
+// blocks b < (origins of the previous step) first fold that step's partials
+// (one origin each), then every block writes its partial sums of
+// V_{n+1} . V(t0) for each active origin (particle i is thread i of the
+// grid; FP32 warp and block sums in a fixed order) and stores the new origin.
+// All threads of the block take part (valid: thread i holds particle i).
+__device__ __forceinline__ void cforce_vacf(const StepParams& P, Ctrl* __restrict__ ctrl, const float4 v, bool valid,
+                                            int i, float4* __restrict__ vorig, float* __restrict__ partial,
+                                            double* __restrict__ csum, long long* __restrict__ ccnt,
+                                            long long* __restrict__ norig, int blk, int nblk)
+{
+    if (ctrl->pv_nact > 0)  // uniform over the block
+        vacf_fold(P, partial, csum, ccnt, ctrl->pv_buf, ctrl->pv_nact, ctrl->pv_lag0, nblk, blk, nblk);
+    if (!ctrl->vacf_on) return;  // uniform over the grid
+    const int n_act = ctrl->vacf_nact;
+    const bool is_origin = ctrl->vacf_origin != 0;
+    const int slot0 = ctrl->vacf_slot0;  // slot of age j: (slot0 - j) mod n_os
+    if (blk == 0 && threadIdx.x == 0) {
+        ctrl->vacf_pending = 1;
+        if (is_origin) *norig += 1;
+    }
+    __shared__ float wsum[kThreads / 32][kVacfGroup];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float* out = partial + (size_t)ctrl->vacf_buf * P.n_os * nblk;
+    for (int q0 = 0; q0 < n_act; q0 += kVacfGroup) {
+        float4 w[kVacfGroup];
+#pragma unroll
+        for (int q = 0; q < kVacfGroup; ++q) {
+            const int j = q0 + q;
+            const int sl = slot0 - j < 0 ? slot0 - j + P.n_os : slot0 - j;
+            // the origin of age 0 on an origin step is V_{n+1} itself
+            const bool use = valid && j < n_act && !(j == 0 && is_origin);
+            w[q] = use ? __ldcs(vorig + (size_t)sl * P.n + i) : v;
+        }
+#pragma unroll
+        for (int q = 0; q < kVacfGroup; ++q) {
+            const float d = (valid && q0 + q < n_act) ? fmaf(v.x, w[q].x, fmaf(v.y, w[q].y, v.z * w[q].z)) : 0.f;
+            const float sq = warp_sum_f(d);
+            if (lane == 0) wsum[warp][q] = sq;
+        }
+        __syncthreads();
+        if (threadIdx.x < kVacfGroup && q0 + (int)threadIdx.x < n_act) {
+            float sb = 0.f;
+            for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) sb += wsum[w2][threadIdx.x];
+            out[(size_t)(q0 + threadIdx.x) * nblk + blk] = sb;
+        }
+        __syncthreads();
+    }
+    if (is_origin && valid) vorig[(size_t)slot0 * P.n + i] = v;
+}
+
 // ---- conservative force and velocity finish --------------------------------
 // R_{n+1} is read from pos_next (every thread reads neighbours there) and
 // copied into pos for the next step.
-template <bool STEP>
+// VACF (with STEP): the VACF terms of V_{n+1} too (cforce_vacf; one lane per
+// particle, blocks of kThreads particles, nblk = the VACF partial count).
+template <bool STEP, bool VACF = false>
 __device__ __forceinline__ void cforce_body(const StepParams& P, Ctrl* __restrict__ ctrl, const float4* __restrict__ pos_next,
            float4* __restrict__ pos, const int* __restrict__ perm, const int* __restrict__ nbr,
            const int* __restrict__ nbr_cnt, const float4* __restrict__ vhalf, float4* __restrict__ vel,
-           float4* __restrict__ fc, const float* __restrict__ fctab, int blk, int nblk)
+           float4* __restrict__ fc, const float* __restrict__ fctab, int blk, int nblk,
+           float4* __restrict__ vorig = nullptr, float* __restrict__ vpartial = nullptr,
+           double* __restrict__ csum = nullptr, long long* __restrict__ ccnt = nullptr,
+           long long* __restrict__ norig = nullptr)
 {
+    static_assert(!VACF || kCforceLanes == 1, "the fused VACF takes one particle per thread");
+    float4 vnew = make_float4(0.f, 0.f, 0.f, 0.f);
     // kCforceLanes consecutive lanes share a particle and split its list
     const int k = (blk * blockDim.x + threadIdx.x) / kCforceLanes;
     const int lr = threadIdx.x & (kCforceLanes - 1);
@@ -523,10 +645,13 @@ __device__ __forceinline__ void cforce_body(const StepParams& P, Ctrl* __restric
             fc[id] = make_float4(fx, fy, fz, 0.f);
             if (STEP) {
                 const float4 vh = vhalf[id];
-                vel[id] = make_float4(fmaf(P.vf_fc, fx, vh.x), fmaf(P.vf_fc, fy, vh.y), fmaf(P.vf_fc, fz, vh.z), 0.f);
+                vnew = make_float4(fmaf(P.vf_fc, fx, vh.x), fmaf(P.vf_fc, fy, vh.y), fmaf(P.vf_fc, fz, vh.z), 0.f);
+                vel[id] = vnew;
             }
         }
     }
+    if (STEP && VACF)
+        cforce_vacf(P, ctrl, vnew, k < P.n, k, vorig, vpartial, csum, ccnt, norig, blk, nblk);
     if (STEP) {
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -541,77 +666,16 @@ __device__ __forceinline__ void cforce_body(const StepParams& P, Ctrl* __restric
     }
 }
 
-template <bool STEP>
+template <bool STEP, bool VACF>
 __global__ void __launch_bounds__(kThreads) cforce(const StepParams P, Ctrl* __restrict__ ctrl, const float4* __restrict__ pos_next,
            float4* __restrict__ pos, const int* __restrict__ perm, const int* __restrict__ nbr,
            const int* __restrict__ nbr_cnt, const float4* __restrict__ vhalf, float4* __restrict__ vel,
-           float4* __restrict__ fc, const float* __restrict__ fctab)
+           float4* __restrict__ fc, const float* __restrict__ fctab, float4* __restrict__ vorig,
+           float* __restrict__ vpartial, double* __restrict__ csum, long long* __restrict__ ccnt,
+           long long* __restrict__ norig)
 {
-    cforce_body<STEP>(P, ctrl, pos_next, pos, perm, nbr, nbr_cnt, vhalf, vel, fc, fctab, blockIdx.x, gridDim.x);
-}
-
-// ---- velocity autocorrelation ------------------------------------------------
-constexpr int kVacfMaxOrigins = 32;  // origins in flight (vacf_len / vacf_stride)
-constexpr int kVacfGroup = 4;        // origins per block row of the VACF grid
-static_assert(kVacfMaxBlocks % 32 == 0 && kVacfMaxBlocks <= kThreads, "VACF partials are folded one per thread");
-
-__device__ __forceinline__ float warp_sum_f(float v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Knuth's two-sum: s + e equals a + b exactly (no contraction: additions only).
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
-{
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
-
-// (hi, lo) += (bhi, blo) in double-float arithmetic on the FP32 pipes.
-__device__ __forceinline__ void df_add(float& hi, float& lo, float bhi, float blo)
-{
-    float s, e;
-    two_sum(hi, bhi, s, e);
-    e += lo + blo;
-    hi = s + e;
-    lo = e - (hi - s);
-}
-
-// Adds the block partials of origins q = first, first + step, ... (buffer
-// buf, nblk partials each) to C(lag0 + q*stride): double-float sums on the
-// FP32 pipes in a fixed order, one FP64 addition per origin.
-__device__ __forceinline__ void vacf_fold(const StepParams& P, const float* __restrict__ partial, double* __restrict__ csum,
-                                          long long* __restrict__ ccnt, int buf, int nact, int lag0, int nblk, int first,
-                                          int step)
-{
-    __shared__ float sh[kThreads / 32][2];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const float* base = partial + (size_t)buf * P.n_os * nblk;
-    for (int q = first; q < nact; q += step) {
-        float hi = 0.f, lo = 0.f;
-        if ((int)threadIdx.x < nblk) hi = __ldcg(base + (size_t)q * nblk + threadIdx.x);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float h2 = __shfl_xor_sync(0xffffffffu, hi, o), l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-            df_add(hi, lo, h2, l2);
-        }
-        if (lane == 0) {
-            sh[warp][0] = hi;
-            sh[warp][1] = lo;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            float h = 0.f, l = 0.f;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) df_add(h, l, sh[w][0], sh[w][1]);
-            const int lg = lag0 + q * P.vacf_stride;  // < vacf_len for q < nact
-            csum[lg] += (double)h + (double)l;
-            ccnt[lg] += 1;
-        }
-        __syncthreads();
-    }
+    cforce_body<STEP, VACF>(P, ctrl, pos_next, pos, perm, nbr, nbr_cnt, vhalf, vel, fc, fctab, blockIdx.x, gridDim.x,
+                            vorig, vpartial, csum, ccnt, norig);
 }
 
 // Block (x, y) of the grid (gx <= 256 = blockDim) takes the particles
@@ -1287,12 +1351,11 @@ cudaError_t launch_rebuild(const StepParams& P, const ParticleBuffers& B, cudaSt
 cudaError_t launch_cforce(const StepParams& P, const ParticleBuffers& B, int mode, cudaStream_t st)
 {
     const unsigned grid = (unsigned)(((long long)P.n * kCforceLanes + kThreads - 1) / kThreads);
-    if (mode)
-        cforce<true><<<grid, kThreads, 0, st>>>(P, B.ctrl, B.pos_next, B.pos, B.perm, B.nbr, B.nbr_cnt, B.vhalf,
-                                                B.vel, B.fc, B.fctab);
-    else
-        cforce<false><<<grid, kThreads, 0, st>>>(P, B.ctrl, B.pos_next, B.pos, B.perm, B.nbr, B.nbr_cnt, B.vhalf,
-                                                 B.vel, B.fc, B.fctab);
+    const bool vac = mode && P.vacf_len > 0;
+    if (vac && (P.n_os > kVacfMaxOrigins || (int)grid != B.vacf_gx)) return cudaErrorInvalidValue;
+    auto k = mode ? (vac ? cforce<true, true> : cforce<true, false>) : cforce<false, false>;
+    k<<<grid, kThreads, 0, st>>>(P, B.ctrl, B.pos_next, B.pos, B.perm, B.nbr, B.nbr_cnt, B.vhalf, B.vel, B.fc,
+                                 B.fctab, B.vorig, B.vpartial, B.csum, B.ccnt, B.norig);
     return cudaGetLastError();
 }
 
