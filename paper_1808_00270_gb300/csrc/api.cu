@@ -328,11 +328,11 @@ void pn_release(gld_ctx* c)
 void kry_release(gld_ctx* c)
 {
     auto& K = c->kry;
-    for (float** p : {&K.V, &K.Y, &K.cf}) {
+    for (float** p : {&K.V, &K.Y, &K.cf, &K.cosT}) {
         dfree(c, *p);
         *p = nullptr;
     }
-    for (double** p : {&K.part, &K.alpha, &K.beta, &K.xnorm, &K.wc}) {
+    for (double** p : {&K.part, &K.alpha, &K.beta, &K.wc}) {
         dfree(c, *p);
         *p = nullptr;
     }
@@ -413,43 +413,39 @@ void tri_sqrt_e1(int j, const double* alpha, const double* beta, double xnorm, s
 }
 
 // F^R of the current step by Algorithm 1, into its row of the F^R block
-// (eager: host decisions between chunks of iterations).
+// (eager: host decisions between chunks of iterations).  R_0 is the
+// transformed window, beta_0 = |R_0|; iteration k gives alpha_k and
+// beta_{k+1} = |R_{k+1}|, and the tridiagonal matrix of dimension j has
+// alpha_0 .. alpha_{j-1} on its diagonal and beta_1 .. beta_{j-1} beside it.
 gld_status pair_noise_krylov(gld_ctx* c, cudaStream_t st)
 {
     const StepParams& P = c->P;
     auto& K = c->kry;
     const int M = K.M, Mp = K.Mp;
     const size_t vs = 3 * (size_t)P.n_pad * Mp;
-    auto V = [&](int p) { return K.V + (size_t)p * vs; };
+    auto R = [&](int p) { return K.V + (size_t)p * vs; };
+    auto A = [&](int p) { return K.alpha + (size_t)p * Mp; };
+    auto Bt = [&](int p) { return K.beta + (size_t)p * Mp; };
     GLD_CUDA(c, cudaMemsetAsync(K.alive, 1, sizeof(int) * Mp, st));  // nonzero: alive
-    GLD_CUDA(c, kry_ft(P, c->B.ctrl, c->W, M, Mp, V(0), st));
-    GLD_CUDA(c, kry_dot(P, V(0), V(0), Mp, K.part, K.xnorm, 2, nullptr, K.alive, st));
-    GLD_CUDA(c, kry_scale(P, V(0), V(0), Mp, K.xnorm, K.alive, st));
-    GLD_CUDA(c, kry_matvec(P, c->B, K.wc, Mp, V(0), K.Y, st));
-    GLD_CUDA(c, kry_dot(P, V(0), K.Y, Mp, K.part, K.alpha, 0, nullptr, K.alive, st));
-    int k = 1;  // Lanczos vectors so far
+    GLD_CUDA(c, kry_ft(P, c->B.ctrl, c->W, K.cosT, M, Mp, R(0), st));
+    GLD_CUDA(c, kry_dot(P, R(0), R(0), Mp, K.part, Bt(0), 2, nullptr, K.alive, st));
+    int k = 0;  // iterations done
     const int chunk = 4;
-    std::vector<double> ha, hb, hx(Mp);
-    std::vector<std::vector<double>> cprev(M), cfin(M);
+    std::vector<double> ha, hb;
+    std::vector<std::vector<double>> cfin(M);
     std::vector<int> done(M, 0), kw(M, 0);
     int ndone = 0;
     double worst_change = 0.0, worst_neg = 0.0;
     while (true) {
         for (int it = 0; it < chunk && k < K.kmax; ++it, ++k) {
-            GLD_CUDA(c, kry_resid(P, K.Y, V(k - 1), k >= 2 ? V(k - 2) : nullptr, K.alpha + (size_t)(k - 1) * Mp,
-                                  K.beta + (size_t)(k >= 2 ? k - 2 : 0) * Mp, Mp, V(k), st));
-            GLD_CUDA(c, kry_dot(P, V(k), V(k), Mp, K.part, K.beta + (size_t)(k - 1) * Mp, 1, K.alpha, K.alive, st));
-            GLD_CUDA(c, kry_scale(P, V(k), V(k), Mp, K.beta + (size_t)(k - 1) * Mp, K.alive, st));
-            GLD_CUDA(c, kry_matvec(P, c->B, K.wc, Mp, V(k), K.Y, st));
-            GLD_CUDA(c, kry_dot(P, V(k), K.Y, Mp, K.part, K.alpha + (size_t)k * Mp, 0, nullptr, K.alive, st));
+            GLD_CUDA(c, kry_matvec(P, c->B, K.wc, Bt(k), K.alive, Mp, R(k), K.Y, K.part, A(k), st));
+            GLD_CUDA(c, kry_resid(P, K.Y, R(k), k > 0 ? R(k - 1) : nullptr, A(k), Bt(k), k > 0 ? Bt(k - 1) : nullptr,
+                                  K.alive, A(0), Mp, R(k + 1), K.part, Bt(k + 1), st));
         }
         ha.resize((size_t)k * Mp);
-        hb.resize((size_t)std::max(k - 1, 1) * Mp);
+        hb.resize((size_t)(k + 1) * Mp);
         GLD_CUDA(c, cudaMemcpyAsync(ha.data(), K.alpha, sizeof(double) * ha.size(), cudaMemcpyDeviceToHost, st));
-        if (k > 1)
-            GLD_CUDA(c, cudaMemcpyAsync(hb.data(), K.beta, sizeof(double) * (size_t)(k - 1) * Mp, cudaMemcpyDeviceToHost,
-                                        st));
-        GLD_CUDA(c, cudaMemcpyAsync(hx.data(), K.xnorm, sizeof(double) * Mp, cudaMemcpyDeviceToHost, st));
+        GLD_CUDA(c, cudaMemcpyAsync(hb.data(), K.beta, sizeof(double) * hb.size(), cudaMemcpyDeviceToHost, st));
         GLD_TRY(sync_and_check(c));
         for (int w = 0; w < M; ++w) {
             if (done[w]) continue;
@@ -459,22 +455,24 @@ gld_status pair_noise_krylov(gld_ctx* c, cudaStream_t st)
             for (int p = 0; p < k; ++p) al[p] = ha[(size_t)p * Mp + w];
             bool exhausted = false;
             for (int p = 0; p + 1 < k; ++p) {
-                be[p] = hb[(size_t)p * Mp + w];
+                be[p] = hb[(size_t)(p + 1) * Mp + w];
                 if (!(be[p] > 0.0)) {
                     exhausted = true;
                     break;
                 }
                 ++j;
             }
+            if (!exhausted && j == k && !(hb[(size_t)k * Mp + w] > 0.0)) exhausted = true;
+            const double xnorm = hb[w];
             std::vector<double> cj;
             double neg = 0.0;
-            tri_sqrt_e1(j, al.data(), be.data(), hx[w], cj, &neg);
+            tri_sqrt_e1(j, al.data(), be.data(), xnorm, cj, &neg);
             worst_neg = std::min(worst_neg, neg);
             double change = 0.0, nrm = 0.0;
-            if (j >= 2 || exhausted) {
+            if (j >= 2) {
                 std::vector<double> cm;
                 double neg2 = 0.0;
-                if (j >= 2) tri_sqrt_e1(j - 1, al.data(), be.data(), hx[w], cm, &neg2);
+                tri_sqrt_e1(j - 1, al.data(), be.data(), xnorm, cm, &neg2);
                 cm.resize(j, 0.0);
                 for (int p = 0; p < j; ++p) {
                     change += (cj[p] - cm[p]) * (cj[p] - cm[p]);
@@ -482,7 +480,7 @@ gld_status pair_noise_krylov(gld_ctx* c, cudaStream_t st)
                 }
                 change = nrm > 0 ? std::sqrt(change / nrm) : 0.0;
             } else {
-                change = 1.0;
+                change = exhausted ? 0.0 : 1.0;
             }
             if (exhausted || change <= K.tol) {
                 done[w] = 1;
@@ -507,9 +505,13 @@ gld_status pair_noise_krylov(gld_ctx* c, cudaStream_t st)
     }
     if (ndone < M)
         return fail(c, GLD_E_TIMEOUT, "pair noise (Lanczos): no convergence within the iteration limit");
+    // x_w = sum_p c_p v_p = sum_p (c_p / beta_p) R_p
     std::vector<float> cf((size_t)M * k, 0.f);
     for (int w = 0; w < M; ++w)
-        for (int p = 0; p < kw[w]; ++p) cf[(size_t)w * k + p] = (float)cfin[w][p];
+        for (int p = 0; p < kw[w]; ++p) {
+            const double bp = hb[(size_t)p * Mp + w];
+            cf[(size_t)w * k + p] = bp > 0.0 ? (float)(cfin[w][p] / bp) : 0.f;
+        }
     GLD_CUDA(c, cudaMemcpyAsync(K.cf, cf.data(), sizeof(float) * cf.size(), cudaMemcpyHostToDevice, st));
     const long long row = c->host_step - c->block_start;
     GLD_CUDA(c, kry_combine(P, K.V, K.cf, k, M, Mp, c->B.frblock + (size_t)row * 3 * P.n_pad, st));
@@ -1754,6 +1756,8 @@ gld_status gld_set_pair_noise_krylov(gld_ctx* c, double tol, int32_t kmax)
     auto& K = c->kry;
     const int M = P.m_max, Mp = (M + 31) & ~31, nacc = P.nacc;
     const long long L = 2LL * M - 1;
+    if (!kry_fits(P, Mp))
+        return fail(c, GLD_E_INVAL, "gld_set_pair_noise_krylov: m_max too large for the transform's shared memory");
     // transforms (Eq. FT) of kT a_m / dt times each discrete time factor:
     // a_w (self), g_qw (pair terms), gs_qw (self-difference terms), FP64
     std::vector<double> wc((size_t)nacc * Mp, 0.0);
@@ -1766,15 +1770,21 @@ gld_status gld_set_pair_noise_krylov(gld_ctx* c, double tol, int32_t kmax)
             wc[(size_t)a * Mp + w] = f0 * v;
         }
     }
+    // cos(2 pi w s / L) for s = 0 .. m_max - 1 (the transform of the window),
+    // columns w >= m_max zero
+    std::vector<float> cosT((size_t)M * Mp, 0.f);
+    for (int sg = 0; sg < M; ++sg)
+        for (int w = 0; w < M; ++w)
+            cosT[(size_t)sg * Mp + w] = (float)std::cos(2.0 * M_PI * (double)(((long long)w * sg) % L) / (double)L);
     const size_t vs = 3 * (size_t)P.n_pad * Mp;
     bool ok = true;
     K.V = alloc_n<float>(c, (size_t)(kmax + 1) * vs, ok);
     K.Y = alloc_n<float>(c, vs, ok);
     K.cf = alloc_n<float>(c, (size_t)M * (kmax + 1), ok);
-    K.part = alloc_n<double>(c, (size_t)kry_dot_blocks(P) * Mp, ok);
+    K.cosT = alloc_n<float>(c, cosT.size(), ok);
+    K.part = alloc_n<double>(c, (size_t)kry_part_blocks(P) * Mp, ok);
     K.alpha = alloc_n<double>(c, (size_t)(kmax + 1) * Mp, ok);
     K.beta = alloc_n<double>(c, (size_t)(kmax + 1) * Mp, ok);
-    K.xnorm = alloc_n<double>(c, Mp, ok);
     K.wc = alloc_n<double>(c, wc.size(), ok);
     K.alive = alloc_n<int>(c, Mp, ok);
     if (!ok) {
@@ -1782,6 +1792,7 @@ gld_status gld_set_pair_noise_krylov(gld_ctx* c, double tol, int32_t kmax)
         return fail(c, GLD_E_NOMEM, "gld_set_pair_noise_krylov: allocation failed");
     }
     GLD_CUDA(c, cudaMemcpyAsync(K.wc, wc.data(), sizeof(double) * wc.size(), cudaMemcpyHostToDevice, c->st));
+    GLD_CUDA(c, cudaMemcpyAsync(K.cosT, cosT.data(), sizeof(float) * cosT.size(), cudaMemcpyHostToDevice, c->st));
     K.M = M;
     K.Mp = Mp;
     K.kmax = kmax;

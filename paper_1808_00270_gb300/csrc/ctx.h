@@ -79,8 +79,8 @@ struct gld_ctx {
     struct Krylov {
         int M = 0, Mp = 0, kmax = 0;
         double tol = 0.0;
-        float *V = nullptr, *Y = nullptr, *cf = nullptr;
-        double *part = nullptr, *alpha = nullptr, *beta = nullptr, *xnorm = nullptr, *wc = nullptr;
+        float *V = nullptr, *Y = nullptr, *cf = nullptr, *cosT = nullptr;
+        double *part = nullptr, *alpha = nullptr, *beta = nullptr, *wc = nullptr;
         int* alive = nullptr;
         int last_iters = 0;
         double last_change = 0.0;

@@ -9,56 +9,85 @@
 // neighbours), D_q the self-difference matrices (diagonal blocks summed over
 // neighbours) and a_w, g_qw, gs_qw the transforms (Eq. FT) of kT a_m / dt
 // times the discrete time factors.  For every w = 0 .. m_max - 1 the
-// iteration builds the Krylov basis V of hat K_w from the transformed white
+// iteration builds the Krylov basis of hat K_w from the transformed white
 // noise hat W_w (its real part, hat K_w being real) and approximates
 // sqrt(hat K_w) hat W_w = |hat W_w| V sqrt(H) e_1 (H the tridiagonal Lanczos
 // matrix); F_n = (x_0 + 2 sum_{w >= 1} x_w) / (2 m_max - 1).
 //
 // All frequencies run together: vectors are stored [3 n_pad][Mp] with the
-// frequency the fast index (Mp = m_max rounded up to 32), so one warp handles
-// 32 frequencies of one vector entry and every neighbour sweep reads 128
-// contiguous bytes per entry; one sweep applies hat K_w for all w.  Products
-// are FP32, every dot product and norm is summed in FP64 in a fixed order
-// (block partials folded by one thread per frequency).  The square roots of
-// the small tridiagonal matrices and the stopping test (Algorithm 1's Delta)
-// run on the host.
+// frequency the fast index (Mp = m_max rounded up to 32), so a warp reads 128
+// contiguous bytes per vector entry and one neighbour sweep applies hat K_w
+// for every w.  The Lanczos vectors are kept unnormalised (R_k, with
+// v_k = R_k / beta_k and beta_k = |R_k|), so no pass only rescales; the
+// sweep also sums the partials of alpha_k = v_k . hat K v_k, the residual
+// kernel those of |R_{k+1}|^2.  Products are FP32; sums are FP32 over at most
+// 16 terms and FP64 beyond, folded in a fixed order, so a run is
+// deterministic.  The square roots of the small tridiagonal matrices and the
+// stopping test (Algorithm 1's Delta) run on the host.
 #include "launch.h"
 
 namespace gld {
 
 namespace {
 
-constexpr int kKryWarps = 8;  // vector entries (one per warp) per block; 32 frequencies per warp
+constexpr int kKryWarps = 8;    // warps per block of the elementwise kernels and the sweep
+constexpr int kFtThreads = 256; // entries per block of the transform
+constexpr int kMvGroups = 4;    // frequency groups (of 32) per neighbour pass of the sweep
+constexpr int kChunk = 16;      // FP32 terms summed before an FP64 addition
 
-// V0[I][w] = sum_{s=-H}^{H} W_{n+s}[I] cos(2 pi w s / L), I = c n_pad + i, L = 2H + 1.
-__global__ void __launch_bounds__(32 * kKryWarps)
-    pnk_ft(const StepParams P, const Ctrl* __restrict__ ctrl, const float* __restrict__ W, int M, int Mp,
-           float* __restrict__ V0)
+// V0[I][w] = W_n[I] + sum_{s=1}^{H} (W_{n+s}[I] + W_{n-s}[I]) cos(2 pi w s / L)
+// (cos is even in s), I = c n_pad + i, L = 2H + 1.  Block (g, y) takes the
+// frequencies 32g .. 32g + 31 of the entries 256y .. 256y + 255, one entry
+// per thread with 32 accumulators; the group's 32 columns of the cosine
+// table (cosT[s][w], s = 0..H) are staged in shared memory, where all lanes of
+// a warp read the same row (a broadcast).  The frequency groups of one entry
+// chunk are adjacent in the grid, so they share the W window through L2.
+__global__ void __launch_bounds__(kFtThreads)
+    pnk_ft(const StepParams P, const Ctrl* __restrict__ ctrl, const float* __restrict__ W,
+           const float* __restrict__ cosT, int M, int Mp, float* __restrict__ V0)
 {
-    extern __shared__ float cosL[];  // cos(2 pi t / L), t < L
-    const int H = P.H, L = 2 * H + 1;
-    for (int t = threadIdx.x; t < L; t += blockDim.x) cosL[t] = (float)cospi(2.0 * t / (double)L);
+    extern __shared__ float4 cs4[];  // [H + 1][8]
+    const int H = P.H, g = blockIdx.x;
+    for (int e = threadIdx.x; e < (H + 1) * 8; e += blockDim.x)
+        cs4[e] = reinterpret_cast<const float4*>(cosT + (size_t)(e >> 3) * Mp + g * 32)[e & 7];
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long np3 = 3LL * P.n_pad;
-    const long long I = (long long)blockIdx.x * kKryWarps + warp;
-    const int w = blockIdx.y * 32 + lane;
-    if (I >= np3) return;
-    const long long n = ctrl->step;
-    int t = (int)((((long long)w * -H) % L + L) % L);  // (w s) mod L at s = -H
-    const int dw = w % L;
-    float acc = 0.f;
-    for (int s = -H; s <= H; ++s) {
-        long long slot = (n + s) % P.lw;
-        if (slot < 0) slot += P.lw;
-        acc = fmaf(__ldg(W + (size_t)slot * np3 + I), cosL[t], acc);
-        t += dw;
-        if (t >= L) t -= L;
+    const long long I = (long long)blockIdx.y * blockDim.x + threadIdx.x;
+    if (I >= np3) return;  // after the only barrier
+    const long long n = ctrl->step, lw = P.lw;
+    long long s0 = n % lw;
+    if (s0 < 0) s0 += lw;
+    float acc[32];
+    const float w0 = __ldg(W + (size_t)s0 * np3 + I);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc[j] = w0;  // s = 0: cos 0 = 1
+    long long sp = s0 + 1 == lw ? 0 : s0 + 1, sm = s0 == 0 ? lw - 1 : s0 - 1;
+    for (int s = 1; s <= H; ++s) {
+        const float p = __ldg(W + (size_t)sp * np3 + I) + __ldg(W + (size_t)sm * np3 + I);
+        const float4* c = cs4 + s * 8;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float4 cc = c[k];
+            acc[4 * k] = fmaf(p, cc.x, acc[4 * k]);
+            acc[4 * k + 1] = fmaf(p, cc.y, acc[4 * k + 1]);
+            acc[4 * k + 2] = fmaf(p, cc.z, acc[4 * k + 2]);
+            acc[4 * k + 3] = fmaf(p, cc.w, acc[4 * k + 3]);
+        }
+        sp = sp + 1 == lw ? 0 : sp + 1;
+        sm = sm == 0 ? lw - 1 : sm - 1;
     }
-    V0[(size_t)I * Mp + w] = w < M ? acc : 0.f;
+    float4* out = reinterpret_cast<float4*>(V0 + (size_t)I * Mp + g * 32);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        float v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[e] = g * 32 + 4 * k + e < M ? acc[4 * k + e] : 0.f;  // padding frequencies
+        out[k] = make_float4(v[0], v[1], v[2], v[3]);
+    }
 }
 
-// part[b][w] = sum over the entries of block-row b of a[I][w] * b[I][w] (FP64).
+// part[b][w] = sum over the entries of block-row b of a[I][w] * b[I][w]:
+// FP32 over chunks of kChunk entries, FP64 beyond.
 __global__ void __launch_bounds__(32 * kKryWarps)
     pnk_dot(const float* __restrict__ a, const float* __restrict__ b, long long np3, int Mp,
             double* __restrict__ part)
@@ -67,8 +96,17 @@ __global__ void __launch_bounds__(32 * kKryWarps)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int w = blockIdx.y * 32 + lane;
     double acc = 0.0;
-    for (long long I = (long long)blockIdx.x * kKryWarps + warp; I < np3; I += (long long)gridDim.x * kKryWarps)
-        acc += (double)a[(size_t)I * Mp + w] * (double)b[(size_t)I * Mp + w];
+    float c = 0.f;
+    int t = 0;
+    for (long long I = (long long)blockIdx.x * kKryWarps + warp; I < np3; I += (long long)gridDim.x * kKryWarps) {
+        c = fmaf(a[(size_t)I * Mp + w], b[(size_t)I * Mp + w], c);
+        if (++t == kChunk) {
+            acc += (double)c;
+            c = 0.f;
+            t = 0;
+        }
+    }
+    acc += (double)c;
     red[warp][lane] = acc;
     __syncthreads();
     if (warp == 0) {
@@ -78,18 +116,26 @@ __global__ void __launch_bounds__(32 * kKryWarps)
     }
 }
 
-// out[w] = sum_b part[b][w] in block order; mode 0: the sum; mode 1: its
-// square root, and alive[w] = 0 (the vector of that frequency is set to zero
-// from then on) when the root is below 1e-6 |ref[w]| (a Krylov space
-// exhausted to the precision of FP32 vectors: the result is exact to that
-// precision already); mode 2: the square root.
-__global__ void pnk_fold(const double* __restrict__ part, int nblk, int Mp, double* __restrict__ out, int mode,
-                         const double* __restrict__ ref, int* __restrict__ alive)
+// out[w] = sum_b part[b][w] in block order (8 warps split the blocks, then
+// their sums in warp order); mode 0: the sum; mode 1: its square root, and
+// alive[w] = 0 (that frequency's vectors are zero from then on) when the root
+// is below 1e-6 |ref[w]| (a Krylov space exhausted to the precision of FP32
+// vectors: the result is exact to that precision already); mode 2: the
+// square root.  Block x takes the frequencies 32x .. 32x + 31.
+__global__ void __launch_bounds__(32 * kKryWarps)
+    pnk_fold(const double* __restrict__ part, int nblk, int Mp, double* __restrict__ out, int mode,
+             const double* __restrict__ ref, int* __restrict__ alive)
 {
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= Mp) return;
+    __shared__ double red[kKryWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int w = blockIdx.x * 32 + lane;
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += part[(size_t)b * Mp + w];
+    for (int b = warp; b < nblk; b += kKryWarps) s += part[(size_t)b * Mp + w];
+    red[warp][lane] = s;
+    __syncthreads();
+    if (warp != 0) return;
+    s = 0.0;
+    for (int k = 0; k < kKryWarps; ++k) s += red[k][lane];
     if (mode == 0) {
         out[w] = s;
         return;
@@ -102,99 +148,160 @@ __global__ void pnk_fold(const double* __restrict__ part, int nblk, int Mp, doub
     out[w] = r;
 }
 
-// dst[I][w] = src[I][w] / d[w] (zero where d[w] is zero or the frequency is done).
-__global__ void __launch_bounds__(32 * kKryWarps)
-    pnk_scale(const float* __restrict__ src, float* __restrict__ dst, long long np3, int Mp,
-              const double* __restrict__ d, const int* __restrict__ alive)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int w = blockIdx.y * 32 + lane;
-    const double dd = d[w];
-    const float inv = (alive[w] && dd > 0.0) ? (float)(1.0 / dd) : 0.f;
-    for (long long I = (long long)blockIdx.x * kKryWarps + warp; I < np3; I += (long long)gridDim.x * kKryWarps)
-        dst[(size_t)I * Mp + w] = src[(size_t)I * Mp + w] * inv;
-}
-
-// r = Y - alpha_k v_k - beta_{k-1} v_{k-1} (v_{k-1} may be null).
-__global__ void __launch_bounds__(32 * kKryWarps)
-    pnk_resid(const float* __restrict__ Y, const float* __restrict__ vk, const float* __restrict__ vkm1,
-              const double* __restrict__ alpha, const double* __restrict__ beta, long long np3, int Mp,
-              float* __restrict__ r)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int w = blockIdx.y * 32 + lane;
-    const float a = (float)alpha[w], b = vkm1 ? (float)beta[w] : 0.f;
-    for (long long I = (long long)blockIdx.x * kKryWarps + warp; I < np3; I += (long long)gridDim.x * kKryWarps) {
-        const size_t k = (size_t)I * Mp + w;
-        float v = fmaf(-a, vk[k], Y[k]);
-        if (vkm1) v = fmaf(-b, vkm1[k], v);
-        r[k] = v;
-    }
-}
-
 __device__ __forceinline__ float kdot3(float ax, float ay, float az, float bx, float by, float bz)
 {
     return fmaf(ax, bx, fmaf(ay, by, az * bz));
 }
 
-// Y = hat K_w V for every frequency: a_w v_i + sum_q g_qw sum_j B_q(ij) v_j
-// + sum_q gs_qw sum_j Bs_q(ij) v_i, B = f e e^T + fp (1 - e e^T) at
-// max(r, r_c,min), neighbours within r_c from the lists.  wc[a][w]: row 0 a_w,
-// rows 1..Q g_qw, rows 1+Q.. gs_qw.
+// Z = hat K_w v_k for every frequency (v_k = R_k / beta_k), and the block
+// partials of alpha_k = v_k . Z.  One warp per particle (particles
+// blk * 8 + warp, then strided by the grid), lanes over the 32 frequencies
+// of a group; a neighbour's geometry and radial factors are computed once
+// per pass over kMvGroups groups.  Blocks f e e^T + fp (1 - e e^T) at
+// max(r, r_c,min) for pairs within r_c, from the lists.  wc rows: a_w, g_qw
+// (q < Q), gs_qw (q < Qs), staged in shared memory as FP32 with 1 / beta_k
+// (0 for exhausted frequencies); alpha partials per warp in FP64 there.
 __global__ void __launch_bounds__(32 * kKryWarps)
     pnk_matvec(const StepParams P, const float4* __restrict__ pos, const int* __restrict__ nbr,
                const int* __restrict__ nbr_cnt, const float* __restrict__ ftab, const float* __restrict__ fptab,
-               const double* __restrict__ wc, int Mp, const float* __restrict__ V, float* __restrict__ Y)
+               const double* __restrict__ wc, const double* __restrict__ beta, const int* __restrict__ alive, int Mp,
+               const float* __restrict__ R, float* __restrict__ Z, double* __restrict__ part)
 {
+    extern __shared__ double smd[];
+    const int nrow = 1 + P.Q + P.Qs;
+    double* red = smd;                          // [kKryWarps][Mp]
+    float* wcs = (float*)(smd + kKryWarps * Mp); // [nrow][Mp]
+    float* ib = wcs + (size_t)nrow * Mp;         // [Mp]
+    for (int e = threadIdx.x; e < nrow * Mp; e += blockDim.x) wcs[e] = (float)wc[e];
+    for (int w = threadIdx.x; w < Mp; w += blockDim.x) ib[w] = (alive[w] && beta[w] > 0.0) ? (float)(1.0 / beta[w]) : 0.f;
+    for (int e = threadIdx.x; e < kKryWarps * Mp; e += blockDim.x) red[e] = 0.0;
+    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int i = blockIdx.x * kKryWarps + warp;
-    const int w = blockIdx.y * 32 + lane;
-    if (i >= P.n) return;  // uniform over the warp
+    const int ng = Mp / 32;
     const long long np = P.n_pad;
-    float gq[kMaxQ], gsq[kMaxQ];
+    double* myred = red + (size_t)warp * Mp;
+    for (int i = blockIdx.x * kKryWarps + warp; i < P.n; i += gridDim.x * kKryWarps) {
+        const float4 pi = pos[i];
+        for (int g0 = 0; g0 < ng; g0 += kMvGroups) {
+            float vi[kMvGroups][3], y[kMvGroups][3];
 #pragma unroll
-    for (int q = 0; q < kMaxQ; ++q) {
-        gq[q] = q < P.Q ? (float)wc[(size_t)(1 + q) * Mp + w] : 0.f;
-        gsq[q] = q < P.Qs ? (float)wc[(size_t)(1 + P.Q + q) * Mp + w] : 0.f;
+            for (int gg = 0; gg < kMvGroups; ++gg) {
+                const int w = (g0 + gg) * 32 + lane;
+                const bool in = g0 + gg < ng;
+                const float b = in ? ib[w] : 0.f, aw = in ? wcs[w] : 0.f;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    vi[gg][c] = in ? b * R[((size_t)c * np + i) * Mp + w] : 0.f;
+                    y[gg][c] = aw * vi[gg][c];
+                }
+            }
+            for_each_listed(pi, i, nbr, nbr_cnt[i], P.n_pad, pos, P, [&](int jd, float dx, float dy, float dz, float r2) {
+                const float r = sqrtf(r2);
+                const float inv_r = 1.0f / r;
+                const float ex = dx * inv_r, ey = dy * inv_r, ez = dz * inv_r;
+                const float xr = fmaxf(r, P.rc_min) * P.inv_dr;
+                float fq[kMaxQ], fpq[kMaxQ], fs[kMaxQ], fsp[kMaxQ];
+#pragma unroll
+                for (int q = 0; q < kMaxQ; ++q) {
+                    fq[q] = q < P.Q ? table_at(ftab + q * P.nr, P.nr, xr) : 0.f;
+                    fpq[q] = (q < P.Q && P.perp) ? table_at(fptab + q * P.nr, P.nr, xr) : 0.f;
+                    fs[q] = q < P.Qs ? table_at(ftab + (P.Q + q) * P.nr, P.nr, xr) : 0.f;
+                    fsp[q] = (q < P.Qs && P.perp) ? table_at(fptab + (P.Q + q) * P.nr, P.nr, xr) : 0.f;
+                }
+#pragma unroll
+                for (int gg = 0; gg < kMvGroups; ++gg) {
+                    if (g0 + gg >= ng) break;  // uniform over the warp
+                    const int w = (g0 + gg) * 32 + lane;
+                    float cpar = 0.f, cperp = 0.f, spar = 0.f, sperp = 0.f;  // the pair's combined radial factors
+#pragma unroll
+                    for (int q = 0; q < kMaxQ; ++q) {
+                        if (q < P.Q) {
+                            const float gq = wcs[(1 + q) * Mp + w];
+                            cpar = fmaf(gq, fq[q], cpar);
+                            cperp = fmaf(gq, fpq[q], cperp);
+                        }
+                        if (q < P.Qs) {
+                            const float gs = wcs[(1 + P.Q + q) * Mp + w];
+                            spar = fmaf(gs, fs[q], spar);
+                            sperp = fmaf(gs, fsp[q], sperp);
+                        }
+                    }
+                    const float b = ib[w];
+                    const float vjx = b * R[(size_t)jd * Mp + w], vjy = b * R[((size_t)np + jd) * Mp + w],
+                                vjz = b * R[((size_t)2 * np + jd) * Mp + w];
+                    const float ej = kdot3(ex, ey, ez, vjx, vjy, vjz);
+                    const float ei = kdot3(ex, ey, ez, vi[gg][0], vi[gg][1], vi[gg][2]);
+                    // (par - perp) (e.x) e + perp x, for x = v_j (pair) and x = v_i (self-difference)
+                    const float pj = (cpar - cperp) * ej, si = (spar - sperp) * ei;
+                    y[gg][0] += fmaf(pj + si, ex, fmaf(cperp, vjx, sperp * vi[gg][0]));
+                    y[gg][1] += fmaf(pj + si, ey, fmaf(cperp, vjy, sperp * vi[gg][1]));
+                    y[gg][2] += fmaf(pj + si, ez, fmaf(cperp, vjz, sperp * vi[gg][2]));
+                }
+            });
+#pragma unroll
+            for (int gg = 0; gg < kMvGroups; ++gg) {
+                if (g0 + gg >= ng) break;
+                const int w = (g0 + gg) * 32 + lane;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) Z[((size_t)c * np + i) * Mp + w] = y[gg][c];
+                myred[w] += (double)kdot3(vi[gg][0], vi[gg][1], vi[gg][2], y[gg][0], y[gg][1], y[gg][2]);
+            }
+        }
     }
-    const float aw = (float)wc[w];
-    const float vix = V[(size_t)i * Mp + w], viy = V[(size_t)(np + i) * Mp + w], viz = V[(size_t)(2 * np + i) * Mp + w];
-    float yx = aw * vix, yy = aw * viy, yz = aw * viz;
-    const float4 pi = pos[i];
-    for_each_listed(pi, i, nbr, nbr_cnt[i], P.n_pad, pos, P, [&](int jd, float dx, float dy, float dz, float r2) {
-        const float r = sqrtf(r2);
-        const float inv_r = 1.0f / r;
-        const float ex = dx * inv_r, ey = dy * inv_r, ez = dz * inv_r;
-        const float xr = fmaxf(r, P.rc_min) * P.inv_dr;
-        const float vjx = V[(size_t)jd * Mp + w], vjy = V[(size_t)(np + jd) * Mp + w],
-                    vjz = V[(size_t)(2 * np + jd) * Mp + w];
-        const float ej = kdot3(ex, ey, ez, vjx, vjy, vjz), ei = kdot3(ex, ey, ez, vix, viy, viz);
-        float cpar = 0.f, cperp = 0.f, spar = 0.f, sperp = 0.f;  // combined radial factors of this pair
-        for (int q = 0; q < P.Q; ++q) {
-            const float f = table_at(ftab + q * P.nr, P.nr, xr);
-            const float fp = P.perp ? table_at(fptab + q * P.nr, P.nr, xr) : 0.f;
-            cpar = fmaf(gq[q], f, cpar);
-            cperp = fmaf(gq[q], fp, cperp);
-        }
-        for (int q = 0; q < P.Qs; ++q) {
-            const float f = table_at(ftab + (P.Q + q) * P.nr, P.nr, xr);
-            const float fp = P.perp ? table_at(fptab + (P.Q + q) * P.nr, P.nr, xr) : 0.f;
-            spar = fmaf(gsq[q], f, spar);
-            sperp = fmaf(gsq[q], fp, sperp);
-        }
-        // (par - perp) (e.x) e + perp x, for x = v_j (pair) and x = v_i (self-difference)
-        const float pj = (cpar - cperp) * ej, si = (spar - sperp) * ei;
-        yx += fmaf(pj + si, ex, fmaf(cperp, vjx, sperp * vix));
-        yy += fmaf(pj + si, ey, fmaf(cperp, vjy, sperp * viy));
-        yz += fmaf(pj + si, ez, fmaf(cperp, vjz, sperp * viz));
-    });
-    Y[(size_t)i * Mp + w] = yx;
-    Y[(size_t)(np + i) * Mp + w] = yy;
-    Y[(size_t)(2 * np + i) * Mp + w] = yz;
+    __syncthreads();
+    for (int w = threadIdx.x; w < Mp; w += blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < kKryWarps; ++k) s += red[(size_t)k * Mp + w];
+        part[(size_t)blockIdx.x * Mp + w] = s;
+    }
 }
 
-// out[I] = (sum_w c_w sum_p cf[w][p] V_p[I][w]) / L, c_0 = 1, c_w = 2: one
-// warp per entry, lanes over frequencies, a fixed-order warp sum.
+// R_{k+1} = Z - (alpha_k / beta_k) R_k - (beta_k / beta_{k-1}) R_{k-1} (the
+// last term when R_{k-1} is given), zero for exhausted frequencies; block
+// partials of |R_{k+1}|^2 (FP32 over kChunk entries, FP64 beyond).
+__global__ void __launch_bounds__(32 * kKryWarps)
+    pnk_resid(const float* __restrict__ Z, const float* __restrict__ Rk, const float* __restrict__ Rkm1,
+              const double* __restrict__ alpha_k, const double* __restrict__ beta_k,
+              const double* __restrict__ beta_km1, const int* __restrict__ alive, long long np3, int Mp,
+              float* __restrict__ Rkp1, double* __restrict__ part)
+{
+    __shared__ double red[kKryWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int w = blockIdx.y * 32 + lane;
+    const bool on = alive[w] && beta_k[w] > 0.0;
+    const float a = on ? (float)(alpha_k[w] / beta_k[w]) : 0.f;
+    const float b = (on && Rkm1 && beta_km1[w] > 0.0) ? (float)(beta_k[w] / beta_km1[w]) : 0.f;
+    double acc = 0.0;
+    float c = 0.f;
+    int t = 0;
+    for (long long I = (long long)blockIdx.x * kKryWarps + warp; I < np3; I += (long long)gridDim.x * kKryWarps) {
+        const size_t e = (size_t)I * Mp + w;
+        float r = 0.f;
+        if (on) {
+            r = fmaf(-a, Rk[e], Z[e]);
+            if (Rkm1) r = fmaf(-b, Rkm1[e], r);
+        }
+        Rkp1[e] = r;
+        c = fmaf(r, r, c);
+        if (++t == kChunk) {
+            acc += (double)c;
+            c = 0.f;
+            t = 0;
+        }
+    }
+    acc += (double)c;
+    red[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0) {
+        double s = 0.0;
+        for (int k = 0; k < kKryWarps; ++k) s += red[k][lane];
+        part[(size_t)blockIdx.x * Mp + w] = s;
+    }
+}
+
+// out[I] = (sum_w c_w sum_p cf[w][p] R_p[I][w]) / L, c_0 = 1, c_w = 2 (cf
+// includes 1 / beta_p): one warp per entry, lanes over frequencies, a
+// fixed-order warp sum.
 __global__ void __launch_bounds__(32 * kKryWarps)
     pnk_combine(const float* __restrict__ V, const float* __restrict__ cf, int kp, int M, int Mp, long long np3,
                 float inv_L, float* __restrict__ out)
@@ -214,58 +321,87 @@ __global__ void __launch_bounds__(32 * kKryWarps)
     if (lane == 0) out[I] = acc * inv_L;
 }
 
-unsigned blocks_for(long long np3) { return (unsigned)std::min<long long>((np3 + kKryWarps - 1) / kKryWarps, 1024); }
+unsigned elem_blocks(long long np3) { return (unsigned)std::min<long long>((np3 + kKryWarps - 1) / kKryWarps, 1024); }
+unsigned sweep_blocks(int n) { return (unsigned)std::min<long long>((n + kKryWarps - 1) / kKryWarps, 1024); }
+
+size_t sweep_smem(const StepParams& P, int Mp)
+{
+    return sizeof(double) * kKryWarps * Mp + sizeof(float) * (size_t)(1 + P.Q + P.Qs + 1) * Mp;
+}
+
+cudaError_t set_smem(const void* f, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
 
 }  // namespace
 
-cudaError_t kry_ft(const StepParams& P, const Ctrl* ctrl, const float* W, int M, int Mp, float* V0, cudaStream_t st)
+bool kry_fits(const StepParams& P, int Mp)
+{
+    return (size_t)(P.H + 1) * 8 * sizeof(float4) <= 227 * 1024 && sweep_smem(P, Mp) <= 227 * 1024;
+}
+
+int kry_part_blocks(const StepParams& P)
+{
+    return (int)std::max(elem_blocks(3LL * P.n_pad), sweep_blocks(P.n));
+}
+
+cudaError_t kry_ft(const StepParams& P, const Ctrl* ctrl, const float* W, const float* cosT, int M, int Mp, float* V0,
+                   cudaStream_t st)
 {
     const long long np3 = 3LL * P.n_pad;
-    const dim3 g((unsigned)((np3 + kKryWarps - 1) / kKryWarps), (unsigned)(Mp / 32));
-    const size_t smem = sizeof(float) * (size_t)(2 * P.H + 1);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(pnk_ft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    pnk_ft<<<g, 32 * kKryWarps, smem, st>>>(P, ctrl, W, M, Mp, V0);
+    const dim3 g((unsigned)(Mp / 32), (unsigned)((np3 + kFtThreads - 1) / kFtThreads));
+    const size_t smem = (size_t)(P.H + 1) * 8 * sizeof(float4);
+    cudaError_t e = set_smem((const void*)pnk_ft, smem);
+    if (e != cudaSuccess) return e;
+    pnk_ft<<<g, kFtThreads, smem, st>>>(P, ctrl, W, cosT, M, Mp, V0);
     return cudaGetLastError();
 }
 
-int kry_dot_blocks(const StepParams& P) { return (int)blocks_for(3LL * P.n_pad); }
+cudaError_t kry_fold(const double* part, int nblk, int Mp, double* out, int mode, const double* ref, int* alive,
+                     cudaStream_t st)
+{
+    pnk_fold<<<(unsigned)(Mp / 32), 32 * kKryWarps, 0, st>>>(part, nblk, Mp, out, mode, ref, alive);
+    return cudaGetLastError();
+}
 
 cudaError_t kry_dot(const StepParams& P, const float* a, const float* b, int Mp, double* part, double* out, int mode,
                     const double* ref, int* alive, cudaStream_t st)
 {
     const long long np3 = 3LL * P.n_pad;
-    const unsigned nb = blocks_for(np3);
+    const unsigned nb = elem_blocks(np3);
     pnk_dot<<<dim3(nb, (unsigned)(Mp / 32)), 32 * kKryWarps, 0, st>>>(a, b, np3, Mp, part);
-    pnk_fold<<<(Mp + 127) / 128, 128, 0, st>>>(part, (int)nb, Mp, out, mode, ref, alive);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return kry_fold(part, (int)nb, Mp, out, mode, ref, alive, st);
 }
 
-cudaError_t kry_scale(const StepParams& P, const float* src, float* dst, int Mp, const double* d, const int* alive,
-                      cudaStream_t st)
+cudaError_t kry_matvec(const StepParams& P, const ParticleBuffers& B, const double* wc, const double* beta_k,
+                       const int* alive, int Mp, const float* R, float* Z, double* part, double* alpha_k,
+                       cudaStream_t st)
+{
+    const unsigned nb = sweep_blocks(P.n);
+    const size_t smem = sweep_smem(P, Mp);
+    cudaError_t e = set_smem((const void*)pnk_matvec, smem);
+    if (e != cudaSuccess) return e;
+    pnk_matvec<<<nb, 32 * kKryWarps, smem, st>>>(P, B.pos, B.nbr, B.nbr_cnt, B.ftab, B.fptab, wc, beta_k, alive, Mp,
+                                                 R, Z, part);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return kry_fold(part, (int)nb, Mp, alpha_k, 0, nullptr, nullptr, st);
+}
+
+cudaError_t kry_resid(const StepParams& P, const float* Z, const float* Rk, const float* Rkm1, const double* alpha_k,
+                      const double* beta_k, const double* beta_km1, int* alive, const double* ref, int Mp,
+                      float* Rkp1, double* part, double* beta_kp1, cudaStream_t st)
 {
     const long long np3 = 3LL * P.n_pad;
-    pnk_scale<<<dim3(blocks_for(np3), (unsigned)(Mp / 32)), 32 * kKryWarps, 0, st>>>(src, dst, np3, Mp, d, alive);
-    return cudaGetLastError();
-}
-
-cudaError_t kry_resid(const StepParams& P, const float* Y, const float* vk, const float* vkm1, const double* alpha,
-                      const double* beta, int Mp, float* r, cudaStream_t st)
-{
-    const long long np3 = 3LL * P.n_pad;
-    pnk_resid<<<dim3(blocks_for(np3), (unsigned)(Mp / 32)), 32 * kKryWarps, 0, st>>>(Y, vk, vkm1, alpha, beta, np3,
-                                                                                     Mp, r);
-    return cudaGetLastError();
-}
-
-cudaError_t kry_matvec(const StepParams& P, const ParticleBuffers& B, const double* wc, int Mp, const float* V,
-                       float* Y, cudaStream_t st)
-{
-    const dim3 g((unsigned)((P.n + kKryWarps - 1) / kKryWarps), (unsigned)(Mp / 32));
-    pnk_matvec<<<g, 32 * kKryWarps, 0, st>>>(P, B.pos, B.nbr, B.nbr_cnt, B.ftab, B.fptab, wc, Mp, V, Y);
-    return cudaGetLastError();
+    const unsigned nb = elem_blocks(np3);
+    pnk_resid<<<dim3(nb, (unsigned)(Mp / 32)), 32 * kKryWarps, 0, st>>>(Z, Rk, Rkm1, alpha_k, beta_k, beta_km1,
+                                                                         alive, np3, Mp, Rkp1, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return kry_fold(part, (int)nb, Mp, beta_kp1, 1, ref, alive, st);
 }
 
 cudaError_t kry_combine(const StepParams& P, const float* V, const float* cf, int kp, int M, int Mp, float* out,

@@ -88,23 +88,30 @@ cudaError_t launch_pn_spectrum(const StepParams& P, const ParticleBuffers& B, fl
                                double lo, double hi, int check, double* out, cudaStream_t st);
 int pn_spectrum_blocks(const StepParams& P);
 // Pair-correlated noise by Algorithm 1 (k_pn_krylov.cu): vectors [3 n_pad][Mp]
-// (frequency fastest).  kry_ft: the transformed white-noise window of step
-// ctrl->step into V0; kry_dot: per-frequency dot products a.b into out
-// (mode 0), or square roots of the sums (2; 1 also marks exhausted Krylov
-// spaces in alive, relative to ref); kry_scale: dst = src / d; kry_resid:
-// r = Y - alpha v_k - beta v_{k-1}; kry_matvec: Y = hat K_w V for every w
-// (wc: a_w, g_qw, gs_qw rows); kry_combine: out[I] = (sum_w c_w sum_p
-// cf[w][p] V_p[I][w]) / (2 m_max - 1).
-cudaError_t kry_ft(const StepParams& P, const Ctrl* ctrl, const float* W, int M, int Mp, float* V0, cudaStream_t st);
-int kry_dot_blocks(const StepParams& P);
+// (frequency fastest), Lanczos vectors unnormalised (R_k, v_k = R_k / beta_k).
+// kry_ft: the transformed white-noise window of step ctrl->step into V0
+// (cosT[s][w] = cos(2 pi w s / (2 m_max - 1)), s < m_max, zero columns for
+// w >= M); kry_dot: per-frequency a.b folded into out (mode 0), or the
+// square roots (2; 1 also marks exhausted Krylov spaces in alive, relative
+// to ref); kry_matvec: Z = hat K_w R_k / beta_k for every w (wc: a_w, g_qw,
+// gs_qw rows) and alpha_k; kry_resid: R_{k+1} = Z - alpha_k v_k - beta_k
+// v_{k-1} and beta_{k+1} (fold mode 1); kry_combine: out[I] = (sum_w c_w
+// sum_p cf[w][p] R_p[I][w]) / (2 m_max - 1).  part: kry_part_blocks x Mp
+// doubles.  kry_fits: the transform's and the sweep's shared memory fit.
+bool kry_fits(const StepParams& P, int Mp);
+int kry_part_blocks(const StepParams& P);
+cudaError_t kry_ft(const StepParams& P, const Ctrl* ctrl, const float* W, const float* cosT, int M, int Mp, float* V0,
+                   cudaStream_t st);
+cudaError_t kry_fold(const double* part, int nblk, int Mp, double* out, int mode, const double* ref, int* alive,
+                     cudaStream_t st);
 cudaError_t kry_dot(const StepParams& P, const float* a, const float* b, int Mp, double* part, double* out, int mode,
                     const double* ref, int* alive, cudaStream_t st);
-cudaError_t kry_scale(const StepParams& P, const float* src, float* dst, int Mp, const double* d, const int* alive,
-                      cudaStream_t st);
-cudaError_t kry_resid(const StepParams& P, const float* Y, const float* vk, const float* vkm1, const double* alpha,
-                      const double* beta, int Mp, float* r, cudaStream_t st);
-cudaError_t kry_matvec(const StepParams& P, const ParticleBuffers& B, const double* wc, int Mp, const float* V,
-                       float* Y, cudaStream_t st);
+cudaError_t kry_matvec(const StepParams& P, const ParticleBuffers& B, const double* wc, const double* beta_k,
+                       const int* alive, int Mp, const float* R, float* Z, double* part, double* alpha_k,
+                       cudaStream_t st);
+cudaError_t kry_resid(const StepParams& P, const float* Z, const float* Rk, const float* Rkm1, const double* alpha_k,
+                      const double* beta_k, const double* beta_km1, int* alive, const double* ref, int Mp,
+                      float* Rkp1, double* part, double* beta_kp1, cudaStream_t st);
 cudaError_t kry_combine(const StepParams& P, const float* V, const float* cf, int kp, int M, int Mp, float* out,
                         cudaStream_t st);
 // Largest Gershgorin row sum sum_j |f(r_ij)| of the pair matrix at the
