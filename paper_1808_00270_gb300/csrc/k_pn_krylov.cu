@@ -62,8 +62,7 @@ __global__ void __launch_bounds__(kFtThreads)
 #pragma unroll
     for (int j = 0; j < 32; ++j) acc[j] = w0;  // s = 0: cos 0 = 1
     long long sp = s0 + 1 == lw ? 0 : s0 + 1, sm = s0 == 0 ? lw - 1 : s0 - 1;
-    for (int s = 1; s <= H; ++s) {
-        const float p = __ldg(W + (size_t)sp * np3 + I) + __ldg(W + (size_t)sm * np3 + I);
+    auto term = [&](float p, int s) {
         const float4* c = cs4 + s * 8;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
@@ -73,6 +72,22 @@ __global__ void __launch_bounds__(kFtThreads)
             acc[4 * k + 2] = fmaf(p, cc.z, acc[4 * k + 2]);
             acc[4 * k + 3] = fmaf(p, cc.w, acc[4 * k + 3]);
         }
+    };
+    int s = 1;
+    for (; s + 3 <= H; s += 4) {  // the loads of four window pairs in flight together
+        float a[4], b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            a[u] = __ldg(W + (size_t)sp * np3 + I);
+            b[u] = __ldg(W + (size_t)sm * np3 + I);
+            sp = sp + 1 == lw ? 0 : sp + 1;
+            sm = sm == 0 ? lw - 1 : sm - 1;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) term(a[u] + b[u], s + u);
+    }
+    for (; s <= H; ++s) {
+        term(__ldg(W + (size_t)sp * np3 + I) + __ldg(W + (size_t)sm * np3 + I), s);
         sp = sp + 1 == lw ? 0 : sp + 1;
         sm = sm == 0 ? lw - 1 : sm - 1;
     }
@@ -161,7 +176,7 @@ __device__ __forceinline__ float kdot3(float ax, float ay, float az, float bx, f
 // max(r, r_c,min) for pairs within r_c, from the lists.  wc rows: a_w, g_qw
 // (q < Q), gs_qw (q < Qs), staged in shared memory as FP32 with 1 / beta_k
 // (0 for exhausted frequencies); alpha partials per warp in FP64 there.
-__global__ void __launch_bounds__(32 * kKryWarps)
+__global__ void __launch_bounds__(32 * kKryWarps, 3)
     pnk_matvec(const StepParams P, const float4* __restrict__ pos, const int* __restrict__ nbr,
                const int* __restrict__ nbr_cnt, const float* __restrict__ ftab, const float* __restrict__ fptab,
                const double* __restrict__ wc, const double* __restrict__ beta, const int* __restrict__ alive, int Mp,
@@ -195,7 +210,23 @@ __global__ void __launch_bounds__(32 * kKryWarps)
                     y[gg][c] = aw * vi[gg][c];
                 }
             }
-            for_each_listed(pi, i, nbr, nbr_cnt[i], P.n_pad, pos, P, [&](int jd, float dx, float dy, float dz, float r2) {
+            // the list in order, one neighbour at a time with the next one's
+            // index and position in flight; the pair test of the list walkers
+            const int cnt = nbr_cnt[i];
+            int jn = cnt > 0 ? __ldg(nbr + i) : 0;
+            float4 pn = cnt > 0 ? __ldg(pos + jn) : pi;
+            for (int sl = 0; sl < cnt; ++sl) {
+                const int jd = jn;
+                const float4 pj = pn;
+                if (sl + 1 < cnt) {
+                    jn = __ldg(nbr + (size_t)(sl + 1) * P.n_pad + i);
+                    pn = __ldg(pos + jn);
+                }
+                const float dx = min_image(pi.x, pj.x, P.box, P.half_box);
+                const float dy = min_image(pi.y, pj.y, P.box, P.half_box);
+                const float dz = min_image(pi.z, pj.z, P.box, P.half_box);
+                const float r2 = dist2(dx, dy, dz);
+                if (!(r2 < P.rc2)) continue;
                 const float r = sqrtf(r2);
                 const float inv_r = 1.0f / r;
                 const float ex = dx * inv_r, ey = dy * inv_r, ez = dz * inv_r;
@@ -237,7 +268,7 @@ __global__ void __launch_bounds__(32 * kKryWarps)
                     y[gg][1] += fmaf(pj + si, ey, fmaf(cperp, vjy, sperp * vi[gg][1]));
                     y[gg][2] += fmaf(pj + si, ez, fmaf(cperp, vjz, sperp * vi[gg][2]));
                 }
-            });
+            }
 #pragma unroll
             for (int gg = 0; gg < kMvGroups; ++gg) {
                 if (g0 + gg >= ng) break;
