@@ -32,7 +32,7 @@ namespace {
 
 constexpr int kKryWarps = 8;    // warps per block of the elementwise kernels and the sweep
 constexpr int kFtThreads = 256; // entries per block of the transform
-constexpr int kMvGroups = 4;    // frequency groups (of 32) per neighbour pass of the sweep
+constexpr int kMvGroups = 8;    // frequency groups (of 32) per neighbour pass of the sweep
 constexpr int kChunk = 16;      // FP32 terms summed before an FP64 addition
 
 // V0[I][w] = W_n[I] + sum_{s=1}^{H} (W_{n+s}[I] + W_{n-s}[I]) cos(2 pi w s / L)
@@ -176,7 +176,7 @@ __device__ __forceinline__ float kdot3(float ax, float ay, float az, float bx, f
 // max(r, r_c,min) for pairs within r_c, from the lists.  wc rows: a_w, g_qw
 // (q < Q), gs_qw (q < Qs), staged in shared memory as FP32 with 1 / beta_k
 // (0 for exhausted frequencies); alpha partials per warp in FP64 there.
-__global__ void __launch_bounds__(32 * kKryWarps, 3)
+__global__ void __launch_bounds__(32 * kKryWarps, 2)
     pnk_matvec(const StepParams P, const float4* __restrict__ pos, const int* __restrict__ nbr,
                const int* __restrict__ nbr_cnt, const float* __restrict__ ftab, const float* __restrict__ fptab,
                const double* __restrict__ wc, const double* __restrict__ beta, const int* __restrict__ alive, int Mp,
@@ -305,19 +305,36 @@ __global__ void __launch_bounds__(32 * kKryWarps)
     double acc = 0.0;
     float c = 0.f;
     int t = 0;
-    for (long long I = (long long)blockIdx.x * kKryWarps + warp; I < np3; I += (long long)gridDim.x * kKryWarps) {
-        const size_t e = (size_t)I * Mp + w;
-        float r = 0.f;
-        if (on) {
-            r = fmaf(-a, Rk[e], Z[e]);
-            if (Rkm1) r = fmaf(-b, Rkm1[e], r);
+    const long long st = (long long)gridDim.x * kKryWarps;
+    // four entries per round with their loads in flight together (summed in
+    // the order of the entries, as one at a time)
+    for (long long I0 = (long long)blockIdx.x * kKryWarps + warp; I0 < np3; I0 += 4 * st) {
+        float z[4], rk[4], rm[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const long long I = I0 + u * st;
+            const bool in = I < np3;
+            const size_t e = (size_t)(in ? I : I0) * Mp + w;
+            z[u] = in && on ? Z[e] : 0.f;
+            rk[u] = in && on ? Rk[e] : 0.f;
+            rm[u] = in && on && Rkm1 ? Rkm1[e] : 0.f;
         }
-        Rkp1[e] = r;
-        c = fmaf(r, r, c);
-        if (++t == kChunk) {
-            acc += (double)c;
-            c = 0.f;
-            t = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const long long I = I0 + u * st;
+            if (I >= np3) break;
+            float r = 0.f;
+            if (on) {
+                r = fmaf(-a, rk[u], z[u]);
+                if (Rkm1) r = fmaf(-b, rm[u], r);
+            }
+            Rkp1[(size_t)I * Mp + w] = r;
+            c = fmaf(r, r, c);
+            if (++t == kChunk) {
+                acc += (double)c;
+                c = 0.f;
+                t = 0;
+            }
         }
     }
     acc += (double)c;
@@ -344,7 +361,15 @@ __global__ void __launch_bounds__(32 * kKryWarps)
     float acc = 0.f;
     for (int w = lane; w < M; w += 32) {
         float x = 0.f;
-        for (int p = 0; p < kp; ++p) x = fmaf(cf[(size_t)w * kp + p], V[p * stride + (size_t)I * Mp + w], x);
+        int p = 0;
+        for (; p + 4 <= kp; p += 4) {  // four vectors' loads in flight, summed in order
+            float v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = V[(p + u) * stride + (size_t)I * Mp + w];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x = fmaf(cf[(size_t)w * kp + p + u], v[u], x);
+        }
+        for (; p < kp; ++p) x = fmaf(cf[(size_t)w * kp + p], V[p * stride + (size_t)I * Mp + w], x);
         acc = fmaf(w == 0 ? 1.f : 2.f, x, acc);
     }
 #pragma unroll
