@@ -808,6 +808,39 @@ __device__ __forceinline__ void pcorr_fold(const StepParams& P, long long* __res
 // are added to the bin of r_ij(t) in 2^-28 fixed point (integer sums do not
 // depend on the order of the atomics, so results are reproducible bit for
 // bit).  The previous launch's sums are folded into the FP64 sums meanwhile.
+// Each warp scans its 32 particles' lists and queues the pairs that count
+// (about a quarter of the entries: j > i and r < r_max) in shared memory;
+// the origin loop then runs over full warps of queued pairs.
+struct PcPair {
+    int i, j, bin;
+    float ex, ey, ez, vit, vjt;
+};
+constexpr int kPcQueue = 64;  // queued pairs per warp (processed 32 at a time)
+
+__device__ __forceinline__ void pcorr_pairs(const StepParams& P, const PcPair& e, const float4* __restrict__ vorig,
+                                            long long* __restrict__ hs, long long* __restrict__ hn, int n_act,
+                                            bool is_origin, int slot0, int nb)
+{
+    atomicAdd((unsigned long long*)(hn + e.bin), 1ull);  // the same pairs for every origin
+    // lanes start at different origins, so that the shared-memory atomics of
+    // one instruction seldom meet on the same (origin, bin)
+    const int q0 = (threadIdx.x & 31) % n_act;
+    for (int qq = 0; qq < n_act; ++qq) {
+        const int q = qq + q0 < n_act ? qq + q0 : qq + q0 - n_act;
+        float vi0 = e.vit, vj0 = e.vjt;
+        if (!(q == 0 && is_origin)) {
+            int sl = slot0 - q;
+            sl = sl < 0 ? sl + P.n_os : sl;
+            const float4 oi = __ldg(vorig + (size_t)sl * P.n + e.i), oj = __ldg(vorig + (size_t)sl * P.n + e.j);
+            vi0 = oi.x * e.ex + oi.y * e.ey + oi.z * e.ez;
+            vj0 = oj.x * e.ex + oj.y * e.ey + oj.z * e.ez;
+        }
+        long long* h = hs + 3 * (q * nb + e.bin);
+        atomicAdd((unsigned long long*)h, (unsigned long long)pc_fixed(e.vit * vi0 + e.vjt * vj0));
+        atomicAdd((unsigned long long*)(h + 1), (unsigned long long)pc_fixed(e.vit * vj0 + e.vjt * vi0));
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) pcorr(const StepParams P, Ctrl* __restrict__ ctrl,
                                                   const float4* __restrict__ pos, const float4* __restrict__ vel,
                                                   const float4* __restrict__ vorig, const int* __restrict__ nbr,
@@ -826,49 +859,64 @@ __global__ void __launch_bounds__(kThreads) pcorr(const StepParams P, Ctrl* __re
     if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->pc_pending = 1;
     extern __shared__ long long hs[];  // [n_act][nbins][3] (a, c, unused) then [nbins] pair counts
     long long* hn = hs + 3 * P.n_os * nb;
+    __shared__ PcPair queue[kThreads / 32][kPcQueue];
     for (int k = threadIdx.x; k < n_act * nb * 3; k += blockDim.x) hs[k] = 0;
     for (int k = threadIdx.x; k < nb; k += blockDim.x) hn[k] = 0;
     __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    PcPair* qw = queue[warp];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < P.n) {
-        const float4 pi = pos[i], vi = vel[i];
-        const int cnt = nbr_cnt[i];
-        for (int s = 0; s < cnt; ++s) {
+    const bool own = i < P.n;
+    float4 pi = make_float4(0.f, 0.f, 0.f, 0.f), vi = pi;
+    int cnt = 0;
+    if (own) {
+        pi = pos[i];
+        vi = vel[i];
+        cnt = nbr_cnt[i];
+    }
+    int count = 0;  // queued pairs (uniform over the warp)
+    for (int s = 0; __any_sync(0xffffffffu, s < cnt); ++s) {
+        bool take = false;
+        PcPair e;
+        if (s < cnt) {
             const int j = __ldg(nbr + (size_t)s * P.n_pad + i);
-            if (j <= i) continue;
-            const float4 pj = __ldg(pos + j);
-            const float dx = min_image(pi.x, pj.x, P.box, P.half_box);
-            const float dy = min_image(pi.y, pj.y, P.box, P.half_box);
-            const float dz = min_image(pi.z, pj.z, P.box, P.half_box);
-            const float r2 = dist2(dx, dy, dz);
-            if (!(r2 < P.pc_rmax2)) continue;
-            const float r = sqrtf(r2);
-            const float inv = 1.0f / r;
-            const float ex = dx * inv, ey = dy * inv, ez = dz * inv;
-            const int bin = min((int)(r * P.pc_inv_dr), nb - 1);
-            const float4 vj = __ldg(vel + j);
-            const float vit = vi.x * ex + vi.y * ey + vi.z * ez;
-            const float vjt = vj.x * ex + vj.y * ey + vj.z * ez;
-            atomicAdd((unsigned long long*)(hn + bin), 1ull);  // the same pairs for every origin
-            // lanes start at different origins, so that the shared-memory
-            // atomics of one instruction seldom meet on the same (origin, bin)
-            const int q0 = (threadIdx.x & 31) % n_act;
-            for (int qq = 0; qq < n_act; ++qq) {
-                const int q = qq + q0 < n_act ? qq + q0 : qq + q0 - n_act;
-                float vi0 = vit, vj0 = vjt;
-                if (!(q == 0 && is_origin)) {
-                    int sl = slot0 - q;
-                    sl = sl < 0 ? sl + P.n_os : sl;
-                    const float4 oi = __ldg(vorig + (size_t)sl * P.n + i), oj = __ldg(vorig + (size_t)sl * P.n + j);
-                    vi0 = oi.x * ex + oi.y * ey + oi.z * ez;
-                    vj0 = oj.x * ex + oj.y * ey + oj.z * ez;
+            if (j > i) {
+                const float4 pj = __ldg(pos + j);
+                const float dx = min_image(pi.x, pj.x, P.box, P.half_box);
+                const float dy = min_image(pi.y, pj.y, P.box, P.half_box);
+                const float dz = min_image(pi.z, pj.z, P.box, P.half_box);
+                const float r2 = dist2(dx, dy, dz);
+                if (r2 < P.pc_rmax2) {
+                    const float r = sqrtf(r2);
+                    const float inv = 1.0f / r;
+                    e.i = i;
+                    e.j = j;
+                    e.ex = dx * inv;
+                    e.ey = dy * inv;
+                    e.ez = dz * inv;
+                    e.bin = min((int)(r * P.pc_inv_dr), nb - 1);
+                    const float4 vj = __ldg(vel + j);
+                    e.vit = vi.x * e.ex + vi.y * e.ey + vi.z * e.ez;
+                    e.vjt = vj.x * e.ex + vj.y * e.ey + vj.z * e.ez;
+                    take = true;
                 }
-                long long* h = hs + 3 * (q * nb + bin);
-                atomicAdd((unsigned long long*)h, (unsigned long long)pc_fixed(vit * vi0 + vjt * vj0));
-                atomicAdd((unsigned long long*)(h + 1), (unsigned long long)pc_fixed(vit * vj0 + vjt * vi0));
             }
         }
+        const unsigned m = __ballot_sync(0xffffffffu, take);
+        if (take) qw[count + __popc(m & ((1u << lane) - 1u))] = e;
+        count += __popc(m);  // <= 31 + 32 < kPcQueue
+        __syncwarp();
+        if (count >= 32) {  // a full warp of pairs; the rest moves to the front
+            pcorr_pairs(P, qw[lane], vorig, hs, hn, n_act, is_origin, slot0, nb);
+            __syncwarp();
+            const PcPair rest = qw[32 + lane];
+            __syncwarp();
+            if (lane < count - 32) qw[lane] = rest;
+            count -= 32;
+            __syncwarp();
+        }
     }
+    if (lane < count) pcorr_pairs(P, qw[lane], vorig, hs, hn, n_act, is_origin, slot0, nb);
     __syncthreads();
     long long* out = step_sums + (size_t)ctrl->pc_buf * P.n_os * nb * 3;
     for (int k = threadIdx.x; k < n_act * nb * 3; k += blockDim.x) {
@@ -1380,7 +1428,8 @@ cudaError_t launch_pcorr(const StepParams& P, const ParticleBuffers& B, cudaStre
     if (P.pc_nbins <= 0 || P.vacf_len <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)std::max(1, (P.n + kThreads - 1) / kThreads);
     const size_t smem = sizeof(long long) * (3 * (size_t)P.n_os * P.pc_nbins + P.pc_nbins);
-    if (smem > 48 * 1024) {
+    // beside the static pair queues (16 KB)
+    if (smem + sizeof(PcPair) * (kThreads / 32) * kPcQueue > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(pcorr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
