@@ -283,8 +283,11 @@ gld_status gld_set_perpendicular(gld_ctx* ctx, const double* fp, const double* f
  * (gs = c g: its blocks c fs(r) e e^T join M on the diagonal; GLD_E_INVAL
  * otherwise); GLD_E_NOT_PSD if h_w < |g_w| lambda for some w (positive
  * semi-definiteness not guaranteed) unless psd_clamp.  degree = 0 returns to
- * the self-kernel noise; gld_set_kernels does too.  Such a context cannot join
- * a batch.  Synchronizes. */
+ * the self-kernel noise; gld_set_kernels does too.  Such a context can join a
+ * batch: its K + 1 filters run in the batch's noise block and its Clenshaw
+ * sweeps as batch launches over the members' particle tiles (the batch uses
+ * the FP32-pipe filter, so a member's F^R differs from the context alone by
+ * FP32 rounding).  Synchronizes. */
 gld_status gld_set_pair_noise(gld_ctx* ctx, int32_t degree, double* lambda, double* cheb_err);
 /* The filters of gld_set_pair_noise, on the host (no device needed): from the
  * discrete weights ks[m_max] of the self kernel and g[m_max] of the pair
@@ -426,7 +429,11 @@ gld_status gld_destroy(gld_ctx* ctx);
  * share the number of kernel terms, the history type and compensation with
  * the other members.  A member's kernels, tables and parameters are read when
  * it joins: change them only while it is out of the batch.  Results of a
- * member do not depend on the other members.
+ * member do not depend on the other members.  Members may carry the
+ * pair-correlated noise of gld_set_pair_noise (not the interval form of
+ * gld_set_pair_noise_on, whose check runs a Lanczos iteration per member,
+ * nor gld_set_pair_noise_krylov: GLD_E_INVAL); pair correlations and memory
+ * modes are single-context features.
  * The convolution's tile schedule is picked by timing four candidates on the
  * current composition (256- or 128-column tiles, longest memory first, member
  * order, or one block per member). */

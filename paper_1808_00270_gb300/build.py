@@ -62,7 +62,9 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = f"{LIB}.{os.getpid()}.tmp"
-    r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
+    # every symbol resolved at link time (a missing definition fails here, not when the library loads)
+    r = subprocess.run([cc, *ARCH, "-shared", "-Xlinker", "--no-undefined", "-o", tmp, *objs], capture_output=True,
+                       text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)

@@ -2222,8 +2222,13 @@ gld_status batch_plan(gld_batch* b, int schedule)
         d.B = c->B;
         d.coef = c->coef;
         d.W = c->W;
-        d.taps = c->Acp;
+        d.taps = c->P.pn_deg > 0 ? c->d_pntaps : c->Acp;  // row 0 of the pair-noise filters
         d.ntaps = fir_taps_len(c->P.H);
+        d.pntaps = c->d_pntaps;
+        d.zblk = c->d_zblk;
+        d.bvec = c->d_bvec;
+        d.pn_la = c->la;
+        P.pn_kmax = std::max(P.pn_kmax, c->P.pn_deg);
         d.k0 = (uint32_t)c->prm.seed;
         d.k1 = (uint32_t)(c->prm.seed >> 32);
         d.int2ext = c->d_int2ext;
@@ -2402,9 +2407,10 @@ gld_status gld_batch_add(gld_batch* b, gld_ctx* c)
     if (!c->have_kernels) return bfail(b, GLD_E_STATE, "gld_batch_add: the member has no kernels set");
     if (c->st != b->st) return bfail(b, GLD_E_INVAL, "gld_batch_add: the member must use the batch's stream");
     if (c->P.T != kMaxNoiseBlock) return bfail(b, GLD_E_INVAL, "gld_batch_add: the member's noise block must be 64");
-    if (c->P.pc_nbins > 0 || c->P.nmodes > 0 || c->P.pn_deg > 0 || c->P.pn_kry)
+    if (c->P.pc_nbins > 0 || c->P.nmodes > 0 || c->P.pn_iv || c->P.pn_kry)
         return bfail(b, GLD_E_INVAL,
-                     "gld_batch_add: pair correlations, memory modes and pair noise are single-context features");
+                     "gld_batch_add: pair correlations, memory modes, and pair noise on an estimated interval or by "
+                     "Lanczos iterations are single-context features");
     if (c->noise_valid && c->host_step != c->noise_end)
         return bfail(b, GLD_E_STATE, "gld_batch_add: the member is inside a noise block (step a multiple of 64)");
     for (gld_ctx* m : b->members)
@@ -2445,7 +2451,8 @@ gld_status gld_batch_step(gld_batch* b, int64_t nsteps)
     for (size_t m = 0; m < b->members.size() && !b->dirty; ++m)  // kernels reset since the plan
         if (m >= b->snap.size() || std::memcmp(&b->snap[m].P, &b->members[m]->P, sizeof(StepParams)) != 0 ||
             std::memcmp(&b->snap[m].B, &b->members[m]->B, sizeof(ParticleBuffers)) != 0 ||
-            b->snap[m].coef != b->members[m]->coef)
+            b->snap[m].coef != b->members[m]->coef || b->snap[m].pntaps != b->members[m]->d_pntaps ||
+            b->snap[m].zblk != b->members[m]->d_zblk || b->snap[m].bvec != b->members[m]->d_bvec)
             b->dirty = true;
     GLD_TRY(batch_prepare(b));
     for (int64_t k = 0; k < nsteps; k += kMaxNoiseBlock) {

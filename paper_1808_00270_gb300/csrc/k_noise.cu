@@ -329,6 +329,18 @@ cudaError_t launch_noise_filter(const StepParams& P, Ctrl* ctrl, const float* W,
     return cudaGetLastError();
 }
 
+// Pass k >= 1 of the pair-noise filters: Z_k of the members whose degree
+// reaches k (the others' tiles return at once).
+__global__ void __launch_bounds__(kFirThreads)
+    b_fir_pn(const SysDesc* __restrict__ D, const Tile* __restrict__ tiles, int chunk, int k)
+{
+    const Tile t = tiles[blockIdx.x];
+    const SysDesc& d = D[t.m];
+    if (k > d.P.pn_deg) return;  // uniform over the block
+    fir_body(d.P, d.B.ctrl, d.W, d.pntaps + (size_t)k * d.pn_la, d.ntaps, chunk,
+             d.zblk + (size_t)(k - 1) * d.P.T * 3 * d.P.n_pad, t.b, d.nb_fir);
+}
+
 cudaError_t launch_batch_noise(const BatchPlan& bp, cudaStream_t st)
 {
     static_assert(kGenThreads == kBatchPartBlock, "white-noise tiles use the particle tiles");
@@ -341,6 +353,12 @@ cudaError_t launch_batch_noise(const BatchPlan& bp, cudaStream_t st)
     cudaError_t e = cudaFuncSetAttribute(b_fir, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     b_fir<<<bp.n_fir, kFirThreads, smem, st>>>(bp.desc, bp.fir, chunk);
+    if (bp.pn_kmax > 0) {
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(b_fir_pn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return e;
+        for (int k = 1; k <= bp.pn_kmax; ++k) b_fir_pn<<<bp.n_fir, kFirThreads, smem, st>>>(bp.desc, bp.fir, chunk, k);
+    }
     return cudaGetLastError();
 }
 

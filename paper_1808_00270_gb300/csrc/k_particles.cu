@@ -1117,12 +1117,12 @@ __device__ __forceinline__ void pn_apply(const StepParams& P, const float4* __re
     });
 }
 
-__global__ void __launch_bounds__(kThreads)
-    pn_stage(const StepParams P, Ctrl* __restrict__ ctrl, const float4* __restrict__ pos, const int* __restrict__ nbr,
-             const int* __restrict__ nbr_cnt, const float* __restrict__ ftab, const float* __restrict__ fptab,
-             const PnStage S)
+__device__ __forceinline__ void pn_stage_body(const StepParams& P, Ctrl* __restrict__ ctrl, const float4* __restrict__ pos,
+                                              const int* __restrict__ nbr, const int* __restrict__ nbr_cnt,
+                                              const float* __restrict__ ftab, const float* __restrict__ fptab,
+                                              const PnStage& S, int blk)
 {
-    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    const int id = blk * blockDim.x + threadIdx.x;
     if (id >= P.n) return;
     const long long np = P.n_pad;
     const long long row = ctrl->step - ctrl->noise_n0;
@@ -1152,6 +1152,44 @@ __global__ void __launch_bounds__(kThreads)
     // the symmetric bound is checked every step by Gershgorin; an interval
     // from Ritz values by the Lanczos run at each noise block
     if (S.last && !P.pn_iv && rowsum > P.pn_lambda) atomicOr(&ctrl->err, kErrPnBound);
+}
+
+// Clenshaw stage k of a degree-K evaluation: b_K = Z_K (read in place), b_k
+// for K > k >= 1 in bvec[k % 3], the last stage writes F over the Z_0 row.
+__host__ __device__ __forceinline__ PnStage pn_stage_args(const StepParams& P, const float* frblock, const float* zblk,
+                                                 float* bvec, int K, int k)
+{
+    const size_t blk = (size_t)P.T * 3 * P.n_pad, vec = (size_t)3 * P.n_pad;
+    auto zk = [&](int q) -> const float* { return q == 0 ? frblock : zblk + (size_t)(q - 1) * blk; };
+    PnStage S{};
+    S.z = zk(k);
+    S.last = k == 0;
+    if (k + 1 == K) { S.b1 = zk(K); S.b1_rows = 1; }
+    else { S.b1 = bvec + (size_t)((k + 1) % 3) * vec; }
+    if (k + 2 == K) { S.b2 = zk(K); S.b2_rows = 1; }
+    else if (k + 2 < K) { S.b2 = bvec + (size_t)((k + 2) % 3) * vec; }
+    if (k == 0) { S.out = const_cast<float*>(frblock); S.out_rows = 1; }
+    else { S.out = bvec + (size_t)(k % 3) * vec; }
+    return S;
+}
+
+__global__ void __launch_bounds__(kThreads)
+    pn_stage(const StepParams P, Ctrl* __restrict__ ctrl, const float4* __restrict__ pos, const int* __restrict__ nbr,
+             const int* __restrict__ nbr_cnt, const float* __restrict__ ftab, const float* __restrict__ fptab,
+             const PnStage S)
+{
+    pn_stage_body(P, ctrl, pos, nbr, nbr_cnt, ftab, fptab, S, blockIdx.x);
+}
+
+// Stage k of every member whose degree exceeds k, over the particle tiles.
+__global__ void __launch_bounds__(kThreads) b_pn_stage(const SysDesc* __restrict__ D, const Tile* __restrict__ tiles, int k)
+{
+    const Tile t = tiles[blockIdx.x];
+    const SysDesc& d = D[t.m];
+    const int K = d.P.pn_deg;
+    if (k >= K) return;
+    const PnStage S = pn_stage_args(d.P, d.B.frblock, d.zblk, d.bvec, K, k);
+    pn_stage_body(d.P, d.B.ctrl, d.B.pos, d.B.nbr, d.B.nbr_cnt, d.B.ftab, d.B.fptab, S, t.b);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -1333,6 +1371,9 @@ __global__ void lz_final(const double* __restrict__ ab, double lo, double hi, in
 
 cudaError_t launch_batch_particles(const BatchPlan& bp, cudaStream_t st)
 {
+    static_assert(kBatchPartBlock == kThreads, "Clenshaw stages use the particle tiles");
+    if (bp.n_part)  // pair-correlated noise of the step, stage by stage over all members
+        for (int k = bp.pn_kmax - 1; k >= 0; --k) b_pn_stage<<<bp.n_part, kThreads, 0, st>>>(bp.desc, bp.part, k);
     if (bp.n_pair) {
         if (bp.pair_fast) b_pair<true><<<bp.n_pair, kPairThreads, 0, st>>>(bp.desc, bp.pair);
         else b_pair<false><<<bp.n_pair, kPairThreads, 0, st>>>(bp.desc, bp.pair);
@@ -1450,21 +1491,10 @@ cudaError_t launch_pair_noise(const StepParams& P, const ParticleBuffers& B, con
 {
     const int K = P.pn_deg;
     if (K <= 0) return cudaSuccess;
-    const size_t blk = (size_t)P.T * 3 * P.n_pad, vec = (size_t)3 * P.n_pad;
-    auto zk = [&](int k) -> const float* { return k == 0 ? B.frblock : zblk + (size_t)(k - 1) * blk; };
     const unsigned grid = (unsigned)((P.n + kThreads - 1) / kThreads);
-    // b_K = Z_K (read in place); b_k for K > k >= 1 in bvec[k % 3]
     for (int k = K - 1; k >= 0; --k) {
-        PnStage S{};
-        S.z = zk(k);
-        S.last = k == 0;
-        if (k + 1 == K) { S.b1 = zk(K); S.b1_rows = 1; }
-        else { S.b1 = bvec + (size_t)((k + 1) % 3) * vec; }
-        if (k + 2 == K) { S.b2 = zk(K); S.b2_rows = 1; }
-        else if (k + 2 < K) { S.b2 = bvec + (size_t)((k + 2) % 3) * vec; }
-        if (k == 0) { S.out = B.frblock; S.out_rows = 1; }
-        else { S.out = bvec + (size_t)(k % 3) * vec; }
-        pn_stage<<<grid, kThreads, 0, st>>>(P, B.ctrl, B.pos, B.nbr, B.nbr_cnt, B.ftab, B.fptab, S);
+        pn_stage<<<grid, kThreads, 0, st>>>(P, B.ctrl, B.pos, B.nbr, B.nbr_cnt, B.ftab, B.fptab,
+                                            pn_stage_args(P, B.frblock, zblk, bvec, K, k));
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -139,6 +139,13 @@ struct SysDesc {
     uint32_t k0, k1;         // Philox key
     const int* int2ext;
     int nb_pair, nb_part, nb_cell, nb_vacf, nb_conv, nb_fir, nb_cf;
+    // pair-correlated noise (Chebyshev form, P.pn_deg > 0): taps
+    // [pn_deg + 1][pn_la] (row 0 is `taps`), the blocks Z_1 .. Z_deg and three
+    // Clenshaw vectors [3][n_pad]
+    const float* pntaps;
+    float* zblk;
+    float* bvec;
+    int pn_la;
 };
 struct Tile {
     int m, b;   // member, block within member
@@ -151,6 +158,7 @@ struct BatchPlan {
     int max_H, max_n, max_ntaps, nacc, bf16, kahan, vacf_no;
     int conv_block;  // threads per convolution tile (128 or 256)
     int pair_fast;   // every member has one pair term and no self-difference term
+    int pn_kmax;     // the largest Chebyshev degree of the members' pair noise (0: none)
 };
 cudaError_t launch_batch_conv(const BatchPlan& bp, cudaStream_t st);      // k_history.cu
 cudaError_t launch_batch_particles(const BatchPlan& bp, cudaStream_t st); // k_particles.cu

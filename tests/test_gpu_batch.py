@@ -180,3 +180,65 @@ def test_batch_history_precision_against_oracle():
     print("displacement relative L2 vs FP64 oracle after 128 batched steps:", errs)
     assert max(errs["f32"]) < 1e-4
     assert max(errs["bf16_kahan"]) < 1e-2
+
+
+def _pn_member(w, degree=0, strength=0.3):
+    """A context with the workload's pair kernel scaled by `strength` and, for
+    degree > 0, the Chebyshev pair noise on the Gershgorin bound."""
+    from paper_1808_00270_gb300 import GLD, inputs
+    pos, vel = inputs.initial_state(w)
+    g, f, dr = inputs.pair_kernel_tables(w)
+    s = GLD(n=w.n, box=w.box, mass=w.mass, kT=w.kT, dt=w.dt, m_max=w.m_max, r_c=w.r_c, A_cons=w.A_cons,
+            seed=w.seed, pos=pos, vel=vel)
+    s.set_kernels(inputs.self_kernel_samples(w), g=g, f=strength * f, dr=dr)
+    if degree:
+        s.set_pair_noise(degree)
+    return s
+
+
+def test_batch_pair_noise_matches_single_system():
+    """Members with the Chebyshev pair noise (degrees 8 and 4) beside one
+    without: over two noise blocks each follows the same system stepped
+    alone (F^R of the last step, positions, velocities and displacements
+    within 1e-5; the batch filters on the FP32 pipes, a context alone on the
+    tensor cores), and the member without pair noise gets the bits it gets in
+    a batch of its own."""
+    from paper_1808_00270_gb300 import ARR_FR, Batch
+    ws = [_workload("pn_a", 128, 0.1, 200, 21), _workload("pn_b", 500, 0.08, 200, 22),
+          _workload("pn_c", 300, 0.05, 100, 23)]
+    degs = [8, 4, 0]
+    alone = [_pn_member(w, d) for w, d in zip(ws, degs)]
+    inb = [_pn_member(w, d) for w, d in zip(ws, degs)]
+    b = Batch()
+    for g in inb:
+        b.add(g)
+    b.step(128)
+    b.sync()
+    for a in alone:
+        a.step(128)
+    for a, g in zip(alone, inb):
+        assert rel_l2(g.get(ARR_FR), a.get(ARR_FR)) < 1e-5
+        for x, y in zip(_state(a), _state(g)):
+            assert rel_l2(y, x) < 1e-5
+    solo = _pn_member(ws[2])
+    b2 = Batch()
+    b2.add(solo)
+    b2.step(128)
+    b2.sync()
+    for x, y in zip(_state(solo), _state(inb[2])):
+        assert np.array_equal(x, y)
+
+
+def test_batch_refuses_the_estimated_interval_and_lanczos_forms():
+    from paper_1808_00270_gb300 import Batch, GLDError
+    from paper_1808_00270_gb300.binding import E_INVAL
+    w = _workload("pn_d", 128, 0.1, 200, 24)
+    for form in ("interval", "lanczos"):
+        g = _pn_member(w, strength=1.0)
+        if form == "interval":
+            g.set_pair_noise_on(8)
+        else:
+            g.set_pair_noise_krylov(1e-6, 16)
+        with pytest.raises(GLDError) as e:
+            Batch().add(g)
+        assert e.value.status == E_INVAL
