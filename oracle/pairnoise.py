@@ -28,9 +28,14 @@ Radial factors use max(r, r_c,min) and linear interpolation on r = k dr with
 the last value held (as the dissipative force of the oracle); pairs are those
 with r < r_c.
 
+With the window of the remark after Algorithm 1 (``random_force_window``),
+one window W_{n-H} .. W_{n+H} gives F at the times n .. n + rows - 1 through
+the whole inverse transform of hat F_w (its sine part too).
+
 Deliberate mistakes for the pin test (``variant``): 11 the sign of the pair
 blocks flipped; 12 the inverse transform scaled by 1 / m_max; 17 the radial
-factors read at the unclamped distance (r_c,min ignored).
+factors read at the unclamped distance (r_c,min ignored); 18 the sine part of
+the window's inverse transform with the wrong sign.
 """
 from __future__ import annotations
 
@@ -122,6 +127,35 @@ def sqrt_psd(Kh: np.ndarray, clamp: bool = False):
     if worst < -1e-12 and not clamp:
         raise ValueError(f"correlation matrix not positive semi-definite (eigenvalue {worst:.3e} of max)")
     return (U * np.sqrt(np.clip(lam, 0.0, None))) @ U.T, worst
+
+
+def random_force_window(terms, kT: float, dt: float, m_max: int, Wwin, rows: int, clamp: bool = False,
+                        variant: int = 0):
+    """F_{n+m} [rows, N, 3] for m = 0 .. rows - 1 from ONE window
+    Wwin[s + m_max - 1] = W_{n+s}: the time window of the remark after
+    Algorithm 1 (kernels held at R_n).  hat F_w = sqrt(hat K_w) hat W_w with
+    the complex transform hat W_w = sum_s W_{n+s} exp(-2 pi i w s / L) =
+    C_w - i S_w, and the whole inverse transform at the first `rows` times,
+    F_{n+m} = (1/L) sum_{w=-(m_max-1)}^{m_max-1} hat F_w exp(2 pi i w m / L)
+            = (X^c_0 + 2 sum_{w>=1} (X^c_w cos(2 pi w m / L) + X^s_w sin(2 pi w m / L))) / L,
+    X^c_w = sqrt(hat K_w) C_w, X^s_w = sqrt(hat K_w) S_w (hat K_{-w} = hat K_w
+    is real).  Row 0 is random_force's F_n.  variant 18 flips the sign of the
+    sine part (a time-reversed window)."""
+    L = 2 * m_max - 1
+    Wwin = np.asarray(Wwin, dtype=float)
+    n = Wwin.shape[1]
+    shifts = np.arange(-(m_max - 1), m_max)
+    m = np.arange(rows)
+    F = np.zeros((rows, 3 * n))
+    for w in range(m_max):
+        ph = 2.0 * np.pi * ((w * shifts) % L) / L
+        C = np.tensordot(np.cos(ph), Wwin, axes=1).reshape(3 * n)
+        S = np.tensordot(np.sin(ph), Wwin, axes=1).reshape(3 * n)
+        R, _ = sqrt_psd(transformed(terms, kT, dt, m_max, w), clamp)
+        th = 2.0 * np.pi * ((w * m) % L) / L
+        sgn = -1.0 if variant == 18 else 1.0
+        F += (1.0 if w == 0 else 2.0) * (np.outer(np.cos(th), R @ C) + sgn * np.outer(np.sin(th), R @ S))
+    return (F / L).reshape(rows, n, 3)
 
 
 def random_force(terms, kT: float, dt: float, m_max: int, Wwin, clamp: bool = False, variant: int = 0):

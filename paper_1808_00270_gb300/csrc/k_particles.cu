@@ -34,6 +34,7 @@ namespace {
 
 constexpr int kPairThreads = kBatchPairBlock;
 constexpr int kPairLanes = kBatchPairLanes;  // lanes per particle in the one-term pair kernel
+constexpr int kPairBatch = 4;                 // list entries per round of the one-term pair kernel
 constexpr int kCforceLanes = kBatchCforceLanes;  // lanes per particle in the F^C kernel
 constexpr int kCellThreads = kBatchCellChunk;
 constexpr int kThreads = kBatchPartBlock;
@@ -146,17 +147,18 @@ __device__ __forceinline__ void pair_force_integrate_body(const StepParams& P, C
             f0x = fmaf(-inst, ex, f0x); f0y = fmaf(-inst, ey, f0y); f0z = fmaf(-inst, ez, f0z);
             fhx = fmaf(-hist, ex, fhx); fhy = fmaf(-hist, ey, fhy); fhz = fmaf(-hist, ez, fhz);
         };
-        // lane lr takes the entries lr, lr + LANES, ...: four of them per
-        // round with all their loads in flight together
+        // lane lr takes the entries lr, lr + LANES, ...: kPairBatch of them
+        // per round with all their loads in flight together
+        constexpr int NB = kPairBatch;
         int base = lr;
-        for (; base + 3 * LANES < cnt; base += 4 * LANES) {
-            int j[4];
-            float4 pj[4], vj[4];
-            float qx[4], qy[4], qz[4];
+        for (; base + (NB - 1) * LANES < cnt; base += NB * LANES) {
+            int j[NB];
+            float4 pj[NB], vj[NB];
+            float qx[NB], qy[NB], qz[NB];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) j[u] = __ldg(nbr + (size_t)(base + u * LANES) * P.n_pad + id);
+            for (int u = 0; u < NB; ++u) j[u] = __ldg(nbr + (size_t)(base + u * LANES) * P.n_pad + id);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < NB; ++u) {
                 pj[u] = __ldg(pos + j[u]);
                 vj[u] = __ldg(vel + j[u]);
                 qx[u] = __ldg(pj0 + j[u]);
@@ -164,7 +166,7 @@ __device__ __forceinline__ void pair_force_integrate_body(const StepParams& P, C
                 qz[u] = __ldg(pj0 + 2 * np + j[u]);
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) term(j[u], pj[u], vj[u], qx[u], qy[u], qz[u]);
+            for (int u = 0; u < NB; ++u) term(j[u], pj[u], vj[u], qx[u], qy[u], qz[u]);
         }
         for (; base < cnt; base += LANES) {
             const int jd = __ldg(nbr + (size_t)base * P.n_pad + id);

@@ -828,6 +828,64 @@ def pin_pair_noise_covariance(variant=0):
     return bool(worst < 1e-10), f"sum_s B_s B_(s+m)^T vs K_m {worst:.1e}"
 
 
+def pin_pair_noise_window_self(variant=0):
+    """The time window after Algorithm 1 without pair kernels: row m of the
+    window's inverse transform is the circular moving average
+    sum_s A_s W_{n + ((m + s) wrapped into the window)} with the scalar
+    generator's taps A_s (Eq. noise_production, periodic over the 2 m_max - 1
+    points of Eq. FT), for every m of the window; row 0 is the per-step F_n."""
+    from oracle import pairnoise
+    M, dt, kT = 8, 0.02, 0.9
+    Ks = _pn_kernels(M, dt)[0]
+    rng = np.random.default_rng(13)
+    pos = rng.uniform(0, 6.0, (4, 3))
+    terms = pairnoise.matrix_terms(pos, 6.0, 2.0, 0.0, M, dt, Ks)
+    L, H = 2 * M - 1, M - 1
+    W = rng.normal(size=(L, 4, 3))
+    F = pairnoise.random_force_window(terms, kT, dt, M, W, L, variant=variant)
+    Kd = Ks * dt
+    Kd[0] *= 0.5
+    st, _, _, A, _ = oracle.noise_coefs(Kd, kT, dt)
+    worst = 0.0
+    for m in range(L):
+        want = sum(A[s + H] * W[(m + s + H) % L] for s in range(-H, H + 1))
+        worst = max(worst, np.abs(F[m] - want).max() / np.abs(want).max())
+    F0 = pairnoise.random_force(terms, kT, dt, M, W)
+    worst = max(worst, np.abs(F[0] - F0).max() / np.abs(F0).max())
+    return bool(st == 0 and worst < 1e-12), f"window rows vs circular moving average {worst:.1e}"
+
+
+def pin_pair_noise_window_covariance(variant=0):
+    """Within the window the generated forces have the covariance of Eq.
+    noise_ansatz exactly: with impulse responses B^m_s (F_{n+m} =
+    sum_s B^m_s W_{n+s}), sum_s B^m_s (B^m'_s)^T = K_{m-m'} for the 3N x 3N
+    correlation matrices of a 5-particle cluster with pair and
+    self-difference terms (the periodic images of the lag fall beyond
+    m_max for |m - m'| <= L - m_max)."""
+    from oracle import pairnoise
+    M, dt, kT = 6, 0.05, 1.1
+    Ks, g, f, dr = _pn_kernels(M, dt)
+    rng = np.random.default_rng(2)
+    pos = 3.0 + rng.uniform(0, 1.6, (5, 3))
+    terms = pairnoise.matrix_terms(pos, 8.0, 2.0, 0.3, M, dt, Ks, g, f, dr, gs=0.5 * g, fs=0.3 * f)
+    L, n3, rows = 2 * M - 1, 15, 2 * M - 1 - (M - 1)
+    B = np.zeros((rows, L, n3, n3))
+    for sh in range(L):
+        for J in range(n3):
+            Wwin = np.zeros((L, 5, 3))
+            Wwin[sh, J // 3, J % 3] = 1.0
+            B[:, sh, :, J] = pairnoise.random_force_window(terms, kT, dt, M, Wwin, rows,
+                                                           variant=variant).reshape(rows, n3)
+    scale = np.abs(pairnoise.correlation_matrix(terms, kT, dt, 0)).max()
+    worst = 0.0
+    for a in range(rows):
+        for b in range(rows):
+            Cab = sum(B[a, sh] @ B[b, sh].T for sh in range(L))
+            Kab = pairnoise.correlation_matrix(terms, kT, dt, abs(a - b)) if abs(a - b) < M else 0.0
+            worst = max(worst, np.abs(Cab - Kab).max() / scale)
+    return bool(worst < 1e-10), f"sum_s B^m_s B^m'_s^T vs K_(m-m') {worst:.1e}"
+
+
 ALL = {
     "philox_kat": pin_philox_kat,
     "gauss_moments": pin_gauss_moments,
@@ -853,4 +911,6 @@ ALL = {
     "pair_noise_covariance": pin_pair_noise_covariance,
     "perpendicular_decoupling": pin_perpendicular_decoupling,
     "rc_min_clamp": pin_rc_min_clamp,
+    "pair_noise_window_self": pin_pair_noise_window_self,
+    "pair_noise_window_covariance": pin_pair_noise_window_covariance,
 }

@@ -1,6 +1,6 @@
 """A pin set is only trusted if it fails for plausible mistakes: each of these
 oracle builds carries one planted error (OR_PLANT in oracle/gldref.c, or the
-``variant`` of oracle/pairnoise.py for 11, 12 and 17), and at least one pin must
+``variant`` of oracle/pairnoise.py for 11, 12, 17 and 18), and at least one pin must
 reject it.  The mistakes are planted on the CPU only."""
 import pytest
 
@@ -24,6 +24,7 @@ PLANTS = {
     15: "perpendicular factors read at the unclamped distance",
     16: "the clamped distance used for the unit vector e",
     17: "pair-noise radial factors read at the unclamped distance",
+    18: "the sine part of the window's inverse transform with the wrong sign",
 }
 
 
