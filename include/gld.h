@@ -352,6 +352,19 @@ gld_status gld_pair_noise_spectrum(gld_ctx* ctx, double* out);
  * in a batch); gld_profile_steps refuses it.  A new gld_set_kernels turns it
  * off.  Synchronizes. */
 gld_status gld_set_pair_noise_krylov(gld_ctx* ctx, double tol, int32_t kmax);
+/* gld_set_pair_noise_krylov with a choice of window: 0 as there (Algorithm 1
+ * every step); 1 the time window of the remark after Algorithm 1 -- with the
+ * kernels held at the configuration of a 64-step noise block's first step,
+ * one Lanczos iteration per frequency on both the cosine and the sine
+ * transform of that step's white-noise window gives hat F_w, and the whole
+ * inverse transform gives F at all 64 steps of the block:
+ *   F_{n0+m} = (X^c_0 + 2 sum_{w>=1} (X^c_w cos(2 pi w m / L) + X^s_w sin(2 pi w m / L))) / L.
+ * Within a block the forces have the covariance of Eq. noise_ansatz exactly
+ * (the periodic images of a lag below 64 fall beyond m_max); across blocks
+ * they come from different windows.  Twice the vectors of window 0, once per
+ * block instead of every step.  Needs 64-step noise blocks (GLD_E_INVAL
+ * otherwise); else as gld_set_pair_noise_krylov.  Synchronizes. */
+gld_status gld_set_pair_noise_lanczos(gld_ctx* ctx, double tol, int32_t kmax, int32_t window);
 
 /* Memory sums in auxiliary-variable form (App. C discusses auxiliary-variable
  * expansions as the alternative to a stored history).  When every kernel

@@ -247,6 +247,18 @@ class System:
         return pairnoise.random_force(terms, G["kT"], G["dt"], self.m_max, self.white_window(), clamp=clamp,
                                       variant=self._variant)
 
+    def pair_random_force_window(self, rows: int, clamp: bool = False) -> np.ndarray:
+        """F^R of the coming `rows` steps [rows, N, 3] from the one window of
+        the coming step with the kernels at the current configuration (the
+        time window of the remark after Algorithm 1; see pairnoise.py)."""
+        from . import pairnoise
+        k, G = self._kern, self._geom
+        terms = pairnoise.matrix_terms(self.get(POS), G["box"], G["rc"], G["rc_min"], self.m_max, G["dt"],
+                                       k["Ks"], k["g"], k["f"], k["dr"], k["gs"], k["fs"], k["discrete"],
+                                       variant=self._variant, fp=k["fp"], fsp=k["fsp"])
+        return pairnoise.random_force_window(terms, G["kT"], G["dt"], self.m_max, self.white_window(), rows,
+                                             clamp=clamp, variant=self._variant)
+
     def step_pair_noise(self, nsteps: int = 1, clamp: bool = False) -> None:
         """Steps with the pair-correlated random force instead of the
         self-kernel noise."""

@@ -103,6 +103,7 @@ def lib():
             "gld_set_pair_noise": (i32, [vp, i32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
             "gld_set_perpendicular": (i32, [vp, vp, vp]),
             "gld_set_pair_noise_krylov": (i32, [vp, C.c_double, i32]),
+            "gld_set_pair_noise_lanczos": (i32, [vp, C.c_double, i32, i32]),
             "gld_set_pair_noise_on": (i32, [vp, i32, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                             C.POINTER(C.c_double)]),
             "gld_pair_noise_spectrum": (i32, [vp, vp]),
@@ -159,7 +160,8 @@ def exported_symbols() -> list[str]:
             "gld_pair_correlation", "gld_set_memory_modes", "gld_set_conservative_table",
             "gld_set_kernels_table", "gld_separable_terms", "gld_set_pair_noise",
             "gld_set_perpendicular", "gld_pair_noise_filters", "gld_save_observables", "gld_load_observables",
-            "gld_set_pair_noise_krylov", "gld_set_pair_noise_on", "gld_pair_noise_spectrum",
+            "gld_set_pair_noise_krylov", "gld_set_pair_noise_lanczos", "gld_set_pair_noise_on",
+            "gld_pair_noise_spectrum",
             "gld_pair_noise_filters_on"]
 
 
@@ -387,6 +389,12 @@ class GLD:
         self._check(lib().gld_pair_noise_spectrum(self._h, _ptr(out)))
         return dict(ritz_min=float(out[0]), ritz_max=float(out[1]), krylov_dim=int(out[2]), lo=float(out[3]),
                     hi=float(out[4]))
+
+    def set_pair_noise_lanczos(self, tol: float = 1e-6, kmax: int = 32, window: int = 0):
+        """Pair-correlated noise by Algorithm 1: window 0 every step, window 1
+        one run per 64-step noise block giving all its rows (the time window
+        after Algorithm 1); tol <= 0 turns it off."""
+        self._check(lib().gld_set_pair_noise_lanczos(self._h, float(tol), int(kmax), int(window)))
 
     def set_pair_noise_krylov(self, tol: float = 1e-6, kmax: int = 32):
         """Pair-correlated noise by a Lanczos iteration per frequency

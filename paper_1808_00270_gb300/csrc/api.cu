@@ -328,7 +328,7 @@ void pn_release(gld_ctx* c)
 void kry_release(gld_ctx* c)
 {
     auto& K = c->kry;
-    for (float** p : {&K.V, &K.Y, &K.cf, &K.cosT}) {
+    for (float** p : {&K.V, &K.Y, &K.cf, &K.cosT, &K.wgt}) {
         dfree(c, *p);
         *p = nullptr;
     }
@@ -338,7 +338,7 @@ void kry_release(gld_ctx* c)
     }
     dfree(c, K.alive);
     K.alive = nullptr;
-    K.M = K.Mp = K.kmax = 0;
+    K.M = K.Mp = K.kmax = K.window = K.Mc = 0;
     K.last_iters = 0;
     c->P.pn_kry = 0;
 }
@@ -427,13 +427,20 @@ gld_status pair_noise_krylov(gld_ctx* c, cudaStream_t st)
     auto A = [&](int p) { return K.alpha + (size_t)p * Mp; };
     auto Bt = [&](int p) { return K.beta + (size_t)p * Mp; };
     GLD_CUDA(c, cudaMemsetAsync(K.alive, 1, sizeof(int) * Mp, st));  // nonzero: alive
-    GLD_CUDA(c, kry_ft(P, c->B.ctrl, c->W, K.cosT, M, Mp, R(0), st));
+    GLD_CUDA(c, kry_ft(P, c->B.ctrl, c->W, K.cosT, M, Mp, K.Mc, R(0), st));
     GLD_CUDA(c, kry_dot(P, R(0), R(0), Mp, K.part, Bt(0), 2, nullptr, K.alive, st));
+    // the columns iterated: the cosine transforms of w < M and, with the time
+    // window, the sine transforms of 1 <= w < M (columns Mc + w)
+    std::vector<int> cols;
+    for (int w = 0; w < M; ++w) cols.push_back(w);
+    if (K.window)
+        for (int w = 1; w < M; ++w) cols.push_back(K.Mc + w);
+    const int NC = (int)cols.size();
     int k = 0;  // iterations done
     const int chunk = 4;
     std::vector<double> ha, hb;
-    std::vector<std::vector<double>> cfin(M);
-    std::vector<int> done(M, 0), kw(M, 0);
+    std::vector<std::vector<double>> cfin(NC);
+    std::vector<int> done(NC, 0), kw(NC, 0);
     int ndone = 0;
     double worst_change = 0.0, worst_neg = 0.0;
     while (true) {
@@ -447,8 +454,9 @@ gld_status pair_noise_krylov(gld_ctx* c, cudaStream_t st)
         GLD_CUDA(c, cudaMemcpyAsync(ha.data(), K.alpha, sizeof(double) * ha.size(), cudaMemcpyDeviceToHost, st));
         GLD_CUDA(c, cudaMemcpyAsync(hb.data(), K.beta, sizeof(double) * hb.size(), cudaMemcpyDeviceToHost, st));
         GLD_TRY(sync_and_check(c));
-        for (int w = 0; w < M; ++w) {
-            if (done[w]) continue;
+        for (int ci = 0; ci < NC; ++ci) {
+            if (done[ci]) continue;
+            const int w = cols[ci];
             // the Krylov space of w ends at the first vanished beta (exact result)
             int j = 1;
             std::vector<double> al(k), be(std::max(k - 1, 0));
@@ -483,18 +491,18 @@ gld_status pair_noise_krylov(gld_ctx* c, cudaStream_t st)
                 change = exhausted ? 0.0 : 1.0;
             }
             if (exhausted || change <= K.tol) {
-                done[w] = 1;
+                done[ci] = 1;
                 ++ndone;
-                cfin[w] = cj;
-                kw[w] = j;
+                cfin[ci] = cj;
+                kw[ci] = j;
                 worst_change = std::max(worst_change, exhausted ? 0.0 : change);
             } else if (k >= K.kmax) {
-                cfin[w] = cj;
-                kw[w] = j;
+                cfin[ci] = cj;
+                kw[ci] = j;
                 worst_change = std::max(worst_change, change);
             }
         }
-        if (ndone == M || k >= K.kmax) break;
+        if (ndone == NC || k >= K.kmax) break;
     }
     K.last_iters = *std::max_element(kw.begin(), kw.end());  // the largest Krylov dimension used
     K.last_change = worst_change;
@@ -503,18 +511,23 @@ gld_status pair_noise_krylov(gld_ctx* c, cudaStream_t st)
         if (c->latched == GLD_OK) c->latched = GLD_E_NOT_PSD;
         return GLD_E_NOT_PSD;
     }
-    if (ndone < M)
+    if (ndone < NC)
         return fail(c, GLD_E_TIMEOUT, "pair noise (Lanczos): no convergence within the iteration limit");
     // x_w = sum_p c_p v_p = sum_p (c_p / beta_p) R_p
-    std::vector<float> cf((size_t)M * k, 0.f);
-    for (int w = 0; w < M; ++w)
-        for (int p = 0; p < kw[w]; ++p) {
+    std::vector<float> cf((size_t)Mp * k, 0.f);
+    for (int ci = 0; ci < NC; ++ci)
+        for (int p = 0; p < kw[ci]; ++p) {
+            const int w = cols[ci];
             const double bp = hb[(size_t)p * Mp + w];
-            cf[(size_t)w * k + p] = bp > 0.0 ? (float)(cfin[w][p] / bp) : 0.f;
+            cf[(size_t)w * k + p] = bp > 0.0 ? (float)(cfin[ci][p] / bp) : 0.f;
         }
     GLD_CUDA(c, cudaMemcpyAsync(K.cf, cf.data(), sizeof(float) * cf.size(), cudaMemcpyHostToDevice, st));
-    const long long row = c->host_step - c->block_start;
-    GLD_CUDA(c, kry_combine(P, K.V, K.cf, k, M, Mp, c->B.frblock + (size_t)row * 3 * P.n_pad, st));
+    if (K.window) {  // every row of the block from the one window
+        GLD_CUDA(c, kry_rows(P, K.V, K.cf, k, Mp, K.wgt, K.Y, c->B.frblock, st));
+    } else {
+        const long long row = c->host_step - c->block_start;
+        GLD_CUDA(c, kry_combine(P, K.V, K.cf, k, M, Mp, c->B.frblock + (size_t)row * 3 * P.n_pad, st));
+    }
     GLD_CUDA(c, cudaStreamSynchronize(st));  // cf is reused by the next step
     return GLD_OK;
 }
@@ -994,8 +1007,9 @@ gld_status gld_step(gld_ctx* c, int64_t nsteps)
             c->block_start = c->host_step;
             c->noise_end = c->host_step + T;
             c->noise_valid = true;
+            if (c->P.pn_kry && c->kry.window) GLD_TRY(pair_noise_krylov(c, c->st));  // the block's rows at once
         }
-        if (c->P.pn_kry) GLD_TRY(pair_noise_krylov(c, c->st));
+        if (c->P.pn_kry && !c->kry.window) GLD_TRY(pair_noise_krylov(c, c->st));
         GLD_CUDA(c, launch_one_step(c, c->st));
         c->conv_valid_step = -1;
         c->last_fr_row = c->host_step - c->block_start;
@@ -1741,47 +1755,70 @@ gld_status gld_pair_noise_spectrum(gld_ctx* c, double* out)
     return GLD_OK;
 }
 
-gld_status gld_set_pair_noise_krylov(gld_ctx* c, double tol, int32_t kmax)
+gld_status gld_set_pair_noise_lanczos(gld_ctx* c, double tol, int32_t kmax, int32_t window)
 {
     if (!c) return GLD_E_INVAL;
     StepParams& P = c->P;
-    if (tol > 0 && !c->have_kernels) return fail(c, GLD_E_STATE, "gld_set_pair_noise_krylov: set the kernels first");
-    if (tol > 0 && (kmax < 2 || kmax > 64 || !(tol < 1.0)))
-        return fail(c, GLD_E_INVAL, "gld_set_pair_noise_krylov: need 0 < tol < 1 and 2 <= kmax <= 64");
+    if (tol > 0 && !c->have_kernels) return fail(c, GLD_E_STATE, "gld_set_pair_noise_lanczos: set the kernels first");
+    if (tol > 0 && (kmax < 2 || kmax > 64 || !(tol < 1.0) || (window != 0 && window != 1)))
+        return fail(c, GLD_E_INVAL, "gld_set_pair_noise_lanczos: need 0 < tol < 1, 2 <= kmax <= 64, window 0 or 1");
     GLD_TRY(sync_and_check(c));
     kry_release(c);
     invalidate_graph(c);
     if (!(tol > 0)) return sync_and_check(c);
+    if (window && P.T != kMaxNoiseBlock)
+        return fail(c, GLD_E_INVAL, "gld_set_pair_noise_lanczos: the time window needs 64-step noise blocks");
     pn_release(c);  // the Chebyshev form is replaced
+    GLD_TRY(invalidate_noise(c));  // the current block's rows are regenerated
     auto& K = c->kry;
-    const int M = P.m_max, Mp = (M + 31) & ~31, nacc = P.nacc;
+    const int M = P.m_max, Mc = (M + 31) & ~31, Mp = window ? 2 * Mc : Mc, nacc = P.nacc;
     const long long L = 2LL * M - 1;
     if (!kry_fits(P, Mp))
-        return fail(c, GLD_E_INVAL, "gld_set_pair_noise_krylov: m_max too large for the transform's shared memory");
+        return fail(c, GLD_E_INVAL, "gld_set_pair_noise_lanczos: m_max too large for the transform's shared memory");
+    auto freq = [&](int col) { return col < Mc ? col : col - Mc; };  // the frequency of a column
+    auto phase = [&](long long a) { return 2.0 * M_PI * (double)(a % L) / (double)L; };
     // transforms (Eq. FT) of kT a_m / dt times each discrete time factor:
-    // a_w (self), g_qw (pair terms), gs_qw (self-difference terms), FP64
+    // a_w (self), g_qw (pair terms), gs_qw (self-difference terms), FP64; the
+    // sine columns take their frequency's values
     std::vector<double> wc((size_t)nacc * Mp, 0.0);
     const double f0 = c->prm.kT / c->prm.dt;
     for (int a = 0; a < nacc; ++a) {
         const double* wt = c->wts.data() + (size_t)a * M;
         for (int w = 0; w < M; ++w) {
             double v = 2.0 * wt[0];
-            for (int m = 1; m < M; ++m) v += 2.0 * wt[m] * std::cos(2.0 * M_PI * (double)(((long long)w * m) % L) / (double)L);
+            for (int m = 1; m < M; ++m) v += 2.0 * wt[m] * std::cos(phase((long long)w * m));
             wc[(size_t)a * Mp + w] = f0 * v;
+            if (window) wc[(size_t)a * Mp + Mc + w] = f0 * v;
         }
     }
-    // cos(2 pi w s / L) for s = 0 .. m_max - 1 (the transform of the window),
-    // columns w >= m_max zero
+    // cos (sin) of 2 pi w s / L for s = 0 .. m_max - 1: the transforms of the
+    // window; columns of frequencies >= m_max zero
     std::vector<float> cosT((size_t)M * Mp, 0.f);
     for (int sg = 0; sg < M; ++sg)
-        for (int w = 0; w < M; ++w)
-            cosT[(size_t)sg * Mp + w] = (float)std::cos(2.0 * M_PI * (double)(((long long)w * sg) % L) / (double)L);
+        for (int col = 0; col < Mp; ++col)
+            if (freq(col) < M)
+                cosT[(size_t)sg * Mp + col] = (float)(col < Mc ? std::cos(phase((long long)freq(col) * sg))
+                                                               : std::sin(phase((long long)freq(col) * sg)));
+    // the window's row weights: (1 or 2) cos(2 pi w m / L) and 2 sin(2 pi w m / L)
+    std::vector<float> wgt;
+    if (window) {
+        wgt.assign((size_t)Mp * kMaxNoiseBlock, 0.f);
+        for (int col = 0; col < Mp; ++col) {
+            const int w = freq(col);
+            if (w >= M || (col >= Mc && w == 0)) continue;
+            for (int m = 0; m < kMaxNoiseBlock; ++m)
+                wgt[(size_t)col * kMaxNoiseBlock + m] =
+                    (float)(col < Mc ? (w == 0 ? 1.0 : 2.0) * std::cos(phase((long long)w * m))
+                                     : 2.0 * std::sin(phase((long long)w * m)));
+        }
+    }
     const size_t vs = 3 * (size_t)P.n_pad * Mp;
     bool ok = true;
     K.V = alloc_n<float>(c, (size_t)(kmax + 1) * vs, ok);
     K.Y = alloc_n<float>(c, vs, ok);
-    K.cf = alloc_n<float>(c, (size_t)M * (kmax + 1), ok);
+    K.cf = alloc_n<float>(c, (size_t)Mp * (kmax + 1), ok);
     K.cosT = alloc_n<float>(c, cosT.size(), ok);
+    if (window) K.wgt = alloc_n<float>(c, wgt.size(), ok);
     K.part = alloc_n<double>(c, (size_t)kry_part_blocks(P) * Mp, ok);
     K.alpha = alloc_n<double>(c, (size_t)(kmax + 1) * Mp, ok);
     K.beta = alloc_n<double>(c, (size_t)(kmax + 1) * Mp, ok);
@@ -1789,18 +1826,27 @@ gld_status gld_set_pair_noise_krylov(gld_ctx* c, double tol, int32_t kmax)
     K.alive = alloc_n<int>(c, Mp, ok);
     if (!ok) {
         kry_release(c);
-        return fail(c, GLD_E_NOMEM, "gld_set_pair_noise_krylov: allocation failed");
+        return fail(c, GLD_E_NOMEM, "gld_set_pair_noise_lanczos: allocation failed");
     }
     GLD_CUDA(c, cudaMemcpyAsync(K.wc, wc.data(), sizeof(double) * wc.size(), cudaMemcpyHostToDevice, c->st));
     GLD_CUDA(c, cudaMemcpyAsync(K.cosT, cosT.data(), sizeof(float) * cosT.size(), cudaMemcpyHostToDevice, c->st));
+    if (window)
+        GLD_CUDA(c, cudaMemcpyAsync(K.wgt, wgt.data(), sizeof(float) * wgt.size(), cudaMemcpyHostToDevice, c->st));
     K.M = M;
     K.Mp = Mp;
+    K.Mc = Mc;
+    K.window = window;
     K.kmax = kmax;
     K.tol = tol;
     K.last_iters = 0;
     K.last_change = 0.0;
     P.pn_kry = 1;
     return sync_and_check(c);
+}
+
+gld_status gld_set_pair_noise_krylov(gld_ctx* c, double tol, int32_t kmax)
+{
+    return gld_set_pair_noise_lanczos(c, tol, kmax, 0);
 }
 
 gld_status gld_set_memory_modes(gld_ctx* c, int32_t nmodes, const double* rate, const double* omega)

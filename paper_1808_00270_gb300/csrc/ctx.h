@@ -79,7 +79,8 @@ struct gld_ctx {
     struct Krylov {
         int M = 0, Mp = 0, kmax = 0;
         double tol = 0.0;
-        float *V = nullptr, *Y = nullptr, *cf = nullptr, *cosT = nullptr;
+        int window = 0, Mc = 0;  // the time window (one run per noise block), columns of the cosine part
+        float *V = nullptr, *Y = nullptr, *cf = nullptr, *cosT = nullptr, *wgt = nullptr;
         double *part = nullptr, *alpha = nullptr, *beta = nullptr, *wc = nullptr;
         int* alive = nullptr;
         int last_iters = 0;

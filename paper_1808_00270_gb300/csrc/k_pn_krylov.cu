@@ -42,12 +42,17 @@ constexpr int kChunk = 16;      // FP32 terms summed before an FP64 addition
 // table (cosT[s][w], s = 0..H) are staged in shared memory, where all lanes of
 // a warp read the same row (a broadcast).  The frequency groups of one entry
 // chunk are adjacent in the grid, so they share the W window through L2.
+// With the time window (Mc < Mp): columns Mc + w hold the sine transform
+// S_w = sum_{s=1}^{H} (W_{n+s} - W_{n-s}) sin(2 pi w s / L) (no s = 0 term),
+// their table columns the sines.
 __global__ void __launch_bounds__(kFtThreads)
     pnk_ft(const StepParams P, const Ctrl* __restrict__ ctrl, const float* __restrict__ W,
-           const float* __restrict__ cosT, int M, int Mp, float* __restrict__ V0)
+           const float* __restrict__ cosT, int M, int Mp, int Mc, float* __restrict__ V0)
 {
     extern __shared__ float4 cs4[];  // [H + 1][8]
     const int H = P.H, g = blockIdx.x;
+    const bool sine = g * 32 >= Mc;  // uniform over the block
+    const float sg = sine ? -1.f : 1.f;
     for (int e = threadIdx.x; e < (H + 1) * 8; e += blockDim.x)
         cs4[e] = reinterpret_cast<const float4*>(cosT + (size_t)(e >> 3) * Mp + g * 32)[e & 7];
     __syncthreads();
@@ -60,7 +65,7 @@ __global__ void __launch_bounds__(kFtThreads)
     float acc[32];
     const float w0 = __ldg(W + (size_t)s0 * np3 + I);
 #pragma unroll
-    for (int j = 0; j < 32; ++j) acc[j] = w0;  // s = 0: cos 0 = 1
+    for (int j = 0; j < 32; ++j) acc[j] = sine ? 0.f : w0;  // s = 0: cos 0 = 1, sin 0 = 0
     long long sp = s0 + 1 == lw ? 0 : s0 + 1, sm = s0 == 0 ? lw - 1 : s0 - 1;
     auto term = [&](float p, int s) {
         const float4* c = cs4 + s * 8;
@@ -84,10 +89,10 @@ __global__ void __launch_bounds__(kFtThreads)
             sm = sm == 0 ? lw - 1 : sm - 1;
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) term(a[u] + b[u], s + u);
+        for (int u = 0; u < 4; ++u) term(fmaf(sg, b[u], a[u]), s + u);
     }
     for (; s <= H; ++s) {
-        term(__ldg(W + (size_t)sp * np3 + I) + __ldg(W + (size_t)sm * np3 + I), s);
+        term(fmaf(sg, __ldg(W + (size_t)sm * np3 + I), __ldg(W + (size_t)sp * np3 + I)), s);
         sp = sp + 1 == lw ? 0 : sp + 1;
         sm = sm == 0 ? lw - 1 : sm - 1;
     }
@@ -96,7 +101,10 @@ __global__ void __launch_bounds__(kFtThreads)
     for (int k = 0; k < 8; ++k) {
         float v[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) v[e] = g * 32 + 4 * k + e < M ? acc[4 * k + e] : 0.f;  // padding frequencies
+        for (int e = 0; e < 4; ++e) {
+            const int col = g * 32 + 4 * k + e;
+            v[e] = (sine ? col - Mc : col) < M ? acc[4 * k + e] : 0.f;  // padding frequencies
+        }
         out[k] = make_float4(v[0], v[1], v[2], v[3]);
     }
 }
@@ -377,6 +385,69 @@ __global__ void __launch_bounds__(32 * kKryWarps)
     if (lane == 0) out[I] = acc * inv_L;
 }
 
+// Y[I][c] = sum_p cf[c][p] R_p[I][c] (cf includes 1 / beta_p): warps over
+// entries, lanes over columns, four vectors' loads in flight, in order.
+__global__ void __launch_bounds__(32 * kKryWarps)
+    pnk_combine_y(const float* __restrict__ V, const float* __restrict__ cf, int kp, int Mp, long long np3,
+                  float* __restrict__ Y)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.y * 32 + lane;
+    const size_t stride = (size_t)np3 * Mp;
+    for (long long I = (long long)blockIdx.x * kKryWarps + warp; I < np3; I += (long long)gridDim.x * kKryWarps) {
+        float x = 0.f;
+        int p = 0;
+        for (; p + 4 <= kp; p += 4) {
+            float v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = V[(p + u) * stride + (size_t)I * Mp + c];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x = fmaf(cf[(size_t)c * kp + p + u], v[u], x);
+        }
+        for (; p < kp; ++p) x = fmaf(cf[(size_t)c * kp + p], V[p * stride + (size_t)I * Mp + c], x);
+        Y[(size_t)I * Mp + c] = x;
+    }
+}
+
+constexpr int kRowsChunk = 64;  // columns of the row weights staged at a time
+
+// out[m][I] = inv_L sum_c wgt[c][m] Y[I][c] for the T rows m of a block: one
+// entry per thread with T accumulators; the weights of kRowsChunk columns at a
+// time in shared memory (all lanes read the same column: a broadcast).
+__global__ void __launch_bounds__(256)
+    pnk_rows(const float* __restrict__ Y, const float* __restrict__ wgt, int ncol, int Mp, long long np3,
+             float inv_L, float* __restrict__ out)
+{
+    constexpr int T = kMaxNoiseBlock;
+    __shared__ float4 ws4[kRowsChunk][T / 4];
+    const long long I = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    float acc[T];
+#pragma unroll
+    for (int m = 0; m < T; ++m) acc[m] = 0.f;
+    for (int c0 = 0; c0 < ncol; c0 += kRowsChunk) {
+        const int nc = min(kRowsChunk, ncol - c0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < nc * (T / 4); e += blockDim.x)
+            ws4[e / (T / 4)][e % (T / 4)] = reinterpret_cast<const float4*>(wgt + (size_t)(c0 + e / (T / 4)) * T)[e % (T / 4)];
+        __syncthreads();
+        if (I < np3)
+            for (int c = 0; c < nc; ++c) {
+                const float y = Y[(size_t)I * Mp + c0 + c];
+#pragma unroll
+                for (int k = 0; k < T / 4; ++k) {
+                    const float4 w = ws4[c][k];
+                    acc[4 * k] = fmaf(w.x, y, acc[4 * k]);
+                    acc[4 * k + 1] = fmaf(w.y, y, acc[4 * k + 1]);
+                    acc[4 * k + 2] = fmaf(w.z, y, acc[4 * k + 2]);
+                    acc[4 * k + 3] = fmaf(w.w, y, acc[4 * k + 3]);
+                }
+            }
+    }
+    if (I < np3)
+#pragma unroll
+        for (int m = 0; m < T; ++m) out[(size_t)m * np3 + I] = acc[m] * inv_L;
+}
+
 unsigned elem_blocks(long long np3) { return (unsigned)std::min<long long>((np3 + kKryWarps - 1) / kKryWarps, 1024); }
 unsigned sweep_blocks(int n) { return (unsigned)std::min<long long>((n + kKryWarps - 1) / kKryWarps, 1024); }
 
@@ -403,15 +474,27 @@ int kry_part_blocks(const StepParams& P)
     return (int)std::max(elem_blocks(3LL * P.n_pad), sweep_blocks(P.n));
 }
 
-cudaError_t kry_ft(const StepParams& P, const Ctrl* ctrl, const float* W, const float* cosT, int M, int Mp, float* V0,
-                   cudaStream_t st)
+cudaError_t kry_ft(const StepParams& P, const Ctrl* ctrl, const float* W, const float* cosT, int M, int Mp, int Mc,
+                   float* V0, cudaStream_t st)
 {
     const long long np3 = 3LL * P.n_pad;
     const dim3 g((unsigned)(Mp / 32), (unsigned)((np3 + kFtThreads - 1) / kFtThreads));
     const size_t smem = (size_t)(P.H + 1) * 8 * sizeof(float4);
     cudaError_t e = set_smem((const void*)pnk_ft, smem);
     if (e != cudaSuccess) return e;
-    pnk_ft<<<g, kFtThreads, smem, st>>>(P, ctrl, W, cosT, M, Mp, V0);
+    pnk_ft<<<g, kFtThreads, smem, st>>>(P, ctrl, W, cosT, M, Mp, Mc, V0);
+    return cudaGetLastError();
+}
+
+cudaError_t kry_rows(const StepParams& P, const float* V, const float* cf, int kp, int Mp, const float* wgt, float* Y,
+                     float* out, cudaStream_t st)
+{
+    if (P.T != kMaxNoiseBlock) return cudaErrorInvalidValue;
+    const long long np3 = 3LL * P.n_pad;
+    pnk_combine_y<<<dim3(elem_blocks(np3), (unsigned)(Mp / 32)), 32 * kKryWarps, 0, st>>>(V, cf, kp, Mp, np3, Y);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    pnk_rows<<<(unsigned)((np3 + 255) / 256), 256, 0, st>>>(Y, wgt, Mp, Mp, np3, 1.0f / (float)(2 * P.H + 1), out);
     return cudaGetLastError();
 }
 

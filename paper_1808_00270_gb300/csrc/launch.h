@@ -91,7 +91,7 @@ int pn_spectrum_blocks(const StepParams& P);
 // (frequency fastest), Lanczos vectors unnormalised (R_k, v_k = R_k / beta_k).
 // kry_ft: the transformed white-noise window of step ctrl->step into V0
 // (cosT[s][w] = cos(2 pi w s / (2 m_max - 1)), s < m_max, zero columns for
-// w >= M); kry_dot: per-frequency a.b folded into out (mode 0), or the
+// w >= M; with the time window, columns Mc + w the sine transform); kry_dot: per-frequency a.b folded into out (mode 0), or the
 // square roots (2; 1 also marks exhausted Krylov spaces in alive, relative
 // to ref); kry_matvec: Z = hat K_w R_k / beta_k for every w (wc: a_w, g_qw,
 // gs_qw rows) and alpha_k; kry_resid: R_{k+1} = Z - alpha_k v_k - beta_k
@@ -100,8 +100,12 @@ int pn_spectrum_blocks(const StepParams& P);
 // doubles.  kry_fits: the transform's and the sweep's shared memory fit.
 bool kry_fits(const StepParams& P, int Mp);
 int kry_part_blocks(const StepParams& P);
-cudaError_t kry_ft(const StepParams& P, const Ctrl* ctrl, const float* W, const float* cosT, int M, int Mp, float* V0,
-                   cudaStream_t st);
+cudaError_t kry_ft(const StepParams& P, const Ctrl* ctrl, const float* W, const float* cosT, int M, int Mp, int Mc,
+                   float* V0, cudaStream_t st);
+// The time window: out[m][I] (m < 64, the block's rows) = (1/L) sum_c
+// wgt[c][m] sum_p cf[c][p] R_p[I][c]; Y is scratch [3 n_pad][Mp].
+cudaError_t kry_rows(const StepParams& P, const float* V, const float* cf, int kp, int Mp, const float* wgt, float* Y,
+                     float* out, cudaStream_t st);
 cudaError_t kry_fold(const double* part, int nblk, int Mp, double* out, int mode, const double* ref, int* alive,
                      cudaStream_t st);
 cudaError_t kry_dot(const StepParams& P, const float* a, const float* b, int Mp, double* part, double* out, int mode,

@@ -171,3 +171,44 @@ def test_krylov_arguments_and_exclusions():
     gpu.set_pair_noise_krylov(0.0, 16)  # off: back to the self-kernel noise
     gpu.step(64)
     assert gpu.diag()["krylov_iterations"] == 0
+
+
+@pytest.mark.parametrize("form", ["unscaled", "general"])
+def test_krylov_window_matches_dense_square_roots(form):
+    """The time window after Algorithm 1: at the start of a 64-step noise
+    block one Lanczos run per frequency on the cosine and sine transforms of
+    the window gives every row of the block; each step's F^R within 1e-5 of
+    the oracle's window rows (dense square roots, kernels at the block's
+    first configuration), for the unscaled workload kernel and for a
+    self-difference term with perpendicular factors."""
+    from paper_1808_00270_gb300 import ARR_FR
+    w = _workload(seed=35)
+    gpu = _gpu(w, form)
+    gpu.set_pair_noise_lanczos(TOL, KMAX, window=1)
+    gpu.step(64)
+    ref = _oracle_from(w, gpu, form)
+    want = ref.pair_random_force_window(64)
+    worst = 0.0
+    for m in range(64):
+        gpu.step(1)
+        worst = max(worst, rel_l2(gpu.get(ARR_FR), want[m]))
+    its = gpu.diag()["krylov_iterations"]
+    print(f"window, {form}: worst row F^R {worst:.2e}, Krylov dimension {its}")
+    assert worst < 1e-5 and 1 <= its <= KMAX
+    gpu.close()
+
+
+def test_krylov_window_arguments():
+    from paper_1808_00270_gb300 import GLDError
+    from paper_1808_00270_gb300.binding import E_INVAL
+    w = _workload()
+    gpu = _gpu(w, "unscaled")
+    with pytest.raises(GLDError) as e:
+        gpu.set_pair_noise_lanczos(1e-6, 16, window=2)
+    assert e.value.status == E_INVAL
+    gpu.set_pair_noise_lanczos(1e-6, 16, window=1)
+    gpu.step(3)  # a block started: its rows came from one run
+    assert gpu.diag()["krylov_iterations"] >= 1
+    gpu.set_pair_noise_lanczos(0.0, 16)  # off
+    gpu.step(64)
+    assert gpu.diag()["krylov_iterations"] == 0
