@@ -62,6 +62,10 @@ def parse():
                     help="pair-correlated random force with a Chebyshev form of this degree on an interval of the "
                          "pair matrix's spectrum (estimated by a Lanczos run, checked at every noise block); the "
                          "workload's full-strength pair kernel")
+    ap.add_argument("--pair-noise-lanczos", type=int, default=-1, choices=[-1, 0, 1],
+                    help="pair-correlated random force by Algorithm 1 (a Lanczos iteration per frequency, tol 1e-6, "
+                         "at most 24 vectors; eager steps): 0 every step, 1 one run per 64-step block over the time "
+                         "window; the workload's full-strength pair kernel")
     ap.add_argument("--hist", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--kahan", action="store_true")
     ap.add_argument("--reference-seconds", type=float, default=120.0)
@@ -427,6 +431,9 @@ def main():
         cfg["memory"] = "auxiliary-variable modes (O(1) per particle-step in m_max)"
     if args.pair_noise > 0:
         cfg["pair_noise"] = {"degree": args.pair_noise, "pair_kernel_scale": 1.0}
+    if args.pair_noise_lanczos >= 0:
+        cfg["pair_noise"] = {"lanczos_window": args.pair_noise_lanczos, "tol": 1e-6, "kmax": 24,
+                             "pair_kernel_scale": 1.0}
     cfg.update({"global_batch": w.n * world, "parallelism": f"replicas{world}",
                 "l2": "inputs larger than L2: 1.26 GB FP32 history ring streamed every step"})
 
@@ -472,6 +479,8 @@ def main():
         lo, hi, cheb = sim.set_pair_noise_on(args.pair_noise)
         cfg["pair_noise"].update({"interval": [lo, hi], "interpolation_error": cheb,
                                   "interval_estimated_at_step": 64})
+    if args.pair_noise_lanczos >= 0:
+        sim.set_pair_noise_lanczos(1e-6, 24, window=args.pair_noise_lanczos)
     T = 64
     # warm-up: at least W steps and until the VACF runs with every origin in
     # flight (burn-in + vacf_len steps), so the clock sees its full cost; then
@@ -507,7 +516,13 @@ def main():
     value = replica_value(w.n, K, world, ms)
     blocks = (K + T - 1) // T
 
-    # per-kernel device time with CUDA events on the same stream
+    # per-kernel device time with CUDA events on the same stream (the Lanczos
+    # forms decide on the host between launches: profiled without them)
+    if args.pair_noise_lanczos >= 0:
+        kdim = sim.diag()["krylov_iterations"]
+        sim.set_pair_noise_lanczos(0.0)
+        cfg["pair_noise"]["krylov_dimension"] = kdim
+        cfg["pair_noise"]["kernel_profile"] = "without the pair noise"
     prof = sim.profile_steps(args.profile_steps)
     h_ms, h_n = prof["hist_conv"]
     nacc = 2
@@ -545,6 +560,10 @@ def main():
         launches += K
     if args.pair_noise > 0:  # Clenshaw sweeps per step; filters and the Lanczos check per block
         launches += args.pair_noise * (K + T_blocks) + (2 + 2 * 32) * T_blocks
+    if args.pair_noise_lanczos >= 0:  # eager steps; per run: transform, norm, 4 launches per iteration, output
+        iters = 4 * ((cfg["pair_noise"]["krylov_dimension"] + 3) // 4)
+        runs = T_blocks if args.pair_noise_lanczos == 1 else K
+        launches = K * 7 + 2 * T_blocks + runs * (3 + 4 * iters + (2 if args.pair_noise_lanczos == 1 else 1))
     e2e = None
     if not args.no_e2e:
         torch.cuda.synchronize()
@@ -558,6 +577,8 @@ def main():
         e2e_pn = None
         if args.pair_noise > 0:  # here on the unrelaxed start: a wider interval
             e2e_pn = e.set_pair_noise_on(args.pair_noise)
+        if args.pair_noise_lanczos >= 0:
+            e.set_pair_noise_lanczos(1e-6, 24, window=args.pair_noise_lanczos)
         e.step(K)
         cv, _ = e.vacf()
         p_out, v_out = e.get_state()
