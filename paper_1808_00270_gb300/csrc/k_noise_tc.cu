@@ -189,6 +189,17 @@ __device__ __forceinline__ void split_f16(float v, uint32_t& hi, uint32_t& lo)
     lo = __half_as_ushort(__float2half_rn((v - __half2float(h)) * 2048.0f));
 }
 
+// The same for two values at once with packed conversions: v0 in the low
+// halves (bit for bit split_f16 of each).
+__device__ __forceinline__ void split2_f16(float v0, float v1, uint32_t& hi, uint32_t& lo)
+{
+    const __half2 h = __floats2half2_rn(v0, v1);
+    const float2 f = __half22float2(h);
+    const __half2 l = __floats2half2_rn((v0 - f.x) * 2048.0f, (v1 - f.y) * 2048.0f);
+    hi = (uint32_t)__half_as_ushort(__low2half(h)) | ((uint32_t)__half_as_ushort(__high2half(h)) << 16);
+    lo = (uint32_t)__half_as_ushort(__low2half(l)) | ((uint32_t)__half_as_ushort(__high2half(l)) << 16);
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
 {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
@@ -387,14 +398,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) fir_tc(const __grid_constant__ 
                 const int k = kTcChunk * c + r;
                 const float v0 = (k >= a && k < a + nk) ? sp[r * 128] : 0.f;
                 const float v1 = (k + 1 >= a && k + 1 < a + nk) ? sp[(r + 1) * 128] : 0.f;
-                uint32_t h0, l0, h1, l1;
-                split_f16(v0, h0, l0);
-                split_f16(v1, h1, l1);
-                hv[r >> 1] = h0 | (h1 << 16);
-                lv[r >> 1] = l0 | (l1 << 16);
+                split2_f16(v0, v1, hv[r >> 1], lv[r >> 1]);
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);  // the stage may be loaded again
+            __syncwarp();  // converged for the aligned TMEM stores
             const uint32_t ta = tm + lane_base + kTcAcol + 32u * (uint32_t)b;
             tmem_st16(ta, hv);
             tmem_st16(ta + 16u, lv);
