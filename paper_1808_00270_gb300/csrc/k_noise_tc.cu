@@ -393,12 +393,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) fir_tc(const __grid_constant__ 
             if (!__all_sync(0xffffffffu, okw)) break;  // the same decision in every lane
             uint32_t hv[16], lv[16];  // two FP16 per column, the earlier row in the low half
             const float* sp = stage + (size_t)s * kTcStageFloats + ct;
+            const int k0 = kTcChunk * c;
+            if (k0 >= a && k0 + kTcChunk <= a + nk) {  // (uniform) a chunk inside the window
 #pragma unroll
-            for (int r = 0; r < 32; r += 2) {
-                const int k = kTcChunk * c + r;
-                const float v0 = (k >= a && k < a + nk) ? sp[r * 128] : 0.f;
-                const float v1 = (k + 1 >= a && k + 1 < a + nk) ? sp[(r + 1) * 128] : 0.f;
-                split2_f16(v0, v1, hv[r >> 1], lv[r >> 1]);
+                for (int r = 0; r < 32; r += 2) split2_f16(sp[r * 128], sp[(r + 1) * 128], hv[r >> 1], lv[r >> 1]);
+            } else {  // rows outside the window are zero
+#pragma unroll
+                for (int r = 0; r < 32; r += 2) {
+                    const int k = k0 + r;
+                    const float v0 = (k >= a && k < a + nk) ? sp[r * 128] : 0.f;
+                    const float v1 = (k + 1 >= a && k + 1 < a + nk) ? sp[(r + 1) * 128] : 0.f;
+                    split2_f16(v0, v1, hv[r >> 1], lv[r >> 1]);
+                }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);  // the stage may be loaded again
@@ -425,15 +431,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) fir_tc(const __grid_constant__ 
             if (!__all_sync(0xffffffffu, okw)) break;
             tc_fence_after();
 #pragma unroll
-            for (int part = 0; part < 4; ++part) {
-                uint32_t dv1[16], dv2[16];
-                tmem_ld16(tm + lane_base + 128u * (uint32_t)d + 16u * (uint32_t)part, dv1);
-                tmem_ld16(tm + lane_base + 128u * (uint32_t)d + 64u + 16u * (uint32_t)part, dv2);
+            for (int half = 0; half < 2; ++half) {  // two column groups per wait for the loads
+                uint32_t dv1[2][16], dv2[2][16];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t col = 16u * (uint32_t)(2 * half + h);
+                    tmem_ld16(tm + lane_base + 128u * (uint32_t)d + col, dv1[h]);
+                    tmem_ld16(tm + lane_base + 128u * (uint32_t)d + 64u + col, dv2[h]);
+                }
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                for (int q = 0; q < 16; ++q)
-                    acc[16 * part + q] = __fadd_rn(acc[16 * part + q],
-                                                   __fmaf_rn(__uint_as_float(dv2[q]), 1.0f / 2048.0f, __uint_as_float(dv1[q])));
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const int o = 16 * (2 * half + h) + q;
+                        acc[o] = __fadd_rn(acc[o], __fmaf_rn(__uint_as_float(dv2[h][q]), 1.0f / 2048.0f,
+                                                             __uint_as_float(dv1[h][q])));
+                    }
             }
             tc_fence_before();
             __syncwarp();
