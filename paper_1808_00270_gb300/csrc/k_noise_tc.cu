@@ -385,6 +385,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) fir_tc(const __grid_constant__ 
         // ---- converters: stage rows -> TF32 part / remainder in TMEM ------------
         const int ct = tid - 128;  // stream within the tile = TMEM lane
         const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+        int b_prev = -1;  // A buffer whose stores are still in flight
         for (long long g = 0; g < G; ++g) {
             const int c = (int)(g % nch);
             const int s = (int)(g % nst), b = (int)(g % kTcNA);
@@ -408,14 +409,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) fir_tc(const __grid_constant__ 
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);  // the stage may be loaded again
-            __syncwarp();  // converged for the aligned TMEM stores
+            __syncwarp();  // converged for the aligned TMEM operations
+            // the previous chunk's stores completed while this one was split
+            // (chunk g waited only for the MMAs of chunk g - 4)
+            if (b_prev >= 0) {
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&afull[b_prev]);
+                __syncwarp();
+            }
             const uint32_t ta = tm + lane_base + kTcAcol + 32u * (uint32_t)b;
             tmem_st16(ta, hv);
             tmem_st16(ta + 16u, lv);
+            b_prev = b;
+        }
+        __syncwarp();
+        if (b_prev >= 0) {  // uniform: every lane ran the same rounds; the stores end before TMEM is freed
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&afull[b]);
+            if (lane == 0 && !*abort_flag) mbar_arrive(&afull[b_prev]);
         }
     } else if (ok0 && warp >= 8) {
         // ---- accumulators: D -> FP32 registers, F^R at the end of a tile -------
