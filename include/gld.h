@@ -507,6 +507,9 @@ typedef struct {
     int64_t steps;        /* steps to run (>= 0) */
     double arrival;       /* server clock (s) before which it is not admitted; non-decreasing */
     int32_t keep_state;   /* also return the final positions and velocities */
+    int32_t pair_noise;   /* Chebyshev degree of the pair-correlated random force (as gld_set_pair_noise on
+                             the Gershgorin bound at the initial positions, admission counting its bytes);
+                             0: self noise only.  A kernel form it does not take fails the request. */
 } gld_request;
 enum {  /* gld_server_stats slots */
     GLD_SRV_QUEUED = 0, GLD_SRV_ACTIVE = 1, GLD_SRV_RETIRING = 2, GLD_SRV_DONE = 3, GLD_SRV_FAILED = 4,

@@ -53,7 +53,7 @@ class Request(C.Structure):
                 ("Q", C.c_int32), ("g", C.c_void_p), ("f", C.c_void_p), ("nr", C.c_int32), ("dr", C.c_double),
                 ("dKs_g", C.c_void_p), ("dKs_f", C.c_void_p), ("Qs", C.c_int32),
                 ("kernel_convention", C.c_int32), ("steps", C.c_int64), ("arrival", C.c_double),
-                ("keep_state", C.c_int32)]
+                ("keep_state", C.c_int32), ("pair_noise", C.c_int32)]
 
 
 SRV_STATS = ["queued", "active", "retiring", "done", "failed", "blocks", "particle_steps", "bytes", "bytes_peak",
@@ -569,7 +569,8 @@ class Server:
 
     def submit(self, *, n, box, dt, m_max, r_c, pos, vel, Ks, g=None, f=None, dr=1.0, gs=None, fs=None,
                discrete=False, steps, arrival=0.0, keep_state=False, mass=1.0, kT=1.0, r_c_min=0.0, A_cons=0.0,
-               skin=0.0, seed=1, hist_dtype="f32", kahan=False, vacf_len=0, vacf_stride=1, vacf_burnin=-1) -> int:
+               skin=0.0, seed=1, hist_dtype="f32", kahan=False, vacf_len=0, vacf_stride=1, vacf_burnin=-1,
+               pair_noise=0) -> int:
         L = lib()
         r = Request()
         p = r.params
@@ -602,6 +603,7 @@ class Server:
         r.dKs_f = None if fs is None else fs.ctypes.data
         r.kernel_convention = KDISCRETE if discrete else KCONT
         r.steps, r.arrival, r.keep_state = int(steps), float(arrival), int(bool(keep_state))
+        r.pair_noise = int(pair_noise)
         rid = C.c_int64()
         st = L.gld_server_submit(self._h, C.byref(r), C.byref(rid))
         del keep

@@ -700,6 +700,19 @@ size_t ctx_bytes_needed(const gld_params* p, int Q, int Qs, int nr, int num_sms)
     return total;
 }
 
+size_t pn_bytes_needed(const gld_params* p, int K)
+{
+    if (K <= 0) return 0;
+    StepParams P{};
+    int ncells = 0;
+    ctx_derive(p, P, ncells);
+    const size_t sizes[] = {4 * (size_t)(K + 1) * fir_taps_len(P.H), 4 * (size_t)K * P.T * 3 * P.n_pad,
+                            4 * 9 * (size_t)P.n_pad, 4};
+    size_t total = 0;
+    for (size_t b : sizes) total += (b + 255) & ~(size_t)255;
+    return total;
+}
+
 }  // namespace gld
 
 extern "C" {

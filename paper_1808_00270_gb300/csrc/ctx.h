@@ -118,6 +118,10 @@ void ctx_derive(const gld_params* p, StepParams& P, int& ncells);
 // Device bytes a context holds after gld_create + gld_set_kernels with Q pair
 // and Qs self-difference terms on nr table points (num_sms: of the device).
 size_t ctx_bytes_needed(const gld_params* p, int Q, int Qs, int nr, int num_sms);
+// Device bytes gld_set_pair_noise(degree K, Gershgorin bound) adds to them:
+// the K + 1 filters, the blocks Z_1 .. Z_K, the Clenshaw vectors and the
+// row-sum word.
+size_t pn_bytes_needed(const gld_params* p, int K);
 // [n][3] doubles in the caller's order from float4 rows in internal order.
 void ctx_to_caller(const gld_ctx* c, const float4* h, double* dst);
 }  // namespace gld

@@ -32,7 +32,7 @@ struct Req {
     int64_t id = 0;
     gld_params prm{};
     std::vector<double> pos, vel, Ks, g, f, gs, fs;
-    int32_t Q = 0, Qs = 0, nr = 2, conv = GLD_KCONT, keep_state = 0;
+    int32_t Q = 0, Qs = 0, nr = 2, conv = GLD_KCONT, keep_state = 0, pn_deg = 0;
     double dr = 1.0;
     int64_t steps = 0, left = 0;
     double arrival = 0, admitted = -1, done = -1;
@@ -151,6 +151,7 @@ gld_status admit(gld_server* s, Req* r)
     if (st != GLD_OK) return st;
     st = gld_set_kernels(c, r->Ks.data(), r->Q, r->Q ? r->g.data() : nullptr, r->Q ? r->f.data() : nullptr, r->nr,
                          r->dr, r->Qs ? r->gs.data() : nullptr, r->Qs ? r->fs.data() : nullptr, r->Qs, r->conv);
+    if (st == GLD_OK && r->pn_deg > 0) st = gld_set_pair_noise(c, r->pn_deg, nullptr, nullptr);
     if (st != GLD_OK) {
         r->msg = gld_last_error(c);
         gld_destroy(c);
@@ -344,7 +345,7 @@ gld_status gld_server_submit(gld_server* s, const gld_request* q, int64_t* id)
     const int M = p.m_max;
     if (!q->pos || !q->vel || !q->Ks || q->steps < 0 || p.n < 1 || M < 2 || q->Q < 0 || q->Qs < 0 ||
         (q->Q > 0 && (!q->g || !q->f)) || (q->Qs > 0 && (!q->dKs_g || !q->dKs_f)) ||
-        (q->Q + q->Qs > 0 && q->nr < 2)) {
+        (q->Q + q->Qs > 0 && q->nr < 2) || q->pair_noise < 0 || q->pair_noise > kMaxPnDegree) {
         s->msg = "gld_server_submit: invalid request";
         return GLD_E_INVAL;
     }
@@ -373,12 +374,13 @@ gld_status gld_server_submit(gld_server* s, const gld_request* q, int64_t* id)
     r->dr = q->dr;
     r->conv = q->kernel_convention;
     r->keep_state = q->keep_state;
+    r->pn_deg = q->pair_noise;
     r->steps = r->left = q->steps;
     r->arrival = q->arrival;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    r->bytes = ctx_bytes_needed(&p, q->Q, q->Qs, q->nr, sms);
+    r->bytes = ctx_bytes_needed(&p, q->Q, q->Qs, q->nr, sms) + pn_bytes_needed(&p, r->pn_deg);
     s->reqs.push_back(r);
     s->queue.push_back(r);
     if (id) *id = r->id;

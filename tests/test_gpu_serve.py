@@ -166,3 +166,84 @@ def test_cancel_and_forced_drain_timeout():
     assert st["bytes"] == 0 and st["failed"] == 2 and st["done"] == 1
     with pytest.raises(GLDError):
         s.cancel(b)  # already finished
+
+
+def _pn_plain(w, strength, degree):
+    from paper_1808_00270_gb300 import GLD, inputs
+    from gld_cases import common_kwargs
+    pos, vel = inputs.initial_state(w)
+    ks, g, f, dr = kernels(w)
+    sim = GLD(pos=pos, vel=vel, **common_kwargs(w, **VACF))
+    sim.set_kernels(ks, g=g, f=strength * f, dr=dr)
+    sim.set_pair_noise(degree)
+    return sim
+
+
+def _pn_submit(srv, w, steps, strength, degree, arrival=0.0):
+    from paper_1808_00270_gb300 import inputs
+    pos, vel = inputs.initial_state(w)
+    ks, g, f, dr = kernels(w)
+    return srv.submit(n=w.n, box=w.box, dt=w.dt, m_max=w.m_max, r_c=w.r_c, pos=pos, vel=vel, Ks=ks, g=g,
+                      f=strength * f, dr=dr, steps=steps, arrival=arrival, keep_state=True, mass=w.mass, kT=w.kT,
+                      A_cons=w.A_cons, r_c_min=w.r_c_min, seed=w.seed, pair_noise=degree, **VACF)
+
+
+def test_served_pair_noise_matches_a_plain_run():
+    """A request with the pair-correlated random force (degree 8, the pair
+    kernel at 0.3 of the workload's) integrates what a plain context with
+    gld_set_pair_noise(8) integrates, among other requests with and without
+    it (FP32 summation orders differ between the batched and the single
+    filter: the tolerances of the plain comparison)."""
+    from paper_1808_00270_gb300 import Server
+    w, steps = TARGET
+    sim = _pn_plain(w, 0.3, 8)
+    sim.step(steps)
+    c, n = sim.vacf()
+    p, v = sim.get_state()
+    s = Server()
+    others = [_submit(s, *_mix()[0]), _pn_submit(s, *_mix()[1], 0.3, 6)]
+    r = _pn_submit(s, w, steps, 0.3, 8, arrival=0.01)
+    s.drain(120)
+    out = s.result(r)
+    assert out["status"] == 0 and out["n_origins"] == n
+    assert np.max(np.abs(out["vacf"] - c)) <= 1e-4 * abs(c[0])
+    assert rel_l2(out["vel"], v) < 1e-4
+    d = out["pos"] - p
+    d -= w.box * np.round(d / w.box)
+    assert np.max(np.abs(d)) < 1e-3
+    for i in others:
+        assert s.result(i)["status"] == 0
+    # the pair noise changes the trajectory: the same request without it differs
+    s2 = Server()
+    r2 = _pn_submit(s2, w, steps, 0.3, 0)
+    s2.drain(120)
+    assert rel_l2(s2.result(r2)["vel"], v) > 1e-2
+
+
+def test_served_pair_noise_admission_counts_its_bytes():
+    """Admission counts the pair-noise buffers exactly: a budget of the bytes
+    a plain context holds after gld_set_pair_noise admits the request, one
+    byte less refuses it (GLD_E_NOMEM); a pair kernel the Gershgorin bound
+    refuses fails its request alone (GLD_E_NOT_PSD); a degree outside
+    [0, 16] is refused at submission."""
+    from paper_1808_00270_gb300 import GLDError, Server
+    from paper_1808_00270_gb300.binding import E_INVAL, E_NOMEM, E_NOT_PSD
+    w = _workload("pn_bytes", 1200, 0.1, 120, 61)
+    held = _pn_plain(w, 0.3, 10).bytes()
+    for budget, want in ((held, 0), (held - 1, E_NOMEM)):
+        s = Server(hbm_budget=budget)
+        i = _pn_submit(s, w, 70, 0.3, 10)
+        s.drain(60)
+        assert s.result(i)["status"] == want
+        if want == 0:
+            assert s.stats()["bytes_peak"] == held
+    s = Server()
+    bad = _pn_submit(s, w, 70, 1.0, 8)
+    ok = _pn_submit(s, w, 70, 0.3, 8)
+    s.drain(60)
+    assert s.result(bad)["status"] == E_NOT_PSD and s.result(ok)["status"] == 0
+    assert s.stats()["failed"] == 1 and s.stats()["bytes"] == 0
+    for deg in (-1, 17):
+        with pytest.raises(GLDError) as e:
+            _pn_submit(s, w, 70, 0.3, deg)
+        assert e.value.status == E_INVAL
