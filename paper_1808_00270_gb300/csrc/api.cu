@@ -172,6 +172,27 @@ gld_status invalidate_noise(gld_ctx* c)
     return GLD_OK;
 }
 
+// The white-noise ring holds the FP16 split form while the context steps
+// alone with the tensor-core filter, FP32 inside a batch (the batched filter
+// runs on the FP32 pipes).  A change of form clears the ring (stale values of
+// the other form need not be finite read in this one, and the tensor-core
+// filter multiplies the rows around its window by zero taps) and marks it
+// empty, so the next block generates its whole window again; the values are
+// counter-based, so nothing else changes.  Issued on stream s.
+gld_status ring_form(gld_ctx* c, bool alone, cudaStream_t s)
+{
+    const int want = alone && c->have_wmap ? 1 : 0;
+    if (c->P.wsplit == want) return GLD_OK;
+    c->P.wsplit = want;
+    invalidate_graph(c);
+    c->noise_valid = false;
+    c->conv_valid_step = -1;
+    GLD_CUDA(c, cudaMemsetAsync(c->W, 0, sizeof(float) * (size_t)c->P.lw * 3 * c->P.n_pad, s));
+    long long w[2] = {0, 1};  // {w_hi, w_lo}: empty
+    GLD_CUDA(c, cudaMemcpyAsync(&c->B.ctrl->w_hi, w, sizeof(w), cudaMemcpyHostToDevice, s));
+    return GLD_OK;
+}
+
 // Positions were replaced (pos and pos_next hold them): new lists and F^C.
 gld_status rebuild_cells_and_fc(gld_ctx* c)
 {
@@ -857,6 +878,7 @@ gld_status gld_create(const gld_params* p, const double* pos, const double* vel,
     // filter runs on the FP32 pipes when it cannot be made)
     c->have_wmap = noise_filter_tc_ok(P) && make_noise_ring_map(c->W, P, &c->wmap) == cudaSuccess;
     cudaGetLastError();
+    P.wsplit = c->have_wmap ? 1 : 0;  // the ring starts zeroed: valid in either form
     gld_status s = GLD_OK;
     if (cudaMemsetAsync(B.cell_head, 0xff, sizeof(int) * ncells, c->st) != cudaSuccess) s = GLD_E_CUDA;
     Ctrl h{};
@@ -1000,6 +1022,7 @@ gld_status gld_step(gld_ctx* c, int64_t nsteps)
     if (!c->have_kernels) return fail(c, GLD_E_STATE, "gld_step: gld_set_kernels has not succeeded");
     if (c->latched != GLD_OK) return c->latched;
     const int T = c->P.T;
+    if (nsteps > 0) GLD_TRY(ring_form(c, true, c->st));
     if (nsteps > 0) GLD_TRY(refresh_modes(c));
     while (nsteps > 0) {
         if (!c->noise_valid || c->host_step >= c->noise_end) {
@@ -1259,6 +1282,7 @@ gld_status gld_profile_steps(gld_ctx* c, int64_t nsteps, double* ms, int64_t* la
         return fail(c, GLD_E_STATE, "gld_profile_steps: not with the Lanczos pair noise (host decisions every step)");
     // untimed steps up to the next noise-block boundary
     if (c->noise_valid && c->host_step < c->noise_end) GLD_TRY(gld_step(c, c->noise_end - c->host_step));
+    GLD_TRY(ring_form(c, true, c->st));
     GLD_TRY(refresh_modes(c));
     GLD_TRY(sync_and_check(c));
     c->conv_valid_step = -1;  // the eager steps below leave no next-step projections
@@ -2278,6 +2302,7 @@ gld_status batch_plan(gld_batch* b, int schedule)
         gld_ctx* c = ms[m];
         SysDesc& d = desc[m];
         d.P = c->P;
+        d.P.wsplit = 0;  // the batched filter reads the FP32 ring
         d.B = c->B;
         d.coef = c->coef;
         d.W = c->W;
@@ -2506,6 +2531,10 @@ gld_status gld_batch_step(gld_batch* b, int64_t nsteps)
         if (!c->have_kernels) return bfail(b, GLD_E_STATE, "gld_batch_step: a member has no kernels set");
         if (c->noise_valid && c->host_step != c->noise_end)
             return bfail(b, GLD_E_STATE, "gld_batch_step: a member left its noise-block boundary");
+    }
+    for (gld_ctx* c : b->members) {
+        const gld_status st = ring_form(c, false, b->st);
+        if (st != GLD_OK) return bfail(b, st, "gld_batch_step: the white-noise ring of a member");
     }
     for (size_t m = 0; m < b->members.size() && !b->dirty; ++m)  // kernels reset since the plan
         if (m >= b->snap.size() || std::memcmp(&b->snap[m].P, &b->members[m]->P, sizeof(StepParams)) != 0 ||

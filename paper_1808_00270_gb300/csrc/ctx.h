@@ -29,8 +29,8 @@ struct gld_ctx {
     size_t bytes = 0;  // device bytes held
     ParticleBuffers B{};
     float* W = nullptr;
-    CUtensorMap wmap{};      // W as 32 x 128 tiles for the tensor-core filter
-    bool have_wmap = false;
+    CUtensorMap wmap{};      // W in split form as 32 x 64 FP16 boxes for the tensor-core filter
+    bool have_wmap = false;  // stepped alone, the ring holds the split form (P.wsplit)
     float* Acp = nullptr;
     int la = 0;
     float* coef = nullptr;

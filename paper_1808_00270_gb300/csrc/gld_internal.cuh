@@ -9,6 +9,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace gld {
@@ -95,6 +96,9 @@ struct StepParams {
     int perp;
     // pair-correlated noise by a Lanczos iteration per frequency (Algorithm 1)
     int pn_kry;
+    // the white-noise ring holds the FP16 split of each value (the form the
+    // tensor-core filter multiplies) instead of FP32
+    int wsplit;
 };
 
 // ---------------------------------------------------------------- Philox --
@@ -140,6 +144,28 @@ __device__ inline float3 gauss3(uint32_t k0, uint32_t k1, uint32_t particle, lon
     sincospif(2.0f * u01(c[1]), &s1, &c1);
     sincospif(2.0f * u01(c[3]), &s3, &c3);
     return make_float3(r01 * c1, r01 * s1, r23 * c3);
+}
+
+// White noise w as the FP16 pair the tensor-core filter multiplies:
+// hi = fp16(w), lo = fp16((w - hi) 2^11) (round to nearest each); hi + 2^-11 lo
+// is w to 2^-22 of |w|.
+__device__ __forceinline__ void split_f16(float v, unsigned short& hi, unsigned short& lo)
+{
+    const __half h = __float2half_rn(v);
+    hi = __half_as_ushort(h);
+    lo = __half_as_ushort(__float2half_rn((v - __half2float(h)) * 2048.0f));
+}
+
+// Entry idx = slot * 3 n_pad + stream of the white-noise ring, in either form:
+// FP32, or (wsplit) an FP16 plane of hi parts followed by one of lo parts.
+__device__ __forceinline__ float ring_w(const StepParams& P, const float* __restrict__ W, size_t idx)
+{
+    if (P.wsplit) {
+        const __half* h = (const __half*)W;
+        const size_t plane = (size_t)P.lw * 3 * P.n_pad;
+        return fmaf(__half2float(__ldg(h + plane + idx)), 1.0f / 2048.0f, __half2float(__ldg(h + idx)));
+    }
+    return __ldg(W + idx);
 }
 
 // ------------------------------------------------------------ geometry --

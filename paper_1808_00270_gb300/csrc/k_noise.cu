@@ -6,7 +6,8 @@
 //   A_s = inverse transform of sqrt(hat C) (Sec. II C, with 1/(2 m_max - 1)),
 //   and the integrator factors a, b of Eq. aa-bb.
 // wgen: white noise W_{i,k} from Philox4x32-10 into a ring of times, each
-//   (particle, time) drawn exactly once over the whole run.
+//   (particle, time) drawn exactly once over the whole run; FP32, or split
+//   into the FP16 parts the tensor-core filter multiplies.
 // fir:  F^R_{i,n+t} = sum_{s=-(m_max-1)}^{m_max-1} A_s W_{i,n+t+s} for a block
 //   of T = 64 steps at once (the windowed generation remarked on in Sec. II C),
 //   from a shared-memory tile of W with a sliding register window.
@@ -134,10 +135,18 @@ __device__ __forceinline__ void wgen_body(const StepParams& P, const Ctrl* __res
         long long slot = time % P.lw;
         if (slot < 0) slot += P.lw;
         const float3 z = gauss3(k0, k1, (uint32_t)__ldg(int2ext + i), time, 0u);
-        float* w = W + (size_t)slot * 3 * np + i;
-        w[0] = z.x;
-        w[np] = z.y;
-        w[2 * np] = z.z;
+        if (P.wsplit) {  // FP16 planes: hi parts, then lo parts
+            unsigned short* h = (unsigned short*)W + (size_t)slot * 3 * np + i;
+            unsigned short* l = h + (size_t)P.lw * 3 * np;
+            split_f16(z.x, h[0], l[0]);
+            split_f16(z.y, h[np], l[np]);
+            split_f16(z.z, h[2 * np], l[2 * np]);
+        } else {
+            float* w = W + (size_t)slot * 3 * np + i;
+            w[0] = z.x;
+            w[np] = z.y;
+            w[2 * np] = z.z;
+        }
     }
 }
 
@@ -303,7 +312,8 @@ cudaError_t launch_noise_block(const StepParams& P, Ctrl* ctrl, float* W, const 
     const long long streams = 3LL * P.n_pad;
     (void)la;
     if (P.T != 64) return cudaErrorInvalidValue;
-    if (wmap && noise_filter_tc_ok(P)) return launch_noise_filter_tc(P, ctrl, wmap, Acp, frblock, num_sms, st);
+    // the split ring is read by the tensor-core filter, FP32 by the FP32-pipe one
+    if (P.wsplit) return wmap ? launch_noise_filter_tc(P, ctrl, wmap, Acp, frblock, num_sms, st) : cudaErrorInvalidValue;
     const int ntaps = fir_taps_len(P.H);
     const int chunk = std::min(ntaps, kFirChunk);
     const size_t smem = fir_smem(chunk);
@@ -318,7 +328,7 @@ cudaError_t launch_noise_filter(const StepParams& P, Ctrl* ctrl, const float* W,
                                 const CUtensorMap* wmap, int num_sms, cudaStream_t st)
 {
     if (P.T != 64) return cudaErrorInvalidValue;
-    if (wmap && noise_filter_tc_ok(P)) return launch_noise_filter_tc(P, ctrl, wmap, taps, out, num_sms, st);
+    if (P.wsplit) return wmap ? launch_noise_filter_tc(P, ctrl, wmap, taps, out, num_sms, st) : cudaErrorInvalidValue;
     const int ntaps = fir_taps_len(P.H);
     const int chunk = std::min(ntaps, kFirChunk);
     const size_t smem = fir_smem(chunk);

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kFtThreads)
     long long s0 = n % lw;
     if (s0 < 0) s0 += lw;
     float acc[32];
-    const float w0 = __ldg(W + (size_t)s0 * np3 + I);
+    const float w0 = ring_w(P, W, (size_t)s0 * np3 + I);
 #pragma unroll
     for (int j = 0; j < 32; ++j) acc[j] = sine ? 0.f : w0;  // s = 0: cos 0 = 1, sin 0 = 0
     long long sp = s0 + 1 == lw ? 0 : s0 + 1, sm = s0 == 0 ? lw - 1 : s0 - 1;
@@ -83,8 +83,8 @@ __global__ void __launch_bounds__(kFtThreads)
         float a[4], b[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            a[u] = __ldg(W + (size_t)sp * np3 + I);
-            b[u] = __ldg(W + (size_t)sm * np3 + I);
+            a[u] = ring_w(P, W, (size_t)sp * np3 + I);
+            b[u] = ring_w(P, W, (size_t)sm * np3 + I);
             sp = sp + 1 == lw ? 0 : sp + 1;
             sm = sm == 0 ? lw - 1 : sm - 1;
         }
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kFtThreads)
         for (int u = 0; u < 4; ++u) term(fmaf(sg, b[u], a[u]), s + u);
     }
     for (; s <= H; ++s) {
-        term(fmaf(sg, __ldg(W + (size_t)sm * np3 + I), __ldg(W + (size_t)sp * np3 + I)), s);
+        term(fmaf(sg, ring_w(P, W, (size_t)sm * np3 + I), ring_w(P, W, (size_t)sp * np3 + I)), s);
         sp = sp + 1 == lw ? 0 : sp + 1;
         sm = sm == 0 ? lw - 1 : sm - 1;
     }

@@ -205,8 +205,10 @@ int fir_copy_len(int T, int H);
 int fir_taps_len(int H);
 
 // int2ext maps the internal index to the caller's index, which keys the noise.
-// With wmap (the ring's tensor map, make_noise_ring_map) the filter runs on
-// the tensor cores when noise_filter_tc_ok(P), else on the FP32 pipes.
+// With P.wsplit the ring holds the FP16 split of the white noise and the
+// filter runs on the tensor cores (wmap: the ring's tensor map,
+// make_noise_ring_map; required); else the ring is FP32 and the filter runs
+// on the FP32 pipes.
 cudaError_t launch_noise_block(const StepParams& P, Ctrl* ctrl, float* W, const float* Acp, int la,
                                float* frblock, unsigned long long seed, const int* int2ext,
                                const CUtensorMap* wmap, int num_sms, cudaStream_t st);
@@ -216,7 +218,8 @@ cudaError_t launch_noise_filter(const StepParams& P, Ctrl* ctrl, const float* W,
                                 const CUtensorMap* wmap, int num_sms, cudaStream_t st);
 // Tensor-core filter (k_noise_tc.cu): whether it serves these parameters
 // (64-step blocks, a ring of 32-row tiles, taps that fit shared memory), the
-// tensor map of the ring W [lw][3 n_pad] FP32 in 32 x 128 tiles, and the launch.
+// tensor map of the split ring (FP16 planes hi [lw][3 n_pad], then lo) in
+// boxes of 32 rows x 64 streams with 128-byte swizzle, and the launch.
 bool noise_filter_tc_ok(const StepParams& P);
 cudaError_t make_noise_ring_map(void* W, const StepParams& P, CUtensorMap* map);
 cudaError_t launch_noise_filter_tc(const StepParams& P, Ctrl* ctrl, const CUtensorMap* wmap, const float* taps,
