@@ -108,6 +108,35 @@ def test_batch_matches_single_system_path():
         assert rel_l2(y, x) < 1e-5
 
 
+def test_white_noise_ring_changes_form_between_batch_and_alone():
+    """Stepped alone, a context keeps its white-noise ring in the FP16 split
+    the tensor-core filter multiplies; inside a batch, in FP32 for the batched
+    filter.  Each change clears the ring and regenerates the window: F^R of
+    the first step alone after a batched block is within 1e-5 of the
+    oracle's, and after alone / batch / alone / batch / alone the state
+    matches the context stepped alone throughout (FP32 rounding)."""
+    from paper_1808_00270_gb300 import ARR_FR, Batch
+    from gld_cases import oracle_from_gpu
+    w = _mixed()[3]  # 1500 particles, m_max = 400: the tensor-core filter when alone
+    a = make_gpu(w)
+    g = make_gpu(w)
+    g.step(64)
+    for _ in range(2):
+        b = Batch()
+        b.add(g)
+        b.step(64)
+        b.sync()
+        b.remove(g)
+        ref = oracle_from_gpu(w, g)
+        g.step(1)
+        ref.step(1)
+        assert rel_l2(g.get(ARR_FR), ref.get(oracle.FR)) < 1e-5
+        g.step(63)
+    a.step(320)
+    for x, y in zip(_state(a), _state(g)):
+        assert rel_l2(y, x) < 1e-5
+
+
 def test_batch_vacf_matches_single_system():
     """The VACF accumulated inside a batch equals the one of the same system
     stepped alone (to FP32 rounding of the trajectory)."""
