@@ -666,6 +666,7 @@ void ctx_derive(const gld_params* p, StepParams& P, int& ncells)
     P.lw = ((long long)P.T + 2LL * P.H + 31 + 31) / 32 * 32;
     P.box = (float)p->box;
     P.half_box = 0.5f * P.box;
+    P.inv_box = 1.0f / P.box;
     P.inv_cell = (float)(nc / p->box);
     P.rc2 = (float)(p->r_c * p->r_c);
     P.rc_min = (float)p->r_c_min;

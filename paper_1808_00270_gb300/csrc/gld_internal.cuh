@@ -62,7 +62,7 @@ struct StepParams {
     int nc;                   // cells per dimension (1 or >= 3)
     int T;                    // noise block length
     long long lw;             // W ring length (times)
-    float box, half_box, inv_cell, rc2, rc_min, inv_dr, inv_dt;
+    float box, half_box, inv_box, inv_cell, rc2, rc_min, inv_dr, inv_dt;
     float pos_v, pos_f;       // b dt, b dt^2 / (2M)
     float vh_v, vh_fc, vh_f;  // a, a dt/(2M), b dt/M
     float vf_fc;              // dt/(2M)
@@ -189,6 +189,15 @@ __device__ inline float min_image(float a, float b, float L, float half)
     if (d > half) d = __fsub_rn(d, L);
     else if (d < -half) d = __fadd_rn(d, L);
     return d;
+}
+
+// The same without branches: d - L rint(d / L), one rounding like the
+// subtraction above, so the same bits whenever |d| is not within rounding of
+// L / 2 (every pair inside a cutoff below half the box).
+__device__ inline float min_image_fma(float a, float b, float L, float inv_L)
+{
+    const float d = __fsub_rn(a, b);
+    return fmaf(-L, rintf(__fmul_rn(d, inv_L)), d);
 }
 
 __device__ inline float dist2(float dx, float dy, float dz)

@@ -130,13 +130,13 @@ __device__ __forceinline__ void pair_force_integrate_body(const StepParams& P, C
         const float g00 = __ldg(g0);
         const int cnt = nbr_cnt[id];
         auto term = [&](int jd, float4 pj, float4 vj, float qx, float qy, float qz) {
-            const float dx = min_image(pi.x, pj.x, P.box, P.half_box);
-            const float dy = min_image(pi.y, pj.y, P.box, P.half_box);
-            const float dz = min_image(pi.z, pj.z, P.box, P.half_box);
+            const float dx = min_image_fma(pi.x, pj.x, P.box, P.inv_box);
+            const float dy = min_image_fma(pi.y, pj.y, P.box, P.inv_box);
+            const float dz = min_image_fma(pi.z, pj.z, P.box, P.inv_box);
             const float r2 = dist2(dx, dy, dz);
             if (!(r2 < P.rc2)) return;
-            const float r = sqrtf(r2);
-            const float inv_r = 1.0f / r;
+            const float inv_r = rsqrtf(r2);  // listed pairs are distinct particles: r2 > 0
+            const float r = r2 * inv_r;
             const float ex = dx * inv_r, ey = dy * inv_r, ez = dz * inv_r;
             const float x = fmaxf(r, P.rc_min) * P.inv_dr;
             const float evj = dot3(ex, ey, ez, vj.x, vj.y, vj.z);
@@ -149,14 +149,16 @@ __device__ __forceinline__ void pair_force_integrate_body(const StepParams& P, C
         };
         // lane lr takes the entries lr, lr + LANES, ...: kPairBatch of them
         // per round with all their loads in flight together
+        // (the last round is masked: entries past the list stand for the
+        // particle itself, whose loads hit cache, and add nothing)
         constexpr int NB = kPairBatch;
-        int base = lr;
-        for (; base + (NB - 1) * LANES < cnt; base += NB * LANES) {
+        for (int base = lr; base < cnt; base += NB * LANES) {
             int j[NB];
             float4 pj[NB], vj[NB];
             float qx[NB], qy[NB], qz[NB];
 #pragma unroll
-            for (int u = 0; u < NB; ++u) j[u] = __ldg(nbr + (size_t)(base + u * LANES) * P.n_pad + id);
+            for (int u = 0; u < NB; ++u)
+                j[u] = base + u * LANES < cnt ? __ldg(nbr + (size_t)(base + u * LANES) * P.n_pad + id) : id;
 #pragma unroll
             for (int u = 0; u < NB; ++u) {
                 pj[u] = __ldg(pos + j[u]);
@@ -166,11 +168,8 @@ __device__ __forceinline__ void pair_force_integrate_body(const StepParams& P, C
                 qz[u] = __ldg(pj0 + 2 * np + j[u]);
             }
 #pragma unroll
-            for (int u = 0; u < NB; ++u) term(j[u], pj[u], vj[u], qx[u], qy[u], qz[u]);
-        }
-        for (; base < cnt; base += LANES) {
-            const int jd = __ldg(nbr + (size_t)base * P.n_pad + id);
-            term(jd, __ldg(pos + jd), __ldg(vel + jd), __ldg(pj0 + jd), __ldg(pj0 + np + jd), __ldg(pj0 + 2 * np + jd));
+            for (int u = 0; u < NB; ++u)
+                if (j[u] != id) term(j[u], pj[u], vj[u], qx[u], qy[u], qz[u]);
         }
         if (LANES > 1) {  // sum over the lanes of the particle (same result in each)
             const unsigned grp = ((1u << LANES) - 1u) << ((threadIdx.x & 31) & ~(LANES - 1));

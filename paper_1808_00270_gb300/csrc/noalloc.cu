@@ -87,6 +87,7 @@ extern "C" gld_status gld_pairs_noalloc(const float* pos4, int32_t n, double box
     P.nc = nc;
     P.box = (float)box;
     P.half_box = 0.5f * P.box;
+    P.inv_box = 1.0f / P.box;
     P.inv_cell = (float)(nc / box);
     P.rc2 = (float)(r_c * r_c);
     ParticleBuffers B{};
