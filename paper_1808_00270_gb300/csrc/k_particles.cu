@@ -151,14 +151,19 @@ __device__ __forceinline__ void pair_force_integrate_body(const StepParams& P, C
         // per round with all their loads in flight together
         // (the last round is masked: entries past the list stand for the
         // particle itself, whose loads hit cache, and add nothing)
+        // (the last round is masked: entries past the list stand for the
+        // particle itself, whose loads hit cache, and add nothing; the next
+        // round's list entries load while this round's gathers are in flight)
         constexpr int NB = kPairBatch;
+        int jn[NB];
+#pragma unroll
+        for (int u = 0; u < NB; ++u) jn[u] = lr + u * LANES < cnt ? __ldg(nbr + (size_t)(lr + u * LANES) * P.n_pad + id) : id;
         for (int base = lr; base < cnt; base += NB * LANES) {
             int j[NB];
             float4 pj[NB], vj[NB];
             float qx[NB], qy[NB], qz[NB];
 #pragma unroll
-            for (int u = 0; u < NB; ++u)
-                j[u] = base + u * LANES < cnt ? __ldg(nbr + (size_t)(base + u * LANES) * P.n_pad + id) : id;
+            for (int u = 0; u < NB; ++u) j[u] = jn[u];
 #pragma unroll
             for (int u = 0; u < NB; ++u) {
                 pj[u] = __ldg(pos + j[u]);
@@ -167,6 +172,10 @@ __device__ __forceinline__ void pair_force_integrate_body(const StepParams& P, C
                 qy[u] = __ldg(pj0 + np + j[u]);
                 qz[u] = __ldg(pj0 + 2 * np + j[u]);
             }
+            const int nb = base + NB * LANES;
+#pragma unroll
+            for (int u = 0; u < NB; ++u)
+                jn[u] = nb + u * LANES < cnt ? __ldg(nbr + (size_t)(nb + u * LANES) * P.n_pad + id) : id;
 #pragma unroll
             for (int u = 0; u < NB; ++u)
                 if (j[u] != id) term(j[u], pj[u], vj[u], qx[u], qy[u], qz[u]);
@@ -618,16 +627,17 @@ __device__ __forceinline__ void cforce_body(const StepParams& P, Ctrl* __restric
             for (int u = 0; u < 4; ++u) pj[u] = __ldg(pos_next + (j[u] < 0 ? id : j[u]));
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const float dx = min_image(pi.x, pj[u].x, P.box, P.half_box);
-                const float dy = min_image(pi.y, pj[u].y, P.box, P.half_box);
-                const float dz = min_image(pi.z, pj[u].z, P.box, P.half_box);
+                const float dx = min_image_fma(pi.x, pj[u].x, P.box, P.inv_box);
+                const float dy = min_image_fma(pi.y, pj[u].y, P.box, P.inv_box);
+                const float dz = min_image_fma(pi.z, pj[u].z, P.box, P.inv_box);
                 const float r2 = dist2(dx, dy, dz);
                 if (j[u] >= 0 && r2 < P.rc2) {
-                    const float r = sqrtf(r2);
+                    const float inv_r = rsqrtf(r2);  // listed pairs are distinct particles: r2 > 0
+                    const float r = r2 * inv_r;
                     // -dU/dr e_ij with U = A (1 - r/r_c)^2, e_ij = (R_i - R_j)/r
                     // -dU/dr: a table (P.fc_nr > 0) or the soft repulsion A (1 - r/r_c)^2
                     const float sc = (P.fc_nr > 0 ? table_at(fctab, P.fc_nr, r * P.fc_inv_dr)
-                                                   : P.fc_mag * (1.0f - r * P.inv_rc)) / r;
+                                                   : P.fc_mag * (1.0f - r * P.inv_rc)) * inv_r;
                     fx = fmaf(sc, dx, fx);
                     fy = fmaf(sc, dy, fy);
                     fz = fmaf(sc, dz, fz);
