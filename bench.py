@@ -66,6 +66,8 @@ def parse():
                     help="pair-correlated random force by Algorithm 1 (a Lanczos iteration per frequency, tol 1e-6, "
                          "at most 24 vectors; eager steps): 0 every step, 1 one run per 64-step block over the time "
                          "window; the workload's full-strength pair kernel")
+    ap.add_argument("--skin", type=float, default=0.0,
+                    help="Verlet-list skin (0: the library's choice); results do not depend on it")
     ap.add_argument("--hist", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--kahan", action="store_true")
     ap.add_argument("--reference-seconds", type=float, default=120.0)
@@ -436,6 +438,8 @@ def main():
                              "pair_kernel_scale": 1.0}
     cfg.update({"global_batch": w.n * world, "parallelism": f"replicas{world}",
                 "l2": "inputs larger than L2: 1.26 GB FP32 history ring streamed every step"})
+    if args.skin > 0:
+        cfg["skin"] = args.skin
 
     if args.impl == "reference":
         if rank != 0:
@@ -464,7 +468,7 @@ def main():
     vacf = dict(vacf_len=w.m_max, vacf_stride=max(1, w.m_max // 10), vacf_burnin=2 * w.m_max)
     common = dict(n=w.n, box=w.box, mass=w.mass, kT=w.kT, dt=w.dt, m_max=w.m_max, r_c=w.r_c, A_cons=w.A_cons,
                   seed=w.seed + rank, hist_dtype=args.hist, kahan=args.kahan,
-                  use_graphs=2 if args.graph_form == "gated" else 1, **vacf)
+                  use_graphs=2 if args.graph_form == "gated" else 1, skin=args.skin, **vacf)
     sim = GLD(pos=pos, vel=vel, **common)
     sim.set_kernels(ks, g=g, f=f, dr=dr)
     if args.pcorr > 0:
