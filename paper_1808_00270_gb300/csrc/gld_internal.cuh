@@ -259,31 +259,30 @@ __device__ inline void for_each_listed(const float4 pi, const int k, const int* 
                                        const int cnt, const int stride, const float4* __restrict__ pos,
                                        const StepParams& P, F&& f)
 {
-    int s = 0;
-    for (; s + 4 <= cnt; s += 4) {
+    // four entries per round with their loads in flight together; the next
+    // round's entries load during this round's gathers, and the last round is
+    // masked (entries past the list stand for i itself, never listed)
+    int jn[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) jn[u] = u < cnt ? __ldg(nbr + (size_t)u * stride + k) : k;
+    for (int s = 0; s < cnt; s += 4) {
         int j[4];
         float4 pj[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) j[u] = __ldg(nbr + (size_t)(s + u) * stride + k);
+        for (int u = 0; u < 4; ++u) j[u] = jn[u];
 #pragma unroll
         for (int u = 0; u < 4; ++u) pj[u] = __ldg(pos + j[u]);
 #pragma unroll
+        for (int u = 0; u < 4; ++u) jn[u] = s + 4 + u < cnt ? __ldg(nbr + (size_t)(s + 4 + u) * stride + k) : k;
+#pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const float dx = min_image(pi.x, pj[u].x, P.box, P.half_box);
-            const float dy = min_image(pi.y, pj[u].y, P.box, P.half_box);
-            const float dz = min_image(pi.z, pj[u].z, P.box, P.half_box);
+            if (j[u] == k) continue;
+            const float dx = min_image_fma(pi.x, pj[u].x, P.box, P.inv_box);
+            const float dy = min_image_fma(pi.y, pj[u].y, P.box, P.inv_box);
+            const float dz = min_image_fma(pi.z, pj[u].z, P.box, P.inv_box);
             const float r2 = dist2(dx, dy, dz);
             if (r2 < P.rc2) f(j[u], dx, dy, dz, r2);
         }
-    }
-    for (; s < cnt; ++s) {
-        const int j = __ldg(nbr + (size_t)s * stride + k);
-        const float4 pj = __ldg(pos + j);
-        const float dx = min_image(pi.x, pj.x, P.box, P.half_box);
-        const float dy = min_image(pi.y, pj.y, P.box, P.half_box);
-        const float dz = min_image(pi.z, pj.z, P.box, P.half_box);
-        const float r2 = dist2(dx, dy, dz);
-        if (r2 < P.rc2) f(j, dx, dy, dz, r2);
     }
 }
 
