@@ -1,7 +1,7 @@
 """The colored-noise filter on the tensor cores (needs a GPU): F^R of Eq.
 noise_production against the FP64 oracle's direct sum for windows that start
-at every offset within a 32-row tile (including blocks that start before the
-memory window is filled, n0 < m_max - 1), for stream counts that leave a
+at offsets spread over the filter's 64-row accumulation groups (including
+blocks that start before the memory window is filled, n0 < m_max - 1), for stream counts that leave a
 partial last tile, and for memory lengths from 32 to 1000; and F^R of a given
 time does not depend on where its 64-step block started (the result of a
 checkpointed run does not depend on where it was resumed)."""
@@ -37,7 +37,7 @@ def _w(n, m_max, rho=0.1, seed=7):
 @pytest.mark.parametrize("n,m_max,rho", [(1500, 400, 0.2), (77, 32, 0.1), (4096, 200, 0.1), (500, 1000, 0.1)])
 def test_filter_matches_oracle_at_window_offsets(n, m_max, rho):
     """One step's F^R within 1e-5 of the oracle after set_step to steps whose
-    window start n0 - (m_max - 1) falls at different offsets of a 32-row tile."""
+    window start n0 - (m_max - 1) falls at different offsets of a 64-row group."""
     from paper_1808_00270_gb300 import ARR_FR
     w = _w(n, m_max, rho)
     g = make_gpu(w)
