@@ -130,11 +130,10 @@ __device__ __forceinline__ void wgen_body(const StepParams& P, const Ctrl* __res
     const long long np = P.n_pad;
     const int i = blk * blockDim.x + threadIdx.x;
     if (i >= P.n) return;
-    for (long long kk = blockIdx.y; kk < count; kk += gridDim.y) {
-        const long long time = lo + kk;
+    const uint32_t ext = (uint32_t)__ldg(int2ext + i);
+    auto put = [&](long long time, float3 z) {
         long long slot = time % P.lw;
         if (slot < 0) slot += P.lw;
-        const float3 z = gauss3(k0, k1, (uint32_t)__ldg(int2ext + i), time, 0u);
         if (P.wsplit) {  // FP16 planes: hi parts, then lo parts
             unsigned short* h = (unsigned short*)W + (size_t)slot * 3 * np + i;
             unsigned short* l = h + (size_t)P.lw * 3 * np;
@@ -147,6 +146,15 @@ __device__ __forceinline__ void wgen_body(const StepParams& P, const Ctrl* __res
             w[np] = z.y;
             w[2 * np] = z.z;
         }
+    };
+    // two independent draws per round (times kk and kk + gridDim.y), so that
+    // their Philox rounds and transcendental functions overlap
+    for (long long kk = blockIdx.y; kk < count; kk += 2LL * gridDim.y) {
+        const long long kk2 = kk + gridDim.y;
+        const float3 z0 = gauss3(k0, k1, ext, lo + kk, 0u);
+        const float3 z1 = gauss3(k0, k1, ext, lo + (kk2 < count ? kk2 : kk), 0u);
+        put(lo + kk, z0);
+        if (kk2 < count) put(lo + kk2, z1);
     }
 }
 
@@ -307,7 +315,7 @@ cudaError_t launch_noise_block(const StepParams& P, Ctrl* ctrl, float* W, const 
                                cudaStream_t st)
 {
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    dim3 g((P.n + kGenThreads - 1) / kGenThreads, (unsigned)P.T);
+    dim3 g((P.n + kGenThreads - 1) / kGenThreads, (unsigned)(P.T / 2));  // two times per thread and round
     wgen<<<g, kGenThreads, 0, st>>>(P, ctrl, W, k0, k1, int2ext);
     const long long streams = 3LL * P.n_pad;
     (void)la;
@@ -356,7 +364,7 @@ cudaError_t launch_batch_noise(const BatchPlan& bp, cudaStream_t st)
     static_assert(kGenThreads == kBatchPartBlock, "white-noise tiles use the particle tiles");
     static_assert(kFirStreams == kBatchFirStreams, "filter tiles");
     if (!bp.n_part || !bp.n_fir) return cudaSuccess;
-    dim3 g((unsigned)bp.n_part, 64u);
+    dim3 g((unsigned)bp.n_part, 32u);  // two times per thread and round
     b_wgen<<<g, kGenThreads, 0, st>>>(bp.desc, bp.part);
     const int chunk = std::min(bp.max_ntaps, kFirChunk);
     const size_t smem = fir_smem(chunk);
